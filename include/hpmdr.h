@@ -1,0 +1,178 @@
+/*
+ * hpmdr.h - C ABI of the GB300 (sm_103a) progressive data refactoring library.
+ *
+ * Method: HP-MDR (arXiv 2505.00227).  A field is decomposed into multilevel
+ * coefficients (Sec. 3), each level is aligned to its maximum exponent and
+ * split into bitplanes (Sec. 4, Algorithm 1), every four bitplanes are merged
+ * and stored with Huffman, RLE or direct copy (Sec. 5, Algorithm 2), and a
+ * retrieval fetches only the bitplane groups needed for an L-infinity or QoI
+ * error bound (Sec. 3, Sec. 6.2, Algorithm 3), incrementally over earlier
+ * retrievals of the same handle.
+ *
+ * Conventions
+ *   - Every call returns an hpmdr_status; nothing else crosses the boundary.
+ *   - Arrays are C order, dims[0] slowest (z), dims[2] fastest (x); a 1D or 2D
+ *     field passes ndims = 1 or 2 and its sizes in the last entries.
+ *   - "on_device" flags tell whether a pointer is CUDA device memory (1) or
+ *     host memory (0).  Host memory may be pageable or pinned.
+ *   - The caller owns every input and output buffer.  The library owns
+ *     contexts, handles and everything they hold; views stay valid until the
+ *     owning object is freed.
+ *   - All GPU work is ordered on the context's CUDA stream.  A call returns
+ *     when its results are complete (output buffers written, info filled).
+ *   - No call falls back to the CPU: without a usable sm_103a device every
+ *     compute call returns HPMDR_ERR_CUDA.
+ */
+#ifndef HPMDR_H
+#define HPMDR_H
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HPMDR_API __attribute__((visibility("default")))
+#else
+#define HPMDR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HPMDR_OK = 0,
+  HPMDR_ERR_ARG = -1,           /* bad argument, unsupported shape or value range */
+  HPMDR_ERR_NOMEM = -2,         /* an allocation failed or the budget is spent */
+  HPMDR_ERR_CUDA = -3,          /* a CUDA call failed (message: hpmdr_last_error) */
+  HPMDR_ERR_CORRUPT = -4,       /* stored bytes failed a bounds or format check */
+  HPMDR_ERR_UNATTAINABLE = -5,  /* even all bitplanes cannot meet the bound */
+  HPMDR_ERR_TIMEOUT = -6,       /* a bounded device or host wait gave up */
+  HPMDR_ERR_BUSY = -7           /* request not finished yet (serving) */
+} hpmdr_status;
+
+typedef enum { HPMDR_F32 = 0, HPMDR_F64 = 1 } hpmdr_dtype;
+
+/* storage method of a merged bitplane group (Sec. 5.1); non-leading planes of
+ * a group hold a placeholder entry (Algorithm 2) */
+typedef enum { HPMDR_DC = 0, HPMDR_HUFFMAN = 1, HPMDR_RLE = 2, HPMDR_PLACEHOLDER = 3 } hpmdr_method;
+
+/* Optional allocator hook for device memory.  alloc returns device memory
+ * usable on `stream`, or NULL; free releases it after work on `stream`. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, void* stream, void* user);
+  void* user;
+} hpmdr_allocator;
+
+/* Parameters of Algorithm 2 (Sec. 5.2).  Zero fields take the defaults:
+ * group_m = 4 planes, size_threshold T_s = 4096 bytes, compression-ratio
+ * threshold T_cr = cr_num/cr_den = 2/1.  T_cr must be >= 1. */
+typedef struct {
+  int group_m;              /* only 4 is supported */
+  uint64_t size_threshold;  /* T_s: groups of S <= T_s bytes are copied */
+  uint32_t cr_num, cr_den;  /* T_cr = cr_num / cr_den */
+  uint64_t reserved[4];
+} hpmdr_config;
+
+typedef struct hpmdr_ctx hpmdr_ctx;        /* stream, allocator, workspace */
+typedef struct hpmdr_handle hpmdr_handle;  /* one refactored field + retrieval state */
+
+typedef struct {
+  double est_linf;              /* rigorous L-infinity bound of this reconstruction */
+  double requested_abs;         /* the absolute bound that was asked for */
+  uint64_t est_units_hi, est_units_lo;  /* est_linf exactly, in units of 2^(E_f-51-B) */
+  uint64_t bytes_fetched_total; /* stored bytes of all groups fetched so far */
+  uint64_t bytes_fetched_new;   /* stored bytes fetched by this call */
+  int groups_per_level[64];     /* bitplane groups used per level (level 0 = root) */
+  int nlevels;
+  int status;                   /* HPMDR_OK or HPMDR_ERR_UNATTAINABLE */
+} hpmdr_retrieve_info;
+
+/* ---- context ------------------------------------------------------------ */
+/* cfg and alloc may be NULL (defaults; stream-ordered CUDA pool allocation).
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream). */
+HPMDR_API hpmdr_status hpmdr_ctx_create(hpmdr_ctx** ctx, const hpmdr_config* cfg,
+                              const hpmdr_allocator* alloc, void* cuda_stream);
+HPMDR_API void hpmdr_ctx_destroy(hpmdr_ctx* ctx);
+HPMDR_API hpmdr_status hpmdr_ctx_set_stream(hpmdr_ctx* ctx, void* cuda_stream);
+
+/* ---- refactor (Sec. 3 pipeline: decompose, align + Algorithm 1, Algorithm 2)
+ * field: N = prod(dims) values of dtype; dims[d] >= 1, N < 2^32.
+ * Values must be finite with max|f| < 2^121 (F32) or in [2^-1001, 2^1017)
+ * (F64, or an all-zero field); otherwise HPMDR_ERR_ARG.
+ * On success *out is a new handle (free with hpmdr_handle_free). */
+HPMDR_API hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int field_on_device, int ndims,
+                            const uint64_t dims[3], hpmdr_dtype dtype, hpmdr_handle** out);
+
+/* ---- retrieve (Sec. 3 "error control", Algorithm 3's copy_to_device/recompose)
+ * Reconstructs the whole field into `out` (N values of the handle's dtype)
+ * from the shortest prefix of the handle's greedy group sequence whose error
+ * estimate meets the bound.  Only groups not fetched by an earlier call on
+ * this handle are decoded (incremental).  rel_linf_bound is relative to the
+ * value range max(f) - min(f); hpmdr_retrieve_abs takes an absolute bound.
+ * Returns HPMDR_ERR_UNATTAINABLE, with the best reconstruction written and
+ * info filled, when all groups together cannot meet the bound.  info may be NULL. */
+HPMDR_API hpmdr_status hpmdr_retrieve(hpmdr_ctx* ctx, hpmdr_handle* h, double rel_linf_bound, void* out,
+                            int out_on_device, hpmdr_retrieve_info* info);
+HPMDR_API hpmdr_status hpmdr_retrieve_abs(hpmdr_ctx* ctx, hpmdr_handle* h, double abs_linf_bound, void* out,
+                                int out_on_device, hpmdr_retrieve_info* info);
+
+/* ---- QoI retrieval (Sec. 6.2, Algorithm 3) for the velocity magnitude
+ * |v| = sqrt(vx^2 + vy^2 + vz^2) of three FP32 handles of equal shape.
+ * rel_qoi_bound is relative to max|v| - min|v| of the refactored data.
+ * Writes the three components (out[c], may be NULL) and |v| (out_vmag).
+ * info[0..2] describe the components, info[3] the QoI (est_linf = QoI bound). */
+HPMDR_API hpmdr_status hpmdr_qoi_prepare_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[3], const void* vx,
+                                    const void* vy, const void* vz, int on_device);
+HPMDR_API hpmdr_status hpmdr_retrieve_qoi_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[3], double rel_qoi_bound,
+                                     void* out[3], void* out_vmag, int on_device,
+                                     hpmdr_retrieve_info info[4]);
+
+/* ---- handle inspection -------------------------------------------------- */
+HPMDR_API hpmdr_status hpmdr_handle_field_info(const hpmdr_handle* h, int* dtype, uint64_t dims[3],
+                                     int* nlevels, int* E_f, int* input_exact,
+                                     double stats[4] /* max|f|, min, max, range */);
+HPMDR_API hpmdr_status hpmdr_handle_level_info(const hpmdr_handle* h, int level, uint64_t* n, int* bl,
+                                     int* ngroups, int* exact);
+/* stored bytes of one group copied to host `buf` (NULL: only *len); method
+ * and the Huffman / RLE size estimates of Sec. 5.2 (est may be NULL) */
+HPMDR_API hpmdr_status hpmdr_handle_group(const hpmdr_handle* h, int level, int group, void* buf,
+                                uint64_t* len, int* method, uint64_t est[2]);
+/* the level's (B+1) bitplanes as produced by Algorithm 1 (host copy) */
+HPMDR_API hpmdr_status hpmdr_handle_planes(const hpmdr_handle* h, int level, void* buf, uint64_t* len);
+/* the tau-independent greedy group sequence (level index per step) */
+HPMDR_API hpmdr_status hpmdr_handle_sequence(const hpmdr_handle* h, int* seq, int cap, int* len);
+/* serialized handle (stored groups + metadata); buf NULL: *len = size needed */
+HPMDR_API hpmdr_status hpmdr_handle_export(const hpmdr_handle* h, void* buf, uint64_t* len);
+HPMDR_API hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uint64_t len,
+                                 hpmdr_handle** out);
+/* forget the fetched groups; poison != 0 also overwrites the device copies of
+ * Huffman/RLE groups so that the next retrieval must decode them again */
+HPMDR_API hpmdr_status hpmdr_handle_reset(hpmdr_ctx* ctx, hpmdr_handle* h, int poison);
+HPMDR_API void hpmdr_handle_free(hpmdr_handle* h);
+
+/* ---- stage entry points (device pointers, ordered on `stream`) ---------- */
+/* Algorithm 1 on one level: q holds n aligned integers (uint32 for B = 32,
+ * uint64 for B = 64), sign n bytes (0/1).  planes receives (B+1) planes of
+ * 4*ceil(n/128) uint32 words: plane 0 = sign, plane 1+p = bit B-1-p; element
+ * j at word j>>5, bit j&31; padding bits zero. */
+HPMDR_API hpmdr_status hpmdr_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int B,
+                                   uint32_t* planes, void* stream);
+/* inverse: keeps the top k magnitude planes (k = 0..B); sign_out gets the
+ * sign plane when k > 0, else zeros */
+HPMDR_API hpmdr_status hpmdr_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, void* q_out,
+                                   uint8_t* sign_out, void* stream);
+/* Algorithm 2 on one byte group G (device memory, S bytes): force = -1 picks the
+ * method as Algorithm 2 does, else HPMDR_DC / HPMDR_HUFFMAN / HPMDR_RLE.
+ * out (device) needs cap bytes; *len receives the stored length. */
+HPMDR_API hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uint64_t S, int force,
+                                uint8_t* out, uint64_t cap, uint64_t* len, int* method);
+HPMDR_API hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, uint64_t len, int method,
+                                uint8_t* G, uint64_t S);
+
+HPMDR_API const char* hpmdr_strerror(hpmdr_status s);
+HPMDR_API const char* hpmdr_last_error(void);  /* text of the last CUDA failure on this thread */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -48,6 +48,8 @@ def lib():
             "or_fixed_point": (C.c_int64, [cvp, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_int)]),
             "or_level_coeffs": (None, [cvp, dims_t, C.c_int, C.c_int, C.c_int, vp]),
             "or_bitlen_max": (C.c_int, [vp, C.c_uint64]),
+            "or_level_bitlen": (C.c_int, [cvp, dims_t, C.c_int, C.c_int, C.c_int]),
+            "or_node_coeff": (C.c_int64, [cvp, dims_t, C.c_int, C.c_int, C.c_int, C.c_uint64]),
             "or_quantize": (None, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp]),
             "or_level_exact": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int]),
             "or_bitplane_encode": (None, [vp, vp, C.c_uint64, C.c_int, vp]),
@@ -146,6 +148,16 @@ def level_coeffs(f, E_f, l):
     out = np.zeros(n, dtype=np.int64)
     lib().or_level_coeffs(_p(f), _dims(f.shape), _dtype_code(f), E_f, l, _p(out))
     return out
+
+
+def level_bitlen(f, E_f, l):
+    f = np.ascontiguousarray(f)
+    return lib().or_level_bitlen(_p(f), _dims(f.shape), _dtype_code(f), E_f, l)
+
+
+def node_coeff(f, E_f, l, j):
+    f = np.ascontiguousarray(f)
+    return int(lib().or_node_coeff(_p(f), _dims(f.shape), _dtype_code(f), E_f, l, j))
 
 
 def bitlen_max(C8):
@@ -249,6 +261,16 @@ def rle_estimate(G):
 
 def hybrid_cfg(Ts=4096, cr_num=2, cr_den=1):
     return HybridCfg(Ts, cr_num, cr_den)
+
+
+def hybrid_encode(G, Ts=4096, cr_num=2, cr_den=1):
+    G = np.ascontiguousarray(G, dtype=np.uint8)
+    cfg = hybrid_cfg(Ts, cr_num, cr_den)
+    m = C.c_int()
+    n = lib().or_hybrid_encode(_p(G), G.size, C.byref(cfg), C.byref(m), None)
+    out = np.zeros(n, dtype=np.uint8)
+    lib().or_hybrid_encode(_p(G), G.size, C.byref(cfg), C.byref(m), _p(out))
+    return out, m.value
 
 
 def hybrid_choose(S, est_H, est_R, cfg=None):

@@ -1,0 +1,330 @@
+"""Thin ctypes binding of the C ABI in ``include/hpmdr.h``.
+
+Only argument marshalling happens here: every step of refactoring and
+retrieval runs in the sm_103a kernels of ``libhpmdr.so``.  PyTorch supplies
+device memory (tensors) and the CUDA stream.  If the shared library has not
+been built, importing the binding raises; there is no fallback.
+"""
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhpmdr.so")
+
+OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_CORRUPT, ERR_UNATTAINABLE, ERR_TIMEOUT, ERR_BUSY = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+F32, F64 = 0, 1
+DC, HUFFMAN, RLE, PLACEHOLDER = 0, 1, 2, 3
+
+
+class Config(C.Structure):
+    _fields_ = [("group_m", C.c_int), ("size_threshold", C.c_uint64), ("cr_num", C.c_uint32),
+                ("cr_den", C.c_uint32), ("reserved", C.c_uint64 * 4)]
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)),
+                ("free", C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)),
+                ("user", C.c_void_p)]
+
+
+class RetrieveInfo(C.Structure):
+    _fields_ = [("est_linf", C.c_double), ("requested_abs", C.c_double),
+                ("est_units_hi", C.c_uint64), ("est_units_lo", C.c_uint64),
+                ("bytes_fetched_total", C.c_uint64), ("bytes_fetched_new", C.c_uint64),
+                ("groups_per_level", C.c_int * 64), ("nlevels", C.c_int), ("status", C.c_int)]
+
+    @property
+    def groups(self):
+        return list(self.groups_per_level[: self.nlevels])
+
+    @property
+    def est_units(self):
+        return (self.est_units_hi << 64) | self.est_units_lo
+
+
+class HpmdrError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.hpmdr_strerror(status).decode() if _lib else str(status)
+        detail = _lib.hpmdr_last_error().decode() if _lib else ""
+        super().__init__(f"{where}: {msg} ({status}) {detail}".strip())
+
+
+_lib = None
+vp = C.c_void_p
+u64p = C.POINTER(C.c_uint64)
+ip = C.POINTER(C.c_int)
+
+_SIGS = {
+    "hpmdr_ctx_create": (C.c_int, [C.POINTER(vp), C.POINTER(Config), C.POINTER(Allocator), vp]),
+    "hpmdr_ctx_destroy": (None, [vp]),
+    "hpmdr_ctx_set_stream": (C.c_int, [vp, vp]),
+    "hpmdr_refactor": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_uint64 * 3, C.c_int, C.POINTER(vp)]),
+    "hpmdr_retrieve": (C.c_int, [vp, vp, C.c_double, vp, C.c_int, C.POINTER(RetrieveInfo)]),
+    "hpmdr_retrieve_abs": (C.c_int, [vp, vp, C.c_double, vp, C.c_int, C.POINTER(RetrieveInfo)]),
+    "hpmdr_qoi_prepare_vmag": (C.c_int, [vp, vp * 3, vp, vp, vp, C.c_int]),
+    "hpmdr_retrieve_qoi_vmag": (C.c_int, [vp, vp * 3, C.c_double, vp * 3, vp, C.c_int,
+                                          RetrieveInfo * 4]),
+    "hpmdr_handle_field_info": (C.c_int, [vp, ip, C.c_uint64 * 3, ip, ip, ip, C.c_double * 4]),
+    "hpmdr_handle_level_info": (C.c_int, [vp, C.c_int, u64p, ip, ip, ip]),
+    "hpmdr_handle_group": (C.c_int, [vp, C.c_int, C.c_int, vp, u64p, ip, C.c_uint64 * 2]),
+    "hpmdr_handle_planes": (C.c_int, [vp, C.c_int, vp, u64p]),
+    "hpmdr_handle_sequence": (C.c_int, [vp, ip, C.c_int, ip]),
+    "hpmdr_handle_export": (C.c_int, [vp, vp, u64p]),
+    "hpmdr_handle_import": (C.c_int, [vp, vp, C.c_uint64, C.POINTER(vp)]),
+    "hpmdr_handle_reset": (C.c_int, [vp, vp, C.c_int]),
+    "hpmdr_handle_free": (None, [vp]),
+    "hpmdr_bitplane_encode": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, vp]),
+    "hpmdr_bitplane_decode": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp, vp]),
+    "hpmdr_encode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64, u64p, ip]),
+    "hpmdr_decode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64]),
+    "hpmdr_strerror": (C.c_char_p, [C.c_int]),
+    "hpmdr_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2505_00227_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status, where, allow=()):
+    if status != OK and status not in allow:
+        raise HpmdrError(status, where)
+    return status
+
+
+def _dims3(shape):
+    s = tuple(int(x) for x in shape)
+    if not 1 <= len(s) <= 3:
+        raise ValueError("1 to 3 dimensions")
+    full = (1,) * (3 - len(s)) + s
+    return len(s), (C.c_uint64 * 3)(*full)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return vp(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+# ------------------------------------------------------------------ objects
+class Context:
+    """hpmdr_ctx bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, size_threshold=0, cr_num=0, cr_den=0, stream=None):
+        cfg = Config(4, size_threshold, cr_num, cr_den)
+        self._p = vp()
+        _check(lib().hpmdr_ctx_create(C.byref(self._p), C.byref(cfg), None, _stream_ptr(stream)),
+               "hpmdr_ctx_create")
+
+    def set_stream(self, stream):
+        _check(lib().hpmdr_ctx_set_stream(self._p, _stream_ptr(stream)), "hpmdr_ctx_set_stream")
+
+    def close(self):
+        if self._p:
+            lib().hpmdr_ctx_destroy(self._p)
+            self._p = vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- refactor / retrieve ------------------------------------------------
+    def refactor(self, field):
+        """field: torch tensor (CUDA or CPU), float32/float64, 1-3 dims, contiguous."""
+        import torch
+        if not field.is_contiguous():
+            raise ValueError("field must be contiguous")
+        nd, dims = _dims3(field.shape)
+        out = vp()
+        _check(lib().hpmdr_refactor(self._p, vp(field.data_ptr()), int(field.is_cuda), nd, dims,
+                                    _dtype_code(field), C.byref(out)), "hpmdr_refactor")
+        return Handle(self, out, tuple(field.shape), field.dtype)
+
+    def import_handle(self, blob):
+        buf = (C.c_uint8 * len(blob)).from_buffer_copy(bytes(blob))
+        out = vp()
+        _check(lib().hpmdr_handle_import(self._p, buf, len(blob), C.byref(out)), "hpmdr_handle_import")
+        h = Handle(self, out, None, None)
+        h._fill_shape()
+        return h
+
+    def retrieve_qoi_vmag(self, handles, rel_bound, outs=None, out_vmag=None):
+        """handles: three FP32 Handles; outs: three tensors or None; returns (vmag, infos)."""
+        import torch
+        ref = handles[0]
+        dev = outs[0].is_cuda if outs is not None and outs[0] is not None else True
+        if out_vmag is None:
+            out_vmag = torch.empty(ref.shape, dtype=torch.float32,
+                                   device="cuda" if dev else "cpu")
+        arr = (vp * 3)(*[h._p for h in handles])
+        oarr = (vp * 3)(*[(vp(o.data_ptr()) if o is not None else None) for o in (outs or [None] * 3)])
+        infos = (RetrieveInfo * 4)()
+        st = lib().hpmdr_retrieve_qoi_vmag(self._p, arr, float(rel_bound), oarr,
+                                           vp(out_vmag.data_ptr()), int(out_vmag.is_cuda), infos)
+        _check(st, "hpmdr_retrieve_qoi_vmag", allow=(ERR_UNATTAINABLE,))
+        return out_vmag, list(infos), st
+
+    def prepare_vmag(self, handles, vx, vy, vz):
+        arr = (vp * 3)(*[h._p for h in handles])
+        _check(lib().hpmdr_qoi_prepare_vmag(self._p, arr, vp(vx.data_ptr()), vp(vy.data_ptr()),
+                                            vp(vz.data_ptr()), int(vx.is_cuda)),
+               "hpmdr_qoi_prepare_vmag")
+
+    # ---- stage entry points ---------------------------------------------------
+    def encode_group(self, G, force=-1, cap=None):
+        import torch
+        cap = cap if cap is not None else G.numel() * 2 + 4096
+        out = torch.empty(cap, dtype=torch.uint8, device=G.device)
+        ln, m = C.c_uint64(0), C.c_int(0)
+        _check(lib().hpmdr_encode_group(self._p, vp(G.data_ptr()), G.numel(), force,
+                                        vp(out.data_ptr()), cap, C.byref(ln), C.byref(m)),
+               "hpmdr_encode_group")
+        return out[: ln.value], m.value
+
+    def decode_group(self, data, method, S):
+        import torch
+        G = torch.empty(S, dtype=torch.uint8, device=data.device)
+        st = lib().hpmdr_decode_group(self._p, vp(data.data_ptr()), data.numel(), method,
+                                      vp(G.data_ptr()), S)
+        return st, G
+
+
+class Handle:
+    """One refactored field (hpmdr_handle) and its incremental retrieval state."""
+
+    def __init__(self, ctx, p, shape, dtype):
+        self.ctx, self._p, self.shape, self.dtype = ctx, p, shape, dtype
+
+    def _fill_shape(self):
+        import torch
+        info = self.field_info()
+        self.shape = tuple(int(d) for d in info["dims"])
+        self.dtype = torch.float32 if info["dtype"] == F32 else torch.float64
+
+    def free(self):
+        if self._p:
+            lib().hpmdr_handle_free(self._p)
+            self._p = vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def retrieve(self, bound, out=None, absolute=False):
+        """Reconstruct into `out` (allocated on the GPU if None).  Returns (out, info, status)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        info = RetrieveInfo()
+        fn = lib().hpmdr_retrieve_abs if absolute else lib().hpmdr_retrieve
+        st = fn(self.ctx._p, self._p, float(bound), vp(out.data_ptr()), int(out.is_cuda),
+                C.byref(info))
+        _check(st, "hpmdr_retrieve", allow=(ERR_UNATTAINABLE,))
+        return out, info, st
+
+    def field_info(self):
+        dt, nl, ef, ie = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        dims = (C.c_uint64 * 3)()
+        stats = (C.c_double * 4)()
+        _check(lib().hpmdr_handle_field_info(self._p, C.byref(dt), dims, C.byref(nl), C.byref(ef),
+                                             C.byref(ie), stats), "hpmdr_handle_field_info")
+        return {"dtype": dt.value, "dims": list(dims), "nlevels": nl.value, "E_f": ef.value,
+                "input_exact": bool(ie.value), "maxabs": stats[0], "vmin": stats[1],
+                "vmax": stats[2], "range": stats[3]}
+
+    def level_info(self, level):
+        n, bl, ng, ex = C.c_uint64(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().hpmdr_handle_level_info(self._p, level, C.byref(n), C.byref(bl), C.byref(ng),
+                                             C.byref(ex)), "hpmdr_handle_level_info")
+        return n.value, bl.value, ng.value, bool(ex.value)
+
+    def group(self, level, group):
+        """(stored bytes as a numpy uint8 array, method, (est_H, est_R))"""
+        import numpy as np
+        ln, m = C.c_uint64(), C.c_int()
+        est = (C.c_uint64 * 2)()
+        _check(lib().hpmdr_handle_group(self._p, level, group, None, C.byref(ln), C.byref(m), est),
+               "hpmdr_handle_group")
+        buf = np.zeros(ln.value, dtype=np.uint8)
+        _check(lib().hpmdr_handle_group(self._p, level, group, buf.ctypes.data_as(vp), C.byref(ln),
+                                        C.byref(m), est), "hpmdr_handle_group")
+        return buf, m.value, (int(est[0]), int(est[1]))
+
+    def planes(self, level):
+        import numpy as np
+        ln = C.c_uint64()
+        _check(lib().hpmdr_handle_planes(self._p, level, None, C.byref(ln)), "hpmdr_handle_planes")
+        buf = np.zeros(ln.value // 4, dtype=np.uint32)
+        _check(lib().hpmdr_handle_planes(self._p, level, buf.ctypes.data_as(vp), C.byref(ln)),
+               "hpmdr_handle_planes")
+        return buf
+
+    def sequence(self):
+        n = C.c_int()
+        _check(lib().hpmdr_handle_sequence(self._p, None, 0, C.byref(n)), "hpmdr_handle_sequence")
+        arr = (C.c_int * max(n.value, 1))()
+        _check(lib().hpmdr_handle_sequence(self._p, arr, n.value, C.byref(n)), "hpmdr_handle_sequence")
+        return list(arr[: n.value])
+
+    def export(self):
+        ln = C.c_uint64()
+        _check(lib().hpmdr_handle_export(self._p, None, C.byref(ln)), "hpmdr_handle_export")
+        buf = (C.c_uint8 * ln.value)()
+        _check(lib().hpmdr_handle_export(self._p, buf, C.byref(ln)), "hpmdr_handle_export")
+        return bytes(buf)
+
+    def reset(self, poison=False):
+        _check(lib().hpmdr_handle_reset(self.ctx._p, self._p, int(poison)), "hpmdr_handle_reset")
+
+
+def bitplane_encode(q, sign, B, stream=None):
+    """q: CUDA int32/int64 tensor viewed as uint32/uint64 bits; sign: uint8 tensor."""
+    import torch
+    n = q.numel()
+    W = 4 * ((n + 127) // 128)
+    planes = torch.empty((B + 1) * W, dtype=torch.int32, device=q.device)
+    _check(lib().hpmdr_bitplane_encode(vp(q.data_ptr()), vp(sign.data_ptr()), n, B,
+                                       vp(planes.data_ptr()), _stream_ptr(stream)),
+           "hpmdr_bitplane_encode")
+    return planes
+
+
+def bitplane_decode(planes, n, B, k, stream=None):
+    import torch
+    q = torch.empty(n, dtype=torch.int32 if B == 32 else torch.int64, device=planes.device)
+    s = torch.empty(n, dtype=torch.uint8, device=planes.device)
+    _check(lib().hpmdr_bitplane_decode(vp(planes.data_ptr()), n, B, k, vp(q.data_ptr()),
+                                       vp(s.data_ptr()), _stream_ptr(stream)),
+           "hpmdr_bitplane_decode")
+    return q, s

@@ -1,0 +1,171 @@
+// Device helpers shared by the sm_103a kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+#define HP_FULL 0xffffffffu
+
+namespace hp {
+
+// ---------------------------------------------------------------- division
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) l++;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s = l;  // shifts derived from l: s1 = min(l,1), s2 = max(l-1,0)
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  uint32_t t = __umulhi(f.m, n);
+  uint32_t s1 = f.s ? 1u : 0u, s2 = f.s ? f.s - 1u : 0u;
+  return (t + ((n - t) >> s1)) >> s2;
+}
+
+// --------------------------------------------------------- bit transposition
+// In-register 32x32 bit-matrix transpose: on return a[c] bit r = old a[r] bit c.
+// Recursive off-diagonal block swap at scales 16, 8, 4, 2, 1.
+__device__ __forceinline__ void transpose32(uint32_t a[32]) {
+#define HP_TSTAGE(S, M)                                            \
+  _Pragma("unroll") for (int i = 0; i < 32; i++) {                \
+    if ((i & S) == 0) {                                            \
+      uint32_t t = ((a[i] >> S) ^ a[i + S]) & (M);                 \
+      a[i + S] ^= t;                                               \
+      a[i] ^= t << S;                                              \
+    }                                                              \
+  }
+  HP_TSTAGE(16, 0x0000FFFFu)
+  HP_TSTAGE(8, 0x00FF00FFu)
+  HP_TSTAGE(4, 0x0F0F0F0Fu)
+  HP_TSTAGE(2, 0x33333333u)
+  HP_TSTAGE(1, 0x55555555u)
+#undef HP_TSTAGE
+}
+
+// ------------------------------------------------------------- fixed point
+// F = sign(v) * floor(|v| / 2^(E_f-48)), exactly, from the IEEE fields.
+__device__ __forceinline__ int64_t fixed_point(float v, int E_f, uint32_t& floored) {
+  uint32_t u = __float_as_uint(v);
+  uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  int ee = e ? (int)e : 1;
+  if (e) m |= 0x800000u;
+  int s = ee - 102 - E_f;
+  uint64_t mag;
+  if (s >= 0) {
+    mag = (uint64_t)m << s;
+  } else {
+    int r = -s;
+    if (r >= 32) {
+      mag = 0;
+      floored |= (m != 0);
+    } else {
+      mag = m >> r;
+      floored |= ((m & ((1u << r) - 1u)) != 0);
+    }
+  }
+  return (u >> 31) ? -(int64_t)mag : (int64_t)mag;
+}
+
+__device__ __forceinline__ int64_t fixed_point(double v, int E_f, uint32_t& floored) {
+  uint64_t u = (uint64_t)__double_as_longlong(v);
+  uint32_t e = (uint32_t)((u >> 52) & 0x7ffu);
+  uint64_t m = u & 0xfffffffffffffull;
+  int ee = e ? (int)e : 1;
+  if (e) m |= 0x10000000000000ull;
+  int s = ee - 1027 - E_f;
+  uint64_t mag;
+  if (s >= 0) {
+    mag = m << s;
+  } else {
+    int r = -s;
+    if (r >= 64) {
+      mag = 0;
+      floored |= (m != 0);
+    } else {
+      mag = m >> r;
+      floored |= ((m & ((1ull << r) - 1ull)) != 0);
+    }
+  }
+  return (u >> 63) ? -(int64_t)mag : (int64_t)mag;
+}
+
+__device__ __forceinline__ uint64_t umag(int64_t c) {
+  return c < 0 ? (uint64_t)(-c) : (uint64_t)c;
+}
+
+__device__ __forceinline__ int bitlen64(uint64_t v) { return 64 - __clzll((long long)v); }
+
+// floor(a / 2^s) for signed a (arithmetic shift is floor division on two's complement)
+__device__ __forceinline__ int64_t floor_shift(int64_t a, int s) { return a >> s; }
+
+// --------------------------------------------------------- warp reductions
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    uint64_t w = __shfl_xor_sync(HP_FULL, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint64_t warp_or_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v |= __shfl_xor_sync(HP_FULL, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(HP_FULL, v, o);
+  return v;
+}
+
+// ------------------------------------------------------ level node geometry
+// Node j of a level: parity type t (1..7), and its coordinates in the level grid.
+struct NodePos {
+  int t;
+  uint32_t gz, gy, gx;  // coordinates in G_h
+};
+
+__device__ __forceinline__ NodePos node_pos(const LevelDesc& L, uint32_t j) {
+  NodePos p;
+  int t = 1;
+#pragma unroll
+  for (int k = 2; k <= 7; k++) t += (j >= L.off[k]) ? 1 : 0;
+  uint32_t local = j - L.off[t];
+  uint32_t r = fdiv(local, L.dx[t]);
+  uint32_t x = local - r * L.cnt[t][2];
+  uint32_t z = fdiv(r, L.dy[t]);
+  uint32_t y = r - z * L.cnt[t][1];
+  p.t = t;
+  p.gx = 2 * x + (t & 1);
+  p.gy = 2 * y + ((t >> 1) & 1);
+  p.gz = 2 * z + ((t >> 2) & 1);
+  return p;
+}
+
+// lo/hi neighbour along one axis at grid coordinate c (odd), grid size G
+__device__ __forceinline__ void axis_nb(uint32_t c, uint32_t G, uint32_t& lo, uint32_t& hi) {
+  lo = c - 1;
+  hi = (c + 1 < G) ? c + 1 : c - 1;
+}
+
+// --------------------------------------------------- ordered float keys
+__device__ __forceinline__ uint64_t order_key(float v) {
+  uint32_t u = __float_as_uint(v);
+  return (u & 0x80000000u) ? (uint64_t)(~u) : (uint64_t)(u | 0x80000000u);
+}
+__device__ __forceinline__ uint64_t order_key(double v) {
+  uint64_t u = (uint64_t)__double_as_longlong(v);
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ uint64_t abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+__device__ __forceinline__ uint64_t abs_key(double v) {
+  return (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+}  // namespace hp

@@ -1,0 +1,152 @@
+// Internal data structures shared by the host runtime and the sm_103a kernels.
+//
+// Layout in HBM of one refactored field (a "handle"):
+//   planes   : for each level l, (B+1) bitplanes of W_l uint32 words, plane 0 =
+//              sign, plane 1+p = magnitude bit B-1-p (Algorithm 1 order).  A
+//              merged group (Sec. 5.2) is a contiguous byte range of it.  Groups
+//              stored by direct copy live here; Huffman/RLE groups are decoded
+//              back into their range on retrieval.
+//   slots    : one fixed slot per (level, group) of capacity S*cr_den/cr_num
+//              (+header room) for the Huffman or RLE bytes of that group.
+//   meta     : FieldMeta (device), mirrored to the host after refactor.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#define HP_MAX_LEVELS 33
+#define HP_MAX_GROUPS 16
+#define HP_CHUNK 16384u
+#define HP_TILE 1024u  // level-linear elements per warp tile (32 words)
+#define HP_SEQ_MAX (HP_MAX_LEVELS * HP_MAX_GROUPS)
+
+// unsigned 32-bit division by a runtime constant (round-up multiplier method)
+struct FastDiv {
+  uint32_t d, m, s;  // q = (umulhi(n, m) + n) >> s  for d > 1
+};
+
+struct LevelDesc {
+  uint64_t plane_off;  // byte offset of this level's planes in the plane buffer
+  uint32_t n;          // nodes in the level
+  uint32_t W;          // uint32 words per plane
+  uint32_t tile0;      // first global tile of this level
+  uint32_t ntiles;
+  int32_t level;       // l (0 = root)
+  int32_t hlog;        // log2 of the half-stride h (-1 for the root)
+  uint32_t g[3];       // level grid G_h dims (z, y, x): ceil(n_d / h)
+  uint32_t gc[3];      // coarse grid G_2h dims: ceil(g_d / 2)
+  uint32_t off[9];     // offset of parity type t (t = 1..7) in the level, off[8] = n
+  uint32_t cnt[8][3];  // nodes of type t along (z, y, x)
+  FastDiv dx[8], dy[8];
+};
+
+struct GroupMeta {
+  uint64_t S;           // raw bytes of the merged group
+  uint64_t plane_off;   // byte offset of the group in the plane buffer
+  uint64_t slot_off;    // byte offset of its slot in the slot buffer
+  uint64_t cap;         // slot capacity
+  uint64_t stored_len;  // stored bytes (DC: S)
+  uint64_t est_H, est_R;
+  uint32_t nchunks, chunk0;  // 16 KiB chunks and the global index of the first
+  int32_t method;
+  int32_t pad;
+};
+
+struct FieldMeta {
+  int32_t status;  // HPMDR_OK or an error raised on the device
+  int32_t dtype, B, nlev, ngroups, E_f, input_exact, has_range;
+  uint64_t key_absmax, key_min, key_max;  // order-preserving keys of max|f|, min, max
+  double maxabs, vmin, vmax, range;
+  uint32_t floored;                       // some f_i lost bits in the fixed point
+  uint32_t pad0;
+  uint64_t m8[HP_MAX_LEVELS];             // max |C8| per level
+  uint64_t lowbits[HP_MAX_LEVELS];        // OR of the bits dropped by alignment
+  int32_t bl[HP_MAX_LEVELS], exact[HP_MAX_LEVELS];
+  GroupMeta grp[HP_MAX_LEVELS][HP_MAX_GROUPS];
+  // greedy sequence and the estimate after each prefix (128-bit units)
+  int32_t seq_len, pad1;
+  uint8_t seq[HP_SEQ_MAX];
+  uint64_t E_hi[HP_SEQ_MAX + 1], E_lo[HP_SEQ_MAX + 1];
+  // retrieval state
+  int32_t fetched[HP_MAX_LEVELS];  // groups present in the plane buffer per level
+  int32_t cur[HP_MAX_LEVELS];      // groups used by the current reconstruction
+  // QoI triplet data (velocity magnitude range) when prepared
+  float qmin, qmax;
+};
+
+// retrieval info written by the selection kernel
+struct RetrieveDev {
+  int32_t status, nsel;
+  uint64_t E_hi, E_lo;
+  double E_abs, tau_abs;
+  uint64_t bytes_new, bytes_total;
+  uint32_t n_new;                     // groups newly fetched by this retrieval
+  uint32_t items;                     // Huffman/RLE chunks to decode
+  int32_t g[HP_MAX_LEVELS];           // groups used per level
+  uint32_t new_gi[HP_SEQ_MAX];        // flat index of each newly fetched coded group
+  uint32_t new_pref[HP_SEQ_MAX + 1];  // prefix of their chunk counts
+};
+
+// launchers implemented in the .cu files --------------------------------------
+typedef struct CUstream_st* cstream;
+
+namespace hp {
+
+// stats.cu
+void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, cstream s);
+void launch_stats(const void* f, uint64_t N, int dtype, FieldMeta* meta, cstream s);
+void launch_stats_finalize(FieldMeta* meta, cstream s);
+
+// decompose.cu
+void launch_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* levels,
+                     int nlev, uint32_t total_tiles, FieldMeta* meta, cstream s);
+void launch_bitlen(FieldMeta* meta, cstream s);
+void launch_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* levels,
+                   int nlev, uint32_t total_tiles, FieldMeta* meta, uint32_t* planes, cstream s);
+void launch_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int B,
+                            uint32_t* planes, cstream s);
+void launch_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, void* q,
+                            uint8_t* sign, cstream s);
+
+// lossless.cu
+struct ChunkMap {
+  const uint32_t* chunk_group;  // global chunk -> flat group index (l * ngroups + g)
+  uint32_t total_chunks;
+};
+void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* chunk_hist,
+                        uint32_t* chunk_cost, cstream s);
+void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_hist,
+                   const uint32_t* chunk_cost, uint8_t* lens, uint64_t Ts, uint32_t cr_num,
+                   uint32_t cr_den, int force, cstream s);
+void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm, const uint8_t* lens,
+                      uint32_t* chunk_words, cstream s);
+void launch_group_offsets(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_words,
+                          const uint32_t* chunk_cost, uint32_t* chunk_out, cstream s);
+void launch_huff_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                        const uint8_t* lens, const uint32_t* chunk_out, uint8_t* slots, cstream s);
+void launch_rle_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                       const uint32_t* chunk_out, uint8_t* slots, cstream s);
+void launch_headers(FieldMeta* meta, int ngroups_total, const uint8_t* lens,
+                    const uint32_t* chunk_out, uint8_t* slots, cstream s);
+void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
+                   uint32_t max_items, uint8_t* planes, cstream s);
+
+// select.cu
+void launch_sequence(FieldMeta* meta, cstream s);
+void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s);
+
+// recompose.cu  (final_dtype: -1 = int64 level grid, 0 = float out, 1 = double out)
+void launch_recompose_root(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* L0,
+                           int64_t* xroot, void* out, int dtype, cstream s);
+void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const int64_t* coarse,
+                           void* dst, int final_dtype, const FieldMeta* meta, cstream s);
+void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,
+                            const LevelDesc& Lh_host, const int64_t* coarse, void* dst, int B,
+                            int final_dtype, cstream s);
+
+// qoi.cu
+void launch_vmag_range(const float* vx, const float* vy, const float* vz, uint64_t N,
+                       float* qrange /* device: [min, max] */, cstream s);
+void launch_vmag(const float* vx, const float* vy, const float* vz, uint64_t N, float* out,
+                 cstream s);
+
+}  // namespace hp

@@ -1,0 +1,690 @@
+// Hybrid lossless coding of merged bitplane groups (Sec. 5): Huffman, RLE and
+// direct copy, chosen per group by Algorithm 2 from light-weight size
+// estimates (Sec. 5.2), plus the matching decoders used on retrieval.
+//
+// Formats (all little-endian, payload chunked by 16 KiB of input):
+//   Huffman: u64 orig_len, u32 chunk_bytes, u32 nchunks, u8 len[256],
+//            u32 word_off[nchunks+1], payload words; canonical codes in
+//            (length, symbol) order, written MSB-first, each chunk starting on
+//            a fresh 32-bit word.
+//   RLE:     u64 orig_len, u32 chunk_bytes, u32 nchunks, u32 byte_off[nchunks+1],
+//            payload of (byte, LEB128(run-1)) records; runs end at chunk ends.
+//   DC:      the group bytes as they are (they stay in the plane buffer).
+//
+// GPU mapping: one CTA per 16 KiB chunk for statistics and encoding (chunk in
+// shared memory), one CTA per group for the decision, one warp per chunk for
+// decoding.  No inter-CTA waits anywhere.
+#include "dev_common.cuh"
+
+namespace hp {
+
+__device__ __forceinline__ uint32_t huff_header_bytes(uint32_t nchunks) {
+  return 8 + 4 + 4 + 256 + 4 * (nchunks + 1);
+}
+__device__ __forceinline__ uint32_t rle_header_bytes(uint32_t nchunks) {
+  return 8 + 4 + 4 + 4 * (nchunks + 1);
+}
+
+struct ChunkRef {
+  const GroupMeta* gm;
+  uint32_t gi, cl, len;  // flat group index, chunk within group, bytes in chunk
+  uint64_t start;        // byte offset of the chunk within the group
+};
+
+__device__ __forceinline__ ChunkRef chunk_ref(const FieldMeta* meta, const uint32_t* chunk_group,
+                                              uint32_t c) {
+  ChunkRef r;
+  r.gi = chunk_group[c];
+  const int ng = meta->ngroups;
+  r.gm = &meta->grp[r.gi / ng][r.gi % ng];
+  r.cl = c - r.gm->chunk0;
+  r.start = (uint64_t)r.cl * HP_CHUNK;
+  uint64_t rest = r.gm->S - r.start;
+  r.len = (uint32_t)(rest < HP_CHUNK ? rest : HP_CHUNK);
+  return r;
+}
+
+// load one chunk (16-byte aligned start) into shared memory: 128-bit loads for
+// the bulk, bytes for a ragged tail
+__device__ __forceinline__ void load_chunk(const uint8_t* __restrict__ src, uint32_t len,
+                                           uint8_t* dst) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (uint32_t i = threadIdx.x; i < len / 16; i += blockDim.x) d4[i] = __ldcs(s4 + i);
+  for (uint32_t i = (len & ~15u) + threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
+}
+
+// ------------------------------------------------- statistics per 16 KiB chunk
+// byte histogram (for the Huffman estimate) and the exact RLE cost
+// sum over runs of (1 + LEB128 length of run-1) = 2 runs + #(runs >= 129)
+__global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__ planes,
+                                                     const FieldMeta* __restrict__ meta,
+                                                     const uint32_t* __restrict__ chunk_group,
+                                                     uint32_t* __restrict__ chunk_hist,
+                                                     uint32_t* __restrict__ chunk_cost) {
+  __shared__ __align__(16) uint8_t buf[HP_CHUNK];
+  __shared__ uint32_t hist[8][256];
+  __shared__ uint32_t red[8];
+  const uint32_t c = blockIdx.x;
+  if (meta->status) return;
+  ChunkRef r = chunk_ref(meta, chunk_group, c);
+  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
+  load_chunk(planes + r.gm->plane_off + r.start, r.len, buf);
+  __syncthreads();
+  const int w = threadIdx.x >> 5;
+  uint32_t cost = 0;
+  for (uint32_t i = threadIdx.x; i < r.len; i += blockDim.x) {
+    uint8_t b = buf[i];
+    atomicAdd(&hist[w][b], 1u);
+    if (i == 0 || buf[i - 1] != b) {
+      uint32_t k = 1;
+      while (k <= 128 && i + k < r.len && buf[i + k] == b) k++;
+      cost += 2 + (k > 128 ? 1u : 0u);
+    }
+  }
+  __syncthreads();
+  {
+    uint32_t t = threadIdx.x, s = 0;
+    for (int k = 0; k < 8; k++) s += hist[k][t];
+    chunk_hist[(size_t)c * 256 + t] = s;
+  }
+  for (int o = 16; o; o >>= 1) cost += __shfl_xor_sync(HP_FULL, cost, o);
+  if ((threadIdx.x & 31) == 0) red[w] = cost;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int k = 0; k < 8; k++) s += red[k];
+    chunk_cost[c] = s;
+  }
+}
+
+void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* chunk_hist,
+                        uint32_t* chunk_cost, cstream s) {
+  if (cm.total_chunks == 0) return;
+  k_chunk_stats<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, chunk_hist,
+                                                chunk_cost);
+}
+
+// -------------------------------------------- Algorithm 2 decision per group
+// Huffman code lengths by the two-queue construction (leaves by (freq,
+// symbol), a leaf wins a weight tie, internal nodes in creation order), capped
+// at 16 by halving the counts and rebuilding.
+__device__ void huffman_lengths_block(const uint64_t* f_in, uint8_t* len_out, uint64_t* f,
+                                      int* sorted, uint64_t* w, int* parent, int* depth, int* flag) {
+  const int t = threadIdx.x;  // 256 threads, t = symbol
+  f[t] = f_in[t];
+  __syncthreads();
+  for (int round = 0; round < 64; round++) {
+    // rank of symbol t among the nonzero symbols by (freq, symbol)
+    int rank = 0, n = 0;
+    uint64_t ft = f[t];
+    for (int s = 0; s < 256; s++) {
+      uint64_t fs = f[s];
+      if (fs > 0) {
+        n++;
+        if (fs < ft || (fs == ft && s < t)) rank++;
+      }
+    }
+    if (ft > 0) sorted[rank] = t;
+    len_out[t] = 0;
+    __syncthreads();
+    if (t == 0) {
+      int maxlen = 0;
+      if (n == 1) {
+        len_out[sorted[0]] = 1;
+        maxlen = 1;
+      } else if (n > 1) {
+        for (int i = 0; i < n; i++) w[i] = f[sorted[i]];
+        int nl = 0, ni = n, created = n;
+        for (int step = 0; step < n - 1; step++) {
+          int pick[2];
+          for (int k = 0; k < 2; k++) {
+            bool leaf_ok = nl < n, int_ok = ni < created;
+            if (leaf_ok && (!int_ok || w[nl] <= w[ni])) pick[k] = nl++;
+            else pick[k] = ni++;
+          }
+          w[created] = w[pick[0]] + w[pick[1]];
+          parent[pick[0]] = created;
+          parent[pick[1]] = created;
+          created++;
+        }
+        depth[created - 1] = 0;
+        for (int v = created - 2; v >= 0; v--) depth[v] = depth[parent[v]] + 1;
+        for (int i = 0; i < n; i++) {
+          len_out[sorted[i]] = (uint8_t)depth[i];
+          maxlen = depth[i] > maxlen ? depth[i] : maxlen;
+        }
+      }
+      *flag = maxlen > 16;
+    }
+    __syncthreads();
+    if (!*flag) break;
+    if (f[t] > 0) f[t] = (f[t] + 1) >> 1;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t* __restrict__ chunk_hist,
+                                                const uint32_t* __restrict__ chunk_cost,
+                                                uint8_t* __restrict__ lens, uint64_t Ts,
+                                                uint32_t cr_num, uint32_t cr_den, int force) {
+  __shared__ uint64_t hist[256], f[256], w[512];
+  __shared__ int sorted[256], parent[512], depth[512], flag;
+  __shared__ uint8_t len[256];
+  __shared__ uint64_t red[8];
+  if (meta->status) return;
+  const uint32_t gi = blockIdx.x;
+  const int ng = meta->ngroups;
+  GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
+  const int t = threadIdx.x;
+  uint64_t h = 0;
+  for (uint32_t c = 0; c < gm->nchunks; c++) h += chunk_hist[(size_t)(gm->chunk0 + c) * 256 + t];
+  hist[t] = h;
+  uint64_t cost = 0;
+  for (uint32_t c = t; c < gm->nchunks; c += 256) cost += chunk_cost[gm->chunk0 + c];
+  cost = warp_sum_u64(cost);
+  if ((t & 31) == 0) red[t >> 5] = cost;
+  __syncthreads();
+  huffman_lengths_block(hist, len, f, sorted, w, parent, depth, &flag);
+  __syncthreads();
+  uint64_t bits = hist[t] * (uint64_t)len[t];
+  bits = warp_sum_u64(bits);
+  __shared__ uint64_t redb[8];
+  if ((t & 31) == 0) redb[t >> 5] = bits;
+  lens[(size_t)gi * 256 + t] = len[t];
+  __syncthreads();
+  if (t == 0) {
+    uint64_t tb = 0, tc = 0;
+    for (int k = 0; k < 8; k++) {
+      tb += redb[k];
+      tc += red[k];
+    }
+    const uint64_t S = gm->S;
+    const uint32_t nc = gm->nchunks;
+    uint64_t est_H = huff_header_bytes(nc) + (tb + 7) / 8 + 4ull * nc;
+    uint64_t est_R = rle_header_bytes(nc) + tc;
+    gm->est_H = est_H;
+    gm->est_R = est_R;
+    int m = 0;  // DC
+    if (S > Ts) {
+      unsigned __int128 lhs = (unsigned __int128)S * cr_den;
+      if (lhs > (unsigned __int128)cr_num * est_H) m = 1;       // Huffman
+      else if (lhs > (unsigned __int128)cr_num * est_R) m = 2;  // RLE
+    }
+    if (force >= 0) m = force;  // stage entry point: caller-chosen method
+    gm->method = m;
+    gm->stored_len = S;  // final for DC; set by the offsets pass otherwise
+  }
+}
+
+void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_hist,
+                   const uint32_t* chunk_cost, uint8_t* lens, uint64_t Ts, uint32_t cr_num,
+                   uint32_t cr_den, int force, cstream s) {
+  k_decide<<<ngroups_total, 256, 0, s>>>(meta, chunk_hist, chunk_cost, lens, Ts, cr_num, cr_den,
+                                         force);
+}
+
+// --------------------------------------------------- canonical Huffman codes
+// code[t] for the canonical code of lengths len[] ((length, symbol) order)
+__device__ void canonical_codes_block(const uint8_t* len, uint32_t* code, uint32_t* first) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    uint32_t cnt[17];
+    for (int L = 0; L <= 16; L++) cnt[L] = 0;
+    for (int s = 0; s < 256; s++) cnt[len[s]]++;
+    uint32_t c = 0;
+    for (int L = 1; L <= 16; L++) {
+      first[L] = c;
+      c = (c + cnt[L]) << 1;
+    }
+  }
+  __syncthreads();
+  uint32_t L = len[t], r = 0;
+  if (L) {
+    for (int s = 0; s < t; s++) r += (len[s] == L) ? 1u : 0u;
+    code[t] = first[L] + r;
+  } else {
+    code[t] = 0;
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------- Huffman: bits per chunk
+__global__ void __launch_bounds__(256) k_huff_bits(const uint8_t* __restrict__ planes,
+                                                   const FieldMeta* __restrict__ meta,
+                                                   const uint32_t* __restrict__ chunk_group,
+                                                   const uint8_t* __restrict__ lens,
+                                                   uint32_t* __restrict__ chunk_words) {
+  __shared__ uint8_t len[256];
+  __shared__ uint32_t red[8];
+  if (meta->status) return;
+  ChunkRef r = chunk_ref(meta, chunk_group, blockIdx.x);
+  if (r.gm->method != 1) return;
+  len[threadIdx.x] = lens[(size_t)r.gi * 256 + threadIdx.x];
+  __syncthreads();
+  const uint8_t* src = planes + r.gm->plane_off + r.start;
+  uint32_t bits = 0;
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  for (uint32_t i = threadIdx.x; i < r.len / 16; i += blockDim.x) {
+    uint4 v = __ldcs(s4 + i);
+    uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int b = 0; b < 4; b++) bits += len[(wv[k] >> (8 * b)) & 0xffu];
+  }
+  for (uint32_t i = (r.len & ~15u) + threadIdx.x; i < r.len; i += blockDim.x) bits += len[src[i]];
+  for (int o = 16; o; o >>= 1) bits += __shfl_xor_sync(HP_FULL, bits, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bits;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int k = 0; k < 8; k++) s += red[k];
+    chunk_words[blockIdx.x] = (s + 31) / 32;
+  }
+}
+
+void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm, const uint8_t* lens,
+                      uint32_t* chunk_words, cstream s) {
+  if (cm.total_chunks == 0) return;
+  k_huff_bits<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_words);
+}
+
+// ------------------------------------ per-group chunk output offsets (scan)
+// Huffman: word offset of each chunk in the payload; RLE: byte offset.
+__global__ void __launch_bounds__(256) k_group_offsets(FieldMeta* meta,
+                                                       const uint32_t* __restrict__ chunk_words,
+                                                       const uint32_t* __restrict__ chunk_cost,
+                                                       uint32_t* __restrict__ chunk_out) {
+  __shared__ uint64_t part[256];
+  if (meta->status) return;
+  const uint32_t gi = blockIdx.x;
+  const int ng = meta->ngroups;
+  GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
+  const int m = gm->method;
+  if (m == 0) return;
+  const uint32_t* src = (m == 1 ? chunk_words : chunk_cost) + gm->chunk0;
+  const uint32_t nc = gm->nchunks, t = threadIdx.x;
+  const uint32_t per = (nc + 255) / 256, a = t * per, b = min(nc, a + per);
+  uint64_t s = 0;
+  for (uint32_t c = a; c < b; c++) s += src[c];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    uint64_t run = 0;
+    for (int k = 0; k < 256; k++) {
+      uint64_t v = part[k];
+      part[k] = run;
+      run += v;
+    }
+    uint64_t hdr = m == 1 ? huff_header_bytes(nc) : rle_header_bytes(nc);
+    uint64_t total = hdr + (m == 1 ? 4 * run : run);
+    gm->stored_len = total;
+    if (total > gm->cap) atomicExch(&meta->status, -4);  // cannot happen for T_cr >= 1
+  }
+  __syncthreads();
+  uint64_t o = part[t];
+  for (uint32_t c = a; c < b; c++) {
+    chunk_out[gm->chunk0 + c] = (uint32_t)o;
+    o += src[c];
+  }
+}
+
+void launch_group_offsets(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_words,
+                          const uint32_t* chunk_cost, uint32_t* chunk_out, cstream s) {
+  k_group_offsets<<<ngroups_total, 256, 0, s>>>(meta, chunk_words, chunk_cost, chunk_out);
+}
+
+// -------------------------------------------------------- Huffman: encode
+__global__ void __launch_bounds__(256) k_huff_encode(const uint8_t* __restrict__ planes,
+                                                     const FieldMeta* __restrict__ meta,
+                                                     const uint32_t* __restrict__ chunk_group,
+                                                     const uint8_t* __restrict__ lens,
+                                                     const uint32_t* __restrict__ chunk_out,
+                                                     uint8_t* __restrict__ slots) {
+  __shared__ uint8_t len[256];
+  __shared__ uint32_t code[256], first[17];
+  __shared__ uint32_t outw[HP_CHUNK * 16 / 32];  // worst case: 16 bits per byte
+  __shared__ uint32_t scan[256];
+  if (meta->status) return;
+  ChunkRef r = chunk_ref(meta, chunk_group, blockIdx.x);
+  if (r.gm->method != 1) return;
+  const int t = threadIdx.x;
+  len[t] = lens[(size_t)r.gi * 256 + t];
+  for (int i = t; i < HP_CHUNK * 16 / 32; i += 256) outw[i] = 0;
+  __syncthreads();
+  canonical_codes_block(len, code, first);
+  // thread t encodes bytes [64 t, 64 t + 64) of the chunk, in order
+  const uint8_t* src = planes + r.gm->plane_off + r.start;
+  const uint32_t a = t * 64u, b = min(r.len, a + 64u);
+  uint8_t mine[64];
+  uint32_t bits = 0;
+  for (uint32_t i = a; i < b; i += 16) {
+    if (i + 16 <= b) {
+      uint4 v = __ldcs(reinterpret_cast<const uint4*>(src + i));
+      memcpy(mine + (i - a), &v, 16);
+    } else {
+      for (uint32_t k = i; k < b; k++) mine[k - a] = src[k];
+    }
+  }
+  for (uint32_t i = a; i < b; i++) bits += len[mine[i - a]];
+  scan[t] = bits;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < 256; k++) {
+      uint32_t v = scan[k];
+      scan[k] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  uint32_t pos = scan[t];
+  for (uint32_t i = a; i < b; i++) {
+    uint32_t s = mine[i - a], L = len[s], cw = code[s];
+    uint32_t wd = pos >> 5, o = pos & 31;
+    if (o + L <= 32) {
+      atomicOr(&outw[wd], cw << (32 - o - L));
+    } else {
+      uint32_t spill = o + L - 32;
+      atomicOr(&outw[wd], cw >> spill);
+      atomicOr(&outw[wd + 1], cw << (32 - spill));
+    }
+    pos += L;
+  }
+  __shared__ uint32_t nbits;
+  if (t == 255) nbits = pos;
+  __syncthreads();
+  const uint32_t nwords = (nbits + 31) / 32;
+  uint32_t* dst = reinterpret_cast<uint32_t*>(slots + r.gm->slot_off +
+                                              huff_header_bytes(r.gm->nchunks)) +
+                  chunk_out[blockIdx.x];
+  for (uint32_t i = t; i < nwords; i += 256) dst[i] = outw[i];
+}
+
+void launch_huff_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                        const uint8_t* lens, const uint32_t* chunk_out, uint8_t* slots, cstream s) {
+  if (cm.total_chunks == 0) return;
+  k_huff_encode<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_out,
+                                                slots);
+}
+
+// ------------------------------------------------------------ RLE: encode
+__global__ void __launch_bounds__(256) k_rle_encode(const uint8_t* __restrict__ planes,
+                                                    const FieldMeta* __restrict__ meta,
+                                                    const uint32_t* __restrict__ chunk_group,
+                                                    const uint32_t* __restrict__ chunk_out,
+                                                    uint8_t* __restrict__ slots) {
+  __shared__ __align__(16) uint8_t buf[HP_CHUNK];
+  __shared__ uint32_t scan[256];
+  if (meta->status) return;
+  ChunkRef r = chunk_ref(meta, chunk_group, blockIdx.x);
+  if (r.gm->method != 2) return;
+  const int t = threadIdx.x;
+  load_chunk(planes + r.gm->plane_off + r.start, r.len, buf);
+  __syncthreads();
+  const uint32_t a = t * 64u, b = min(r.len, a + 64u);
+  uint32_t cost = 0;
+  for (uint32_t i = a; i < b; i++) {
+    if (i == 0 || buf[i - 1] != buf[i]) {
+      uint32_t k = 1;
+      while (i + k < r.len && buf[i + k] == buf[i]) k++;
+      cost += 2 + (k > 128 ? 1u : 0u);
+    }
+  }
+  scan[t] = cost;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < 256; k++) {
+      uint32_t v = scan[k];
+      scan[k] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  uint8_t* dst = slots + r.gm->slot_off + rle_header_bytes(r.gm->nchunks) + chunk_out[blockIdx.x] +
+                 scan[t];
+  uint32_t o = 0;
+  for (uint32_t i = a; i < b; i++) {
+    if (i == 0 || buf[i - 1] != buf[i]) {
+      uint32_t k = 1;
+      while (i + k < r.len && buf[i + k] == buf[i]) k++;
+      dst[o++] = buf[i];
+      uint32_t x = k - 1;
+      while (x >= 128) {
+        dst[o++] = (uint8_t)((x & 127u) | 128u);
+        x >>= 7;
+      }
+      dst[o++] = (uint8_t)x;
+    }
+  }
+}
+
+void launch_rle_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                       const uint32_t* chunk_out, uint8_t* slots, cstream s) {
+  if (cm.total_chunks == 0) return;
+  k_rle_encode<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, chunk_out, slots);
+}
+
+// ---------------------------------------------------------- group headers
+__global__ void __launch_bounds__(256) k_headers(const FieldMeta* __restrict__ meta,
+                                                 const uint8_t* __restrict__ lens,
+                                                 const uint32_t* __restrict__ chunk_out,
+                                                 uint8_t* __restrict__ slots) {
+  if (meta->status) return;
+  const uint32_t gi = blockIdx.x;
+  const int ng = meta->ngroups;
+  const GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
+  const int m = gm->method;
+  if (m == 0) return;
+  uint8_t* h = slots + gm->slot_off;
+  const uint32_t nc = gm->nchunks, t = threadIdx.x;
+  if (t == 0) {
+    *reinterpret_cast<uint64_t*>(h) = gm->S;
+    *reinterpret_cast<uint32_t*>(h + 8) = HP_CHUNK;
+    *reinterpret_cast<uint32_t*>(h + 12) = nc;
+  }
+  uint32_t* offs;
+  uint32_t endv;
+  if (m == 1) {
+    h[16 + t] = lens[(size_t)gi * 256 + t];
+    offs = reinterpret_cast<uint32_t*>(h + 272);
+    endv = (uint32_t)((gm->stored_len - huff_header_bytes(nc)) / 4);
+  } else {
+    offs = reinterpret_cast<uint32_t*>(h + 16);
+    endv = (uint32_t)(gm->stored_len - rle_header_bytes(nc));
+  }
+  for (uint32_t c = t; c < nc; c += 256) offs[c] = chunk_out[gm->chunk0 + c];
+  if (t == 0) offs[nc] = endv;
+}
+
+void launch_headers(FieldMeta* meta, int ngroups_total, const uint8_t* lens,
+                    const uint32_t* chunk_out, uint8_t* slots, cstream s) {
+  k_headers<<<ngroups_total, 256, 0, s>>>(meta, lens, chunk_out, slots);
+}
+
+// ================================================================ decoding
+// One warp per queued chunk.  Every read of the stored bytes is checked
+// against the group's stored length; a failed check sets status CORRUPT and
+// abandons the chunk (no trap).
+__device__ __forceinline__ void set_corrupt(FieldMeta* meta) { atomicExch(&meta->status, -4); }
+
+struct HuffTables {
+  uint16_t count[17];
+  uint32_t first[17];
+  uint16_t index[17];
+  uint8_t sorted[256];
+};
+
+__device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm,
+                                  uint32_t cl, uint32_t len, uint8_t* __restrict__ dst,
+                                  HuffTables& T, FieldMeta* meta) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nc = gm->nchunks;
+  const uint64_t hdr = 272 + 4ull * (nc + 1);
+  bool ok = gm->stored_len >= hdr && *reinterpret_cast<const uint64_t*>(stored) == gm->S &&
+            *reinterpret_cast<const uint32_t*>(stored + 8) == HP_CHUNK &&
+            *reinterpret_cast<const uint32_t*>(stored + 12) == nc;
+  if (!__all_sync(HP_FULL, ok)) {
+    if (lane == 0) set_corrupt(meta);
+    return;
+  }
+  const uint8_t* lens = stored + 16;
+  if (lane == 0) {
+    for (int L = 0; L <= 16; L++) T.count[L] = 0;
+    bool bad = false;
+    for (int s = 0; s < 256; s++) {
+      if (lens[s] > 16) bad = true;
+      else T.count[lens[s]]++;
+    }
+    T.count[0] = 0;
+    uint32_t c = 0;
+    uint16_t idx = 0;
+    for (int L = 1; L <= 16; L++) {
+      T.first[L] = c;
+      T.index[L] = idx;
+      for (int s = 0; s < 256; s++)
+        if (lens[s] == L) T.sorted[idx++] = (uint8_t)s;
+      c = (c + T.count[L]) << 1;
+    }
+    if (bad) set_corrupt(meta);
+  }
+  __syncwarp();
+  const uint32_t* offs = reinterpret_cast<const uint32_t*>(stored + 272);
+  const uint32_t w0 = offs[cl], w1 = offs[cl + 1];
+  const uint64_t words = (gm->stored_len - hdr) / 4;
+  if (w0 > w1 || w1 > words) {
+    if (lane == 0) set_corrupt(meta);
+    return;
+  }
+  if (lane != 0) return;
+  const uint32_t* pay = reinterpret_cast<const uint32_t*>(stored + hdr);
+  uint64_t pos = (uint64_t)w0 * 32, lim = (uint64_t)w1 * 32;
+  uint32_t acc = 0;
+  for (uint32_t i = 0; i < len; i++) {
+    uint32_t code = 0;
+    int sym = -1;
+    for (int L = 1; L <= 16; L++) {
+      if (pos >= lim) break;
+      uint32_t wv = pay[pos >> 5];
+      code = (code << 1) | ((wv >> (31 - (pos & 31))) & 1u);
+      pos++;
+      if (T.count[L] && code >= T.first[L] && code - T.first[L] < T.count[L]) {
+        sym = T.sorted[T.index[L] + (code - T.first[L])];
+        break;
+      }
+    }
+    if (sym < 0) {
+      set_corrupt(meta);
+      return;
+    }
+    acc |= (uint32_t)sym << (8 * (i & 3));
+    if ((i & 3) == 3) {
+      reinterpret_cast<uint32_t*>(dst)[i >> 2] = acc;
+      acc = 0;
+    }
+  }
+  for (uint32_t i = len & ~3u; i < len; i++) dst[i] = (uint8_t)(acc >> (8 * (i & 3)));
+}
+
+__device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm, uint32_t cl,
+                                 uint32_t len, uint8_t* __restrict__ dst, FieldMeta* meta) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nc = gm->nchunks;
+  const uint64_t hdr = 16 + 4ull * (nc + 1);
+  bool ok = gm->stored_len >= hdr && *reinterpret_cast<const uint64_t*>(stored) == gm->S &&
+            *reinterpret_cast<const uint32_t*>(stored + 8) == HP_CHUNK &&
+            *reinterpret_cast<const uint32_t*>(stored + 12) == nc;
+  if (!__all_sync(HP_FULL, ok)) {
+    if (lane == 0) set_corrupt(meta);
+    return;
+  }
+  const uint32_t* offs = reinterpret_cast<const uint32_t*>(stored + 16);
+  uint64_t p = offs[cl], pe = offs[cl + 1];
+  if (p > pe || hdr + pe > gm->stored_len) {
+    if (lane == 0) set_corrupt(meta);
+    return;
+  }
+  const uint8_t* pay = stored + hdr;
+  uint32_t out = 0;
+  int bad = 0;
+  while (true) {
+    uint32_t v = 0, run = 0;
+    int more = 0;
+    if (lane == 0) {
+      more = p < pe;
+      if (more) {
+        v = pay[p++];
+        uint32_t x = 0;
+        int shift = 0;
+        while (true) {
+          if (p >= pe || shift > 28) {
+            bad = 1;
+            break;
+          }
+          uint8_t byte = pay[p++];
+          x |= (uint32_t)(byte & 127u) << shift;
+          shift += 7;
+          if (!(byte & 128u)) break;
+        }
+        run = x + 1;
+        if (!bad && run > len - out) bad = 1;
+      }
+    }
+    more = __shfl_sync(HP_FULL, more, 0);
+    bad = __shfl_sync(HP_FULL, bad, 0);
+    if (bad) {
+      if (lane == 0) set_corrupt(meta);
+      return;
+    }
+    if (!more) break;
+    v = __shfl_sync(HP_FULL, v, 0);
+    run = __shfl_sync(HP_FULL, run, 0);
+    for (uint32_t k = lane; k < run; k += 32) dst[out + k] = (uint8_t)v;
+    out += run;
+  }
+  if (out != len && lane == 0) set_corrupt(meta);
+}
+
+__global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ slots, FieldMeta* meta,
+                                                const RetrieveDev* __restrict__ rd,
+                                                uint8_t* __restrict__ planes) {
+  __shared__ HuffTables tabs[8];
+  const int w = threadIdx.x >> 5;
+  const uint32_t total = rd->items, ngr = rd->n_new;
+  const int ng = meta->ngroups;
+  for (uint32_t item = blockIdx.x * 8 + w; item < total; item += gridDim.x * 8) {
+    // newly fetched group holding this item: last k with new_pref[k] <= item
+    uint32_t lo = 0, hi = ngr;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) / 2;
+      if (rd->new_pref[mid] <= item) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t gi = rd->new_gi[lo];
+    const GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
+    const uint32_t cl = item - rd->new_pref[lo];
+    const uint64_t start = (uint64_t)cl * HP_CHUNK, rest = gm->S - start;
+    const uint32_t len = (uint32_t)(rest < HP_CHUNK ? rest : HP_CHUNK);
+    const uint8_t* stored = slots + gm->slot_off;
+    uint8_t* dst = planes + gm->plane_off + start;
+    if (gm->method == 1) huff_decode_chunk(stored, gm, cl, len, dst, tabs[w], meta);
+    else rle_decode_chunk(stored, gm, cl, len, dst, meta);
+    __syncwarp();
+  }
+}
+
+void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
+                   uint32_t max_items, uint8_t* planes, cstream s) {
+  if (max_items == 0) return;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t blocks = (max_items + 7) / 8;
+  uint32_t cap = (uint32_t)sms * 8;
+  if (blocks > cap) blocks = cap;
+  k_decode<<<blocks, 256, 0, s>>>(slots, meta, rd, planes);
+}
+
+}  // namespace hp

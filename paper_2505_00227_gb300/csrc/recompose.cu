@@ -1,0 +1,212 @@
+// Recomposition from the fetched bitplanes (Sec. 3 reverse path; Algorithm 3
+// `recompose`).  Coarse to fine, level by level: the top k = 4 g_l magnitude
+// planes (and the sign plane) give q_hat by the inverse register-block
+// transpose, c8_hat = +-(q_hat aligned back by the level exponent), and a node
+// of parity type t with odd axes O becomes
+//   X_hat = floor((c8_hat * 2^|O| + 8 * sum of its 2^|O| coarse corners) / 2^(3+|O|))
+// in exact int64 (units of U = 2^(E_f-48)).  The finest level writes the
+// output, f_hat = round-to-nearest(X_hat) * U in the field's type.
+#include "dev_common.cuh"
+
+namespace hp {
+
+template <typename T>
+__device__ __forceinline__ T convert_out(int64_t X, int E_f);
+
+template <>
+__device__ __forceinline__ float convert_out<float>(int64_t X, int E_f) {
+  const int e = E_f - 48;
+  if (e >= -126 && E_f <= 121)
+    return __fmul_rn(__ll2float_rn(X), __int_as_float((e + 127) << 23));
+  const double d = __dmul_rn(__ll2double_rn(X), __longlong_as_double((long long)(e + 1023) << 52));
+  return __double2float_rn(d);
+}
+
+template <>
+__device__ __forceinline__ double convert_out<double>(int64_t X, int E_f) {
+  const int e = E_f - 48;
+  const double x = __ll2double_rn(X);
+  if (e >= -1022) return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
+  const double y = __dmul_rn(x, __longlong_as_double((long long)(-500 + 1023) << 52));
+  return __dmul_rn(y, __longlong_as_double((long long)(e + 500 + 1023) << 52));
+}
+
+__device__ __forceinline__ int64_t dequant(uint64_t qh, bool neg, int B, int bl) {
+  uint64_t a;
+  if (bl == 0) a = 0;
+  else if (B >= bl) a = qh >> (B - bl);
+  else a = qh << (bl - B);
+  return neg ? -(int64_t)a : (int64_t)a;
+}
+
+// root: X_root = floor(c8_hat / 8)
+template <typename T>
+__global__ void k_recompose_root(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
+                                 const LevelDesc* __restrict__ L0, int64_t* xroot, T* out) {
+  if (m->status) return;
+  const int B = m->B, k = 4 * m->cur[0];
+  const uint32_t* P = planes + L0->plane_off / 4;
+  const uint32_t W = L0->W;
+  uint64_t q = 0;
+  for (int p = 0; p < k; p++) q |= (uint64_t)(P[(size_t)(1 + p) * W] & 1u) << (B - 1 - p);
+  const bool neg = k > 0 && (P[0] & 1u);
+  const int64_t X = dequant(q, neg, B, m->bl[0]) >> 3;
+  if (xroot) *xroot = X;
+  if (out) *out = convert_out<T>(X, m->E_f);
+}
+
+void launch_recompose_root(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* L0,
+                           int64_t* xroot, void* out, int dtype, cstream s) {
+  if (dtype == 0)
+    k_recompose_root<float><<<1, 1, 0, s>>>(planes, meta, L0, xroot, (float*)out);
+  else
+    k_recompose_root<double><<<1, 1, 0, s>>>(planes, meta, L0, xroot, (double*)out);
+}
+
+// coarse nodes (all coordinates even in G_h) are copied from G_2h
+template <typename T, bool FINAL>
+__global__ void __launch_bounds__(256) k_recompose_copy(const LevelDesc* __restrict__ Lp,
+                                                        const int64_t* __restrict__ coarse,
+                                                        void* __restrict__ dst,
+                                                        const FieldMeta* __restrict__ m) {
+  const LevelDesc& L = *Lp;
+  const uint32_t cz = L.gc[0], cy = L.gc[1], cx = L.gc[2];
+  const uint64_t total = (uint64_t)cz * cy * cx;
+  const int E_f = m->E_f;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = (uint32_t)(i % cx);
+    const uint64_t r = i / cx;
+    const uint32_t y = (uint32_t)(r % cy), z = (uint32_t)(r / cy);
+    const size_t d = ((size_t)(2 * z) * L.g[1] + 2 * y) * L.g[2] + 2 * x;
+    const int64_t X = coarse[i];
+    if (FINAL) reinterpret_cast<T*>(dst)[d] = convert_out<T>(X, E_f);
+    else reinterpret_cast<int64_t*>(dst)[d] = X;
+  }
+}
+
+// detail nodes of one level: warp tile of 1024 level-linear nodes
+template <typename T, int B, bool FINAL>
+__global__ void __launch_bounds__(B == 32 ? 256 : 128)
+    k_recompose_level(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
+                      const LevelDesc* __restrict__ Lp, const int64_t* __restrict__ coarse,
+                      void* __restrict__ dst) {
+  constexpr int WPB = B == 32 ? 8 : 4;
+  __shared__ uint32_t s_hi[WPB][32 * 33];
+  __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
+  __shared__ uint32_t s_sign[WPB][32];
+  if (m->status) return;
+  const LevelDesc& L = *Lp;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* hi = s_hi[w];
+  uint32_t* lo = s_lo[B == 64 ? w : 0];
+  const int k = 4 * m->cur[L.level], bl = m->bl[L.level], E_f = m->E_f;
+  const uint32_t* P = planes + L.plane_off / 4;
+  const uint32_t W = L.W;
+  for (uint32_t tile = blockIdx.x * WPB + w; tile < L.ntiles; tile += gridDim.x * WPB) {
+    const uint32_t base = tile * HP_TILE;
+    const uint32_t wi = base / 32 + lane;
+    if (wi < W) {
+      uint32_t a[32];
+#pragma unroll
+      for (int p = 0; p < 32; p++) a[31 - p] = (p < k) ? P[(size_t)(1 + p) * W + wi] : 0u;
+      transpose32(a);
+#pragma unroll
+      for (int b = 0; b < 32; b++) hi[lane * 33 + b] = a[b];
+      if (B == 64) {
+#pragma unroll
+        for (int p = 0; p < 32; p++) a[31 - p] = (32 + p < k) ? P[(size_t)(33 + p) * W + wi] : 0u;
+        transpose32(a);
+#pragma unroll
+        for (int b = 0; b < 32; b++) lo[lane * 33 + b] = a[b];
+      }
+      s_sign[w][lane] = k > 0 ? P[wi] : 0u;
+    }
+    __syncwarp();
+    for (int r = 0; r < 32; r++) {
+      const uint32_t j = base + r * 32 + lane;
+      if (j < L.n) {
+        const uint64_t qh = B == 64 ? (((uint64_t)hi[r * 33 + lane] << 32) | lo[r * 33 + lane])
+                                    : (uint64_t)hi[r * 33 + lane];
+        const bool neg = (s_sign[w][r] >> lane) & 1u;
+        const int64_t c8 = dequant(qh, neg, B, bl);
+        const NodePos p = node_pos(L, j);
+        uint32_t zs[2], ys[2], xs[2];
+        int nz = 1, ny = 1, nx = 1;
+        zs[0] = zs[1] = p.gz >> 1;
+        ys[0] = ys[1] = p.gy >> 1;
+        xs[0] = xs[1] = p.gx >> 1;
+        if (p.t & 4) {
+          uint32_t a, b;
+          axis_nb(p.gz, L.g[0], a, b);
+          zs[0] = a >> 1; zs[1] = b >> 1; nz = 2;
+        }
+        if (p.t & 2) {
+          uint32_t a, b;
+          axis_nb(p.gy, L.g[1], a, b);
+          ys[0] = a >> 1; ys[1] = b >> 1; ny = 2;
+        }
+        if (p.t & 1) {
+          uint32_t a, b;
+          axis_nb(p.gx, L.g[2], a, b);
+          xs[0] = a >> 1; xs[1] = b >> 1; nx = 2;
+        }
+        int64_t sum = 0;
+        for (int a = 0; a < nz; a++)
+          for (int b = 0; b < ny; b++)
+            for (int c = 0; c < nx; c++)
+              sum += __ldg(coarse + ((size_t)zs[a] * L.gc[1] + ys[b]) * L.gc[2] + xs[c]);
+        const int nodd = __popc(p.t);
+        const int64_t X = floor_shift(c8 * ((int64_t)1 << nodd) + 8 * sum, 3 + nodd);
+        const size_t d = ((size_t)p.gz * L.g[1] + p.gy) * L.g[2] + p.gx;
+        if (FINAL) reinterpret_cast<T*>(dst)[d] = convert_out<T>(X, E_f);
+        else reinterpret_cast<int64_t*>(dst)[d] = X;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+static int sms() {
+  int dev = 0, n = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n;
+}
+
+void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const int64_t* coarse,
+                           void* dst, int final_dtype, const FieldMeta* meta, cstream s) {
+  uint64_t total = (uint64_t)Lh_host.gc[0] * Lh_host.gc[1] * Lh_host.gc[2];
+  uint64_t blocks = (total + 255) / 256, cap = (uint64_t)sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  if (final_dtype < 0)
+    k_recompose_copy<float, false><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+  else if (final_dtype == 0)
+    k_recompose_copy<float, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+  else
+    k_recompose_copy<double, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+}
+
+void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,
+                            const LevelDesc& Lh_host, const int64_t* coarse, void* dst, int B,
+                            int final_dtype, cstream s) {
+  const uint32_t wpb = B == 32 ? 8 : 4;
+  uint32_t blocks = (Lh_host.ntiles + wpb - 1) / wpb, cap = (uint32_t)sms() * (B == 32 ? 8 : 16);
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  const int thr = B == 32 ? 256 : 128;
+  if (B == 32) {
+    if (final_dtype < 0)
+      k_recompose_level<float, 32, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+    else
+      k_recompose_level<float, 32, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+  } else {
+    if (final_dtype < 0)
+      k_recompose_level<double, 64, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+    else
+      k_recompose_level<double, 64, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+  }
+}
+
+}  // namespace hp

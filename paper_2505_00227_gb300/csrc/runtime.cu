@@ -1,0 +1,1098 @@
+// Host runtime behind the C ABI of include/hpmdr.h: contexts, handles,
+// device memory, the launch order of the refactor and retrieve paths, and
+// the serialized handle format.  All arithmetic of the method runs in the
+// kernels of the other .cu files; this file only plans, allocates, launches
+// and copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/hpmdr.h"
+#include "dev_common.cuh"
+
+using namespace hp;
+
+static thread_local std::string g_last_error;
+
+#define HP_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      g_last_error = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+      return HPMDR_ERR_CUDA;                                                       \
+    }                                                                              \
+  } while (0)
+
+#define HP_TRY(expr)                \
+  do {                              \
+    hpmdr_status s_ = (expr);       \
+    if (s_ != HPMDR_OK) return s_;  \
+  } while (0)
+
+struct Allocator {
+  hpmdr_allocator hook{};
+  bool has_hook = false;
+  cudaMemPool_t pool = nullptr;
+
+  hpmdr_status alloc(void** p, size_t bytes, cudaStream_t s) const {
+    *p = nullptr;
+    if (bytes == 0) return HPMDR_OK;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (has_hook) {
+      *p = hook.alloc(bytes, (void*)s, hook.user);
+      return *p ? HPMDR_OK : HPMDR_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e != cudaSuccess) {
+      g_last_error = std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? HPMDR_ERR_NOMEM : HPMDR_ERR_CUDA;
+    }
+    return HPMDR_OK;
+  }
+  void release(void* p, cudaStream_t s) const {
+    if (!p) return;
+    if (has_hook) hook.free(p, (void*)s, hook.user);
+    else cudaFreeAsync(p, s);
+  }
+};
+
+struct hpmdr_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  uint64_t Ts = 4096;
+  uint32_t cr_num = 2, cr_den = 1;
+  Allocator A;
+};
+
+struct hpmdr_handle {
+  Allocator A;
+  cudaStream_t stream = nullptr;  // stream used to free device memory
+  int dtype = 0, B = 32, nlev = 0, ngroups = 8;
+  uint64_t dims[3] = {1, 1, 1}, N = 1;
+  std::vector<LevelDesc> levels;
+  uint32_t total_tiles = 0, total_chunks = 0, max_items = 0;
+  uint64_t plane_bytes = 0, slot_bytes = 0;
+  LevelDesc* d_levels = nullptr;
+  uint8_t* d_planes = nullptr;
+  uint8_t* d_slots = nullptr;
+  FieldMeta* d_meta = nullptr;
+  uint32_t* d_chunk_group = nullptr;
+  RetrieveDev* d_rd = nullptr;
+  int64_t* d_xa = nullptr;  // |G_2| int64 (recompose scratch)
+  int64_t* d_xb = nullptr;  // |G_4| int64
+  int64_t* d_xroot = nullptr;
+  uint64_t xa_elems = 0, xb_elems = 0;
+  std::unique_ptr<FieldMeta> meta{new FieldMeta()};  // host mirror after refactor/import
+  bool qoi_ready = false;
+  float qmin = 0, qmax = 0;
+
+  ~hpmdr_handle() {
+    A.release(d_levels, stream);
+    A.release(d_planes, stream);
+    A.release(d_slots, stream);
+    A.release(d_meta, stream);
+    A.release(d_chunk_group, stream);
+    A.release(d_rd, stream);
+    A.release(d_xa, stream);
+    A.release(d_xb, stream);
+    A.release(d_xroot, stream);
+  }
+};
+
+// ------------------------------------------------------------------ geometry
+static int detail_levels(const uint64_t d[3]) {
+  uint64_t n = std::max(d[0], std::max(d[1], d[2]));
+  int L = 0;
+  for (uint64_t h = 1; h < n; h *= 2) L++;
+  return L;
+}
+
+static uint32_t axis_count(uint64_t g, int o) { return (uint32_t)(o ? g / 2 : (g + 1) / 2); }
+
+static void plan_levels(hpmdr_handle* H) {
+  const int L = detail_levels(H->dims);
+  H->nlev = L + 1;
+  H->levels.assign(H->nlev, LevelDesc{});
+  uint64_t poff = 0;
+  uint32_t tile = 0;
+  for (int l = 0; l < H->nlev; l++) {
+    LevelDesc& D = H->levels[l];
+    memset(&D, 0, sizeof(D));
+    D.level = l;
+    D.hlog = l == 0 ? -1 : (L - l);
+    uint64_t h = l == 0 ? (1ull << L) * 2 : (1ull << (L - l));
+    for (int d = 0; d < 3; d++) {
+      D.g[d] = (uint32_t)((H->dims[d] + h - 1) / h);
+      D.gc[d] = (D.g[d] + 1) / 2;
+    }
+    uint64_t n = 0;
+    if (l == 0) {
+      n = 1;
+      for (int t = 0; t <= 8; t++) D.off[t] = 0;
+      D.off[8] = 1;
+    } else {
+      D.off[0] = D.off[1] = 0;
+      for (int t = 1; t < 8; t++) {
+        int oz = (t >> 2) & 1, oy = (t >> 1) & 1, ox = t & 1;
+        D.cnt[t][0] = axis_count(D.g[0], oz);
+        D.cnt[t][1] = axis_count(D.g[1], oy);
+        D.cnt[t][2] = axis_count(D.g[2], ox);
+        D.dx[t] = make_fastdiv(std::max(D.cnt[t][2], 1u));
+        D.dy[t] = make_fastdiv(std::max(D.cnt[t][1], 1u));
+        uint64_t c = (uint64_t)D.cnt[t][0] * D.cnt[t][1] * D.cnt[t][2];
+        D.off[t] = (uint32_t)n;
+        n += c;
+      }
+      D.off[8] = (uint32_t)n;
+    }
+    D.n = (uint32_t)n;
+    D.W = (uint32_t)(4 * ((n + 127) / 128));
+    D.plane_off = poff;
+    poff += (uint64_t)(H->B + 1) * D.W * 4;
+    D.tile0 = tile;
+    D.ntiles = (uint32_t)((n + HP_TILE - 1) / HP_TILE);
+    tile += D.ntiles;
+  }
+  H->plane_bytes = poff;
+  H->total_tiles = tile;
+}
+
+static uint64_t round16(uint64_t v) { return (v + 15) & ~15ull; }
+
+// group geometry and slot capacities; fills the host FieldMeta
+static void plan_groups(hpmdr_handle* H, uint64_t Ts, uint32_t num, uint32_t den,
+                        std::vector<uint32_t>& chunk_group) {
+  FieldMeta& M = *H->meta;
+  uint32_t chunk = 0;
+  uint64_t slot = 0;
+  chunk_group.clear();
+  for (int l = 0; l < H->nlev; l++) {
+    const LevelDesc& D = H->levels[l];
+    for (int g = 0; g < H->ngroups; g++) {
+      GroupMeta& G = M.grp[l][g];
+      memset(&G, 0, sizeof(G));
+      G.S = (uint64_t)(g == 0 ? 5 : 4) * D.W * 4;
+      G.plane_off = D.plane_off + (g == 0 ? 0 : (uint64_t)(4 * g + 1) * D.W * 4);
+      G.nchunks = (uint32_t)((G.S + HP_CHUNK - 1) / HP_CHUNK);
+      G.chunk0 = chunk;
+      for (uint32_t c = 0; c < G.nchunks; c++) chunk_group.push_back((uint32_t)(l * H->ngroups + g));
+      chunk += G.nchunks;
+      G.stored_len = G.S;
+      if (G.S > Ts) {
+        // a coded group is chosen only if S / est > num / den, so est < S den / num
+        G.cap = round16((G.S * den + num - 1) / num) + 16;
+        G.slot_off = slot;
+        slot += G.cap;
+      }
+    }
+  }
+  H->total_chunks = chunk;
+  H->slot_bytes = slot;
+}
+
+static void init_meta(hpmdr_handle* H) {
+  FieldMeta& M = *H->meta;
+  M.status = 0;
+  M.dtype = H->dtype;
+  M.B = H->B;
+  M.nlev = H->nlev;
+  M.ngroups = H->ngroups;
+  M.E_f = 0;
+  M.input_exact = 1;
+  M.key_absmax = 0;
+  M.key_min = ~0ull;
+  M.key_max = 0;
+  M.floored = 0;
+  for (int l = 0; l < HP_MAX_LEVELS; l++) {
+    M.m8[l] = 0;
+    M.lowbits[l] = 0;
+    M.bl[l] = 0;
+    M.exact[l] = 1;
+    M.fetched[l] = 0;
+    M.cur[l] = 0;
+  }
+  M.seq_len = 0;
+}
+
+static hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t dims[3], uint64_t* N) {
+  if (ndims < 1 || ndims > 3 || !dims_in) return HPMDR_ERR_ARG;
+  uint64_t in[3] = {dims_in[0], dims_in[1], dims_in[2]};  // dims may alias dims_in
+  dims[0] = dims[1] = dims[2] = 1;
+  for (int i = 0; i < ndims; i++) dims[3 - ndims + i] = in[3 - ndims + i];
+  uint64_t n = 1;
+  for (int d = 0; d < 3; d++) {
+    if (dims[d] == 0 || dims[d] > 0xffffffffull) return HPMDR_ERR_ARG;
+    n *= dims[d];
+    if (n >= 0xffffffffull) return HPMDR_ERR_ARG;
+  }
+  *N = n;
+  return HPMDR_OK;
+}
+
+// ------------------------------------------------------------------- context
+extern "C" hpmdr_status hpmdr_ctx_create(hpmdr_ctx** out, const hpmdr_config* cfg,
+                                         const hpmdr_allocator* alloc, void* stream) {
+  if (!out) return HPMDR_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<hpmdr_ctx> c(new hpmdr_ctx());
+  if (cfg) {
+    if (cfg->group_m != 0 && cfg->group_m != 4) return HPMDR_ERR_ARG;
+    if (cfg->size_threshold) c->Ts = cfg->size_threshold;
+    if (cfg->cr_num || cfg->cr_den) {
+      if (!cfg->cr_num || !cfg->cr_den || cfg->cr_num < cfg->cr_den) return HPMDR_ERR_ARG;
+      c->cr_num = cfg->cr_num;
+      c->cr_den = cfg->cr_den;
+    }
+  }
+  int ndev = 0;
+  HP_CUDA(cudaGetDeviceCount(&ndev));
+  if (ndev <= 0) return HPMDR_ERR_CUDA;
+  HP_CUDA(cudaGetDevice(&c->device));
+  c->stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    c->A.hook = *alloc;
+    c->A.has_hook = true;
+  } else {
+    HP_CUDA(cudaDeviceGetDefaultMemPool(&c->A.pool, c->device));
+    uint64_t thr = ~0ull;  // keep freed blocks cached in the pool
+    HP_CUDA(cudaMemPoolSetAttribute(c->A.pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  }
+  *out = c.release();
+  return HPMDR_OK;
+}
+
+extern "C" void hpmdr_ctx_destroy(hpmdr_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+extern "C" hpmdr_status hpmdr_ctx_set_stream(hpmdr_ctx* ctx, void* stream) {
+  if (!ctx) return HPMDR_ERR_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return HPMDR_OK;
+}
+
+// ------------------------------------------------------------------ refactor
+static hpmdr_status finish_meta(hpmdr_handle* H, cudaStream_t s) {
+  HP_CUDA(cudaMemcpyAsync(H->meta.get(), H->d_meta, sizeof(FieldMeta), cudaMemcpyDeviceToHost, s));
+  HP_CUDA(cudaStreamSynchronize(s));
+  H->max_items = 0;
+  for (int l = 0; l < H->nlev; l++)
+    for (int g = 0; g < H->ngroups; g++)
+      if (H->meta->grp[l][g].method != HPMDR_DC) H->max_items += H->meta->grp[l][g].nchunks;
+  return (hpmdr_status)H->meta->status;
+}
+
+extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int field_on_device,
+                                       int ndims, const uint64_t dims_in[3], hpmdr_dtype dtype,
+                                       hpmdr_handle** out) {
+  if (!ctx || !field || !out || (dtype != HPMDR_F32 && dtype != HPMDR_F64)) return HPMDR_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<hpmdr_handle> H(new hpmdr_handle());
+  HP_TRY(check_dims(ndims, dims_in, H->dims, &H->N));
+  const cudaStream_t s = ctx->stream;
+  H->A = ctx->A;
+  H->stream = s;
+  H->dtype = dtype;
+  H->B = dtype == HPMDR_F32 ? 32 : 64;
+  H->ngroups = H->B / 4;
+  plan_levels(H.get());
+  if (H->nlev > HP_MAX_LEVELS) return HPMDR_ERR_ARG;
+  std::vector<uint32_t> chunk_group;
+  init_meta(H.get());
+  plan_groups(H.get(), ctx->Ts, ctx->cr_num, ctx->cr_den, chunk_group);
+
+  const size_t esz = dtype == HPMDR_F32 ? 4 : 8;
+  const void* f = field;
+  void* d_field = nullptr;
+  const int ngt = H->nlev * H->ngroups;
+  uint32_t *d_hist = nullptr, *d_cost = nullptr, *d_words = nullptr, *d_out = nullptr;
+  uint8_t* d_lens = nullptr;
+  hpmdr_status st = HPMDR_OK;
+  auto cleanup = [&]() {
+    H->A.release(d_field, s);
+    H->A.release(d_hist, s);
+    H->A.release(d_cost, s);
+    H->A.release(d_words, s);
+    H->A.release(d_out, s);
+    H->A.release(d_lens, s);
+  };
+  do {
+    if (!field_on_device) {
+      if ((st = H->A.alloc(&d_field, H->N * esz, s))) break;
+      if (cudaMemcpyAsync(d_field, field, H->N * esz, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        st = HPMDR_ERR_CUDA;
+        g_last_error = "field upload failed";
+        break;
+      }
+      f = d_field;
+    }
+    const uint32_t tc = std::max(H->total_chunks, 1u);
+    if ((st = H->A.alloc((void**)&H->d_levels, sizeof(LevelDesc) * H->nlev, s))) break;
+    if ((st = H->A.alloc((void**)&H->d_planes, H->plane_bytes, s))) break;
+    if ((st = H->A.alloc((void**)&H->d_slots, H->slot_bytes, s))) break;
+    if ((st = H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s))) break;
+    if ((st = H->A.alloc((void**)&H->d_chunk_group, 4ull * tc, s))) break;
+    if ((st = H->A.alloc((void**)&d_hist, 1024ull * tc, s))) break;
+    if ((st = H->A.alloc((void**)&d_cost, 4ull * tc, s))) break;
+    if ((st = H->A.alloc((void**)&d_words, 4ull * tc, s))) break;
+    if ((st = H->A.alloc((void**)&d_out, 4ull * tc, s))) break;
+    if ((st = H->A.alloc((void**)&d_lens, 256ull * ngt, s))) break;
+    if (cudaMemcpyAsync(H->d_levels, H->levels.data(), sizeof(LevelDesc) * H->nlev,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(H->d_meta, H->meta.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(H->d_chunk_group, chunk_group.data(), 4ull * H->total_chunks,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      g_last_error = "metadata upload failed";
+      break;
+    }
+    ChunkMap cm{H->d_chunk_group, H->total_chunks};
+    launch_stats(f, H->N, dtype, H->d_meta, s);
+    launch_stats_finalize(H->d_meta, s);
+    launch_levelmax(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_meta, s);
+    launch_bitlen(H->d_meta, s);
+    launch_encode(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_meta,
+                  (uint32_t*)H->d_planes, s);
+    launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_cost, s);
+    launch_decide(H->d_meta, ngt, d_hist, d_cost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, -1, s);
+    launch_huff_bits(H->d_planes, H->d_meta, cm, d_lens, d_words, s);
+    launch_group_offsets(H->d_meta, ngt, d_words, d_cost, d_out, s);
+    launch_huff_encode(H->d_planes, H->d_meta, cm, d_lens, d_out, H->d_slots, s);
+    launch_rle_encode(H->d_planes, H->d_meta, cm, d_out, H->d_slots, s);
+    launch_headers(H->d_meta, ngt, d_lens, d_out, H->d_slots, s);
+    launch_sequence(H->d_meta, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      g_last_error = std::string("refactor launch: ") + cudaGetErrorString(e);
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+  } while (0);
+  cleanup();
+  if (st != HPMDR_OK) return st;
+  st = finish_meta(H.get(), s);
+  if (st != HPMDR_OK) return st;
+  *out = H.release();
+  return HPMDR_OK;
+}
+
+// ------------------------------------------------------------------ retrieve
+static hpmdr_status ensure_retrieve_buffers(hpmdr_handle* H, cudaStream_t s) {
+  if (!H->d_rd) HP_TRY(H->A.alloc((void**)&H->d_rd, sizeof(RetrieveDev), s));
+  if (!H->d_xroot) HP_TRY(H->A.alloc((void**)&H->d_xroot, 8, s));
+  const int L = H->nlev - 1;
+  if (L >= 2 && !H->d_xa) {
+    const LevelDesc& D = H->levels[L];  // h = 1: coarse grid is G_2
+    H->xa_elems = (uint64_t)D.gc[0] * D.gc[1] * D.gc[2];
+    HP_TRY(H->A.alloc((void**)&H->d_xa, 8 * H->xa_elems, s));
+  }
+  if (L >= 3 && !H->d_xb) {
+    const LevelDesc& D = H->levels[L - 1];  // h = 2: coarse grid is G_4
+    H->xb_elems = (uint64_t)D.gc[0] * D.gc[1] * D.gc[2];
+    HP_TRY(H->A.alloc((void**)&H->d_xb, 8 * H->xb_elems, s));
+  }
+  return HPMDR_OK;
+}
+
+// enqueue select -> decode -> recompose for one handle (device-resident out)
+static hpmdr_status enqueue_retrieve(hpmdr_handle* H, double tau, int is_abs, void* d_out,
+                                     cudaStream_t s) {
+  HP_TRY(ensure_retrieve_buffers(H, s));
+  launch_select(H->d_meta, tau, is_abs, H->d_rd, s);
+  launch_decode(H->d_slots, H->d_meta, H->d_rd, H->max_items, H->d_planes, s);
+  const uint32_t* P = (const uint32_t*)H->d_planes;
+  const int L = H->nlev - 1;
+  if (L == 0) {
+    launch_recompose_root(P, H->d_meta, H->d_levels, nullptr, d_out, H->dtype, s);
+  } else {
+    launch_recompose_root(P, H->d_meta, H->d_levels, H->d_xroot, nullptr, H->dtype, s);
+    const int64_t* coarse = H->d_xroot;
+    for (int l = 1; l <= L; l++) {
+      const bool final = l == L;
+      void* dst = final ? d_out : (void*)(((L - l) % 2 == 1) ? H->d_xa : H->d_xb);
+      const int fd = final ? H->dtype : -1;
+      launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s);
+      launch_recompose_level(P, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst, H->B, fd, s);
+      coarse = (const int64_t*)dst;
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_last_error = std::string("retrieve launch: ") + cudaGetErrorString(e);
+    return HPMDR_ERR_CUDA;
+  }
+  return HPMDR_OK;
+}
+
+static hpmdr_status collect_info(hpmdr_handle* H, hpmdr_retrieve_info* info, cudaStream_t s) {
+  RetrieveDev rd;
+  int32_t mstatus = 0;
+  HP_CUDA(cudaMemcpyAsync(&rd, H->d_rd, sizeof(rd), cudaMemcpyDeviceToHost, s));
+  HP_CUDA(cudaMemcpyAsync(&mstatus, &H->d_meta->status, 4, cudaMemcpyDeviceToHost, s));
+  HP_CUDA(cudaStreamSynchronize(s));
+  if (mstatus) return (hpmdr_status)mstatus;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->est_linf = rd.E_abs;
+    info->requested_abs = rd.tau_abs;
+    info->est_units_hi = rd.E_hi;
+    info->est_units_lo = rd.E_lo;
+    info->bytes_fetched_total = rd.bytes_total;
+    info->bytes_fetched_new = rd.bytes_new;
+    info->nlevels = H->nlev;
+    for (int l = 0; l < H->nlev && l < 64; l++) info->groups_per_level[l] = rd.g[l];
+    info->status = rd.status;
+  }
+  return (hpmdr_status)rd.status;
+}
+
+static hpmdr_status retrieve_common(hpmdr_ctx* ctx, hpmdr_handle* H, double tau, int is_abs,
+                                    void* out, int out_on_device, hpmdr_retrieve_info* info) {
+  if (!ctx || !H || !out || !(tau >= 0.0)) return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  const size_t bytes = H->N * (H->dtype == HPMDR_F32 ? 4 : 8);
+  void* d_out = out;
+  if (!out_on_device) HP_TRY(H->A.alloc(&d_out, bytes, s));
+  hpmdr_status st = enqueue_retrieve(H, tau, is_abs, d_out, s);
+  if (st == HPMDR_OK && !out_on_device &&
+      cudaMemcpyAsync(out, d_out, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = HPMDR_ERR_CUDA;
+  hpmdr_status st2 = st == HPMDR_OK ? collect_info(H, info, s) : st;
+  if (!out_on_device) H->A.release(d_out, s);
+  return st2;
+}
+
+extern "C" hpmdr_status hpmdr_retrieve(hpmdr_ctx* ctx, hpmdr_handle* h, double rel, void* out,
+                                       int out_on_device, hpmdr_retrieve_info* info) {
+  return retrieve_common(ctx, h, rel, 0, out, out_on_device, info);
+}
+
+extern "C" hpmdr_status hpmdr_retrieve_abs(hpmdr_ctx* ctx, hpmdr_handle* h, double tau, void* out,
+                                           int out_on_device, hpmdr_retrieve_info* info) {
+  return retrieve_common(ctx, h, tau, 1, out, out_on_device, info);
+}
+
+// ----------------------------------------------------------------------- QoI
+extern "C" hpmdr_status hpmdr_qoi_prepare_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[3], const void* vx,
+                                               const void* vy, const void* vz, int on_device) {
+  if (!ctx || !v || !v[0] || !v[1] || !v[2] || !vx || !vy || !vz) return HPMDR_ERR_ARG;
+  for (int c = 0; c < 3; c++)
+    if (v[c]->dtype != HPMDR_F32 || v[c]->N != v[0]->N) return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  const uint64_t N = v[0]->N;
+  const void* src[3] = {vx, vy, vz};
+  void* tmp[3] = {nullptr, nullptr, nullptr};
+  float* d_q = nullptr;
+  hpmdr_status st = HPMDR_OK;
+  float q[2];
+  do {
+    for (int c = 0; c < 3 && !on_device; c++) {
+      if ((st = ctx->A.alloc(&tmp[c], N * 4, s))) break;
+      if (cudaMemcpyAsync(tmp[c], src[c], N * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        st = HPMDR_ERR_CUDA;
+        break;
+      }
+      src[c] = tmp[c];
+    }
+    if (st) break;
+    if ((st = ctx->A.alloc((void**)&d_q, 8, s))) break;
+    launch_vmag_range((const float*)src[0], (const float*)src[1], (const float*)src[2], N, d_q, s);
+    if (cudaMemcpyAsync(q, d_q, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    if (!(q[1] >= ldexpf(1.0f, -60))) st = HPMDR_ERR_ARG;  // |v| too small for FP32 squares
+    for (int c = 0; c < 3; c++) {
+      v[c]->qmin = q[0];
+      v[c]->qmax = q[1];
+      v[c]->qoi_ready = st == HPMDR_OK;
+    }
+  } while (0);
+  for (int c = 0; c < 3; c++) ctx->A.release(tmp[c], s);
+  ctx->A.release(d_q, s);
+  return st;
+}
+
+// bounds of the velocity-magnitude QoI: |(|v_hat| - |v|)| <= sqrt(sum eps_c^2),
+// plus the FP32 evaluation error of |v| on both sides (< 3 ulps relative each)
+static double qoi_component_bound(double tau_q, double qmax) {
+  const double u = ldexp(1.0, -24);
+  double slack = 7.0 * u * (qmax + tau_q);
+  double eps = (tau_q - slack) / sqrt(3.0);
+  eps = eps * (1.0 - ldexp(1.0, -50));
+  return eps > 0.0 ? eps : 0.0;
+}
+
+static double qoi_estimate(const double E[3], double qmax) {
+  const double u = ldexp(1.0, -24);
+  double r = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
+  return (r + 7.0 * u * (qmax + r)) * (1.0 + ldexp(1.0, -50));
+}
+
+extern "C" hpmdr_status hpmdr_retrieve_qoi_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[3], double rel,
+                                                void* out[3], void* out_vmag, int on_device,
+                                                hpmdr_retrieve_info info[4]) {
+  if (!ctx || !v || !out_vmag || !(rel >= 0.0)) return HPMDR_ERR_ARG;
+  for (int c = 0; c < 3; c++)
+    if (!v[c] || !v[c]->qoi_ready || v[c]->N != v[0]->N) return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  const uint64_t N = v[0]->N;
+  const double tau_q = rel * ((double)v[0]->qmax - (double)v[0]->qmin);
+  const double eps = qoi_component_bound(tau_q, (double)v[0]->qmax);
+  void* comp[3] = {nullptr, nullptr, nullptr};
+  bool own[3] = {false, false, false};
+  void* d_vm = on_device ? out_vmag : nullptr;
+  hpmdr_status st = HPMDR_OK, worst = HPMDR_OK;
+  hpmdr_retrieve_info tmp[4];
+  hpmdr_retrieve_info* inf = info ? info : tmp;
+  double E[3];
+  do {
+    for (int c = 0; c < 3; c++) {
+      if (on_device && out && out[c]) comp[c] = out[c];
+      else {
+        if ((st = ctx->A.alloc(&comp[c], N * 4, s))) break;
+        own[c] = true;
+      }
+    }
+    if (st) break;
+    if (!d_vm && (st = ctx->A.alloc(&d_vm, N * 4, s))) break;
+    for (int c = 0; c < 3; c++) {
+      if ((st = enqueue_retrieve(v[c], eps, 1, comp[c], s))) break;
+      hpmdr_status r = collect_info(v[c], &inf[c], s);
+      if (r != HPMDR_OK && r != HPMDR_ERR_UNATTAINABLE) {
+        st = r;
+        break;
+      }
+      if (r != HPMDR_OK) worst = r;
+      E[c] = inf[c].est_linf;
+    }
+    if (st) break;
+    launch_vmag((const float*)comp[0], (const float*)comp[1], (const float*)comp[2], N,
+                (float*)d_vm, s);
+    if (!on_device) {
+      for (int c = 0; c < 3; c++)
+        if (out && out[c] && cudaMemcpyAsync(out[c], comp[c], N * 4, cudaMemcpyDeviceToHost, s) !=
+                                 cudaSuccess)
+          st = HPMDR_ERR_CUDA;
+      if (cudaMemcpyAsync(out_vmag, d_vm, N * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = HPMDR_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = HPMDR_ERR_CUDA;
+    memset(&inf[3], 0, sizeof(inf[3]));
+    inf[3].est_linf = qoi_estimate(E, (double)v[0]->qmax);
+    inf[3].requested_abs = tau_q;
+    inf[3].status = worst;
+    for (int c = 0; c < 3; c++) {
+      inf[3].bytes_fetched_new += inf[c].bytes_fetched_new;
+      inf[3].bytes_fetched_total += inf[c].bytes_fetched_total;
+    }
+    if (worst == HPMDR_OK && inf[3].est_linf > tau_q) worst = HPMDR_ERR_UNATTAINABLE;
+    inf[3].status = worst;
+  } while (0);
+  for (int c = 0; c < 3; c++)
+    if (own[c]) ctx->A.release(comp[c], s);
+  if (!on_device) ctx->A.release(d_vm, s);
+  return st != HPMDR_OK ? st : worst;
+}
+
+// ------------------------------------------------------------- inspection
+extern "C" hpmdr_status hpmdr_handle_field_info(const hpmdr_handle* h, int* dtype, uint64_t dims[3],
+                                                int* nlevels, int* E_f, int* input_exact,
+                                                double stats[4]) {
+  if (!h) return HPMDR_ERR_ARG;
+  if (dtype) *dtype = h->dtype;
+  if (dims) memcpy(dims, h->dims, sizeof(h->dims));
+  if (nlevels) *nlevels = h->nlev;
+  if (E_f) *E_f = h->meta->E_f;
+  if (input_exact) *input_exact = h->meta->input_exact;
+  if (stats) {
+    stats[0] = h->meta->maxabs;
+    stats[1] = h->meta->vmin;
+    stats[2] = h->meta->vmax;
+    stats[3] = h->meta->range;
+  }
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_handle_level_info(const hpmdr_handle* h, int level, uint64_t* n,
+                                                int* bl, int* ngroups, int* exact) {
+  if (!h || level < 0 || level >= h->nlev) return HPMDR_ERR_ARG;
+  if (n) *n = h->levels[level].n;
+  if (bl) *bl = h->meta->bl[level];
+  if (ngroups) *ngroups = h->ngroups;
+  if (exact) *exact = h->meta->exact[level];
+  return HPMDR_OK;
+}
+
+static const uint8_t* group_src(const hpmdr_handle* h, int l, int g) {
+  const GroupMeta& G = h->meta->grp[l][g];
+  return G.method == HPMDR_DC ? h->d_planes + G.plane_off : h->d_slots + G.slot_off;
+}
+
+extern "C" hpmdr_status hpmdr_handle_group(const hpmdr_handle* h, int level, int group, void* buf,
+                                           uint64_t* len, int* method, uint64_t est[2]) {
+  if (!h || !len || level < 0 || level >= h->nlev || group < 0 || group >= h->ngroups)
+    return HPMDR_ERR_ARG;
+  const GroupMeta& G = h->meta->grp[level][group];
+  if (method) *method = G.method;
+  if (est) {
+    est[0] = G.est_H;
+    est[1] = G.est_R;
+  }
+  if (!buf) {
+    *len = G.stored_len;
+    return HPMDR_OK;
+  }
+  if (*len < G.stored_len) return HPMDR_ERR_ARG;
+  *len = G.stored_len;
+  HP_CUDA(cudaMemcpy(buf, group_src(h, level, group), G.stored_len, cudaMemcpyDeviceToHost));
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_handle_planes(const hpmdr_handle* h, int level, void* buf,
+                                            uint64_t* len) {
+  if (!h || !len || level < 0 || level >= h->nlev) return HPMDR_ERR_ARG;
+  const LevelDesc& D = h->levels[level];
+  const uint64_t need = (uint64_t)(h->B + 1) * D.W * 4;
+  if (!buf) {
+    *len = need;
+    return HPMDR_OK;
+  }
+  if (*len < need) return HPMDR_ERR_ARG;
+  *len = need;
+  HP_CUDA(cudaMemcpy(buf, h->d_planes + D.plane_off, need, cudaMemcpyDeviceToHost));
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_handle_sequence(const hpmdr_handle* h, int* seq, int cap, int* len) {
+  if (!h || !len) return HPMDR_ERR_ARG;
+  *len = h->meta->seq_len;
+  for (int i = 0; seq && i < h->meta->seq_len && i < cap; i++) seq[i] = h->meta->seq[i];
+  return HPMDR_OK;
+}
+
+// ------------------------------------------------------------ serialization
+// Layout (little-endian): "HPMDR1\0\0", u32 version=1, u32 reserved,
+// i32 dtype, B, nlev, ngroups, E_f, input_exact, u64 dims[3],
+// f64 maxabs, vmin, vmax, range, f32 qmin, qmax, i32 qoi_ready, i32 seq_len,
+// per level: i32 bl, i32 exact;  per (level, group): u64 stored_len, i32 method,
+// i32 reserved, u64 est_H, u64 est_R;  u8 seq[seq_len] padded to 8;
+// u64 E_hi[seq_len+1], E_lo[seq_len+1];  then each group's stored bytes in
+// (level, group) order, each padded to 16 bytes.
+namespace {
+struct Writer {
+  uint8_t* p;
+  uint64_t n = 0;
+  void put(const void* v, size_t k) {
+    if (p) memcpy(p + n, v, k);
+    n += k;
+  }
+  template <typename T>
+  void val(T v) { put(&v, sizeof(T)); }
+  void pad(size_t a) {
+    while (n % a) val<uint8_t>(0);
+  }
+};
+struct Reader {
+  const uint8_t* p;
+  uint64_t len, n = 0;
+  bool ok = true;
+  void get(void* v, size_t k) {
+    if (n + k > len) {
+      ok = false;
+      memset(v, 0, k);
+      return;
+    }
+    memcpy(v, p + n, k);
+    n += k;
+  }
+  template <typename T>
+  T val() {
+    T v;
+    get(&v, sizeof(T));
+    return v;
+  }
+  void pad(size_t a) { n = (n + a - 1) / a * a; }
+};
+}  // namespace
+
+extern "C" hpmdr_status hpmdr_handle_export(const hpmdr_handle* h, void* buf, uint64_t* len) {
+  if (!h || !len) return HPMDR_ERR_ARG;
+  const FieldMeta& M = *h->meta;
+  for (int pass = 0; pass < 2; pass++) {
+    Writer w{pass ? (uint8_t*)buf : nullptr};
+    w.put("HPMDR1\0\0", 8);
+    w.val<uint32_t>(1);
+    w.val<uint32_t>(0);
+    w.val<int32_t>(h->dtype);
+    w.val<int32_t>(h->B);
+    w.val<int32_t>(h->nlev);
+    w.val<int32_t>(h->ngroups);
+    w.val<int32_t>(M.E_f);
+    w.val<int32_t>(M.input_exact);
+    for (int d = 0; d < 3; d++) w.val<uint64_t>(h->dims[d]);
+    w.val<double>(M.maxabs);
+    w.val<double>(M.vmin);
+    w.val<double>(M.vmax);
+    w.val<double>(M.range);
+    w.val<float>(h->qmin);
+    w.val<float>(h->qmax);
+    w.val<int32_t>(h->qoi_ready ? 1 : 0);
+    w.val<int32_t>(M.seq_len);
+    for (int l = 0; l < h->nlev; l++) {
+      w.val<int32_t>(M.bl[l]);
+      w.val<int32_t>(M.exact[l]);
+    }
+    for (int l = 0; l < h->nlev; l++)
+      for (int g = 0; g < h->ngroups; g++) {
+        const GroupMeta& G = M.grp[l][g];
+        w.val<uint64_t>(G.stored_len);
+        w.val<int32_t>(G.method);
+        w.val<int32_t>(0);
+        w.val<uint64_t>(G.est_H);
+        w.val<uint64_t>(G.est_R);
+      }
+    w.put(M.seq, M.seq_len);
+    w.pad(8);
+    for (int i = 0; i <= M.seq_len; i++) w.val<uint64_t>(M.E_hi[i]);
+    for (int i = 0; i <= M.seq_len; i++) w.val<uint64_t>(M.E_lo[i]);
+    w.pad(16);
+    for (int l = 0; l < h->nlev; l++)
+      for (int g = 0; g < h->ngroups; g++) {
+        const GroupMeta& G = M.grp[l][g];
+        if (pass) HP_CUDA(cudaMemcpy(w.p + w.n, group_src(h, l, g), G.stored_len,
+                                     cudaMemcpyDeviceToHost));
+        w.n += G.stored_len;
+        w.pad(16);
+      }
+    if (!pass) {
+      if (!buf) {
+        *len = w.n;
+        return HPMDR_OK;
+      }
+      if (*len < w.n) return HPMDR_ERR_ARG;
+    } else {
+      *len = w.n;
+    }
+  }
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uint64_t len,
+                                            hpmdr_handle** out) {
+  if (!ctx || !buf || !out) return HPMDR_ERR_ARG;
+  *out = nullptr;
+  Reader r{(const uint8_t*)buf, len};
+  char magic[8];
+  r.get(magic, 8);
+  if (!r.ok || memcmp(magic, "HPMDR1\0\0", 8) != 0) return HPMDR_ERR_CORRUPT;
+  if (r.val<uint32_t>() != 1) return HPMDR_ERR_CORRUPT;
+  r.val<uint32_t>();
+  std::unique_ptr<hpmdr_handle> H(new hpmdr_handle());
+  const cudaStream_t s = ctx->stream;
+  H->A = ctx->A;
+  H->stream = s;
+  H->dtype = r.val<int32_t>();
+  H->B = r.val<int32_t>();
+  const int nlev = r.val<int32_t>();
+  H->ngroups = r.val<int32_t>();
+  if (!r.ok || (H->dtype != 0 && H->dtype != 1) || H->B != (H->dtype ? 64 : 32) ||
+      H->ngroups != H->B / 4)
+    return HPMDR_ERR_CORRUPT;
+  const int32_t E_f = r.val<int32_t>(), input_exact = r.val<int32_t>();
+  for (int d = 0; d < 3; d++) H->dims[d] = r.val<uint64_t>();
+  if (!r.ok || check_dims(3, H->dims, H->dims, &H->N) != HPMDR_OK) return HPMDR_ERR_CORRUPT;
+  plan_levels(H.get());
+  if (H->nlev != nlev || nlev > HP_MAX_LEVELS) return HPMDR_ERR_CORRUPT;
+  init_meta(H.get());
+  FieldMeta& M = *H->meta;
+  M.E_f = E_f;
+  M.input_exact = input_exact;
+  M.maxabs = r.val<double>();
+  M.vmin = r.val<double>();
+  M.vmax = r.val<double>();
+  M.range = r.val<double>();
+  H->qmin = r.val<float>();
+  H->qmax = r.val<float>();
+  H->qoi_ready = r.val<int32_t>() != 0;
+  M.seq_len = r.val<int32_t>();
+  if (M.seq_len < 0 || M.seq_len > HP_SEQ_MAX) return HPMDR_ERR_CORRUPT;
+  for (int l = 0; l < nlev; l++) {
+    M.bl[l] = r.val<int32_t>();
+    M.exact[l] = r.val<int32_t>();
+  }
+  std::vector<uint32_t> chunk_group;
+  plan_groups(H.get(), ~0ull, 1, 1, chunk_group);  // geometry only; slots re-laid below
+  uint64_t slot = 0;
+  for (int l = 0; l < nlev; l++)
+    for (int g = 0; g < H->ngroups; g++) {
+      GroupMeta& G = M.grp[l][g];
+      G.stored_len = r.val<uint64_t>();
+      G.method = r.val<int32_t>();
+      r.val<int32_t>();
+      G.est_H = r.val<uint64_t>();
+      G.est_R = r.val<uint64_t>();
+      if (G.method < 0 || G.method > 2 || (G.method == HPMDR_DC && G.stored_len != G.S))
+        return HPMDR_ERR_CORRUPT;
+      if (G.method != HPMDR_DC) {
+        G.cap = round16(G.stored_len);
+        G.slot_off = slot;
+        slot += G.cap;
+      } else {
+        G.cap = 0;
+        G.slot_off = 0;
+      }
+    }
+  H->slot_bytes = slot;
+  r.get(M.seq, M.seq_len);
+  r.pad(8);
+  for (int i = 0; i <= M.seq_len; i++) M.E_hi[i] = r.val<uint64_t>();
+  for (int i = 0; i <= M.seq_len; i++) M.E_lo[i] = r.val<uint64_t>();
+  for (int i = 0; i < M.seq_len; i++)
+    if (M.seq[i] >= nlev) return HPMDR_ERR_CORRUPT;
+  r.pad(16);
+  if (!r.ok) return HPMDR_ERR_CORRUPT;
+  const uint64_t tc = std::max(H->total_chunks, 1u);
+  HP_TRY(H->A.alloc((void**)&H->d_levels, sizeof(LevelDesc) * nlev, s));
+  HP_TRY(H->A.alloc((void**)&H->d_planes, H->plane_bytes, s));
+  HP_TRY(H->A.alloc((void**)&H->d_slots, H->slot_bytes, s));
+  HP_TRY(H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s));
+  HP_TRY(H->A.alloc((void**)&H->d_chunk_group, 4 * tc, s));
+  for (int l = 0; l < nlev; l++)
+    for (int g = 0; g < H->ngroups; g++) {
+      const GroupMeta& G = M.grp[l][g];
+      if (r.n + G.stored_len > len) return HPMDR_ERR_CORRUPT;
+      uint8_t* dst = G.method == HPMDR_DC ? H->d_planes + G.plane_off : H->d_slots + G.slot_off;
+      HP_CUDA(cudaMemcpyAsync(dst, r.p + r.n, G.stored_len, cudaMemcpyHostToDevice, s));
+      r.n += G.stored_len;
+      r.pad(16);
+    }
+  HP_CUDA(cudaMemcpyAsync(H->d_levels, H->levels.data(), sizeof(LevelDesc) * nlev,
+                          cudaMemcpyHostToDevice, s));
+  HP_CUDA(cudaMemcpyAsync(H->d_meta, H->meta.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s));
+  HP_CUDA(cudaMemcpyAsync(H->d_chunk_group, chunk_group.data(), 4ull * H->total_chunks,
+                          cudaMemcpyHostToDevice, s));
+  HP_CUDA(cudaStreamSynchronize(s));
+  H->max_items = 0;
+  for (int l = 0; l < nlev; l++)
+    for (int g = 0; g < H->ngroups; g++)
+      if (M.grp[l][g].method != HPMDR_DC) H->max_items += M.grp[l][g].nchunks;
+  *out = H.release();
+  return HPMDR_OK;
+}
+
+__global__ void k_reset(FieldMeta* m) {
+  for (int l = 0; l < HP_MAX_LEVELS; l++) {
+    m->fetched[l] = 0;
+    m->cur[l] = 0;
+  }
+}
+
+extern "C" hpmdr_status hpmdr_handle_reset(hpmdr_ctx* ctx, hpmdr_handle* h, int poison) {
+  if (!ctx || !h) return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  k_reset<<<1, 1, 0, s>>>(h->d_meta);
+  if (poison)
+    for (int l = 0; l < h->nlev; l++)
+      for (int g = 0; g < h->ngroups; g++) {
+        const GroupMeta& G = h->meta->grp[l][g];
+        if (G.method != HPMDR_DC) HP_CUDA(cudaMemsetAsync(h->d_planes + G.plane_off, 0xA5, G.S, s));
+      }
+  HP_CUDA(cudaStreamSynchronize(s));
+  return HPMDR_OK;
+}
+
+extern "C" void hpmdr_handle_free(hpmdr_handle* h) { delete h; }
+
+// --------------------------------------------------------- stage entry points
+extern "C" hpmdr_status hpmdr_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int B,
+                                              uint32_t* planes, void* stream) {
+  if (!q || !sign || !planes || n == 0 || n >= 0xffffffffull || (B != 32 && B != 64))
+    return HPMDR_ERR_ARG;
+  launch_bitplane_encode(q, sign, n, B, planes, (cudaStream_t)stream);
+  HP_CUDA(cudaGetLastError());
+  HP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k,
+                                              void* q_out, uint8_t* sign_out, void* stream) {
+  if (!planes || !q_out || !sign_out || n == 0 || n >= 0xffffffffull || (B != 32 && B != 64) ||
+      k < 0 || k > B)
+    return HPMDR_ERR_ARG;
+  launch_bitplane_decode(planes, n, B, k, q_out, sign_out, (cudaStream_t)stream);
+  HP_CUDA(cudaGetLastError());
+  HP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return HPMDR_OK;
+}
+
+// one group as a one-level, one-group "field" through the same kernels
+extern "C" hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uint64_t S, int force,
+                                           uint8_t* out, uint64_t cap, uint64_t* len, int* method) {
+  if (!ctx || !G || !out || !len || S == 0 || S >= 0xffffffffull || force < -1 || force > 2)
+    return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  std::unique_ptr<FieldMeta> M(new FieldMeta());
+  memset(M.get(), 0, sizeof(FieldMeta));
+  M->nlev = 1;
+  M->ngroups = 1;
+  GroupMeta& gm = M->grp[0][0];
+  gm.S = S;
+  gm.nchunks = (uint32_t)((S + HP_CHUNK - 1) / HP_CHUNK);
+  gm.chunk0 = 0;
+  gm.cap = cap;
+  gm.slot_off = 0;
+  gm.plane_off = 0;
+  const uint32_t nc = gm.nchunks;
+  std::vector<uint32_t> cg(nc, 0u);
+  FieldMeta* d_meta = nullptr;
+  uint8_t *d_G = nullptr, *d_lens = nullptr;
+  uint32_t *d_cg = nullptr, *d_hist = nullptr, *d_cost = nullptr, *d_words = nullptr,
+           *d_off = nullptr;
+  hpmdr_status st = HPMDR_OK;
+  do {
+    if ((st = ctx->A.alloc((void**)&d_meta, sizeof(FieldMeta), s))) break;
+    if ((st = ctx->A.alloc((void**)&d_G, round16(S), s))) break;
+    if ((st = ctx->A.alloc((void**)&d_lens, 256, s))) break;
+    if ((st = ctx->A.alloc((void**)&d_cg, 4ull * nc, s))) break;
+    if ((st = ctx->A.alloc((void**)&d_hist, 1024ull * nc, s))) break;
+    if ((st = ctx->A.alloc((void**)&d_cost, 4ull * nc, s))) break;
+    if ((st = ctx->A.alloc((void**)&d_words, 4ull * nc, s))) break;
+    if ((st = ctx->A.alloc((void**)&d_off, 4ull * nc, s))) break;
+    if (cudaMemcpyAsync(d_G, G, S, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_meta, M.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_cg, cg.data(), 4ull * nc, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    ChunkMap cm{d_cg, nc};
+    launch_chunk_stats(d_G, d_meta, cm, d_hist, d_cost, s);
+    launch_decide(d_meta, 1, d_hist, d_cost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, force, s);
+    launch_huff_bits(d_G, d_meta, cm, d_lens, d_words, s);
+    launch_group_offsets(d_meta, 1, d_words, d_cost, d_off, s);
+    launch_huff_encode(d_G, d_meta, cm, d_lens, d_off, out, s);
+    launch_rle_encode(d_G, d_meta, cm, d_off, out, s);
+    launch_headers(d_meta, 1, d_lens, d_off, out, s);
+    if (cudaMemcpyAsync(M.get(), d_meta, sizeof(FieldMeta), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    *len = M->grp[0][0].stored_len;
+    if (method) *method = M->grp[0][0].method;
+    if (M->status) {
+      st = HPMDR_ERR_ARG;  // the coded bytes did not fit in cap
+      break;
+    }
+    if (M->grp[0][0].method == HPMDR_DC) {
+      if (cap < S) {
+        st = HPMDR_ERR_ARG;
+        break;
+      }
+      if (cudaMemcpyAsync(out, G, S, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        st = HPMDR_ERR_CUDA;
+    }
+  } while (0);
+  ctx->A.release(d_meta, s);
+  ctx->A.release(d_G, s);
+  ctx->A.release(d_lens, s);
+  ctx->A.release(d_cg, s);
+  ctx->A.release(d_hist, s);
+  ctx->A.release(d_cost, s);
+  ctx->A.release(d_words, s);
+  ctx->A.release(d_off, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
+extern "C" hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, uint64_t len,
+                                           int method, uint8_t* G, uint64_t S) {
+  if (!ctx || !in || !G || S == 0 || S >= 0xffffffffull || method < 0 || method > 2)
+    return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  if (method == HPMDR_DC) {
+    if (len != S) return HPMDR_ERR_CORRUPT;
+    HP_CUDA(cudaMemcpyAsync(G, in, S, cudaMemcpyDeviceToDevice, s));
+    HP_CUDA(cudaStreamSynchronize(s));
+    return HPMDR_OK;
+  }
+  std::unique_ptr<FieldMeta> M(new FieldMeta());
+  memset(M.get(), 0, sizeof(FieldMeta));
+  M->nlev = 1;
+  M->ngroups = 1;
+  GroupMeta& gm = M->grp[0][0];
+  gm.S = S;
+  gm.nchunks = (uint32_t)((S + HP_CHUNK - 1) / HP_CHUNK);
+  gm.stored_len = len;
+  gm.method = method;
+  std::unique_ptr<RetrieveDev> rd(new RetrieveDev());
+  memset(rd.get(), 0, sizeof(RetrieveDev));
+  rd->n_new = 1;
+  rd->new_gi[0] = 0;
+  rd->new_pref[0] = 0;
+  rd->new_pref[1] = gm.nchunks;
+  rd->items = gm.nchunks;
+  FieldMeta* d_meta = nullptr;
+  RetrieveDev* d_rd = nullptr;
+  uint8_t *d_in = nullptr, *d_G = nullptr;
+  hpmdr_status st = HPMDR_OK;
+  do {
+    if ((st = ctx->A.alloc((void**)&d_meta, sizeof(FieldMeta), s))) break;
+    if ((st = ctx->A.alloc((void**)&d_rd, sizeof(RetrieveDev), s))) break;
+    if ((st = ctx->A.alloc((void**)&d_in, round16(len), s))) break;
+    if ((st = ctx->A.alloc((void**)&d_G, round16(S), s))) break;
+    if (cudaMemcpyAsync(d_in, in, len, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_meta, M.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_rd, rd.get(), sizeof(RetrieveDev), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    launch_decode(d_in, d_meta, d_rd, gm.nchunks, d_G, s);
+    int32_t ms = 0;
+    if (cudaMemcpyAsync(&ms, &d_meta->status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(G, d_G, S, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    if (ms) st = (hpmdr_status)ms;
+  } while (0);
+  ctx->A.release(d_meta, s);
+  ctx->A.release(d_rd, s);
+  ctx->A.release(d_in, s);
+  ctx->A.release(d_G, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
+// ------------------------------------------------------------------- errors
+extern "C" const char* hpmdr_strerror(hpmdr_status s) {
+  switch (s) {
+    case HPMDR_OK: return "ok";
+    case HPMDR_ERR_ARG: return "invalid argument";
+    case HPMDR_ERR_NOMEM: return "out of memory";
+    case HPMDR_ERR_CUDA: return "CUDA error";
+    case HPMDR_ERR_CORRUPT: return "corrupt stored data";
+    case HPMDR_ERR_UNATTAINABLE: return "error bound unattainable";
+    case HPMDR_ERR_TIMEOUT: return "timeout";
+    case HPMDR_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* hpmdr_last_error(void) { return g_last_error.c_str(); }

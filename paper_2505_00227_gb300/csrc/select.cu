@@ -1,0 +1,186 @@
+// Error-bound-driven selection of bitplane groups (Sec. 3 error control;
+// Algorithm 3's copy_to_device(S, eps)).
+//
+// Estimator: with k magnitude planes of level l fetched, every coefficient is
+// off by less than 2^(bl_l-k) units of U/8, i.e. delta_l = 2^(bl_l-k-3) U (zero
+// for an all-zero level, when k >= bl_l, and at k = B when the alignment
+// dropped no nonzero bit).  Recomposition adds each coefficient to a convex
+// combination of coarser values, so |x_hat - x| <= sum_l delta_l, plus one U per
+// level for the floors (when some delta > 0), plus U for the fixed-point floor
+// of the input (when it lost bits), plus half an ulp of the output type.  The
+// estimate is an exact 128-bit integer in units of 2^(E_f-51-B).
+//
+// Greedy order (independent of the bound): repeatedly fetch the next group of
+// the level with the largest 2^(bl-k) / stored bytes, ties to the smaller
+// level.  A retrieval uses the shortest prefix whose estimate meets the bound,
+// so incremental and from-scratch retrievals agree.
+#include "dev_common.cuh"
+
+namespace hp {
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 p2(int e) {
+  if (e < 0) return 0;
+  if (e > 127) e = 127;
+  return (u128)1 << e;
+}
+
+__device__ __forceinline__ u128 sat_add(u128 a, u128 b) {
+  u128 s = a + b;
+  return s < a ? ~(u128)0 : s;
+}
+
+__device__ u128 level_delta(const FieldMeta* m, int l, int k) {
+  const int bl = m->bl[l];
+  if (bl == 0 || k >= bl) return 0;
+  if (k >= m->B && m->exact[l]) return 0;
+  return p2(bl - k + m->B);
+}
+
+__device__ u128 estimate(const FieldMeta* m, const int* g) {
+  u128 E = 0;
+  bool any = false;
+  for (int l = 0; l < m->nlev; l++) {
+    u128 d = level_delta(m, l, 4 * g[l]);
+    any |= d != 0;
+    E = sat_add(E, d);
+  }
+  const u128 U = p2(m->B + 3);
+  if (any) E = sat_add(E, (u128)m->nlev * U);
+  if (!m->input_exact) E = sat_add(E, U);
+  if (E == 0) return 0;
+  u128 eps;
+  if (E < p2(m->B + 51)) {
+    int e1 = m->dtype == 0 ? m->B + 27 : m->B - 2;
+    int e2 = m->dtype == 0 ? m->B - 99 - m->E_f : m->B - 1024 - m->E_f;
+    eps = p2(e1 > e2 ? e1 : e2);
+  } else {
+    eps = E;
+  }
+  return sat_add(E, eps);
+}
+
+// 2^(bl_a-k_a) * bytes_b > 2^(bl_b-k_b) * bytes_a, ties to the smaller level
+__device__ bool better(const FieldMeta* m, const int* g, int a, int b) {
+  const int sa = m->bl[a] - 4 * g[a], sb = m->bl[b] - 4 * g[b];
+  const u128 ba = m->grp[a][g[a]].stored_len, bb = m->grp[b][g[b]].stored_len;
+  const int lo = sa < sb ? sa : sb;
+  const u128 left = bb << (sa - lo), right = ba << (sb - lo);
+  if (left != right) return left > right;
+  return a < b;
+}
+
+__global__ void k_sequence(FieldMeta* m) {
+  if (m->status) return;
+  int g[HP_MAX_LEVELS];
+  for (int l = 0; l < m->nlev; l++) {
+    g[l] = 0;
+    m->exact[l] = m->lowbits[l] == 0 ? 1 : 0;
+  }
+  int n = 0;
+  u128 E = estimate(m, g);
+  m->E_hi[0] = (uint64_t)(E >> 64);
+  m->E_lo[0] = (uint64_t)E;
+  while (n < HP_SEQ_MAX) {
+    int best = -1;
+    for (int l = 0; l < m->nlev; l++) {
+      if (g[l] >= m->ngroups) continue;
+      if (level_delta(m, l, 4 * g[l]) == 0) continue;
+      if (best < 0 || better(m, g, l, best)) best = l;
+    }
+    if (best < 0) break;
+    m->seq[n] = (uint8_t)best;
+    g[best]++;
+    n++;
+    E = estimate(m, g);
+    m->E_hi[n] = (uint64_t)(E >> 64);
+    m->E_lo[n] = (uint64_t)E;
+  }
+  m->seq_len = n;
+}
+
+void launch_sequence(FieldMeta* meta, cstream s) { k_sequence<<<1, 1, 0, s>>>(meta); }
+
+// floor(tau * 2^(51+B-E_f)) from the IEEE fields of tau, saturating at 2^127
+__device__ u128 tau_units(double tau, int E_f, int B) {
+  const uint64_t u = (uint64_t)__double_as_longlong(tau);
+  if (u >> 63) return 0;                       // negative (or -0)
+  const uint32_t e = (uint32_t)(u >> 52);
+  if (e == 0x7ff) return (u & 0xfffffffffffffull) ? 0 : p2(127);  // NaN -> 0, inf -> max
+  uint64_t m = u & 0xfffffffffffffull;
+  int ex;
+  if (e == 0) ex = -1074;
+  else {
+    m |= 0x10000000000000ull;
+    ex = (int)e - 1075;
+  }
+  if (m == 0) return 0;
+  const int s = ex + 51 + B - E_f;             // tau = m 2^ex, scaled: m 2^s
+  if (s >= 0) {
+    if (bitlen64(m) + s > 127) return p2(127);
+    return (u128)m << s;
+  }
+  if (-s >= 64) return 0;
+  return (u128)(m >> (-s));
+}
+
+__global__ void k_select(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* rd) {
+  rd->status = m->status;
+  if (m->status) return;
+  const double tau_abs = tau_is_abs ? tau : __dmul_rn(tau, m->range);
+  const u128 T = tau_units(tau_abs, m->E_f, m->B);
+  int c = 0;
+  const int n = m->seq_len;
+  while (c <= n) {
+    u128 E = ((u128)m->E_hi[c] << 64) | m->E_lo[c];
+    if (E <= T) break;
+    c++;
+  }
+  int status = 0;
+  if (c > n) {
+    c = n;
+    status = -5;  // HPMDR_ERR_UNATTAINABLE: best reconstruction, estimate reported
+  }
+  int g[HP_MAX_LEVELS];
+  for (int l = 0; l < m->nlev; l++) g[l] = 0;
+  for (int i = 0; i < c; i++) g[m->seq[i]]++;
+  uint64_t bytes_new = 0, bytes_total = 0;
+  uint32_t n_new = 0, items = 0;
+  const int ng = m->ngroups;
+  for (int l = 0; l < m->nlev; l++) {
+    for (int q = m->fetched[l]; q < g[l]; q++) {
+      const GroupMeta& gm = m->grp[l][q];
+      bytes_new += gm.stored_len;
+      if (gm.method != 0) {
+        rd->new_gi[n_new] = (uint32_t)(l * ng + q);
+        rd->new_pref[n_new] = items;
+        items += gm.nchunks;
+        n_new++;
+      }
+    }
+    if (g[l] > m->fetched[l]) m->fetched[l] = g[l];
+    for (int q = 0; q < m->fetched[l]; q++) bytes_total += m->grp[l][q].stored_len;
+    m->cur[l] = g[l];
+    rd->g[l] = g[l];
+  }
+  rd->new_pref[n_new] = items;
+  rd->n_new = n_new;
+  rd->items = items;
+  rd->bytes_new = bytes_new;
+  rd->bytes_total = bytes_total;
+  rd->nsel = c;
+  rd->status = status;
+  rd->E_hi = m->E_hi[c];
+  rd->E_lo = m->E_lo[c];
+  double v = __dadd_rn(__dmul_rn(__ull2double_rn(m->E_hi[c]), 18446744073709551616.0),
+                       __ull2double_rn(m->E_lo[c]));
+  rd->E_abs = ldexp(v, m->E_f - 51 - m->B);
+  rd->tau_abs = tau_abs;
+}
+
+void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s) {
+  k_select<<<1, 1, 0, s>>>(meta, tau, tau_is_abs, rd);
+}
+
+}  // namespace hp

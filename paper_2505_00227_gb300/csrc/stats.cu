@@ -1,0 +1,151 @@
+// Field statistics: max|f|, min f, max f in one streaming pass, then the
+// exponent E_f that fixes the alignment unit U = 2^(E_f-48) (Sec. 4, the
+// "AlignExponent" step of Algorithm 1 needs the maximum exponent first).
+#include "dev_common.cuh"
+
+namespace hp {
+
+__global__ void k_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups) {
+  meta->status = 0;
+  meta->dtype = dtype;
+  meta->B = B;
+  meta->nlev = nlev;
+  meta->ngroups = ngroups;
+  meta->key_absmax = 0;
+  meta->key_min = ~0ull;
+  meta->key_max = 0;
+  meta->floored = 0;
+  for (int l = 0; l < HP_MAX_LEVELS; l++) {
+    meta->m8[l] = 0;
+    meta->lowbits[l] = 0;
+    meta->bl[l] = 0;
+    meta->exact[l] = 1;
+    meta->fetched[l] = 0;
+    meta->cur[l] = 0;
+  }
+  meta->seq_len = 0;
+}
+
+void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, cstream s) {
+  k_meta_init<<<1, 1, 0, s>>>(meta, dtype, B, nlev, ngroups);
+}
+
+// 128-bit vector loads over the bulk, scalar loads for the tail.
+template <typename T>
+__global__ void __launch_bounds__(256) k_stats(const T* __restrict__ f, uint64_t N,
+                                               int aligned, FieldMeta* meta) {
+  constexpr int VEC = 16 / sizeof(T);
+  uint64_t amax = 0, kmin = ~0ull, kmax = 0;
+  const uint64_t nvec = aligned ? N / VEC : 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint4* fv = reinterpret_cast<const uint4*>(f);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += stride) {
+    uint4 w = __ldcs(fv + i);
+    T v[VEC];
+    memcpy(v, &w, 16);
+#pragma unroll
+    for (int k = 0; k < VEC; k++) {
+      uint64_t a = abs_key(v[k]), o = order_key(v[k]);
+      amax = a > amax ? a : amax;
+      kmin = o < kmin ? o : kmin;
+      kmax = o > kmax ? o : kmax;
+    }
+  }
+  for (uint64_t i = nvec * VEC + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += stride) {
+    T v = f[i];
+    uint64_t a = abs_key(v), o = order_key(v);
+    amax = a > amax ? a : amax;
+    kmin = o < kmin ? o : kmin;
+    kmax = o > kmax ? o : kmax;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    uint64_t a = __shfl_xor_sync(HP_FULL, amax, o);
+    uint64_t b = __shfl_xor_sync(HP_FULL, kmin, o);
+    uint64_t c = __shfl_xor_sync(HP_FULL, kmax, o);
+    amax = a > amax ? a : amax;
+    kmin = b < kmin ? b : kmin;
+    kmax = c > kmax ? c : kmax;
+  }
+  __shared__ uint64_t sa[8], sb[8], sc[8];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sa[w] = amax;
+    sb[w] = kmin;
+    sc[w] = kmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+      amax = sa[k] > amax ? sa[k] : amax;
+      kmin = sb[k] < kmin ? sb[k] : kmin;
+      kmax = sc[k] > kmax ? sc[k] : kmax;
+    }
+    atomicMax((unsigned long long*)&meta->key_absmax, (unsigned long long)amax);
+    atomicMin((unsigned long long*)&meta->key_min, (unsigned long long)kmin);
+    atomicMax((unsigned long long*)&meta->key_max, (unsigned long long)kmax);
+  }
+}
+
+void launch_stats(const void* f, uint64_t N, int dtype, FieldMeta* meta, cstream s) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint64_t per = dtype == 0 ? 4 : 2;
+  uint64_t want = (N / per + 255) / 256;
+  uint64_t grid = (uint64_t)sms * 8;
+  if (want < grid) grid = want ? want : 1;
+  int aligned = ((uintptr_t)f & 15) == 0;
+  if (dtype == 0)
+    k_stats<float><<<(unsigned)grid, 256, 0, s>>>((const float*)f, N, aligned, meta);
+  else
+    k_stats<double><<<(unsigned)grid, 256, 0, s>>>((const double*)f, N, aligned, meta);
+}
+
+__device__ double key_to_double(uint64_t k, int dtype) {
+  if (dtype == 0) {
+    uint32_t u = (uint32_t)k;
+    u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    return (double)__uint_as_float(u);
+  }
+  uint64_t u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)u);
+}
+
+// E_f = smallest integer with max|f| < 2^E_f (0 for an all-zero field);
+// rejects non-finite values and magnitudes outside the supported range.
+__global__ void k_stats_finalize(FieldMeta* meta) {
+  int dtype = meta->dtype;
+  uint64_t a = meta->key_absmax;
+  int E = 0;
+  bool bad = false;
+  if (dtype == 0) {
+    uint32_t u = (uint32_t)a;
+    bad = u >= 0x7f800000u;
+    uint32_t e = u >> 23, m = u & 0x7fffffu;
+    if (u == 0) E = 0;
+    else if (e == 0) E = (32 - __clz((int)m)) - 149;
+    else E = (int)e - 126;
+    if (E > 121) bad = true;
+    meta->maxabs = (double)__uint_as_float(u);
+  } else {
+    bad = a >= 0x7ff0000000000000ull;
+    uint32_t e = (uint32_t)(a >> 52);
+    uint64_t m = a & 0xfffffffffffffull;
+    if (a == 0) E = 0;
+    else if (e == 0) E = bitlen64(m) - 1074;
+    else E = (int)e - 1022;
+    if (E > 1017 || (a != 0 && E < -1000)) bad = true;
+    meta->maxabs = __longlong_as_double((long long)a);
+  }
+  meta->E_f = E;
+  meta->vmin = key_to_double(meta->key_min, dtype);
+  meta->vmax = key_to_double(meta->key_max, dtype);
+  meta->range = __dsub_rn(meta->vmax, meta->vmin);
+  if (bad) meta->status = -1;  // HPMDR_ERR_ARG
+}
+
+void launch_stats_finalize(FieldMeta* meta, cstream s) { k_stats_finalize<<<1, 1, 0, s>>>(meta); }
+
+}  // namespace hp
