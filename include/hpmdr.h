@@ -169,6 +169,18 @@ HPMDR_API hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uint
 HPMDR_API hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, uint64_t len, int method,
                                 uint8_t* G, uint64_t S);
 
+/* ---- measurement -------------------------------------------------------- */
+/* Kernels launched by this library in this process so far. */
+HPMDR_API uint64_t hpmdr_kernel_launches(void);
+/* enable != 0: record CUDA events on the context stream around every kernel
+ * stage (and clear the totals); 0: stop recording. */
+HPMDR_API hpmdr_status hpmdr_ctx_profile(hpmdr_ctx* ctx, int enable);
+/* totals of stage `index` (0 .. count-1; HPMDR_ERR_ARG past the end): name,
+ * summed event time in ms, launches, and algorithmic bytes (the bytes the
+ * method must read and write in that stage; 0 where not defined) */
+HPMDR_API hpmdr_status hpmdr_ctx_profile_entry(hpmdr_ctx* ctx, int index, const char** name,
+                                               double* total_ms, uint64_t* launches, double* bytes);
+
 HPMDR_API const char* hpmdr_strerror(hpmdr_status s);
 HPMDR_API const char* hpmdr_last_error(void);  /* text of the last CUDA failure on this thread */
 

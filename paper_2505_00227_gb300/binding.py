@@ -79,6 +79,10 @@ _SIGS = {
     "hpmdr_bitplane_decode": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp, vp]),
     "hpmdr_encode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64, u64p, ip]),
     "hpmdr_decode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64]),
+    "hpmdr_kernel_launches": (C.c_uint64, []),
+    "hpmdr_ctx_profile": (C.c_int, [vp, C.c_int]),
+    "hpmdr_ctx_profile_entry": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                                          u64p, C.POINTER(C.c_double)]),
     "hpmdr_strerror": (C.c_char_p, [C.c_int]),
     "hpmdr_last_error": (C.c_char_p, []),
 }
@@ -101,6 +105,11 @@ def lib():
 
 def exported_symbols():
     return list(_SIGS)
+
+
+def kernel_launches():
+    """Kernels launched by libhpmdr.so in this process so far."""
+    return int(lib().hpmdr_kernel_launches())
 
 
 def _check(status, where, allow=()):
@@ -142,6 +151,24 @@ class Context:
         self._p = vp()
         _check(lib().hpmdr_ctx_create(C.byref(self._p), C.byref(cfg), None, _stream_ptr(stream)),
                "hpmdr_ctx_create")
+
+    def profile(self, enable=True):
+        """Record per-stage CUDA events on this context's stream (clears totals)."""
+        _check(lib().hpmdr_ctx_profile(self._p, int(enable)), "hpmdr_ctx_profile")
+
+    def profile_entries(self):
+        """[(stage name, total ms, launches, algorithmic bytes)] since profile(True)."""
+        out = []
+        i = 0
+        while True:
+            name, ms, calls, by = C.c_char_p(), C.c_double(), C.c_uint64(), C.c_double()
+            st = lib().hpmdr_ctx_profile_entry(self._p, i, C.byref(name), C.byref(ms), C.byref(calls),
+                                               C.byref(by))
+            if st != OK:
+                break
+            out.append((name.value.decode(), ms.value, calls.value, by.value))
+            i += 1
+        return out
 
     def set_stream(self, stream):
         _check(lib().hpmdr_ctx_set_stream(self._p, _stream_ptr(stream)), "hpmdr_ctx_set_stream")

@@ -112,10 +112,10 @@ void launch_levelmax(const void* f, int dtype, const uint64_t dims[3], const Lev
   if (blocks == 0) blocks = 1;
   if (dtype == 0) {
     FieldView<float> v{(const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    k_levelmax<float><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta);
+    hp::note_launch(), k_levelmax<float><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta);
   } else {
     FieldView<double> v{(const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    k_levelmax<double><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta);
+    hp::note_launch(), k_levelmax<double><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta);
   }
 }
 
@@ -126,7 +126,7 @@ __global__ void k_bitlen(FieldMeta* meta) {
   if (l == 0) meta->input_exact = meta->floored ? 0 : 1;
 }
 
-void launch_bitlen(FieldMeta* meta, cstream s) { k_bitlen<<<1, HP_MAX_LEVELS, 0, s>>>(meta); }
+void launch_bitlen(FieldMeta* meta, cstream s) { hp::note_launch(), k_bitlen<<<1, HP_MAX_LEVELS, 0, s>>>(meta); }
 
 // ------------------------------------------------- register-block transpose out
 // Lane L holds in shared memory (row L, padded to 33 words) the 32 aligned
@@ -223,10 +223,10 @@ void launch_encode(const void* f, int dtype, const uint64_t dims[3], const Level
   if (blocks == 0) blocks = 1;
   if (dtype == 0) {
     FieldView<float> v{(const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    k_encode<float, 32><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta, planes);
+    hp::note_launch(), k_encode<float, 32><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta, planes);
   } else {
     FieldView<double> v{(const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    k_encode<double, 64><<<blocks, 128, 0, s>>>(v, levels, nlev, total_tiles, meta, planes);
+    hp::note_launch(), k_encode<double, 64><<<blocks, 128, 0, s>>>(v, levels, nlev, total_tiles, meta, planes);
   }
 }
 
@@ -322,9 +322,9 @@ void launch_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int 
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (B == 32)
-    k_bitplane_encode<32><<<blocks, 256, 0, s>>>(q, sign, (uint32_t)n, W, planes);
+    hp::note_launch(), k_bitplane_encode<32><<<blocks, 256, 0, s>>>(q, sign, (uint32_t)n, W, planes);
   else
-    k_bitplane_encode<64><<<blocks, 128, 0, s>>>(q, sign, (uint32_t)n, W, planes);
+    hp::note_launch(), k_bitplane_encode<64><<<blocks, 128, 0, s>>>(q, sign, (uint32_t)n, W, planes);
 }
 
 void launch_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, void* q,
@@ -337,9 +337,9 @@ void launch_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, vo
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (B == 32)
-    k_bitplane_decode<32><<<blocks, 256, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
+    hp::note_launch(), k_bitplane_decode<32><<<blocks, 256, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
   else
-    k_bitplane_decode<64><<<blocks, 128, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
+    hp::note_launch(), k_bitplane_decode<64><<<blocks, 128, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
 }
 
 }  // namespace hp

@@ -91,6 +91,9 @@ typedef struct CUstream_st* cstream;
 
 namespace hp {
 
+// counts every kernel launch made by the library (runtime.cu)
+void note_launch();
+
 // stats.cu
 void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, cstream s);
 void launch_stats(const void* f, uint64_t N, int dtype, FieldMeta* meta, cstream s);

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__
 void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* chunk_hist,
                         uint32_t* chunk_cost, cstream s) {
   if (cm.total_chunks == 0) return;
-  k_chunk_stats<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, chunk_hist,
+  hp::note_launch(), k_chunk_stats<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, chunk_hist,
                                                 chunk_cost);
 }
 
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t*
 void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_hist,
                    const uint32_t* chunk_cost, uint8_t* lens, uint64_t Ts, uint32_t cr_num,
                    uint32_t cr_den, int force, cstream s) {
-  k_decide<<<ngroups_total, 256, 0, s>>>(meta, chunk_hist, chunk_cost, lens, Ts, cr_num, cr_den,
+  hp::note_launch(), k_decide<<<ngroups_total, 256, 0, s>>>(meta, chunk_hist, chunk_cost, lens, Ts, cr_num, cr_den,
                                          force);
 }
 
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256) k_huff_bits(const uint8_t* __restrict__ p
 void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm, const uint8_t* lens,
                       uint32_t* chunk_words, cstream s) {
   if (cm.total_chunks == 0) return;
-  k_huff_bits<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_words);
+  hp::note_launch(), k_huff_bits<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_words);
 }
 
 // ------------------------------------ per-group chunk output offsets (scan)
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256) k_group_offsets(FieldMeta* meta,
 
 void launch_group_offsets(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_words,
                           const uint32_t* chunk_cost, uint32_t* chunk_out, cstream s) {
-  k_group_offsets<<<ngroups_total, 256, 0, s>>>(meta, chunk_words, chunk_cost, chunk_out);
+  hp::note_launch(), k_group_offsets<<<ngroups_total, 256, 0, s>>>(meta, chunk_words, chunk_cost, chunk_out);
 }
 
 // -------------------------------------------------------- Huffman: encode
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256) k_huff_encode(const uint8_t* __restrict__
 void launch_huff_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
                         const uint8_t* lens, const uint32_t* chunk_out, uint8_t* slots, cstream s) {
   if (cm.total_chunks == 0) return;
-  k_huff_encode<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_out,
+  hp::note_launch(), k_huff_encode<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_out,
                                                 slots);
 }
 
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(256) k_rle_encode(const uint8_t* __restrict__ 
 void launch_rle_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
                        const uint32_t* chunk_out, uint8_t* slots, cstream s) {
   if (cm.total_chunks == 0) return;
-  k_rle_encode<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, chunk_out, slots);
+  hp::note_launch(), k_rle_encode<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, chunk_out, slots);
 }
 
 // ---------------------------------------------------------- group headers
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(256) k_headers(const FieldMeta* __restrict__ m
 
 void launch_headers(FieldMeta* meta, int ngroups_total, const uint8_t* lens,
                     const uint32_t* chunk_out, uint8_t* slots, cstream s) {
-  k_headers<<<ngroups_total, 256, 0, s>>>(meta, lens, chunk_out, slots);
+  hp::note_launch(), k_headers<<<ngroups_total, 256, 0, s>>>(meta, lens, chunk_out, slots);
 }
 
 // ================================================================ decoding
@@ -684,7 +684,7 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   uint32_t blocks = (max_items + 7) / 8;
   uint32_t cap = (uint32_t)sms * 8;
   if (blocks > cap) blocks = cap;
-  k_decode<<<blocks, 256, 0, s>>>(slots, meta, rd, planes);
+  hp::note_launch(), k_decode<<<blocks, 256, 0, s>>>(slots, meta, rd, planes);
 }
 
 }  // namespace hp

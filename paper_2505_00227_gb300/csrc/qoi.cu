@@ -44,8 +44,8 @@ void launch_vmag_range(const float* vx, const float* vy, const float* vz, uint64
   uint64_t blocks = (N + 255) / 256, cap = (uint64_t)sms * 8;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  k_vmag_range_init<<<1, 1, 0, s>>>((unsigned int*)qrange);
-  k_vmag_range<<<(unsigned)blocks, 256, 0, s>>>(vx, vy, vz, N, (unsigned int*)qrange);
+  hp::note_launch(), k_vmag_range_init<<<1, 1, 0, s>>>((unsigned int*)qrange);
+  hp::note_launch(), k_vmag_range<<<(unsigned)blocks, 256, 0, s>>>(vx, vy, vz, N, (unsigned int*)qrange);
 }
 
 __global__ void __launch_bounds__(256) k_vmag(const float* __restrict__ vx, const float* __restrict__ vy,
@@ -64,7 +64,7 @@ void launch_vmag(const float* vx, const float* vy, const float* vz, uint64_t N, 
   uint64_t blocks = (N + 255) / 256, cap = (uint64_t)sms * 16;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  k_vmag<<<(unsigned)blocks, 256, 0, s>>>(vx, vy, vz, N, out);
+  hp::note_launch(), k_vmag<<<(unsigned)blocks, 256, 0, s>>>(vx, vy, vz, N, out);
 }
 
 }  // namespace hp

@@ -58,9 +58,9 @@ __global__ void k_recompose_root(const uint32_t* __restrict__ planes, const Fiel
 void launch_recompose_root(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* L0,
                            int64_t* xroot, void* out, int dtype, cstream s) {
   if (dtype == 0)
-    k_recompose_root<float><<<1, 1, 0, s>>>(planes, meta, L0, xroot, (float*)out);
+    hp::note_launch(), k_recompose_root<float><<<1, 1, 0, s>>>(planes, meta, L0, xroot, (float*)out);
   else
-    k_recompose_root<double><<<1, 1, 0, s>>>(planes, meta, L0, xroot, (double*)out);
+    hp::note_launch(), k_recompose_root<double><<<1, 1, 0, s>>>(planes, meta, L0, xroot, (double*)out);
 }
 
 // coarse nodes (all coordinates even in G_h) are copied from G_2h
@@ -181,11 +181,11 @@ void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const 
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (final_dtype < 0)
-    k_recompose_copy<float, false><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+    hp::note_launch(), k_recompose_copy<float, false><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
   else if (final_dtype == 0)
-    k_recompose_copy<float, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+    hp::note_launch(), k_recompose_copy<float, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
   else
-    k_recompose_copy<double, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+    hp::note_launch(), k_recompose_copy<double, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
 }
 
 void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,
@@ -198,14 +198,14 @@ void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const
   const int thr = B == 32 ? 256 : 128;
   if (B == 32) {
     if (final_dtype < 0)
-      k_recompose_level<float, 32, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+      hp::note_launch(), k_recompose_level<float, 32, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
     else
-      k_recompose_level<float, 32, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+      hp::note_launch(), k_recompose_level<float, 32, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
   } else {
     if (final_dtype < 0)
-      k_recompose_level<double, 64, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+      hp::note_launch(), k_recompose_level<double, 64, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
     else
-      k_recompose_level<double, 64, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+      hp::note_launch(), k_recompose_level<double, 64, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
   }
 }
 

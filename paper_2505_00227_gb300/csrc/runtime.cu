@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -18,6 +21,95 @@
 using namespace hp;
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void hp::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------ profiling
+// Optional per-stage CUDA events on the context stream: elapsed time per
+// kernel stage plus the stage's algorithmic bytes (what the method must move).
+enum Stage {
+  ST_STATS, ST_FINALIZE, ST_LEVELMAX, ST_BITLEN, ST_ENCODE, ST_CHUNK_STATS, ST_DECIDE,
+  ST_HUFF_BITS, ST_OFFSETS, ST_HUFF_ENC, ST_RLE_ENC, ST_HEADERS, ST_SEQUENCE, ST_SELECT,
+  ST_DECODE, ST_ROOT, ST_COPY, ST_LEVEL, ST_COPY_OUT, ST_LEVEL_OUT, ST_VMAG, NSTAGE
+};
+static const char* kStageName[NSTAGE] = {
+    "stats", "stats_finalize", "levelmax", "bitlen", "encode", "chunk_stats", "decide",
+    "huff_bits", "group_offsets", "huff_encode", "rle_encode", "headers", "sequence", "select",
+    "decode", "recompose_root", "recompose_copy", "recompose_level", "recompose_copy_out",
+    "recompose_level_out", "vmag"};
+
+struct ProfEntry {
+  int stage;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<ProfEntry> pending;
+  double ms[NSTAGE] = {}, bytes[NSTAGE] = {};
+  uint64_t calls[NSTAGE] = {};
+  cudaEvent_t get() {
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  size_t begin(int stage, double b, cudaStream_t s) {
+    if (!on) return SIZE_MAX;
+    ProfEntry p{stage, get(), get(), b};
+    cudaEventRecord(p.a, s);
+    pending.push_back(p);
+    return pending.size() - 1;
+  }
+  void end(size_t i, cudaStream_t s) {
+    if (i != SIZE_MAX) cudaEventRecord(pending[i].b, s);
+  }
+  void patch(size_t i, double b) {
+    if (i != SIZE_MAX && i < pending.size()) pending[i].bytes = b;
+  }
+  void resolve() {
+    for (auto& p : pending) {
+      float t = 0;
+      cudaEventSynchronize(p.b);
+      cudaEventElapsedTime(&t, p.a, p.b);
+      ms[p.stage] += t;
+      bytes[p.stage] += p.bytes;
+      calls[p.stage]++;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void reset() {
+    resolve();
+    for (int i = 0; i < NSTAGE; i++) ms[i] = bytes[i] = 0, calls[i] = 0;
+  }
+  ~Profiler() {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct ProfScope {
+  Profiler* P;
+  size_t i;
+  cudaStream_t s;
+  ProfScope(Profiler* p, int stage, double bytes, cudaStream_t st)
+      : P(p), i(p ? p->begin(stage, bytes, st) : SIZE_MAX), s(st) {}
+  ~ProfScope() {
+    if (P) P->end(i, s);
+  }
+};
 
 #define HP_CUDA(call)                                                              \
   do {                                                                             \
@@ -68,6 +160,8 @@ struct hpmdr_ctx {
   uint64_t Ts = 4096;
   uint32_t cr_num = 2, cr_den = 1;
   Allocator A;
+  Profiler prof;
+  Profiler* P() { return prof.on ? &prof : nullptr; }
 };
 
 struct hpmdr_handle {
@@ -91,6 +185,9 @@ struct hpmdr_handle {
   std::unique_ptr<FieldMeta> meta{new FieldMeta()};  // host mirror after refactor/import
   bool qoi_ready = false;
   float qmin = 0, qmax = 0;
+  // profiler entries of the last retrieval, patched with bytes known after it
+  std::vector<std::pair<size_t, int>> prof_lv;  // (entry, level*4 + kind)
+  size_t prof_decode = SIZE_MAX;
 
   ~hpmdr_handle() {
     A.release(d_levels, stream);
@@ -315,6 +412,7 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
   const int ngt = H->nlev * H->ngroups;
   uint32_t *d_hist = nullptr, *d_cost = nullptr, *d_words = nullptr, *d_out = nullptr;
   uint8_t* d_lens = nullptr;
+  size_t i_hbits = SIZE_MAX, i_henc = SIZE_MAX, i_renc = SIZE_MAX;
   hpmdr_status st = HPMDR_OK;
   auto cleanup = [&]() {
     H->A.release(d_field, s);
@@ -356,20 +454,31 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
       break;
     }
     ChunkMap cm{H->d_chunk_group, H->total_chunks};
-    launch_stats(f, H->N, dtype, H->d_meta, s);
-    launch_stats_finalize(H->d_meta, s);
-    launch_levelmax(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_meta, s);
-    launch_bitlen(H->d_meta, s);
-    launch_encode(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_meta,
-                  (uint32_t*)H->d_planes, s);
-    launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_cost, s);
-    launch_decide(H->d_meta, ngt, d_hist, d_cost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, -1, s);
-    launch_huff_bits(H->d_planes, H->d_meta, cm, d_lens, d_words, s);
-    launch_group_offsets(H->d_meta, ngt, d_words, d_cost, d_out, s);
-    launch_huff_encode(H->d_planes, H->d_meta, cm, d_lens, d_out, H->d_slots, s);
-    launch_rle_encode(H->d_planes, H->d_meta, cm, d_out, H->d_slots, s);
-    launch_headers(H->d_meta, ngt, d_lens, d_out, H->d_slots, s);
-    launch_sequence(H->d_meta, s);
+    Profiler* P = ctx->P();
+    const double fb = (double)H->N * esz, pb = (double)H->plane_bytes, cb = 1028.0 * tc;
+    { ProfScope p(P, ST_STATS, fb, s); launch_stats(f, H->N, dtype, H->d_meta, s); }
+    { ProfScope p(P, ST_FINALIZE, 0, s); launch_stats_finalize(H->d_meta, s); }
+    { ProfScope p(P, ST_LEVELMAX, fb, s);
+      launch_levelmax(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_meta, s); }
+    { ProfScope p(P, ST_BITLEN, 0, s); launch_bitlen(H->d_meta, s); }
+    { ProfScope p(P, ST_ENCODE, fb + pb, s);
+      launch_encode(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_meta,
+                    (uint32_t*)H->d_planes, s); }
+    { ProfScope p(P, ST_CHUNK_STATS, pb + cb, s);
+      launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_cost, s); }
+    { ProfScope p(P, ST_DECIDE, cb, s);
+      launch_decide(H->d_meta, ngt, d_hist, d_cost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, -1,
+                    s); }
+    { ProfScope p(P, ST_HUFF_BITS, 0, s); i_hbits = p.i;
+      launch_huff_bits(H->d_planes, H->d_meta, cm, d_lens, d_words, s); }
+    { ProfScope p(P, ST_OFFSETS, 0, s);
+      launch_group_offsets(H->d_meta, ngt, d_words, d_cost, d_out, s); }
+    { ProfScope p(P, ST_HUFF_ENC, 0, s); i_henc = p.i;
+      launch_huff_encode(H->d_planes, H->d_meta, cm, d_lens, d_out, H->d_slots, s); }
+    { ProfScope p(P, ST_RLE_ENC, 0, s); i_renc = p.i;
+      launch_rle_encode(H->d_planes, H->d_meta, cm, d_out, H->d_slots, s); }
+    { ProfScope p(P, ST_HEADERS, 0, s); launch_headers(H->d_meta, ngt, d_lens, d_out, H->d_slots, s); }
+    { ProfScope p(P, ST_SEQUENCE, 0, s); launch_sequence(H->d_meta, s); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       g_last_error = std::string("refactor launch: ") + cudaGetErrorString(e);
@@ -381,6 +490,18 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
   if (st != HPMDR_OK) return st;
   st = finish_meta(H.get(), s);
   if (st != HPMDR_OK) return st;
+  if (ctx->prof.on) {  // bytes of the coder stages, known once the methods are chosen
+    double hS = 0, hC = 0, rS = 0, rC = 0;
+    for (int l = 0; l < H->nlev; l++)
+      for (int g = 0; g < H->ngroups; g++) {
+        const GroupMeta& G = H->meta->grp[l][g];
+        if (G.method == HPMDR_HUFFMAN) hS += G.S, hC += G.stored_len;
+        if (G.method == HPMDR_RLE) rS += G.S, rC += G.stored_len;
+      }
+    ctx->prof.patch(i_hbits, hS);
+    ctx->prof.patch(i_henc, hS + hC);
+    ctx->prof.patch(i_renc, rS + rC);
+  }
   *out = H.release();
   return HPMDR_OK;
 }
@@ -404,24 +525,35 @@ static hpmdr_status ensure_retrieve_buffers(hpmdr_handle* H, cudaStream_t s) {
 }
 
 // enqueue select -> decode -> recompose for one handle (device-resident out)
-static hpmdr_status enqueue_retrieve(hpmdr_handle* H, double tau, int is_abs, void* d_out,
-                                     cudaStream_t s) {
+static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau, int is_abs,
+                                     void* d_out, cudaStream_t s) {
   HP_TRY(ensure_retrieve_buffers(H, s));
-  launch_select(H->d_meta, tau, is_abs, H->d_rd, s);
-  launch_decode(H->d_slots, H->d_meta, H->d_rd, H->max_items, H->d_planes, s);
-  const uint32_t* P = (const uint32_t*)H->d_planes;
+  Profiler* P = ctx->P();
+  H->prof_lv.clear();
+  H->prof_decode = SIZE_MAX;
+  { ProfScope p(P, ST_SELECT, 0, s); launch_select(H->d_meta, tau, is_abs, H->d_rd, s); }
+  { ProfScope p(P, ST_DECODE, 0, s); H->prof_decode = p.i;
+    launch_decode(H->d_slots, H->d_meta, H->d_rd, H->max_items, H->d_planes, s); }
+  const uint32_t* Pl = (const uint32_t*)H->d_planes;
   const int L = H->nlev - 1;
   if (L == 0) {
-    launch_recompose_root(P, H->d_meta, H->d_levels, nullptr, d_out, H->dtype, s);
+    ProfScope p(P, ST_ROOT, 0, s);
+    launch_recompose_root(Pl, H->d_meta, H->d_levels, nullptr, d_out, H->dtype, s);
   } else {
-    launch_recompose_root(P, H->d_meta, H->d_levels, H->d_xroot, nullptr, H->dtype, s);
+    { ProfScope p(P, ST_ROOT, 0, s);
+      launch_recompose_root(Pl, H->d_meta, H->d_levels, H->d_xroot, nullptr, H->dtype, s); }
     const int64_t* coarse = H->d_xroot;
     for (int l = 1; l <= L; l++) {
       const bool final = l == L;
       void* dst = final ? d_out : (void*)(((L - l) % 2 == 1) ? H->d_xa : H->d_xb);
       const int fd = final ? H->dtype : -1;
-      launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s);
-      launch_recompose_level(P, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst, H->B, fd, s);
+      { ProfScope p(P, final ? ST_COPY_OUT : ST_COPY, 0, s);
+        H->prof_lv.push_back({p.i, l * 4 + (final ? 2 : 0)});
+        launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s); }
+      { ProfScope p(P, final ? ST_LEVEL_OUT : ST_LEVEL, 0, s);
+        H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
+        launch_recompose_level(Pl, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst, H->B, fd,
+                               s); }
       coarse = (const int64_t*)dst;
     }
   }
@@ -433,13 +565,42 @@ static hpmdr_status enqueue_retrieve(hpmdr_handle* H, double tau, int is_abs, vo
   return HPMDR_OK;
 }
 
-static hpmdr_status collect_info(hpmdr_handle* H, hpmdr_retrieve_info* info, cudaStream_t s) {
+// algorithmic bytes of the last retrieval's stages, once the selection is known
+static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const RetrieveDev& rd) {
+  if (!ctx->prof.on) return;
+  const int ng = H->ngroups;
+  const double esz = H->dtype == HPMDR_F32 ? 4.0 : 8.0;
+  double dec = 0;
+  for (uint32_t i = 0; i < rd.n_new && i < HP_SEQ_MAX; i++) {
+    const GroupMeta& G = H->meta->grp[rd.new_gi[i] / ng][rd.new_gi[i] % ng];
+    dec += (double)G.stored_len + (double)G.S;
+  }
+  ctx->prof.patch(H->prof_decode, dec);
+  for (auto& pe : H->prof_lv) {
+    const int l = pe.second / 4, kind = pe.second % 4;
+    const LevelDesc& D = H->levels[l];
+    const double coarse = (double)D.gc[0] * D.gc[1] * D.gc[2];
+    const double osz = kind >= 2 ? esz : 8.0;
+    double b;
+    if (kind == 0 || kind == 2) {
+      b = coarse * 8.0 + coarse * osz;
+    } else {
+      const int g = rd.g[l];
+      b = (g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0) + coarse * 8.0 + (double)D.n * osz;
+    }
+    ctx->prof.patch(pe.first, b);
+  }
+}
+
+static hpmdr_status collect_info(hpmdr_ctx* ctx, hpmdr_handle* H, hpmdr_retrieve_info* info,
+                                 cudaStream_t s) {
   RetrieveDev rd;
   int32_t mstatus = 0;
   HP_CUDA(cudaMemcpyAsync(&rd, H->d_rd, sizeof(rd), cudaMemcpyDeviceToHost, s));
   HP_CUDA(cudaMemcpyAsync(&mstatus, &H->d_meta->status, 4, cudaMemcpyDeviceToHost, s));
   HP_CUDA(cudaStreamSynchronize(s));
   if (mstatus) return (hpmdr_status)mstatus;
+  patch_retrieve_bytes(ctx, H, rd);
   if (info) {
     memset(info, 0, sizeof(*info));
     info->est_linf = rd.E_abs;
@@ -462,11 +623,11 @@ static hpmdr_status retrieve_common(hpmdr_ctx* ctx, hpmdr_handle* H, double tau,
   const size_t bytes = H->N * (H->dtype == HPMDR_F32 ? 4 : 8);
   void* d_out = out;
   if (!out_on_device) HP_TRY(H->A.alloc(&d_out, bytes, s));
-  hpmdr_status st = enqueue_retrieve(H, tau, is_abs, d_out, s);
+  hpmdr_status st = enqueue_retrieve(ctx, H, tau, is_abs, d_out, s);
   if (st == HPMDR_OK && !out_on_device &&
       cudaMemcpyAsync(out, d_out, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     st = HPMDR_ERR_CUDA;
-  hpmdr_status st2 = st == HPMDR_OK ? collect_info(H, info, s) : st;
+  hpmdr_status st2 = st == HPMDR_OK ? collect_info(ctx, H, info, s) : st;
   if (!out_on_device) H->A.release(d_out, s);
   return st2;
 }
@@ -567,8 +728,8 @@ extern "C" hpmdr_status hpmdr_retrieve_qoi_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[
     if (st) break;
     if (!d_vm && (st = ctx->A.alloc(&d_vm, N * 4, s))) break;
     for (int c = 0; c < 3; c++) {
-      if ((st = enqueue_retrieve(v[c], eps, 1, comp[c], s))) break;
-      hpmdr_status r = collect_info(v[c], &inf[c], s);
+      if ((st = enqueue_retrieve(ctx, v[c], eps, 1, comp[c], s))) break;
+      hpmdr_status r = collect_info(ctx, v[c], &inf[c], s);
       if (r != HPMDR_OK && r != HPMDR_ERR_UNATTAINABLE) {
         st = r;
         break;
@@ -577,8 +738,9 @@ extern "C" hpmdr_status hpmdr_retrieve_qoi_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[
       E[c] = inf[c].est_linf;
     }
     if (st) break;
-    launch_vmag((const float*)comp[0], (const float*)comp[1], (const float*)comp[2], N,
-                (float*)d_vm, s);
+    { ProfScope p(ctx->P(), ST_VMAG, 16.0 * N, s);
+      launch_vmag((const float*)comp[0], (const float*)comp[1], (const float*)comp[2], N,
+                  (float*)d_vm, s); }
     if (!on_device) {
       for (int c = 0; c < 3; c++)
         if (out && out[c] && cudaMemcpyAsync(out[c], comp[c], N * 4, cudaMemcpyDeviceToHost, s) !=
@@ -901,7 +1063,7 @@ __global__ void k_reset(FieldMeta* m) {
 extern "C" hpmdr_status hpmdr_handle_reset(hpmdr_ctx* ctx, hpmdr_handle* h, int poison) {
   if (!ctx || !h) return HPMDR_ERR_ARG;
   const cudaStream_t s = ctx->stream;
-  k_reset<<<1, 1, 0, s>>>(h->d_meta);
+  hp::note_launch(), k_reset<<<1, 1, 0, s>>>(h->d_meta);
   if (poison)
     for (int l = 0; l < h->nlev; l++)
       for (int g = 0; g < h->ngroups; g++) {
@@ -1078,6 +1240,31 @@ extern "C" hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, ui
   ctx->A.release(d_G, s);
   cudaStreamSynchronize(s);
   return st;
+}
+
+// ----------------------------------------------------------------- profiling
+extern "C" uint64_t hpmdr_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" hpmdr_status hpmdr_ctx_profile(hpmdr_ctx* ctx, int enable) {
+  if (!ctx) return HPMDR_ERR_ARG;
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.reset();
+  ctx->prof.on = enable != 0;
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_ctx_profile_entry(hpmdr_ctx* ctx, int index, const char** name,
+                                                double* total_ms, uint64_t* launches,
+                                                double* bytes) {
+  if (!ctx || index < 0) return HPMDR_ERR_ARG;
+  if (index >= NSTAGE) return HPMDR_ERR_ARG;
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.resolve();
+  if (name) *name = kStageName[index];
+  if (total_ms) *total_ms = ctx->prof.ms[index];
+  if (launches) *launches = ctx->prof.calls[index];
+  if (bytes) *bytes = ctx->prof.bytes[index];
+  return HPMDR_OK;
 }
 
 // ------------------------------------------------------------------- errors

@@ -100,7 +100,7 @@ __global__ void k_sequence(FieldMeta* m) {
   m->seq_len = n;
 }
 
-void launch_sequence(FieldMeta* meta, cstream s) { k_sequence<<<1, 1, 0, s>>>(meta); }
+void launch_sequence(FieldMeta* meta, cstream s) { hp::note_launch(), k_sequence<<<1, 1, 0, s>>>(meta); }
 
 // floor(tau * 2^(51+B-E_f)) from the IEEE fields of tau, saturating at 2^127
 __device__ u128 tau_units(double tau, int E_f, int B) {
@@ -180,7 +180,7 @@ __global__ void k_select(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* 
 }
 
 void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s) {
-  k_select<<<1, 1, 0, s>>>(meta, tau, tau_is_abs, rd);
+  hp::note_launch(), k_select<<<1, 1, 0, s>>>(meta, tau, tau_is_abs, rd);
 }
 
 }  // namespace hp

@@ -27,7 +27,7 @@ __global__ void k_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngr
 }
 
 void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, cstream s) {
-  k_meta_init<<<1, 1, 0, s>>>(meta, dtype, B, nlev, ngroups);
+  hp::note_launch(), k_meta_init<<<1, 1, 0, s>>>(meta, dtype, B, nlev, ngroups);
 }
 
 // 128-bit vector loads over the bulk, scalar loads for the tail.
@@ -98,9 +98,9 @@ void launch_stats(const void* f, uint64_t N, int dtype, FieldMeta* meta, cstream
   if (want < grid) grid = want ? want : 1;
   int aligned = ((uintptr_t)f & 15) == 0;
   if (dtype == 0)
-    k_stats<float><<<(unsigned)grid, 256, 0, s>>>((const float*)f, N, aligned, meta);
+    hp::note_launch(), k_stats<float><<<(unsigned)grid, 256, 0, s>>>((const float*)f, N, aligned, meta);
   else
-    k_stats<double><<<(unsigned)grid, 256, 0, s>>>((const double*)f, N, aligned, meta);
+    hp::note_launch(), k_stats<double><<<(unsigned)grid, 256, 0, s>>>((const double*)f, N, aligned, meta);
 }
 
 __device__ double key_to_double(uint64_t k, int dtype) {
@@ -146,6 +146,6 @@ __global__ void k_stats_finalize(FieldMeta* meta) {
   if (bad) meta->status = -1;  // HPMDR_ERR_ARG
 }
 
-void launch_stats_finalize(FieldMeta* meta, cstream s) { k_stats_finalize<<<1, 1, 0, s>>>(meta); }
+void launch_stats_finalize(FieldMeta* meta, cstream s) { hp::note_launch(), k_stats_finalize<<<1, 1, 0, s>>>(meta); }
 
 }  // namespace hp
