@@ -168,6 +168,20 @@ HPMDR_API hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uint
                                 uint8_t* out, uint64_t cap, uint64_t* len, int* method);
 HPMDR_API hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, uint64_t len, int method,
                                 uint8_t* G, uint64_t S);
+/* hpmdr_encode_group for callers that cannot allocate device memory (a
+ * solver that owns all of HBM, or that forbids cudaMalloc/cudaFree between
+ * steps because they may synchronize the device).  No counterpart in the
+ * paper: it is the same Algorithm 2 encoder, bit for bit, but its scratch is a
+ * static device array of about 1.1 MB held by every GPU that loads the
+ * library until exit.  G (device, 16-byte aligned) holds S <= 16 MiB bytes;
+ * larger groups give HPMDR_ERR_ARG.  size_threshold / cr_num / cr_den are the
+ * T_s and T_cr of Algorithm 2 (0 = defaults).  The first call on a device looks
+ * up the array's address (make it before any stream capture).  Calls share the
+ * array: overlapping calls on the GPU race and must be serialized. */
+HPMDR_API hpmdr_status hpmdr_encode_group_noalloc(const uint8_t* G, uint64_t S, int force,
+                                                  uint64_t size_threshold, uint32_t cr_num,
+                                                  uint32_t cr_den, uint8_t* out, uint64_t cap,
+                                                  uint64_t* len, int* method, void* stream);
 
 /* ---- measurement -------------------------------------------------------- */
 /* Kernels launched by this library in this process so far. */

@@ -79,6 +79,8 @@ _SIGS = {
     "hpmdr_bitplane_decode": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp, vp]),
     "hpmdr_encode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64, u64p, ip]),
     "hpmdr_decode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64]),
+    "hpmdr_encode_group_noalloc": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_uint64, C.c_uint32,
+                                             C.c_uint32, vp, C.c_uint64, u64p, ip, vp]),
     "hpmdr_kernel_launches": (C.c_uint64, []),
     "hpmdr_ctx_profile": (C.c_int, [vp, C.c_int]),
     "hpmdr_ctx_profile_entry": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
