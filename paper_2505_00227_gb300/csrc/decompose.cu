@@ -64,7 +64,8 @@ __device__ __forceinline__ int find_level(const uint32_t* tile0, int l, uint32_t
 // ------------------------------------------------------------ pass: level max
 template <typename T>
 __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDesc* __restrict__ levels,
-                                                  int nlev, uint32_t total_tiles, FieldMeta* meta) {
+                                                  int nlev, uint32_t total_tiles,
+                                                  const uint32_t* __restrict__ perm, FieldMeta* meta) {
   __shared__ uint32_t s_tile0[HP_MAX_LEVELS + 1];
   for (int l = threadIdx.x; l <= nlev; l += blockDim.x)
     s_tile0[l] = l < nlev ? levels[l].tile0 : total_tiles;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDes
        tile += gridDim.x * wpb) {
     l = find_level(s_tile0, l, tile);
     const LevelDesc& L = levels[l];
-    const uint32_t base = (tile - L.tile0) * HP_TILE;
+    const uint32_t base = perm[tile] * HP_TILE;
     uint64_t mx = 0;
     uint32_t fl = 0;
     for (int r = 0; r < 32; r++) {
@@ -105,17 +106,18 @@ static int sm_count() {
 }
 
 void launch_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* levels,
-                     int nlev, uint32_t total_tiles, FieldMeta* meta, cstream s) {
+                     int nlev, uint32_t total_tiles, const uint32_t* perm, FieldMeta* meta,
+                     cstream s) {
   uint32_t blocks = (total_tiles + 7) / 8;
   uint32_t cap = (uint32_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (dtype == 0) {
     FieldView<float> v{(const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    hp::note_launch(), k_levelmax<float><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta);
+    hp::note_launch(), k_levelmax<float><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, perm, meta);
   } else {
     FieldView<double> v{(const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    hp::note_launch(), k_levelmax<double><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta);
+    hp::note_launch(), k_levelmax<double><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, perm, meta);
   }
 }
 
@@ -156,7 +158,7 @@ __device__ __forceinline__ void emit_word(const uint32_t* row_hi, const uint32_t
 template <typename T, int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_encode(FieldView<T> v, const LevelDesc* __restrict__ levels, int nlev, uint32_t total_tiles,
-             FieldMeta* meta, uint32_t* __restrict__ planes) {
+             const uint32_t* __restrict__ perm, FieldMeta* meta, uint32_t* __restrict__ planes) {
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_tile0[HP_MAX_LEVELS + 1];
   __shared__ uint32_t s_hi[WPB][32 * 33];
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
   for (uint32_t tile = blockIdx.x * WPB + w; tile < total_tiles; tile += gridDim.x * WPB) {
     l = find_level(s_tile0, l, tile);
     const LevelDesc& L = levels[l];
-    const uint32_t base = (tile - L.tile0) * HP_TILE;
+    const uint32_t base = perm[tile] * HP_TILE;
     const int bl = meta->bl[l];
     uint64_t low = 0;
     uint32_t my_sign = 0, fl = 0;
@@ -215,7 +217,8 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
 }
 
 void launch_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* levels,
-                   int nlev, uint32_t total_tiles, FieldMeta* meta, uint32_t* planes, cstream s) {
+                   int nlev, uint32_t total_tiles, const uint32_t* perm, FieldMeta* meta,
+                   uint32_t* planes, cstream s) {
   uint32_t wpb = dtype == 0 ? 8 : 4;
   uint32_t blocks = (total_tiles + wpb - 1) / wpb;
   uint32_t cap = (uint32_t)sm_count() * (dtype == 0 ? 8 : 16);
@@ -223,10 +226,10 @@ void launch_encode(const void* f, int dtype, const uint64_t dims[3], const Level
   if (blocks == 0) blocks = 1;
   if (dtype == 0) {
     FieldView<float> v{(const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    hp::note_launch(), k_encode<float, 32><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, meta, planes);
+    hp::note_launch(), k_encode<float, 32><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, perm, meta, planes);
   } else {
     FieldView<double> v{(const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    hp::note_launch(), k_encode<double, 64><<<blocks, 128, 0, s>>>(v, levels, nlev, total_tiles, meta, planes);
+    hp::note_launch(), k_encode<double, 64><<<blocks, 128, 0, s>>>(v, levels, nlev, total_tiles, perm, meta, planes);
   }
 }
 

@@ -100,11 +100,15 @@ void launch_stats(const void* f, uint64_t N, int dtype, FieldMeta* meta, cstream
 void launch_stats_finalize(FieldMeta* meta, cstream s);
 
 // decompose.cu
+// perm: per level, the order in which its 1024-node tiles are processed (tiles
+// of the 7 parity types covering the same region of the grid run together)
 void launch_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* levels,
-                     int nlev, uint32_t total_tiles, FieldMeta* meta, cstream s);
+                     int nlev, uint32_t total_tiles, const uint32_t* perm, FieldMeta* meta,
+                     cstream s);
 void launch_bitlen(FieldMeta* meta, cstream s);
 void launch_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* levels,
-                   int nlev, uint32_t total_tiles, FieldMeta* meta, uint32_t* planes, cstream s);
+                   int nlev, uint32_t total_tiles, const uint32_t* perm, FieldMeta* meta,
+                   uint32_t* planes, cstream s);
 void launch_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int B,
                             uint32_t* planes, cstream s);
 void launch_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, void* q,
@@ -143,8 +147,8 @@ void launch_recompose_root(const uint32_t* planes, const FieldMeta* meta, const 
 void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const int64_t* coarse,
                            void* dst, int final_dtype, const FieldMeta* meta, cstream s);
 void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,
-                            const LevelDesc& Lh_host, const int64_t* coarse, void* dst, int B,
-                            int final_dtype, cstream s);
+                            const LevelDesc& Lh_host, const uint32_t* perm, const int64_t* coarse,
+                            void* dst, int B, int final_dtype, cstream s);
 
 // qoi.cu
 void launch_vmag_range(const float* vx, const float* vy, const float* vz, uint64_t N,

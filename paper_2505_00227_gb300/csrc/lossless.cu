@@ -510,12 +510,101 @@ void launch_headers(FieldMeta* meta, int ngroups_total, const uint8_t* lens,
 // abandons the chunk (no trap).
 __device__ __forceinline__ void set_corrupt(FieldMeta* meta) { atomicExch(&meta->status, -4); }
 
+// Huffman decoding of one chunk by one warp, self-synchronizing:
+//  1. tables: canonical first code / count / sorted symbols per length and a
+//     10-bit lookup table for the short codes (built from the stored lengths);
+//  2. the chunk's bits are cut into 32 equal segments; lane i decodes from the
+//     start of segment i (maybe mid-codeword) to the first codeword start at or
+//     beyond segment i+1, recording its first 16 codeword starts;
+//  3. a pass over the lanes in order fixes each lane's true start (the end of
+//     the previous lane's true decoding): if that position is among the lane's
+//     recorded starts, its decoding from there is the true one (Huffman codes
+//     resynchronize after a few codewords); otherwise the lane decodes again;
+//  4. a prefix sum of the true counts gives each lane its output offset, and
+//     every lane decodes its own span again, writing the bytes.
+// All reads are limited to the chunk's words; an invalid code or a wrong
+// symbol count marks the data corrupt.
+#define HP_LUT_BITS 10
+#define HP_NSTART 17
+
 struct HuffTables {
-  uint16_t count[17];
+  uint16_t lut[1 << HP_LUT_BITS];  // (len << 8) | symbol for codes of <= 10 bits, 0 otherwise
   uint32_t first[17];
-  uint16_t index[17];
+  uint32_t count[17];
+  uint32_t index[17];
+  uint32_t fill[17];
   uint8_t sorted[256];
+  uint32_t starts[32][HP_NSTART];
 };
+
+struct BitReader {
+  const uint32_t* w;
+  uint32_t nwords, wi;
+  uint64_t buf;
+  int nb;
+  __device__ __forceinline__ uint32_t load(uint32_t i) const { return i < nwords ? w[i] : 0u; }
+  __device__ __forceinline__ void refill() {
+    while (nb <= 32) {
+      buf |= (uint64_t)load(wi) << (32 - nb);
+      wi++;
+      nb += 32;
+    }
+  }
+  __device__ __forceinline__ void init(uint32_t pos) {
+    wi = pos >> 5;
+    const int o = pos & 31;
+    buf = (uint64_t)load(wi) << (32 + o);
+    nb = 32 - o;
+    wi++;
+    refill();
+  }
+  __device__ __forceinline__ void consume(int L) {
+    buf <<= L;
+    nb -= L;
+    if (nb <= 32) refill();
+  }
+};
+
+// one symbol at the reader's position; returns its length, 0 for an invalid code
+__device__ __forceinline__ int huff_sym(const HuffTables& T, const BitReader& r, uint32_t& sym) {
+  const uint32_t p16 = (uint32_t)(r.buf >> 48);
+  const uint32_t e = T.lut[p16 >> (16 - HP_LUT_BITS)];
+  if (e) {
+    sym = e & 0xffu;
+    return (int)(e >> 8);
+  }
+  for (int L = HP_LUT_BITS + 1; L <= 16; L++) {
+    const uint32_t c = p16 >> (16 - L);
+    if (T.count[L] && c - T.first[L] < T.count[L]) {
+      sym = T.sorted[T.index[L] + (c - T.first[L])];
+      return L;
+    }
+  }
+  return 0;
+}
+
+// decode codewords starting in [pos, stop); returns the count, sets end / fail
+__device__ uint32_t huff_scan(const HuffTables& T, BitReader& r, uint32_t pos, uint32_t stop,
+                              uint32_t* starts, uint32_t& end, bool& fail) {
+  uint32_t c = 0;
+  fail = false;
+  r.init(pos);
+  if (starts) starts[0] = pos;
+  while (pos < stop) {
+    uint32_t sym;
+    const int L = huff_sym(T, r, sym);
+    if (!L) {
+      fail = true;
+      break;
+    }
+    r.consume(L);
+    pos += L;
+    c++;
+    if (starts && c < HP_NSTART) starts[c] = pos;
+  }
+  end = pos;
+  return c;
+}
 
 __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm,
                                   uint32_t cl, uint32_t len, uint8_t* __restrict__ dst,
@@ -531,61 +620,122 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     return;
   }
   const uint8_t* lens = stored + 16;
-  if (lane == 0) {
-    for (int L = 0; L <= 16; L++) T.count[L] = 0;
-    bool bad = false;
-    for (int s = 0; s < 256; s++) {
-      if (lens[s] > 16) bad = true;
-      else T.count[lens[s]]++;
-    }
-    T.count[0] = 0;
-    uint32_t c = 0;
-    uint16_t idx = 0;
-    for (int L = 1; L <= 16; L++) {
-      T.first[L] = c;
-      T.index[L] = idx;
-      for (int s = 0; s < 256; s++)
-        if (lens[s] == L) T.sorted[idx++] = (uint8_t)s;
-      c = (c + T.count[L]) << 1;
-    }
-    if (bad) set_corrupt(meta);
-  }
-  __syncwarp();
   const uint32_t* offs = reinterpret_cast<const uint32_t*>(stored + 272);
   const uint32_t w0 = offs[cl], w1 = offs[cl + 1];
   const uint64_t words = (gm->stored_len - hdr) / 4;
-  if (w0 > w1 || w1 > words) {
+  bool bad = w0 > w1 || w1 > words;
+  // ---- 1. decoding tables
+  if (lane < 17) T.count[lane] = 0;
+  for (int i = lane; i < (1 << HP_LUT_BITS); i += 32) T.lut[i] = 0;
+  __syncwarp();
+  for (int s = lane; s < 256; s += 32) {
+    const uint32_t L = lens[s];
+    if (L > 16) bad = true;
+    else if (L) atomicAdd(&T.count[L], 1u);
+  }
+  __syncwarp();
+  if (__any_sync(HP_FULL, bad)) {
     if (lane == 0) set_corrupt(meta);
     return;
   }
-  if (lane != 0) return;
-  const uint32_t* pay = reinterpret_cast<const uint32_t*>(stored + hdr);
-  uint64_t pos = (uint64_t)w0 * 32, lim = (uint64_t)w1 * 32;
-  uint32_t acc = 0;
-  for (uint32_t i = 0; i < len; i++) {
-    uint32_t code = 0;
-    int sym = -1;
+  if (lane == 0) {
+    uint32_t c = 0, idx = 0;
     for (int L = 1; L <= 16; L++) {
-      if (pos >= lim) break;
-      uint32_t wv = pay[pos >> 5];
-      code = (code << 1) | ((wv >> (31 - (pos & 31))) & 1u);
-      pos++;
-      if (T.count[L] && code >= T.first[L] && code - T.first[L] < T.count[L]) {
-        sym = T.sorted[T.index[L] + (code - T.first[L])];
-        break;
-      }
+      T.first[L] = c;
+      T.index[L] = idx;
+      T.fill[L] = idx;
+      idx += T.count[L];
+      c = (c + T.count[L]) << 1;
     }
-    if (sym < 0) {
-      set_corrupt(meta);
-      return;
-    }
-    acc |= (uint32_t)sym << (8 * (i & 3));
-    if ((i & 3) == 3) {
-      reinterpret_cast<uint32_t*>(dst)[i >> 2] = acc;
-      acc = 0;
+    for (int s = 0; s < 256; s++)  // counting sort into (length, symbol) order
+      if (lens[s]) T.sorted[T.fill[lens[s]]++] = (uint8_t)s;
+  }
+  __syncwarp();
+  for (int L = 1; L <= HP_LUT_BITS; L++) {
+    const uint32_t n = T.count[L];
+    for (uint32_t k = lane; k < n; k += 32) {
+      const uint32_t code = T.first[L] + k, sym = T.sorted[T.index[L] + k];
+      const uint32_t span = 1u << (HP_LUT_BITS - L), base = code << (HP_LUT_BITS - L);
+      if (base + span <= (1u << HP_LUT_BITS))  // a code set breaking Kraft is caught below
+        for (uint32_t r = 0; r < span; r++) T.lut[base + r] = (uint16_t)((L << 8) | sym);
     }
   }
-  for (uint32_t i = len & ~3u; i < len; i++) dst[i] = (uint8_t)(acc >> (8 * (i & 3)));
+  __syncwarp();
+  // ---- 2. speculative decoding of 32 equal bit segments
+  const uint32_t nbits = (w1 - w0) * 32;
+  const uint32_t seg = (nbits + 31) / 32;
+  BitReader rd;
+  rd.w = reinterpret_cast<const uint32_t*>(stored + hdr) + w0;
+  rd.nwords = w1 - w0;
+  const uint32_t s_me = min(lane * seg, nbits), s_next = min((lane + 1) * seg, nbits);
+  uint32_t e_me = s_me;
+  bool f_me = false;
+  uint32_t c_me = huff_scan(T, rd, s_me, s_next, T.starts[lane], e_me, f_me);
+  __syncwarp();
+  // ---- 3. true starts, lane by lane
+  uint32_t t_me = 0, tc_me = 0, t = 0;
+  for (int i = 0; i < 32; i++) {
+    if (lane == i) {
+      t_me = t;
+      bool found = false;
+      const uint32_t lim = c_me < HP_NSTART - 1 ? c_me : HP_NSTART - 1;
+      for (uint32_t m = 0; m <= lim && !found; m++)
+        if (T.starts[i][m] == t) {  // the true decoding joins this lane's path here
+          tc_me = c_me - m;
+          found = true;
+        }
+      uint32_t e = e_me;
+      if (!found) {
+        bool f;
+        if (t < s_next) {
+          tc_me = huff_scan(T, rd, t, s_next, nullptr, e, f);
+        } else {
+          tc_me = 0;
+          e = t;
+        }
+      }
+      t = e;
+    }
+    t = __shfl_sync(HP_FULL, t, i);
+  }
+  // ---- 4. output offsets and the final decoding
+  uint32_t o = tc_me;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t v = __shfl_up_sync(HP_FULL, o, d);
+    if (lane >= d) o += v;
+  }
+  o -= tc_me;  // exclusive
+  const uint32_t n_me = o < len ? min(tc_me, len - o) : 0u;
+  bool fail = false;
+  if (n_me) {
+    rd.init(t_me);
+    uint32_t acc = 0, p = o;
+    for (uint32_t k = 0; k < n_me; k++, p++) {
+      uint32_t sym;
+      const int L = huff_sym(T, rd, sym);
+      if (!L) {
+        fail = true;
+        break;
+      }
+      rd.consume(L);
+      acc |= sym << (8 * (p & 3));
+      if ((p & 3) == 3) {
+        if (p - 3 >= o) reinterpret_cast<uint32_t*>(dst)[p >> 2] = acc;
+        else
+          for (uint32_t q = o; q <= p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
+        acc = 0;
+      }
+    }
+    if (!fail && (p & 3))
+      for (uint32_t q = max(o, p & ~3u); q < p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
+  }
+  uint32_t total = n_me;
+#pragma unroll
+  for (int d = 16; d; d >>= 1) total += __shfl_xor_sync(HP_FULL, total, d);
+  if (__any_sync(HP_FULL, fail) || total != len) {
+    if (lane == 0) set_corrupt(meta);
+  }
 }
 
 __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm, uint32_t cl,

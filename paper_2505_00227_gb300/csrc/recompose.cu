@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(256) k_recompose_copy(const LevelDesc* __restr
 template <typename T, int B, bool FINAL>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_recompose_level(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
-                      const LevelDesc* __restrict__ Lp, const int64_t* __restrict__ coarse,
-                      void* __restrict__ dst) {
+                      const LevelDesc* __restrict__ Lp, const uint32_t* __restrict__ perm,
+                      const int64_t* __restrict__ coarse, void* __restrict__ dst) {
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
   const int k = 4 * m->cur[L.level], bl = m->bl[L.level], E_f = m->E_f;
   const uint32_t* P = planes + L.plane_off / 4;
   const uint32_t W = L.W;
-  for (uint32_t tile = blockIdx.x * WPB + w; tile < L.ntiles; tile += gridDim.x * WPB) {
-    const uint32_t base = tile * HP_TILE;
+  for (uint32_t slot = blockIdx.x * WPB + w; slot < L.ntiles; slot += gridDim.x * WPB) {
+    const uint32_t base = perm[L.tile0 + slot] * HP_TILE;
     const uint32_t wi = base / 32 + lane;
     if (wi < W) {
       uint32_t a[32];
@@ -189,8 +189,8 @@ void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const 
 }
 
 void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,
-                            const LevelDesc& Lh_host, const int64_t* coarse, void* dst, int B,
-                            int final_dtype, cstream s) {
+                            const LevelDesc& Lh_host, const uint32_t* perm, const int64_t* coarse,
+                            void* dst, int B, int final_dtype, cstream s) {
   const uint32_t wpb = B == 32 ? 8 : 4;
   uint32_t blocks = (Lh_host.ntiles + wpb - 1) / wpb, cap = (uint32_t)sms() * (B == 32 ? 8 : 16);
   if (blocks > cap) blocks = cap;
@@ -198,14 +198,14 @@ void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const
   const int thr = B == 32 ? 256 : 128;
   if (B == 32) {
     if (final_dtype < 0)
-      hp::note_launch(), k_recompose_level<float, 32, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+      hp::note_launch(), k_recompose_level<float, 32, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
     else
-      hp::note_launch(), k_recompose_level<float, 32, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+      hp::note_launch(), k_recompose_level<float, 32, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
   } else {
     if (final_dtype < 0)
-      hp::note_launch(), k_recompose_level<double, 64, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+      hp::note_launch(), k_recompose_level<double, 64, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
     else
-      hp::note_launch(), k_recompose_level<double, 64, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, coarse, dst);
+      hp::note_launch(), k_recompose_level<double, 64, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
   }
 }
 

@@ -170,9 +170,11 @@ struct hpmdr_handle {
   int dtype = 0, B = 32, nlev = 0, ngroups = 8;
   uint64_t dims[3] = {1, 1, 1}, N = 1;
   std::vector<LevelDesc> levels;
+  std::vector<uint32_t> perm;  // per level: processing order of its tiles
   uint32_t total_tiles = 0, total_chunks = 0, max_items = 0;
   uint64_t plane_bytes = 0, slot_bytes = 0;
   LevelDesc* d_levels = nullptr;
+  uint32_t* d_perm = nullptr;
   uint8_t* d_planes = nullptr;
   uint8_t* d_slots = nullptr;
   FieldMeta* d_meta = nullptr;
@@ -191,6 +193,7 @@ struct hpmdr_handle {
 
   ~hpmdr_handle() {
     A.release(d_levels, stream);
+    A.release(d_perm, stream);
     A.release(d_planes, stream);
     A.release(d_slots, stream);
     A.release(d_meta, stream);
@@ -258,6 +261,27 @@ static void plan_levels(hpmdr_handle* H) {
   }
   H->plane_bytes = poff;
   H->total_tiles = tile;
+  // Tile order: a tile starting at node j0 of parity type t sits at relative
+  // position (j0 - off_t) / count_t of its type's raster; sorting by that
+  // position makes the tiles of all seven types that cover the same region of
+  // the grid run together, so their shared coarse neighbours and field rows
+  // are read from L2 instead of being streamed from HBM once per type.
+  H->perm.assign(tile, 0);
+  for (int l = 0; l < H->nlev; l++) {
+    const LevelDesc& D = H->levels[l];
+    std::vector<std::pair<double, uint32_t>> key(D.ntiles);
+    for (uint32_t q = 0; q < D.ntiles; q++) {
+      const uint32_t j0 = q * HP_TILE;
+      int t = 1;
+      for (int k = 2; k <= 7; k++)
+        if (j0 >= D.off[k]) t = k;
+      const uint32_t cnt = D.off[t + 1] - D.off[t];
+      const double rel = (l == 0 || cnt == 0) ? 0.0 : (double)(j0 - D.off[t]) / (double)cnt;
+      key[q] = {rel + 1e-9 * t, q};
+    }
+    std::sort(key.begin(), key.end());
+    for (uint32_t q = 0; q < D.ntiles; q++) H->perm[D.tile0 + q] = key[q].second;
+  }
 }
 
 static uint64_t round16(uint64_t v) { return (v + 15) & ~15ull; }
@@ -434,6 +458,7 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
     }
     const uint32_t tc = std::max(H->total_chunks, 1u);
     if ((st = H->A.alloc((void**)&H->d_levels, sizeof(LevelDesc) * H->nlev, s))) break;
+    if ((st = H->A.alloc((void**)&H->d_perm, 4ull * std::max(H->total_tiles, 1u), s))) break;
     if ((st = H->A.alloc((void**)&H->d_planes, H->plane_bytes, s))) break;
     if ((st = H->A.alloc((void**)&H->d_slots, H->slot_bytes, s))) break;
     if ((st = H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s))) break;
@@ -445,6 +470,8 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
     if ((st = H->A.alloc((void**)&d_lens, 256ull * ngt, s))) break;
     if (cudaMemcpyAsync(H->d_levels, H->levels.data(), sizeof(LevelDesc) * H->nlev,
                         cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(H->d_perm, H->perm.data(), 4ull * H->total_tiles, cudaMemcpyHostToDevice,
+                        s) != cudaSuccess ||
         cudaMemcpyAsync(H->d_meta, H->meta.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(H->d_chunk_group, chunk_group.data(), 4ull * H->total_chunks,
@@ -459,11 +486,12 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
     { ProfScope p(P, ST_STATS, fb, s); launch_stats(f, H->N, dtype, H->d_meta, s); }
     { ProfScope p(P, ST_FINALIZE, 0, s); launch_stats_finalize(H->d_meta, s); }
     { ProfScope p(P, ST_LEVELMAX, fb, s);
-      launch_levelmax(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_meta, s); }
+      launch_levelmax(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_perm,
+                      H->d_meta, s); }
     { ProfScope p(P, ST_BITLEN, 0, s); launch_bitlen(H->d_meta, s); }
     { ProfScope p(P, ST_ENCODE, fb + pb, s);
-      launch_encode(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_meta,
-                    (uint32_t*)H->d_planes, s); }
+      launch_encode(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_perm,
+                    H->d_meta, (uint32_t*)H->d_planes, s); }
     { ProfScope p(P, ST_CHUNK_STATS, pb + cb, s);
       launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_cost, s); }
     { ProfScope p(P, ST_DECIDE, cb, s);
@@ -552,8 +580,8 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
         launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s); }
       { ProfScope p(P, final ? ST_LEVEL_OUT : ST_LEVEL, 0, s);
         H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
-        launch_recompose_level(Pl, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst, H->B, fd,
-                               s); }
+        launch_recompose_level(Pl, H->d_meta, H->d_levels + l, H->levels[l], H->d_perm, coarse,
+                               dst, H->B, fd, s); }
       coarse = (const int64_t*)dst;
     }
   }
@@ -1026,6 +1054,7 @@ extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uin
   if (!r.ok) return HPMDR_ERR_CORRUPT;
   const uint64_t tc = std::max(H->total_chunks, 1u);
   HP_TRY(H->A.alloc((void**)&H->d_levels, sizeof(LevelDesc) * nlev, s));
+  HP_TRY(H->A.alloc((void**)&H->d_perm, 4ull * std::max(H->total_tiles, 1u), s));
   HP_TRY(H->A.alloc((void**)&H->d_planes, H->plane_bytes, s));
   HP_TRY(H->A.alloc((void**)&H->d_slots, H->slot_bytes, s));
   HP_TRY(H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s));
@@ -1041,6 +1070,8 @@ extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uin
     }
   HP_CUDA(cudaMemcpyAsync(H->d_levels, H->levels.data(), sizeof(LevelDesc) * nlev,
                           cudaMemcpyHostToDevice, s));
+  HP_CUDA(cudaMemcpyAsync(H->d_perm, H->perm.data(), 4ull * H->total_tiles, cudaMemcpyHostToDevice,
+                          s));
   HP_CUDA(cudaMemcpyAsync(H->d_meta, H->meta.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s));
   HP_CUDA(cudaMemcpyAsync(H->d_chunk_group, chunk_group.data(), 4ull * H->total_chunks,
                           cudaMemcpyHostToDevice, s));
