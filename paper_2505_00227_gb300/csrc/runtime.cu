@@ -11,7 +11,10 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <array>
 #include <string>
 #include <vector>
 
@@ -266,6 +269,17 @@ static void plan_levels(hpmdr_handle* H) {
   // position makes the tiles of all seven types that cover the same region of
   // the grid run together, so their shared coarse neighbours and field rows
   // are read from L2 instead of being streamed from HBM once per type.
+  static std::mutex cache_mu;
+  static std::map<std::array<uint64_t, 4>, std::vector<uint32_t>> cache;
+  const std::array<uint64_t, 4> key_shape = {H->dims[0], H->dims[1], H->dims[2], (uint64_t)H->B};
+  {
+    std::lock_guard<std::mutex> lock(cache_mu);
+    auto it = cache.find(key_shape);
+    if (it != cache.end()) {
+      H->perm = it->second;
+      return;
+    }
+  }
   H->perm.assign(tile, 0);
   for (int l = 0; l < H->nlev; l++) {
     const LevelDesc& D = H->levels[l];
@@ -282,6 +296,9 @@ static void plan_levels(hpmdr_handle* H) {
     std::sort(key.begin(), key.end());
     for (uint32_t q = 0; q < D.ntiles; q++) H->perm[D.tile0 + q] = key[q].second;
   }
+  std::lock_guard<std::mutex> lock(cache_mu);
+  if (cache.size() > 256) cache.clear();
+  cache[key_shape] = H->perm;
 }
 
 static uint64_t round16(uint64_t v) { return (v + 15) & ~15ull; }
