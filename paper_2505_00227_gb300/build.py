@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhpmdr.so")
-UNITS = ["stats.cu", "decompose.cu", "lossless.cu", "select.cu", "recompose.cu", "qoi.cu",
+UNITS = ["stats.cu", "decompose.cu", "lossless.cu", "select.cu", "recompose.cu", "qoi.cu", "cells.cu",
          "runtime.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDes
                                                   const uint32_t* __restrict__ perm, FieldMeta* meta) {
   __shared__ uint32_t s_tile0[HP_MAX_LEVELS + 1];
   for (int l = threadIdx.x; l <= nlev; l += blockDim.x)
-    s_tile0[l] = l < nlev ? levels[l].tile0 : total_tiles;
+    s_tile0[l] = l < nlev ? levels[l].gtile0 : total_tiles;
   __syncthreads();
   if (meta->status) return;
   v.E_f = meta->E_f;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDes
        tile += gridDim.x * wpb) {
     l = find_level(s_tile0, l, tile);
     const LevelDesc& L = levels[l];
-    const uint32_t base = perm[tile] * HP_TILE;
+    const uint32_t base = perm[L.tile0 + (tile - L.gtile0)] * HP_TILE;
     uint64_t mx = 0;
     uint32_t fl = 0;
     for (int r = 0; r < 32; r++) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
   for (int l = threadIdx.x; l <= nlev; l += blockDim.x)
-    s_tile0[l] = l < nlev ? levels[l].tile0 : total_tiles;
+    s_tile0[l] = l < nlev ? levels[l].gtile0 : total_tiles;
   __syncthreads();
   if (meta->status) return;
   v.E_f = meta->E_f;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
   for (uint32_t tile = blockIdx.x * WPB + w; tile < total_tiles; tile += gridDim.x * WPB) {
     l = find_level(s_tile0, l, tile);
     const LevelDesc& L = levels[l];
-    const uint32_t base = perm[tile] * HP_TILE;
+    const uint32_t base = perm[L.tile0 + (tile - L.gtile0)] * HP_TILE;
     const int bl = meta->bl[l];
     uint64_t low = 0;
     uint32_t my_sign = 0, fl = 0;

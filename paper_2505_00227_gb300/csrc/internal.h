@@ -30,6 +30,8 @@ struct LevelDesc {
   uint32_t W;          // uint32 words per plane
   uint32_t tile0;      // first global tile of this level
   uint32_t ntiles;
+  uint32_t gtile0;     // first slot of the level in the generic kernels (0 tiles when fast)
+  int32_t fast;        // level handled by the cell kernels
   int32_t level;       // l (0 = root)
   int32_t hlog;        // log2 of the half-stride h (-1 for the root)
   uint32_t g[3];       // level grid G_h dims (z, y, x): ceil(n_d / h)
@@ -149,6 +151,16 @@ void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const 
 void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,
                             const LevelDesc& Lh_host, const uint32_t* perm, const int64_t* coarse,
                             void* dst, int B, int final_dtype, cstream s);
+
+// cells.cu (FP32 levels with g_x a multiple of 64)
+bool cell_path_ok(const LevelDesc& L, int B);
+void launch_cells_levelmax(const float* f, const uint64_t dims[3], const LevelDesc* Ld,
+                           const LevelDesc& Lh, FieldMeta* meta, cstream s);
+void launch_cells_encode(const float* f, const uint64_t dims[3], const LevelDesc* Ld,
+                         const LevelDesc& Lh, FieldMeta* meta, uint32_t* planes, cstream s);
+void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,
+                            const LevelDesc& Lh, const int64_t* coarse, void* dst, int final,
+                            cstream s);
 
 // qoi.cu
 void launch_vmag_range(const float* vx, const float* vy, const float* vz, uint64_t N,

@@ -34,13 +34,15 @@ void hp::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 enum Stage {
   ST_STATS, ST_FINALIZE, ST_LEVELMAX, ST_BITLEN, ST_ENCODE, ST_CHUNK_STATS, ST_DECIDE,
   ST_HUFF_BITS, ST_OFFSETS, ST_HUFF_ENC, ST_RLE_ENC, ST_HEADERS, ST_SEQUENCE, ST_SELECT,
-  ST_DECODE, ST_ROOT, ST_COPY, ST_LEVEL, ST_COPY_OUT, ST_LEVEL_OUT, ST_VMAG, NSTAGE
+  ST_DECODE, ST_ROOT, ST_COPY, ST_LEVEL, ST_COPY_OUT, ST_LEVEL_OUT, ST_VMAG, ST_CELLS_MAX,
+  ST_CELLS_ENC, ST_CELLS_REC, ST_CELLS_REC_OUT, NSTAGE
 };
 static const char* kStageName[NSTAGE] = {
     "stats", "stats_finalize", "levelmax", "bitlen", "encode", "chunk_stats", "decide",
     "huff_bits", "group_offsets", "huff_encode", "rle_encode", "headers", "sequence", "select",
     "decode", "recompose_root", "recompose_copy", "recompose_level", "recompose_copy_out",
-    "recompose_level_out", "vmag"};
+    "recompose_level_out", "vmag", "cells_levelmax", "cells_encode", "cells_recompose",
+    "cells_recompose_out"};
 
 struct ProfEntry {
   int stage;
@@ -174,7 +176,7 @@ struct hpmdr_handle {
   uint64_t dims[3] = {1, 1, 1}, N = 1;
   std::vector<LevelDesc> levels;
   std::vector<uint32_t> perm;  // per level: processing order of its tiles
-  uint32_t total_tiles = 0, total_chunks = 0, max_items = 0;
+  uint32_t total_tiles = 0, generic_tiles = 0, total_chunks = 0, max_items = 0;
   uint64_t plane_bytes = 0, slot_bytes = 0;
   LevelDesc* d_levels = nullptr;
   uint32_t* d_perm = nullptr;
@@ -223,7 +225,7 @@ static void plan_levels(hpmdr_handle* H) {
   H->nlev = L + 1;
   H->levels.assign(H->nlev, LevelDesc{});
   uint64_t poff = 0;
-  uint32_t tile = 0;
+  uint32_t tile = 0, gtile = 0;
   for (int l = 0; l < H->nlev; l++) {
     LevelDesc& D = H->levels[l];
     memset(&D, 0, sizeof(D));
@@ -261,9 +263,13 @@ static void plan_levels(hpmdr_handle* H) {
     D.tile0 = tile;
     D.ntiles = (uint32_t)((n + HP_TILE - 1) / HP_TILE);
     tile += D.ntiles;
+    D.fast = cell_path_ok(D, H->B) ? 1 : 0;
+    D.gtile0 = gtile;
+    if (!D.fast) gtile += D.ntiles;
   }
   H->plane_bytes = poff;
   H->total_tiles = tile;
+  H->generic_tiles = gtile;
   // Tile order: a tile starting at node j0 of parity type t sits at relative
   // position (j0 - off_t) / count_t of its type's raster; sorting by that
   // position makes the tiles of all seven types that cover the same region of
@@ -502,13 +508,36 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
     const double fb = (double)H->N * esz, pb = (double)H->plane_bytes, cb = 1028.0 * tc;
     { ProfScope p(P, ST_STATS, fb, s); launch_stats(f, H->N, dtype, H->d_meta, s); }
     { ProfScope p(P, ST_FINALIZE, 0, s); launch_stats_finalize(H->d_meta, s); }
-    { ProfScope p(P, ST_LEVELMAX, fb, s);
-      launch_levelmax(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_perm,
-                      H->d_meta, s); }
+    // algorithmic bytes: the field once (split over the level kernels by node
+    // count) and each level's planes once
+    auto lvl_bytes = [&](const LevelDesc& D, bool planes_too) {
+      return (double)D.n * esz + (planes_too ? (double)(H->B + 1) * D.W * 4.0 : 0.0);
+    };
+    double gen_f = 0, gen_p = 0;
+    for (const LevelDesc& D : H->levels)
+      if (!D.fast) gen_f += (double)D.n * esz, gen_p += (double)(H->B + 1) * D.W * 4.0;
+    for (const LevelDesc& D : H->levels)
+      if (D.fast) {
+        ProfScope p(P, ST_CELLS_MAX, lvl_bytes(D, false), s);
+        launch_cells_levelmax((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta, s);
+      }
+    if (H->generic_tiles) {
+      ProfScope p(P, ST_LEVELMAX, gen_f, s);
+      launch_levelmax(f, dtype, H->dims, H->d_levels, H->nlev, H->generic_tiles, H->d_perm,
+                      H->d_meta, s);
+    }
     { ProfScope p(P, ST_BITLEN, 0, s); launch_bitlen(H->d_meta, s); }
-    { ProfScope p(P, ST_ENCODE, fb + pb, s);
-      launch_encode(f, dtype, H->dims, H->d_levels, H->nlev, H->total_tiles, H->d_perm,
-                    H->d_meta, (uint32_t*)H->d_planes, s); }
+    for (const LevelDesc& D : H->levels)
+      if (D.fast) {
+        ProfScope p(P, ST_CELLS_ENC, lvl_bytes(D, true), s);
+        launch_cells_encode((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta,
+                            (uint32_t*)H->d_planes, s);
+      }
+    if (H->generic_tiles) {
+      ProfScope p(P, ST_ENCODE, gen_f + gen_p, s);
+      launch_encode(f, dtype, H->dims, H->d_levels, H->nlev, H->generic_tiles, H->d_perm,
+                    H->d_meta, (uint32_t*)H->d_planes, s);
+    }
     { ProfScope p(P, ST_CHUNK_STATS, pb + cb, s);
       launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_cost, s); }
     { ProfScope p(P, ST_DECIDE, cb, s);
@@ -592,13 +621,21 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
       const bool final = l == L;
       void* dst = final ? d_out : (void*)(((L - l) % 2 == 1) ? H->d_xa : H->d_xb);
       const int fd = final ? H->dtype : -1;
-      { ProfScope p(P, final ? ST_COPY_OUT : ST_COPY, 0, s);
-        H->prof_lv.push_back({p.i, l * 4 + (final ? 2 : 0)});
-        launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s); }
-      { ProfScope p(P, final ? ST_LEVEL_OUT : ST_LEVEL, 0, s);
+      if (H->levels[l].fast) {
+        ProfScope p(P, final ? ST_CELLS_REC_OUT : ST_CELLS_REC, 0, s);
         H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
-        launch_recompose_level(Pl, H->d_meta, H->d_levels + l, H->levels[l], H->d_perm, coarse,
-                               dst, H->B, fd, s); }
+        H->prof_lv.push_back({SIZE_MAX - 1, l * 4 + (final ? 2 : 0)});  // copy folded in
+        launch_cells_recompose(Pl, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst,
+                               final ? 1 : 0, s);
+      } else {
+        { ProfScope p(P, final ? ST_COPY_OUT : ST_COPY, 0, s);
+          H->prof_lv.push_back({p.i, l * 4 + (final ? 2 : 0)});
+          launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s); }
+        { ProfScope p(P, final ? ST_LEVEL_OUT : ST_LEVEL, 0, s);
+          H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
+          launch_recompose_level(Pl, H->d_meta, H->d_levels + l, H->levels[l], H->d_perm, coarse,
+                                 dst, H->B, fd, s); }
+      }
       coarse = (const int64_t*)dst;
     }
   }
@@ -621,11 +658,13 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
     dec += (double)G.stored_len + (double)G.S;
   }
   ctx->prof.patch(H->prof_decode, dec);
+  size_t last = SIZE_MAX;
+  double last_b = 0;
   for (auto& pe : H->prof_lv) {
     const int l = pe.second / 4, kind = pe.second % 4;
     const LevelDesc& D = H->levels[l];
     const double coarse = (double)D.gc[0] * D.gc[1] * D.gc[2];
-    const double osz = kind >= 2 ? esz : 8.0;
+    const double osz = (kind == 2 || kind == 3) ? esz : 8.0;
     double b;
     if (kind == 0 || kind == 2) {
       b = coarse * 8.0 + coarse * osz;
@@ -633,7 +672,14 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
       const int g = rd.g[l];
       b = (g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0) + coarse * 8.0 + (double)D.n * osz;
     }
+    if (pe.first == SIZE_MAX - 1) {  // a cell kernel also wrote the coarse nodes
+      last_b += coarse * osz;
+      ctx->prof.patch(last, last_b);
+      continue;
+    }
     ctx->prof.patch(pe.first, b);
+    last = pe.first;
+    last_b = b;
   }
 }
 

@@ -46,6 +46,11 @@ def _fields():
         "f64_blobs": S.blobs((33, 20, 18), seed=8, dtype=torch.float64).numpy(),
         "long_x": S.spectral((2, 3, 2500), seed=9).numpy(),
         "subnormal_f32": (rng.standard_normal((6, 7, 8)) * 1e-40).astype(np.float32),
+        # shapes whose large levels take the cell kernels (x extent a multiple of 64)
+        "cells_ragged_yz": S.spectral((7, 37, 128), seed=12).numpy(),
+        "cells_2d": S.blobs((1, 64, 128), seed=13).numpy(),
+        "cells_three_words": S.spectral((5, 9, 192), seed=14).numpy(),
+        "cells_256": S.spectral((24, 40, 256), seed=15).numpy(),
     }
 
 
