@@ -201,6 +201,10 @@ __global__ void __launch_bounds__(256, 2) k_cells_encode(const float* __restrict
   uint32_t* P = planes + L.plane_off / 4;
   const uint32_t W = L.W;
   uint64_t low = 0;
+  if (blockIdx.x == 0) {  // the padding words past the last node of every plane are zero
+    const uint32_t used = (L.n + 31) / 32, pad = W - used;
+    for (uint32_t k = i; k < pad * (32 + 1); k += blockDim.x) P[(size_t)(k / pad) * W + used + k % pad] = 0u;
+  }
   for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x) {
     uint32_t cz, cy0, x0;
     tile_origin(G, tile, cz, cy0, x0);
