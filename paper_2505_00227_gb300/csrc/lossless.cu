@@ -672,27 +672,42 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
   bool f_me = false;
   uint32_t c_me = huff_scan(T, rd, s_me, s_next, T.starts[lane], e_me, f_me);
   __syncwarp();
-  // ---- 3. true starts, lane by lane
+  // ---- 3. true starts, lane by lane: follow the true path from t until it
+  // meets one of the lane's recorded codeword starts (Huffman codes
+  // resynchronize), else decode the lane's segment again from t
   uint32_t t_me = 0, tc_me = 0, t = 0;
   for (int i = 0; i < 32; i++) {
     if (lane == i) {
       t_me = t;
+      const uint32_t nrec = c_me < HP_NSTART - 1 ? c_me : HP_NSTART - 1;  // starts[0..nrec]
+      const uint32_t last = T.starts[i][nrec];
       bool found = false;
-      const uint32_t lim = c_me < HP_NSTART - 1 ? c_me : HP_NSTART - 1;
-      for (uint32_t m = 0; m <= lim && !found; m++)
-        if (T.starts[i][m] == t) {  // the true decoding joins this lane's path here
-          tc_me = c_me - m;
-          found = true;
-        }
       uint32_t e = e_me;
-      if (!found) {
-        bool f;
-        if (t < s_next) {
-          tc_me = huff_scan(T, rd, t, s_next, nullptr, e, f);
-        } else {
-          tc_me = 0;
-          e = t;
+      if (t < s_next) {
+        uint32_t p = t, d = 0, m = 0;
+        BitReader tr = rd;
+        tr.init(p);
+        while (p <= last && p < s_next) {
+          while (m < nrec && T.starts[i][m] < p) m++;
+          if (T.starts[i][m] == p) {
+            tc_me = d + (c_me - m);
+            found = true;
+            break;
+          }
+          uint32_t sym;
+          const int L = huff_sym(T, tr, sym);
+          if (!L) break;
+          tr.consume(L);
+          p += L;
+          d++;
         }
+        if (!found) {
+          bool f;
+          tc_me = huff_scan(T, rd, t, s_next, nullptr, e, f);
+        }
+      } else {
+        tc_me = 0;
+        e = t;
       }
       t = e;
     }
