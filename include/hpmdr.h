@@ -172,7 +172,7 @@ HPMDR_API hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, uin
  * solver that owns all of HBM, or that forbids cudaMalloc/cudaFree between
  * steps because they may synchronize the device).  No counterpart in the
  * paper: it is the same Algorithm 2 encoder, bit for bit, but its scratch is a
- * static device array of about 1.1 MB held by every GPU that loads the
+ * static device array of about 70 KB held by every GPU that loads the
  * library until exit.  G (device, 16-byte aligned) holds S <= 16 MiB bytes;
  * larger groups give HPMDR_ERR_ARG.  size_threshold / cr_num / cr_den are the
  * T_s and T_cr of Algorithm 2 (0 = defaults).  The first call on a device looks

@@ -302,7 +302,7 @@ __device__ __forceinline__ float out_f32(int64_t X, int E_f) {
 }
 
 template <bool FINAL>
-__global__ void __launch_bounds__(256, 2) k_cells_recompose(const uint32_t* __restrict__ planes,
+__global__ void __launch_bounds__(256, 3) k_cells_recompose(const uint32_t* __restrict__ planes,
                                                          const FieldMeta* __restrict__ meta,
                                                          const LevelDesc* __restrict__ Lp,
                                                          const int64_t* __restrict__ coarse,
@@ -354,52 +354,59 @@ __global__ void __launch_bounds__(256, 2) k_cells_recompose(const uint32_t* __re
             C[a][b][4] = __ldg(row + xe);
           }
         const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
-        int64_t X[8][4];  // [node o = ox + 2 oy + 4 oz][cell k]
-#pragma unroll
-        for (int kk = 0; kk < 4; kk++) {
-          const int64_t c000 = C[0][0][kk], c001 = C[0][0][kk + 1];
-          const int64_t c010 = C[0][1][kk], c011 = C[0][1][kk + 1];
-          const int64_t c100 = C[1][0][kk], c101 = C[1][0][kk + 1];
-          const int64_t c110 = C[1][1][kk], c111 = C[1][1][kk + 1];
-          const int64_t sx0 = c000 + c001, sx1 = c010 + c011, sx2 = c100 + c101, sx3 = c110 + c111;
-          const int64_t S[7] = {sx0, c000 + c010, sx0 + sx1, c000 + c100, sx0 + sx2,
-                                c000 + c010 + c100 + c110, sx0 + sx1 + sx2 + sx3};
-          X[0][kk] = c000;
-#pragma unroll
-          for (int t = 1; t <= 7; t++) {
-            const uint32_t qh = s_q[t - 1][rw][b0 + kk];
-            const bool neg = (s_sw[t - 1][rw] >> (b0 + kk)) & 1u;
-            uint64_t mag;
-            if (bl == 0) mag = 0;
-            else if (bl <= 32) mag = qh >> (32 - bl);
-            else mag = (uint64_t)qh << (bl - 32);
-            const int64_t c8 = neg ? -(int64_t)mag : (int64_t)mag;
-            const int nodd = __popc(t);
-            X[t][kk] = (c8 * ((int64_t)1 << nodd) + 8 * S[t - 1]) >> (3 + nodd);
-          }
-        }
-        // write the 2x2x2 nodes of the 4 cells: rows (2cz+oz, 2cy+oy), x = 2cx .. 2cx+7
+        // one output row (2cz+oz, 2cy+oy) at a time: its even-x nodes are type
+        // te = 2 oy + 4 oz (te = 0: the coarse node itself), its odd-x nodes te + 1
 #pragma unroll
         for (int oz = 0; oz < 2; oz++)
 #pragma unroll
           for (int oy = 0; oy < 2; oy++) {
             if ((oz && !hz) || (oy && !hy)) continue;
-            const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
-            const int o0 = 2 * oy + 4 * oz;
-            if (FINAL) {
-              float v[8];
+            const int te = 2 * oy + 4 * oz;
+            int64_t V[8];
 #pragma unroll
-              for (int kk = 0; kk < 4; kk++) {
-                v[2 * kk] = out_f32(X[o0][kk], E_f);
-                v[2 * kk + 1] = out_f32(X[o0 + 1][kk], E_f);
+            for (int kk = 0; kk < 4; kk++) {
+#pragma unroll
+              for (int par = 0; par < 2; par++) {
+                const int t = te + par;
+                int64_t X;
+                if (t == 0) {
+                  X = C[0][0][kk];
+                } else {
+                  // corner sum of type t: the corners along its odd axes
+                  int64_t S = 0;
+#pragma unroll
+                  for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+                    for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                      for (int dx = 0; dx < 2; dx++) {
+                        if ((dz && !(t & 4)) || (dy && !(t & 2)) || (dx && !(t & 1))) continue;
+                        S += C[dz][dy][kk + dx];
+                      }
+                  const uint32_t qh = s_q[t - 1][rw][b0 + kk];
+                  const bool neg = (s_sw[t - 1][rw] >> (b0 + kk)) & 1u;
+                  uint64_t mag;
+                  if (bl == 0) mag = 0;
+                  else if (bl <= 32) mag = qh >> (32 - bl);
+                  else mag = (uint64_t)qh << (bl - 32);
+                  const int64_t c8 = neg ? -(int64_t)mag : (int64_t)mag;
+                  const int nodd = __popc(t);
+                  X = (c8 * ((int64_t)1 << nodd) + 8 * S) >> (3 + nodd);
+                }
+                V[2 * kk + par] = X;
               }
+            }
+            const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
+            if (FINAL) {
               float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base);
-              d4[0] = make_float4(v[0], v[1], v[2], v[3]);
-              d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+              d4[0] = make_float4(out_f32(V[0], E_f), out_f32(V[1], E_f), out_f32(V[2], E_f),
+                                  out_f32(V[3], E_f));
+              d4[1] = make_float4(out_f32(V[4], E_f), out_f32(V[5], E_f), out_f32(V[6], E_f),
+                                  out_f32(V[7], E_f));
             } else {
               longlong2* d2 = reinterpret_cast<longlong2*>(reinterpret_cast<int64_t*>(dst) + base);
 #pragma unroll
-              for (int kk = 0; kk < 4; kk++) d2[kk] = make_longlong2(X[o0][kk], X[o0 + 1][kk]);
+              for (int kk = 0; kk < 4; kk++) d2[kk] = make_longlong2(V[2 * kk], V[2 * kk + 1]);
             }
           }
       }

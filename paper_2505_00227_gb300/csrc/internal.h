@@ -121,11 +121,12 @@ struct ChunkMap {
   const uint32_t* chunk_group;  // global chunk -> flat group index (l * ngroups + g)
   uint32_t total_chunks;
 };
-void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* chunk_hist,
-                        uint32_t* chunk_cost, cstream s);
-void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_hist,
-                   const uint32_t* chunk_cost, uint8_t* lens, uint64_t Ts, uint32_t cr_num,
-                   uint32_t cr_den, int force, cstream s);
+// group_hist (256 per group) and group_cost (per group) must start at zero
+void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* group_hist,
+                        unsigned long long* group_cost, uint32_t* chunk_cost, cstream s);
+void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* group_hist,
+                   const unsigned long long* group_cost, uint8_t* lens, uint64_t Ts,
+                   uint32_t cr_num, uint32_t cr_den, int force, cstream s);
 void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm, const uint8_t* lens,
                       uint32_t* chunk_words, cstream s);
 void launch_group_offsets(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_words,

@@ -60,7 +60,8 @@ __device__ __forceinline__ void load_chunk(const uint8_t* __restrict__ src, uint
 __global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__ planes,
                                                      const FieldMeta* __restrict__ meta,
                                                      const uint32_t* __restrict__ chunk_group,
-                                                     uint32_t* __restrict__ chunk_hist,
+                                                     uint32_t* __restrict__ group_hist,
+                                                     unsigned long long* __restrict__ group_cost,
                                                      uint32_t* __restrict__ chunk_cost) {
   __shared__ __align__(16) uint8_t buf[HP_CHUNK];
   __shared__ uint32_t hist[8][256];
@@ -83,10 +84,10 @@ __global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__
     }
   }
   __syncthreads();
-  {
+  {  // the group's histogram is the sum over its chunks (integer atomics: exact)
     uint32_t t = threadIdx.x, s = 0;
     for (int k = 0; k < 8; k++) s += hist[k][t];
-    chunk_hist[(size_t)c * 256 + t] = s;
+    if (s) atomicAdd(&group_hist[(size_t)r.gi * 256 + t], s);
   }
   for (int o = 16; o; o >>= 1) cost += __shfl_xor_sync(HP_FULL, cost, o);
   if ((threadIdx.x & 31) == 0) red[w] = cost;
@@ -95,14 +96,16 @@ __global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__
     uint32_t s = 0;
     for (int k = 0; k < 8; k++) s += red[k];
     chunk_cost[c] = s;
+    atomicAdd(&group_cost[r.gi], (unsigned long long)s);
   }
 }
 
-void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* chunk_hist,
-                        uint32_t* chunk_cost, cstream s) {
+void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* group_hist,
+                        unsigned long long* group_cost, uint32_t* chunk_cost, cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_chunk_stats<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, chunk_hist,
-                                                chunk_cost);
+  hp::note_launch(), k_chunk_stats<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group,
+                                                                   group_hist, group_cost,
+                                                                   chunk_cost);
 }
 
 // -------------------------------------------- Algorithm 2 decision per group
@@ -164,8 +167,8 @@ __device__ void huffman_lengths_block(const uint64_t* f_in, uint8_t* len_out, ui
   }
 }
 
-__global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t* __restrict__ chunk_hist,
-                                                const uint32_t* __restrict__ chunk_cost,
+__global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t* __restrict__ group_hist,
+                                                const unsigned long long* __restrict__ group_cost,
                                                 uint8_t* __restrict__ lens, uint64_t Ts,
                                                 uint32_t cr_num, uint32_t cr_den, int force) {
   __shared__ uint64_t hist[256], f[256], w[512];
@@ -177,13 +180,8 @@ __global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t*
   const int ng = meta->ngroups;
   GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
   const int t = threadIdx.x;
-  uint64_t h = 0;
-  for (uint32_t c = 0; c < gm->nchunks; c++) h += chunk_hist[(size_t)(gm->chunk0 + c) * 256 + t];
-  hist[t] = h;
-  uint64_t cost = 0;
-  for (uint32_t c = t; c < gm->nchunks; c += 256) cost += chunk_cost[gm->chunk0 + c];
-  cost = warp_sum_u64(cost);
-  if ((t & 31) == 0) red[t >> 5] = cost;
+  hist[t] = group_hist[(size_t)gi * 256 + t];
+  if (t == 0) red[0] = group_cost[gi];
   __syncthreads();
   huffman_lengths_block(hist, len, f, sorted, w, parent, depth, &flag);
   __syncthreads();
@@ -194,11 +192,8 @@ __global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t*
   lens[(size_t)gi * 256 + t] = len[t];
   __syncthreads();
   if (t == 0) {
-    uint64_t tb = 0, tc = 0;
-    for (int k = 0; k < 8; k++) {
-      tb += redb[k];
-      tc += red[k];
-    }
+    uint64_t tb = 0, tc = red[0];
+    for (int k = 0; k < 8; k++) tb += redb[k];
     const uint64_t S = gm->S;
     const uint32_t nc = gm->nchunks;
     uint64_t est_H = huff_header_bytes(nc) + (tb + 7) / 8 + 4ull * nc;
@@ -217,11 +212,11 @@ __global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t*
   }
 }
 
-void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_hist,
-                   const uint32_t* chunk_cost, uint8_t* lens, uint64_t Ts, uint32_t cr_num,
-                   uint32_t cr_den, int force, cstream s) {
-  hp::note_launch(), k_decide<<<ngroups_total, 256, 0, s>>>(meta, chunk_hist, chunk_cost, lens, Ts, cr_num, cr_den,
-                                         force);
+void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* group_hist,
+                   const unsigned long long* group_cost, uint8_t* lens, uint64_t Ts,
+                   uint32_t cr_num, uint32_t cr_den, int force, cstream s) {
+  hp::note_launch(), k_decide<<<ngroups_total, 256, 0, s>>>(meta, group_hist, group_cost, lens, Ts,
+                                                            cr_num, cr_den, force);
 }
 
 // --------------------------------------------------- canonical Huffman codes
@@ -753,6 +748,32 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
   }
 }
 
+// one (byte, LEB128(run-1)) record starting at s; returns its length in bytes,
+// 0 when it does not fit below pe or its run field is malformed
+__device__ __forceinline__ uint32_t rle_record(const uint8_t* __restrict__ pay, uint32_t s,
+                                               uint32_t pe, uint32_t& v, uint32_t& run) {
+  if (s + 1 >= pe) return 0;
+  v = pay[s];
+  uint32_t x = 0, q = s + 1;
+  int shift = 0;
+  while (true) {
+    if (q >= pe || shift > 28) return 0;
+    const uint32_t b = pay[q++];
+    x |= (b & 127u) << shift;
+    shift += 7;
+    if (!(b & 128u)) break;
+  }
+  run = x + 1;
+  return q - s;
+}
+
+// RLE decoding of one chunk by one warp.  The record stream is cut into 32
+// byte segments; every lane parses its segment speculatively from the three
+// possible record phases (our records are 2 or 3 bytes long), a pass over the
+// lanes picks each lane's true phase from where the previous lane's records
+// end, a prefix sum of the run lengths gives output offsets, and every lane
+// expands its own runs.  Reads stay inside the chunk's bytes; any inconsistency
+// marks the data corrupt.
 __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm, uint32_t cl,
                                  uint32_t len, uint8_t* __restrict__ dst, FieldMeta* meta) {
   const int lane = threadIdx.x & 31;
@@ -766,50 +787,99 @@ __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const Group
     return;
   }
   const uint32_t* offs = reinterpret_cast<const uint32_t*>(stored + 16);
-  uint64_t p = offs[cl], pe = offs[cl + 1];
-  if (p > pe || hdr + pe > gm->stored_len) {
+  const uint32_t p0 = offs[cl], p1 = offs[cl + 1];
+  if (p0 > p1 || hdr + p1 > gm->stored_len) {
     if (lane == 0) set_corrupt(meta);
     return;
   }
-  const uint8_t* pay = stored + hdr;
-  uint32_t out = 0;
-  int bad = 0;
-  while (true) {
-    uint32_t v = 0, run = 0;
-    int more = 0;
-    if (lane == 0) {
-      more = p < pe;
-      if (more) {
-        v = pay[p++];
-        uint32_t x = 0;
-        int shift = 0;
-        while (true) {
-          if (p >= pe || shift > 28) {
-            bad = 1;
+  const uint8_t* pay = stored + hdr + p0;
+  const uint32_t n = p1 - p0, seg = (n + 31) / 32;
+  const uint32_t a = min(lane * seg, n), a_next = min((lane + 1) * seg, n);
+  // speculative parses from phases 0, 1, 2
+  uint32_t endp[3], outp[3];
+  bool val[3];
+#pragma unroll
+  for (int ph = 0; ph < 3; ph++) {
+    uint32_t s = a + ph, out = 0;
+    bool good = true;
+    while (s < a_next) {
+      uint32_t v, run;
+      const uint32_t L = rle_record(pay, s, n, v, run);
+      if (!L) {
+        good = false;
+        break;
+      }
+      s += L;
+      out += run;
+    }
+    endp[ph] = s;
+    outp[ph] = out;
+    val[ph] = good;
+  }
+  // true starts, lane by lane
+  uint32_t t = 0, t_me = 0, nout = 0;
+  bool bad = false;
+  for (int i = 0; i < 32; i++) {
+    if (lane == i) {
+      t_me = t;
+      uint32_t e = t;
+      if (t >= a_next) {
+        nout = 0;  // a record from the previous segment covers this one
+      } else if (t - a < 3 && val[t - a]) {
+        nout = outp[t - a];
+        e = endp[t - a];
+      } else {  // not one of the three phases (or malformed): parse again from t
+        uint32_t s = t, out = 0;
+        while (s < a_next) {
+          uint32_t v, run;
+          const uint32_t L = rle_record(pay, s, n, v, run);
+          if (!L) {
+            bad = true;
             break;
           }
-          uint8_t byte = pay[p++];
-          x |= (uint32_t)(byte & 127u) << shift;
-          shift += 7;
-          if (!(byte & 128u)) break;
+          s += L;
+          out += run;
         }
-        run = x + 1;
-        if (!bad && run > len - out) bad = 1;
+        nout = out;
+        e = s;
       }
+      t = e;
     }
-    more = __shfl_sync(HP_FULL, more, 0);
-    bad = __shfl_sync(HP_FULL, bad, 0);
-    if (bad) {
-      if (lane == 0) set_corrupt(meta);
-      return;
-    }
-    if (!more) break;
-    v = __shfl_sync(HP_FULL, v, 0);
-    run = __shfl_sync(HP_FULL, run, 0);
-    for (uint32_t k = lane; k < run; k += 32) dst[out + k] = (uint8_t)v;
-    out += run;
+    t = __shfl_sync(HP_FULL, t, i);
   }
-  if (out != len && lane == 0) set_corrupt(meta);
+  uint32_t o = nout;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t v = __shfl_up_sync(HP_FULL, o, d);
+    if (lane >= d) o += v;
+  }
+  o -= nout;
+  uint32_t total = nout;
+#pragma unroll
+  for (int d = 16; d; d >>= 1) total += __shfl_xor_sync(HP_FULL, total, d);
+  bad = __any_sync(HP_FULL, bad) || total != len || t != n;
+  if (bad) {
+    if (lane == 0) set_corrupt(meta);
+    return;
+  }
+  // expand this lane's runs into dst[o ..)
+  uint32_t s = t_me, pos = o;
+  while (s < a_next) {
+    uint32_t v, run;
+    const uint32_t L = rle_record(pay, s, n, v, run);
+    s += L;
+    uint32_t r = run;
+    while (r && (pos & 3)) {
+      dst[pos++] = (uint8_t)v;
+      r--;
+    }
+    const uint32_t word = v * 0x01010101u;
+    for (; r >= 4; r -= 4, pos += 4) *reinterpret_cast<uint32_t*>(dst + pos) = word;
+    while (r) {
+      dst[pos++] = (uint8_t)v;
+      r--;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ slots, FieldMeta* meta,

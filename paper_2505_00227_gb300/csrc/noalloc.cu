@@ -13,7 +13,7 @@
 // Limits and rules:
 //   - groups of at most HP_NOALLOC_MAX_BYTES (16 MiB, 1024 coder chunks); larger
 //     groups are rejected with HPMDR_ERR_ARG;
-//   - the array (about 1.1 MB) is a file-scope __device__ variable: every GPU
+//   - the array (about 70 KB) is a file-scope __device__ variable: every GPU
 //     that loads this library holds it until the process exits;
 //   - the first call on each device looks up the array's device address with
 //     cudaGetSymbolAddress (with that device current); make that first call
@@ -38,8 +38,9 @@ using namespace hp;
 struct NoAllocScratch {
   FieldMeta meta;
   uint32_t chunk_group[HP_NOALLOC_MAX_CHUNKS];
-  uint32_t hist[HP_NOALLOC_MAX_CHUNKS * 256];
-  uint32_t cost[HP_NOALLOC_MAX_CHUNKS];
+  uint32_t hist[256];               // the group's byte histogram
+  unsigned long long cost;           // the group's exact RLE size
+  uint32_t chunk_cost[HP_NOALLOC_MAX_CHUNKS];
   uint32_t words[HP_NOALLOC_MAX_CHUNKS];
   uint32_t off[HP_NOALLOC_MAX_CHUNKS];
   uint8_t lens[256];
@@ -66,8 +67,9 @@ static hpmdr_status noalloc_scratch(NoAllocScratch** out) {
 }
 
 // The shared array keeps the previous call's contents: reset the one-group
-// metadata and the chunk map before the coder kernels run.  (Histograms, run
-// costs, word counts and offsets are fully written before they are read.)
+// metadata, the chunk map and the atomically accumulated histogram and RLE size
+// before the coder kernels run.  (Per-chunk run costs, word counts and offsets
+// are fully written before they are read.)
 __global__ void k_noalloc_init(NoAllocScratch* sc, uint64_t S, uint64_t cap, uint32_t nchunks) {
   FieldMeta& m = sc->meta;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -87,6 +89,10 @@ __global__ void k_noalloc_init(NoAllocScratch* sc, uint64_t S, uint64_t cap, uin
   }
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x)
     sc->chunk_group[c] = 0;
+  if (blockIdx.x == 0) {  // accumulated by atomics: must start at zero
+    sc->hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) sc->cost = 0;
+  }
 }
 
 extern "C" hpmdr_status hpmdr_encode_group_noalloc(const uint8_t* G, uint64_t S, int force,
@@ -107,10 +113,10 @@ extern "C" hpmdr_status hpmdr_encode_group_noalloc(const uint8_t* G, uint64_t S,
   hp::note_launch(), k_noalloc_init<<<1, 256, 0, s>>>(sc, S, cap, nc);
   ChunkMap cm{sc->chunk_group, nc};
   FieldMeta* m = &sc->meta;
-  launch_chunk_stats(G, m, cm, sc->hist, sc->cost, s);
-  launch_decide(m, 1, sc->hist, sc->cost, sc->lens, Ts, cr_num, cr_den, force, s);
+  launch_chunk_stats(G, m, cm, sc->hist, &sc->cost, sc->chunk_cost, s);
+  launch_decide(m, 1, sc->hist, &sc->cost, sc->lens, Ts, cr_num, cr_den, force, s);
   launch_huff_bits(G, m, cm, sc->lens, sc->words, s);
-  launch_group_offsets(m, 1, sc->words, sc->cost, sc->off, s);
+  launch_group_offsets(m, 1, sc->words, sc->chunk_cost, sc->off, s);
   launch_huff_encode(G, m, cm, sc->lens, sc->off, out, s);
   launch_rle_encode(G, m, cm, sc->off, out, s);
   launch_headers(m, 1, sc->lens, sc->off, out, s);

@@ -458,12 +458,14 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
   void* d_field = nullptr;
   const int ngt = H->nlev * H->ngroups;
   uint32_t *d_hist = nullptr, *d_cost = nullptr, *d_words = nullptr, *d_out = nullptr;
+  unsigned long long* d_gcost = nullptr;
   uint8_t* d_lens = nullptr;
   size_t i_hbits = SIZE_MAX, i_henc = SIZE_MAX, i_renc = SIZE_MAX;
   hpmdr_status st = HPMDR_OK;
   auto cleanup = [&]() {
     H->A.release(d_field, s);
     H->A.release(d_hist, s);
+    H->A.release(d_gcost, s);
     H->A.release(d_cost, s);
     H->A.release(d_words, s);
     H->A.release(d_out, s);
@@ -486,7 +488,13 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
     if ((st = H->A.alloc((void**)&H->d_slots, H->slot_bytes, s))) break;
     if ((st = H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s))) break;
     if ((st = H->A.alloc((void**)&H->d_chunk_group, 4ull * tc, s))) break;
-    if ((st = H->A.alloc((void**)&d_hist, 1024ull * tc, s))) break;
+    if ((st = H->A.alloc((void**)&d_hist, 1024ull * ngt, s))) break;
+    if ((st = H->A.alloc((void**)&d_gcost, 8ull * ngt, s))) break;
+    if (cudaMemsetAsync(d_hist, 0, 1024ull * ngt, s) != cudaSuccess ||
+        cudaMemsetAsync(d_gcost, 0, 8ull * ngt, s) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
     if ((st = H->A.alloc((void**)&d_cost, 4ull * tc, s))) break;
     if ((st = H->A.alloc((void**)&d_words, 4ull * tc, s))) break;
     if ((st = H->A.alloc((void**)&d_out, 4ull * tc, s))) break;
@@ -505,7 +513,7 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
     }
     ChunkMap cm{H->d_chunk_group, H->total_chunks};
     Profiler* P = ctx->P();
-    const double fb = (double)H->N * esz, pb = (double)H->plane_bytes, cb = 1028.0 * tc;
+    const double fb = (double)H->N * esz, pb = (double)H->plane_bytes, cb = 4.0 * tc + 1032.0 * ngt;
     { ProfScope p(P, ST_STATS, fb, s); launch_stats(f, H->N, dtype, H->d_meta, s); }
     { ProfScope p(P, ST_FINALIZE, 0, s); launch_stats_finalize(H->d_meta, s); }
     // algorithmic bytes: the field once (split over the level kernels by node
@@ -539,9 +547,9 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
                     H->d_meta, (uint32_t*)H->d_planes, s);
     }
     { ProfScope p(P, ST_CHUNK_STATS, pb + cb, s);
-      launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_cost, s); }
+      launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_gcost, d_cost, s); }
     { ProfScope p(P, ST_DECIDE, cb, s);
-      launch_decide(H->d_meta, ngt, d_hist, d_cost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, -1,
+      launch_decide(H->d_meta, ngt, d_hist, d_gcost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, -1,
                     s); }
     { ProfScope p(P, ST_HUFF_BITS, 0, s); i_hbits = p.i;
       launch_huff_bits(H->d_planes, H->d_meta, cm, d_lens, d_words, s); }
@@ -1215,13 +1223,20 @@ extern "C" hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uin
   uint8_t *d_G = nullptr, *d_lens = nullptr;
   uint32_t *d_cg = nullptr, *d_hist = nullptr, *d_cost = nullptr, *d_words = nullptr,
            *d_off = nullptr;
+  unsigned long long* d_gcost = nullptr;
   hpmdr_status st = HPMDR_OK;
   do {
     if ((st = ctx->A.alloc((void**)&d_meta, sizeof(FieldMeta), s))) break;
     if ((st = ctx->A.alloc((void**)&d_G, round16(S), s))) break;
     if ((st = ctx->A.alloc((void**)&d_lens, 256, s))) break;
     if ((st = ctx->A.alloc((void**)&d_cg, 4ull * nc, s))) break;
-    if ((st = ctx->A.alloc((void**)&d_hist, 1024ull * nc, s))) break;
+    if ((st = ctx->A.alloc((void**)&d_hist, 1024ull, s))) break;
+    if ((st = ctx->A.alloc((void**)&d_gcost, 8ull, s))) break;
+    if (cudaMemsetAsync(d_hist, 0, 1024ull, s) != cudaSuccess ||
+        cudaMemsetAsync(d_gcost, 0, 8ull, s) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
     if ((st = ctx->A.alloc((void**)&d_cost, 4ull * nc, s))) break;
     if ((st = ctx->A.alloc((void**)&d_words, 4ull * nc, s))) break;
     if ((st = ctx->A.alloc((void**)&d_off, 4ull * nc, s))) break;
@@ -1233,8 +1248,8 @@ extern "C" hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uin
       break;
     }
     ChunkMap cm{d_cg, nc};
-    launch_chunk_stats(d_G, d_meta, cm, d_hist, d_cost, s);
-    launch_decide(d_meta, 1, d_hist, d_cost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, force, s);
+    launch_chunk_stats(d_G, d_meta, cm, d_hist, d_gcost, d_cost, s);
+    launch_decide(d_meta, 1, d_hist, d_gcost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, force, s);
     launch_huff_bits(d_G, d_meta, cm, d_lens, d_words, s);
     launch_group_offsets(d_meta, 1, d_words, d_cost, d_off, s);
     launch_huff_encode(d_G, d_meta, cm, d_lens, d_off, out, s);
@@ -1267,6 +1282,7 @@ extern "C" hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uin
   ctx->A.release(d_lens, s);
   ctx->A.release(d_cg, s);
   ctx->A.release(d_hist, s);
+  ctx->A.release(d_gcost, s);
   ctx->A.release(d_cost, s);
   ctx->A.release(d_words, s);
   ctx->A.release(d_off, s);

@@ -38,16 +38,21 @@ __device__ u128 level_delta(const FieldMeta* m, int l, int k) {
   return p2(bl - k + m->B);
 }
 
-__device__ u128 estimate(const FieldMeta* m, const int* g) {
-  u128 E = 0;
-  bool any = false;
-  for (int l = 0; l < m->nlev; l++) {
-    u128 d = level_delta(m, l, 4 * g[l]);
-    any |= d != 0;
-    E = sat_add(E, d);
-  }
+// 2^(bl_a-k_a) * bytes_b > 2^(bl_b-k_b) * bytes_a, ties to the smaller level
+__device__ bool better(const FieldMeta* m, const int* g, int a, int b) {
+  const int sa = m->bl[a] - 4 * g[a], sb = m->bl[b] - 4 * g[b];
+  const u128 ba = m->grp[a][g[a]].stored_len, bb = m->grp[b][g[b]].stored_len;
+  const int lo = sa < sb ? sa : sb;
+  const u128 left = bb << (sa - lo), right = ba << (sb - lo);
+  if (left != right) return left > right;
+  return a < b;
+}
+
+// E from the sum of the per-level truncation errors (same terms as estimate())
+__device__ u128 finish_estimate(const FieldMeta* m, u128 sum_delta) {
+  u128 E = sum_delta;
   const u128 U = p2(m->B + 3);
-  if (any) E = sat_add(E, (u128)m->nlev * U);
+  if (sum_delta) E = sat_add(E, (u128)m->nlev * U);
   if (!m->input_exact) E = sat_add(E, U);
   if (E == 0) return 0;
   u128 eps;
@@ -61,46 +66,55 @@ __device__ u128 estimate(const FieldMeta* m, const int* g) {
   return sat_add(E, eps);
 }
 
-// 2^(bl_a-k_a) * bytes_b > 2^(bl_b-k_b) * bytes_a, ties to the smaller level
-__device__ bool better(const FieldMeta* m, const int* g, int a, int b) {
-  const int sa = m->bl[a] - 4 * g[a], sb = m->bl[b] - 4 * g[b];
-  const u128 ba = m->grp[a][g[a]].stored_len, bb = m->grp[b][g[b]].stored_len;
-  const int lo = sa < sb ? sa : sb;
-  const u128 left = bb << (sa - lo), right = ba << (sb - lo);
-  if (left != right) return left > right;
-  return a < b;
-}
-
+// One warp: lane l evaluates levels l and l + 32; the best level of each step
+// is a warp-wide reduction with the greedy comparison.  The estimate after
+// each step is updated from the chosen level's change only.
 __global__ void k_sequence(FieldMeta* m) {
+  __shared__ int g[64];
+  const int lane = threadIdx.x;
   if (m->status) return;
-  int g[HP_MAX_LEVELS];
-  for (int l = 0; l < m->nlev; l++) {
+  const int nlev = m->nlev;
+  for (int l = lane; l < 64; l += 32) {
     g[l] = 0;
-    m->exact[l] = m->lowbits[l] == 0 ? 1 : 0;
+    if (l < nlev) m->exact[l] = m->lowbits[l] == 0 ? 1 : 0;
+  }
+  __syncwarp();
+  u128 sum = 0;
+  if (lane == 0) {
+    for (int l = 0; l < nlev; l++) sum += level_delta(m, l, 0);
+    const u128 E = finish_estimate(m, sum);
+    m->E_hi[0] = (uint64_t)(E >> 64);
+    m->E_lo[0] = (uint64_t)E;
   }
   int n = 0;
-  u128 E = estimate(m, g);
-  m->E_hi[0] = (uint64_t)(E >> 64);
-  m->E_lo[0] = (uint64_t)E;
   while (n < HP_SEQ_MAX) {
     int best = -1;
-    for (int l = 0; l < m->nlev; l++) {
-      if (g[l] >= m->ngroups) continue;
-      if (level_delta(m, l, 4 * g[l]) == 0) continue;
+    for (int l = lane; l < nlev; l += 32) {
+      if (g[l] >= m->ngroups || level_delta(m, l, 4 * g[l]) == 0) continue;
       if (best < 0 || better(m, g, l, best)) best = l;
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const int other = __shfl_xor_sync(HP_FULL, best, o);
+      if (other >= 0 && (best < 0 || better(m, g, other, best))) best = other;
+    }
     if (best < 0) break;
-    m->seq[n] = (uint8_t)best;
-    g[best]++;
+    if (lane == 0) {
+      sum -= level_delta(m, best, 4 * g[best]);
+      g[best]++;
+      sum += level_delta(m, best, 4 * g[best]);
+      m->seq[n] = (uint8_t)best;
+      const u128 E = finish_estimate(m, sum);
+      m->E_hi[n + 1] = (uint64_t)(E >> 64);
+      m->E_lo[n + 1] = (uint64_t)E;
+    }
     n++;
-    E = estimate(m, g);
-    m->E_hi[n] = (uint64_t)(E >> 64);
-    m->E_lo[n] = (uint64_t)E;
+    __syncwarp();
   }
-  m->seq_len = n;
+  if (lane == 0) m->seq_len = n;
 }
 
-void launch_sequence(FieldMeta* meta, cstream s) { hp::note_launch(), k_sequence<<<1, 1, 0, s>>>(meta); }
+void launch_sequence(FieldMeta* meta, cstream s) { hp::note_launch(), k_sequence<<<1, 32, 0, s>>>(meta); }
 
 // floor(tau * 2^(51+B-E_f)) from the IEEE fields of tau, saturating at 2^127
 __device__ u128 tau_units(double tau, int E_f, int B) {
@@ -130,14 +144,17 @@ __global__ void k_select(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* 
   if (m->status) return;
   const double tau_abs = tau_is_abs ? tau : __dmul_rn(tau, m->range);
   const u128 T = tau_units(tau_abs, m->E_f, m->B);
-  int c = 0;
+  // the estimates never increase along the sequence: binary search for the
+  // shortest prefix whose estimate meets the bound
   const int n = m->seq_len;
-  while (c <= n) {
-    u128 E = ((u128)m->E_hi[c] << 64) | m->E_lo[c];
-    if (E <= T) break;
-    c++;
+  int lo = 0, hi = n + 1;  // answer in [lo, hi]; hi = n + 1 means none
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    const u128 E = ((u128)m->E_hi[mid] << 64) | m->E_lo[mid];
+    if (E <= T) hi = mid;
+    else lo = mid + 1;
   }
-  int status = 0;
+  int c = lo, status = 0;
   if (c > n) {
     c = n;
     status = -5;  // HPMDR_ERR_UNATTAINABLE: best reconstruction, estimate reported
