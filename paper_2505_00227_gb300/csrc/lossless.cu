@@ -506,21 +506,27 @@ void launch_headers(FieldMeta* meta, int ngroups_total, const uint8_t* lens,
 __device__ __forceinline__ void set_corrupt(FieldMeta* meta) { atomicExch(&meta->status, -4); }
 
 // Huffman decoding of one chunk by one warp, self-synchronizing:
-//  1. tables: canonical first code / count / sorted symbols per length and a
-//     10-bit lookup table for the short codes (built from the stored lengths);
+//  1. tables: canonical first code / count / sorted symbols per length (a
+//     counting sort by warp ballots) and a 10-bit lookup table for short codes;
 //  2. the chunk's bits are cut into 32 equal segments; lane i decodes from the
-//     start of segment i (maybe mid-codeword) to the first codeword start at or
-//     beyond segment i+1, recording its first 16 codeword starts;
-//  3. a pass over the lanes in order fixes each lane's true start (the end of
-//     the previous lane's true decoding): if that position is among the lane's
-//     recorded starts, its decoding from there is the true one (Huffman codes
-//     resynchronize after a few codewords); otherwise the lane decodes again;
-//  4. a prefix sum of the true counts gives each lane its output offset, and
+//     start of its segment (maybe mid-codeword) up to the first codeword start
+//     at or beyond the next segment, marking every codeword start it visits in
+//     a bitmap of the chunk's bits (segments do not overlap, so each lane owns
+//     the marks of its segment);
+//  3. lane by lane, the true path enters segment i at t (the end of lane i-1's
+//     true decoding); lane i follows it until it lands on a marked bit, from
+//     where its speculative decoding is the true one (Huffman codes
+//     resynchronize), so its count is the codewords walked plus the marks from
+//     there on; if the walk leaves the segment first, the walk itself is the
+//     lane's true decoding;
+//  4. a prefix sum of the true counts gives each lane its output offset and
 //     every lane decodes its own span again, writing the bytes.
-// All reads are limited to the chunk's words; an invalid code or a wrong
-// symbol count marks the data corrupt.
+// Chunks longer than the bitmap (more than 16 bits per symbol on average are
+// impossible, but a forced Huffman group of incompressible bytes can exceed
+// it) are decoded by one lane.  All reads stay inside the chunk's words; an
+// invalid code or a wrong symbol count marks the data corrupt.
 #define HP_LUT_BITS 10
-#define HP_NSTART 17
+#define HP_MAP_WORDS 2048  // bitmap of 65536 bit positions per warp
 
 struct HuffTables {
   uint16_t lut[1 << HP_LUT_BITS];  // (len << 8) | symbol for codes of <= 10 bits, 0 otherwise
@@ -529,7 +535,7 @@ struct HuffTables {
   uint32_t index[17];
   uint32_t fill[17];
   uint8_t sorted[256];
-  uint32_t starts[32][HP_NSTART];
+  uint32_t map[HP_MAP_WORDS];      // codeword starts of the speculative decodings
 };
 
 struct BitReader {
@@ -578,27 +584,39 @@ __device__ __forceinline__ int huff_sym(const HuffTables& T, const BitReader& r,
   return 0;
 }
 
-// decode codewords starting in [pos, stop); returns the count, sets end / fail
-__device__ uint32_t huff_scan(const HuffTables& T, BitReader& r, uint32_t pos, uint32_t stop,
-                              uint32_t* starts, uint32_t& end, bool& fail) {
-  uint32_t c = 0;
-  fail = false;
-  r.init(pos);
-  if (starts) starts[0] = pos;
-  while (pos < stop) {
-    uint32_t sym;
-    const int L = huff_sym(T, r, sym);
-    if (!L) {
-      fail = true;
-      break;
-    }
-    r.consume(L);
-    pos += L;
-    c++;
-    if (starts && c < HP_NSTART) starts[c] = pos;
+// number of marked bits in [a, b)
+__device__ __forceinline__ uint32_t map_count(const uint32_t* map, uint32_t a, uint32_t b) {
+  uint32_t n = 0;
+  while (a < b) {
+    const uint32_t w = a >> 5, o = a & 31, k = min(32u - o, b - a);
+    const uint32_t m = (k == 32 ? 0xffffffffu : ((1u << k) - 1u)) << o;
+    n += __popc(map[w] & m);
+    a += k;
   }
-  end = pos;
-  return c;
+  return n;
+}
+
+// write the n symbols decoded from bit `pos` to dst[o ..)
+__device__ __forceinline__ bool huff_emit(const HuffTables& T, BitReader& rd, uint32_t pos,
+                                          uint32_t n, uint8_t* __restrict__ dst, uint32_t o) {
+  rd.init(pos);
+  uint32_t acc = 0, p = o;
+  for (uint32_t k = 0; k < n; k++, p++) {
+    uint32_t sym;
+    const int L = huff_sym(T, rd, sym);
+    if (!L) return false;
+    rd.consume(L);
+    acc |= sym << (8 * (p & 3));
+    if ((p & 3) == 3) {
+      if (p - 3 >= o) reinterpret_cast<uint32_t*>(dst)[p >> 2] = acc;
+      else
+        for (uint32_t q = o; q <= p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
+      acc = 0;
+    }
+  }
+  if (p & 3)
+    for (uint32_t q = max(o, p & ~3u); q < p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
+  return true;
 }
 
 __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm,
@@ -620,19 +638,26 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
   const uint64_t words = (gm->stored_len - hdr) / 4;
   bool bad = w0 > w1 || w1 > words;
   // ---- 1. decoding tables
-  if (lane < 17) T.count[lane] = 0;
-  for (int i = lane; i < (1 << HP_LUT_BITS); i += 32) T.lut[i] = 0;
-  __syncwarp();
-  for (int s = lane; s < 256; s += 32) {
-    const uint32_t L = lens[s];
-    if (L > 16) bad = true;
-    else if (L) atomicAdd(&T.count[L], 1u);
+  uint32_t myL[8];
+#pragma unroll
+  for (int r = 0; r < 8; r++) {
+    myL[r] = lens[32 * r + lane];
+    bad |= myL[r] > 16;
   }
-  __syncwarp();
   if (__any_sync(HP_FULL, bad)) {
     if (lane == 0) set_corrupt(meta);
     return;
   }
+  uint32_t cnt = 0;  // lane L (1..16) counts the symbols of length L
+#pragma unroll
+  for (int r = 0; r < 8; r++)
+    for (int L = 1; L <= 16; L++) {
+      const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
+      if (lane == L) cnt += __popc(m);
+    }
+  if (lane <= 16) T.count[lane] = lane ? cnt : 0;
+  for (int i = lane; i < (1 << HP_LUT_BITS); i += 32) T.lut[i] = 0;
+  __syncwarp();
   if (lane == 0) {
     uint32_t c = 0, idx = 0;
     for (int L = 1; L <= 16; L++) {
@@ -642,10 +667,19 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
       idx += T.count[L];
       c = (c + T.count[L]) << 1;
     }
-    for (int s = 0; s < 256; s++)  // counting sort into (length, symbol) order
-      if (lens[s]) T.sorted[T.fill[lens[s]]++] = (uint8_t)s;
   }
   __syncwarp();
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < 8; r++) {  // counting sort into (length, symbol) order
+    for (int L = 1; L <= 16; L++) {
+      const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
+      if (myL[r] == (uint32_t)L) T.sorted[T.fill[L] + __popc(m & lt)] = (uint8_t)(32 * r + lane);
+      __syncwarp();
+      if (lane == 0) T.fill[L] += __popc(m);
+      __syncwarp();
+    }
+  }
   for (int L = 1; L <= HP_LUT_BITS; L++) {
     const uint32_t n = T.count[L];
     for (uint32_t k = lane; k < n; k += 32) {
@@ -656,93 +690,86 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     }
   }
   __syncwarp();
-  // ---- 2. speculative decoding of 32 equal bit segments
-  const uint32_t nbits = (w1 - w0) * 32;
-  const uint32_t seg = (nbits + 31) / 32;
   BitReader rd;
   rd.w = reinterpret_cast<const uint32_t*>(stored + hdr) + w0;
   rd.nwords = w1 - w0;
-  const uint32_t s_me = min(lane * seg, nbits), s_next = min((lane + 1) * seg, nbits);
-  uint32_t e_me = s_me;
-  bool f_me = false;
-  uint32_t c_me = huff_scan(T, rd, s_me, s_next, T.starts[lane], e_me, f_me);
-  __syncwarp();
-  // ---- 3. true starts, lane by lane: follow the true path from t until it
-  // meets one of the lane's recorded codeword starts (Huffman codes
-  // resynchronize), else decode the lane's segment again from t
-  uint32_t t_me = 0, tc_me = 0, t = 0;
-  for (int i = 0; i < 32; i++) {
-    if (lane == i) {
-      t_me = t;
-      const uint32_t nrec = c_me < HP_NSTART - 1 ? c_me : HP_NSTART - 1;  // starts[0..nrec]
-      const uint32_t last = T.starts[i][nrec];
-      bool found = false;
-      uint32_t e = e_me;
-      if (t < s_next) {
-        uint32_t p = t, d = 0, m = 0;
-        BitReader tr = rd;
-        tr.init(p);
-        while (p <= last && p < s_next) {
-          while (m < nrec && T.starts[i][m] < p) m++;
-          if (T.starts[i][m] == p) {
-            tc_me = d + (c_me - m);
-            found = true;
-            break;
-          }
-          uint32_t sym;
-          const int L = huff_sym(T, tr, sym);
-          if (!L) break;
-          tr.consume(L);
-          p += L;
-          d++;
-        }
-        if (!found) {
-          bool f;
-          tc_me = huff_scan(T, rd, t, s_next, nullptr, e, f);
-        }
-      } else {
-        tc_me = 0;
-        e = t;
-      }
-      t = e;
-    }
-    t = __shfl_sync(HP_FULL, t, i);
-  }
-  // ---- 4. output offsets and the final decoding
-  uint32_t o = tc_me;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t v = __shfl_up_sync(HP_FULL, o, d);
-    if (lane >= d) o += v;
-  }
-  o -= tc_me;  // exclusive
-  const uint32_t n_me = o < len ? min(tc_me, len - o) : 0u;
+  const uint32_t nbits = (w1 - w0) * 32;
   bool fail = false;
-  if (n_me) {
-    rd.init(t_me);
-    uint32_t acc = 0, p = o;
-    for (uint32_t k = 0; k < n_me; k++, p++) {
-      uint32_t sym;
-      const int L = huff_sym(T, rd, sym);
-      if (!L) {
-        fail = true;
-        break;
+  uint32_t total = 0;
+  if (nbits > HP_MAP_WORDS * 32) {  // too long for the bitmap: one lane decodes
+    if (lane == 0) fail = !huff_emit(T, rd, 0, len, dst, 0);
+    total = len;
+  } else {
+    // ---- 2. speculative decoding of 32 equal segments, marking codeword starts
+    const uint32_t mw = (nbits + 31) / 32;
+    for (uint32_t i = lane; i < mw; i += 32) T.map[i] = 0;
+    __syncwarp();
+    const uint32_t seg = (nbits + 31) / 32;
+    const uint32_t s_me = min(lane * seg, nbits), s_next = min((lane + 1) * seg, nbits);
+    uint32_t c_me = 0, e_me = s_me;
+    {
+      uint32_t pos = s_me;
+      rd.init(pos);
+      while (pos < s_next) {
+        uint32_t sym;
+        const int L = huff_sym(T, rd, sym);
+        if (!L) break;
+        atomicOr(&T.map[pos >> 5], 1u << (pos & 31));
+        rd.consume(L);
+        pos += L;
+        c_me++;
       }
-      rd.consume(L);
-      acc |= sym << (8 * (p & 3));
-      if ((p & 3) == 3) {
-        if (p - 3 >= o) reinterpret_cast<uint32_t*>(dst)[p >> 2] = acc;
-        else
-          for (uint32_t q = o; q <= p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
-        acc = 0;
-      }
+      e_me = pos;
     }
-    if (!fail && (p & 3))
-      for (uint32_t q = max(o, p & ~3u); q < p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
-  }
-  uint32_t total = n_me;
+    __syncwarp();
+    // ---- 3. true entry point and count of every lane
+    uint32_t t_me = 0, tc_me = 0, t = 0;
+    for (int i = 0; i < 32; i++) {
+      if (lane == i) {
+        t_me = t;
+        uint32_t e = t, d = 0, p = t;
+        bool joined = false;
+        if (t < s_next) {
+          BitReader tr = rd;
+          tr.init(p);
+          while (p < s_next) {
+            if ((T.map[p >> 5] >> (p & 31)) & 1u) {
+              joined = true;
+              break;
+            }
+            uint32_t sym;
+            const int L = huff_sym(T, tr, sym);
+            if (!L) break;  // invalid: counts stop here (checked in step 4)
+            tr.consume(L);
+            p += L;
+            d++;
+          }
+        }
+        if (joined) {
+          tc_me = d + map_count(T.map, p, s_next);
+          e = e_me;
+        } else {
+          tc_me = d;
+          e = p;
+        }
+        t = e;
+      }
+      t = __shfl_sync(HP_FULL, t, i);
+    }
+    // ---- 4. output offsets and the final decoding
+    uint32_t o = tc_me;
 #pragma unroll
-  for (int d = 16; d; d >>= 1) total += __shfl_xor_sync(HP_FULL, total, d);
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint32_t v = __shfl_up_sync(HP_FULL, o, dd);
+      if (lane >= dd) o += v;
+    }
+    o -= tc_me;
+    const uint32_t n_me = o < len ? min(tc_me, len - o) : 0u;
+    if (n_me) fail = !huff_emit(T, rd, t_me, n_me, dst, o);
+    total = n_me;
+#pragma unroll
+    for (int dd = 16; dd; dd >>= 1) total += __shfl_xor_sync(HP_FULL, total, dd);
+  }
   if (__any_sync(HP_FULL, fail) || total != len) {
     if (lane == 0) set_corrupt(meta);
   }
@@ -882,14 +909,14 @@ __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const Group
   }
 }
 
-__global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ slots, FieldMeta* meta,
+__global__ void __launch_bounds__(128) k_decode(const uint8_t* __restrict__ slots, FieldMeta* meta,
                                                 const RetrieveDev* __restrict__ rd,
                                                 uint8_t* __restrict__ planes) {
-  __shared__ HuffTables tabs[8];
+  __shared__ HuffTables tabs[4];
   const int w = threadIdx.x >> 5;
   const uint32_t total = rd->items, ngr = rd->n_new;
   const int ng = meta->ngroups;
-  for (uint32_t item = blockIdx.x * 8 + w; item < total; item += gridDim.x * 8) {
+  for (uint32_t item = blockIdx.x * 4 + w; item < total; item += gridDim.x * 4) {
     // newly fetched group holding this item: last k with new_pref[k] <= item
     uint32_t lo = 0, hi = ngr;
     while (hi - lo > 1) {
@@ -916,10 +943,10 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t blocks = (max_items + 7) / 8;
-  uint32_t cap = (uint32_t)sms * 8;
+  uint32_t blocks = (max_items + 3) / 4;
+  uint32_t cap = (uint32_t)sms * 16;
   if (blocks > cap) blocks = cap;
-  hp::note_launch(), k_decode<<<blocks, 256, 0, s>>>(slots, meta, rd, planes);
+  hp::note_launch(), k_decode<<<blocks, 128, 0, s>>>(slots, meta, rd, planes);
 }
 
 }  // namespace hp

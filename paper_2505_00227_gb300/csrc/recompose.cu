@@ -85,7 +85,77 @@ __global__ void __launch_bounds__(256) k_recompose_copy(const LevelDesc* __restr
   }
 }
 
-// detail nodes of one level: warp tile of 1024 level-linear nodes
+// detail nodes of one level, one warp tile of 1024 level-linear nodes starting
+// at node `base`: lane = word for the inverse transpose, then lane = node
+template <typename T, int B, bool FINAL>
+__device__ __forceinline__ void recompose_tile(const uint32_t* __restrict__ P, const LevelDesc& L,
+                                               uint32_t base, int k, int bl, int E_f,
+                                               const int64_t* __restrict__ coarse,
+                                               void* __restrict__ dst, uint32_t* hi, uint32_t* lo,
+                                               uint32_t* sgn) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t W = L.W;
+  const uint32_t wi = base / 32 + lane;
+  if (wi < W) {
+    uint32_t a[32];
+#pragma unroll
+    for (int p = 0; p < 32; p++) a[31 - p] = (p < k) ? P[(size_t)(1 + p) * W + wi] : 0u;
+    if (k) transpose32(a);
+#pragma unroll
+    for (int b = 0; b < 32; b++) hi[lane * 33 + b] = a[b];
+    if (B == 64) {
+#pragma unroll
+      for (int p = 0; p < 32; p++) a[31 - p] = (32 + p < k) ? P[(size_t)(33 + p) * W + wi] : 0u;
+      if (k > 32) transpose32(a);
+#pragma unroll
+      for (int b = 0; b < 32; b++) lo[lane * 33 + b] = a[b];
+    }
+    sgn[lane] = k > 0 ? P[wi] : 0u;
+  }
+  __syncwarp();
+  for (int r = 0; r < 32; r++) {
+    const uint32_t j = base + r * 32 + lane;
+    if (j < L.n) {
+      const uint64_t qh = B == 64 ? (((uint64_t)hi[r * 33 + lane] << 32) | lo[r * 33 + lane])
+                                  : (uint64_t)hi[r * 33 + lane];
+      const bool neg = (sgn[r] >> lane) & 1u;
+      const int64_t c8 = dequant(qh, neg, B, bl);
+      const NodePos p = node_pos(L, j);
+      uint32_t zs[2], ys[2], xs[2];
+      int nz = 1, ny = 1, nx = 1;
+      zs[0] = zs[1] = p.gz >> 1;
+      ys[0] = ys[1] = p.gy >> 1;
+      xs[0] = xs[1] = p.gx >> 1;
+      if (p.t & 4) {
+        uint32_t a, b;
+        axis_nb(p.gz, L.g[0], a, b);
+        zs[0] = a >> 1; zs[1] = b >> 1; nz = 2;
+      }
+      if (p.t & 2) {
+        uint32_t a, b;
+        axis_nb(p.gy, L.g[1], a, b);
+        ys[0] = a >> 1; ys[1] = b >> 1; ny = 2;
+      }
+      if (p.t & 1) {
+        uint32_t a, b;
+        axis_nb(p.gx, L.g[2], a, b);
+        xs[0] = a >> 1; xs[1] = b >> 1; nx = 2;
+      }
+      int64_t sum = 0;
+      for (int a = 0; a < nz; a++)
+        for (int b = 0; b < ny; b++)
+          for (int c = 0; c < nx; c++)
+            sum += coarse[((size_t)zs[a] * L.gc[1] + ys[b]) * L.gc[2] + xs[c]];
+      const int nodd = __popc(p.t);
+      const int64_t X = floor_shift(c8 * ((int64_t)1 << nodd) + 8 * sum, 3 + nodd);
+      const size_t d = ((size_t)p.gz * L.g[1] + p.gy) * L.g[2] + p.gx;
+      if (FINAL) reinterpret_cast<T*>(dst)[d] = convert_out<T>(X, E_f);
+      else reinterpret_cast<int64_t*>(dst)[d] = X;
+    }
+  }
+  __syncwarp();
+}
+
 template <typename T, int B, bool FINAL>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_recompose_level(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
@@ -97,73 +167,70 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
   __shared__ uint32_t s_sign[WPB][32];
   if (m->status) return;
   const LevelDesc& L = *Lp;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t* hi = s_hi[w];
-  uint32_t* lo = s_lo[B == 64 ? w : 0];
+  const int w = threadIdx.x >> 5;
   const int k = 4 * m->cur[L.level], bl = m->bl[L.level], E_f = m->E_f;
   const uint32_t* P = planes + L.plane_off / 4;
-  const uint32_t W = L.W;
-  for (uint32_t slot = blockIdx.x * WPB + w; slot < L.ntiles; slot += gridDim.x * WPB) {
-    const uint32_t base = perm[L.tile0 + slot] * HP_TILE;
-    const uint32_t wi = base / 32 + lane;
-    if (wi < W) {
-      uint32_t a[32];
-#pragma unroll
-      for (int p = 0; p < 32; p++) a[31 - p] = (p < k) ? P[(size_t)(1 + p) * W + wi] : 0u;
-      transpose32(a);
-#pragma unroll
-      for (int b = 0; b < 32; b++) hi[lane * 33 + b] = a[b];
-      if (B == 64) {
-#pragma unroll
-        for (int p = 0; p < 32; p++) a[31 - p] = (32 + p < k) ? P[(size_t)(33 + p) * W + wi] : 0u;
-        transpose32(a);
-#pragma unroll
-        for (int b = 0; b < 32; b++) lo[lane * 33 + b] = a[b];
-      }
-      s_sign[w][lane] = k > 0 ? P[wi] : 0u;
+  for (uint32_t slot = blockIdx.x * WPB + w; slot < L.ntiles; slot += gridDim.x * WPB)
+    recompose_tile<T, B, FINAL>(P, L, perm[L.tile0 + slot] * HP_TILE, k, bl, E_f, coarse, dst,
+                                s_hi[w], s_lo[B == 64 ? w : 0], s_sign[w]);
+}
+
+// The root and a run of small levels 1..l_end in one CTA (levels are
+// sequential: each needs the whole coarser grid): X_root, then per level the
+// coarse-node copy and the detail tiles, separated by block barriers.  Grids
+// alternate between the two scratch buffers as in the per-level path.
+template <typename T, int B>
+__global__ void __launch_bounds__(512)
+    k_recompose_small(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
+                      const LevelDesc* __restrict__ levels, int l_end, int nlev,
+                      int64_t* xroot, int64_t* xa, int64_t* xb, void* __restrict__ out) {
+  constexpr int WPB = 16;
+  extern __shared__ uint32_t sm[];
+  uint32_t* s_hi = sm;                                      // [WPB][32*33]
+  uint32_t* s_lo = sm + WPB * 32 * 33;                      // [WPB][32*33] (B = 64)
+  uint32_t* s_sign = sm + (B == 64 ? 2 : 1) * WPB * 32 * 33;  // [WPB][32]
+  if (m->status) return;
+  const int L = nlev - 1, w = threadIdx.x >> 5, E_f = m->E_f;
+  if (threadIdx.x == 0) {
+    const LevelDesc& D = levels[0];
+    const uint32_t* P = planes + D.plane_off / 4;
+    const int k = 4 * m->cur[0];
+    uint64_t q = 0;
+    for (int p = 0; p < k; p++) q |= (uint64_t)(P[(size_t)(1 + p) * D.W] & 1u) << (B - 1 - p);
+    const bool neg = k > 0 && (P[0] & 1u);
+    const int64_t X = dequant(q, neg, B, m->bl[0]) >> 3;
+    *xroot = X;
+    if (L == 0) *reinterpret_cast<T*>(out) = convert_out<T>(X, E_f);
+  }
+  __syncthreads();
+  const int64_t* coarse = xroot;
+  for (int l = 1; l <= l_end; l++) {
+    const LevelDesc& D = levels[l];
+    const bool final = l == L;
+    void* dst = final ? out : (void*)(((L - l) % 2 == 1) ? xa : xb);
+    // coarse nodes of G_h come from G_2h
+    const uint32_t cz = D.gc[0], cy = D.gc[1], cx = D.gc[2];
+    const uint32_t total = cz * cy * cx;
+    for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+      const uint32_t x = i % cx, r = i / cx, y = r % cy, z = r / cy;
+      const size_t d = ((size_t)(2 * z) * D.g[1] + 2 * y) * D.g[2] + 2 * x;
+      if (final) reinterpret_cast<T*>(dst)[d] = convert_out<T>(coarse[i], E_f);
+      else reinterpret_cast<int64_t*>(dst)[d] = coarse[i];
     }
-    __syncwarp();
-    for (int r = 0; r < 32; r++) {
-      const uint32_t j = base + r * 32 + lane;
-      if (j < L.n) {
-        const uint64_t qh = B == 64 ? (((uint64_t)hi[r * 33 + lane] << 32) | lo[r * 33 + lane])
-                                    : (uint64_t)hi[r * 33 + lane];
-        const bool neg = (s_sign[w][r] >> lane) & 1u;
-        const int64_t c8 = dequant(qh, neg, B, bl);
-        const NodePos p = node_pos(L, j);
-        uint32_t zs[2], ys[2], xs[2];
-        int nz = 1, ny = 1, nx = 1;
-        zs[0] = zs[1] = p.gz >> 1;
-        ys[0] = ys[1] = p.gy >> 1;
-        xs[0] = xs[1] = p.gx >> 1;
-        if (p.t & 4) {
-          uint32_t a, b;
-          axis_nb(p.gz, L.g[0], a, b);
-          zs[0] = a >> 1; zs[1] = b >> 1; nz = 2;
-        }
-        if (p.t & 2) {
-          uint32_t a, b;
-          axis_nb(p.gy, L.g[1], a, b);
-          ys[0] = a >> 1; ys[1] = b >> 1; ny = 2;
-        }
-        if (p.t & 1) {
-          uint32_t a, b;
-          axis_nb(p.gx, L.g[2], a, b);
-          xs[0] = a >> 1; xs[1] = b >> 1; nx = 2;
-        }
-        int64_t sum = 0;
-        for (int a = 0; a < nz; a++)
-          for (int b = 0; b < ny; b++)
-            for (int c = 0; c < nx; c++)
-              sum += __ldg(coarse + ((size_t)zs[a] * L.gc[1] + ys[b]) * L.gc[2] + xs[c]);
-        const int nodd = __popc(p.t);
-        const int64_t X = floor_shift(c8 * ((int64_t)1 << nodd) + 8 * sum, 3 + nodd);
-        const size_t d = ((size_t)p.gz * L.g[1] + p.gy) * L.g[2] + p.gx;
-        if (FINAL) reinterpret_cast<T*>(dst)[d] = convert_out<T>(X, E_f);
-        else reinterpret_cast<int64_t*>(dst)[d] = X;
-      }
+    const int k = 4 * m->cur[l], bl = m->bl[l];
+    const uint32_t* P = planes + D.plane_off / 4;
+    for (uint32_t tile = w; tile < D.ntiles; tile += WPB) {
+      if (final)
+        recompose_tile<T, B, true>(P, D, tile * HP_TILE, k, bl, E_f, coarse, dst,
+                                   s_hi + w * 32 * 33, s_lo + (B == 64 ? w * 32 * 33 : 0),
+                                   s_sign + w * 32);
+      else
+        recompose_tile<T, B, false>(P, D, tile * HP_TILE, k, bl, E_f, coarse, dst,
+                                    s_hi + w * 32 * 33, s_lo + (B == 64 ? w * 32 * 33 : 0),
+                                    s_sign + w * 32);
     }
-    __syncwarp();
+    __syncthreads();
+    coarse = (const int64_t*)dst;
   }
 }
 
@@ -186,6 +253,31 @@ void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const 
     hp::note_launch(), k_recompose_copy<float, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
   else
     hp::note_launch(), k_recompose_copy<double, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+}
+
+void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* levels,
+                            int l_end, int nlev, int64_t* xroot, int64_t* xa, int64_t* xb,
+                            void* out, int dtype, cstream s) {
+  const size_t smem = (size_t)((dtype == 0 ? 1 : 2) * 16 * 32 * 33 + 16 * 32) * 4;
+  if (dtype == 0) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_recompose_small<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      attr = true;
+    }
+    hp::note_launch(), k_recompose_small<float, 32><<<1, 512, smem, s>>>(
+        planes, meta, levels, l_end, nlev, xroot, xa, xb, out);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_recompose_small<double, 64>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    hp::note_launch(), k_recompose_small<double, 64><<<1, 512, smem, s>>>(
+        planes, meta, levels, l_end, nlev, xroot, xa, xb, out);
+  }
 }
 
 void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,

@@ -35,14 +35,14 @@ enum Stage {
   ST_STATS, ST_FINALIZE, ST_LEVELMAX, ST_BITLEN, ST_ENCODE, ST_CHUNK_STATS, ST_DECIDE,
   ST_HUFF_BITS, ST_OFFSETS, ST_HUFF_ENC, ST_RLE_ENC, ST_HEADERS, ST_SEQUENCE, ST_SELECT,
   ST_DECODE, ST_ROOT, ST_COPY, ST_LEVEL, ST_COPY_OUT, ST_LEVEL_OUT, ST_VMAG, ST_CELLS_MAX,
-  ST_CELLS_ENC, ST_CELLS_REC, ST_CELLS_REC_OUT, NSTAGE
+  ST_CELLS_ENC, ST_CELLS_REC, ST_CELLS_REC_OUT, ST_SMALL, NSTAGE
 };
 static const char* kStageName[NSTAGE] = {
     "stats", "stats_finalize", "levelmax", "bitlen", "encode", "chunk_stats", "decide",
     "huff_bits", "group_offsets", "huff_encode", "rle_encode", "headers", "sequence", "select",
     "decode", "recompose_root", "recompose_copy", "recompose_level", "recompose_copy_out",
     "recompose_level_out", "vmag", "cells_levelmax", "cells_encode", "cells_recompose",
-    "cells_recompose_out"};
+    "cells_recompose_out", "recompose_small"};
 
 struct ProfEntry {
   int stage;
@@ -194,7 +194,8 @@ struct hpmdr_handle {
   float qmin = 0, qmax = 0;
   // profiler entries of the last retrieval, patched with bytes known after it
   std::vector<std::pair<size_t, int>> prof_lv;  // (entry, level*4 + kind)
-  size_t prof_decode = SIZE_MAX;
+  size_t prof_decode = SIZE_MAX, prof_small = SIZE_MAX;
+  int small_end = 0;
 
   ~hpmdr_handle() {
     A.release(d_levels, stream);
@@ -613,39 +614,44 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
   Profiler* P = ctx->P();
   H->prof_lv.clear();
   H->prof_decode = SIZE_MAX;
+  H->prof_small = SIZE_MAX;
   { ProfScope p(P, ST_SELECT, 0, s); launch_select(H->d_meta, tau, is_abs, H->d_rd, s); }
   { ProfScope p(P, ST_DECODE, 0, s); H->prof_decode = p.i;
     launch_decode(H->d_slots, H->d_meta, H->d_rd, H->max_items, H->d_planes, s); }
   const uint32_t* Pl = (const uint32_t*)H->d_planes;
   const int L = H->nlev - 1;
-  if (L == 0) {
-    ProfScope p(P, ST_ROOT, 0, s);
-    launch_recompose_root(Pl, H->d_meta, H->d_levels, nullptr, d_out, H->dtype, s);
-  } else {
-    { ProfScope p(P, ST_ROOT, 0, s);
-      launch_recompose_root(Pl, H->d_meta, H->d_levels, H->d_xroot, nullptr, H->dtype, s); }
-    const int64_t* coarse = H->d_xroot;
-    for (int l = 1; l <= L; l++) {
-      const bool final = l == L;
-      void* dst = final ? d_out : (void*)(((L - l) % 2 == 1) ? H->d_xa : H->d_xb);
-      const int fd = final ? H->dtype : -1;
-      if (H->levels[l].fast) {
-        ProfScope p(P, final ? ST_CELLS_REC_OUT : ST_CELLS_REC, 0, s);
+  // the root and the leading run of small generic levels run in one CTA
+  int l_end = 0;
+  while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= 65536) l_end++;
+  {
+    ProfScope p(P, ST_SMALL, 0, s);
+    H->prof_small = p.i;
+    H->small_end = l_end;
+    launch_recompose_small(Pl, H->d_meta, H->d_levels, l_end, H->nlev, H->d_xroot, H->d_xa,
+                           H->d_xb, d_out, H->dtype, s);
+  }
+  const int64_t* coarse =
+      l_end == 0 ? H->d_xroot : (((L - l_end) % 2 == 1) ? H->d_xa : H->d_xb);
+  for (int l = l_end + 1; l <= L; l++) {
+    const bool final = l == L;
+    void* dst = final ? d_out : (void*)(((L - l) % 2 == 1) ? H->d_xa : H->d_xb);
+    const int fd = final ? H->dtype : -1;
+    if (H->levels[l].fast) {
+      ProfScope p(P, final ? ST_CELLS_REC_OUT : ST_CELLS_REC, 0, s);
+      H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
+      H->prof_lv.push_back({SIZE_MAX - 1, l * 4 + (final ? 2 : 0)});  // copy folded in
+      launch_cells_recompose(Pl, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst,
+                             final ? 1 : 0, s);
+    } else {
+      { ProfScope p(P, final ? ST_COPY_OUT : ST_COPY, 0, s);
+        H->prof_lv.push_back({p.i, l * 4 + (final ? 2 : 0)});
+        launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s); }
+      { ProfScope p(P, final ? ST_LEVEL_OUT : ST_LEVEL, 0, s);
         H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
-        H->prof_lv.push_back({SIZE_MAX - 1, l * 4 + (final ? 2 : 0)});  // copy folded in
-        launch_cells_recompose(Pl, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst,
-                               final ? 1 : 0, s);
-      } else {
-        { ProfScope p(P, final ? ST_COPY_OUT : ST_COPY, 0, s);
-          H->prof_lv.push_back({p.i, l * 4 + (final ? 2 : 0)});
-          launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s); }
-        { ProfScope p(P, final ? ST_LEVEL_OUT : ST_LEVEL, 0, s);
-          H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
-          launch_recompose_level(Pl, H->d_meta, H->d_levels + l, H->levels[l], H->d_perm, coarse,
-                                 dst, H->B, fd, s); }
-      }
-      coarse = (const int64_t*)dst;
+        launch_recompose_level(Pl, H->d_meta, H->d_levels + l, H->levels[l], H->d_perm, coarse,
+                               dst, H->B, fd, s); }
     }
+    coarse = (const int64_t*)dst;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -666,6 +672,18 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
     dec += (double)G.stored_len + (double)G.S;
   }
   ctx->prof.patch(H->prof_decode, dec);
+  {  // small levels: their planes, coarse grids and outputs
+    double b = 0;
+    for (int l = 1; l <= H->small_end; l++) {
+      const LevelDesc& D = H->levels[l];
+      const double coarse = (double)D.gc[0] * D.gc[1] * D.gc[2];
+      const double osz = l == H->nlev - 1 ? esz : 8.0;
+      const int g = rd.g[l];
+      b += (g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0) + coarse * 8.0 +
+           ((double)D.n + coarse) * osz;
+    }
+    ctx->prof.patch(H->prof_small, b);
+  }
   size_t last = SIZE_MAX;
   double last_b = 0;
   for (auto& pe : H->prof_lv) {
