@@ -704,8 +704,34 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     const uint32_t mw = (nbits + 31) / 32;
     for (uint32_t i = lane; i < mw; i += 32) T.map[i] = 0;
     __syncwarp();
+    // every true codeword starts at a multiple of the gcd of the code lengths in
+    // use (e.g. 2 when all lengths are even): starting the speculative decodes on
+    // that lattice is what lets them meet the true parse
+    uint32_t gl = 0;
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      uint32_t a = gl, b = myL[r];
+      while (b) {
+        const uint32_t tmp = a % b;
+        a = b;
+        b = tmp;
+      }
+      gl = a;
+    }
+#pragma unroll
+    for (int dd = 16; dd; dd >>= 1) {
+      uint32_t a = gl, b = __shfl_xor_sync(HP_FULL, gl, dd);
+      while (b) {
+        const uint32_t tmp = a % b;
+        a = b;
+        b = tmp;
+      }
+      gl = a;
+    }
+    if (gl == 0) gl = 1;
     const uint32_t seg = (nbits + 31) / 32;
-    const uint32_t s_me = min(lane * seg, nbits), s_next = min((lane + 1) * seg, nbits);
+    const uint32_t s_me = min(lane * seg, nbits) / gl * gl;
+    const uint32_t s_next = lane == 31 ? nbits : min((lane + 1) * seg, nbits) / gl * gl;
     uint32_t c_me = 0, e_me = s_me;
     {
       uint32_t pos = s_me;
