@@ -521,12 +521,11 @@ __device__ __forceinline__ void set_corrupt(FieldMeta* meta) { atomicExch(&meta-
 //     lane's true decoding;
 //  4. a prefix sum of the true counts gives each lane its output offset and
 //     every lane decodes its own span again, writing the bytes.
-// Chunks longer than the bitmap (more than 16 bits per symbol on average are
-// impossible, but a forced Huffman group of incompressible bytes can exceed
-// it) are decoded by one lane.  All reads stay inside the chunk's words; an
+// The bitmap covers the longest possible chunk (16384 codes of 16 bits); a
+// chunk claiming more bits is decoded by one lane and then fails its checks.  All reads stay inside the chunk's words; an
 // invalid code or a wrong symbol count marks the data corrupt.
 #define HP_LUT_BITS 10
-#define HP_MAP_WORDS 2048  // bitmap of 65536 bit positions per warp
+#define HP_MAP_WORDS 8192  // bitmap of 262144 bit positions per warp: 16 bits x 16384 symbols
 
 struct HuffTables {
   uint16_t lut[1 << HP_LUT_BITS];  // (len << 8) | symbol for codes of <= 10 bits, 0 otherwise
@@ -935,14 +934,15 @@ __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const Group
   }
 }
 
-__global__ void __launch_bounds__(128) k_decode(const uint8_t* __restrict__ slots, FieldMeta* meta,
+__global__ void __launch_bounds__(64) k_decode(const uint8_t* __restrict__ slots, FieldMeta* meta,
                                                 const RetrieveDev* __restrict__ rd,
                                                 uint8_t* __restrict__ planes) {
-  __shared__ HuffTables tabs[4];
+  extern __shared__ __align__(16) unsigned char dec_smem[];
+  HuffTables* tabs = reinterpret_cast<HuffTables*>(dec_smem);  // one per warp
   const int w = threadIdx.x >> 5;
   const uint32_t total = rd->items, ngr = rd->n_new;
   const int ng = meta->ngroups;
-  for (uint32_t item = blockIdx.x * 4 + w; item < total; item += gridDim.x * 4) {
+  for (uint32_t item = blockIdx.x * 2 + w; item < total; item += gridDim.x * 2) {
     // newly fetched group holding this item: last k with new_pref[k] <= item
     uint32_t lo = 0, hi = ngr;
     while (hi - lo > 1) {
@@ -969,10 +969,16 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t blocks = (max_items + 3) / 4;
-  uint32_t cap = (uint32_t)sms * 16;
+  uint32_t blocks = (max_items + 1) / 2;
+  uint32_t cap = (uint32_t)sms * 3;
   if (blocks > cap) blocks = cap;
-  hp::note_launch(), k_decode<<<blocks, 128, 0, s>>>(slots, meta, rd, planes);
+  const size_t smem = 2 * sizeof(HuffTables);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  hp::note_launch(), k_decode<<<blocks, 64, smem, s>>>(slots, meta, rd, planes);
 }
 
 }  // namespace hp
