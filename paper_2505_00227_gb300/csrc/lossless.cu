@@ -770,8 +770,8 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
             d++;
           }
         }
-        if (joined) {
-          tc_me = d + map_count(T.map, p, s_next);
+        if (joined) {  // the lane's own codewords from p on, plus the d walked ones
+          tc_me = d + c_me - map_count(T.map, s_me, p);
           e = e_me;
         } else {
           tc_me = d;
