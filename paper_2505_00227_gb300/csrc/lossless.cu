@@ -618,185 +618,250 @@ __device__ __forceinline__ bool huff_emit(const HuffTables& T, BitReader& rd, ui
   return true;
 }
 
+// block-wide exclusive prefix sum over HP_DEC_THREADS values (any thread count
+// that is a multiple of 32, up to 1024); returns the inclusive total too
+#define HP_DEC_THREADS 128
+__device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* scratch, uint32_t& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(HP_FULL, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) scratch[w] = x;
+  __syncthreads();
+  uint32_t base = 0, all = 0;
+  for (int k = 0; k < nw; k++) {
+    if (k < w) base += scratch[k];
+    all += scratch[k];
+  }
+  __syncthreads();
+  total = all;
+  return base + x - v;
+}
+
 __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm,
                                   uint32_t cl, uint32_t len, uint8_t* __restrict__ dst,
-                                  HuffTables& T, FieldMeta* meta) {
-  const int lane = threadIdx.x & 31;
+                                  HuffTables& T, uint32_t* scratch, FieldMeta* meta) {
+  const int tid = threadIdx.x, lane = tid & 31, NT = blockDim.x;
   const uint32_t nc = gm->nchunks;
   const uint64_t hdr = 272 + 4ull * (nc + 1);
-  bool ok = gm->stored_len >= hdr && *reinterpret_cast<const uint64_t*>(stored) == gm->S &&
-            *reinterpret_cast<const uint32_t*>(stored + 8) == HP_CHUNK &&
-            *reinterpret_cast<const uint32_t*>(stored + 12) == nc;
-  if (!__all_sync(HP_FULL, ok)) {
-    if (lane == 0) set_corrupt(meta);
+  const bool ok = gm->stored_len >= hdr && *reinterpret_cast<const uint64_t*>(stored) == gm->S &&
+                  *reinterpret_cast<const uint32_t*>(stored + 8) == HP_CHUNK &&
+                  *reinterpret_cast<const uint32_t*>(stored + 12) == nc;
+  if (!ok) {  // same outcome in every thread
+    if (tid == 0) set_corrupt(meta);
     return;
   }
   const uint8_t* lens = stored + 16;
   const uint32_t* offs = reinterpret_cast<const uint32_t*>(stored + 272);
   const uint32_t w0 = offs[cl], w1 = offs[cl + 1];
   const uint64_t words = (gm->stored_len - hdr) / 4;
-  bool bad = w0 > w1 || w1 > words;
-  // ---- 1. decoding tables
-  uint32_t myL[8];
+  // ---- 1. decoding tables (warp 0), the gcd of the code lengths
+  __shared__ uint32_t s_flag, s_gl;
+  if (tid < 32) {
+    uint32_t myL[8];
+    bool bad = w0 > w1 || w1 > words;
+    uint32_t gl = 0;
 #pragma unroll
-  for (int r = 0; r < 8; r++) {
-    myL[r] = lens[32 * r + lane];
-    bad |= myL[r] > 16;
+    for (int r = 0; r < 8; r++) {
+      myL[r] = lens[32 * r + lane];
+      bad |= myL[r] > 16;
+      uint32_t x = gl, y = myL[r];
+      while (y) {
+        const uint32_t t = x % y;
+        x = y;
+        y = t;
+      }
+      gl = x;
+    }
+#pragma unroll
+    for (int dd = 16; dd; dd >>= 1) {
+      uint32_t x = gl, y = __shfl_xor_sync(HP_FULL, gl, dd);
+      while (y) {
+        const uint32_t t = x % y;
+        x = y;
+        y = t;
+      }
+      gl = x;
+    }
+    bad = __any_sync(HP_FULL, bad);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int r = 0; r < 8; r++)
+      for (int L = 1; L <= 16; L++) {
+        const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
+        if (lane == L) cnt += __popc(m);
+      }
+    if (lane <= 16) T.count[lane] = lane ? cnt : 0;
+    __syncwarp();
+    if (lane == 0) {
+      uint32_t c = 0, idx = 0;
+      for (int L = 1; L <= 16; L++) {
+        T.first[L] = c;
+        T.index[L] = idx;
+        T.fill[L] = idx;
+        idx += T.count[L];
+        c = (c + T.count[L]) << 1;
+      }
+      s_flag = bad ? 1u : 0u;
+      s_gl = gl ? gl : 1u;
+    }
+    __syncwarp();
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      for (int L = 1; L <= 16; L++) {
+        const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
+        if (myL[r] == (uint32_t)L) T.sorted[T.fill[L] + __popc(m & lt)] = (uint8_t)(32 * r + lane);
+        __syncwarp();
+        if (lane == 0) T.fill[L] += __popc(m);
+        __syncwarp();
+      }
+    }
   }
-  if (__any_sync(HP_FULL, bad)) {
-    if (lane == 0) set_corrupt(meta);
+  for (int i = tid; i < (1 << HP_LUT_BITS); i += NT) T.lut[i] = 0;
+  __syncthreads();
+  if (s_flag) {
+    if (tid == 0) set_corrupt(meta);
     return;
-  }
-  uint32_t cnt = 0;  // lane L (1..16) counts the symbols of length L
-#pragma unroll
-  for (int r = 0; r < 8; r++)
-    for (int L = 1; L <= 16; L++) {
-      const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
-      if (lane == L) cnt += __popc(m);
-    }
-  if (lane <= 16) T.count[lane] = lane ? cnt : 0;
-  for (int i = lane; i < (1 << HP_LUT_BITS); i += 32) T.lut[i] = 0;
-  __syncwarp();
-  if (lane == 0) {
-    uint32_t c = 0, idx = 0;
-    for (int L = 1; L <= 16; L++) {
-      T.first[L] = c;
-      T.index[L] = idx;
-      T.fill[L] = idx;
-      idx += T.count[L];
-      c = (c + T.count[L]) << 1;
-    }
-  }
-  __syncwarp();
-  const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-  for (int r = 0; r < 8; r++) {  // counting sort into (length, symbol) order
-    for (int L = 1; L <= 16; L++) {
-      const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
-      if (myL[r] == (uint32_t)L) T.sorted[T.fill[L] + __popc(m & lt)] = (uint8_t)(32 * r + lane);
-      __syncwarp();
-      if (lane == 0) T.fill[L] += __popc(m);
-      __syncwarp();
-    }
   }
   for (int L = 1; L <= HP_LUT_BITS; L++) {
     const uint32_t n = T.count[L];
-    for (uint32_t k = lane; k < n; k += 32) {
+    for (uint32_t k = tid; k < n; k += NT) {
       const uint32_t code = T.first[L] + k, sym = T.sorted[T.index[L] + k];
       const uint32_t span = 1u << (HP_LUT_BITS - L), base = code << (HP_LUT_BITS - L);
       if (base + span <= (1u << HP_LUT_BITS))  // a code set breaking Kraft is caught below
         for (uint32_t r = 0; r < span; r++) T.lut[base + r] = (uint16_t)((L << 8) | sym);
     }
   }
-  __syncwarp();
+  const uint32_t nbits = (w1 - w0) * 32, mw = (nbits + 31) / 32;
+  for (uint32_t i = tid; i < mw && i < HP_MAP_WORDS; i += NT) T.map[i] = 0;
+  __syncthreads();
   BitReader rd;
   rd.w = reinterpret_cast<const uint32_t*>(stored + hdr) + w0;
   rd.nwords = w1 - w0;
-  const uint32_t nbits = (w1 - w0) * 32;
-  bool fail = false;
-  uint32_t total = 0;
-  if (nbits > HP_MAP_WORDS * 32) {  // too long for the bitmap: one lane decodes
-    if (lane == 0) fail = !huff_emit(T, rd, 0, len, dst, 0);
-    total = len;
-  } else {
-    // ---- 2. speculative decoding of 32 equal segments, marking codeword starts
-    const uint32_t mw = (nbits + 31) / 32;
-    for (uint32_t i = lane; i < mw; i += 32) T.map[i] = 0;
-    __syncwarp();
-    // every true codeword starts at a multiple of the gcd of the code lengths in
-    // use (e.g. 2 when all lengths are even): starting the speculative decodes on
-    // that lattice is what lets them meet the true parse
-    uint32_t gl = 0;
-#pragma unroll
-    for (int r = 0; r < 8; r++) {
-      uint32_t a = gl, b = myL[r];
-      while (b) {
-        const uint32_t tmp = a % b;
-        a = b;
-        b = tmp;
-      }
-      gl = a;
+  if (nbits > HP_MAP_WORDS * 32) {  // impossible for a valid chunk: one thread, then checks
+    bool fail = false;
+    if (tid == 0) fail = !huff_emit(T, rd, 0, len, dst, 0);
+    if (tid == 0 && fail) set_corrupt(meta);
+    return;
+  }
+  // ---- 2. speculative decoding of NT segments on the gcd lattice, marking starts
+  const uint32_t gl = s_gl, seg = (nbits + NT - 1) / NT;
+  auto seg_start = [&](int i) -> uint32_t {
+    return i >= NT ? nbits : min((uint32_t)i * seg, nbits) / gl * gl;
+  };
+  const uint32_t s_me = seg_start(tid), s_next = seg_start(tid + 1), s_next2 = seg_start(tid + 2);
+  uint32_t c_me = 0, e_me = s_me;
+  {
+    uint32_t pos = s_me;
+    rd.init(pos);
+    while (pos < s_next) {
+      uint32_t sym;
+      const int L = huff_sym(T, rd, sym);
+      if (!L) break;
+      atomicOr(&T.map[pos >> 5], 1u << (pos & 31));
+      rd.consume(L);
+      pos += L;
+      c_me++;
     }
-#pragma unroll
-    for (int dd = 16; dd; dd >>= 1) {
-      uint32_t a = gl, b = __shfl_xor_sync(HP_FULL, gl, dd);
-      while (b) {
-        const uint32_t tmp = a % b;
-        a = b;
-        b = tmp;
-      }
-      gl = a;
-    }
-    if (gl == 0) gl = 1;
-    const uint32_t seg = (nbits + 31) / 32;
-    const uint32_t s_me = min(lane * seg, nbits) / gl * gl;
-    const uint32_t s_next = lane == 31 ? nbits : min((lane + 1) * seg, nbits) / gl * gl;
-    uint32_t c_me = 0, e_me = s_me;
-    {
-      uint32_t pos = s_me;
-      rd.init(pos);
-      while (pos < s_next) {
+    e_me = pos;
+  }
+  __syncthreads();
+  // ---- 3. every segment continues into the next one until it lands on a start
+  // marked there; from segment 0 on, by induction, each join is a true boundary
+  uint32_t J = e_me, dj = 0;
+  bool joined = true;
+  if (tid + 1 < NT) {
+    joined = false;
+    if (e_me >= s_next) {
+      BitReader tr = rd;
+      uint32_t p = e_me;
+      tr.init(p);
+      while (p < s_next2) {
+        if ((T.map[p >> 5] >> (p & 31)) & 1u) {
+          joined = true;
+          break;
+        }
         uint32_t sym;
-        const int L = huff_sym(T, rd, sym);
+        const int L = huff_sym(T, tr, sym);
         if (!L) break;
-        atomicOr(&T.map[pos >> 5], 1u << (pos & 31));
-        rd.consume(L);
-        pos += L;
-        c_me++;
+        tr.consume(L);
+        p += L;
+        dj++;
       }
-      e_me = pos;
+      if (!joined && p >= s_next2 && s_next2 >= nbits) joined = true;  // ran off the data end
+      J = p;
     }
-    __syncwarp();
-    // ---- 3. true entry point and count of every lane
-    uint32_t t_me = 0, tc_me = 0, t = 0;
-    for (int i = 0; i < 32; i++) {
-      if (lane == i) {
-        t_me = t;
-        uint32_t e = t, d = 0, p = t;
-        bool joined = false;
-        if (t < s_next) {
+  }
+  __shared__ uint32_t s_J[HP_DEC_THREADS], s_dj[HP_DEC_THREADS], s_e[HP_DEC_THREADS];
+  __shared__ uint32_t s_t[HP_DEC_THREADS], s_tc[HP_DEC_THREADS];
+  __shared__ int s_all;
+  s_J[tid] = J;
+  s_dj[tid] = dj;
+  s_e[tid] = e_me;
+  if (tid == 0) s_all = 1;
+  __syncthreads();
+  if (!joined) s_all = 0;
+  __syncthreads();
+  uint32_t t_me, tc_me;
+  if (s_all) {
+    t_me = tid == 0 ? 0u : s_e[tid - 1];
+    tc_me = tid == 0 ? c_me : s_dj[tid - 1] + c_me - map_count(T.map, s_me, min(s_J[tid - 1], s_next));
+    if (tid > 0 && s_J[tid - 1] >= s_next) tc_me = s_dj[tid - 1];  // the join lies past this segment
+  } else {
+    // rare: resolve the segments in order from the true start of segment 0
+    if (tid == 0) {
+      uint32_t t = 0;
+      for (int i = 0; i < NT; i++) {
+        const uint32_t a = seg_start(i), b = seg_start(i + 1);
+        uint32_t p = t, d = 0, e = t, cnt = 0;
+        if (t < b) {
           BitReader tr = rd;
           tr.init(p);
-          while (p < s_next) {
-            if ((T.map[p >> 5] >> (p & 31)) & 1u) {
-              joined = true;
+          bool jn = false;
+          while (p < b) {
+            if (p >= a && ((T.map[p >> 5] >> (p & 31)) & 1u)) {
+              jn = true;
               break;
             }
             uint32_t sym;
             const int L = huff_sym(T, tr, sym);
-            if (!L) break;  // invalid: counts stop here (checked in step 4)
+            if (!L) break;
             tr.consume(L);
             p += L;
             d++;
           }
+          if (jn) {
+            cnt = d + (uint32_t)map_count(T.map, p, b);
+            e = s_e[i];
+          } else {
+            cnt = d;
+            e = p;
+          }
         }
-        if (joined) {  // the lane's own codewords from p on, plus the d walked ones
-          tc_me = d + c_me - map_count(T.map, s_me, p);
-          e = e_me;
-        } else {
-          tc_me = d;
-          e = p;
-        }
+        s_t[i] = t;
+        s_tc[i] = cnt;
         t = e;
       }
-      t = __shfl_sync(HP_FULL, t, i);
     }
-    // ---- 4. output offsets and the final decoding
-    uint32_t o = tc_me;
-#pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const uint32_t v = __shfl_up_sync(HP_FULL, o, dd);
-      if (lane >= dd) o += v;
-    }
-    o -= tc_me;
-    const uint32_t n_me = o < len ? min(tc_me, len - o) : 0u;
-    if (n_me) fail = !huff_emit(T, rd, t_me, n_me, dst, o);
-    total = n_me;
-#pragma unroll
-    for (int dd = 16; dd; dd >>= 1) total += __shfl_xor_sync(HP_FULL, total, dd);
+    __syncthreads();
+    t_me = s_t[tid];
+    tc_me = s_tc[tid];
   }
-  if (__any_sync(HP_FULL, fail) || total != len) {
-    if (lane == 0) set_corrupt(meta);
+  // ---- 4. output offsets and the final decoding
+  uint32_t total_tc;
+  const uint32_t o = block_exscan(tc_me, scratch, total_tc);
+  const uint32_t n_me = o < len ? min(tc_me, len - o) : 0u;
+  bool fail = false;
+  if (n_me) fail = !huff_emit(T, rd, t_me, n_me, dst, o);
+  uint32_t total;
+  (void)block_exscan(n_me, scratch, total);
+  const int any_fail = __syncthreads_or(fail ? 1 : 0);
+  if (any_fail || total != len) {
+    if (tid == 0) set_corrupt(meta);
   }
 }
 
@@ -934,15 +999,16 @@ __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const Group
   }
 }
 
-__global__ void __launch_bounds__(64) k_decode(const uint8_t* __restrict__ slots, FieldMeta* meta,
-                                                const RetrieveDev* __restrict__ rd,
-                                                uint8_t* __restrict__ planes) {
+__global__ void __launch_bounds__(HP_DEC_THREADS) k_decode(const uint8_t* __restrict__ slots,
+                                                           FieldMeta* meta,
+                                                           const RetrieveDev* __restrict__ rd,
+                                                           uint8_t* __restrict__ planes) {
   extern __shared__ __align__(16) unsigned char dec_smem[];
-  HuffTables* tabs = reinterpret_cast<HuffTables*>(dec_smem);  // one per warp
-  const int w = threadIdx.x >> 5;
+  HuffTables& T = *reinterpret_cast<HuffTables*>(dec_smem);
+  __shared__ uint32_t scratch[HP_DEC_THREADS / 32];
   const uint32_t total = rd->items, ngr = rd->n_new;
   const int ng = meta->ngroups;
-  for (uint32_t item = blockIdx.x * 2 + w; item < total; item += gridDim.x * 2) {
+  for (uint32_t item = blockIdx.x; item < total; item += gridDim.x) {
     // newly fetched group holding this item: last k with new_pref[k] <= item
     uint32_t lo = 0, hi = ngr;
     while (hi - lo > 1) {
@@ -957,9 +1023,9 @@ __global__ void __launch_bounds__(64) k_decode(const uint8_t* __restrict__ slots
     const uint32_t len = (uint32_t)(rest < HP_CHUNK ? rest : HP_CHUNK);
     const uint8_t* stored = slots + gm->slot_off;
     uint8_t* dst = planes + gm->plane_off + start;
-    if (gm->method == 1) huff_decode_chunk(stored, gm, cl, len, dst, tabs[w], meta);
-    else rle_decode_chunk(stored, gm, cl, len, dst, meta);
-    __syncwarp();
+    if (gm->method == 1) huff_decode_chunk(stored, gm, cl, len, dst, T, scratch, meta);
+    else if (threadIdx.x < 32) rle_decode_chunk(stored, gm, cl, len, dst, meta);
+    __syncthreads();
   }
 }
 
@@ -969,16 +1035,15 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t blocks = (max_items + 1) / 2;
-  uint32_t cap = (uint32_t)sms * 3;
+  uint32_t blocks = max_items, cap = (uint32_t)sms * 6;
   if (blocks > cap) blocks = cap;
-  const size_t smem = 2 * sizeof(HuffTables);
+  const size_t smem = sizeof(HuffTables);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  hp::note_launch(), k_decode<<<blocks, 64, smem, s>>>(slots, meta, rd, planes);
+  hp::note_launch(), k_decode<<<blocks, HP_DEC_THREADS, smem, s>>>(slots, meta, rd, planes);
 }
 
 }  // namespace hp
