@@ -72,6 +72,54 @@ __device__ __forceinline__ void load_cell_F(const float* __restrict__ f, const C
   for (int t = 0; t < 7; t++)
 #pragma unroll
     for (int k = 0; k < 4; k++) F.nd[t][k] = 0;
+  if (hl == 0) {  // finest level: 2 x 16-byte loads give the 8 values of a row segment
+    uint32_t& sf0 = SELF_FLOOR ? fl : ign;
+    auto row8 = [&](uint32_t z, uint32_t y, float v[8]) {
+      const float4* r4 = reinterpret_cast<const float4*>(f + ((size_t)z * ny + y) * nx + X0);
+      const float4 a = __ldg(r4), b = __ldg(r4 + 1);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    };
+    float v[8];
+    const uint32_t zz0[2] = {Z0, Z2}, yy0[2] = {Y0, Y2};
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int b = 0; b < 2; b++) {
+        row8(zz0[a], yy0[b], v);
+#pragma unroll
+        for (int i = 0; i < 4; i++) F.co[a][b][i] = fixed_point(v[2 * i], E_f, ign);
+        F.co[a][b][4] = fixed_point(__ldg(f + ((size_t)zz0[a] * ny + yy0[b]) * nx + Xe), E_f, ign);
+        if (a == 0 && b == 0)
+#pragma unroll
+          for (int k = 0; k < 4; k++) F.nd[0][k] = fixed_point(v[2 * k + 1], E_f, sf0);
+      }
+    if (hy) {
+      row8(Z0, Y1, v);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        F.nd[1][k] = fixed_point(v[2 * k], E_f, sf0);
+        F.nd[2][k] = fixed_point(v[2 * k + 1], E_f, sf0);
+      }
+    }
+    if (hz) {
+      row8(Z1, Y0, v);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        F.nd[3][k] = fixed_point(v[2 * k], E_f, sf0);
+        F.nd[4][k] = fixed_point(v[2 * k + 1], E_f, sf0);
+      }
+    }
+    if (hz && hy) {
+      row8(Z1, Y1, v);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        F.nd[5][k] = fixed_point(v[2 * k], E_f, sf0);
+        F.nd[6][k] = fixed_point(v[2 * k + 1], E_f, sf0);
+      }
+    }
+    return;
+  }
   auto row = [&](uint32_t z, uint32_t y) {
     return f + ((size_t)(z << hl) * ny + (y << hl)) * nx;
   };
@@ -349,8 +397,13 @@ __global__ void __launch_bounds__(256, 3) k_cells_recompose(const uint32_t* __re
 #pragma unroll
           for (int b = 0; b < 2; b++) {
             const int64_t* row = coarse + ((size_t)zz[a] * gc1 + yy[b]) * gc2;
-#pragma unroll
-            for (int q = 0; q < 4; q++) C[a][b][q] = __ldg(row + cx + q);
+            // cx is a multiple of 4 and gc2 of 32: two aligned 16-byte loads
+            const longlong2 p0 = __ldg(reinterpret_cast<const longlong2*>(row + cx));
+            const longlong2 p1 = __ldg(reinterpret_cast<const longlong2*>(row + cx) + 1);
+            C[a][b][0] = p0.x;
+            C[a][b][1] = p0.y;
+            C[a][b][2] = p1.x;
+            C[a][b][3] = p1.y;
             C[a][b][4] = __ldg(row + xe);
           }
         const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;

@@ -56,43 +56,105 @@ __device__ __forceinline__ void load_chunk(const uint8_t* __restrict__ src, uint
 
 // ------------------------------------------------- statistics per 16 KiB chunk
 // byte histogram (for the Huffman estimate) and the exact RLE cost
-// sum over runs of (1 + LEB128 length of run-1) = 2 runs + #(runs >= 129)
+// sum over runs of (1 + LEB128 length of run-1) = 2 runs + #(runs >= 129).
+// Thread t owns bytes [64t, 64t+64) in registers: run starts are a 64-bit mask
+// (a byte differing from its predecessor, the chunk's first byte always), and
+// only a segment's last run can reach 129 bytes, so its length comes from the
+// first run start of the following segments (a block-wide suffix minimum).
+// Zero bytes are counted with a word trick and added to the histogram once.
 __global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__ planes,
                                                      const FieldMeta* __restrict__ meta,
                                                      const uint32_t* __restrict__ chunk_group,
                                                      uint32_t* __restrict__ group_hist,
                                                      unsigned long long* __restrict__ group_cost,
                                                      uint32_t* __restrict__ chunk_cost) {
-  __shared__ __align__(16) uint8_t buf[HP_CHUNK];
   __shared__ uint32_t hist[8][256];
+  __shared__ uint32_t s_first[256], s_wmin[8];
+  __shared__ uint8_t s_last[256];
   __shared__ uint32_t red[8];
-  const uint32_t c = blockIdx.x;
+  const uint32_t c = blockIdx.x, t = threadIdx.x;
+  const int lane = t & 31, w = t >> 5;
   if (meta->status) return;
   ChunkRef r = chunk_ref(meta, chunk_group, c);
-  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
-  load_chunk(planes + r.gm->plane_off + r.start, r.len, buf);
-  __syncthreads();
-  const int w = threadIdx.x >> 5;
-  uint32_t cost = 0;
-  for (uint32_t i = threadIdx.x; i < r.len; i += blockDim.x) {
-    uint8_t b = buf[i];
-    atomicAdd(&hist[w][b], 1u);
-    if (i == 0 || buf[i - 1] != b) {
-      uint32_t k = 1;
-      while (k <= 128 && i + k < r.len && buf[i + k] == b) k++;
-      cost += 2 + (k > 128 ? 1u : 0u);
+  for (int i = t; i < 8 * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
+  const uint8_t* src = planes + r.gm->plane_off + r.start;
+  const uint32_t a = 64 * t, b = min(r.len, a + 64u), nb = b > a ? b - a : 0u;
+  uint32_t wv[16];
+  if (nb == 64) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + a);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint4 v = __ldcs(s4 + k);
+      wv[4 * k] = v.x;
+      wv[4 * k + 1] = v.y;
+      wv[4 * k + 2] = v.z;
+      wv[4 * k + 3] = v.w;
     }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      uint32_t x = 0;
+      for (int q = 0; q < 4; q++)
+        if (4u * k + q < nb) x |= (uint32_t)src[a + 4 * k + q] << (8 * q);
+      wv[k] = x;
+    }
+  }
+  if (nb) s_last[t] = (uint8_t)(wv[(nb - 1) / 4] >> (8 * ((nb - 1) % 4)));
+  __syncthreads();
+  // run starts and histogram
+  uint64_t mask = 0;
+  uint32_t prev = (t > 0 && nb) ? s_last[t - 1] : 0x100u;  // 0x100: the chunk start
+  uint32_t zeros = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    const uint32_t x = wv[k];
+    const uint32_t zm = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);  // 0x80 per zero byte
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint32_t idx = 4 * k + q;
+      if (idx < nb) {
+        const uint32_t v = (x >> (8 * q)) & 0xffu;
+        if (v != prev) mask |= 1ull << idx;
+        prev = v;
+        if (v) atomicAdd(&hist[w][v], 1u);
+      }
+    }
+    zeros += __popc(zm & (k * 4 + 4 <= nb ? 0xffffffffu : (k * 4 < nb ? (0xffffffffu >> (32 - 8 * (nb - 4 * k))) : 0u)));
+  }
+  if (zeros) atomicAdd(&hist[w][0], zeros);
+  // first run start of each segment, suffix minimum over the following segments
+  const uint32_t INF = 0xffffffffu;
+  uint32_t f = mask ? a + (uint32_t)(__ffsll((long long)mask) - 1) : INF;
+  uint32_t sm = f;  // inclusive suffix min inside the warp
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_down_sync(HP_FULL, sm, d);
+    if (lane + d < 32) sm = min(sm, o);
+  }
+  if (lane == 0) s_wmin[w] = sm;
+  s_first[t] = sm;
+  __syncthreads();
+  uint32_t next;  // first run start after this segment (chunk end if none)
+  {
+    uint32_t nx = lane < 31 ? s_first[t + 1] : INF;
+    for (int k = w + 1; k < 8; k++) nx = min(nx, s_wmin[k]);
+    next = nx == INF ? r.len : nx;
+  }
+  uint32_t cost = 2u * (uint32_t)__popcll((long long)mask);
+  if (mask) {
+    const uint32_t last = a + 63u - (uint32_t)__clzll((long long)mask);
+    if (next - last >= 129u) cost += 1;
   }
   __syncthreads();
   {  // the group's histogram is the sum over its chunks (integer atomics: exact)
-    uint32_t t = threadIdx.x, s = 0;
+    uint32_t s = 0;
     for (int k = 0; k < 8; k++) s += hist[k][t];
     if (s) atomicAdd(&group_hist[(size_t)r.gi * 256 + t], s);
   }
   for (int o = 16; o; o >>= 1) cost += __shfl_xor_sync(HP_FULL, cost, o);
-  if ((threadIdx.x & 31) == 0) red[w] = cost;
+  if (lane == 0) red[w] = cost;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     uint32_t s = 0;
     for (int k = 0; k < 8; k++) s += red[k];
     chunk_cost[c] = s;

@@ -473,9 +473,13 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
     H->A.release(d_lens, s);
   };
   do {
-    if (!field_on_device) {
+    // host input, or a device pointer without 16-byte alignment (the kernels read
+    // rows with 16-byte loads): stage it in an aligned device buffer
+    if (!field_on_device || ((uintptr_t)field & 15)) {
       if ((st = H->A.alloc(&d_field, H->N * esz, s))) break;
-      if (cudaMemcpyAsync(d_field, field, H->N * esz, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      if (cudaMemcpyAsync(d_field, field, H->N * esz,
+                          field_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          s) != cudaSuccess) {
         st = HPMDR_ERR_CUDA;
         g_last_error = "field upload failed";
         break;
@@ -622,7 +626,7 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
   const int L = H->nlev - 1;
   // the root and the leading run of small generic levels run in one CTA
   int l_end = 0;
-  while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= 65536) l_end++;
+  while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= 4096) l_end++;
   {
     ProfScope p(P, ST_SMALL, 0, s);
     H->prof_small = p.i;
