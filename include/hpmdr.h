@@ -150,6 +150,97 @@ HPMDR_API hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uint
 HPMDR_API hpmdr_status hpmdr_handle_reset(hpmdr_ctx* ctx, hpmdr_handle* h, int poison);
 HPMDR_API void hpmdr_handle_free(hpmdr_handle* h);
 
+/* ---- device plane cache -------------------------------------------------
+ * A refactored handle keeps its full plane buffer (the encoder's output; DC
+ * groups are read from it).  hpmdr_handle_compact packs every group's stored
+ * bytes, DC groups included, into one device buffer and releases the planes:
+ * the handle then holds only its compressed streams, and the plane buffer
+ * becomes a cache that the next retrieval allocates and fills with the groups
+ * it selects (Huffman/RLE decoded, DC copied), growing incrementally as later
+ * retrievals tighten the bound.  hpmdr_handle_drop_cache releases that cache
+ * (compacting first if needed).  Results do not depend on the cache state. */
+HPMDR_API hpmdr_status hpmdr_handle_compact(hpmdr_ctx* ctx, hpmdr_handle* h);
+HPMDR_API hpmdr_status hpmdr_handle_drop_cache(hpmdr_ctx* ctx, hpmdr_handle* h);
+/* device bytes: resident = held until hpmdr_handle_free (streams, metadata,
+ * and the planes of a handle that is not compact); cache = plane cache and
+ * recompose scratch held now; cache_max = what they take once allocated.
+ * Any pointer may be NULL. */
+HPMDR_API hpmdr_status hpmdr_handle_memory(const hpmdr_handle* h, uint64_t* resident, uint64_t* cache,
+                                           uint64_t* cache_max);
+
+/* ---- chunk streaming (Sec. 5.3 pipeline) ------------------------------------
+ * A field of dims (ndims entries, as for hpmdr_refactor) is cut into
+ * independent sub-blocks of `chunk` (the last ones along an axis may be
+ * smaller), numbered in C order over the chunk grid; each is refactored as a
+ * field of its own.  Chunk c runs on stream c mod nstreams (1..16 streams
+ * ordered after the context stream): its host<->device copy overlaps the
+ * kernels of the chunks on the other streams.  Overlap needs page-locked host
+ * memory; pageable memory works but serializes the copies.
+ * hpmdr_refactor_chunked: out == NULL only sets *nchunks; else out[0..cap)
+ * receives *nchunks new handles (cap >= *nchunks).
+ * hpmdr_retrieve_chunked: hs are those handles in the same order; every chunk
+ * is retrieved with the absolute bound rel_linf_bound * (max_c max f - min_c
+ * min f), i.e. relative to the whole field's range, and written into its box
+ * of out (prod(dims) values).  infos (may be NULL) receives one entry per
+ * chunk.  Returns HPMDR_ERR_UNATTAINABLE if any chunk is. */
+HPMDR_API hpmdr_status hpmdr_refactor_chunked(hpmdr_ctx* ctx, const void* field, int field_on_device,
+                                              int ndims, const uint64_t dims[3],
+                                              const uint64_t chunk[3], hpmdr_dtype dtype,
+                                              int nstreams, hpmdr_handle** out, uint64_t cap,
+                                              uint64_t* nchunks);
+HPMDR_API hpmdr_status hpmdr_retrieve_chunked(hpmdr_ctx* ctx, hpmdr_handle* const* hs, uint64_t n,
+                                              int ndims, const uint64_t dims[3],
+                                              const uint64_t chunk[3], double rel_linf_bound,
+                                              void* out, int out_on_device, int nstreams,
+                                              hpmdr_retrieve_info* infos);
+
+/* ---- serving ---------------------------------------------------------------
+ * A request loop over refactored fields.  hpmdr_server_add_field compacts a
+ * handle (see hpmdr_handle_compact) and admits its stored bytes against the
+ * HBM budget (HPMDR_ERR_NOMEM if they do not fit).  hpmdr_server_submit queues
+ * a request and returns at once; max_slots worker threads, each with its own
+ * CUDA stream, run requests concurrently.  A request starts as soon as a slot
+ * is free, none of its handles is used by a running request, and the budget
+ * has room for the plane caches it fills (idle caches are evicted least
+ * recently used first); requests that cannot start do not block later ones.
+ * keep_cache = 0 gives the plain per-request path: every request decodes all
+ * groups it uses and drops them afterwards.  A request's result does not
+ * depend on the requests before or beside it.  Outputs are device buffers of
+ * the caller, valid until the request is polled done.  Handles must stay
+ * alive and must not be used outside the server while it runs. */
+typedef struct hpmdr_server hpmdr_server;
+typedef enum { HPMDR_REQ_FIELD = 0, HPMDR_REQ_VMAG = 1 } hpmdr_request_kind;
+typedef struct {
+  int kind;             /* hpmdr_request_kind */
+  hpmdr_handle* h[3];   /* FIELD: h[0]; VMAG: the (vx, vy, vz) triplet, prepared with
+                           hpmdr_qoi_prepare_vmag */
+  double rel_bound;     /* relative L-infinity bound (FIELD) or relative QoI bound (VMAG) */
+  void* out[3];         /* FIELD: out[0] receives the field; VMAG: components (entries may
+                           be NULL) */
+  void* out_vmag;       /* VMAG: receives |v| */
+} hpmdr_request;
+typedef struct {
+  int max_slots;        /* requests running at once, 1..64 */
+  int keep_cache;       /* 1: keep plane caches between requests; 0: plain path */
+  uint64_t hbm_budget;  /* device bytes for stored fields + plane caches + QoI scratch */
+} hpmdr_server_config;
+HPMDR_API hpmdr_status hpmdr_server_create(hpmdr_ctx* ctx, const hpmdr_server_config* cfg,
+                                           hpmdr_server** out);
+/* drops queued requests, waits for running ones */
+HPMDR_API void hpmdr_server_destroy(hpmdr_server* s);
+HPMDR_API hpmdr_status hpmdr_server_add_field(hpmdr_server* s, hpmdr_ctx* ctx, hpmdr_handle* h);
+/* HPMDR_ERR_ARG for a handle not added, HPMDR_ERR_NOMEM if the request cannot
+ * fit in the budget even with every other cache evicted */
+HPMDR_API hpmdr_status hpmdr_server_submit(hpmdr_server* s, const hpmdr_request* r, uint64_t* ticket);
+/* The request's status once done (the ticket is then consumed), else
+ * HPMDR_ERR_BUSY (wait = 0) or block until done (wait != 0).  info: 1 entry
+ * for FIELD, 4 for VMAG (may be NULL).  times: submit, start and completion
+ * instants in seconds of the monotonic clock (may be NULL). */
+HPMDR_API hpmdr_status hpmdr_server_poll(hpmdr_server* s, uint64_t ticket, int wait,
+                                         hpmdr_retrieve_info info[4], double times[3]);
+/* budget bytes in use, peak, cache evictions, completed, queued, running */
+HPMDR_API hpmdr_status hpmdr_server_stats(hpmdr_server* s, uint64_t stats[6]);
+
 /* ---- stage entry points (device pointers, ordered on `stream`) ---------- */
 /* Algorithm 1 on one level: q holds n aligned integers (uint32 for B = 32,
  * uint64 for B = 64), sign n bytes (0/1).  planes receives (B+1) planes of

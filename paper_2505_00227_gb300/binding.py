@@ -43,6 +43,18 @@ class RetrieveInfo(C.Structure):
         return (self.est_units_hi << 64) | self.est_units_lo
 
 
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("h", C.c_void_p * 3), ("rel_bound", C.c_double),
+                ("out", C.c_void_p * 3), ("out_vmag", C.c_void_p)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_slots", C.c_int), ("keep_cache", C.c_int), ("hbm_budget", C.c_uint64)]
+
+
+REQ_FIELD, REQ_VMAG = 0, 1
+
+
 class HpmdrError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -75,6 +87,20 @@ _SIGS = {
     "hpmdr_handle_import": (C.c_int, [vp, vp, C.c_uint64, C.POINTER(vp)]),
     "hpmdr_handle_reset": (C.c_int, [vp, vp, C.c_int]),
     "hpmdr_handle_free": (None, [vp]),
+    "hpmdr_handle_compact": (C.c_int, [vp, vp]),
+    "hpmdr_handle_drop_cache": (C.c_int, [vp, vp]),
+    "hpmdr_handle_memory": (C.c_int, [vp, u64p, u64p, u64p]),
+    "hpmdr_refactor_chunked": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_uint64 * 3, C.c_uint64 * 3,
+                                         C.c_int, C.c_int, C.POINTER(vp), C.c_uint64, u64p]),
+    "hpmdr_retrieve_chunked": (C.c_int, [vp, C.POINTER(vp), C.c_uint64, C.c_int, C.c_uint64 * 3,
+                                         C.c_uint64 * 3, C.c_double, vp, C.c_int, C.c_int,
+                                         C.POINTER(RetrieveInfo)]),
+    "hpmdr_server_create": (C.c_int, [vp, C.POINTER(ServerConfig), C.POINTER(vp)]),
+    "hpmdr_server_destroy": (None, [vp]),
+    "hpmdr_server_add_field": (C.c_int, [vp, vp, vp]),
+    "hpmdr_server_submit": (C.c_int, [vp, C.POINTER(Request), u64p]),
+    "hpmdr_server_poll": (C.c_int, [vp, C.c_uint64, C.c_int, RetrieveInfo * 4, C.c_double * 3]),
+    "hpmdr_server_stats": (C.c_int, [vp, C.c_uint64 * 6]),
     "hpmdr_bitplane_encode": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, vp]),
     "hpmdr_bitplane_decode": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp, vp]),
     "hpmdr_encode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64, u64p, ip]),
@@ -222,6 +248,42 @@ class Context:
         _check(st, "hpmdr_retrieve_qoi_vmag", allow=(ERR_UNATTAINABLE,))
         return out_vmag, list(infos), st
 
+    def refactor_chunked(self, field, chunk, nstreams=2):
+        """Refactor `field` (contiguous tensor, pinned CPU or CUDA) as independent
+        chunks of shape `chunk`; returns the chunk handles in C order."""
+        if not field.is_contiguous():
+            raise ValueError("field must be contiguous")
+        nd, dims = _dims3(field.shape)
+        ndc, cdims = _dims3(chunk)
+        if ndc != nd:
+            raise ValueError("chunk needs as many dimensions as the field")
+        n = C.c_uint64()
+        _check(lib().hpmdr_refactor_chunked(self._p, None, 0, nd, dims, cdims, _dtype_code(field), 1,
+                                            None, 0, C.byref(n)), "hpmdr_refactor_chunked")
+        arr = (vp * n.value)()
+        _check(lib().hpmdr_refactor_chunked(self._p, vp(field.data_ptr()), int(field.is_cuda), nd,
+                                            dims, cdims, _dtype_code(field), int(nstreams), arr,
+                                            n.value, C.byref(n)), "hpmdr_refactor_chunked")
+        out = []
+        for i in range(n.value):
+            h = Handle(self, vp(arr[i]), None, None)
+            h._fill_shape()
+            out.append(h)
+        return out
+
+    def retrieve_chunked(self, handles, shape, chunk, rel_bound, out, nstreams=2):
+        """Reconstruct a chunk-streamed field into `out` (tensor of `shape`);
+        returns (infos, status)."""
+        nd, dims = _dims3(shape)
+        _, cdims = _dims3(chunk)
+        arr = (vp * len(handles))(*[h._p for h in handles])
+        infos = (RetrieveInfo * len(handles))()
+        st = lib().hpmdr_retrieve_chunked(self._p, arr, len(handles), nd, dims, cdims,
+                                          float(rel_bound), vp(out.data_ptr()), int(out.is_cuda),
+                                          int(nstreams), infos)
+        _check(st, "hpmdr_retrieve_chunked", allow=(ERR_UNATTAINABLE,))
+        return list(infos), st
+
     def prepare_vmag(self, handles, vx, vy, vz):
         arr = (vp * 3)(*[h._p for h in handles])
         _check(lib().hpmdr_qoi_prepare_vmag(self._p, arr, vp(vx.data_ptr()), vp(vy.data_ptr()),
@@ -336,6 +398,19 @@ class Handle:
     def reset(self, poison=False):
         _check(lib().hpmdr_handle_reset(self.ctx._p, self._p, int(poison)), "hpmdr_handle_reset")
 
+    def compact(self):
+        _check(lib().hpmdr_handle_compact(self.ctx._p, self._p), "hpmdr_handle_compact")
+
+    def drop_cache(self):
+        _check(lib().hpmdr_handle_drop_cache(self.ctx._p, self._p), "hpmdr_handle_drop_cache")
+
+    def memory(self):
+        """(resident, cache, cache_max) device bytes"""
+        r, c, m = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(lib().hpmdr_handle_memory(self._p, C.byref(r), C.byref(c), C.byref(m)),
+               "hpmdr_handle_memory")
+        return r.value, c.value, m.value
+
 
 def bitplane_encode(q, sign, B, stream=None):
     """q: CUDA int32/int64 tensor viewed as uint32/uint64 bits; sign: uint8 tensor."""
@@ -357,3 +432,67 @@ def bitplane_decode(planes, n, B, k, stream=None):
                                        vp(s.data_ptr()), _stream_ptr(stream)),
            "hpmdr_bitplane_decode")
     return q, s
+
+
+class Server:
+    """hpmdr_server: concurrent retrieval requests over added handles."""
+
+    def __init__(self, ctx, hbm_budget, max_slots=8, keep_cache=True):
+        self.ctx = ctx
+        cfg = ServerConfig(int(max_slots), int(bool(keep_cache)), int(hbm_budget))
+        self._p = vp()
+        _check(lib().hpmdr_server_create(ctx._p, C.byref(cfg), C.byref(self._p)),
+               "hpmdr_server_create")
+        self._keep = {}
+
+    def add(self, handle):
+        _check(lib().hpmdr_server_add_field(self._p, self.ctx._p, handle._p), "hpmdr_server_add_field")
+
+    def submit(self, handles, rel_bound, out=None, out_vmag=None):
+        """One handle: field request into `out`; three handles: |v| into `out_vmag`
+        (out: optional list of three component tensors).  Returns the ticket."""
+        r = Request()
+        if len(handles) == 1:
+            r.kind = REQ_FIELD
+            r.h[0] = handles[0]._p
+            r.out[0] = out.data_ptr()
+            keep = (out,)
+        else:
+            r.kind = REQ_VMAG
+            for i in range(3):
+                r.h[i] = handles[i]._p
+                r.out[i] = out[i].data_ptr() if out is not None and out[i] is not None else None
+            r.out_vmag = out_vmag.data_ptr()
+            keep = (out, out_vmag)
+        r.rel_bound = float(rel_bound)
+        t = C.c_uint64()
+        _check(lib().hpmdr_server_submit(self._p, C.byref(r), C.byref(t)), "hpmdr_server_submit")
+        self._keep[t.value] = keep
+        return t.value
+
+    def poll(self, ticket, wait=True):
+        """(status, infos, (t_submit, t_start, t_done)) or None while pending."""
+        infos = (RetrieveInfo * 4)()
+        times = (C.c_double * 3)()
+        st = lib().hpmdr_server_poll(self._p, ticket, int(wait), infos, times)
+        if st == ERR_BUSY:
+            return None
+        self._keep.pop(ticket, None)
+        _check(st, "hpmdr_server_poll", allow=(ERR_UNATTAINABLE,))
+        return st, list(infos), tuple(times)
+
+    def stats(self):
+        a = (C.c_uint64 * 6)()
+        _check(lib().hpmdr_server_stats(self._p, a), "hpmdr_server_stats")
+        return dict(zip(["used", "peak", "evictions", "completed", "queued", "running"], list(a)))
+
+    def close(self):
+        if self._p:
+            lib().hpmdr_server_destroy(self._p)
+            self._p = vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -8,6 +8,9 @@
 //              back into their range on retrieval.
 //   slots    : one fixed slot per (level, group) of capacity S*cr_den/cr_num
 //              (+header room) for the Huffman or RLE bytes of that group.
+//              A compacted handle packs every group's stored bytes here, DC
+//              groups included, and its plane buffer becomes a cache that a
+//              retrieval allocates and fills (DC groups by copying).
 //   meta     : FieldMeta (device), mirrored to the host after refactor.
 #pragma once
 #include <cstddef>
@@ -73,6 +76,8 @@ struct FieldMeta {
   int32_t cur[HP_MAX_LEVELS];      // groups used by the current reconstruction
   // QoI triplet data (velocity magnitude range) when prepared
   float qmin, qmax;
+  // 1: every group (DC included) is read from the slot buffer on retrieval
+  int32_t compact, pad2;
 };
 
 // retrieval info written by the selection kernel
@@ -95,6 +100,8 @@ namespace hp {
 
 // counts every kernel launch made by the library (runtime.cu)
 void note_launch();
+// raises a kernel's dynamic shared memory limit once per device (thread-safe)
+void set_smem_once(const void* func, int bytes);
 
 // stats.cu
 void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, cstream s);

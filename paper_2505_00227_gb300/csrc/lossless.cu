@@ -1085,8 +1085,15 @@ __global__ void __launch_bounds__(HP_DEC_THREADS) k_decode(const uint8_t* __rest
     const uint32_t len = (uint32_t)(rest < HP_CHUNK ? rest : HP_CHUNK);
     const uint8_t* stored = slots + gm->slot_off;
     uint8_t* dst = planes + gm->plane_off + start;
-    if (gm->method == 1) huff_decode_chunk(stored, gm, cl, len, dst, T, scratch, meta);
-    else if (threadIdx.x < 32) rle_decode_chunk(stored, gm, cl, len, dst, meta);
+    if (gm->method == 1) {
+      huff_decode_chunk(stored, gm, cl, len, dst, T, scratch, meta);
+    } else if (gm->method == 2) {
+      if (threadIdx.x < 32) rle_decode_chunk(stored, gm, cl, len, dst, meta);
+    } else {  // direct copy of a DC group held in the slots of a compact handle
+      const uint4* src = reinterpret_cast<const uint4*>(stored + start);
+      uint4* d = reinterpret_cast<uint4*>(dst);
+      for (uint32_t i = threadIdx.x; i < len / 16; i += blockDim.x) d[i] = src[i];
+    }
     __syncthreads();
   }
 }
@@ -1100,11 +1107,7 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   uint32_t blocks = max_items, cap = (uint32_t)sms * 6;
   if (blocks > cap) blocks = cap;
   const size_t smem = sizeof(HuffTables);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  set_smem_once((const void*)k_decode, (int)smem);
   hp::note_launch(), k_decode<<<blocks, HP_DEC_THREADS, smem, s>>>(slots, meta, rd, planes);
 }
 

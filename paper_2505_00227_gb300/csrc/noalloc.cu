@@ -74,6 +74,7 @@ __global__ void k_noalloc_init(NoAllocScratch* sc, uint64_t S, uint64_t cap, uin
   FieldMeta& m = sc->meta;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     m.status = 0;
+    m.compact = 0;
     m.nlev = 1;
     m.ngroups = 1;
     GroupMeta& g = m.grp[0][0];

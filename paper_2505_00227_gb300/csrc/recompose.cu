@@ -260,21 +260,11 @@ void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const
                             void* out, int dtype, cstream s) {
   const size_t smem = (size_t)((dtype == 0 ? 1 : 2) * 16 * 32 * 33 + 16 * 32) * 4;
   if (dtype == 0) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_recompose_small<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-      attr = true;
-    }
+    set_smem_once((const void*)k_recompose_small<float, 32>, (int)smem);
     hp::note_launch(), k_recompose_small<float, 32><<<1, 512, smem, s>>>(
         planes, meta, levels, l_end, nlev, xroot, xa, xb, out);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_recompose_small<double, 64>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
+    set_smem_once((const void*)k_recompose_small<double, 64>, (int)smem);
     hp::note_launch(), k_recompose_small<double, 64><<<1, 512, smem, s>>>(
         planes, meta, levels, l_end, nlev, xroot, xa, xb, out);
   }

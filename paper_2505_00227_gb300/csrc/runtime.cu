@@ -14,6 +14,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <array>
 #include <string>
 #include <vector>
@@ -27,6 +28,17 @@ static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
 void hp::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void hp::set_smem_once(const void* func, int bytes) {
+  static std::mutex* mu = new std::mutex();
+  static std::set<std::pair<const void*, int>>* done = new std::set<std::pair<const void*, int>>();
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(*mu);
+  if (done->count({func, dev})) return;
+  cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  done->insert({func, dev});
+}
 
 // ------------------------------------------------------------------ profiling
 // Optional per-stage CUDA events on the context stream: elapsed time per
@@ -166,48 +178,10 @@ struct hpmdr_ctx {
   uint32_t cr_num = 2, cr_den = 1;
   Allocator A;
   Profiler prof;
+  std::vector<cudaStream_t> aux;  // extra streams of the chunk pipelines (created on demand)
   Profiler* P() { return prof.on ? &prof : nullptr; }
-};
-
-struct hpmdr_handle {
-  Allocator A;
-  cudaStream_t stream = nullptr;  // stream used to free device memory
-  int dtype = 0, B = 32, nlev = 0, ngroups = 8;
-  uint64_t dims[3] = {1, 1, 1}, N = 1;
-  std::vector<LevelDesc> levels;
-  std::vector<uint32_t> perm;  // per level: processing order of its tiles
-  uint32_t total_tiles = 0, generic_tiles = 0, total_chunks = 0, max_items = 0;
-  uint64_t plane_bytes = 0, slot_bytes = 0;
-  LevelDesc* d_levels = nullptr;
-  uint32_t* d_perm = nullptr;
-  uint8_t* d_planes = nullptr;
-  uint8_t* d_slots = nullptr;
-  FieldMeta* d_meta = nullptr;
-  uint32_t* d_chunk_group = nullptr;
-  RetrieveDev* d_rd = nullptr;
-  int64_t* d_xa = nullptr;  // |G_2| int64 (recompose scratch)
-  int64_t* d_xb = nullptr;  // |G_4| int64
-  int64_t* d_xroot = nullptr;
-  uint64_t xa_elems = 0, xb_elems = 0;
-  std::unique_ptr<FieldMeta> meta{new FieldMeta()};  // host mirror after refactor/import
-  bool qoi_ready = false;
-  float qmin = 0, qmax = 0;
-  // profiler entries of the last retrieval, patched with bytes known after it
-  std::vector<std::pair<size_t, int>> prof_lv;  // (entry, level*4 + kind)
-  size_t prof_decode = SIZE_MAX, prof_small = SIZE_MAX;
-  int small_end = 0;
-
-  ~hpmdr_handle() {
-    A.release(d_levels, stream);
-    A.release(d_perm, stream);
-    A.release(d_planes, stream);
-    A.release(d_slots, stream);
-    A.release(d_meta, stream);
-    A.release(d_chunk_group, stream);
-    A.release(d_rd, stream);
-    A.release(d_xa, stream);
-    A.release(d_xb, stream);
-    A.release(d_xroot, stream);
+  ~hpmdr_ctx() {
+    for (cudaStream_t s : aux) cudaStreamDestroy(s);
   }
 };
 
@@ -221,20 +195,63 @@ static int detail_levels(const uint64_t d[3]) {
 
 static uint32_t axis_count(uint64_t g, int o) { return (uint32_t)(o ? g / 2 : (g + 1) / 2); }
 
-static void plan_levels(hpmdr_handle* H) {
-  const int L = detail_levels(H->dims);
-  H->nlev = L + 1;
-  H->levels.assign(H->nlev, LevelDesc{});
+static uint64_t round16(uint64_t v) { return (v + 15) & ~15ull; }
+
+static hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t dims[3], uint64_t* N) {
+  if (ndims < 1 || ndims > 3 || !dims_in) return HPMDR_ERR_ARG;
+  uint64_t in[3] = {dims_in[0], dims_in[1], dims_in[2]};  // dims may alias dims_in
+  dims[0] = dims[1] = dims[2] = 1;
+  for (int i = 0; i < ndims; i++) dims[3 - ndims + i] = in[3 - ndims + i];
+  uint64_t n = 1;
+  for (int d = 0; d < 3; d++) {
+    if (dims[d] == 0 || dims[d] > 0xffffffffull) return HPMDR_ERR_ARG;
+    n *= dims[d];
+    if (n >= 0xffffffffull) return HPMDR_ERR_ARG;
+  }
+  *N = n;
+  return HPMDR_OK;
+}
+
+// The geometry of one field shape under one coder configuration: the level
+// descriptors, the tile order, the chunk -> group map and the initial
+// FieldMeta (group sizes, chunk ranges, slot layout).  It depends only on
+// (dims, B, T_s, T_cr), so it is built and uploaded once and shared by every
+// handle of that shape: refactoring the same shape again, or the chunks of a
+// streamed field, repeats no host planning and no metadata upload.
+struct Plan {
+  uint64_t dims[3] = {1, 1, 1}, N = 1;
+  int B = 32, ngroups = 8, nlev = 0;
+  std::vector<LevelDesc> levels;
+  std::vector<uint32_t> perm;         // per level: processing order of its tiles
+  std::vector<uint32_t> chunk_group;  // global chunk -> flat group index
+  uint32_t total_tiles = 0, generic_tiles = 0, total_chunks = 0;
+  uint64_t plane_bytes = 0, slot_bytes = 0;
+  std::unique_ptr<FieldMeta> meta0{new FieldMeta()};
+  // one device buffer holding levels, perm, chunk map and meta0
+  unsigned char* d_buf = nullptr;
+  LevelDesc* d_levels = nullptr;
+  uint32_t* d_perm = nullptr;
+  uint32_t* d_chunk_group = nullptr;
+  FieldMeta* d_meta0 = nullptr;
+  ~Plan() {
+    if (d_buf) cudaFree(d_buf);
+  }
+};
+
+static void plan_levels(Plan& P) {
+  const int L = detail_levels(P.dims);
+  P.nlev = L + 1;
+  P.levels.assign(P.nlev, LevelDesc{});
   uint64_t poff = 0;
   uint32_t tile = 0, gtile = 0;
-  for (int l = 0; l < H->nlev; l++) {
-    LevelDesc& D = H->levels[l];
+  for (int l = 0; l < P.nlev; l++) {
+    LevelDesc& D = P.levels[l];
     memset(&D, 0, sizeof(D));
     D.level = l;
     D.hlog = l == 0 ? -1 : (L - l);
     uint64_t h = l == 0 ? (1ull << L) * 2 : (1ull << (L - l));
     for (int d = 0; d < 3; d++) {
-      D.g[d] = (uint32_t)((H->dims[d] + h - 1) / h);
+      D.g[d] = (uint32_t)((P.dims[d] + h - 1) / h);
       D.gc[d] = (D.g[d] + 1) / 2;
     }
     uint64_t n = 0;
@@ -260,36 +277,25 @@ static void plan_levels(hpmdr_handle* H) {
     D.n = (uint32_t)n;
     D.W = (uint32_t)(4 * ((n + 127) / 128));
     D.plane_off = poff;
-    poff += (uint64_t)(H->B + 1) * D.W * 4;
+    poff += (uint64_t)(P.B + 1) * D.W * 4;
     D.tile0 = tile;
     D.ntiles = (uint32_t)((n + HP_TILE - 1) / HP_TILE);
     tile += D.ntiles;
-    D.fast = cell_path_ok(D, H->B) ? 1 : 0;
+    D.fast = cell_path_ok(D, P.B) ? 1 : 0;
     D.gtile0 = gtile;
     if (!D.fast) gtile += D.ntiles;
   }
-  H->plane_bytes = poff;
-  H->total_tiles = tile;
-  H->generic_tiles = gtile;
+  P.plane_bytes = poff;
+  P.total_tiles = tile;
+  P.generic_tiles = gtile;
   // Tile order: a tile starting at node j0 of parity type t sits at relative
   // position (j0 - off_t) / count_t of its type's raster; sorting by that
   // position makes the tiles of all seven types that cover the same region of
   // the grid run together, so their shared coarse neighbours and field rows
   // are read from L2 instead of being streamed from HBM once per type.
-  static std::mutex cache_mu;
-  static std::map<std::array<uint64_t, 4>, std::vector<uint32_t>> cache;
-  const std::array<uint64_t, 4> key_shape = {H->dims[0], H->dims[1], H->dims[2], (uint64_t)H->B};
-  {
-    std::lock_guard<std::mutex> lock(cache_mu);
-    auto it = cache.find(key_shape);
-    if (it != cache.end()) {
-      H->perm = it->second;
-      return;
-    }
-  }
-  H->perm.assign(tile, 0);
-  for (int l = 0; l < H->nlev; l++) {
-    const LevelDesc& D = H->levels[l];
+  P.perm.assign(tile, 0);
+  for (int l = 0; l < P.nlev; l++) {
+    const LevelDesc& D = P.levels[l];
     std::vector<std::pair<double, uint32_t>> key(D.ntiles);
     for (uint32_t q = 0; q < D.ntiles; q++) {
       const uint32_t j0 = q * HP_TILE;
@@ -301,32 +307,28 @@ static void plan_levels(hpmdr_handle* H) {
       key[q] = {rel + 1e-9 * t, q};
     }
     std::sort(key.begin(), key.end());
-    for (uint32_t q = 0; q < D.ntiles; q++) H->perm[D.tile0 + q] = key[q].second;
+    for (uint32_t q = 0; q < D.ntiles; q++) P.perm[D.tile0 + q] = key[q].second;
   }
-  std::lock_guard<std::mutex> lock(cache_mu);
-  if (cache.size() > 256) cache.clear();
-  cache[key_shape] = H->perm;
 }
 
-static uint64_t round16(uint64_t v) { return (v + 15) & ~15ull; }
-
-// group geometry and slot capacities; fills the host FieldMeta
-static void plan_groups(hpmdr_handle* H, uint64_t Ts, uint32_t num, uint32_t den,
-                        std::vector<uint32_t>& chunk_group) {
-  FieldMeta& M = *H->meta;
+// group geometry (Sec. 5.2: B/4 groups of 4 planes, the sign plane in group 0)
+// and slot capacities; fills meta0
+static void plan_groups(Plan& P, uint64_t Ts, uint32_t num, uint32_t den) {
+  FieldMeta& M = *P.meta0;
   uint32_t chunk = 0;
   uint64_t slot = 0;
-  chunk_group.clear();
-  for (int l = 0; l < H->nlev; l++) {
-    const LevelDesc& D = H->levels[l];
-    for (int g = 0; g < H->ngroups; g++) {
+  P.chunk_group.clear();
+  for (int l = 0; l < P.nlev; l++) {
+    const LevelDesc& D = P.levels[l];
+    for (int g = 0; g < P.ngroups; g++) {
       GroupMeta& G = M.grp[l][g];
       memset(&G, 0, sizeof(G));
       G.S = (uint64_t)(g == 0 ? 5 : 4) * D.W * 4;
       G.plane_off = D.plane_off + (g == 0 ? 0 : (uint64_t)(4 * g + 1) * D.W * 4);
       G.nchunks = (uint32_t)((G.S + HP_CHUNK - 1) / HP_CHUNK);
       G.chunk0 = chunk;
-      for (uint32_t c = 0; c < G.nchunks; c++) chunk_group.push_back((uint32_t)(l * H->ngroups + g));
+      for (uint32_t c = 0; c < G.nchunks; c++)
+        P.chunk_group.push_back((uint32_t)(l * P.ngroups + g));
       chunk += G.nchunks;
       G.stored_len = G.S;
       if (G.S > Ts) {
@@ -337,47 +339,164 @@ static void plan_groups(hpmdr_handle* H, uint64_t Ts, uint32_t num, uint32_t den
       }
     }
   }
-  H->total_chunks = chunk;
-  H->slot_bytes = slot;
+  P.total_chunks = chunk;
+  P.slot_bytes = slot;
 }
 
-static void init_meta(hpmdr_handle* H) {
-  FieldMeta& M = *H->meta;
+static void init_meta(FieldMeta& M, int dtype, int B, int nlev, int ngroups) {
+  memset(&M, 0, sizeof(M));
   M.status = 0;
-  M.dtype = H->dtype;
-  M.B = H->B;
-  M.nlev = H->nlev;
-  M.ngroups = H->ngroups;
+  M.dtype = dtype;
+  M.B = B;
+  M.nlev = nlev;
+  M.ngroups = ngroups;
   M.E_f = 0;
   M.input_exact = 1;
   M.key_absmax = 0;
   M.key_min = ~0ull;
   M.key_max = 0;
   M.floored = 0;
-  for (int l = 0; l < HP_MAX_LEVELS; l++) {
-    M.m8[l] = 0;
-    M.lowbits[l] = 0;
-    M.bl[l] = 0;
-    M.exact[l] = 1;
-    M.fetched[l] = 0;
-    M.cur[l] = 0;
-  }
+  for (int l = 0; l < HP_MAX_LEVELS; l++) M.exact[l] = 1;
   M.seq_len = 0;
+  M.compact = 0;
 }
 
-static hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t dims[3], uint64_t* N) {
-  if (ndims < 1 || ndims > 3 || !dims_in) return HPMDR_ERR_ARG;
-  uint64_t in[3] = {dims_in[0], dims_in[1], dims_in[2]};  // dims may alias dims_in
-  dims[0] = dims[1] = dims[2] = 1;
-  for (int i = 0; i < ndims; i++) dims[3 - ndims + i] = in[3 - ndims + i];
-  uint64_t n = 1;
-  for (int d = 0; d < 3; d++) {
-    if (dims[d] == 0 || dims[d] > 0xffffffffull) return HPMDR_ERR_ARG;
-    n *= dims[d];
-    if (n >= 0xffffffffull) return HPMDR_ERR_ARG;
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Plans are cached process-wide per (device, shape, B, T_s, T_cr).  Handles
+// hold a reference, so a plan evicted from the cache lives on while used.
+static hpmdr_status get_plan(int device, const uint64_t dims[3], int dtype, uint64_t Ts,
+                             uint32_t num, uint32_t den, std::shared_ptr<const Plan>* out) {
+  typedef std::array<uint64_t, 8> Key;
+  static std::mutex* mu = new std::mutex();  // never destroyed: usable during exit
+  static std::map<Key, std::shared_ptr<const Plan>>* cache =
+      new std::map<Key, std::shared_ptr<const Plan>>();
+  const Key key = {(uint64_t)device, dims[0], dims[1], dims[2], (uint64_t)dtype, Ts,
+                   (uint64_t)num, (uint64_t)den};
+  {
+    std::lock_guard<std::mutex> lock(*mu);
+    auto it = cache->find(key);
+    if (it != cache->end()) {
+      *out = it->second;
+      return HPMDR_OK;
+    }
   }
-  *N = n;
+  std::shared_ptr<Plan> P(new Plan());
+  for (int d = 0; d < 3; d++) P->dims[d] = dims[d];
+  P->N = dims[0] * dims[1] * dims[2];
+  P->B = dtype == HPMDR_F32 ? 32 : 64;
+  P->ngroups = P->B / 4;
+  plan_levels(*P);
+  if (P->nlev > HP_MAX_LEVELS) return HPMDR_ERR_ARG;
+  init_meta(*P->meta0, dtype, P->B, P->nlev, P->ngroups);
+  plan_groups(*P, Ts, num, den);
+  const size_t o_lv = 0, o_perm = align256(sizeof(LevelDesc) * P->nlev);
+  const size_t o_cg = o_perm + align256(4ull * std::max(P->total_tiles, 1u));
+  const size_t o_meta = o_cg + align256(4ull * std::max(P->total_chunks, 1u));
+  const size_t bytes = o_meta + align256(sizeof(FieldMeta));
+  std::vector<unsigned char> host(bytes, 0);
+  memcpy(host.data() + o_lv, P->levels.data(), sizeof(LevelDesc) * P->nlev);
+  memcpy(host.data() + o_perm, P->perm.data(), 4ull * P->total_tiles);
+  memcpy(host.data() + o_cg, P->chunk_group.data(), 4ull * P->total_chunks);
+  memcpy(host.data() + o_meta, P->meta0.get(), sizeof(FieldMeta));
+  HP_CUDA(cudaMalloc((void**)&P->d_buf, bytes));
+  HP_CUDA(cudaMemcpy(P->d_buf, host.data(), bytes, cudaMemcpyHostToDevice));
+  P->d_levels = (LevelDesc*)(P->d_buf + o_lv);
+  P->d_perm = (uint32_t*)(P->d_buf + o_perm);
+  P->d_chunk_group = (uint32_t*)(P->d_buf + o_cg);
+  P->d_meta0 = (FieldMeta*)(P->d_buf + o_meta);
+  std::lock_guard<std::mutex> lock(*mu);
+  if (cache->size() >= 1024) cache->clear();
+  auto ins = cache->insert({key, P});
+  *out = ins.first->second;
   return HPMDR_OK;
+}
+
+struct hpmdr_handle {
+  Allocator A;
+  cudaStream_t stream = nullptr;  // stream used to free device memory
+  int dtype = 0, B = 32, nlev = 0, ngroups = 8;
+  uint64_t dims[3] = {1, 1, 1}, N = 1;
+  std::shared_ptr<const Plan> plan;
+  std::vector<LevelDesc> levels;  // host copy of plan->levels
+  uint32_t total_tiles = 0, generic_tiles = 0, total_chunks = 0, max_items = 0;
+  uint64_t plane_bytes = 0, slot_bytes = 0;
+  const LevelDesc* d_levels = nullptr;      // owned by the plan
+  const uint32_t* d_perm = nullptr;         // owned by the plan
+  const uint32_t* d_chunk_group = nullptr;  // owned by the plan
+  uint8_t* d_planes = nullptr;  // plane buffer (refactor output, retrieval plane cache)
+  uint8_t* d_slots = nullptr;
+  FieldMeta* d_meta = nullptr;
+  RetrieveDev* d_rd = nullptr;
+  int64_t* d_xa = nullptr;  // |G_2| int64 (recompose scratch)
+  int64_t* d_xb = nullptr;  // |G_4| int64
+  int64_t* d_xroot = nullptr;
+  uint64_t xa_elems = 0, xb_elems = 0;
+  // compact: every group's stored bytes (DC groups included) live in the slot
+  // buffer, packed; the plane buffer is then only a cache of decoded planes,
+  // allocated on the first retrieval and released by hpmdr_handle_drop_cache
+  bool compact = false;
+  std::unique_ptr<FieldMeta> meta{new FieldMeta()};  // host mirror after refactor/import
+  bool qoi_ready = false;
+  float qmin = 0, qmax = 0;
+  // profiler entries of the last retrieval, patched with bytes known after it
+  std::vector<std::pair<size_t, int>> prof_lv;  // (entry, level*4 + kind)
+  size_t prof_decode = SIZE_MAX, prof_small = SIZE_MAX;
+  int small_end = 0;
+
+  void release_cache(cudaStream_t s) {
+    A.release(d_planes, s);
+    A.release(d_xa, s);
+    A.release(d_xb, s);
+    d_planes = nullptr;
+    d_xa = d_xb = nullptr;
+  }
+  ~hpmdr_handle() {
+    A.release(d_planes, stream);
+    A.release(d_slots, stream);
+    A.release(d_meta, stream);
+    A.release(d_rd, stream);
+    A.release(d_xa, stream);
+    A.release(d_xb, stream);
+    A.release(d_xroot, stream);
+  }
+};
+
+// a handle with the plan of (ndims, dims, dtype) under ctx's coder settings
+static hpmdr_status new_handle(hpmdr_ctx* ctx, int ndims, const uint64_t dims_in[3], int dtype,
+                               const std::shared_ptr<const Plan>* plan_in,
+                               std::unique_ptr<hpmdr_handle>& H) {
+  if (dtype != HPMDR_F32 && dtype != HPMDR_F64) return HPMDR_ERR_ARG;
+  H.reset(new hpmdr_handle());
+  HP_TRY(check_dims(ndims, dims_in, H->dims, &H->N));
+  if (plan_in) H->plan = *plan_in;
+  else HP_TRY(get_plan(ctx->device, H->dims, dtype, ctx->Ts, ctx->cr_num, ctx->cr_den, &H->plan));
+  const Plan& P = *H->plan;
+  H->A = ctx->A;
+  H->stream = ctx->stream;
+  H->dtype = dtype;
+  H->B = P.B;
+  H->ngroups = P.ngroups;
+  H->nlev = P.nlev;
+  H->levels = P.levels;
+  H->total_tiles = P.total_tiles;
+  H->generic_tiles = P.generic_tiles;
+  H->total_chunks = P.total_chunks;
+  H->plane_bytes = P.plane_bytes;
+  H->slot_bytes = P.slot_bytes;
+  H->d_levels = P.d_levels;
+  H->d_perm = P.d_perm;
+  H->d_chunk_group = P.d_chunk_group;
+  memcpy(H->meta.get(), P.meta0.get(), sizeof(FieldMeta));
+  return HPMDR_OK;
+}
+
+static void count_items(hpmdr_handle* H) {
+  H->max_items = 0;
+  for (int l = 0; l < H->nlev; l++)
+    for (int g = 0; g < H->ngroups; g++)
+      if (H->compact || H->meta->grp[l][g].method != HPMDR_DC)
+        H->max_items += H->meta->grp[l][g].nchunks;
 }
 
 // ------------------------------------------------------------------- context
@@ -415,6 +534,7 @@ extern "C" hpmdr_status hpmdr_ctx_create(hpmdr_ctx** out, const hpmdr_config* cf
 extern "C" void hpmdr_ctx_destroy(hpmdr_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  for (cudaStream_t s : ctx->aux) cudaStreamSynchronize(s);
   delete ctx;
 }
 
@@ -425,158 +545,108 @@ extern "C" hpmdr_status hpmdr_ctx_set_stream(hpmdr_ctx* ctx, void* stream) {
 }
 
 // ------------------------------------------------------------------ refactor
-static hpmdr_status finish_meta(hpmdr_handle* H, cudaStream_t s) {
-  HP_CUDA(cudaMemcpyAsync(H->meta.get(), H->d_meta, sizeof(FieldMeta), cudaMemcpyDeviceToHost, s));
-  HP_CUDA(cudaStreamSynchronize(s));
-  H->max_items = 0;
-  for (int l = 0; l < H->nlev; l++)
-    for (int g = 0; g < H->ngroups; g++)
-      if (H->meta->grp[l][g].method != HPMDR_DC) H->max_items += H->meta->grp[l][g].nchunks;
-  return (hpmdr_status)H->meta->status;
+struct RefactorProf {
+  size_t hbits = SIZE_MAX, henc = SIZE_MAX, renc = SIZE_MAX;
+};
+
+// Every device step of a refactor, enqueued on s without waiting: reads the
+// field f (device, 16-byte aligned, H's dims), allocates and writes H's
+// planes, slots and device metadata.
+static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void* f,
+                                     cudaStream_t s, RefactorProf* rp) {
+  const size_t esz = H->dtype == HPMDR_F32 ? 4 : 8;
+  const int ngt = H->nlev * H->ngroups;
+  const uint32_t tc = std::max(H->total_chunks, 1u);
+  HP_TRY(H->A.alloc((void**)&H->d_planes, H->plane_bytes, s));
+  HP_TRY(H->A.alloc((void**)&H->d_slots, H->slot_bytes, s));
+  HP_TRY(H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s));
+  // per-call scratch in one block: group histograms and RLE sizes (zeroed,
+  // accumulated by atomics), chunk costs, chunk words, chunk offsets, lengths
+  const size_t o_hist = 0, o_gcost = align256(1024ull * ngt);
+  const size_t o_cost = o_gcost + align256(8ull * ngt);
+  const size_t o_words = o_cost + align256(4ull * tc), o_out = o_words + align256(4ull * tc);
+  const size_t o_lens = o_out + align256(4ull * tc), scratch_bytes = o_lens + align256(256ull * ngt);
+  unsigned char* sc = nullptr;
+  HP_TRY(H->A.alloc((void**)&sc, scratch_bytes, s));
+  uint32_t* d_hist = (uint32_t*)(sc + o_hist);
+  unsigned long long* d_gcost = (unsigned long long*)(sc + o_gcost);
+  uint32_t* d_cost = (uint32_t*)(sc + o_cost);
+  uint32_t* d_words = (uint32_t*)(sc + o_words);
+  uint32_t* d_out = (uint32_t*)(sc + o_out);
+  uint8_t* d_lens = (uint8_t*)(sc + o_lens);
+  if (cudaMemsetAsync(sc, 0, o_cost, s) != cudaSuccess ||
+      cudaMemcpyAsync(H->d_meta, H->plan->d_meta0, sizeof(FieldMeta), cudaMemcpyDeviceToDevice,
+                      s) != cudaSuccess) {
+    H->A.release(sc, s);
+    g_last_error = "refactor setup copy failed";
+    return HPMDR_ERR_CUDA;
+  }
+  ChunkMap cm{H->d_chunk_group, H->total_chunks};
+  Profiler* P = ctx->P();
+  const double fb = (double)H->N * esz, pb = (double)H->plane_bytes, cb = 4.0 * tc + 1032.0 * ngt;
+  { ProfScope p(P, ST_STATS, fb, s); launch_stats(f, H->N, H->dtype, H->d_meta, s); }
+  { ProfScope p(P, ST_FINALIZE, 0, s); launch_stats_finalize(H->d_meta, s); }
+  // algorithmic bytes: the field once (split over the level kernels by node
+  // count) and each level's planes once
+  auto lvl_bytes = [&](const LevelDesc& D, bool planes_too) {
+    return (double)D.n * esz + (planes_too ? (double)(H->B + 1) * D.W * 4.0 : 0.0);
+  };
+  double gen_f = 0, gen_p = 0;
+  for (const LevelDesc& D : H->levels)
+    if (!D.fast) gen_f += (double)D.n * esz, gen_p += (double)(H->B + 1) * D.W * 4.0;
+  for (const LevelDesc& D : H->levels)
+    if (D.fast) {
+      ProfScope p(P, ST_CELLS_MAX, lvl_bytes(D, false), s);
+      launch_cells_levelmax((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta, s);
+    }
+  if (H->generic_tiles) {
+    ProfScope p(P, ST_LEVELMAX, gen_f, s);
+    launch_levelmax(f, H->dtype, H->dims, H->d_levels, H->nlev, H->generic_tiles, H->d_perm,
+                    H->d_meta, s);
+  }
+  { ProfScope p(P, ST_BITLEN, 0, s); launch_bitlen(H->d_meta, s); }
+  for (const LevelDesc& D : H->levels)
+    if (D.fast) {
+      ProfScope p(P, ST_CELLS_ENC, lvl_bytes(D, true), s);
+      launch_cells_encode((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta,
+                          (uint32_t*)H->d_planes, s);
+    }
+  if (H->generic_tiles) {
+    ProfScope p(P, ST_ENCODE, gen_f + gen_p, s);
+    launch_encode(f, H->dtype, H->dims, H->d_levels, H->nlev, H->generic_tiles, H->d_perm,
+                  H->d_meta, (uint32_t*)H->d_planes, s);
+  }
+  { ProfScope p(P, ST_CHUNK_STATS, pb + cb, s);
+    launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_gcost, d_cost, s); }
+  { ProfScope p(P, ST_DECIDE, cb, s);
+    launch_decide(H->d_meta, ngt, d_hist, d_gcost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, -1,
+                  s); }
+  { ProfScope p(P, ST_HUFF_BITS, 0, s); rp->hbits = p.i;
+    launch_huff_bits(H->d_planes, H->d_meta, cm, d_lens, d_words, s); }
+  { ProfScope p(P, ST_OFFSETS, 0, s);
+    launch_group_offsets(H->d_meta, ngt, d_words, d_cost, d_out, s); }
+  { ProfScope p(P, ST_HUFF_ENC, 0, s); rp->henc = p.i;
+    launch_huff_encode(H->d_planes, H->d_meta, cm, d_lens, d_out, H->d_slots, s); }
+  { ProfScope p(P, ST_RLE_ENC, 0, s); rp->renc = p.i;
+    launch_rle_encode(H->d_planes, H->d_meta, cm, d_out, H->d_slots, s); }
+  { ProfScope p(P, ST_HEADERS, 0, s); launch_headers(H->d_meta, ngt, d_lens, d_out, H->d_slots, s); }
+  { ProfScope p(P, ST_SEQUENCE, 0, s); launch_sequence(H->d_meta, s); }
+  H->A.release(sc, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_last_error = std::string("refactor launch: ") + cudaGetErrorString(e);
+    return HPMDR_ERR_CUDA;
+  }
+  return HPMDR_OK;
 }
 
-extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int field_on_device,
-                                       int ndims, const uint64_t dims_in[3], hpmdr_dtype dtype,
-                                       hpmdr_handle** out) {
-  if (!ctx || !field || !out || (dtype != HPMDR_F32 && dtype != HPMDR_F64)) return HPMDR_ERR_ARG;
-  *out = nullptr;
-  std::unique_ptr<hpmdr_handle> H(new hpmdr_handle());
-  HP_TRY(check_dims(ndims, dims_in, H->dims, &H->N));
-  const cudaStream_t s = ctx->stream;
-  H->A = ctx->A;
-  H->stream = s;
-  H->dtype = dtype;
-  H->B = dtype == HPMDR_F32 ? 32 : 64;
-  H->ngroups = H->B / 4;
-  plan_levels(H.get());
-  if (H->nlev > HP_MAX_LEVELS) return HPMDR_ERR_ARG;
-  std::vector<uint32_t> chunk_group;
-  init_meta(H.get());
-  plan_groups(H.get(), ctx->Ts, ctx->cr_num, ctx->cr_den, chunk_group);
-
-  const size_t esz = dtype == HPMDR_F32 ? 4 : 8;
-  const void* f = field;
-  void* d_field = nullptr;
-  const int ngt = H->nlev * H->ngroups;
-  uint32_t *d_hist = nullptr, *d_cost = nullptr, *d_words = nullptr, *d_out = nullptr;
-  unsigned long long* d_gcost = nullptr;
-  uint8_t* d_lens = nullptr;
-  size_t i_hbits = SIZE_MAX, i_henc = SIZE_MAX, i_renc = SIZE_MAX;
-  hpmdr_status st = HPMDR_OK;
-  auto cleanup = [&]() {
-    H->A.release(d_field, s);
-    H->A.release(d_hist, s);
-    H->A.release(d_gcost, s);
-    H->A.release(d_cost, s);
-    H->A.release(d_words, s);
-    H->A.release(d_out, s);
-    H->A.release(d_lens, s);
-  };
-  do {
-    // host input, or a device pointer without 16-byte alignment (the kernels read
-    // rows with 16-byte loads): stage it in an aligned device buffer
-    if (!field_on_device || ((uintptr_t)field & 15)) {
-      if ((st = H->A.alloc(&d_field, H->N * esz, s))) break;
-      if (cudaMemcpyAsync(d_field, field, H->N * esz,
-                          field_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          s) != cudaSuccess) {
-        st = HPMDR_ERR_CUDA;
-        g_last_error = "field upload failed";
-        break;
-      }
-      f = d_field;
-    }
-    const uint32_t tc = std::max(H->total_chunks, 1u);
-    if ((st = H->A.alloc((void**)&H->d_levels, sizeof(LevelDesc) * H->nlev, s))) break;
-    if ((st = H->A.alloc((void**)&H->d_perm, 4ull * std::max(H->total_tiles, 1u), s))) break;
-    if ((st = H->A.alloc((void**)&H->d_planes, H->plane_bytes, s))) break;
-    if ((st = H->A.alloc((void**)&H->d_slots, H->slot_bytes, s))) break;
-    if ((st = H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s))) break;
-    if ((st = H->A.alloc((void**)&H->d_chunk_group, 4ull * tc, s))) break;
-    if ((st = H->A.alloc((void**)&d_hist, 1024ull * ngt, s))) break;
-    if ((st = H->A.alloc((void**)&d_gcost, 8ull * ngt, s))) break;
-    if (cudaMemsetAsync(d_hist, 0, 1024ull * ngt, s) != cudaSuccess ||
-        cudaMemsetAsync(d_gcost, 0, 8ull * ngt, s) != cudaSuccess) {
-      st = HPMDR_ERR_CUDA;
-      break;
-    }
-    if ((st = H->A.alloc((void**)&d_cost, 4ull * tc, s))) break;
-    if ((st = H->A.alloc((void**)&d_words, 4ull * tc, s))) break;
-    if ((st = H->A.alloc((void**)&d_out, 4ull * tc, s))) break;
-    if ((st = H->A.alloc((void**)&d_lens, 256ull * ngt, s))) break;
-    if (cudaMemcpyAsync(H->d_levels, H->levels.data(), sizeof(LevelDesc) * H->nlev,
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(H->d_perm, H->perm.data(), 4ull * H->total_tiles, cudaMemcpyHostToDevice,
-                        s) != cudaSuccess ||
-        cudaMemcpyAsync(H->d_meta, H->meta.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(H->d_chunk_group, chunk_group.data(), 4ull * H->total_chunks,
-                        cudaMemcpyHostToDevice, s) != cudaSuccess) {
-      st = HPMDR_ERR_CUDA;
-      g_last_error = "metadata upload failed";
-      break;
-    }
-    ChunkMap cm{H->d_chunk_group, H->total_chunks};
-    Profiler* P = ctx->P();
-    const double fb = (double)H->N * esz, pb = (double)H->plane_bytes, cb = 4.0 * tc + 1032.0 * ngt;
-    { ProfScope p(P, ST_STATS, fb, s); launch_stats(f, H->N, dtype, H->d_meta, s); }
-    { ProfScope p(P, ST_FINALIZE, 0, s); launch_stats_finalize(H->d_meta, s); }
-    // algorithmic bytes: the field once (split over the level kernels by node
-    // count) and each level's planes once
-    auto lvl_bytes = [&](const LevelDesc& D, bool planes_too) {
-      return (double)D.n * esz + (planes_too ? (double)(H->B + 1) * D.W * 4.0 : 0.0);
-    };
-    double gen_f = 0, gen_p = 0;
-    for (const LevelDesc& D : H->levels)
-      if (!D.fast) gen_f += (double)D.n * esz, gen_p += (double)(H->B + 1) * D.W * 4.0;
-    for (const LevelDesc& D : H->levels)
-      if (D.fast) {
-        ProfScope p(P, ST_CELLS_MAX, lvl_bytes(D, false), s);
-        launch_cells_levelmax((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta, s);
-      }
-    if (H->generic_tiles) {
-      ProfScope p(P, ST_LEVELMAX, gen_f, s);
-      launch_levelmax(f, dtype, H->dims, H->d_levels, H->nlev, H->generic_tiles, H->d_perm,
-                      H->d_meta, s);
-    }
-    { ProfScope p(P, ST_BITLEN, 0, s); launch_bitlen(H->d_meta, s); }
-    for (const LevelDesc& D : H->levels)
-      if (D.fast) {
-        ProfScope p(P, ST_CELLS_ENC, lvl_bytes(D, true), s);
-        launch_cells_encode((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta,
-                            (uint32_t*)H->d_planes, s);
-      }
-    if (H->generic_tiles) {
-      ProfScope p(P, ST_ENCODE, gen_f + gen_p, s);
-      launch_encode(f, dtype, H->dims, H->d_levels, H->nlev, H->generic_tiles, H->d_perm,
-                    H->d_meta, (uint32_t*)H->d_planes, s);
-    }
-    { ProfScope p(P, ST_CHUNK_STATS, pb + cb, s);
-      launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_gcost, d_cost, s); }
-    { ProfScope p(P, ST_DECIDE, cb, s);
-      launch_decide(H->d_meta, ngt, d_hist, d_gcost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, -1,
-                    s); }
-    { ProfScope p(P, ST_HUFF_BITS, 0, s); i_hbits = p.i;
-      launch_huff_bits(H->d_planes, H->d_meta, cm, d_lens, d_words, s); }
-    { ProfScope p(P, ST_OFFSETS, 0, s);
-      launch_group_offsets(H->d_meta, ngt, d_words, d_cost, d_out, s); }
-    { ProfScope p(P, ST_HUFF_ENC, 0, s); i_henc = p.i;
-      launch_huff_encode(H->d_planes, H->d_meta, cm, d_lens, d_out, H->d_slots, s); }
-    { ProfScope p(P, ST_RLE_ENC, 0, s); i_renc = p.i;
-      launch_rle_encode(H->d_planes, H->d_meta, cm, d_out, H->d_slots, s); }
-    { ProfScope p(P, ST_HEADERS, 0, s); launch_headers(H->d_meta, ngt, d_lens, d_out, H->d_slots, s); }
-    { ProfScope p(P, ST_SEQUENCE, 0, s); launch_sequence(H->d_meta, s); }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      g_last_error = std::string("refactor launch: ") + cudaGetErrorString(e);
-      st = HPMDR_ERR_CUDA;
-      break;
-    }
-  } while (0);
-  cleanup();
-  if (st != HPMDR_OK) return st;
-  st = finish_meta(H.get(), s);
-  if (st != HPMDR_OK) return st;
+// waits for H's refactor on s and mirrors its metadata to the host
+static hpmdr_status refactor_finish(hpmdr_ctx* ctx, hpmdr_handle* H, cudaStream_t s,
+                                    const RefactorProf& rp) {
+  HP_CUDA(cudaMemcpyAsync(H->meta.get(), H->d_meta, sizeof(FieldMeta), cudaMemcpyDeviceToHost, s));
+  HP_CUDA(cudaStreamSynchronize(s));
+  count_items(H);
+  if (H->meta->status) return (hpmdr_status)H->meta->status;
   if (ctx->prof.on) {  // bytes of the coder stages, known once the methods are chosen
     double hS = 0, hC = 0, rS = 0, rC = 0;
     for (int l = 0; l < H->nlev; l++)
@@ -585,16 +655,184 @@ extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int fi
         if (G.method == HPMDR_HUFFMAN) hS += G.S, hC += G.stored_len;
         if (G.method == HPMDR_RLE) rS += G.S, rC += G.stored_len;
       }
-    ctx->prof.patch(i_hbits, hS);
-    ctx->prof.patch(i_henc, hS + hC);
-    ctx->prof.patch(i_renc, rS + rC);
+    ctx->prof.patch(rp.hbits, hS);
+    ctx->prof.patch(rp.henc, hS + hC);
+    ctx->prof.patch(rp.renc, rS + rC);
   }
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_refactor(hpmdr_ctx* ctx, const void* field, int field_on_device,
+                                       int ndims, const uint64_t dims_in[3], hpmdr_dtype dtype,
+                                       hpmdr_handle** out) {
+  if (!ctx || !field || !out) return HPMDR_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<hpmdr_handle> H;
+  HP_TRY(new_handle(ctx, ndims, dims_in, dtype, nullptr, H));
+  const cudaStream_t s = ctx->stream;
+  const size_t esz = dtype == HPMDR_F32 ? 4 : 8;
+  const void* f = field;
+  void* d_field = nullptr;
+  // host input, or a device pointer without 16-byte alignment (the kernels read
+  // rows with 16-byte loads): stage it in an aligned device buffer
+  if (!field_on_device || ((uintptr_t)field & 15)) {
+    HP_TRY(H->A.alloc(&d_field, H->N * esz, s));
+    if (cudaMemcpyAsync(d_field, field, H->N * esz,
+                        field_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        s) != cudaSuccess) {
+      H->A.release(d_field, s);
+      g_last_error = "field upload failed";
+      return HPMDR_ERR_CUDA;
+    }
+    f = d_field;
+  }
+  RefactorProf rp;
+  hpmdr_status st = refactor_enqueue(ctx, H.get(), f, s, &rp);
+  H->A.release(d_field, s);
+  if (st != HPMDR_OK) return st;
+  HP_TRY(refactor_finish(ctx, H.get(), s, rp));
   *out = H.release();
+  return HPMDR_OK;
+}
+
+// ------------------------------------------------------------ chunk streaming
+// A field too large to stage at once is cut into independent sub-blocks
+// ("chunks") that are refactored and retrieved as separate fields (Sec. 5.3's
+// pipeline).  Chunk c of the grid (ceil(Z/cz), ceil(Y/cy), ceil(X/cx)), in C
+// order, runs on stream c mod nstreams: its host<->device copy overlaps the
+// kernels of the chunks on the other streams.
+struct ChunkGrid {
+  uint64_t dims[3], chunk[3], count[3], n;
+  void box(uint64_t c, uint64_t org[3], uint64_t ext[3]) const {
+    const uint64_t cc[3] = {c / (count[1] * count[2]), (c / count[2]) % count[1], c % count[2]};
+    for (int d = 0; d < 3; d++) {
+      org[d] = cc[d] * chunk[d];
+      ext[d] = std::min(chunk[d], dims[d] - org[d]);
+    }
+  }
+};
+
+static hpmdr_status chunk_grid(int ndims, const uint64_t dims_in[3], const uint64_t chunk_in[3],
+                               ChunkGrid* G) {
+  uint64_t N = 0;
+  HP_TRY(check_dims(ndims, dims_in, G->dims, &N));
+  if (!chunk_in) return HPMDR_ERR_ARG;
+  uint64_t c[3] = {1, 1, 1};
+  for (int i = 0; i < ndims; i++) c[3 - ndims + i] = chunk_in[3 - ndims + i];
+  G->n = 1;
+  for (int d = 0; d < 3; d++) {
+    if (c[d] == 0) return HPMDR_ERR_ARG;
+    G->chunk[d] = std::min(c[d], G->dims[d]);
+    G->count[d] = (G->dims[d] + G->chunk[d] - 1) / G->chunk[d];
+    G->n *= G->count[d];
+  }
+  return HPMDR_OK;
+}
+
+// copy the box (org, ext) between a dense (Z, Y, X) array and a dense ext-sized one
+static hpmdr_status copy_box(void* dst, const void* src, const ChunkGrid& G, const uint64_t org[3],
+                             const uint64_t ext[3], size_t esz, bool to_chunk, cudaMemcpyKind kind,
+                             cudaStream_t s) {
+  cudaMemcpy3DParms p;
+  memset(&p, 0, sizeof(p));
+  const cudaPitchedPtr full =
+      make_cudaPitchedPtr(to_chunk ? (void*)src : dst, G.dims[2] * esz, G.dims[2] * esz, G.dims[1]);
+  const cudaPitchedPtr part =
+      make_cudaPitchedPtr(to_chunk ? dst : (void*)src, ext[2] * esz, ext[2] * esz, ext[1]);
+  const cudaPos at = make_cudaPos(org[2] * esz, org[1], org[0]);
+  if (to_chunk) {
+    p.srcPtr = full;
+    p.srcPos = at;
+    p.dstPtr = part;
+  } else {
+    p.srcPtr = part;
+    p.dstPtr = full;
+    p.dstPos = at;
+  }
+  p.extent = make_cudaExtent(ext[2] * esz, ext[1], ext[0]);
+  p.kind = kind;
+  HP_CUDA(cudaMemcpy3DAsync(&p, s));
+  return HPMDR_OK;
+}
+
+// nstreams streams ordered after ctx->stream
+static hpmdr_status pipeline_streams(hpmdr_ctx* ctx, int nstreams, std::vector<cudaStream_t>& ss) {
+  if (nstreams < 1 || nstreams > 16) return HPMDR_ERR_ARG;
+  while ((int)ctx->aux.size() < nstreams) {
+    cudaStream_t s = nullptr;
+    HP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ctx->aux.push_back(s);
+  }
+  ss.assign(ctx->aux.begin(), ctx->aux.begin() + nstreams);
+  cudaEvent_t e = nullptr;
+  HP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEventRecord(e, ctx->stream);
+  for (cudaStream_t s : ss) cudaStreamWaitEvent(s, e, 0);
+  cudaEventDestroy(e);
+  return HPMDR_OK;
+}
+
+static hpmdr_status join_streams(const std::vector<cudaStream_t>& ss) {
+  hpmdr_status st = HPMDR_OK;
+  for (cudaStream_t s : ss)
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      g_last_error = "chunk pipeline stream failed";
+      st = HPMDR_ERR_CUDA;
+    }
+  return st;
+}
+
+extern "C" hpmdr_status hpmdr_refactor_chunked(hpmdr_ctx* ctx, const void* field,
+                                               int field_on_device, int ndims,
+                                               const uint64_t dims[3], const uint64_t chunk[3],
+                                               hpmdr_dtype dtype, int nstreams,
+                                               hpmdr_handle** out, uint64_t cap,
+                                               uint64_t* nchunks) {
+  if (!ctx || !nchunks || (dtype != HPMDR_F32 && dtype != HPMDR_F64)) return HPMDR_ERR_ARG;
+  ChunkGrid G;
+  HP_TRY(chunk_grid(ndims, dims, chunk, &G));
+  *nchunks = G.n;
+  if (!out) return HPMDR_OK;  // size query
+  if (!field || cap < G.n) return HPMDR_ERR_ARG;
+  for (uint64_t c = 0; c < G.n; c++) out[c] = nullptr;
+  std::vector<cudaStream_t> ss;
+  HP_TRY(pipeline_streams(ctx, nstreams, ss));
+  const size_t esz = dtype == HPMDR_F32 ? 4 : 8;
+  const size_t stage_bytes = G.chunk[0] * G.chunk[1] * G.chunk[2] * esz;
+  std::vector<void*> stage(ss.size(), nullptr);
+  std::vector<std::unique_ptr<hpmdr_handle>> hs(G.n);
+  std::vector<RefactorProf> rps(G.n);
+  std::shared_ptr<const Plan> full_plan;  // every interior chunk shares one plan
+  hpmdr_status st = HPMDR_OK;
+  for (size_t i = 0; i < ss.size() && st == HPMDR_OK; i++)
+    st = ctx->A.alloc(&stage[i], stage_bytes, ss[i]);
+  for (uint64_t c = 0; c < G.n && st == HPMDR_OK; c++) {
+    const cudaStream_t s = ss[c % ss.size()];
+    uint64_t org[3], ext[3];
+    G.box(c, org, ext);
+    const bool full = ext[0] == G.chunk[0] && ext[1] == G.chunk[1] && ext[2] == G.chunk[2];
+    if ((st = new_handle(ctx, 3, ext, dtype, full && full_plan ? &full_plan : nullptr, hs[c])))
+      break;
+    if (full && !full_plan) full_plan = hs[c]->plan;
+    void* buf = stage[c % ss.size()];
+    if ((st = copy_box(buf, field, G, org, ext, esz, true,
+                       field_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s)))
+      break;
+    st = refactor_enqueue(ctx, hs[c].get(), buf, s, &rps[c]);
+  }
+  for (size_t i = 0; i < ss.size(); i++) ctx->A.release(stage[i], ss[i]);
+  hpmdr_status js = join_streams(ss);
+  if (st == HPMDR_OK) st = js;
+  for (uint64_t c = 0; c < G.n && st == HPMDR_OK; c++)
+    st = refactor_finish(ctx, hs[c].get(), ss[c % ss.size()], rps[c]);
+  if (st != HPMDR_OK) return st;
+  for (uint64_t c = 0; c < G.n; c++) out[c] = hs[c].release();
   return HPMDR_OK;
 }
 
 // ------------------------------------------------------------------ retrieve
 static hpmdr_status ensure_retrieve_buffers(hpmdr_handle* H, cudaStream_t s) {
+  if (!H->d_planes) HP_TRY(H->A.alloc((void**)&H->d_planes, H->plane_bytes, s));
   if (!H->d_rd) HP_TRY(H->A.alloc((void**)&H->d_rd, sizeof(RetrieveDev), s));
   if (!H->d_xroot) HP_TRY(H->A.alloc((void**)&H->d_xroot, 8, s));
   const int L = H->nlev - 1;
@@ -763,6 +1001,62 @@ extern "C" hpmdr_status hpmdr_retrieve_abs(hpmdr_ctx* ctx, hpmdr_handle* h, doub
   return retrieve_common(ctx, h, tau, 1, out, out_on_device, info);
 }
 
+// Retrieval of a chunk-streamed field: every chunk is retrieved with the same
+// absolute bound tau = rel * (max_c vmax_c - min_c vmin_c), so the whole field
+// meets the relative bound against its global range.  Each chunk's
+// reconstruction goes to out (a dense (Z, Y, X) array) through a per-stream
+// staging buffer; the copy of one chunk overlaps the kernels of the next.
+extern "C" hpmdr_status hpmdr_retrieve_chunked(hpmdr_ctx* ctx, hpmdr_handle* const* hs,
+                                               uint64_t n, int ndims, const uint64_t dims[3],
+                                               const uint64_t chunk[3], double rel, void* out,
+                                               int out_on_device, int nstreams,
+                                               hpmdr_retrieve_info* infos) {
+  if (!ctx || !hs || !out || !(rel >= 0.0)) return HPMDR_ERR_ARG;
+  ChunkGrid G;
+  HP_TRY(chunk_grid(ndims, dims, chunk, &G));
+  if (n != G.n || n == 0) return HPMDR_ERR_ARG;
+  double lo = 0, hi = 0;
+  for (uint64_t c = 0; c < n; c++) {
+    const hpmdr_handle* H = hs[c];
+    if (!H || H->dtype != hs[0]->dtype) return HPMDR_ERR_ARG;
+    uint64_t org[3], ext[3];
+    G.box(c, org, ext);
+    for (int d = 0; d < 3; d++)
+      if (H->dims[d] != ext[d]) return HPMDR_ERR_ARG;
+    if (c == 0 || H->meta->vmin < lo) lo = H->meta->vmin;
+    if (c == 0 || H->meta->vmax > hi) hi = H->meta->vmax;
+  }
+  const double tau = rel * (hi - lo);
+  const size_t esz = hs[0]->dtype == HPMDR_F32 ? 4 : 8;
+  std::vector<cudaStream_t> ss;
+  HP_TRY(pipeline_streams(ctx, nstreams, ss));
+  const size_t stage_bytes = G.chunk[0] * G.chunk[1] * G.chunk[2] * esz;
+  std::vector<void*> stage(ss.size(), nullptr);
+  hpmdr_status st = HPMDR_OK;
+  for (size_t i = 0; i < ss.size() && st == HPMDR_OK; i++)
+    st = ctx->A.alloc(&stage[i], stage_bytes, ss[i]);
+  for (uint64_t c = 0; c < n && st == HPMDR_OK; c++) {
+    const cudaStream_t s = ss[c % ss.size()];
+    uint64_t org[3], ext[3];
+    G.box(c, org, ext);
+    void* buf = stage[c % ss.size()];
+    if ((st = enqueue_retrieve(ctx, hs[c], tau, 1, buf, s))) break;
+    st = copy_box(out, buf, G, org, ext, esz, false,
+                  out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+  }
+  for (size_t i = 0; i < ss.size(); i++) ctx->A.release(stage[i], ss[i]);
+  hpmdr_status js = join_streams(ss);
+  if (st != HPMDR_OK) return st;
+  if (js != HPMDR_OK) return js;
+  hpmdr_status worst = HPMDR_OK;
+  for (uint64_t c = 0; c < n; c++) {
+    hpmdr_status r = collect_info(ctx, hs[c], infos ? &infos[c] : nullptr, ss[c % ss.size()]);
+    if (r != HPMDR_OK && r != HPMDR_ERR_UNATTAINABLE) return r;
+    if (r != HPMDR_OK) worst = r;
+  }
+  return worst;
+}
+
 // ----------------------------------------------------------------------- QoI
 extern "C" hpmdr_status hpmdr_qoi_prepare_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[3], const void* vx,
                                                const void* vy, const void* vz, int on_device) {
@@ -919,7 +1213,8 @@ extern "C" hpmdr_status hpmdr_handle_level_info(const hpmdr_handle* h, int level
 
 static const uint8_t* group_src(const hpmdr_handle* h, int l, int g) {
   const GroupMeta& G = h->meta->grp[l][g];
-  return G.method == HPMDR_DC ? h->d_planes + G.plane_off : h->d_slots + G.slot_off;
+  return (G.method == HPMDR_DC && !h->compact) ? h->d_planes + G.plane_off
+                                               : h->d_slots + G.slot_off;
 }
 
 extern "C" hpmdr_status hpmdr_handle_group(const hpmdr_handle* h, int level, int group, void* buf,
@@ -951,7 +1246,7 @@ extern "C" hpmdr_status hpmdr_handle_planes(const hpmdr_handle* h, int level, vo
     *len = need;
     return HPMDR_OK;
   }
-  if (*len < need) return HPMDR_ERR_ARG;
+  if (*len < need || !h->d_planes) return HPMDR_ERR_ARG;  // compact handle without a cache
   *len = need;
   HP_CUDA(cudaMemcpy(buf, h->d_planes + D.plane_off, need, cudaMemcpyDeviceToHost));
   return HPMDR_OK;
@@ -1081,23 +1376,19 @@ extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uin
   if (!r.ok || memcmp(magic, "HPMDR1\0\0", 8) != 0) return HPMDR_ERR_CORRUPT;
   if (r.val<uint32_t>() != 1) return HPMDR_ERR_CORRUPT;
   r.val<uint32_t>();
-  std::unique_ptr<hpmdr_handle> H(new hpmdr_handle());
-  const cudaStream_t s = ctx->stream;
-  H->A = ctx->A;
-  H->stream = s;
-  H->dtype = r.val<int32_t>();
-  H->B = r.val<int32_t>();
+  const int32_t dtype = r.val<int32_t>(), B = r.val<int32_t>();
   const int nlev = r.val<int32_t>();
-  H->ngroups = r.val<int32_t>();
-  if (!r.ok || (H->dtype != 0 && H->dtype != 1) || H->B != (H->dtype ? 64 : 32) ||
-      H->ngroups != H->B / 4)
+  const int32_t ngroups = r.val<int32_t>();
+  if (!r.ok || (dtype != 0 && dtype != 1) || B != (dtype ? 64 : 32) || ngroups != B / 4)
     return HPMDR_ERR_CORRUPT;
   const int32_t E_f = r.val<int32_t>(), input_exact = r.val<int32_t>();
-  for (int d = 0; d < 3; d++) H->dims[d] = r.val<uint64_t>();
-  if (!r.ok || check_dims(3, H->dims, H->dims, &H->N) != HPMDR_OK) return HPMDR_ERR_CORRUPT;
-  plan_levels(H.get());
+  uint64_t dims[3], N = 0;
+  for (int d = 0; d < 3; d++) dims[d] = r.val<uint64_t>();
+  if (!r.ok || check_dims(3, dims, dims, &N) != HPMDR_OK) return HPMDR_ERR_CORRUPT;
+  std::unique_ptr<hpmdr_handle> H;
+  HP_TRY(new_handle(ctx, 3, dims, dtype, nullptr, H));
+  const cudaStream_t s = ctx->stream;
   if (H->nlev != nlev || nlev > HP_MAX_LEVELS) return HPMDR_ERR_CORRUPT;
-  init_meta(H.get());
   FieldMeta& M = *H->meta;
   M.E_f = E_f;
   M.input_exact = input_exact;
@@ -1114,8 +1405,7 @@ extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uin
     M.bl[l] = r.val<int32_t>();
     M.exact[l] = r.val<int32_t>();
   }
-  std::vector<uint32_t> chunk_group;
-  plan_groups(H.get(), ~0ull, 1, 1, chunk_group);  // geometry only; slots re-laid below
+  // the plan's group geometry stays; coded groups get slots of their exact size
   uint64_t slot = 0;
   for (int l = 0; l < nlev; l++)
     for (int g = 0; g < H->ngroups; g++) {
@@ -1145,13 +1435,9 @@ extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uin
     if (M.seq[i] >= nlev) return HPMDR_ERR_CORRUPT;
   r.pad(16);
   if (!r.ok) return HPMDR_ERR_CORRUPT;
-  const uint64_t tc = std::max(H->total_chunks, 1u);
-  HP_TRY(H->A.alloc((void**)&H->d_levels, sizeof(LevelDesc) * nlev, s));
-  HP_TRY(H->A.alloc((void**)&H->d_perm, 4ull * std::max(H->total_tiles, 1u), s));
   HP_TRY(H->A.alloc((void**)&H->d_planes, H->plane_bytes, s));
   HP_TRY(H->A.alloc((void**)&H->d_slots, H->slot_bytes, s));
   HP_TRY(H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s));
-  HP_TRY(H->A.alloc((void**)&H->d_chunk_group, 4 * tc, s));
   for (int l = 0; l < nlev; l++)
     for (int g = 0; g < H->ngroups; g++) {
       const GroupMeta& G = M.grp[l][g];
@@ -1161,18 +1447,9 @@ extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uin
       r.n += G.stored_len;
       r.pad(16);
     }
-  HP_CUDA(cudaMemcpyAsync(H->d_levels, H->levels.data(), sizeof(LevelDesc) * nlev,
-                          cudaMemcpyHostToDevice, s));
-  HP_CUDA(cudaMemcpyAsync(H->d_perm, H->perm.data(), 4ull * H->total_tiles, cudaMemcpyHostToDevice,
-                          s));
   HP_CUDA(cudaMemcpyAsync(H->d_meta, H->meta.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s));
-  HP_CUDA(cudaMemcpyAsync(H->d_chunk_group, chunk_group.data(), 4ull * H->total_chunks,
-                          cudaMemcpyHostToDevice, s));
   HP_CUDA(cudaStreamSynchronize(s));
-  H->max_items = 0;
-  for (int l = 0; l < nlev; l++)
-    for (int g = 0; g < H->ngroups; g++)
-      if (M.grp[l][g].method != HPMDR_DC) H->max_items += M.grp[l][g].nchunks;
+  count_items(H.get());
   *out = H.release();
   return HPMDR_OK;
 }
@@ -1188,13 +1465,101 @@ extern "C" hpmdr_status hpmdr_handle_reset(hpmdr_ctx* ctx, hpmdr_handle* h, int 
   if (!ctx || !h) return HPMDR_ERR_ARG;
   const cudaStream_t s = ctx->stream;
   hp::note_launch(), k_reset<<<1, 1, 0, s>>>(h->d_meta);
-  if (poison)
+  if (poison && h->d_planes)
     for (int l = 0; l < h->nlev; l++)
       for (int g = 0; g < h->ngroups; g++) {
         const GroupMeta& G = h->meta->grp[l][g];
-        if (G.method != HPMDR_DC) HP_CUDA(cudaMemsetAsync(h->d_planes + G.plane_off, 0xA5, G.S, s));
+        if (G.method != HPMDR_DC || h->compact)
+          HP_CUDA(cudaMemsetAsync(h->d_planes + G.plane_off, 0xA5, G.S, s));
       }
   HP_CUDA(cudaStreamSynchronize(s));
+  return HPMDR_OK;
+}
+
+// Packs every group's stored bytes (DC groups included) into one slot buffer
+// and releases the plane buffer: the handle then holds only its compressed
+// streams, and the planes become a cache that the next retrieval allocates
+// and fills by decoding (DC groups by copying).
+extern "C" hpmdr_status hpmdr_handle_compact(hpmdr_ctx* ctx, hpmdr_handle* h) {
+  if (!ctx || !h) return HPMDR_ERR_ARG;
+  if (h->compact) return HPMDR_OK;
+  if (!h->d_planes) return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  FieldMeta& M = *h->meta;
+  std::vector<uint64_t> off((size_t)h->nlev * h->ngroups);
+  uint64_t total = 0;
+  for (int l = 0; l < h->nlev; l++)
+    for (int g = 0; g < h->ngroups; g++) {
+      off[(size_t)l * h->ngroups + g] = total;
+      total += round16(M.grp[l][g].stored_len);
+    }
+  uint8_t* slots = nullptr;
+  HP_TRY(h->A.alloc((void**)&slots, total, s));
+  for (int l = 0; l < h->nlev; l++)
+    for (int g = 0; g < h->ngroups; g++)
+      if (cudaMemcpyAsync(slots + off[(size_t)l * h->ngroups + g], group_src(h, l, g),
+                          M.grp[l][g].stored_len, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        h->A.release(slots, s);
+        cudaStreamSynchronize(s);
+        g_last_error = "compaction copy failed";
+        return HPMDR_ERR_CUDA;
+      }
+  for (int l = 0; l < h->nlev; l++)
+    for (int g = 0; g < h->ngroups; g++) {
+      GroupMeta& G = M.grp[l][g];
+      G.slot_off = off[(size_t)l * h->ngroups + g];
+      G.cap = round16(G.stored_len);
+    }
+  M.compact = 1;
+  for (int l = 0; l < HP_MAX_LEVELS; l++) M.fetched[l] = M.cur[l] = 0;
+  HP_CUDA(cudaMemcpyAsync(h->d_meta, h->meta.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s));
+  h->A.release(h->d_slots, s);
+  h->d_slots = slots;
+  h->slot_bytes = total;
+  h->release_cache(s);
+  h->compact = true;
+  count_items(h);
+  HP_CUDA(cudaStreamSynchronize(s));
+  return HPMDR_OK;
+}
+
+// Releases the plane cache of a handle (compacting it first if needed); the
+// next retrieval decodes every group it uses again.
+extern "C" hpmdr_status hpmdr_handle_drop_cache(hpmdr_ctx* ctx, hpmdr_handle* h) {
+  if (!ctx || !h) return HPMDR_ERR_ARG;
+  if (!h->compact) return hpmdr_handle_compact(ctx, h);
+  if (!h->d_planes) return HPMDR_OK;
+  const cudaStream_t s = ctx->stream;
+  hp::note_launch(), k_reset<<<1, 1, 0, s>>>(h->d_meta);
+  h->release_cache(s);
+  HP_CUDA(cudaGetLastError());
+  return HPMDR_OK;
+}
+
+static uint64_t cache_scratch_bytes(const hpmdr_handle* h) {
+  const int L = h->nlev - 1;
+  uint64_t b = 0;
+  if (L >= 2) {
+    const LevelDesc& D = h->levels[L];
+    b += 8ull * D.gc[0] * D.gc[1] * D.gc[2];
+  }
+  if (L >= 3) {
+    const LevelDesc& D = h->levels[L - 1];
+    b += 8ull * D.gc[0] * D.gc[1] * D.gc[2];
+  }
+  return b;
+}
+
+extern "C" hpmdr_status hpmdr_handle_memory(const hpmdr_handle* h, uint64_t* resident,
+                                            uint64_t* cache, uint64_t* cache_max) {
+  if (!h) return HPMDR_ERR_ARG;
+  const uint64_t fixed = h->slot_bytes + sizeof(FieldMeta) + sizeof(RetrieveDev) + 8;
+  const uint64_t scratch = cache_scratch_bytes(h);
+  if (resident) *resident = fixed + (h->compact ? 0 : h->plane_bytes);
+  if (cache)
+    *cache = (h->compact && h->d_planes ? h->plane_bytes : 0) + (h->d_xa ? 8 * h->xa_elems : 0) +
+             (h->d_xb ? 8 * h->xb_elems : 0);
+  if (cache_max) *cache_max = (h->compact ? h->plane_bytes : 0) + scratch;
   return HPMDR_OK;
 }
 

@@ -169,7 +169,7 @@ __global__ void k_select(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* 
     for (int q = m->fetched[l]; q < g[l]; q++) {
       const GroupMeta& gm = m->grp[l][q];
       bytes_new += gm.stored_len;
-      if (gm.method != 0) {
+      if (gm.method != 0 || m->compact) {  // compact handles copy DC groups too
         rd->new_gi[n_new] = (uint32_t)(l * ng + q);
         rd->new_pref[n_new] = items;
         items += gm.nchunks;

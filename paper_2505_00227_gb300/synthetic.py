@@ -118,6 +118,8 @@ def batch_field(i, shape, seed=1, device="cpu"):
     return spectral(shape, seed=seed * 100003 + i, device=device)
 
 
-def velocity_triplet(side, seed=5, device="cpu"):
-    """(vx, vy, vz), each an independent spectral field on a side^3 grid."""
-    return tuple(spectral((side, side, side), seed=seed * 7 + c, device=device) for c in range(3))
+def velocity_triplet(shape, seed=5, device="cpu"):
+    """(vx, vy, vz), each an independent spectral field on `shape` (an int: a cube)."""
+    if isinstance(shape, int):
+        shape = (shape, shape, shape)
+    return tuple(spectral(shape, seed=seed * 7 + c, device=device) for c in range(3))
