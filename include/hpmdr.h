@@ -241,6 +241,41 @@ HPMDR_API hpmdr_status hpmdr_server_poll(hpmdr_server* s, uint64_t ticket, int w
 /* budget bytes in use, peak, cache evictions, completed, queued, running */
 HPMDR_API hpmdr_status hpmdr_server_stats(hpmdr_server* s, uint64_t stats[6]);
 
+/* ---- batched persistent path ---------------------------------------------
+ * Many fields of uneven sizes (one dtype) refactored, then retrieved, each
+ * pass as one CUDA-graph launch whose every stage is one persistent kernel
+ * over the work units (tiles, chunks, groups) of all fields.  Results are
+ * bit-identical to hpmdr_refactor / hpmdr_retrieve field by field.
+ * hpmdr_batch_create plans n fields of dims[3 j .. 3 j + 2] (C order, as for
+ * hpmdr_refactor with ndims = 3) and allocates their handles once; the batch
+ * owns them (hpmdr_batch_handle gives views usable with every handle entry
+ * point; do not free them) and must be destroyed before its context.
+ * hpmdr_batch_refactor: fields[j] are device pointers, 16-byte aligned.
+ * hpmdr_batch_retrieve: relative L-infinity bound and device output per field,
+ * incremental per handle like hpmdr_retrieve; infos (may be NULL) gets n
+ * entries.  Returns the first error, else HPMDR_ERR_UNATTAINABLE if any field
+ * is, else HPMDR_OK.
+ * hpmdr_batch_autotune times both graphs under each candidate tuning
+ * {persistent CTAs per SM of the tile and chunk kernels, values per unit of
+ * the statistics pass, persistent CTAs per SM of the decoder} and keeps the
+ * fastest (written to best, may be NULL); it leaves the batch refactored from
+ * `fields` with empty retrieval state.  hpmdr_batch_last_ms: device time of
+ * the last refactor and retrieval call (graph launch to results on host). */
+typedef struct hpmdr_batch hpmdr_batch;
+HPMDR_API hpmdr_status hpmdr_batch_create(hpmdr_ctx* ctx, uint64_t n, const uint64_t* dims,
+                                          hpmdr_dtype dtype, hpmdr_batch** out);
+HPMDR_API void hpmdr_batch_destroy(hpmdr_batch* b);
+HPMDR_API hpmdr_status hpmdr_batch_handle(hpmdr_batch* b, uint64_t i, hpmdr_handle** h);
+HPMDR_API hpmdr_status hpmdr_batch_refactor(hpmdr_batch* b, const void* const* fields);
+HPMDR_API hpmdr_status hpmdr_batch_retrieve(hpmdr_batch* b, const double* rel_bounds,
+                                            void* const* outs, hpmdr_retrieve_info* infos);
+HPMDR_API hpmdr_status hpmdr_batch_autotune(hpmdr_batch* b, const void* const* fields,
+                                            const double* rel_bounds, void* const* outs,
+                                            uint32_t best[3]);
+HPMDR_API hpmdr_status hpmdr_batch_set_tuning(hpmdr_batch* b, const uint32_t tuning[3]);
+HPMDR_API hpmdr_status hpmdr_batch_get_tuning(const hpmdr_batch* b, uint32_t tuning[3]);
+HPMDR_API hpmdr_status hpmdr_batch_last_ms(const hpmdr_batch* b, double ms[2]);
+
 /* ---- stage entry points (device pointers, ordered on `stream`) ---------- */
 /* Algorithm 1 on one level: q holds n aligned integers (uint32 for B = 32,
  * uint64 for B = 64), sign n bytes (0/1).  planes receives (B+1) planes of

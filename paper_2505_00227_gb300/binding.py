@@ -101,6 +101,17 @@ _SIGS = {
     "hpmdr_server_submit": (C.c_int, [vp, C.POINTER(Request), u64p]),
     "hpmdr_server_poll": (C.c_int, [vp, C.c_uint64, C.c_int, RetrieveInfo * 4, C.c_double * 3]),
     "hpmdr_server_stats": (C.c_int, [vp, C.c_uint64 * 6]),
+    "hpmdr_batch_create": (C.c_int, [vp, C.c_uint64, u64p, C.c_int, C.POINTER(vp)]),
+    "hpmdr_batch_destroy": (None, [vp]),
+    "hpmdr_batch_handle": (C.c_int, [vp, C.c_uint64, C.POINTER(vp)]),
+    "hpmdr_batch_refactor": (C.c_int, [vp, C.POINTER(vp)]),
+    "hpmdr_batch_retrieve": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(vp),
+                                       C.POINTER(RetrieveInfo)]),
+    "hpmdr_batch_autotune": (C.c_int, [vp, C.POINTER(vp), C.POINTER(C.c_double), C.POINTER(vp),
+                                       C.c_uint32 * 3]),
+    "hpmdr_batch_set_tuning": (C.c_int, [vp, C.c_uint32 * 3]),
+    "hpmdr_batch_get_tuning": (C.c_int, [vp, C.c_uint32 * 3]),
+    "hpmdr_batch_last_ms": (C.c_int, [vp, C.c_double * 2]),
     "hpmdr_bitplane_encode": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, vp]),
     "hpmdr_bitplane_decode": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp, vp]),
     "hpmdr_encode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64, u64p, ip]),
@@ -489,6 +500,82 @@ class Server:
     def close(self):
         if self._p:
             lib().hpmdr_server_destroy(self._p)
+            self._p = vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BorrowedHandle(Handle):
+    """A handle owned by a Batch (never freed from Python)."""
+
+    def free(self):
+        self._p = vp()
+
+
+class Batch:
+    """hpmdr_batch: many fields refactored / retrieved by one graph launch per pass."""
+
+    def __init__(self, ctx, shapes, dtype):
+        import torch
+        self.ctx = ctx
+        self.shapes = [tuple(int(d) for d in ((1,) * (3 - len(sh)) + tuple(sh))) for sh in shapes]
+        self.dtype = dtype
+        n = len(self.shapes)
+        dims = (C.c_uint64 * (3 * n))(*[d for sh in self.shapes for d in sh])
+        self._p = vp()
+        code = F32 if dtype == torch.float32 else F64
+        _check(lib().hpmdr_batch_create(ctx._p, n, dims, code, C.byref(self._p)), "hpmdr_batch_create")
+        self.handles = []
+        for i in range(n):
+            h = vp()
+            _check(lib().hpmdr_batch_handle(self._p, i, C.byref(h)), "hpmdr_batch_handle")
+            self.handles.append(BorrowedHandle(ctx, h, self.shapes[i], dtype))
+
+    def _ptrs(self, tensors):
+        return (vp * len(tensors))(*[t.data_ptr() for t in tensors])
+
+    def refactor(self, fields):
+        _check(lib().hpmdr_batch_refactor(self._p, self._ptrs(fields)), "hpmdr_batch_refactor")
+
+    def retrieve(self, bounds, outs):
+        n = len(self.shapes)
+        b = (C.c_double * n)(*[float(x) for x in bounds])
+        infos = (RetrieveInfo * n)()
+        st = lib().hpmdr_batch_retrieve(self._p, b, self._ptrs(outs), infos)
+        _check(st, "hpmdr_batch_retrieve", allow=(ERR_UNATTAINABLE,))
+        return list(infos), st
+
+    def autotune(self, fields, bounds, outs):
+        n = len(self.shapes)
+        b = (C.c_double * n)(*[float(x) for x in bounds])
+        best = (C.c_uint32 * 3)()
+        _check(lib().hpmdr_batch_autotune(self._p, self._ptrs(fields), b, self._ptrs(outs), best),
+               "hpmdr_batch_autotune")
+        return tuple(best)
+
+    def set_tuning(self, grid_mul, seg, dec_mul):
+        _check(lib().hpmdr_batch_set_tuning(self._p, (C.c_uint32 * 3)(grid_mul, seg, dec_mul)),
+               "hpmdr_batch_set_tuning")
+
+    def tuning(self):
+        t = (C.c_uint32 * 3)()
+        _check(lib().hpmdr_batch_get_tuning(self._p, t), "hpmdr_batch_get_tuning")
+        return tuple(t)
+
+    def last_ms(self):
+        ms = (C.c_double * 2)()
+        _check(lib().hpmdr_batch_last_ms(self._p, ms), "hpmdr_batch_last_ms")
+        return ms[0], ms[1]
+
+    def close(self):
+        for h in self.handles:
+            h._p = vp()
+        if self._p:
+            lib().hpmdr_batch_destroy(self._p)
             self._p = vp()
 
     def __del__(self):

@@ -196,7 +196,41 @@ __device__ __forceinline__ void tile_origin(const CellGeom& G, uint32_t tile, ui
   x0 = tx * G.XW;
 }
 
-// level max of |C8| (and the floor flag of the level's own nodes)
+// level max of |C8| (and the floor flag of the level's own nodes): one tile
+__device__ __forceinline__ void cells_levelmax_tile(const float* __restrict__ f, const CellGeom& G,
+                                                    uint32_t ny, uint32_t nx, int hl, int E_f,
+                                                    uint32_t tile, uint64_t& mx, uint32_t& fl) {
+  const uint32_t i = threadIdx.x, per_row = G.XW / 4;
+  uint32_t cz, cy0, x0;
+  tile_origin(G, tile, cz, cy0, x0);
+  const uint32_t cy = cy0 + i / per_row, cx = x0 + 4 * (i % per_row);
+  if (cy >= G.c[1]) return;
+  CellF F;
+  load_cell_F<true>(f, G, ny, nx, hl, E_f, cz, cy, cx, F, fl);
+  const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    int64_t c8[7];
+    cell_c8(F, k, c8);
+#pragma unroll
+    for (int t = 1; t <= 7; t++)
+      if (type_exists(t, hz, hy)) {
+        const uint64_t m = umag(c8[t - 1]);
+        mx = m > mx ? m : mx;
+      }
+  }
+}
+
+__device__ __forceinline__ void cells_levelmax_flush(FieldMeta* meta, int level, uint64_t mx,
+                                                     uint32_t fl) {
+  mx = warp_max_u64(mx);
+  const unsigned anyfl = __any_sync(HP_FULL, fl != 0);
+  if ((threadIdx.x & 31) == 0) {
+    if (mx) atomicMax((unsigned long long*)&meta->m8[level], (unsigned long long)mx);
+    if (anyfl) atomicOr(&meta->floored, 1u);
+  }
+}
+
 __global__ void __launch_bounds__(256, 2) k_cells_levelmax(const float* __restrict__ f, uint32_t ny,
                                                         uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                         FieldMeta* meta) {
@@ -204,114 +238,107 @@ __global__ void __launch_bounds__(256, 2) k_cells_levelmax(const float* __restri
   const LevelDesc& L = *Lp;
   const CellGeom G = cell_geom(L);
   const int E_f = meta->E_f, hl = L.hlog;
-  const uint32_t i = threadIdx.x, per_row = G.XW / 4;
   uint64_t mx = 0;
   uint32_t fl = 0;
-  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x) {
-    uint32_t cz, cy0, x0;
-    tile_origin(G, tile, cz, cy0, x0);
-    const uint32_t cy = cy0 + i / per_row, cx = x0 + 4 * (i % per_row);
-    if (cy >= G.c[1]) continue;
-    CellF F;
-    load_cell_F<true>(f, G, ny, nx, hl, E_f, cz, cy, cx, F, fl);
-    const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      int64_t c8[7];
-      cell_c8(F, k, c8);
-#pragma unroll
-      for (int t = 1; t <= 7; t++)
-        if (type_exists(t, hz, hy)) {
-          const uint64_t m = umag(c8[t - 1]);
-          mx = m > mx ? m : mx;
-        }
-    }
-  }
-  mx = warp_max_u64(mx);
-  const unsigned anyfl = __any_sync(HP_FULL, fl != 0);
-  if ((threadIdx.x & 31) == 0) {
-    if (mx) atomicMax((unsigned long long*)&meta->m8[L.level], (unsigned long long)mx);
-    if (anyfl) atomicOr(&meta->floored, 1u);
-  }
+  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
+    cells_levelmax_tile(f, G, ny, nx, hl, E_f, tile, mx, fl);
+  cells_levelmax_flush(meta, L.level, mx, fl);
 }
 
-// quantize + Algorithm 1 for the level
+// quantize + Algorithm 1: one tile of 1024 cells (all 7 types)
+typedef uint32_t CellQ[7][32][33];   // [type][row * NW + word][cell within word]
+typedef uint8_t CellS[7][32][32];    // sign per cell
+
+__device__ __forceinline__ void cells_zero_padding(const LevelDesc& L, uint32_t* P) {
+  // the padding words past the last node of every plane are zero
+  const uint32_t W = L.W, used = (L.n + 31) / 32, pad = W - used;
+  for (uint32_t k = threadIdx.x; k < pad * (32 + 1); k += blockDim.x)
+    P[(size_t)(k / pad) * W + used + k % pad] = 0u;
+}
+
+__device__ __forceinline__ void cells_encode_tile(const float* __restrict__ f, const CellGeom& G,
+                                                  const LevelDesc& L, uint32_t ny, uint32_t nx,
+                                                  int E_f, int bl, uint32_t* __restrict__ P,
+                                                  uint32_t tile, uint64_t& low, CellQ& s_q,
+                                                  CellS& s_s) {
+  const int hl = L.hlog;
+  const uint32_t i = threadIdx.x, per_row = G.XW / 4, W = L.W;
+  uint32_t cz, cy0, x0;
+  tile_origin(G, tile, cz, cy0, x0);
+  {  // phase cells
+    const uint32_t r = i / per_row, xl = 4 * (i % per_row), cy = cy0 + r, cx = x0 + xl;
+    if (cy < G.c[1]) {
+      CellF F;
+      uint32_t ign = 0;
+      load_cell_F<false>(f, G, ny, nx, hl, E_f, cz, cy, cx, F, ign);
+      const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
+      const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        int64_t c8[7];
+        cell_c8(F, k, c8);
+#pragma unroll
+        for (int t = 1; t <= 7; t++) {
+          uint32_t q = 0;
+          uint8_t sg = 0;
+          if (type_exists(t, hz, hy)) {
+            const uint64_t m = umag(c8[t - 1]);
+            sg = c8[t - 1] < 0;
+            if (bl == 0) q = 0;
+            else if (bl <= 32) q = (uint32_t)(m << (32 - bl));
+            else {
+              q = (uint32_t)(m >> (bl - 32));
+              low |= m & ((1ull << (bl - 32)) - 1ull);
+            }
+          }
+          s_q[t - 1][rw][b0 + k] = q;
+          s_s[t - 1][rw][b0 + k] = sg;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (i < 224) {  // phase words: thread = (type, row, word)
+    const int t = i / 32 + 1;
+    const uint32_t rw = i % 32, r = rw / G.NW, w = rw % G.NW, cy = cy0 + r;
+    if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
+      uint32_t a[32];
+#pragma unroll
+      for (int b = 0; b < 32; b++) a[b] = s_q[t - 1][rw][b];
+      transpose32(a);
+      uint32_t sw = 0;
+#pragma unroll
+      for (int b = 0; b < 32; b++) sw |= (uint32_t)s_s[t - 1][rw][b] << b;
+      const uint32_t word = (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
+      P[word] = sw;
+#pragma unroll
+      for (int p = 0; p < 32; p++) P[(size_t)(1 + p) * W + word] = a[31 - p];
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void cells_lowbits_flush(FieldMeta* meta, int level, uint64_t low) {
+  low = warp_or_u64(low);
+  if ((threadIdx.x & 31) == 0 && low)
+    atomicOr((unsigned long long*)&meta->lowbits[level], (unsigned long long)low);
+}
+
 __global__ void __launch_bounds__(256, 2) k_cells_encode(const float* __restrict__ f, uint32_t ny,
                                                       uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                       FieldMeta* meta, uint32_t* __restrict__ planes) {
-  __shared__ uint32_t s_q[7][32][33];  // [type][row * NW + word][cell within word]
-  __shared__ uint8_t s_s[7][32][32];   // sign per cell
+  __shared__ CellQ s_q;
+  __shared__ CellS s_s;
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   const CellGeom G = cell_geom(L);
-  const int E_f = meta->E_f, hl = L.hlog, bl = meta->bl[L.level];
-  const uint32_t i = threadIdx.x, per_row = G.XW / 4;
+  const int E_f = meta->E_f, bl = meta->bl[L.level];
   uint32_t* P = planes + L.plane_off / 4;
-  const uint32_t W = L.W;
   uint64_t low = 0;
-  if (blockIdx.x == 0) {  // the padding words past the last node of every plane are zero
-    const uint32_t used = (L.n + 31) / 32, pad = W - used;
-    for (uint32_t k = i; k < pad * (32 + 1); k += blockDim.x) P[(size_t)(k / pad) * W + used + k % pad] = 0u;
-  }
-  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x) {
-    uint32_t cz, cy0, x0;
-    tile_origin(G, tile, cz, cy0, x0);
-    {  // phase cells
-      const uint32_t r = i / per_row, xl = 4 * (i % per_row), cy = cy0 + r, cx = x0 + xl;
-      if (cy < G.c[1]) {
-        CellF F;
-        uint32_t ign = 0;
-        load_cell_F<false>(f, G, ny, nx, hl, E_f, cz, cy, cx, F, ign);
-        const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
-        const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          int64_t c8[7];
-          cell_c8(F, k, c8);
-#pragma unroll
-          for (int t = 1; t <= 7; t++) {
-            uint32_t q = 0;
-            uint8_t sg = 0;
-            if (type_exists(t, hz, hy)) {
-              const uint64_t m = umag(c8[t - 1]);
-              sg = c8[t - 1] < 0;
-              if (bl == 0) q = 0;
-              else if (bl <= 32) q = (uint32_t)(m << (32 - bl));
-              else {
-                q = (uint32_t)(m >> (bl - 32));
-                low |= m & ((1ull << (bl - 32)) - 1ull);
-              }
-            }
-            s_q[t - 1][rw][b0 + k] = q;
-            s_s[t - 1][rw][b0 + k] = sg;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (i < 224) {  // phase words: thread = (type, row, word)
-      const int t = i / 32 + 1;
-      const uint32_t rw = i % 32, r = rw / G.NW, w = rw % G.NW, cy = cy0 + r;
-      if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
-        uint32_t a[32];
-#pragma unroll
-        for (int b = 0; b < 32; b++) a[b] = s_q[t - 1][rw][b];
-        transpose32(a);
-        uint32_t sw = 0;
-#pragma unroll
-        for (int b = 0; b < 32; b++) sw |= (uint32_t)s_s[t - 1][rw][b] << b;
-        const uint32_t word =
-            (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
-        P[word] = sw;
-#pragma unroll
-        for (int p = 0; p < 32; p++) P[(size_t)(1 + p) * W + word] = a[31 - p];
-      }
-    }
-    __syncthreads();
-  }
-  low = warp_or_u64(low);
-  if ((threadIdx.x & 31) == 0 && low)
-    atomicOr((unsigned long long*)&meta->lowbits[L.level], (unsigned long long)low);
+  if (blockIdx.x == 0) cells_zero_padding(L, P);
+  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
+    cells_encode_tile(f, G, L, ny, nx, E_f, bl, P, tile, low, s_q, s_s);
+  cells_lowbits_flush(meta, L.level, low);
 }
 
 static int nsm() {
@@ -349,123 +376,135 @@ __device__ __forceinline__ float out_f32(int64_t X, int E_f) {
   return __double2float_rn(d);
 }
 
+typedef uint32_t CellSW[7][32];
+
+// recomposition of one tile of 1024 cells from the coarse grid and the planes
+template <bool FINAL>
+__device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict__ P,
+                                                     const LevelDesc& L, const CellGeom& G,
+                                                     int E_f, int bl, int k,
+                                                     const int64_t* __restrict__ coarse,
+                                                     void* __restrict__ dst, uint32_t tile,
+                                                     CellQ& s_q, CellSW& s_sw) {
+  const uint32_t i = threadIdx.x, per_row = G.XW / 4;
+  const uint32_t W = L.W;
+  const uint32_t gc1 = L.gc[1], gc2 = L.gc[2];
+  uint32_t cz, cy0, x0;
+  tile_origin(G, tile, cz, cy0, x0);
+  if (i < 224) {  // phase words: planes -> q_hat per cell
+    const int t = i / 32 + 1;
+    const uint32_t rw = i % 32, r = rw / G.NW, w = rw % G.NW, cy = cy0 + r;
+    if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
+      const uint32_t word = (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
+      uint32_t a[32];
+#pragma unroll
+      for (int p = 0; p < 32; p++) a[31 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
+      if (k) transpose32(a);
+#pragma unroll
+      for (int b = 0; b < 32; b++) s_q[t - 1][rw][b] = a[b];
+      s_sw[t - 1][rw] = k ? __ldcs(P + word) : 0u;
+    }
+  }
+  __syncthreads();
+  {  // phase cells
+    const uint32_t r = i / per_row, xl = 4 * (i % per_row), cy = cy0 + r, cx = x0 + xl;
+    if (cy < G.c[1]) {
+      const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
+      // coarse corners: rows (cz | cz+1 clamped) x (cy | cy+1 clamped), x = cx .. cx+4 clamped
+      const uint32_t cz1 = 2 * cz + 2 < G.g[0] ? cz + 1 : cz, cy1 = 2 * cy + 2 < G.g[1] ? cy + 1 : cy;
+      const uint32_t xe = 2 * cx + 8 < G.g[2] ? cx + 4 : cx + 3;
+      int64_t C[2][2][5];
+      const uint32_t zz[2] = {cz, cz1}, yy[2] = {cy, cy1};
+#pragma unroll
+      for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+          const int64_t* row = coarse + ((size_t)zz[a] * gc1 + yy[b]) * gc2;
+          // cx is a multiple of 4 and gc2 of 32: two aligned 16-byte loads
+          const longlong2 p0 = __ldg(reinterpret_cast<const longlong2*>(row + cx));
+          const longlong2 p1 = __ldg(reinterpret_cast<const longlong2*>(row + cx) + 1);
+          C[a][b][0] = p0.x;
+          C[a][b][1] = p0.y;
+          C[a][b][2] = p1.x;
+          C[a][b][3] = p1.y;
+          C[a][b][4] = __ldg(row + xe);
+        }
+      const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
+      // one output row (2cz+oz, 2cy+oy) at a time: its even-x nodes are type
+      // te = 2 oy + 4 oz (te = 0: the coarse node itself), its odd-x nodes te + 1
+#pragma unroll
+      for (int oz = 0; oz < 2; oz++)
+#pragma unroll
+        for (int oy = 0; oy < 2; oy++) {
+          if ((oz && !hz) || (oy && !hy)) continue;
+          const int te = 2 * oy + 4 * oz;
+          int64_t V[8];
+#pragma unroll
+          for (int kk = 0; kk < 4; kk++) {
+#pragma unroll
+            for (int par = 0; par < 2; par++) {
+              const int t = te + par;
+              int64_t X;
+              if (t == 0) {
+                X = C[0][0][kk];
+              } else {
+                // corner sum of type t: the corners along its odd axes
+                int64_t S = 0;
+#pragma unroll
+                for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+                  for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                    for (int dx = 0; dx < 2; dx++) {
+                      if ((dz && !(t & 4)) || (dy && !(t & 2)) || (dx && !(t & 1))) continue;
+                      S += C[dz][dy][kk + dx];
+                    }
+                const uint32_t qh = s_q[t - 1][rw][b0 + kk];
+                const bool neg = (s_sw[t - 1][rw] >> (b0 + kk)) & 1u;
+                uint64_t mag;
+                if (bl == 0) mag = 0;
+                else if (bl <= 32) mag = qh >> (32 - bl);
+                else mag = (uint64_t)qh << (bl - 32);
+                const int64_t c8 = neg ? -(int64_t)mag : (int64_t)mag;
+                const int nodd = __popc(t);
+                X = (c8 * ((int64_t)1 << nodd) + 8 * S) >> (3 + nodd);
+              }
+              V[2 * kk + par] = X;
+            }
+          }
+          const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
+          if (FINAL) {
+            float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base);
+            d4[0] = make_float4(out_f32(V[0], E_f), out_f32(V[1], E_f), out_f32(V[2], E_f),
+                                out_f32(V[3], E_f));
+            d4[1] = make_float4(out_f32(V[4], E_f), out_f32(V[5], E_f), out_f32(V[6], E_f),
+                                out_f32(V[7], E_f));
+          } else {
+            longlong2* d2 = reinterpret_cast<longlong2*>(reinterpret_cast<int64_t*>(dst) + base);
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++) d2[kk] = make_longlong2(V[2 * kk], V[2 * kk + 1]);
+          }
+        }
+    }
+  }
+  __syncthreads();
+}
+
 template <bool FINAL>
 __global__ void __launch_bounds__(256, 3) k_cells_recompose(const uint32_t* __restrict__ planes,
                                                          const FieldMeta* __restrict__ meta,
                                                          const LevelDesc* __restrict__ Lp,
                                                          const int64_t* __restrict__ coarse,
                                                          void* __restrict__ dst) {
-  __shared__ uint32_t s_q[7][32][33];
-  __shared__ uint32_t s_sw[7][32];
+  __shared__ CellQ s_q;
+  __shared__ CellSW s_sw;
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   const CellGeom G = cell_geom(L);
   const int E_f = meta->E_f, bl = meta->bl[L.level], k = 4 * meta->cur[L.level];
-  const uint32_t i = threadIdx.x, per_row = G.XW / 4;
   const uint32_t* P = planes + L.plane_off / 4;
-  const uint32_t W = L.W;
-  const uint32_t gc1 = L.gc[1], gc2 = L.gc[2];
-  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x) {
-    uint32_t cz, cy0, x0;
-    tile_origin(G, tile, cz, cy0, x0);
-    if (i < 224) {  // phase words: planes -> q_hat per cell
-      const int t = i / 32 + 1;
-      const uint32_t rw = i % 32, r = rw / G.NW, w = rw % G.NW, cy = cy0 + r;
-      if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
-        const uint32_t word = (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
-        uint32_t a[32];
-#pragma unroll
-        for (int p = 0; p < 32; p++) a[31 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
-        if (k) transpose32(a);
-#pragma unroll
-        for (int b = 0; b < 32; b++) s_q[t - 1][rw][b] = a[b];
-        s_sw[t - 1][rw] = k ? __ldcs(P + word) : 0u;
-      }
-    }
-    __syncthreads();
-    {  // phase cells
-      const uint32_t r = i / per_row, xl = 4 * (i % per_row), cy = cy0 + r, cx = x0 + xl;
-      if (cy < G.c[1]) {
-        const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
-        // coarse corners: rows (cz | cz+1 clamped) x (cy | cy+1 clamped), x = cx .. cx+4 clamped
-        const uint32_t cz1 = 2 * cz + 2 < G.g[0] ? cz + 1 : cz, cy1 = 2 * cy + 2 < G.g[1] ? cy + 1 : cy;
-        const uint32_t xe = 2 * cx + 8 < G.g[2] ? cx + 4 : cx + 3;
-        int64_t C[2][2][5];
-        const uint32_t zz[2] = {cz, cz1}, yy[2] = {cy, cy1};
-#pragma unroll
-        for (int a = 0; a < 2; a++)
-#pragma unroll
-          for (int b = 0; b < 2; b++) {
-            const int64_t* row = coarse + ((size_t)zz[a] * gc1 + yy[b]) * gc2;
-            // cx is a multiple of 4 and gc2 of 32: two aligned 16-byte loads
-            const longlong2 p0 = __ldg(reinterpret_cast<const longlong2*>(row + cx));
-            const longlong2 p1 = __ldg(reinterpret_cast<const longlong2*>(row + cx) + 1);
-            C[a][b][0] = p0.x;
-            C[a][b][1] = p0.y;
-            C[a][b][2] = p1.x;
-            C[a][b][3] = p1.y;
-            C[a][b][4] = __ldg(row + xe);
-          }
-        const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
-        // one output row (2cz+oz, 2cy+oy) at a time: its even-x nodes are type
-        // te = 2 oy + 4 oz (te = 0: the coarse node itself), its odd-x nodes te + 1
-#pragma unroll
-        for (int oz = 0; oz < 2; oz++)
-#pragma unroll
-          for (int oy = 0; oy < 2; oy++) {
-            if ((oz && !hz) || (oy && !hy)) continue;
-            const int te = 2 * oy + 4 * oz;
-            int64_t V[8];
-#pragma unroll
-            for (int kk = 0; kk < 4; kk++) {
-#pragma unroll
-              for (int par = 0; par < 2; par++) {
-                const int t = te + par;
-                int64_t X;
-                if (t == 0) {
-                  X = C[0][0][kk];
-                } else {
-                  // corner sum of type t: the corners along its odd axes
-                  int64_t S = 0;
-#pragma unroll
-                  for (int dz = 0; dz < 2; dz++)
-#pragma unroll
-                    for (int dy = 0; dy < 2; dy++)
-#pragma unroll
-                      for (int dx = 0; dx < 2; dx++) {
-                        if ((dz && !(t & 4)) || (dy && !(t & 2)) || (dx && !(t & 1))) continue;
-                        S += C[dz][dy][kk + dx];
-                      }
-                  const uint32_t qh = s_q[t - 1][rw][b0 + kk];
-                  const bool neg = (s_sw[t - 1][rw] >> (b0 + kk)) & 1u;
-                  uint64_t mag;
-                  if (bl == 0) mag = 0;
-                  else if (bl <= 32) mag = qh >> (32 - bl);
-                  else mag = (uint64_t)qh << (bl - 32);
-                  const int64_t c8 = neg ? -(int64_t)mag : (int64_t)mag;
-                  const int nodd = __popc(t);
-                  X = (c8 * ((int64_t)1 << nodd) + 8 * S) >> (3 + nodd);
-                }
-                V[2 * kk + par] = X;
-              }
-            }
-            const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
-            if (FINAL) {
-              float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base);
-              d4[0] = make_float4(out_f32(V[0], E_f), out_f32(V[1], E_f), out_f32(V[2], E_f),
-                                  out_f32(V[3], E_f));
-              d4[1] = make_float4(out_f32(V[4], E_f), out_f32(V[5], E_f), out_f32(V[6], E_f),
-                                  out_f32(V[7], E_f));
-            } else {
-              longlong2* d2 = reinterpret_cast<longlong2*>(reinterpret_cast<int64_t*>(dst) + base);
-#pragma unroll
-              for (int kk = 0; kk < 4; kk++) d2[kk] = make_longlong2(V[2 * kk], V[2 * kk + 1]);
-            }
-          }
-      }
-    }
-    __syncthreads();
-  }
+  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
+    cells_recompose_tile<FINAL>(P, L, G, E_f, bl, k, coarse, dst, tile, s_q, s_sw);
 }
 
 void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,
@@ -479,6 +518,98 @@ void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const
     hp::note_launch(), k_cells_recompose<true><<<blocks, 256, 0, s>>>(planes, meta, Ld, coarse, dst);
   else
     hp::note_launch(), k_cells_recompose<false><<<blocks, 256, 0, s>>>(planes, meta, Ld, coarse, dst);
+}
+
+// ------------------------------------------------------------------ batched
+uint32_t cell_tiles(const LevelDesc& L) { return cell_geom(L).ntiles; }
+
+// unit = one tile of 1024 cells of one (job, level) entry
+__global__ void __launch_bounds__(256, 2) kb_cells_levelmax(const BatchJob* __restrict__ jobs,
+                                                         const LevelRef* __restrict__ refs,
+                                                         const uint32_t* __restrict__ unit0,
+                                                         uint32_t nrefs, uint32_t total) {
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const CellGeom G = cell_geom(L);
+    uint64_t mx = 0;
+    uint32_t fl = 0;
+    cells_levelmax_tile(reinterpret_cast<const float*>(J.f), G, J.dims[1], J.dims[2], L.hlog,
+                        meta->E_f, u - unit0[e], mx, fl);
+    cells_levelmax_flush(meta, L.level, mx, fl);
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) kb_cells_encode(const BatchJob* __restrict__ jobs,
+                                                       const LevelRef* __restrict__ refs,
+                                                       const uint32_t* __restrict__ unit0,
+                                                       uint32_t nrefs, uint32_t total) {
+  __shared__ CellQ s_q;
+  __shared__ CellS s_s;
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const CellGeom G = cell_geom(L);
+    uint32_t* P = reinterpret_cast<uint32_t*>(J.planes) + L.plane_off / 4;
+    const uint32_t tile = u - unit0[e];
+    if (tile == 0) cells_zero_padding(L, P);
+    uint64_t low = 0;
+    cells_encode_tile(reinterpret_cast<const float*>(J.f), G, L, J.dims[1], J.dims[2], meta->E_f,
+                      meta->bl[L.level], P, tile, low, s_q, s_s);
+    cells_lowbits_flush(meta, L.level, low);
+  }
+}
+
+__global__ void __launch_bounds__(256, 3) kb_cells_recompose(const BatchJob* __restrict__ jobs,
+                                                          const LevelRef* __restrict__ refs,
+                                                          const uint32_t* __restrict__ unit0,
+                                                          uint32_t nrefs, uint32_t total) {
+  __shared__ CellQ s_q;
+  __shared__ CellSW s_sw;
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    const FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const CellGeom G = cell_geom(L);
+    const uint32_t* P = reinterpret_cast<const uint32_t*>(J.planes) + L.plane_off / 4;
+    const int E_f = meta->E_f, bl = meta->bl[L.level], k = 4 * meta->cur[L.level];
+    if (R.final)
+      cells_recompose_tile<true>(P, L, G, E_f, bl, k, R.coarse, J.out, u - unit0[e], s_q, s_sw);
+    else
+      cells_recompose_tile<false>(P, L, G, E_f, bl, k, R.coarse, R.dst, u - unit0[e], s_q, s_sw);
+  }
+}
+
+void launch_b_cells_levelmax(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                             uint32_t nrefs, uint32_t total, uint32_t grid, cstream s) {
+  if (!total) return;
+  if (grid > total) grid = total;
+  hp::note_launch(), kb_cells_levelmax<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+}
+
+void launch_b_cells_encode(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                           uint32_t nrefs, uint32_t total, uint32_t grid, cstream s) {
+  if (!total) return;
+  if (grid > total) grid = total;
+  hp::note_launch(), kb_cells_encode<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+}
+
+void launch_b_cells_recompose(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                              uint32_t nrefs, uint32_t total, uint32_t grid, cstream s) {
+  if (!total) return;
+  if (grid > total) grid = total;
+  hp::note_launch(), kb_cells_recompose<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
 }
 
 }  // namespace hp

@@ -62,6 +62,28 @@ __device__ __forceinline__ int find_level(const uint32_t* tile0, int l, uint32_t
 }
 
 // ------------------------------------------------------------ pass: level max
+// one warp: max |C8| over the 1024-node tile at `base` of level L
+template <typename T>
+__device__ __forceinline__ void levelmax_tile(const FieldView<T>& v, const LevelDesc& L,
+                                              uint32_t base, FieldMeta* meta) {
+  const int lane = threadIdx.x & 31;
+  uint64_t mx = 0;
+  uint32_t fl = 0;
+  for (int r = 0; r < 32; r++) {
+    uint32_t j = base + r * 32 + lane;
+    if (j < L.n) {
+      uint64_t m = umag(level_c8(v, L, j, fl));
+      mx = m > mx ? m : mx;
+    }
+  }
+  mx = warp_max_u64(mx);
+  unsigned anyfl = __any_sync(HP_FULL, fl != 0);
+  if (lane == 0) {
+    if (mx) atomicMax((unsigned long long*)&meta->m8[L.level], (unsigned long long)mx);
+    if (anyfl) atomicOr(&meta->floored, 1u);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDesc* __restrict__ levels,
                                                   int nlev, uint32_t total_tiles,
@@ -72,29 +94,13 @@ __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDes
   __syncthreads();
   if (meta->status) return;
   v.E_f = meta->E_f;
-  const int lane = threadIdx.x & 31;
   const uint32_t wpb = blockDim.x >> 5;
   int l = 0;
   for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < total_tiles;
        tile += gridDim.x * wpb) {
     l = find_level(s_tile0, l, tile);
     const LevelDesc& L = levels[l];
-    const uint32_t base = perm[L.tile0 + (tile - L.gtile0)] * HP_TILE;
-    uint64_t mx = 0;
-    uint32_t fl = 0;
-    for (int r = 0; r < 32; r++) {
-      uint32_t j = base + r * 32 + lane;
-      if (j < L.n) {
-        uint64_t m = umag(level_c8(v, L, j, fl));
-        mx = m > mx ? m : mx;
-      }
-    }
-    mx = warp_max_u64(mx);
-    unsigned anyfl = __any_sync(HP_FULL, fl != 0);
-    if (lane == 0) {
-      if (mx) atomicMax((unsigned long long*)&meta->m8[l], (unsigned long long)mx);
-      if (anyfl) atomicOr(&meta->floored, 1u);
-    }
+    levelmax_tile(v, L, perm[L.tile0 + (tile - L.gtile0)] * HP_TILE, meta);
   }
 }
 
@@ -122,11 +128,12 @@ void launch_levelmax(const void* f, int dtype, const uint64_t dims[3], const Lev
 }
 
 // bl_l = bit length of max|C8|; input exactness from the floor flags
-__global__ void k_bitlen(FieldMeta* meta) {
-  int l = threadIdx.x;
+__device__ __forceinline__ void bitlen_level(FieldMeta* meta, int l) {
   if (l < meta->nlev) meta->bl[l] = meta->m8[l] ? bitlen64(meta->m8[l]) : 0;
   if (l == 0) meta->input_exact = meta->floored ? 0 : 1;
 }
+
+__global__ void k_bitlen(FieldMeta* meta) { bitlen_level(meta, threadIdx.x); }
 
 void launch_bitlen(FieldMeta* meta, cstream s) { hp::note_launch(), k_bitlen<<<1, HP_MAX_LEVELS, 0, s>>>(meta); }
 
@@ -155,6 +162,51 @@ __device__ __forceinline__ void emit_word(const uint32_t* row_hi, const uint32_t
 }
 
 // ------------------------------------------------ pass: quantize + Algorithm 1
+// one warp: the 1024-node tile at `base` of level L, hi/lo its shared rows
+template <typename T, int B>
+__device__ __forceinline__ void encode_tile(const FieldView<T>& v, const LevelDesc& L,
+                                            uint32_t base, FieldMeta* meta,
+                                            uint32_t* __restrict__ planes, uint32_t* hi,
+                                            uint32_t* lo) {
+  const int lane = threadIdx.x & 31;
+  const int bl = meta->bl[L.level];
+  uint64_t low = 0;
+  uint32_t my_sign = 0, fl = 0;
+  // phase A: lane = node
+  for (int r = 0; r < 32; r++) {
+    uint32_t j = base + r * 32 + lane;
+    uint64_t q = 0;
+    bool neg = false;
+    if (j < L.n) {
+      int64_t c8 = level_c8(v, L, j, fl);
+      uint64_t m = umag(c8);
+      neg = c8 < 0;
+      if (bl == 0) q = 0;
+      else if (B >= bl) q = m << (B - bl);
+      else {
+        q = m >> (bl - B);
+        low |= m & ((1ull << (bl - B)) - 1ull);
+      }
+    }
+    uint32_t sw = __ballot_sync(HP_FULL, neg);
+    if (lane == r) my_sign = sw;
+    if (B == 64) {
+      hi[r * 33 + lane] = (uint32_t)(q >> 32);
+      lo[r * 33 + lane] = (uint32_t)q;
+    } else {
+      hi[r * 33 + lane] = (uint32_t)q;
+    }
+  }
+  low = warp_or_u64(low);
+  if (lane == 0 && low)
+    atomicOr((unsigned long long*)&meta->lowbits[L.level], (unsigned long long)low);
+  __syncwarp();
+  // phase B: lane = word
+  const uint32_t wi = base / 32 + lane;
+  if (wi < L.W) emit_word<B>(hi + lane * 33, lo + lane * 33, my_sign, planes + L.plane_off / 4, L.W, wi);
+  __syncwarp();
+}
+
 template <typename T, int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_encode(FieldView<T> v, const LevelDesc* __restrict__ levels, int nlev, uint32_t total_tiles,
@@ -168,51 +220,14 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
   __syncthreads();
   if (meta->status) return;
   v.E_f = meta->E_f;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5;
   uint32_t* hi = s_hi[w];
   uint32_t* lo = s_lo[B == 64 ? w : 0];
   int l = 0;
   for (uint32_t tile = blockIdx.x * WPB + w; tile < total_tiles; tile += gridDim.x * WPB) {
     l = find_level(s_tile0, l, tile);
     const LevelDesc& L = levels[l];
-    const uint32_t base = perm[L.tile0 + (tile - L.gtile0)] * HP_TILE;
-    const int bl = meta->bl[l];
-    uint64_t low = 0;
-    uint32_t my_sign = 0, fl = 0;
-    // phase A: lane = node
-    for (int r = 0; r < 32; r++) {
-      uint32_t j = base + r * 32 + lane;
-      uint64_t q = 0;
-      bool neg = false;
-      if (j < L.n) {
-        int64_t c8 = level_c8(v, L, j, fl);
-        uint64_t m = umag(c8);
-        neg = c8 < 0;
-        if (bl == 0) q = 0;
-        else if (B >= bl) q = m << (B - bl);
-        else {
-          q = m >> (bl - B);
-          low |= m & ((1ull << (bl - B)) - 1ull);
-        }
-      }
-      uint32_t sw = __ballot_sync(HP_FULL, neg);
-      if (lane == r) my_sign = sw;
-      if (B == 64) {
-        hi[r * 33 + lane] = (uint32_t)(q >> 32);
-        lo[r * 33 + lane] = (uint32_t)q;
-      } else {
-        hi[r * 33 + lane] = (uint32_t)q;
-      }
-    }
-    low = warp_or_u64(low);
-    if (lane == 0 && low) atomicOr((unsigned long long*)&meta->lowbits[l], (unsigned long long)low);
-    __syncwarp();
-    // phase B: lane = word
-    const uint32_t wi = base / 32 + lane;
-    if (wi < L.W)
-      emit_word<B>(hi + lane * 33, lo + lane * 33, my_sign,
-                   planes + L.plane_off / 4, L.W, wi);
-    __syncwarp();
+    encode_tile<T, B>(v, L, perm[L.tile0 + (tile - L.gtile0)] * HP_TILE, meta, planes, hi, lo);
   }
 }
 
@@ -231,6 +246,82 @@ void launch_encode(const void* f, int dtype, const uint64_t dims[3], const Level
     FieldView<double> v{(const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
     hp::note_launch(), k_encode<double, 64><<<blocks, 128, 0, s>>>(v, levels, nlev, total_tiles, perm, meta, planes);
   }
+}
+
+// ------------------------------------------------------------------ batched
+// warp unit = one generic tile of one job (the job's generic tiles in its
+// level-then-perm order)
+__device__ __forceinline__ int generic_level(const LevelDesc* __restrict__ levels, int nlev,
+                                             uint32_t tile) {
+  int l = 0;
+  while (l + 1 < nlev && levels[l + 1].gtile0 <= tile) l++;
+  return l;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_levelmax(const BatchJob* __restrict__ jobs,
+                                                   const uint32_t* __restrict__ unit0,
+                                                   uint32_t njobs, uint32_t total) {
+  const uint32_t wpb = blockDim.x >> 5;
+  for (uint32_t u = blockIdx.x * wpb + (threadIdx.x >> 5); u < total; u += gridDim.x * wpb) {
+    const uint32_t j = unit_owner(unit0, njobs, u);
+    const BatchJob& J = jobs[j];
+    FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const uint32_t tile = u - unit0[j];
+    const LevelDesc& L = J.levels[generic_level(J.levels, J.nlev, tile)];
+    FieldView<T> v{reinterpret_cast<const T*>(J.f), J.dims[1], J.dims[2], meta->E_f};
+    levelmax_tile(v, L, J.perm[L.tile0 + (tile - L.gtile0)] * HP_TILE, meta);
+  }
+}
+
+void launch_b_levelmax(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                       int dtype, uint32_t grid, cstream s) {
+  if (!total) return;
+  const uint32_t need = (total + 7) / 8;
+  if (grid > need) grid = need;
+  if (dtype == 0) hp::note_launch(), kb_levelmax<float><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total);
+  else hp::note_launch(), kb_levelmax<double><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total);
+}
+
+__global__ void kb_bitlen(const BatchJob* __restrict__ jobs) {
+  bitlen_level(jobs[blockIdx.x].meta, threadIdx.x);
+}
+
+void launch_b_bitlen(const BatchJob* jobs, uint32_t njobs, cstream s) {
+  if (njobs) hp::note_launch(), kb_bitlen<<<njobs, HP_MAX_LEVELS, 0, s>>>(jobs);
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(B == 32 ? 256 : 128)
+    kb_encode(const BatchJob* __restrict__ jobs, const uint32_t* __restrict__ unit0, uint32_t njobs,
+              uint32_t total) {
+  constexpr int WPB = B == 32 ? 8 : 4;
+  __shared__ uint32_t s_hi[WPB][32 * 33];
+  __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
+  const int w = threadIdx.x >> 5;
+  for (uint32_t u = blockIdx.x * WPB + w; u < total; u += gridDim.x * WPB) {
+    const uint32_t j = unit_owner(unit0, njobs, u);
+    const BatchJob& J = jobs[j];
+    FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const uint32_t tile = u - unit0[j];
+    const LevelDesc& L = J.levels[generic_level(J.levels, J.nlev, tile)];
+    FieldView<T> v{reinterpret_cast<const T*>(J.f), J.dims[1], J.dims[2], meta->E_f};
+    encode_tile<T, B>(v, L, J.perm[L.tile0 + (tile - L.gtile0)] * HP_TILE, meta,
+                      reinterpret_cast<uint32_t*>(J.planes), s_hi[w], s_lo[B == 64 ? w : 0]);
+  }
+}
+
+void launch_b_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                     int dtype, uint32_t grid, cstream s) {
+  if (!total) return;
+  const uint32_t wpb = dtype == 0 ? 8 : 4, need = (total + wpb - 1) / wpb;
+  if (grid > need) grid = need;
+  if (dtype == 0)
+    hp::note_launch(), kb_encode<float, 32><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total);
+  else
+    hp::note_launch(), kb_encode<double, 64><<<grid, 128, 0, s>>>(jobs, unit0, njobs, total);
 }
 
 // ------------------------------------------- stand-alone Algorithm 1 and inverse

@@ -168,4 +168,17 @@ __device__ __forceinline__ uint64_t abs_key(double v) {
   return (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 
+// Batched launches: the job (or level entry) owning work unit u is the last
+// j with unit0[j] <= u (unit0 ascending; jobs without units repeat a value)
+__device__ __forceinline__ uint32_t unit_owner(const uint32_t* __restrict__ unit0, uint32_t n,
+                                               uint32_t u) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(unit0 + mid) <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 }  // namespace hp

@@ -56,7 +56,7 @@ struct GroupMeta {
   int32_t pad;
 };
 
-struct FieldMeta {
+struct alignas(16) FieldMeta {
   int32_t status;  // HPMDR_OK or an error raised on the device
   int32_t dtype, B, nlev, ngroups, E_f, input_exact, has_range;
   uint64_t key_absmax, key_min, key_max;  // order-preserving keys of max|f|, min, max
@@ -81,7 +81,7 @@ struct FieldMeta {
 };
 
 // retrieval info written by the selection kernel
-struct RetrieveDev {
+struct alignas(16) RetrieveDev {
   int32_t status, nsel;
   uint64_t E_hi, E_lo;
   double E_abs, tau_abs;
@@ -93,6 +93,50 @@ struct RetrieveDev {
   uint32_t new_pref[HP_SEQ_MAX + 1];  // prefix of their chunk counts
 };
 
+// --------------------------------------------------------- batched launches
+// One field of a batched launch: every pointer the stage kernels of one field
+// need.  A batched kernel runs over the work units of all its jobs (tiles,
+// chunks, groups ... of every field); job j owns units [unit0[j], unit0[j+1]).
+struct BatchJob {
+  const void* f;  // field (device, 16-byte aligned)
+  uint64_t N;
+  uint32_t dims[3];
+  uint32_t nlev, ngt, generic_tiles, total_chunks, pad0;
+  FieldMeta* meta;
+  const FieldMeta* meta0;  // the plan's initial metadata
+  uint8_t* planes;
+  uint8_t* slots;
+  const LevelDesc* levels;
+  const uint32_t* perm;
+  const uint32_t* chunk_group;
+  // refactor scratch: group histograms (256 per group), group RLE sizes,
+  // chunk RLE costs, chunk Huffman words, chunk output offsets, code lengths
+  uint32_t* hist;
+  unsigned long long* gcost;
+  uint32_t* ccost;
+  uint32_t* cwords;
+  uint32_t* cout;
+  uint8_t* lens;
+  // retrieval
+  RetrieveDev* rd;
+  int64_t* xroot;
+  int64_t* xa;
+  int64_t* xb;
+  void* out;
+  double tau;        // relative L-infinity bound
+  int32_t small_end;  // last level recomposed by the one-CTA small-level kernel
+  int32_t pad1;
+};
+
+// (job, level) entry of a level-granular batched launch
+struct LevelRef {
+  uint32_t job, level;
+  const int64_t* coarse;  // recomposition: the coarse grid G_2h
+  int64_t* dst;           // recomposition: the level grid (unused when final)
+  int32_t final;          // recomposition: the level writes the job's output
+  int32_t pad;
+};
+
 // launchers implemented in the .cu files --------------------------------------
 typedef struct CUstream_st* cstream;
 
@@ -100,6 +144,8 @@ namespace hp {
 
 // counts every kernel launch made by the library (runtime.cu)
 void note_launch();
+// takes back launches counted while a CUDA graph was being captured
+void unnote_launches(uint64_t k);
 // raises a kernel's dynamic shared memory limit once per device (thread-safe)
 void set_smem_once(const void* func, int bytes);
 
@@ -173,6 +219,53 @@ void launch_cells_encode(const float* f, const uint64_t dims[3], const LevelDesc
 void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,
                             const LevelDesc& Lh, const int64_t* coarse, void* dst, int final,
                             cstream s);
+
+// batched stage launchers (one launch covers every job).  unit0 tables live
+// in device memory; `grid` is the persistent grid size.
+void launch_b_init(const BatchJob* jobs, uint32_t njobs, cstream s);
+void launch_b_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                    uint32_t seg, int dtype, uint32_t grid, cstream s);
+void launch_b_finalize(const BatchJob* jobs, uint32_t njobs, cstream s);
+void launch_b_levelmax(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                       int dtype, uint32_t grid, cstream s);
+void launch_b_bitlen(const BatchJob* jobs, uint32_t njobs, cstream s);
+void launch_b_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                     int dtype, uint32_t grid, cstream s);
+void launch_b_cells_levelmax(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                             uint32_t nrefs, uint32_t total, uint32_t grid, cstream s);
+void launch_b_cells_encode(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                           uint32_t nrefs, uint32_t total, uint32_t grid, cstream s);
+void launch_b_cells_recompose(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                              uint32_t nrefs, uint32_t total, uint32_t grid, cstream s);
+uint32_t cell_tiles(const LevelDesc& L);
+void launch_b_chunk_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                          uint32_t total, uint32_t grid, cstream s);
+void launch_b_decide(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                     uint64_t Ts, uint32_t cr_num, uint32_t cr_den, uint32_t grid, cstream s);
+void launch_b_huff_bits(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                        uint32_t total, uint32_t grid, cstream s);
+void launch_b_group_offsets(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                            uint32_t total, uint32_t grid, cstream s);
+void launch_b_huff_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                          uint32_t total, uint32_t grid, cstream s);
+void launch_b_rle_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                         uint32_t total, uint32_t grid, cstream s);
+void launch_b_headers(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                      uint32_t grid, cstream s);
+void launch_b_sequence(const BatchJob* jobs, uint32_t njobs, cstream s);
+void launch_b_select(const BatchJob* jobs, uint32_t njobs, cstream s);
+// unit0_out[j] = sum of rd->items of jobs before j (njobs + 1 entries)
+void launch_b_items_prefix(const BatchJob* jobs, uint32_t njobs, uint32_t* unit0_out, cstream s);
+void launch_b_decode(const BatchJob* jobs, const uint32_t* unit0_dev, uint32_t njobs,
+                     uint32_t grid, cstream s);
+void launch_b_recompose_small(const BatchJob* jobs, uint32_t njobs, int dtype, cstream s);
+void launch_b_recompose_copy(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                             uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s);
+void launch_b_recompose_level(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                              uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s);
+// contiguous copies of every job's FieldMeta and RetrieveDev (for one download)
+void launch_b_gather(const BatchJob* jobs, uint32_t njobs, FieldMeta* metas, RetrieveDev* rds,
+                     int32_t* statuses, cstream s);
 
 // qoi.cu
 void launch_vmag_range(const float* vx, const float* vy, const float* vz, uint64_t N,

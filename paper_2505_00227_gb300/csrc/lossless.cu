@@ -62,17 +62,18 @@ __device__ __forceinline__ void load_chunk(const uint8_t* __restrict__ src, uint
 // only a segment's last run can reach 129 bytes, so its length comes from the
 // first run start of the following segments (a block-wide suffix minimum).
 // Zero bytes are counted with a word trick and added to the histogram once.
-__global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__ planes,
+__device__ __forceinline__ void chunk_stats_unit(const uint8_t* __restrict__ planes,
                                                      const FieldMeta* __restrict__ meta,
                                                      const uint32_t* __restrict__ chunk_group,
                                                      uint32_t* __restrict__ group_hist,
                                                      unsigned long long* __restrict__ group_cost,
-                                                     uint32_t* __restrict__ chunk_cost) {
+                                                     uint32_t* __restrict__ chunk_cost,
+    uint32_t c_unit) {
   __shared__ uint32_t hist[8][256];
   __shared__ uint32_t s_first[256], s_wmin[8];
   __shared__ uint8_t s_last[256];
   __shared__ uint32_t red[8];
-  const uint32_t c = blockIdx.x, t = threadIdx.x;
+  const uint32_t c = c_unit, t = threadIdx.x;
   const int lane = t & 31, w = t >> 5;
   if (meta->status) return;
   ChunkRef r = chunk_ref(meta, chunk_group, c);
@@ -162,6 +163,15 @@ __global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__
   }
 }
 
+__global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__ planes,
+                                                     const FieldMeta* __restrict__ meta,
+                                                     const uint32_t* __restrict__ chunk_group,
+                                                     uint32_t* __restrict__ group_hist,
+                                                     unsigned long long* __restrict__ group_cost,
+                                                     uint32_t* __restrict__ chunk_cost) {
+  chunk_stats_unit(planes, meta, chunk_group, group_hist, group_cost, chunk_cost, blockIdx.x);
+}
+
 void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* group_hist,
                         unsigned long long* group_cost, uint32_t* chunk_cost, cstream s) {
   if (cm.total_chunks == 0) return;
@@ -229,16 +239,17 @@ __device__ void huffman_lengths_block(const uint64_t* f_in, uint8_t* len_out, ui
   }
 }
 
-__global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t* __restrict__ group_hist,
+__device__ __forceinline__ void decide_unit(FieldMeta* meta, const uint32_t* __restrict__ group_hist,
                                                 const unsigned long long* __restrict__ group_cost,
                                                 uint8_t* __restrict__ lens, uint64_t Ts,
-                                                uint32_t cr_num, uint32_t cr_den, int force) {
+                                                uint32_t cr_num, uint32_t cr_den, int force,
+    uint32_t g_unit) {
   __shared__ uint64_t hist[256], f[256], w[512];
   __shared__ int sorted[256], parent[512], depth[512], flag;
   __shared__ uint8_t len[256];
   __shared__ uint64_t red[8];
   if (meta->status) return;
-  const uint32_t gi = blockIdx.x;
+  const uint32_t gi = g_unit;
   const int ng = meta->ngroups;
   GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
   const int t = threadIdx.x;
@@ -274,6 +285,13 @@ __global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t*
   }
 }
 
+__global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t* __restrict__ group_hist,
+                                                const unsigned long long* __restrict__ group_cost,
+                                                uint8_t* __restrict__ lens, uint64_t Ts,
+                                                uint32_t cr_num, uint32_t cr_den, int force) {
+  decide_unit(meta, group_hist, group_cost, lens, Ts, cr_num, cr_den, force, blockIdx.x);
+}
+
 void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* group_hist,
                    const unsigned long long* group_cost, uint8_t* lens, uint64_t Ts,
                    uint32_t cr_num, uint32_t cr_den, int force, cstream s) {
@@ -307,15 +325,16 @@ __device__ void canonical_codes_block(const uint8_t* len, uint32_t* code, uint32
 }
 
 // --------------------------------------------------- Huffman: bits per chunk
-__global__ void __launch_bounds__(256) k_huff_bits(const uint8_t* __restrict__ planes,
+__device__ __forceinline__ void huff_bits_unit(const uint8_t* __restrict__ planes,
                                                    const FieldMeta* __restrict__ meta,
                                                    const uint32_t* __restrict__ chunk_group,
                                                    const uint8_t* __restrict__ lens,
-                                                   uint32_t* __restrict__ chunk_words) {
+                                                   uint32_t* __restrict__ chunk_words,
+    uint32_t c_unit) {
   __shared__ uint8_t len[256];
   __shared__ uint32_t red[8];
   if (meta->status) return;
-  ChunkRef r = chunk_ref(meta, chunk_group, blockIdx.x);
+  ChunkRef r = chunk_ref(meta, chunk_group, c_unit);
   if (r.gm->method != 1) return;
   len[threadIdx.x] = lens[(size_t)r.gi * 256 + threadIdx.x];
   __syncthreads();
@@ -337,8 +356,16 @@ __global__ void __launch_bounds__(256) k_huff_bits(const uint8_t* __restrict__ p
   if (threadIdx.x == 0) {
     uint32_t s = 0;
     for (int k = 0; k < 8; k++) s += red[k];
-    chunk_words[blockIdx.x] = (s + 31) / 32;
+    chunk_words[c_unit] = (s + 31) / 32;
   }
+}
+
+__global__ void __launch_bounds__(256) k_huff_bits(const uint8_t* __restrict__ planes,
+                                                   const FieldMeta* __restrict__ meta,
+                                                   const uint32_t* __restrict__ chunk_group,
+                                                   const uint8_t* __restrict__ lens,
+                                                   uint32_t* __restrict__ chunk_words) {
+  huff_bits_unit(planes, meta, chunk_group, lens, chunk_words, blockIdx.x);
 }
 
 void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm, const uint8_t* lens,
@@ -349,13 +376,14 @@ void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
 
 // ------------------------------------ per-group chunk output offsets (scan)
 // Huffman: word offset of each chunk in the payload; RLE: byte offset.
-__global__ void __launch_bounds__(256) k_group_offsets(FieldMeta* meta,
+__device__ __forceinline__ void group_offsets_unit(FieldMeta* meta,
                                                        const uint32_t* __restrict__ chunk_words,
                                                        const uint32_t* __restrict__ chunk_cost,
-                                                       uint32_t* __restrict__ chunk_out) {
+                                                       uint32_t* __restrict__ chunk_out,
+    uint32_t g_unit) {
   __shared__ uint64_t part[256];
   if (meta->status) return;
-  const uint32_t gi = blockIdx.x;
+  const uint32_t gi = g_unit;
   const int ng = meta->ngroups;
   GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
   const int m = gm->method;
@@ -387,24 +415,32 @@ __global__ void __launch_bounds__(256) k_group_offsets(FieldMeta* meta,
   }
 }
 
+__global__ void __launch_bounds__(256) k_group_offsets(FieldMeta* meta,
+                                                       const uint32_t* __restrict__ chunk_words,
+                                                       const uint32_t* __restrict__ chunk_cost,
+                                                       uint32_t* __restrict__ chunk_out) {
+  group_offsets_unit(meta, chunk_words, chunk_cost, chunk_out, blockIdx.x);
+}
+
 void launch_group_offsets(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_words,
                           const uint32_t* chunk_cost, uint32_t* chunk_out, cstream s) {
   hp::note_launch(), k_group_offsets<<<ngroups_total, 256, 0, s>>>(meta, chunk_words, chunk_cost, chunk_out);
 }
 
 // -------------------------------------------------------- Huffman: encode
-__global__ void __launch_bounds__(256) k_huff_encode(const uint8_t* __restrict__ planes,
+__device__ __forceinline__ void huff_encode_unit(const uint8_t* __restrict__ planes,
                                                      const FieldMeta* __restrict__ meta,
                                                      const uint32_t* __restrict__ chunk_group,
                                                      const uint8_t* __restrict__ lens,
                                                      const uint32_t* __restrict__ chunk_out,
-                                                     uint8_t* __restrict__ slots) {
+                                                     uint8_t* __restrict__ slots,
+    uint32_t c_unit) {
   __shared__ uint8_t len[256];
   __shared__ uint32_t code[256], first[17];
   __shared__ uint32_t outw[HP_CHUNK * 16 / 32];  // worst case: 16 bits per byte
   __shared__ uint32_t scan[256];
   if (meta->status) return;
-  ChunkRef r = chunk_ref(meta, chunk_group, blockIdx.x);
+  ChunkRef r = chunk_ref(meta, chunk_group, c_unit);
   if (r.gm->method != 1) return;
   const int t = threadIdx.x;
   len[t] = lens[(size_t)r.gi * 256 + t];
@@ -455,8 +491,17 @@ __global__ void __launch_bounds__(256) k_huff_encode(const uint8_t* __restrict__
   const uint32_t nwords = (nbits + 31) / 32;
   uint32_t* dst = reinterpret_cast<uint32_t*>(slots + r.gm->slot_off +
                                               huff_header_bytes(r.gm->nchunks)) +
-                  chunk_out[blockIdx.x];
+                  chunk_out[c_unit];
   for (uint32_t i = t; i < nwords; i += 256) dst[i] = outw[i];
+}
+
+__global__ void __launch_bounds__(256) k_huff_encode(const uint8_t* __restrict__ planes,
+                                                     const FieldMeta* __restrict__ meta,
+                                                     const uint32_t* __restrict__ chunk_group,
+                                                     const uint8_t* __restrict__ lens,
+                                                     const uint32_t* __restrict__ chunk_out,
+                                                     uint8_t* __restrict__ slots) {
+  huff_encode_unit(planes, meta, chunk_group, lens, chunk_out, slots, blockIdx.x);
 }
 
 void launch_huff_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
@@ -467,15 +512,16 @@ void launch_huff_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap c
 }
 
 // ------------------------------------------------------------ RLE: encode
-__global__ void __launch_bounds__(256) k_rle_encode(const uint8_t* __restrict__ planes,
+__device__ __forceinline__ void rle_encode_unit(const uint8_t* __restrict__ planes,
                                                     const FieldMeta* __restrict__ meta,
                                                     const uint32_t* __restrict__ chunk_group,
                                                     const uint32_t* __restrict__ chunk_out,
-                                                    uint8_t* __restrict__ slots) {
+                                                    uint8_t* __restrict__ slots,
+    uint32_t c_unit) {
   __shared__ __align__(16) uint8_t buf[HP_CHUNK];
   __shared__ uint32_t scan[256];
   if (meta->status) return;
-  ChunkRef r = chunk_ref(meta, chunk_group, blockIdx.x);
+  ChunkRef r = chunk_ref(meta, chunk_group, c_unit);
   if (r.gm->method != 2) return;
   const int t = threadIdx.x;
   load_chunk(planes + r.gm->plane_off + r.start, r.len, buf);
@@ -500,7 +546,7 @@ __global__ void __launch_bounds__(256) k_rle_encode(const uint8_t* __restrict__ 
     }
   }
   __syncthreads();
-  uint8_t* dst = slots + r.gm->slot_off + rle_header_bytes(r.gm->nchunks) + chunk_out[blockIdx.x] +
+  uint8_t* dst = slots + r.gm->slot_off + rle_header_bytes(r.gm->nchunks) + chunk_out[c_unit] +
                  scan[t];
   uint32_t o = 0;
   for (uint32_t i = a; i < b; i++) {
@@ -518,6 +564,14 @@ __global__ void __launch_bounds__(256) k_rle_encode(const uint8_t* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(256) k_rle_encode(const uint8_t* __restrict__ planes,
+                                                    const FieldMeta* __restrict__ meta,
+                                                    const uint32_t* __restrict__ chunk_group,
+                                                    const uint32_t* __restrict__ chunk_out,
+                                                    uint8_t* __restrict__ slots) {
+  rle_encode_unit(planes, meta, chunk_group, chunk_out, slots, blockIdx.x);
+}
+
 void launch_rle_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
                        const uint32_t* chunk_out, uint8_t* slots, cstream s) {
   if (cm.total_chunks == 0) return;
@@ -525,12 +579,13 @@ void launch_rle_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm
 }
 
 // ---------------------------------------------------------- group headers
-__global__ void __launch_bounds__(256) k_headers(const FieldMeta* __restrict__ meta,
+__device__ __forceinline__ void headers_unit(const FieldMeta* __restrict__ meta,
                                                  const uint8_t* __restrict__ lens,
                                                  const uint32_t* __restrict__ chunk_out,
-                                                 uint8_t* __restrict__ slots) {
+                                                 uint8_t* __restrict__ slots,
+    uint32_t g_unit) {
   if (meta->status) return;
-  const uint32_t gi = blockIdx.x;
+  const uint32_t gi = g_unit;
   const int ng = meta->ngroups;
   const GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
   const int m = gm->method;
@@ -554,6 +609,13 @@ __global__ void __launch_bounds__(256) k_headers(const FieldMeta* __restrict__ m
   }
   for (uint32_t c = t; c < nc; c += 256) offs[c] = chunk_out[gm->chunk0 + c];
   if (t == 0) offs[nc] = endv;
+}
+
+__global__ void __launch_bounds__(256) k_headers(const FieldMeta* __restrict__ meta,
+                                                 const uint8_t* __restrict__ lens,
+                                                 const uint32_t* __restrict__ chunk_out,
+                                                 uint8_t* __restrict__ slots) {
+  headers_unit(meta, lens, chunk_out, slots, blockIdx.x);
 }
 
 void launch_headers(FieldMeta* meta, int ngroups_total, const uint8_t* lens,
@@ -1061,6 +1123,39 @@ __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const Group
   }
 }
 
+// one 16 KiB chunk of a newly fetched group (item = its index in the
+// retrieval's list of chunks to decode)
+__device__ __forceinline__ void decode_item(const uint8_t* __restrict__ slots, FieldMeta* meta,
+                                            const RetrieveDev* __restrict__ rd,
+                                            uint8_t* __restrict__ planes, uint32_t item,
+                                            HuffTables& T, uint32_t* scratch) {
+  const uint32_t ngr = rd->n_new;
+  const int ng = meta->ngroups;
+  // newly fetched group holding this item: last k with new_pref[k] <= item
+  uint32_t lo = 0, hi = ngr;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) / 2;
+    if (rd->new_pref[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  const uint32_t gi = rd->new_gi[lo];
+  const GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
+  const uint32_t cl = item - rd->new_pref[lo];
+  const uint64_t start = (uint64_t)cl * HP_CHUNK, rest = gm->S - start;
+  const uint32_t len = (uint32_t)(rest < HP_CHUNK ? rest : HP_CHUNK);
+  const uint8_t* stored = slots + gm->slot_off;
+  uint8_t* dst = planes + gm->plane_off + start;
+  if (gm->method == 1) {
+    huff_decode_chunk(stored, gm, cl, len, dst, T, scratch, meta);
+  } else if (gm->method == 2) {
+    if (threadIdx.x < 32) rle_decode_chunk(stored, gm, cl, len, dst, meta);
+  } else {  // direct copy of a DC group held in the slots of a compact handle
+    const uint4* src = reinterpret_cast<const uint4*>(stored + start);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (uint32_t i = threadIdx.x; i < len / 16; i += blockDim.x) d[i] = src[i];
+  }
+}
+
 __global__ void __launch_bounds__(HP_DEC_THREADS) k_decode(const uint8_t* __restrict__ slots,
                                                            FieldMeta* meta,
                                                            const RetrieveDev* __restrict__ rd,
@@ -1068,32 +1163,9 @@ __global__ void __launch_bounds__(HP_DEC_THREADS) k_decode(const uint8_t* __rest
   extern __shared__ __align__(16) unsigned char dec_smem[];
   HuffTables& T = *reinterpret_cast<HuffTables*>(dec_smem);
   __shared__ uint32_t scratch[HP_DEC_THREADS / 32];
-  const uint32_t total = rd->items, ngr = rd->n_new;
-  const int ng = meta->ngroups;
+  const uint32_t total = rd->items;
   for (uint32_t item = blockIdx.x; item < total; item += gridDim.x) {
-    // newly fetched group holding this item: last k with new_pref[k] <= item
-    uint32_t lo = 0, hi = ngr;
-    while (hi - lo > 1) {
-      uint32_t mid = (lo + hi) / 2;
-      if (rd->new_pref[mid] <= item) lo = mid;
-      else hi = mid;
-    }
-    const uint32_t gi = rd->new_gi[lo];
-    const GroupMeta* gm = &meta->grp[gi / ng][gi % ng];
-    const uint32_t cl = item - rd->new_pref[lo];
-    const uint64_t start = (uint64_t)cl * HP_CHUNK, rest = gm->S - start;
-    const uint32_t len = (uint32_t)(rest < HP_CHUNK ? rest : HP_CHUNK);
-    const uint8_t* stored = slots + gm->slot_off;
-    uint8_t* dst = planes + gm->plane_off + start;
-    if (gm->method == 1) {
-      huff_decode_chunk(stored, gm, cl, len, dst, T, scratch, meta);
-    } else if (gm->method == 2) {
-      if (threadIdx.x < 32) rle_decode_chunk(stored, gm, cl, len, dst, meta);
-    } else {  // direct copy of a DC group held in the slots of a compact handle
-      const uint4* src = reinterpret_cast<const uint4*>(stored + start);
-      uint4* d = reinterpret_cast<uint4*>(dst);
-      for (uint32_t i = threadIdx.x; i < len / 16; i += blockDim.x) d[i] = src[i];
-    }
+    decode_item(slots, meta, rd, planes, item, T, scratch);
     __syncthreads();
   }
 }
@@ -1109,6 +1181,122 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   const size_t smem = sizeof(HuffTables);
   set_smem_once((const void*)k_decode, (int)smem);
   hp::note_launch(), k_decode<<<blocks, HP_DEC_THREADS, smem, s>>>(slots, meta, rd, planes);
+}
+
+// ------------------------------------------------------------------ batched
+// unit = one chunk (or one group) of one job, one CTA each
+#define HP_BATCH_UNITS(BODY)                                      \
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {      \
+    const uint32_t j = unit_owner(unit0, njobs, u);               \
+    const BatchJob& J = jobs[j];                                  \
+    const uint32_t local = u - unit0[j];                          \
+    BODY;                                                         \
+    __syncthreads();                                              \
+  }
+
+#define HP_BATCH_PARAMS                                                                     \
+  const BatchJob* __restrict__ jobs, const uint32_t* __restrict__ unit0, uint32_t njobs, \
+      uint32_t total
+
+__global__ void __launch_bounds__(256) kb_chunk_stats(HP_BATCH_PARAMS) {
+  HP_BATCH_UNITS(chunk_stats_unit(J.planes, J.meta, J.chunk_group, J.hist, J.gcost, J.ccost, local))
+}
+__global__ void __launch_bounds__(256) kb_decide(HP_BATCH_PARAMS, uint64_t Ts, uint32_t cr_num,
+                                                 uint32_t cr_den) {
+  HP_BATCH_UNITS(decide_unit(J.meta, J.hist, J.gcost, J.lens, Ts, cr_num, cr_den, -1, local))
+}
+__global__ void __launch_bounds__(256) kb_huff_bits(HP_BATCH_PARAMS) {
+  HP_BATCH_UNITS(huff_bits_unit(J.planes, J.meta, J.chunk_group, J.lens, J.cwords, local))
+}
+__global__ void __launch_bounds__(256) kb_group_offsets(HP_BATCH_PARAMS) {
+  HP_BATCH_UNITS(group_offsets_unit(J.meta, J.cwords, J.ccost, J.cout, local))
+}
+__global__ void __launch_bounds__(256) kb_huff_encode(HP_BATCH_PARAMS) {
+  HP_BATCH_UNITS(huff_encode_unit(J.planes, J.meta, J.chunk_group, J.lens, J.cout, J.slots, local))
+}
+__global__ void __launch_bounds__(256) kb_rle_encode(HP_BATCH_PARAMS) {
+  HP_BATCH_UNITS(rle_encode_unit(J.planes, J.meta, J.chunk_group, J.cout, J.slots, local))
+}
+__global__ void __launch_bounds__(256) kb_headers(HP_BATCH_PARAMS) {
+  HP_BATCH_UNITS(headers_unit(J.meta, J.lens, J.cout, J.slots, local))
+}
+
+static uint32_t cap_grid(uint32_t grid, uint32_t total) { return grid < total ? grid : total; }
+
+void launch_b_chunk_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                          uint32_t total, uint32_t grid, cstream s) {
+  if (total)
+    hp::note_launch(), kb_chunk_stats<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+}
+void launch_b_decide(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                     uint64_t Ts, uint32_t cr_num, uint32_t cr_den, uint32_t grid, cstream s) {
+  if (total)
+    hp::note_launch(), kb_decide<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total, Ts,
+                                                                       cr_num, cr_den);
+}
+void launch_b_huff_bits(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                        uint32_t total, uint32_t grid, cstream s) {
+  if (total)
+    hp::note_launch(), kb_huff_bits<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+}
+void launch_b_group_offsets(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                            uint32_t total, uint32_t grid, cstream s) {
+  if (total)
+    hp::note_launch(), kb_group_offsets<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+}
+void launch_b_huff_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                          uint32_t total, uint32_t grid, cstream s) {
+  if (total)
+    hp::note_launch(), kb_huff_encode<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+}
+void launch_b_rle_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
+                         uint32_t total, uint32_t grid, cstream s) {
+  if (total)
+    hp::note_launch(), kb_rle_encode<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+}
+void launch_b_headers(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                      uint32_t grid, cstream s) {
+  if (total)
+    hp::note_launch(), kb_headers<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+}
+
+// decode: unit = one item (chunk to decode) of one job; the per-job item
+// counts are known only after the selection, so unit0 is computed on the device
+__global__ void kb_items_prefix(const BatchJob* __restrict__ jobs, uint32_t njobs, uint32_t* unit0) {
+  if (threadIdx.x != 0) return;
+  uint32_t run = 0;
+  for (uint32_t j = 0; j < njobs; j++) {
+    unit0[j] = run;
+    const RetrieveDev* rd = jobs[j].rd;
+    if (rd->status == 0 || rd->status == -5) run += rd->items;
+  }
+  unit0[njobs] = run;
+}
+
+void launch_b_items_prefix(const BatchJob* jobs, uint32_t njobs, uint32_t* unit0_out, cstream s) {
+  hp::note_launch(), kb_items_prefix<<<1, 32, 0, s>>>(jobs, njobs, unit0_out);
+}
+
+__global__ void __launch_bounds__(HP_DEC_THREADS) kb_decode(const BatchJob* __restrict__ jobs,
+                                                            const uint32_t* __restrict__ unit0,
+                                                            uint32_t njobs) {
+  extern __shared__ __align__(16) unsigned char dec_smem[];
+  HuffTables& T = *reinterpret_cast<HuffTables*>(dec_smem);
+  __shared__ uint32_t scratch[HP_DEC_THREADS / 32];
+  const uint32_t total = unit0[njobs];
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t j = unit_owner(unit0, njobs, u);
+    const BatchJob& J = jobs[j];
+    decode_item(J.slots, J.meta, J.rd, J.planes, u - unit0[j], T, scratch);
+    __syncthreads();
+  }
+}
+
+void launch_b_decode(const BatchJob* jobs, const uint32_t* unit0_dev, uint32_t njobs,
+                     uint32_t grid, cstream s) {
+  const size_t smem = sizeof(HuffTables);
+  set_smem_once((const void*)kb_decode, (int)smem);
+  hp::note_launch(), kb_decode<<<grid, HP_DEC_THREADS, smem, s>>>(jobs, unit0_dev, njobs);
 }
 
 }  // namespace hp

@@ -180,12 +180,13 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
 // coarse-node copy and the detail tiles, separated by block barriers.  Grids
 // alternate between the two scratch buffers as in the per-level path.
 template <typename T, int B>
-__global__ void __launch_bounds__(512)
-    k_recompose_small(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
-                      const LevelDesc* __restrict__ levels, int l_end, int nlev,
-                      int64_t* xroot, int64_t* xa, int64_t* xb, void* __restrict__ out) {
+__device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict__ planes,
+                                                     const FieldMeta* __restrict__ m,
+                                                     const LevelDesc* __restrict__ levels,
+                                                     int l_end, int nlev, int64_t* xroot,
+                                                     int64_t* xa, int64_t* xb,
+                                                     void* __restrict__ out, uint32_t* sm) {
   constexpr int WPB = 16;
-  extern __shared__ uint32_t sm[];
   uint32_t* s_hi = sm;                                      // [WPB][32*33]
   uint32_t* s_lo = sm + WPB * 32 * 33;                      // [WPB][32*33] (B = 64)
   uint32_t* s_sign = sm + (B == 64 ? 2 : 1) * WPB * 32 * 33;  // [WPB][32]
@@ -232,6 +233,15 @@ __global__ void __launch_bounds__(512)
     __syncthreads();
     coarse = (const int64_t*)dst;
   }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(512)
+    k_recompose_small(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
+                      const LevelDesc* __restrict__ levels, int l_end, int nlev,
+                      int64_t* xroot, int64_t* xa, int64_t* xb, void* __restrict__ out) {
+  extern __shared__ uint32_t sm[];
+  recompose_small_body<T, B>(planes, m, levels, l_end, nlev, xroot, xa, xb, out, sm);
 }
 
 static int sms() {
@@ -289,6 +299,101 @@ void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const
     else
       hp::note_launch(), k_recompose_level<double, 64, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
   }
+}
+
+// ------------------------------------------------------------------ batched
+template <typename T, int B>
+__global__ void __launch_bounds__(512) kb_recompose_small(const BatchJob* __restrict__ jobs) {
+  extern __shared__ uint32_t sm[];
+  const BatchJob& J = jobs[blockIdx.x];
+  recompose_small_body<T, B>(reinterpret_cast<const uint32_t*>(J.planes), J.meta, J.levels,
+                             J.small_end, (int)J.nlev, J.xroot, J.xa, J.xb, J.out, sm);
+}
+
+void launch_b_recompose_small(const BatchJob* jobs, uint32_t njobs, int dtype, cstream s) {
+  if (!njobs) return;
+  const size_t smem = (size_t)((dtype == 0 ? 1 : 2) * 16 * 32 * 33 + 16 * 32) * 4;
+  if (dtype == 0) {
+    set_smem_once((const void*)kb_recompose_small<float, 32>, (int)smem);
+    hp::note_launch(), kb_recompose_small<float, 32><<<njobs, 512, smem, s>>>(jobs);
+  } else {
+    set_smem_once((const void*)kb_recompose_small<double, 64>, (int)smem);
+    hp::note_launch(), kb_recompose_small<double, 64><<<njobs, 512, smem, s>>>(jobs);
+  }
+}
+
+// unit = 256 coarse nodes of one (job, level) entry
+template <typename T>
+__global__ void __launch_bounds__(256) kb_recompose_copy(const BatchJob* __restrict__ jobs,
+                                                         const LevelRef* __restrict__ refs,
+                                                         const uint32_t* __restrict__ unit0,
+                                                         uint32_t nrefs, uint32_t total) {
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    const LevelDesc& L = J.levels[R.level];
+    const uint32_t cz = L.gc[0], cy = L.gc[1], cx = L.gc[2];
+    const uint64_t n = (uint64_t)cz * cy * cx;
+    const uint64_t i = (uint64_t)(u - unit0[e]) * 256 + threadIdx.x;
+    if (i >= n) continue;
+    const uint32_t x = (uint32_t)(i % cx);
+    const uint64_t r = i / cx;
+    const uint32_t y = (uint32_t)(r % cy), z = (uint32_t)(r / cy);
+    const size_t d = ((size_t)(2 * z) * L.g[1] + 2 * y) * L.g[2] + 2 * x;
+    const int64_t X = R.coarse[i];
+    if (R.final) reinterpret_cast<T*>(J.out)[d] = convert_out<T>(X, J.meta->E_f);
+    else R.dst[d] = X;
+  }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(B == 32 ? 256 : 128)
+    kb_recompose_level(const BatchJob* __restrict__ jobs, const LevelRef* __restrict__ refs,
+                       const uint32_t* __restrict__ unit0, uint32_t nrefs, uint32_t total) {
+  constexpr int WPB = B == 32 ? 8 : 4;
+  __shared__ uint32_t s_hi[WPB][32 * 33];
+  __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
+  __shared__ uint32_t s_sign[WPB][32];
+  const int w = threadIdx.x >> 5;
+  for (uint32_t u = blockIdx.x * WPB + w; u < total; u += gridDim.x * WPB) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    const FieldMeta* m = J.meta;
+    if (m->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const int k = 4 * m->cur[L.level], bl = m->bl[L.level], E_f = m->E_f;
+    const uint32_t* P = reinterpret_cast<const uint32_t*>(J.planes) + L.plane_off / 4;
+    const uint32_t base = J.perm[L.tile0 + (u - unit0[e])] * HP_TILE;
+    if (R.final)
+      recompose_tile<T, B, true>(P, L, base, k, bl, E_f, R.coarse, J.out, s_hi[w],
+                                 s_lo[B == 64 ? w : 0], s_sign[w]);
+    else
+      recompose_tile<T, B, false>(P, L, base, k, bl, E_f, R.coarse, R.dst, s_hi[w],
+                                  s_lo[B == 64 ? w : 0], s_sign[w]);
+  }
+}
+
+void launch_b_recompose_copy(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                             uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s) {
+  if (!total) return;
+  if (grid > total) grid = total;
+  if (dtype == 0)
+    hp::note_launch(), kb_recompose_copy<float><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  else
+    hp::note_launch(), kb_recompose_copy<double><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+}
+
+void launch_b_recompose_level(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                              uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s) {
+  if (!total) return;
+  const uint32_t wpb = dtype == 0 ? 8 : 4, need = (total + wpb - 1) / wpb;
+  if (grid > need) grid = need;
+  if (dtype == 0)
+    hp::note_launch(), kb_recompose_level<float, 32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  else
+    hp::note_launch(), kb_recompose_level<double, 64><<<grid, 128, 0, s>>>(jobs, refs, unit0, nrefs, total);
 }
 
 }  // namespace hp

@@ -21,13 +21,22 @@
 
 #include "../../include/hpmdr.h"
 #include "dev_common.cuh"
+#include "runtime.h"
 
 using namespace hp;
 
-static thread_local std::string g_last_error;
+thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
+const char* kStageName[NSTAGE] = {
+    "stats", "stats_finalize", "levelmax", "bitlen", "encode", "chunk_stats", "decide",
+    "huff_bits", "group_offsets", "huff_encode", "rle_encode", "headers", "sequence", "select",
+    "decode", "recompose_root", "recompose_copy", "recompose_level", "recompose_copy_out",
+    "recompose_level_out", "vmag", "cells_levelmax", "cells_encode", "cells_recompose",
+    "cells_recompose_out", "recompose_small"};
+
 void hp::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void hp::unnote_launches(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 
 void hp::set_smem_once(const void* func, int bytes) {
   static std::mutex* mu = new std::mutex();
@@ -40,151 +49,6 @@ void hp::set_smem_once(const void* func, int bytes) {
   done->insert({func, dev});
 }
 
-// ------------------------------------------------------------------ profiling
-// Optional per-stage CUDA events on the context stream: elapsed time per
-// kernel stage plus the stage's algorithmic bytes (what the method must move).
-enum Stage {
-  ST_STATS, ST_FINALIZE, ST_LEVELMAX, ST_BITLEN, ST_ENCODE, ST_CHUNK_STATS, ST_DECIDE,
-  ST_HUFF_BITS, ST_OFFSETS, ST_HUFF_ENC, ST_RLE_ENC, ST_HEADERS, ST_SEQUENCE, ST_SELECT,
-  ST_DECODE, ST_ROOT, ST_COPY, ST_LEVEL, ST_COPY_OUT, ST_LEVEL_OUT, ST_VMAG, ST_CELLS_MAX,
-  ST_CELLS_ENC, ST_CELLS_REC, ST_CELLS_REC_OUT, ST_SMALL, NSTAGE
-};
-static const char* kStageName[NSTAGE] = {
-    "stats", "stats_finalize", "levelmax", "bitlen", "encode", "chunk_stats", "decide",
-    "huff_bits", "group_offsets", "huff_encode", "rle_encode", "headers", "sequence", "select",
-    "decode", "recompose_root", "recompose_copy", "recompose_level", "recompose_copy_out",
-    "recompose_level_out", "vmag", "cells_levelmax", "cells_encode", "cells_recompose",
-    "cells_recompose_out", "recompose_small"};
-
-struct ProfEntry {
-  int stage;
-  cudaEvent_t a, b;
-  double bytes;
-};
-
-struct Profiler {
-  bool on = false;
-  std::vector<cudaEvent_t> pool;
-  std::vector<ProfEntry> pending;
-  double ms[NSTAGE] = {}, bytes[NSTAGE] = {};
-  uint64_t calls[NSTAGE] = {};
-  cudaEvent_t get() {
-    cudaEvent_t e = nullptr;
-    if (!pool.empty()) {
-      e = pool.back();
-      pool.pop_back();
-    } else {
-      cudaEventCreate(&e);
-    }
-    return e;
-  }
-  size_t begin(int stage, double b, cudaStream_t s) {
-    if (!on) return SIZE_MAX;
-    ProfEntry p{stage, get(), get(), b};
-    cudaEventRecord(p.a, s);
-    pending.push_back(p);
-    return pending.size() - 1;
-  }
-  void end(size_t i, cudaStream_t s) {
-    if (i != SIZE_MAX) cudaEventRecord(pending[i].b, s);
-  }
-  void patch(size_t i, double b) {
-    if (i != SIZE_MAX && i < pending.size()) pending[i].bytes = b;
-  }
-  void resolve() {
-    for (auto& p : pending) {
-      float t = 0;
-      cudaEventSynchronize(p.b);
-      cudaEventElapsedTime(&t, p.a, p.b);
-      ms[p.stage] += t;
-      bytes[p.stage] += p.bytes;
-      calls[p.stage]++;
-      pool.push_back(p.a);
-      pool.push_back(p.b);
-    }
-    pending.clear();
-  }
-  void reset() {
-    resolve();
-    for (int i = 0; i < NSTAGE; i++) ms[i] = bytes[i] = 0, calls[i] = 0;
-  }
-  ~Profiler() {
-    for (auto& p : pending) {
-      cudaEventDestroy(p.a);
-      cudaEventDestroy(p.b);
-    }
-    for (auto e : pool) cudaEventDestroy(e);
-  }
-};
-
-struct ProfScope {
-  Profiler* P;
-  size_t i;
-  cudaStream_t s;
-  ProfScope(Profiler* p, int stage, double bytes, cudaStream_t st)
-      : P(p), i(p ? p->begin(stage, bytes, st) : SIZE_MAX), s(st) {}
-  ~ProfScope() {
-    if (P) P->end(i, s);
-  }
-};
-
-#define HP_CUDA(call)                                                              \
-  do {                                                                             \
-    cudaError_t e_ = (call);                                                       \
-    if (e_ != cudaSuccess) {                                                       \
-      g_last_error = std::string(#call) + ": " + cudaGetErrorString(e_);           \
-      return HPMDR_ERR_CUDA;                                                       \
-    }                                                                              \
-  } while (0)
-
-#define HP_TRY(expr)                \
-  do {                              \
-    hpmdr_status s_ = (expr);       \
-    if (s_ != HPMDR_OK) return s_;  \
-  } while (0)
-
-struct Allocator {
-  hpmdr_allocator hook{};
-  bool has_hook = false;
-  cudaMemPool_t pool = nullptr;
-
-  hpmdr_status alloc(void** p, size_t bytes, cudaStream_t s) const {
-    *p = nullptr;
-    if (bytes == 0) return HPMDR_OK;
-    bytes = (bytes + 255) & ~(size_t)255;
-    if (has_hook) {
-      *p = hook.alloc(bytes, (void*)s, hook.user);
-      return *p ? HPMDR_OK : HPMDR_ERR_NOMEM;
-    }
-    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
-    if (e != cudaSuccess) {
-      g_last_error = std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e);
-      cudaGetLastError();
-      return e == cudaErrorMemoryAllocation ? HPMDR_ERR_NOMEM : HPMDR_ERR_CUDA;
-    }
-    return HPMDR_OK;
-  }
-  void release(void* p, cudaStream_t s) const {
-    if (!p) return;
-    if (has_hook) hook.free(p, (void*)s, hook.user);
-    else cudaFreeAsync(p, s);
-  }
-};
-
-struct hpmdr_ctx {
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  uint64_t Ts = 4096;
-  uint32_t cr_num = 2, cr_den = 1;
-  Allocator A;
-  Profiler prof;
-  std::vector<cudaStream_t> aux;  // extra streams of the chunk pipelines (created on demand)
-  Profiler* P() { return prof.on ? &prof : nullptr; }
-  ~hpmdr_ctx() {
-    for (cudaStream_t s : aux) cudaStreamDestroy(s);
-  }
-};
-
 // ------------------------------------------------------------------ geometry
 static int detail_levels(const uint64_t d[3]) {
   uint64_t n = std::max(d[0], std::max(d[1], d[2]));
@@ -195,9 +59,9 @@ static int detail_levels(const uint64_t d[3]) {
 
 static uint32_t axis_count(uint64_t g, int o) { return (uint32_t)(o ? g / 2 : (g + 1) / 2); }
 
-static uint64_t round16(uint64_t v) { return (v + 15) & ~15ull; }
+uint64_t round16(uint64_t v) { return (v + 15) & ~15ull; }
 
-static hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t dims[3], uint64_t* N) {
+hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t dims[3], uint64_t* N) {
   if (ndims < 1 || ndims > 3 || !dims_in) return HPMDR_ERR_ARG;
   uint64_t in[3] = {dims_in[0], dims_in[1], dims_in[2]};  // dims may alias dims_in
   dims[0] = dims[1] = dims[2] = 1;
@@ -211,32 +75,6 @@ static hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t di
   *N = n;
   return HPMDR_OK;
 }
-
-// The geometry of one field shape under one coder configuration: the level
-// descriptors, the tile order, the chunk -> group map and the initial
-// FieldMeta (group sizes, chunk ranges, slot layout).  It depends only on
-// (dims, B, T_s, T_cr), so it is built and uploaded once and shared by every
-// handle of that shape: refactoring the same shape again, or the chunks of a
-// streamed field, repeats no host planning and no metadata upload.
-struct Plan {
-  uint64_t dims[3] = {1, 1, 1}, N = 1;
-  int B = 32, ngroups = 8, nlev = 0;
-  std::vector<LevelDesc> levels;
-  std::vector<uint32_t> perm;         // per level: processing order of its tiles
-  std::vector<uint32_t> chunk_group;  // global chunk -> flat group index
-  uint32_t total_tiles = 0, generic_tiles = 0, total_chunks = 0;
-  uint64_t plane_bytes = 0, slot_bytes = 0;
-  std::unique_ptr<FieldMeta> meta0{new FieldMeta()};
-  // one device buffer holding levels, perm, chunk map and meta0
-  unsigned char* d_buf = nullptr;
-  LevelDesc* d_levels = nullptr;
-  uint32_t* d_perm = nullptr;
-  uint32_t* d_chunk_group = nullptr;
-  FieldMeta* d_meta0 = nullptr;
-  ~Plan() {
-    if (d_buf) cudaFree(d_buf);
-  }
-};
 
 static void plan_levels(Plan& P) {
   const int L = detail_levels(P.dims);
@@ -361,11 +199,11 @@ static void init_meta(FieldMeta& M, int dtype, int B, int nlev, int ngroups) {
   M.compact = 0;
 }
 
-static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Plans are cached process-wide per (device, shape, B, T_s, T_cr).  Handles
 // hold a reference, so a plan evicted from the cache lives on while used.
-static hpmdr_status get_plan(int device, const uint64_t dims[3], int dtype, uint64_t Ts,
+hpmdr_status get_plan(int device, const uint64_t dims[3], int dtype, uint64_t Ts,
                              uint32_t num, uint32_t den, std::shared_ptr<const Plan>* out) {
   typedef std::array<uint64_t, 8> Key;
   static std::mutex* mu = new std::mutex();  // never destroyed: usable during exit
@@ -412,58 +250,8 @@ static hpmdr_status get_plan(int device, const uint64_t dims[3], int dtype, uint
   return HPMDR_OK;
 }
 
-struct hpmdr_handle {
-  Allocator A;
-  cudaStream_t stream = nullptr;  // stream used to free device memory
-  int dtype = 0, B = 32, nlev = 0, ngroups = 8;
-  uint64_t dims[3] = {1, 1, 1}, N = 1;
-  std::shared_ptr<const Plan> plan;
-  std::vector<LevelDesc> levels;  // host copy of plan->levels
-  uint32_t total_tiles = 0, generic_tiles = 0, total_chunks = 0, max_items = 0;
-  uint64_t plane_bytes = 0, slot_bytes = 0;
-  const LevelDesc* d_levels = nullptr;      // owned by the plan
-  const uint32_t* d_perm = nullptr;         // owned by the plan
-  const uint32_t* d_chunk_group = nullptr;  // owned by the plan
-  uint8_t* d_planes = nullptr;  // plane buffer (refactor output, retrieval plane cache)
-  uint8_t* d_slots = nullptr;
-  FieldMeta* d_meta = nullptr;
-  RetrieveDev* d_rd = nullptr;
-  int64_t* d_xa = nullptr;  // |G_2| int64 (recompose scratch)
-  int64_t* d_xb = nullptr;  // |G_4| int64
-  int64_t* d_xroot = nullptr;
-  uint64_t xa_elems = 0, xb_elems = 0;
-  // compact: every group's stored bytes (DC groups included) live in the slot
-  // buffer, packed; the plane buffer is then only a cache of decoded planes,
-  // allocated on the first retrieval and released by hpmdr_handle_drop_cache
-  bool compact = false;
-  std::unique_ptr<FieldMeta> meta{new FieldMeta()};  // host mirror after refactor/import
-  bool qoi_ready = false;
-  float qmin = 0, qmax = 0;
-  // profiler entries of the last retrieval, patched with bytes known after it
-  std::vector<std::pair<size_t, int>> prof_lv;  // (entry, level*4 + kind)
-  size_t prof_decode = SIZE_MAX, prof_small = SIZE_MAX;
-  int small_end = 0;
-
-  void release_cache(cudaStream_t s) {
-    A.release(d_planes, s);
-    A.release(d_xa, s);
-    A.release(d_xb, s);
-    d_planes = nullptr;
-    d_xa = d_xb = nullptr;
-  }
-  ~hpmdr_handle() {
-    A.release(d_planes, stream);
-    A.release(d_slots, stream);
-    A.release(d_meta, stream);
-    A.release(d_rd, stream);
-    A.release(d_xa, stream);
-    A.release(d_xb, stream);
-    A.release(d_xroot, stream);
-  }
-};
-
 // a handle with the plan of (ndims, dims, dtype) under ctx's coder settings
-static hpmdr_status new_handle(hpmdr_ctx* ctx, int ndims, const uint64_t dims_in[3], int dtype,
+hpmdr_status new_handle(hpmdr_ctx* ctx, int ndims, const uint64_t dims_in[3], int dtype,
                                const std::shared_ptr<const Plan>* plan_in,
                                std::unique_ptr<hpmdr_handle>& H) {
   if (dtype != HPMDR_F32 && dtype != HPMDR_F64) return HPMDR_ERR_ARG;
@@ -491,7 +279,7 @@ static hpmdr_status new_handle(hpmdr_ctx* ctx, int ndims, const uint64_t dims_in
   return HPMDR_OK;
 }
 
-static void count_items(hpmdr_handle* H) {
+void count_items(hpmdr_handle* H) {
   H->max_items = 0;
   for (int l = 0; l < H->nlev; l++)
     for (int g = 0; g < H->ngroups; g++)
@@ -831,7 +619,7 @@ extern "C" hpmdr_status hpmdr_refactor_chunked(hpmdr_ctx* ctx, const void* field
 }
 
 // ------------------------------------------------------------------ retrieve
-static hpmdr_status ensure_retrieve_buffers(hpmdr_handle* H, cudaStream_t s) {
+hpmdr_status ensure_retrieve_buffers(hpmdr_handle* H, cudaStream_t s) {
   if (!H->d_planes) HP_TRY(H->A.alloc((void**)&H->d_planes, H->plane_bytes, s));
   if (!H->d_rd) HP_TRY(H->A.alloc((void**)&H->d_rd, sizeof(RetrieveDev), s));
   if (!H->d_xroot) HP_TRY(H->A.alloc((void**)&H->d_xroot, 8, s));
@@ -951,7 +739,7 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
   }
 }
 
-static hpmdr_status collect_info(hpmdr_ctx* ctx, hpmdr_handle* H, hpmdr_retrieve_info* info,
+hpmdr_status collect_info(hpmdr_ctx* ctx, hpmdr_handle* H, hpmdr_retrieve_info* info,
                                  cudaStream_t s) {
   RetrieveDev rd;
   int32_t mstatus = 0;

@@ -69,8 +69,7 @@ __device__ u128 finish_estimate(const FieldMeta* m, u128 sum_delta) {
 // One warp: lane l evaluates levels l and l + 32; the best level of each step
 // is a warp-wide reduction with the greedy comparison.  The estimate after
 // each step is updated from the chosen level's change only.
-__global__ void k_sequence(FieldMeta* m) {
-  __shared__ int g[64];
+__device__ __forceinline__ void sequence_warp(FieldMeta* m, int* g) {
   const int lane = threadIdx.x;
   if (m->status) return;
   const int nlev = m->nlev;
@@ -114,6 +113,11 @@ __global__ void k_sequence(FieldMeta* m) {
   if (lane == 0) m->seq_len = n;
 }
 
+__global__ void k_sequence(FieldMeta* m) {
+  __shared__ int g[64];
+  sequence_warp(m, g);
+}
+
 void launch_sequence(FieldMeta* meta, cstream s) { hp::note_launch(), k_sequence<<<1, 32, 0, s>>>(meta); }
 
 // floor(tau * 2^(51+B-E_f)) from the IEEE fields of tau, saturating at 2^127
@@ -139,9 +143,13 @@ __device__ u128 tau_units(double tau, int E_f, int B) {
   return (u128)(m >> (-s));
 }
 
-__global__ void k_select(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* rd) {
+__device__ void select_prefix(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* rd) {
   rd->status = m->status;
-  if (m->status) return;
+  if (m->status) {  // nothing to decode or recompose
+    rd->n_new = 0;
+    rd->items = 0;
+    return;
+  }
   const double tau_abs = tau_is_abs ? tau : __dmul_rn(tau, m->range);
   const u128 T = tau_units(tau_abs, m->E_f, m->B);
   // the estimates never increase along the sequence: binary search for the
@@ -196,8 +204,31 @@ __global__ void k_select(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* 
   rd->tau_abs = tau_abs;
 }
 
+__global__ void k_select(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* rd) {
+  select_prefix(m, tau, tau_is_abs, rd);
+}
+
 void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s) {
   hp::note_launch(), k_select<<<1, 1, 0, s>>>(meta, tau, tau_is_abs, rd);
+}
+
+// ------------------------------------------------------------------ batched
+__global__ void kb_sequence(const BatchJob* __restrict__ jobs) {
+  __shared__ int g[64];
+  sequence_warp(jobs[blockIdx.x].meta, g);
+}
+
+void launch_b_sequence(const BatchJob* jobs, uint32_t njobs, cstream s) {
+  if (njobs) hp::note_launch(), kb_sequence<<<njobs, 32, 0, s>>>(jobs);
+}
+
+__global__ void kb_select(const BatchJob* __restrict__ jobs, uint32_t njobs) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < njobs) select_prefix(jobs[j].meta, jobs[j].tau, 0, jobs[j].rd);
+}
+
+void launch_b_select(const BatchJob* jobs, uint32_t njobs, cstream s) {
+  if (njobs) hp::note_launch(), kb_select<<<(njobs + 31) / 32, 32, 0, s>>>(jobs, njobs);
 }
 
 }  // namespace hp

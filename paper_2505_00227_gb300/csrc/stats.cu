@@ -115,7 +115,7 @@ __device__ double key_to_double(uint64_t k, int dtype) {
 
 // E_f = smallest integer with max|f| < 2^E_f (0 for an all-zero field);
 // rejects non-finite values and magnitudes outside the supported range.
-__global__ void k_stats_finalize(FieldMeta* meta) {
+__device__ void stats_finalize(FieldMeta* meta) {
   int dtype = meta->dtype;
   uint64_t a = meta->key_absmax;
   int E = 0;
@@ -146,6 +146,133 @@ __global__ void k_stats_finalize(FieldMeta* meta) {
   if (bad) meta->status = -1;  // HPMDR_ERR_ARG
 }
 
+__global__ void k_stats_finalize(FieldMeta* meta) { stats_finalize(meta); }
+
 void launch_stats_finalize(FieldMeta* meta, cstream s) { hp::note_launch(), k_stats_finalize<<<1, 1, 0, s>>>(meta); }
+
+// ------------------------------------------------------------------ batched
+// 16-byte copy of n bytes (both 16-byte aligned, n a multiple of 16)
+__device__ __forceinline__ void block_copy16(void* dst, const void* src, size_t n) {
+  const uint4* s = reinterpret_cast<const uint4*>(src);
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (size_t i = threadIdx.x; i < n / 16; i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ void block_zero16(void* dst, size_t n) {
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (size_t i = threadIdx.x; i < n / 16; i += blockDim.x) d[i] = make_uint4(0, 0, 0, 0);
+}
+
+static_assert(sizeof(FieldMeta) % 16 == 0, "FieldMeta is copied in 16-byte words");
+static_assert(sizeof(RetrieveDev) % 16 == 0, "RetrieveDev is copied in 16-byte words");
+
+// one CTA per job: the plan's initial metadata, zeroed histograms and RLE sizes
+__global__ void __launch_bounds__(256) kb_init(const BatchJob* __restrict__ jobs) {
+  const BatchJob& J = jobs[blockIdx.x];
+  block_copy16(J.meta, J.meta0, sizeof(FieldMeta));
+  block_zero16(J.hist, 1024ull * J.ngt);
+  for (uint32_t g = threadIdx.x; g < J.ngt; g += blockDim.x) J.gcost[g] = 0ull;
+}
+
+void launch_b_init(const BatchJob* jobs, uint32_t njobs, cstream s) {
+  if (njobs) hp::note_launch(), kb_init<<<njobs, 256, 0, s>>>(jobs);
+}
+
+// unit = `seg` consecutive values of one field (seg a multiple of 256 * 16 bytes)
+template <typename T>
+__global__ void __launch_bounds__(256) kb_stats(const BatchJob* __restrict__ jobs,
+                                                const uint32_t* __restrict__ unit0, uint32_t njobs,
+                                                uint32_t total, uint32_t seg) {
+  constexpr int VEC = 16 / sizeof(T);
+  __shared__ uint64_t sa[8], sb[8], sc[8];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t j = unit_owner(unit0, njobs, u);
+    const BatchJob& J = jobs[j];
+    const uint64_t a = (uint64_t)(u - unit0[j]) * seg, b = min(J.N, a + seg);
+    const T* f = reinterpret_cast<const T*>(J.f);
+    uint64_t amax = 0, kmin = ~0ull, kmax = 0;
+    const uint64_t va = a / VEC, vb = b / VEC;
+    const uint4* fv = reinterpret_cast<const uint4*>(f);
+    for (uint64_t i = va + threadIdx.x; i < vb; i += blockDim.x) {
+      uint4 x = __ldcs(fv + i);
+      T v[VEC];
+      memcpy(v, &x, 16);
+#pragma unroll
+      for (int k = 0; k < VEC; k++) {
+        uint64_t p = abs_key(v[k]), o = order_key(v[k]);
+        amax = p > amax ? p : amax;
+        kmin = o < kmin ? o : kmin;
+        kmax = o > kmax ? o : kmax;
+      }
+    }
+    for (uint64_t i = vb * VEC + threadIdx.x; i < b; i += blockDim.x) {
+      T v = f[i];
+      uint64_t p = abs_key(v), o = order_key(v);
+      amax = p > amax ? p : amax;
+      kmin = o < kmin ? o : kmin;
+      kmax = o > kmax ? o : kmax;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      uint64_t x = __shfl_xor_sync(HP_FULL, amax, o);
+      uint64_t y = __shfl_xor_sync(HP_FULL, kmin, o);
+      uint64_t z = __shfl_xor_sync(HP_FULL, kmax, o);
+      amax = x > amax ? x : amax;
+      kmin = y < kmin ? y : kmin;
+      kmax = z > kmax ? z : kmax;
+    }
+    if (lane == 0) {
+      sa[w] = amax;
+      sb[w] = kmin;
+      sc[w] = kmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+        amax = sa[k] > amax ? sa[k] : amax;
+        kmin = sb[k] < kmin ? sb[k] : kmin;
+        kmax = sc[k] > kmax ? sc[k] : kmax;
+      }
+      atomicMax((unsigned long long*)&J.meta->key_absmax, (unsigned long long)amax);
+      atomicMin((unsigned long long*)&J.meta->key_min, (unsigned long long)kmin);
+      atomicMax((unsigned long long*)&J.meta->key_max, (unsigned long long)kmax);
+    }
+    __syncthreads();
+  }
+}
+
+void launch_b_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
+                    uint32_t seg, int dtype, uint32_t grid, cstream s) {
+  if (!total) return;
+  if (grid > total) grid = total;
+  if (dtype == 0)
+    hp::note_launch(), kb_stats<float><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total, seg);
+  else
+    hp::note_launch(), kb_stats<double><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total, seg);
+}
+
+__global__ void kb_finalize(const BatchJob* __restrict__ jobs, uint32_t njobs) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < njobs) stats_finalize(jobs[j].meta);
+}
+
+void launch_b_finalize(const BatchJob* jobs, uint32_t njobs, cstream s) {
+  if (njobs) hp::note_launch(), kb_finalize<<<(njobs + 63) / 64, 64, 0, s>>>(jobs, njobs);
+}
+
+__global__ void __launch_bounds__(256) kb_gather(const BatchJob* __restrict__ jobs,
+                                                 FieldMeta* metas, RetrieveDev* rds,
+                                                 int32_t* statuses) {
+  const BatchJob& J = jobs[blockIdx.x];
+  if (metas) block_copy16(metas + blockIdx.x, J.meta, sizeof(FieldMeta));
+  if (rds) block_copy16(rds + blockIdx.x, J.rd, sizeof(RetrieveDev));
+  if (statuses && threadIdx.x == 0) statuses[blockIdx.x] = J.meta->status;
+}
+
+void launch_b_gather(const BatchJob* jobs, uint32_t njobs, FieldMeta* metas, RetrieveDev* rds,
+                     int32_t* statuses, cstream s) {
+  if (njobs) hp::note_launch(), kb_gather<<<njobs, 256, 0, s>>>(jobs, metas, rds, statuses);
+}
 
 }  // namespace hp

@@ -7,7 +7,9 @@ method: it only makes input arrays, and both the CUDA path and the CPU oracle
 consume the same arrays.  Every random draw comes from a CPU ``torch.Generator``
 so that a given seed gives the same parameters and noise on any device; the
 optional ``device`` only moves the arithmetic (the spectral filter's FFT) to the
-GPU for large fields.
+GPU for large fields.  ``device_noise=True`` draws the noise with a generator on
+``device`` instead (much faster for benchmark-sized fields; reproducible on the
+same device type and PyTorch version only).
 
 * ``blobs``: sum of Gaussian blobs a*exp(-|x-c|^2 / (2 w^2)), centres uniform
   in the box, widths uniform in [4, 16] cells (scaled with the box for small
@@ -21,14 +23,20 @@ import math
 import torch
 
 
-def _gen(seed):
-    g = torch.Generator(device="cpu")
+def _gen(seed, device="cpu"):
+    g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     return g
 
 
+def _normal(shape, seed_gen, seed, dtype, device, device_noise):
+    if device_noise and str(device) != "cpu":
+        return torch.randn(shape, generator=_gen(seed + 0x5EED, device), dtype=dtype, device=device)
+    return torch.randn(shape, generator=seed_gen, dtype=dtype).to(device)
+
+
 def blobs(shape, seed=0, n_blobs=8, width=(4.0, 16.0), noise=1e-3, dtype=torch.float32,
-          device="cpu"):
+          device="cpu", device_noise=False):
     """Sum of ``n_blobs`` Gaussian blobs plus white noise on a (nz, ny, nx) grid."""
     shape = tuple(int(s) for s in shape)
     g = _gen(seed)
@@ -39,9 +47,8 @@ def blobs(shape, seed=0, n_blobs=8, width=(4.0, 16.0), noise=1e-3, dtype=torch.f
     widths = (width[0] + (width[1] - width[0]) * torch.rand(n_blobs, generator=g,
                                                             dtype=torch.float64)) * max(scale, 0.25)
     amps = torch.randn(n_blobs, generator=g, dtype=torch.float64)
-    eps = torch.randn(shape, generator=g, dtype=torch.float64) * noise
+    f = _normal(shape, g, seed, torch.float64, device, device_noise) * noise
     axes = [torch.arange(s, dtype=torch.float64, device=device) for s in shape]
-    f = eps.to(device)
     for b in range(n_blobs):
         r2 = None
         for d in range(nd):
@@ -54,9 +61,9 @@ def blobs(shape, seed=0, n_blobs=8, width=(4.0, 16.0), noise=1e-3, dtype=torch.f
     return f.to(dtype).contiguous()
 
 
-def _spectral_raw(shape, seed, slope, device, work_dtype):
+def _spectral_raw(shape, seed, slope, device, work_dtype, device_noise=False):
     g = _gen(seed)
-    white = torch.randn(shape, generator=g, dtype=work_dtype).to(device)
+    white = _normal(shape, g, seed, work_dtype, device, device_noise)
     spec = torch.fft.rfftn(white)
     del white
     ks = []
@@ -84,18 +91,21 @@ def _rescale(f):
     return 2.0 * (f - lo) / (hi - lo) - 1.0
 
 
-def spectral(shape, seed=2, slope=-11.0 / 3.0, dtype=torch.float32, device="cpu"):
+def spectral(shape, seed=2, slope=-11.0 / 3.0, dtype=torch.float32, device="cpu",
+             device_noise=False):
     """Isotropic P(k) ~ k^slope Gaussian random field, rescaled to [-1, 1]."""
     shape = tuple(int(s) for s in shape)
     work = torch.float64 if dtype == torch.float64 else torch.float32
-    f = _rescale(_spectral_raw(shape, seed, slope, device, work))
+    f = _rescale(_spectral_raw(shape, seed, slope, device, work, device_noise))
     return f.to(dtype).contiguous()
 
 
-def spectral_trend(shape, seed=3, slope=-11.0 / 3.0, dtype=torch.float64, device="cpu"):
+def spectral_trend(shape, seed=3, slope=-11.0 / 3.0, dtype=torch.float64, device="cpu",
+                   device_noise=False):
     """``spectral`` plus the smooth trend 0.5 sin(2 pi x/L_x) cos(2 pi y/L_y)."""
     shape = tuple(int(s) for s in shape)
-    f = spectral(shape, seed=seed, slope=slope, dtype=torch.float64, device=device)
+    f = spectral(shape, seed=seed, slope=slope, dtype=torch.float64, device=device,
+                 device_noise=device_noise)
     ny, nx = shape[-2], shape[-1]
     x = torch.arange(nx, dtype=torch.float64, device=device) * (2.0 * math.pi / nx)
     y = torch.arange(ny, dtype=torch.float64, device=device) * (2.0 * math.pi / ny)
@@ -111,15 +121,16 @@ def batch_sizes(count=256, lo=32, hi=256, seed=1):
     return [tuple(int(v) for v in row) for row in sizes.clamp(lo, hi)]
 
 
-def batch_field(i, shape, seed=1, device="cpu"):
+def batch_field(i, shape, seed=1, device="cpu", device_noise=False):
     """i-th field of the batched workload: alternating blobs / spectral generators."""
     if i % 2 == 0:
-        return blobs(shape, seed=seed * 100003 + i, device=device)
-    return spectral(shape, seed=seed * 100003 + i, device=device)
+        return blobs(shape, seed=seed * 100003 + i, device=device, device_noise=device_noise)
+    return spectral(shape, seed=seed * 100003 + i, device=device, device_noise=device_noise)
 
 
-def velocity_triplet(shape, seed=5, device="cpu"):
+def velocity_triplet(shape, seed=5, device="cpu", device_noise=False):
     """(vx, vy, vz), each an independent spectral field on `shape` (an int: a cube)."""
     if isinstance(shape, int):
         shape = (shape, shape, shape)
-    return tuple(spectral(shape, seed=seed * 7 + c, device=device) for c in range(3))
+    return tuple(spectral(shape, seed=seed * 7 + c, device=device, device_noise=device_noise)
+                 for c in range(3))
