@@ -119,6 +119,23 @@ def traffic_for(kernel):
         return None
 
 
+# ------------------------------------------------------------ ranks (replicas)
+def slowest_rank(x, world, device):
+    """Max of a per-rank scalar over all ranks (the job's time is the slowest
+    rank's); no collective for one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_rank, seconds_max, world):
+    """Whole-job GB/s of replicas: every rank's bytes over the slowest time."""
+    return world * bytes_per_rank / seconds_max / 1e9
+
+
 # ------------------------------------------------------------- CPU oracle
 def oracle_step(f_np):
     from oracle import pyoracle as O
@@ -447,12 +464,9 @@ def run_ours(args):
     prof = ctx.profile_entries()
     ctx.profile(False)
 
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = slowest_rank(ms, world, "cuda")
     step_bytes = 7 * fbytes
-    value = world * step_bytes / (ms_max * 1e-3) / 1e9
+    value = job_throughput(step_bytes, ms_max * 1e-3, world)
 
     # ---- end to end through the C ABI with pinned host buffers ---------
     host_in = field.cpu().pin_memory()
@@ -472,10 +486,7 @@ def run_ours(args):
         step_host()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_t = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * step_bytes / float(e2e_t.item()) / 1e9
+    e2e_value = job_throughput(step_bytes, slowest_rank(e2e_s, world, "cuda"), world)
 
     if rank == 0:
         peak, peak_kind = peaks()

@@ -49,138 +49,88 @@ bool cell_path_ok(const LevelDesc& L, int B) {
 }
 
 // ------------------------------------------------------------ refactor side
-// fixed-point values of one thread's 4 cells: the 20 coarse corners
-// (rows z in {Z0, Z2} x y in {Y0, Y2}, x = 2cx, 2cx+2, ..., 2cx+8 clamped) and
-// the 28 type nodes
-struct CellF {
-  int64_t co[2][2][5];  // [dz][dy][i]: coarse value at x = 2cx + 2i
-  int64_t nd[7][4];     // [t-1][k]: type-t node of cell cx + k
-};
-
-template <bool SELF_FLOOR>
-__device__ __forceinline__ void load_cell_F(const float* __restrict__ f, const CellGeom& G,
-                                            uint32_t ny, uint32_t nx, int hl, int E_f, uint32_t cz,
-                                            uint32_t cy, uint32_t cx, CellF& F, uint32_t& fl) {
-  // level-grid coordinates -> field coordinates by << hl
+// The seven type coefficients of 4 consecutive cells (cx .. cx+3), computed
+// row by row: only the coarse row (Z0, Y0) and running sums of coarse rows
+// stay live, never all 48 fixed-point values at once.  visit(t, k, C8) gets
+// the coefficient of the type-t node of cell cx + k; types that do not exist
+// at this (cz, cy) are not visited.  Corner sums: with c_yz the coarse value
+// row at (Z0 + 2 dz, Y0 + 2 dy) (clamped), a = c_00 + c_01, d = c_00 + c_10,
+// b = a + c_10 + c_11; a type's corners along x are entries k and k + 1.
+template <bool SELF_FLOOR, typename V>
+__device__ __forceinline__ void cells_visit(const float* __restrict__ f, const CellGeom& G,
+                                            uint32_t ny, uint32_t nx, int hl, int E_f,
+                                            uint32_t cz, uint32_t cy, uint32_t cx, uint32_t& fl,
+                                            V&& visit) {
   const uint32_t Z0 = 2 * cz, Y0 = 2 * cy, X0 = 2 * cx;
   const bool hz = Z0 + 1 < G.g[0], hy = Y0 + 1 < G.g[1];
-  const uint32_t Z1 = hz ? Z0 + 1 : Z0, Y1 = hy ? Y0 + 1 : Y0;
   const uint32_t Z2 = Z0 + 2 < G.g[0] ? Z0 + 2 : Z0, Y2 = Y0 + 2 < G.g[1] ? Y0 + 2 : Y0;
   const uint32_t Xe = X0 + 8 < G.g[2] ? X0 + 8 : X0 + 6;
   uint32_t ign = 0;
-#pragma unroll
-  for (int t = 0; t < 7; t++)
-#pragma unroll
-    for (int k = 0; k < 4; k++) F.nd[t][k] = 0;
-  if (hl == 0) {  // finest level: 2 x 16-byte loads give the 8 values of a row segment
-    uint32_t& sf0 = SELF_FLOOR ? fl : ign;
-    auto row8 = [&](uint32_t z, uint32_t y, float v[8]) {
-      const float4* r4 = reinterpret_cast<const float4*>(f + ((size_t)z * ny + y) * nx + X0);
-      const float4 a = __ldg(r4), b = __ldg(r4 + 1);
-      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    };
-    float v[8];
-    const uint32_t zz0[2] = {Z0, Z2}, yy0[2] = {Y0, Y2};
-#pragma unroll
-    for (int a = 0; a < 2; a++)
-#pragma unroll
-      for (int b = 0; b < 2; b++) {
-        row8(zz0[a], yy0[b], v);
-#pragma unroll
-        for (int i = 0; i < 4; i++) F.co[a][b][i] = fixed_point(v[2 * i], E_f, ign);
-        F.co[a][b][4] = fixed_point(__ldg(f + ((size_t)zz0[a] * ny + yy0[b]) * nx + Xe), E_f, ign);
-        if (a == 0 && b == 0)
-#pragma unroll
-          for (int k = 0; k < 4; k++) F.nd[0][k] = fixed_point(v[2 * k + 1], E_f, sf0);
-      }
-    if (hy) {
-      row8(Z0, Y1, v);
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        F.nd[1][k] = fixed_point(v[2 * k], E_f, sf0);
-        F.nd[2][k] = fixed_point(v[2 * k + 1], E_f, sf0);
-      }
-    }
-    if (hz) {
-      row8(Z1, Y0, v);
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        F.nd[3][k] = fixed_point(v[2 * k], E_f, sf0);
-        F.nd[4][k] = fixed_point(v[2 * k + 1], E_f, sf0);
-      }
-    }
-    if (hz && hy) {
-      row8(Z1, Y1, v);
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        F.nd[5][k] = fixed_point(v[2 * k], E_f, sf0);
-        F.nd[6][k] = fixed_point(v[2 * k + 1], E_f, sf0);
-      }
-    }
-    return;
-  }
-  auto row = [&](uint32_t z, uint32_t y) {
-    return f + ((size_t)(z << hl) * ny + (y << hl)) * nx;
-  };
-  auto ld = [&](const float* r, uint32_t x) { return __ldg(r + ((size_t)x << hl)); };
-  const uint32_t zz[2] = {Z0, Z2}, yy[2] = {Y0, Y2};
-#pragma unroll
-  for (int a = 0; a < 2; a++)
-#pragma unroll
-    for (int b = 0; b < 2; b++) {
-      const float* r = row(zz[a], yy[b]);
-#pragma unroll
-      for (int i = 0; i < 4; i++) F.co[a][b][i] = fixed_point(ld(r, X0 + 2 * i), E_f, ign);
-      F.co[a][b][4] = fixed_point(ld(r, Xe), E_f, ign);
-    }
   uint32_t& sf = SELF_FLOOR ? fl : ign;
-  {
-    const float* r = row(Z0, Y0);
+  // values at x = X0 .. X0 + 7 of level-grid row (z, y); odd x only if asked
+  auto seg = [&](uint32_t z, uint32_t y, float v[8], bool odd) {
+    const float* r = f + ((size_t)(z << hl) * ny + (y << hl)) * nx;
+    if (hl == 0) {  // finest level: two 16-byte loads
+      const float4 p = __ldg(reinterpret_cast<const float4*>(r + X0));
+      const float4 q = __ldg(reinterpret_cast<const float4*>(r + X0) + 1);
+      v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+      v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 4; k++) F.nd[0][k] = fixed_point(ld(r, X0 + 2 * k + 1), E_f, sf);
-  }
+      for (int i = 0; i < 8; i++)
+        if (!(i & 1) || odd) v[i] = __ldg(r + ((size_t)(X0 + i) << hl));
+    }
+  };
+  // the coarse values of a row: x = X0, X0 + 2, X0 + 4, X0 + 6 and the clamped X0 + 8
+  auto coarse = [&](uint32_t z, uint32_t y, int64_t c[5]) {
+    float v[8];
+    seg(z, y, v, false);
+#pragma unroll
+    for (int i = 0; i < 4; i++) c[i] = fixed_point(v[2 * i], E_f, ign);
+    c[4] = fixed_point(__ldg(f + ((size_t)(z << hl) * ny + (y << hl)) * nx + ((size_t)Xe << hl)), E_f,
+                       ign);
+  };
+  float v[8];
+  int64_t c0[5], a[5];
+  coarse(Z0, Y0, c0);
+  seg(Z0, Y0, v, true);  // t = 1 nodes at odd x (the even ones are c0)
+#pragma unroll
+  for (int k = 0; k < 4; k++) visit(1, k, (2 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 4);
   if (hy) {
-    const float* r = row(Z0, Y1);
+    coarse(Z0, Y2, a);
+#pragma unroll
+    for (int i = 0; i < 5; i++) a[i] += c0[i];
+    seg(Z0, Y0 + 1, v, true);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      F.nd[1][k] = fixed_point(ld(r, X0 + 2 * k), E_f, sf);
-      F.nd[2][k] = fixed_point(ld(r, X0 + 2 * k + 1), E_f, sf);
+      visit(2, k, (2 * fixed_point(v[2 * k], E_f, sf) - a[k]) * 4);
+      visit(3, k, (4 * fixed_point(v[2 * k + 1], E_f, sf) - (a[k] + a[k + 1])) * 2);
     }
   }
   if (hz) {
-    const float* r = row(Z1, Y0);
+    int64_t c1[5];
+    coarse(Z2, Y0, c1);
+#pragma unroll
+    for (int i = 0; i < 5; i++) c0[i] += c1[i];  // c0 becomes d
+    seg(Z0 + 1, Y0, v, true);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      F.nd[3][k] = fixed_point(ld(r, X0 + 2 * k), E_f, sf);
-      F.nd[4][k] = fixed_point(ld(r, X0 + 2 * k + 1), E_f, sf);
+      visit(4, k, (2 * fixed_point(v[2 * k], E_f, sf) - c0[k]) * 4);
+      visit(5, k, (4 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 2);
     }
-  }
-  if (hz && hy) {
-    const float* r = row(Z1, Y1);
+    if (hy) {
+      int64_t c3[5];
+      coarse(Z2, Y2, c3);
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-      F.nd[5][k] = fixed_point(ld(r, X0 + 2 * k), E_f, sf);
-      F.nd[6][k] = fixed_point(ld(r, X0 + 2 * k + 1), E_f, sf);
+      for (int i = 0; i < 5; i++) a[i] += c1[i] + c3[i];  // a becomes b
+      seg(Z0 + 1, Y0 + 1, v, true);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        visit(6, k, (4 * fixed_point(v[2 * k], E_f, sf) - a[k]) * 2);
+        visit(7, k, 8 * fixed_point(v[2 * k + 1], E_f, sf) - (a[k] + a[k + 1]));
+      }
     }
   }
-}
-
-// C8 of the 7 type nodes of cell k (types that do not exist are skipped by the caller)
-__device__ __forceinline__ void cell_c8(const CellF& F, int k, int64_t c8[7]) {
-  const int64_t c000 = F.co[0][0][k], c001 = F.co[0][0][k + 1];
-  const int64_t c010 = F.co[0][1][k], c011 = F.co[0][1][k + 1];
-  const int64_t c100 = F.co[1][0][k], c101 = F.co[1][0][k + 1];
-  const int64_t c110 = F.co[1][1][k], c111 = F.co[1][1][k + 1];
-  const int64_t sx0 = c000 + c001, sx1 = c010 + c011, sx2 = c100 + c101, sx3 = c110 + c111;
-  // D = k F - sum of corners, C8 = D * 8 / k
-  c8[0] = (2 * F.nd[0][k] - sx0) * 4;                          // t=1 (x)
-  c8[1] = (2 * F.nd[1][k] - (c000 + c010)) * 4;                // t=2 (y)
-  c8[2] = (4 * F.nd[2][k] - (sx0 + sx1)) * 2;                  // t=3 (x, y)
-  c8[3] = (2 * F.nd[3][k] - (c000 + c100)) * 4;                // t=4 (z)
-  c8[4] = (4 * F.nd[4][k] - (sx0 + sx2)) * 2;                  // t=5 (x, z)
-  c8[5] = (4 * F.nd[5][k] - (c000 + c010 + c100 + c110)) * 2;  // t=6 (y, z)
-  c8[6] = 8 * F.nd[6][k] - (sx0 + sx1 + sx2 + sx3);            // t=7 (x, y, z)
 }
 
 __device__ __forceinline__ bool type_exists(int t, bool hz, bool hy) {
@@ -205,20 +155,10 @@ __device__ __forceinline__ void cells_levelmax_tile(const float* __restrict__ f,
   tile_origin(G, tile, cz, cy0, x0);
   const uint32_t cy = cy0 + i / per_row, cx = x0 + 4 * (i % per_row);
   if (cy >= G.c[1]) return;
-  CellF F;
-  load_cell_F<true>(f, G, ny, nx, hl, E_f, cz, cy, cx, F, fl);
-  const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    int64_t c8[7];
-    cell_c8(F, k, c8);
-#pragma unroll
-    for (int t = 1; t <= 7; t++)
-      if (type_exists(t, hz, hy)) {
-        const uint64_t m = umag(c8[t - 1]);
-        mx = m > mx ? m : mx;
-      }
-  }
+  cells_visit<true>(f, G, ny, nx, hl, E_f, cz, cy, cx, fl, [&](int, int, int64_t c8) {
+    const uint64_t m = umag(c8);
+    mx = m > mx ? m : mx;
+  });
 }
 
 __device__ __forceinline__ void cells_levelmax_flush(FieldMeta* meta, int level, uint64_t mx,
@@ -231,7 +171,7 @@ __device__ __forceinline__ void cells_levelmax_flush(FieldMeta* meta, int level,
   }
 }
 
-__global__ void __launch_bounds__(256, 2) k_cells_levelmax(const float* __restrict__ f, uint32_t ny,
+__global__ void __launch_bounds__(256, 4) k_cells_levelmax(const float* __restrict__ f, uint32_t ny,
                                                         uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                         FieldMeta* meta) {
   if (meta->status) return;
@@ -268,33 +208,20 @@ __device__ __forceinline__ void cells_encode_tile(const float* __restrict__ f, c
   {  // phase cells
     const uint32_t r = i / per_row, xl = 4 * (i % per_row), cy = cy0 + r, cx = x0 + xl;
     if (cy < G.c[1]) {
-      CellF F;
-      uint32_t ign = 0;
-      load_cell_F<false>(f, G, ny, nx, hl, E_f, cz, cy, cx, F, ign);
-      const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
       const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        int64_t c8[7];
-        cell_c8(F, k, c8);
-#pragma unroll
-        for (int t = 1; t <= 7; t++) {
-          uint32_t q = 0;
-          uint8_t sg = 0;
-          if (type_exists(t, hz, hy)) {
-            const uint64_t m = umag(c8[t - 1]);
-            sg = c8[t - 1] < 0;
-            if (bl == 0) q = 0;
-            else if (bl <= 32) q = (uint32_t)(m << (32 - bl));
-            else {
-              q = (uint32_t)(m >> (bl - 32));
-              low |= m & ((1ull << (bl - 32)) - 1ull);
-            }
-          }
-          s_q[t - 1][rw][b0 + k] = q;
-          s_s[t - 1][rw][b0 + k] = sg;
+      uint32_t ign = 0;
+      cells_visit<false>(f, G, ny, nx, hl, E_f, cz, cy, cx, ign, [&](int t, int k, int64_t c8) {
+        const uint64_t m = umag(c8);
+        uint32_t q;
+        if (bl == 0) q = 0;
+        else if (bl <= 32) q = (uint32_t)(m << (32 - bl));
+        else {
+          q = (uint32_t)(m >> (bl - 32));
+          low |= m & ((1ull << (bl - 32)) - 1ull);
         }
-      }
+        s_q[t - 1][rw][b0 + k] = q;
+        s_s[t - 1][rw][b0 + k] = c8 < 0;
+      });
     }
   }
   __syncthreads();
@@ -324,7 +251,7 @@ __device__ __forceinline__ void cells_lowbits_flush(FieldMeta* meta, int level, 
     atomicOr((unsigned long long*)&meta->lowbits[level], (unsigned long long)low);
 }
 
-__global__ void __launch_bounds__(256, 2) k_cells_encode(const float* __restrict__ f, uint32_t ny,
+__global__ void __launch_bounds__(256, 3) k_cells_encode(const float* __restrict__ f, uint32_t ny,
                                                       uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                       FieldMeta* meta, uint32_t* __restrict__ planes) {
   __shared__ CellQ s_q;
@@ -351,7 +278,8 @@ static int nsm() {
 void launch_cells_levelmax(const float* f, const uint64_t dims[3], const LevelDesc* Ld,
                            const LevelDesc& Lh, FieldMeta* meta, cstream s) {
   const CellGeom G = cell_geom(Lh);
-  uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 8;
+  // one wave of resident CTAs (4 per SM), each looping over tiles
+  uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 4;
   if (blocks > cap) blocks = cap;
   if (!blocks) return;
   hp::note_launch(), k_cells_levelmax<<<blocks, 256, 0, s>>>(f, (uint32_t)dims[1], (uint32_t)dims[2],
@@ -361,7 +289,7 @@ void launch_cells_levelmax(const float* f, const uint64_t dims[3], const LevelDe
 void launch_cells_encode(const float* f, const uint64_t dims[3], const LevelDesc* Ld,
                          const LevelDesc& Lh, FieldMeta* meta, uint32_t* planes, cstream s) {
   const CellGeom G = cell_geom(Lh);
-  uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 6;
+  uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 3;  // one wave, 3 CTAs per SM
   if (blocks > cap) blocks = cap;
   if (!blocks) return;
   hp::note_launch(), k_cells_encode<<<blocks, 256, 0, s>>>(f, (uint32_t)dims[1], (uint32_t)dims[2],
@@ -406,92 +334,89 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
     }
   }
   __syncthreads();
-  {  // phase cells
+  {  // phase cells: one output row (2cz + oz, 2cy + oy) at a time
     const uint32_t r = i / per_row, xl = 4 * (i % per_row), cy = cy0 + r, cx = x0 + xl;
     if (cy < G.c[1]) {
       const bool hz = 2 * cz + 1 < G.g[0], hy = 2 * cy + 1 < G.g[1];
-      // coarse corners: rows (cz | cz+1 clamped) x (cy | cy+1 clamped), x = cx .. cx+4 clamped
+      // coarse rows (cz | cz+1 clamped) x (cy | cy+1 clamped), x = cx .. cx+4 clamped
       const uint32_t cz1 = 2 * cz + 2 < G.g[0] ? cz + 1 : cz, cy1 = 2 * cy + 2 < G.g[1] ? cy + 1 : cy;
       const uint32_t xe = 2 * cx + 8 < G.g[2] ? cx + 4 : cx + 3;
-      int64_t C[2][2][5];
-      const uint32_t zz[2] = {cz, cz1}, yy[2] = {cy, cy1};
-#pragma unroll
-      for (int a = 0; a < 2; a++)
-#pragma unroll
-        for (int b = 0; b < 2; b++) {
-          const int64_t* row = coarse + ((size_t)zz[a] * gc1 + yy[b]) * gc2;
-          // cx is a multiple of 4 and gc2 of 32: two aligned 16-byte loads
-          const longlong2 p0 = __ldg(reinterpret_cast<const longlong2*>(row + cx));
-          const longlong2 p1 = __ldg(reinterpret_cast<const longlong2*>(row + cx) + 1);
-          C[a][b][0] = p0.x;
-          C[a][b][1] = p0.y;
-          C[a][b][2] = p1.x;
-          C[a][b][3] = p1.y;
-          C[a][b][4] = __ldg(row + xe);
-        }
       const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
-      // one output row (2cz+oz, 2cy+oy) at a time: its even-x nodes are type
-      // te = 2 oy + 4 oz (te = 0: the coarse node itself), its odd-x nodes te + 1
+      auto load = [&](uint32_t z, uint32_t y, int64_t c[5]) {
+        const int64_t* row = coarse + ((size_t)z * gc1 + y) * gc2;
+        // cx is a multiple of 4 and gc2 of 32: two aligned 16-byte loads
+        const longlong2 p0 = __ldg(reinterpret_cast<const longlong2*>(row + cx));
+        const longlong2 p1 = __ldg(reinterpret_cast<const longlong2*>(row + cx) + 1);
+        c[0] = p0.x;
+        c[1] = p0.y;
+        c[2] = p1.x;
+        c[3] = p1.y;
+        c[4] = __ldg(row + xe);
+      };
+      auto c8of = [&](int t, int kk) -> int64_t {
+        const uint32_t qh = s_q[t - 1][rw][b0 + kk];
+        const bool neg = (s_sw[t - 1][rw] >> (b0 + kk)) & 1u;
+        uint64_t mag;
+        if (bl == 0) mag = 0;
+        else if (bl <= 32) mag = qh >> (32 - bl);
+        else mag = (uint64_t)qh << (bl - 32);
+        return neg ? -(int64_t)mag : (int64_t)mag;
+      };
+      // Row (oz, oy): even-x nodes are type te = 2 oy + 4 oz (te = 0: the coarse
+      // node itself), odd-x nodes te + 1.  e[kk] is the sum of the row's coarse
+      // corners along y and z; a type with n odd axes has
+      // X = floor((c8 2^n + 8 S) / 2^(3+n)) = (c8 + S 2^(3-n)) >> 3.
+      auto emit = [&](int oz, int oy, const int64_t e[5]) {
+        const int te = 2 * oy + 4 * oz, ne = __popc(te), no = ne + 1;
+        int64_t V[8];
 #pragma unroll
-      for (int oz = 0; oz < 2; oz++)
-#pragma unroll
-        for (int oy = 0; oy < 2; oy++) {
-          if ((oz && !hz) || (oy && !hy)) continue;
-          const int te = 2 * oy + 4 * oz;
-          int64_t V[8];
-#pragma unroll
-          for (int kk = 0; kk < 4; kk++) {
-#pragma unroll
-            for (int par = 0; par < 2; par++) {
-              const int t = te + par;
-              int64_t X;
-              if (t == 0) {
-                X = C[0][0][kk];
-              } else {
-                // corner sum of type t: the corners along its odd axes
-                int64_t S = 0;
-#pragma unroll
-                for (int dz = 0; dz < 2; dz++)
-#pragma unroll
-                  for (int dy = 0; dy < 2; dy++)
-#pragma unroll
-                    for (int dx = 0; dx < 2; dx++) {
-                      if ((dz && !(t & 4)) || (dy && !(t & 2)) || (dx && !(t & 1))) continue;
-                      S += C[dz][dy][kk + dx];
-                    }
-                const uint32_t qh = s_q[t - 1][rw][b0 + kk];
-                const bool neg = (s_sw[t - 1][rw] >> (b0 + kk)) & 1u;
-                uint64_t mag;
-                if (bl == 0) mag = 0;
-                else if (bl <= 32) mag = qh >> (32 - bl);
-                else mag = (uint64_t)qh << (bl - 32);
-                const int64_t c8 = neg ? -(int64_t)mag : (int64_t)mag;
-                const int nodd = __popc(t);
-                X = (c8 * ((int64_t)1 << nodd) + 8 * S) >> (3 + nodd);
-              }
-              V[2 * kk + par] = X;
-            }
-          }
-          const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
-          if (FINAL) {
-            float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base);
-            d4[0] = make_float4(out_f32(V[0], E_f), out_f32(V[1], E_f), out_f32(V[2], E_f),
-                                out_f32(V[3], E_f));
-            d4[1] = make_float4(out_f32(V[4], E_f), out_f32(V[5], E_f), out_f32(V[6], E_f),
-                                out_f32(V[7], E_f));
-          } else {
-            longlong2* d2 = reinterpret_cast<longlong2*>(reinterpret_cast<int64_t*>(dst) + base);
-#pragma unroll
-            for (int kk = 0; kk < 4; kk++) d2[kk] = make_longlong2(V[2 * kk], V[2 * kk + 1]);
-          }
+        for (int kk = 0; kk < 4; kk++) {
+          V[2 * kk] = te == 0 ? e[kk] : (c8of(te, kk) + e[kk] * (8 >> ne)) >> 3;
+          V[2 * kk + 1] = (c8of(te + 1, kk) + (e[kk] + e[kk + 1]) * (8 >> no)) >> 3;
         }
+        const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
+        if (FINAL) {
+          float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base);
+          d4[0] = make_float4(out_f32(V[0], E_f), out_f32(V[1], E_f), out_f32(V[2], E_f),
+                              out_f32(V[3], E_f));
+          d4[1] = make_float4(out_f32(V[4], E_f), out_f32(V[5], E_f), out_f32(V[6], E_f),
+                              out_f32(V[7], E_f));
+        } else {
+          longlong2* d2 = reinterpret_cast<longlong2*>(reinterpret_cast<int64_t*>(dst) + base);
+#pragma unroll
+          for (int kk = 0; kk < 4; kk++) d2[kk] = make_longlong2(V[2 * kk], V[2 * kk + 1]);
+        }
+      };
+      int64_t c0[5], a[5];
+      load(cz, cy, c0);
+      emit(0, 0, c0);
+      if (hy) {
+        load(cz, cy1, a);
+#pragma unroll
+        for (int q = 0; q < 5; q++) a[q] += c0[q];
+        emit(0, 1, a);
+      }
+      if (hz) {
+        int64_t c1[5];
+        load(cz1, cy, c1);
+        if (hy) {
+          int64_t c3[5];
+          load(cz1, cy1, c3);
+#pragma unroll
+          for (int q = 0; q < 5; q++) a[q] += c1[q] + c3[q];  // all four rows
+        }
+#pragma unroll
+        for (int q = 0; q < 5; q++) c0[q] += c1[q];  // rows along z
+        emit(1, 0, c0);
+        if (hy) emit(1, 1, a);
+      }
     }
   }
   __syncthreads();
 }
 
 template <bool FINAL>
-__global__ void __launch_bounds__(256, 3) k_cells_recompose(const uint32_t* __restrict__ planes,
+__global__ void __launch_bounds__(256, 4) k_cells_recompose(const uint32_t* __restrict__ planes,
                                                          const FieldMeta* __restrict__ meta,
                                                          const LevelDesc* __restrict__ Lp,
                                                          const int64_t* __restrict__ coarse,
@@ -511,7 +436,7 @@ void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const
                             const LevelDesc& Lh, const int64_t* coarse, void* dst, int final,
                             cstream s) {
   const CellGeom G = cell_geom(Lh);
-  uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 6;
+  uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 4;  // one wave, 4 CTAs per SM
   if (blocks > cap) blocks = cap;
   if (!blocks) return;
   if (final)
@@ -524,7 +449,7 @@ void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const
 uint32_t cell_tiles(const LevelDesc& L) { return cell_geom(L).ntiles; }
 
 // unit = one tile of 1024 cells of one (job, level) entry
-__global__ void __launch_bounds__(256, 2) kb_cells_levelmax(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 4) kb_cells_levelmax(const BatchJob* __restrict__ jobs,
                                                          const LevelRef* __restrict__ refs,
                                                          const uint32_t* __restrict__ unit0,
                                                          uint32_t nrefs, uint32_t total) {
@@ -544,7 +469,7 @@ __global__ void __launch_bounds__(256, 2) kb_cells_levelmax(const BatchJob* __re
   }
 }
 
-__global__ void __launch_bounds__(256, 2) kb_cells_encode(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 3) kb_cells_encode(const BatchJob* __restrict__ jobs,
                                                        const LevelRef* __restrict__ refs,
                                                        const uint32_t* __restrict__ unit0,
                                                        uint32_t nrefs, uint32_t total) {
@@ -568,7 +493,7 @@ __global__ void __launch_bounds__(256, 2) kb_cells_encode(const BatchJob* __rest
   }
 }
 
-__global__ void __launch_bounds__(256, 3) kb_cells_recompose(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 4) kb_cells_recompose(const BatchJob* __restrict__ jobs,
                                                           const LevelRef* __restrict__ refs,
                                                           const uint32_t* __restrict__ unit0,
                                                           uint32_t nrefs, uint32_t total) {

@@ -69,7 +69,8 @@ __device__ __forceinline__ void levelmax_tile(const FieldView<T>& v, const Level
   const int lane = threadIdx.x & 31;
   uint64_t mx = 0;
   uint32_t fl = 0;
-  for (int r = 0; r < 32; r++) {
+#pragma unroll 4
+  for (int r = 0; r < 32; r++) {  // unrolled: several rows' loads in flight
     uint32_t j = base + r * 32 + lane;
     if (j < L.n) {
       uint64_t m = umag(level_c8(v, L, j, fl));
@@ -172,7 +173,8 @@ __device__ __forceinline__ void encode_tile(const FieldView<T>& v, const LevelDe
   const int bl = meta->bl[L.level];
   uint64_t low = 0;
   uint32_t my_sign = 0, fl = 0;
-  // phase A: lane = node
+  // phase A: lane = node (unrolled: several rows' loads in flight)
+#pragma unroll 4
   for (int r = 0; r < 32; r++) {
     uint32_t j = base + r * 32 + lane;
     uint64_t q = 0;

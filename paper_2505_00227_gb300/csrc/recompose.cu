@@ -113,6 +113,9 @@ __device__ __forceinline__ void recompose_tile(const uint32_t* __restrict__ P, c
     sgn[lane] = k > 0 ? P[wi] : 0u;
   }
   __syncwarp();
+  // rows are independent: unrolled so that the coarse loads of several rows
+  // are in flight together
+#pragma unroll 4
   for (int r = 0; r < 32; r++) {
     const uint32_t j = base + r * 32 + lane;
     if (j < L.n) {
