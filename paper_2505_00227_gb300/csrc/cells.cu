@@ -51,9 +51,9 @@ bool cell_path_ok(const LevelDesc& L, int B) {
 // ------------------------------------------------------------ refactor side
 // The seven type coefficients of 4 consecutive cells (cx .. cx+3), computed
 // row by row: only the coarse row (Z0, Y0) and running sums of coarse rows
-// stay live, never all 48 fixed-point values at once.  visit(t, k, C8) gets
-// the coefficient of the type-t node of cell cx + k; types that do not exist
-// at this (cz, cy) are not visited.  Corner sums: with c_yz the coarse value
+// stay live, never all 48 fixed-point values at once.  visit(t, c8) gets the
+// coefficients c8[k] of the type-t nodes of cells cx + k, k = 0..3; types
+// that do not exist at this (cz, cy) are not visited.  Corner sums: with c_yz the coarse value
 // row at (Z0 + 2 dz, Y0 + 2 dy) (clamped), a = c_00 + c_01, d = c_00 + c_10,
 // b = a + c_10 + c_11; a type's corners along x are entries k and k + 1.
 template <bool SELF_FLOOR, typename V>
@@ -91,21 +91,23 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
                        ign);
   };
   float v[8];
-  int64_t c0[5], a[5];
+  int64_t c0[5], a[5], c[4];
   coarse(Z0, Y0, c0);
   seg(Z0, Y0, v, true);  // t = 1 nodes at odd x (the even ones are c0)
 #pragma unroll
-  for (int k = 0; k < 4; k++) visit(1, k, (2 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 4);
+  for (int k = 0; k < 4; k++) c[k] = (2 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 4;
+  visit(1, c);
   if (hy) {
     coarse(Z0, Y2, a);
 #pragma unroll
     for (int i = 0; i < 5; i++) a[i] += c0[i];
     seg(Z0, Y0 + 1, v, true);
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-      visit(2, k, (2 * fixed_point(v[2 * k], E_f, sf) - a[k]) * 4);
-      visit(3, k, (4 * fixed_point(v[2 * k + 1], E_f, sf) - (a[k] + a[k + 1])) * 2);
-    }
+    for (int k = 0; k < 4; k++) c[k] = (2 * fixed_point(v[2 * k], E_f, sf) - a[k]) * 4;
+    visit(2, c);
+#pragma unroll
+    for (int k = 0; k < 4; k++) c[k] = (4 * fixed_point(v[2 * k + 1], E_f, sf) - (a[k] + a[k + 1])) * 2;
+    visit(3, c);
   }
   if (hz) {
     int64_t c1[5];
@@ -114,10 +116,11 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
     for (int i = 0; i < 5; i++) c0[i] += c1[i];  // c0 becomes d
     seg(Z0 + 1, Y0, v, true);
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-      visit(4, k, (2 * fixed_point(v[2 * k], E_f, sf) - c0[k]) * 4);
-      visit(5, k, (4 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 2);
-    }
+    for (int k = 0; k < 4; k++) c[k] = (2 * fixed_point(v[2 * k], E_f, sf) - c0[k]) * 4;
+    visit(4, c);
+#pragma unroll
+    for (int k = 0; k < 4; k++) c[k] = (4 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 2;
+    visit(5, c);
     if (hy) {
       int64_t c3[5];
       coarse(Z2, Y2, c3);
@@ -125,10 +128,11 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
       for (int i = 0; i < 5; i++) a[i] += c1[i] + c3[i];  // a becomes b
       seg(Z0 + 1, Y0 + 1, v, true);
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        visit(6, k, (4 * fixed_point(v[2 * k], E_f, sf) - a[k]) * 2);
-        visit(7, k, 8 * fixed_point(v[2 * k + 1], E_f, sf) - (a[k] + a[k + 1]));
-      }
+      for (int k = 0; k < 4; k++) c[k] = (4 * fixed_point(v[2 * k], E_f, sf) - a[k]) * 2;
+      visit(6, c);
+#pragma unroll
+      for (int k = 0; k < 4; k++) c[k] = 8 * fixed_point(v[2 * k + 1], E_f, sf) - (a[k] + a[k + 1]);
+      visit(7, c);
     }
   }
 }
@@ -155,9 +159,12 @@ __device__ __forceinline__ void cells_levelmax_tile(const float* __restrict__ f,
   tile_origin(G, tile, cz, cy0, x0);
   const uint32_t cy = cy0 + i / per_row, cx = x0 + 4 * (i % per_row);
   if (cy >= G.c[1]) return;
-  cells_visit<true>(f, G, ny, nx, hl, E_f, cz, cy, cx, fl, [&](int, int, int64_t c8) {
-    const uint64_t m = umag(c8);
-    mx = m > mx ? m : mx;
+  cells_visit<true>(f, G, ny, nx, hl, E_f, cz, cy, cx, fl, [&](int, const int64_t* c8) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint64_t m = umag(c8[k]);
+      mx = m > mx ? m : mx;
+    }
   });
 }
 
@@ -186,8 +193,12 @@ __global__ void __launch_bounds__(256, 4) k_cells_levelmax(const float* __restri
 }
 
 // quantize + Algorithm 1: one tile of 1024 cells (all 7 types)
-typedef uint32_t CellQ[7][32][33];   // [type][row * NW + word][cell within word]
-typedef uint8_t CellS[7][32][32];    // sign per cell
+// Shared staging of one tile: aligned integers [type][row * NW + word][cell
+// within word], rows of 36 words so that the 16-byte accesses of both phases
+// (a thread's 4 cells; a word's 32 cells as 8 vectors) are conflict-free; and
+// the sign bits, one 4-bit nibble per 4 cells.
+typedef uint32_t CellQ[7][32][36];
+typedef uint8_t CellS[7][32][8];
 
 __device__ __forceinline__ void cells_zero_padding(const LevelDesc& L, uint32_t* P) {
   // the padding words past the last node of every plane are zero
@@ -210,17 +221,21 @@ __device__ __forceinline__ void cells_encode_tile(const float* __restrict__ f, c
     if (cy < G.c[1]) {
       const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
       uint32_t ign = 0;
-      cells_visit<false>(f, G, ny, nx, hl, E_f, cz, cy, cx, ign, [&](int t, int k, int64_t c8) {
-        const uint64_t m = umag(c8);
-        uint32_t q;
-        if (bl == 0) q = 0;
-        else if (bl <= 32) q = (uint32_t)(m << (32 - bl));
-        else {
-          q = (uint32_t)(m >> (bl - 32));
-          low |= m & ((1ull << (bl - 32)) - 1ull);
+      cells_visit<false>(f, G, ny, nx, hl, E_f, cz, cy, cx, ign, [&](int t, const int64_t* c8) {
+        uint32_t q[4], nib = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const uint64_t m = umag(c8[k]);
+          if (bl == 0) q[k] = 0;
+          else if (bl <= 32) q[k] = (uint32_t)(m << (32 - bl));
+          else {
+            q[k] = (uint32_t)(m >> (bl - 32));
+            low |= m & ((1ull << (bl - 32)) - 1ull);
+          }
+          nib |= (c8[k] < 0 ? 1u : 0u) << k;
         }
-        s_q[t - 1][rw][b0 + k] = q;
-        s_s[t - 1][rw][b0 + k] = c8 < 0;
+        *reinterpret_cast<uint4*>(&s_q[t - 1][rw][b0]) = make_uint4(q[0], q[1], q[2], q[3]);
+        s_s[t - 1][rw][b0 / 4] = (uint8_t)nib;
       });
     }
   }
@@ -231,11 +246,21 @@ __device__ __forceinline__ void cells_encode_tile(const float* __restrict__ f, c
     if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
       uint32_t a[32];
 #pragma unroll
-      for (int b = 0; b < 32; b++) a[b] = s_q[t - 1][rw][b];
+      for (int j = 0; j < 8; j++) {
+        const uint4 x = *reinterpret_cast<const uint4*>(&s_q[t - 1][rw][4 * j]);
+        a[4 * j] = x.x;
+        a[4 * j + 1] = x.y;
+        a[4 * j + 2] = x.z;
+        a[4 * j + 3] = x.w;
+      }
       transpose32(a);
+      const uint2 nb = *reinterpret_cast<const uint2*>(&s_s[t - 1][rw][0]);
       uint32_t sw = 0;
 #pragma unroll
-      for (int b = 0; b < 32; b++) sw |= (uint32_t)s_s[t - 1][rw][b] << b;
+      for (int j = 0; j < 4; j++) {
+        sw |= ((nb.x >> (8 * j)) & 0xfu) << (4 * j);
+        sw |= ((nb.y >> (8 * j)) & 0xfu) << (16 + 4 * j);
+      }
       const uint32_t word = (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
       P[word] = sw;
 #pragma unroll
@@ -329,7 +354,9 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       for (int p = 0; p < 32; p++) a[31 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
       if (k) transpose32(a);
 #pragma unroll
-      for (int b = 0; b < 32; b++) s_q[t - 1][rw][b] = a[b];
+      for (int j = 0; j < 8; j++)
+        *reinterpret_cast<uint4*>(&s_q[t - 1][rw][4 * j]) =
+            make_uint4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
       s_sw[t - 1][rw] = k ? __ldcs(P + word) : 0u;
     }
   }
@@ -353,14 +380,19 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
         c[3] = p1.y;
         c[4] = __ldg(row + xe);
       };
-      auto c8of = [&](int t, int kk) -> int64_t {
-        const uint32_t qh = s_q[t - 1][rw][b0 + kk];
-        const bool neg = (s_sw[t - 1][rw] >> (b0 + kk)) & 1u;
-        uint64_t mag;
-        if (bl == 0) mag = 0;
-        else if (bl <= 32) mag = qh >> (32 - bl);
-        else mag = (uint64_t)qh << (bl - 32);
-        return neg ? -(int64_t)mag : (int64_t)mag;
+      // c8 of the type-t nodes of the thread's 4 cells
+      auto c8of = [&](int t, int64_t c8[4]) {
+        const uint4 x = *reinterpret_cast<const uint4*>(&s_q[t - 1][rw][b0]);
+        const uint32_t qh[4] = {x.x, x.y, x.z, x.w};
+        const uint32_t sg = s_sw[t - 1][rw] >> b0;
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+          uint64_t mag;
+          if (bl == 0) mag = 0;
+          else if (bl <= 32) mag = qh[kk] >> (32 - bl);
+          else mag = (uint64_t)qh[kk] << (bl - 32);
+          c8[kk] = ((sg >> kk) & 1u) ? -(int64_t)mag : (int64_t)mag;
+        }
       };
       // Row (oz, oy): even-x nodes are type te = 2 oy + 4 oz (te = 0: the coarse
       // node itself), odd-x nodes te + 1.  e[kk] is the sum of the row's coarse
@@ -368,11 +400,13 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       // X = floor((c8 2^n + 8 S) / 2^(3+n)) = (c8 + S 2^(3-n)) >> 3.
       auto emit = [&](int oz, int oy, const int64_t e[5]) {
         const int te = 2 * oy + 4 * oz, ne = __popc(te), no = ne + 1;
-        int64_t V[8];
+        int64_t V[8], ce[4], co[4];
+        if (te != 0) c8of(te, ce);
+        c8of(te + 1, co);
 #pragma unroll
         for (int kk = 0; kk < 4; kk++) {
-          V[2 * kk] = te == 0 ? e[kk] : (c8of(te, kk) + e[kk] * (8 >> ne)) >> 3;
-          V[2 * kk + 1] = (c8of(te + 1, kk) + (e[kk] + e[kk + 1]) * (8 >> no)) >> 3;
+          V[2 * kk] = te == 0 ? e[kk] : (ce[kk] + e[kk] * (8 >> ne)) >> 3;
+          V[2 * kk + 1] = (co[kk] + (e[kk] + e[kk + 1]) * (8 >> no)) >> 3;
         }
         const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
         if (FINAL) {
@@ -493,7 +527,7 @@ __global__ void __launch_bounds__(256, 3) kb_cells_encode(const BatchJob* __rest
   }
 }
 
-__global__ void __launch_bounds__(256, 4) kb_cells_recompose(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 3) kb_cells_recompose(const BatchJob* __restrict__ jobs,
                                                           const LevelRef* __restrict__ refs,
                                                           const uint32_t* __restrict__ unit0,
                                                           uint32_t nrefs, uint32_t total) {
