@@ -163,8 +163,8 @@ HPMDR_API hpmdr_status hpmdr_handle_compact(hpmdr_ctx* ctx, hpmdr_handle* h);
 HPMDR_API hpmdr_status hpmdr_handle_drop_cache(hpmdr_ctx* ctx, hpmdr_handle* h);
 /* device bytes: resident = held until hpmdr_handle_free (streams, metadata,
  * and the planes of a handle that is not compact); cache = plane cache and
- * recompose scratch held now; cache_max = what they take once allocated.
- * Any pointer may be NULL. */
+ * recompose grids held now; cache_max = the most a retrieval holds (those
+ * plus its transient staging).  Any pointer may be NULL. */
 HPMDR_API hpmdr_status hpmdr_handle_memory(const hpmdr_handle* h, uint64_t* resident, uint64_t* cache,
                                            uint64_t* cache_max);
 

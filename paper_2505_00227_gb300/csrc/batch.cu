@@ -34,10 +34,15 @@ struct Tuning {
 };
 
 struct Round {
-  uint32_t ncells = 0, ngen = 0;
-  uint32_t cells_total = 0, copy_total = 0, level_total = 0;
+  uint32_t ncells = 0, ngen = 0, ngc = 0;
+  uint32_t cells_total = 0, copy_total = 0, level_total = 0, unpack_total = 0, gc_total = 0;
   size_t o_cells_refs = 0, o_cells_u0 = 0, o_gen_refs = 0, o_copy_u0 = 0, o_level_u0 = 0;
+  size_t o_gc_refs = 0, o_unpack_u0 = 0, o_gc_u0 = 0;
 };
+
+uint32_t gcell_units(const LevelDesc& D) {  // 256 cells per unit
+  return (uint32_t)(((uint64_t)D.gc[0] * D.gc[1] * D.gc[2] + 255) / 256);
+}
 
 // a device table section: bytes appended to a host image, 256-byte aligned
 struct Image {
@@ -91,6 +96,9 @@ struct hpmdr_batch {
   // unit tables (offsets into d_tab) and totals
   size_t o_stats = 0, o_gen = 0, o_chunks = 0, o_groups = 0, o_cells_refs = 0, o_cells_u0 = 0;
   uint32_t t_stats = 0, t_gen = 0, t_chunks = 0, t_groups = 0, t_cells = 0, n_cells_refs = 0;
+  size_t o_gc_refs = 0, o_gc_u0 = 0, o_pack_u0 = 0;
+  uint32_t n_gc_refs = 0, t_gc = 0, t_pack = 0;
+  std::vector<std::vector<uint64_t>> soff;  // per job and level: staging offset
   std::vector<Round> rounds;
   cudaGraphExec_t g_ref = nullptr, g_ret = nullptr;
   uint64_t k_ref = 0, k_ret = 0;  // kernel launches per graph
@@ -138,23 +146,34 @@ struct hpmdr_batch {
   hpmdr_status build_tables() {
     Image im;
     std::vector<uint32_t> u_stats(n), u_gen(n), u_chunks(n), u_groups(n);
-    std::vector<LevelRef> cells;
-    std::vector<uint32_t> u_cells;
+    std::vector<LevelRef> cells, gcs;
+    std::vector<uint32_t> u_cells, u_gc, u_pack;
+    soff.assign(n, {});
     for (uint32_t j = 0; j < n; j++) {
       const hpmdr_handle* H = hs[j].get();
       u_stats[j] = (uint32_t)((H->N + tune.seg - 1) / tune.seg);
       u_gen[j] = H->generic_tiles;
       u_chunks[j] = H->total_chunks;
       u_groups[j] = (uint32_t)(H->nlev * H->ngroups);
-      for (const LevelDesc& D : H->levels)
-        if (D.fast) {
-          LevelRef R;
-          memset(&R, 0, sizeof(R));
-          R.job = j;
-          R.level = (uint32_t)D.level;
+      soff[j].assign(H->nlev, 0);
+      uint64_t so = 0;
+      for (const LevelDesc& D : H->levels) {
+        LevelRef R;
+        memset(&R, 0, sizeof(R));
+        R.job = j;
+        R.level = (uint32_t)D.level;
+        if (D.fast == 1) {
           cells.push_back(R);
           u_cells.push_back(cell_tiles(D));
+        } else if (D.fast == 2) {
+          R.soff = so;
+          soff[j][D.level] = so;
+          so += D.n;
+          gcs.push_back(R);
+          u_gc.push_back(gcell_units(D));
+          u_pack.push_back(D.ntiles);
         }
+      }
     }
     const auto p_stats = prefix(u_stats), p_gen = prefix(u_gen), p_chunks = prefix(u_chunks),
                p_groups = prefix(u_groups), p_cells = prefix(u_cells);
@@ -170,11 +189,20 @@ struct hpmdr_batch {
     o_groups = im.add(p_groups);
     o_cells_refs = im.add(cells);
     o_cells_u0 = im.add(p_cells);
+    {
+      const auto p_gc = prefix(u_gc), p_pack = prefix(u_pack);
+      n_gc_refs = (uint32_t)gcs.size();
+      t_gc = p_gc.back();
+      t_pack = p_pack.back();
+      o_gc_refs = im.add(gcs);
+      o_gc_u0 = im.add(p_gc);
+      o_pack_u0 = im.add(p_pack);
+    }
     // recomposition rounds
     rounds.clear();
     for (uint32_t r = 0;; r++) {
-      std::vector<LevelRef> rc, rg;
-      std::vector<uint32_t> uc, ucopy, ulev;
+      std::vector<LevelRef> rc, rg, rgc;
+      std::vector<uint32_t> uc, ucopy, ulev, uunpack, ugc;
       for (uint32_t j = 0; j < n; j++) {
         const hpmdr_handle* H = hs[j].get();
         const int L = H->nlev - 1, se = jobs[j].small_end, l = se + 1 + (int)r;
@@ -189,19 +217,33 @@ struct hpmdr_batch {
         else R.coarse = ((L - (l - 1)) % 2 == 1) ? H->d_xa : H->d_xb;
         R.dst = R.final ? nullptr : (((L - l) % 2 == 1) ? H->d_xa : H->d_xb);
         const LevelDesc& D = H->levels[l];
-        if (D.fast) {
+        if (D.fast == 1) {
           rc.push_back(R);
           uc.push_back(cell_tiles(D));
+        } else if (D.fast == 2) {
+          R.soff = soff[j][l];
+          rgc.push_back(R);
+          uunpack.push_back(D.ntiles);
+          ugc.push_back(gcell_units(D));
         } else {
           rg.push_back(R);
           ucopy.push_back((uint32_t)(((uint64_t)D.gc[0] * D.gc[1] * D.gc[2] + 255) / 256));
           ulev.push_back(D.ntiles);
         }
       }
-      if (rc.empty() && rg.empty()) break;
+      if (rc.empty() && rg.empty() && rgc.empty()) break;
       Round R;
       R.ncells = (uint32_t)rc.size();
       R.ngen = (uint32_t)rg.size();
+      R.ngc = (uint32_t)rgc.size();
+      {
+        const auto pu = prefix(uunpack), pg = prefix(ugc);
+        R.unpack_total = pu.back();
+        R.gc_total = pg.back();
+        R.o_gc_refs = im.add(rgc);
+        R.o_unpack_u0 = im.add(pu);
+        R.o_gc_u0 = im.add(pg);
+      }
       const auto pc = prefix(uc), pcopy = prefix(ucopy), plev = prefix(ulev);
       R.cells_total = pc.back();
       R.copy_total = pcopy.back();
@@ -230,10 +272,16 @@ struct hpmdr_batch {
     launch_b_finalize(d_jobs, n, s);
     launch_b_cells_levelmax(d_jobs, tab<LevelRef>(o_cells_refs), tab<uint32_t>(o_cells_u0),
                             n_cells_refs, t_cells, g, s);
+    launch_b_gcells_levelmax(d_jobs, tab<LevelRef>(o_gc_refs), tab<uint32_t>(o_gc_u0), n_gc_refs,
+                             t_gc, dtype, g, s);
     launch_b_levelmax(d_jobs, tab<uint32_t>(o_gen), n, t_gen, dtype, g, s);
     launch_b_bitlen(d_jobs, n, s);
     launch_b_cells_encode(d_jobs, tab<LevelRef>(o_cells_refs), tab<uint32_t>(o_cells_u0),
                           n_cells_refs, t_cells, g, s);
+    launch_b_gcells_encode(d_jobs, tab<LevelRef>(o_gc_refs), tab<uint32_t>(o_gc_u0), n_gc_refs,
+                           t_gc, dtype, g, s);
+    launch_b_pack(d_jobs, tab<LevelRef>(o_gc_refs), tab<uint32_t>(o_pack_u0), n_gc_refs, t_pack,
+                  dtype == 0 ? 32 : 64, g, s);
     launch_b_encode(d_jobs, tab<uint32_t>(o_gen), n, t_gen, dtype, g, s);
     launch_b_chunk_stats(d_jobs, tab<uint32_t>(o_chunks), n, t_chunks, g, s);
     launch_b_decide(d_jobs, tab<uint32_t>(o_groups), n, t_groups, Ts, cr_num, cr_den, g, s);
@@ -255,6 +303,10 @@ struct hpmdr_batch {
     for (const Round& R : rounds) {
       launch_b_cells_recompose(d_jobs, tab<LevelRef>(R.o_cells_refs), tab<uint32_t>(R.o_cells_u0),
                                R.ncells, R.cells_total, g, s);
+      launch_b_unpack(d_jobs, tab<LevelRef>(R.o_gc_refs), tab<uint32_t>(R.o_unpack_u0), R.ngc,
+                      R.unpack_total, dtype == 0 ? 32 : 64, g, s);
+      launch_b_gcells_recompose(d_jobs, tab<LevelRef>(R.o_gc_refs), tab<uint32_t>(R.o_gc_u0), R.ngc,
+                                R.gc_total, dtype, g, s);
       launch_b_recompose_copy(d_jobs, tab<LevelRef>(R.o_gen_refs), tab<uint32_t>(R.o_copy_u0),
                               R.ngen, R.copy_total, dtype, g, s);
       launch_b_recompose_level(d_jobs, tab<LevelRef>(R.o_gen_refs), tab<uint32_t>(R.o_level_u0),
@@ -336,9 +388,10 @@ extern "C" hpmdr_status hpmdr_batch_create(hpmdr_ctx* ctx, uint64_t n, const uin
     HP_TRY(H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s));
     HP_TRY(ensure_retrieve_buffers(H, s));  // planes, retrieval record, recompose grids
     const uint32_t ngt = (uint32_t)(H->nlev * H->ngroups), tc = std::max(H->total_chunks, 1u);
+    const uint64_t gs = H->plan->gstage_sum;  // every general cell level staged at once
     o_sc[j] = sc_bytes;
     sc_bytes += align256(1024ull * ngt) + align256(8ull * ngt) + 3 * align256(4ull * tc) +
-                align256(256ull * ngt);
+                align256(256ull * ngt) + align256(gs * (H->B / 8)) + align256(gs);
   }
   HP_TRY(b->A.alloc((void**)&b->d_scratch, sc_bytes, s));
   HP_TRY(b->A.alloc((void**)&b->d_jobs, sizeof(BatchJob) * n, s));
@@ -380,6 +433,10 @@ extern "C" hpmdr_status hpmdr_batch_create(hpmdr_ctx* ctx, uint64_t n, const uin
     J.cout = (uint32_t*)p;
     p += align256(4ull * tc);
     J.lens = p;
+    p += align256(256ull * J.ngt);
+    J.gq = p;
+    p += align256(H->plan->gstage_sum * (H->B / 8));
+    J.gsg = p;
     J.rd = H->d_rd;
     J.xroot = H->d_xroot;
     J.xa = H->d_xa;

@@ -81,10 +81,10 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
         if (!(i & 1) || odd) v[i] = __ldg(r + ((size_t)(X0 + i) << hl));
     }
   };
-  // the coarse values of a row: x = X0, X0 + 2, X0 + 4, X0 + 6 and the clamped X0 + 8
-  auto coarse = [&](uint32_t z, uint32_t y, int64_t c[5]) {
-    float v[8];
-    seg(z, y, v, false);
+  // the coarse values of a row: x = X0, X0 + 2, X0 + 4, X0 + 6 and the clamped
+  // X0 + 8; v receives the row segment (odd x too if asked)
+  auto coarse = [&](uint32_t z, uint32_t y, int64_t c[5], float v[8], bool odd) {
+    seg(z, y, v, odd);
 #pragma unroll
     for (int i = 0; i < 4; i++) c[i] = fixed_point(v[2 * i], E_f, ign);
     c[4] = fixed_point(__ldg(f + ((size_t)(z << hl) * ny + (y << hl)) * nx + ((size_t)Xe << hl)), E_f,
@@ -92,13 +92,12 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
   };
   float v[8];
   int64_t c0[5], a[5], c[4];
-  coarse(Z0, Y0, c0);
-  seg(Z0, Y0, v, true);  // t = 1 nodes at odd x (the even ones are c0)
+  coarse(Z0, Y0, c0, v, true);  // and the t = 1 nodes at odd x
 #pragma unroll
   for (int k = 0; k < 4; k++) c[k] = (2 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 4;
   visit(1, c);
   if (hy) {
-    coarse(Z0, Y2, a);
+    coarse(Z0, Y2, a, v, false);
 #pragma unroll
     for (int i = 0; i < 5; i++) a[i] += c0[i];
     seg(Z0, Y0 + 1, v, true);
@@ -111,7 +110,7 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
   }
   if (hz) {
     int64_t c1[5];
-    coarse(Z2, Y0, c1);
+    coarse(Z2, Y0, c1, v, false);
 #pragma unroll
     for (int i = 0; i < 5; i++) c0[i] += c1[i];  // c0 becomes d
     seg(Z0 + 1, Y0, v, true);
@@ -123,7 +122,7 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
     visit(5, c);
     if (hy) {
       int64_t c3[5];
-      coarse(Z2, Y2, c3);
+      coarse(Z2, Y2, c3, v, false);
 #pragma unroll
       for (int i = 0; i < 5; i++) a[i] += c1[i] + c3[i];  // a becomes b
       seg(Z0 + 1, Y0 + 1, v, true);

@@ -327,6 +327,34 @@ void launch_b_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs
 }
 
 // ------------------------------------------- stand-alone Algorithm 1 and inverse
+// one warp: Algorithm 1 on the 1024 elements of the tile at `base`
+template <int B>
+__device__ __forceinline__ void pack_tile(const void* __restrict__ qv,
+                                          const uint8_t* __restrict__ sign, uint32_t n, uint32_t W,
+                                          uint32_t* __restrict__ planes, uint32_t base, uint32_t* hi,
+                                          uint32_t* lo) {
+  const int lane = threadIdx.x & 31;
+  uint32_t my_sign = 0;
+#pragma unroll 4
+  for (int r = 0; r < 32; r++) {
+    uint32_t j = base + r * 32 + lane;
+    uint64_t q = 0;
+    bool neg = false;
+    if (j < n) {
+      q = B == 64 ? ((const uint64_t*)qv)[j] : ((const uint32_t*)qv)[j];
+      neg = sign[j] != 0;
+    }
+    uint32_t sw = __ballot_sync(HP_FULL, neg);
+    if (lane == r) my_sign = sw;
+    hi[r * 33 + lane] = B == 64 ? (uint32_t)(q >> 32) : (uint32_t)q;
+    if (B == 64) lo[r * 33 + lane] = (uint32_t)q;
+  }
+  __syncwarp();
+  const uint32_t wi = base / 32 + lane;
+  if (wi < W) emit_word<B>(hi + lane * 33, lo + lane * 33, my_sign, planes, W, wi);
+  __syncwarp();
+}
+
 template <int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_bitplane_encode(const void* __restrict__ qv, const uint8_t* __restrict__ sign, uint32_t n,
@@ -334,31 +362,49 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t* hi = s_hi[w];
-  uint32_t* lo = s_lo[B == 64 ? w : 0];
+  const int w = threadIdx.x >> 5;
   const uint32_t ntiles = (n + HP_TILE - 1) / HP_TILE;
-  for (uint32_t tile = blockIdx.x * WPB + w; tile < ntiles; tile += gridDim.x * WPB) {
-    const uint32_t base = tile * HP_TILE;
-    uint32_t my_sign = 0;
-    for (int r = 0; r < 32; r++) {
-      uint32_t j = base + r * 32 + lane;
-      uint64_t q = 0;
-      bool neg = false;
-      if (j < n) {
-        q = B == 64 ? ((const uint64_t*)qv)[j] : ((const uint32_t*)qv)[j];
-        neg = sign[j] != 0;
-      }
-      uint32_t sw = __ballot_sync(HP_FULL, neg);
-      if (lane == r) my_sign = sw;
-      hi[r * 33 + lane] = B == 64 ? (uint32_t)(q >> 32) : (uint32_t)q;
-      if (B == 64) lo[r * 33 + lane] = (uint32_t)q;
+  for (uint32_t tile = blockIdx.x * WPB + w; tile < ntiles; tile += gridDim.x * WPB)
+    pack_tile<B>(qv, sign, n, W, planes, tile * HP_TILE, s_hi[w], s_lo[B == 64 ? w : 0]);
+}
+
+// one warp: the 1024 elements of the tile at `base`, keeping the top k planes
+template <int B>
+__device__ __forceinline__ void unpack_tile(const uint32_t* __restrict__ planes, uint32_t n,
+                                            uint32_t W, int k, void* __restrict__ qv,
+                                            uint8_t* __restrict__ sign, uint32_t base, uint32_t* hi,
+                                            uint32_t* lo, uint32_t* sgn) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t wi = base / 32 + lane;
+  uint32_t a[32];
+  if (wi < W) {
+#pragma unroll
+    for (int p = 0; p < 32; p++) a[31 - p] = (p < k) ? planes[(size_t)(1 + p) * W + wi] : 0u;
+    if (k) transpose32(a);
+#pragma unroll
+    for (int b = 0; b < 32; b++) hi[lane * 33 + b] = a[b];
+    if (B == 64) {
+#pragma unroll
+      for (int p = 0; p < 32; p++)
+        a[31 - p] = (32 + p < k) ? planes[(size_t)(33 + p) * W + wi] : 0u;
+      if (k > 32) transpose32(a);
+#pragma unroll
+      for (int b = 0; b < 32; b++) lo[lane * 33 + b] = a[b];
     }
-    __syncwarp();
-    const uint32_t wi = base / 32 + lane;
-    if (wi < W) emit_word<B>(hi + lane * 33, lo + lane * 33, my_sign, planes, W, wi);
-    __syncwarp();
+    sgn[lane] = k > 0 ? planes[wi] : 0u;
   }
+  __syncwarp();
+  for (int r = 0; r < 32; r++) {
+    uint32_t j = base + r * 32 + lane;
+    if (j < n) {
+      if (B == 64)
+        ((uint64_t*)qv)[j] = ((uint64_t)hi[r * 33 + lane] << 32) | lo[r * 33 + lane];
+      else
+        ((uint32_t*)qv)[j] = hi[r * 33 + lane];
+      sign[j] = (uint8_t)((sgn[r] >> lane) & 1u);
+    }
+  }
+  __syncwarp();
 }
 
 template <int B>
@@ -369,43 +415,43 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
   __shared__ uint32_t s_sign[WPB][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t* hi = s_hi[w];
-  uint32_t* lo = s_lo[B == 64 ? w : 0];
+  const int w = threadIdx.x >> 5;
   const uint32_t ntiles = (n + HP_TILE - 1) / HP_TILE;
-  for (uint32_t tile = blockIdx.x * WPB + w; tile < ntiles; tile += gridDim.x * WPB) {
-    const uint32_t base = tile * HP_TILE;
-    const uint32_t wi = base / 32 + lane;
-    uint32_t a[32];
-    if (wi < W) {
-#pragma unroll
-      for (int p = 0; p < 32; p++) a[31 - p] = (p < k) ? planes[(size_t)(1 + p) * W + wi] : 0u;
-      transpose32(a);
-#pragma unroll
-      for (int b = 0; b < 32; b++) hi[lane * 33 + b] = a[b];
-      if (B == 64) {
-#pragma unroll
-        for (int p = 0; p < 32; p++)
-          a[31 - p] = (32 + p < k) ? planes[(size_t)(33 + p) * W + wi] : 0u;
-        transpose32(a);
-#pragma unroll
-        for (int b = 0; b < 32; b++) lo[lane * 33 + b] = a[b];
-      }
-      s_sign[w][lane] = k > 0 ? planes[wi] : 0u;
-    }
-    __syncwarp();
-    for (int r = 0; r < 32; r++) {
-      uint32_t j = base + r * 32 + lane;
-      if (j < n) {
-        if (B == 64)
-          ((uint64_t*)qv)[j] = ((uint64_t)hi[r * 33 + lane] << 32) | lo[r * 33 + lane];
-        else
-          ((uint32_t*)qv)[j] = hi[r * 33 + lane];
-        sign[j] = (uint8_t)((s_sign[w][r] >> lane) & 1u);
-      }
-    }
-    __syncwarp();
-  }
+  for (uint32_t tile = blockIdx.x * WPB + w; tile < ntiles; tile += gridDim.x * WPB)
+    unpack_tile<B>(planes, n, W, k, qv, sign, tile * HP_TILE, s_hi[w], s_lo[B == 64 ? w : 0],
+                   s_sign[w]);
+}
+
+// a level's planes to its level-linear staging buffer, keeping the planes of
+// the groups the current reconstruction uses (k = 4 cur[l], set by selection)
+template <int B>
+__global__ void __launch_bounds__(B == 32 ? 256 : 128)
+    k_level_unpack(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ meta,
+                   const LevelDesc* __restrict__ Lp, void* __restrict__ qv,
+                   uint8_t* __restrict__ sign) {
+  constexpr int WPB = B == 32 ? 8 : 4;
+  __shared__ uint32_t s_hi[WPB][32 * 33];
+  __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
+  __shared__ uint32_t s_sign[WPB][32];
+  if (meta->status) return;
+  const LevelDesc& L = *Lp;
+  const int w = threadIdx.x >> 5, k = 4 * meta->cur[L.level];
+  const uint32_t* P = planes + L.plane_off / 4;
+  for (uint32_t tile = blockIdx.x * WPB + w; tile < L.ntiles; tile += gridDim.x * WPB)
+    unpack_tile<B>(P, L.n, L.W, k, qv, sign, tile * HP_TILE, s_hi[w], s_lo[B == 64 ? w : 0],
+                   s_sign[w]);
+}
+
+void launch_level_unpack(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,
+                         const LevelDesc& Lh, int B, void* q, uint8_t* sign, cstream s) {
+  const uint32_t wpb = B == 32 ? 8 : 4;
+  uint32_t blocks = (Lh.ntiles + wpb - 1) / wpb, cap = (uint32_t)sm_count() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  if (B == 32)
+    hp::note_launch(), k_level_unpack<32><<<blocks, 256, 0, s>>>(planes, meta, Ld, q, sign);
+  else
+    hp::note_launch(), k_level_unpack<64><<<blocks, 128, 0, s>>>(planes, meta, Ld, q, sign);
 }
 
 void launch_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int B, uint32_t* planes,
@@ -436,6 +482,70 @@ void launch_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, vo
     hp::note_launch(), k_bitplane_decode<32><<<blocks, 256, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
   else
     hp::note_launch(), k_bitplane_decode<64><<<blocks, 128, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
+}
+
+// batched Algorithm 1 / inverse over general cell levels: warp unit = one tile
+// of one (job, level) entry; the staging of entry e starts at element R.soff
+template <int B>
+__global__ void __launch_bounds__(B == 32 ? 256 : 128)
+    kb_pack(const BatchJob* __restrict__ jobs, const LevelRef* __restrict__ refs,
+            const uint32_t* __restrict__ unit0, uint32_t nrefs, uint32_t total) {
+  constexpr int WPB = B == 32 ? 8 : 4;
+  __shared__ uint32_t s_hi[WPB][32 * 33];
+  __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
+  const int w = threadIdx.x >> 5;
+  for (uint32_t u = blockIdx.x * WPB + w; u < total; u += gridDim.x * WPB) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    if (J.meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const void* q = reinterpret_cast<const uint8_t*>(J.gq) + R.soff * (B / 8);
+    pack_tile<B>(q, J.gsg + R.soff, L.n, L.W,
+                 reinterpret_cast<uint32_t*>(J.planes + L.plane_off), (u - unit0[e]) * HP_TILE,
+                 s_hi[w], s_lo[B == 64 ? w : 0]);
+  }
+}
+
+template <int B>
+__global__ void __launch_bounds__(B == 32 ? 256 : 128)
+    kb_unpack(const BatchJob* __restrict__ jobs, const LevelRef* __restrict__ refs,
+              const uint32_t* __restrict__ unit0, uint32_t nrefs, uint32_t total) {
+  constexpr int WPB = B == 32 ? 8 : 4;
+  __shared__ uint32_t s_hi[WPB][32 * 33];
+  __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
+  __shared__ uint32_t s_sign[WPB][32];
+  const int w = threadIdx.x >> 5;
+  for (uint32_t u = blockIdx.x * WPB + w; u < total; u += gridDim.x * WPB) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    const FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    void* q = reinterpret_cast<uint8_t*>(J.gq) + R.soff * (B / 8);
+    unpack_tile<B>(reinterpret_cast<const uint32_t*>(J.planes + L.plane_off), L.n, L.W,
+                   4 * meta->cur[L.level], q, J.gsg + R.soff, (u - unit0[e]) * HP_TILE, s_hi[w],
+                   s_lo[B == 64 ? w : 0], s_sign[w]);
+  }
+}
+
+void launch_b_pack(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                   uint32_t nrefs, uint32_t total, int B, uint32_t grid, cstream s) {
+  if (!total) return;
+  const uint32_t wpb = B == 32 ? 8 : 4, need = (total + wpb - 1) / wpb;
+  if (grid > need) grid = need;
+  if (B == 32) hp::note_launch(), kb_pack<32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  else hp::note_launch(), kb_pack<64><<<grid, 128, 0, s>>>(jobs, refs, unit0, nrefs, total);
+}
+
+void launch_b_unpack(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                     uint32_t nrefs, uint32_t total, int B, uint32_t grid, cstream s) {
+  if (!total) return;
+  const uint32_t wpb = B == 32 ? 8 : 4, need = (total + wpb - 1) / wpb;
+  if (grid > need) grid = need;
+  if (B == 32) hp::note_launch(), kb_unpack<32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  else hp::note_launch(), kb_unpack<64><<<grid, 128, 0, s>>>(jobs, refs, unit0, nrefs, total);
 }
 
 }  // namespace hp

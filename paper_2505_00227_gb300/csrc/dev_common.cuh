@@ -38,8 +38,21 @@ __device__ __forceinline__ void transpose32(uint32_t a[32]) {
       a[i] ^= t << S;                                              \
     }                                                              \
   }
-  HP_TSTAGE(16, 0x0000FFFFu)
-  HP_TSTAGE(8, 0x00FF00FFu)
+  // the 16- and 8-bit stages move whole bytes: one byte permute per word
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    const uint32_t x = a[i], y = a[i + 16];
+    a[i] = __byte_perm(x, y, 0x5410);       // low halves of x, y
+    a[i + 16] = __byte_perm(x, y, 0x7632);  // high halves of x, y
+  }
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    if ((i & 8) == 0) {
+      const uint32_t x = a[i], y = a[i + 8];
+      a[i] = __byte_perm(x, y, 0x6240);      // bytes 0, 2 of x, y interleaved
+      a[i + 8] = __byte_perm(x, y, 0x7351);  // bytes 1, 3 of x, y interleaved
+    }
+  }
   HP_TSTAGE(4, 0x0F0F0F0Fu)
   HP_TSTAGE(2, 0x33333333u)
   HP_TSTAGE(1, 0x55555555u)

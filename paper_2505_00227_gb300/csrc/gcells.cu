@@ -1,0 +1,428 @@
+// General-grid cell kernels: decomposition, quantization and recomposition of
+// a level of any grid size and either precision, one thread per cell.
+//
+// A cell (cz, cy, cx) is the coarse node (2cz, 2cy, 2cx) of the level grid
+// G_h with the up to seven nodes of parity type t = o_x + 2 o_y + 4 o_z next to
+// it (a type exists where 2c + 1 is inside the grid along its odd axes).  Its
+// corners are the coarse nodes 2c and 2c + 2 along each odd axis, the right
+// one replaced by the left one outside the grid (Sec. 3 decomposer; the same
+// coefficients as the tile and fused cell kernels).
+//
+// The bit transposes are separate passes over a level-linear staging buffer
+// (aligned integer and sign per node): quantize (this file) then Algorithm 1
+// (the bitplane encoder); on retrieval the bitplane decoder fills the buffer
+// and the recomposition reads it.  Consecutive threads take consecutive cells
+// along x, so the field reads, the staging reads and writes (type rasters are
+// x-fastest) and the output writes are coalesced for every grid size.
+#include "dev_common.cuh"
+
+namespace hp {
+
+template <typename T>
+struct GView {
+  const T* __restrict__ f;
+  uint32_t ny, nx;
+  int hl, E_f;
+};
+
+template <typename T>
+__device__ __forceinline__ int64_t gF(const GView<T>& v, uint32_t z, uint32_t y, uint32_t x,
+                                      uint32_t& fl) {
+  return fixed_point(
+      __ldg(v.f + ((size_t)(z << v.hl) * v.ny + (y << v.hl)) * v.nx + ((size_t)x << v.hl)), v.E_f,
+      fl);
+}
+
+struct CellPos {
+  uint32_t cz, cy, cx;
+  bool hz, hy, hx;  // the odd neighbour exists along z / y / x
+};
+
+// cells in raster order over the coarse grid (gc); dx[0], dy[0] divide by gc
+__device__ __forceinline__ CellPos cell_pos(const LevelDesc& L, uint32_t c) {
+  CellPos p;
+  const uint32_t r = fdiv(c, L.dx[0]);
+  p.cx = c - r * L.gc[2];
+  p.cz = fdiv(r, L.dy[0]);
+  p.cy = r - p.cz * L.gc[1];
+  p.hz = 2 * p.cz + 1 < L.g[0];
+  p.hy = 2 * p.cy + 1 < L.g[1];
+  p.hx = 2 * p.cx + 1 < L.g[2];
+  return p;
+}
+
+// level-linear index of the type-t node of cell p
+__device__ __forceinline__ uint32_t type_index(const LevelDesc& L, int t, const CellPos& p) {
+  return L.off[t] + (p.cz * L.cnt[t][1] + p.cy) * L.cnt[t][2] + p.cx;
+}
+
+// visit(t, C8) for every existing type of the cell
+template <typename T, bool SELF_FLOOR, typename V>
+__device__ __forceinline__ void gcell_visit(const GView<T>& v, const LevelDesc& L,
+                                            const CellPos& p, uint32_t& fl, V&& visit) {
+  uint32_t ign = 0;
+  uint32_t& sf = SELF_FLOOR ? fl : ign;
+  const uint32_t Z0 = 2 * p.cz, Y0 = 2 * p.cy, X0 = 2 * p.cx;
+  const uint32_t Z2 = Z0 + 2 < L.g[0] ? Z0 + 2 : Z0, Y2 = Y0 + 2 < L.g[1] ? Y0 + 2 : Y0;
+  const uint32_t X2 = X0 + 2 < L.g[2] ? X0 + 2 : X0;
+  const int64_t c000 = gF(v, Z0, Y0, X0, ign);
+  int64_t c001 = 0, c010 = 0, c011 = 0;
+  if (p.hx) {
+    c001 = gF(v, Z0, Y0, X2, ign);
+    visit(1, (2 * gF(v, Z0, Y0, X0 + 1, sf) - (c000 + c001)) * 4);
+  }
+  if (p.hy) {
+    c010 = gF(v, Z0, Y2, X0, ign);
+    visit(2, (2 * gF(v, Z0, Y0 + 1, X0, sf) - (c000 + c010)) * 4);
+    if (p.hx) {
+      c011 = gF(v, Z0, Y2, X2, ign);
+      visit(3, (4 * gF(v, Z0, Y0 + 1, X0 + 1, sf) - (c000 + c001 + c010 + c011)) * 2);
+    }
+  }
+  if (p.hz) {
+    const int64_t c100 = gF(v, Z2, Y0, X0, ign);
+    visit(4, (2 * gF(v, Z0 + 1, Y0, X0, sf) - (c000 + c100)) * 4);
+    int64_t c101 = 0;
+    if (p.hx) {
+      c101 = gF(v, Z2, Y0, X2, ign);
+      visit(5, (4 * gF(v, Z0 + 1, Y0, X0 + 1, sf) - (c000 + c001 + c100 + c101)) * 2);
+    }
+    if (p.hy) {
+      const int64_t c110 = gF(v, Z2, Y2, X0, ign);
+      visit(6, (4 * gF(v, Z0 + 1, Y0 + 1, X0, sf) - (c000 + c010 + c100 + c110)) * 2);
+      if (p.hx) {
+        const int64_t c111 = gF(v, Z2, Y2, X2, ign);
+        visit(7, 8 * gF(v, Z0 + 1, Y0 + 1, X0 + 1, sf) -
+                     (c000 + c001 + c010 + c011 + c100 + c101 + c110 + c111));
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t gcell_count(const LevelDesc& L) {
+  return L.gc[0] * L.gc[1] * L.gc[2];
+}
+
+// ------------------------------------------------------------ level max
+template <typename T>
+__device__ __forceinline__ void gcells_levelmax_range(const GView<T>& v, const LevelDesc& L,
+                                                      uint32_t c0, uint32_t c1, uint32_t step,
+                                                      FieldMeta* meta) {
+  uint64_t mx = 0;
+  uint32_t fl = 0;
+  for (uint32_t c = c0; c < c1; c += step) {
+    const CellPos p = cell_pos(L, c);
+    gcell_visit<T, true>(v, L, p, fl, [&](int, int64_t c8) {
+      const uint64_t m = umag(c8);
+      mx = m > mx ? m : mx;
+    });
+  }
+  mx = warp_max_u64(mx);
+  const unsigned anyfl = __any_sync(HP_FULL, fl != 0);
+  if ((threadIdx.x & 31) == 0) {
+    if (mx) atomicMax((unsigned long long*)&meta->m8[L.level], (unsigned long long)mx);
+    if (anyfl) atomicOr(&meta->floored, 1u);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gcells_levelmax(const T* __restrict__ f, uint32_t ny,
+                                                         uint32_t nx, const LevelDesc* __restrict__ Lp,
+                                                         FieldMeta* meta) {
+  if (meta->status) return;
+  const LevelDesc& L = *Lp;
+  const GView<T> v{f, ny, nx, L.hlog, meta->E_f};
+  gcells_levelmax_range(v, L, blockIdx.x * blockDim.x + threadIdx.x, gcell_count(L),
+                        gridDim.x * blockDim.x, meta);
+}
+
+// ------------------------------------------------------------- quantize
+// q = |C8| aligned to B bits (sign-magnitude), staged level-linear
+template <typename T, int B>
+__device__ __forceinline__ void gcells_encode_range(const GView<T>& v, const LevelDesc& L,
+                                                    uint32_t c0, uint32_t c1, uint32_t step,
+                                                    FieldMeta* meta, void* __restrict__ q,
+                                                    uint8_t* __restrict__ sg) {
+  const int bl = meta->bl[L.level];
+  uint64_t low = 0;
+  uint32_t ign = 0;
+  for (uint32_t c = c0; c < c1; c += step) {
+    const CellPos p = cell_pos(L, c);
+    gcell_visit<T, false>(v, L, p, ign, [&](int t, int64_t c8) {
+      const uint32_t j = type_index(L, t, p);
+      const uint64_t m = umag(c8);
+      uint64_t qv;
+      if (bl == 0) qv = 0;
+      else if (B >= bl) qv = m << (B - bl);
+      else {
+        qv = m >> (bl - B);
+        low |= m & ((1ull << (bl - B)) - 1ull);
+      }
+      if (B == 32) reinterpret_cast<uint32_t*>(q)[j] = (uint32_t)qv;
+      else reinterpret_cast<uint64_t*>(q)[j] = qv;
+      sg[j] = c8 < 0 ? 1 : 0;
+    });
+  }
+  low = warp_or_u64(low);
+  if ((threadIdx.x & 31) == 0 && low)
+    atomicOr((unsigned long long*)&meta->lowbits[L.level], (unsigned long long)low);
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(256) k_gcells_encode(const T* __restrict__ f, uint32_t ny,
+                                                       uint32_t nx, const LevelDesc* __restrict__ Lp,
+                                                       FieldMeta* meta, void* __restrict__ q,
+                                                       uint8_t* __restrict__ sg) {
+  if (meta->status) return;
+  const LevelDesc& L = *Lp;
+  const GView<T> v{f, ny, nx, L.hlog, meta->E_f};
+  gcells_encode_range<T, B>(v, L, blockIdx.x * blockDim.x + threadIdx.x, gcell_count(L),
+                            gridDim.x * blockDim.x, meta, q, sg);
+}
+
+// ---------------------------------------------------------- recompose
+template <typename T>
+__device__ __forceinline__ T gconvert(int64_t X, int E_f);
+
+template <>
+__device__ __forceinline__ float gconvert<float>(int64_t X, int E_f) {
+  const int e = E_f - 48;
+  if (e >= -126 && E_f <= 121)
+    return __fmul_rn(__ll2float_rn(X), __int_as_float((e + 127) << 23));
+  const double d = __dmul_rn(__ll2double_rn(X), __longlong_as_double((long long)(e + 1023) << 52));
+  return __double2float_rn(d);
+}
+
+template <>
+__device__ __forceinline__ double gconvert<double>(int64_t X, int E_f) {
+  const int e = E_f - 48;
+  const double x = __ll2double_rn(X);
+  if (e >= -1022) return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
+  const double y = __dmul_rn(x, __longlong_as_double((long long)(-500 + 1023) << 52));
+  return __dmul_rn(y, __longlong_as_double((long long)(e + 500 + 1023) << 52));
+}
+
+// the node's reconstruction X = floor((c8 2^n + 8 S) / 2^(3+n)) = (c8 + S 2^(3-n)) >> 3,
+// S the sum of its 2^n corners, written to the level grid or the output
+template <typename T, int B>
+__device__ __forceinline__ void gcells_recompose_range(const LevelDesc& L, int bl, int E_f,
+                                                       const void* __restrict__ q,
+                                                       const uint8_t* __restrict__ sg,
+                                                       const int64_t* __restrict__ coarse,
+                                                       void* __restrict__ dst, bool final,
+                                                       uint32_t c0, uint32_t c1, uint32_t step) {
+  const uint32_t gc1 = L.gc[1], gc2 = L.gc[2], g1 = L.g[1], g2 = L.g[2];
+  for (uint32_t c = c0; c < c1; c += step) {
+    const CellPos p = cell_pos(L, c);
+    const uint32_t z1 = 2 * p.cz + 2 < L.g[0] ? p.cz + 1 : p.cz;
+    const uint32_t y1 = 2 * p.cy + 2 < L.g[1] ? p.cy + 1 : p.cy;
+    const uint32_t x1 = 2 * p.cx + 2 < L.g[2] ? p.cx + 1 : p.cx;
+    auto C = [&](uint32_t z, uint32_t y, uint32_t x) {
+      return __ldg(coarse + ((size_t)z * gc1 + y) * gc2 + x);
+    };
+    auto c8 = [&](int t) -> int64_t {
+      const uint32_t j = type_index(L, t, p);
+      const uint64_t qh = B == 32 ? (uint64_t)reinterpret_cast<const uint32_t*>(q)[j]
+                                  : reinterpret_cast<const uint64_t*>(q)[j];
+      uint64_t mag;
+      if (bl == 0) mag = 0;
+      else if (B >= bl) mag = qh >> (B - bl);
+      else mag = qh << (bl - B);
+      return sg[j] ? -(int64_t)mag : (int64_t)mag;
+    };
+    auto put = [&](uint32_t z, uint32_t y, uint32_t x, int64_t X) {
+      const size_t d = ((size_t)z * g1 + y) * g2 + x;
+      if (final) reinterpret_cast<T*>(dst)[d] = gconvert<T>(X, E_f);
+      else reinterpret_cast<int64_t*>(dst)[d] = X;
+    };
+    const uint32_t Z0 = 2 * p.cz, Y0 = 2 * p.cy, X0 = 2 * p.cx;
+    const int64_t c000 = C(p.cz, p.cy, p.cx);
+    put(Z0, Y0, X0, c000);
+    int64_t c001 = 0, c010 = 0, c011 = 0;
+    if (p.hx) {
+      c001 = C(p.cz, p.cy, x1);
+      put(Z0, Y0, X0 + 1, (c8(1) + (c000 + c001) * 4) >> 3);
+    }
+    if (p.hy) {
+      c010 = C(p.cz, y1, p.cx);
+      put(Z0, Y0 + 1, X0, (c8(2) + (c000 + c010) * 4) >> 3);
+      if (p.hx) {
+        c011 = C(p.cz, y1, x1);
+        put(Z0, Y0 + 1, X0 + 1, (c8(3) + (c000 + c001 + c010 + c011) * 2) >> 3);
+      }
+    }
+    if (p.hz) {
+      const int64_t c100 = C(z1, p.cy, p.cx);
+      put(Z0 + 1, Y0, X0, (c8(4) + (c000 + c100) * 4) >> 3);
+      int64_t c101 = 0;
+      if (p.hx) {
+        c101 = C(z1, p.cy, x1);
+        put(Z0 + 1, Y0, X0 + 1, (c8(5) + (c000 + c001 + c100 + c101) * 2) >> 3);
+      }
+      if (p.hy) {
+        const int64_t c110 = C(z1, y1, p.cx);
+        put(Z0 + 1, Y0 + 1, X0, (c8(6) + (c000 + c010 + c100 + c110) * 2) >> 3);
+        if (p.hx) {
+          const int64_t c111 = C(z1, y1, x1);
+          put(Z0 + 1, Y0 + 1, X0 + 1,
+              (c8(7) + (c000 + c001 + c010 + c011 + c100 + c101 + c110 + c111)) >> 3);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(256) k_gcells_recompose(const FieldMeta* __restrict__ meta,
+                                                          const LevelDesc* __restrict__ Lp,
+                                                          const void* __restrict__ q,
+                                                          const uint8_t* __restrict__ sg,
+                                                          const int64_t* __restrict__ coarse,
+                                                          void* __restrict__ dst, int final) {
+  if (meta->status) return;
+  const LevelDesc& L = *Lp;
+  gcells_recompose_range<T, B>(L, meta->bl[L.level], meta->E_f, q, sg, coarse, dst, final != 0,
+                               blockIdx.x * blockDim.x + threadIdx.x, gcell_count(L),
+                               gridDim.x * blockDim.x);
+}
+
+// ------------------------------------------------------------ launchers
+static uint32_t gcell_grid(const LevelDesc& L) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t cells = (uint64_t)L.gc[0] * L.gc[1] * L.gc[2];
+  uint64_t blocks = (cells + 255) / 256, cap = (uint64_t)sms * 8;
+  return (uint32_t)(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
+void launch_gcells_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
+                            const LevelDesc& Lh, FieldMeta* meta, cstream s) {
+  const uint32_t g = gcell_grid(Lh);
+  if (dtype == 0)
+    hp::note_launch(), k_gcells_levelmax<float><<<g, 256, 0, s>>>(
+        (const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
+  else
+    hp::note_launch(), k_gcells_levelmax<double><<<g, 256, 0, s>>>(
+        (const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
+}
+
+void launch_gcells_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
+                          const LevelDesc& Lh, FieldMeta* meta, void* q, uint8_t* sg, cstream s) {
+  const uint32_t g = gcell_grid(Lh);
+  if (dtype == 0)
+    hp::note_launch(), k_gcells_encode<float, 32><<<g, 256, 0, s>>>(
+        (const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta, q, sg);
+  else
+    hp::note_launch(), k_gcells_encode<double, 64><<<g, 256, 0, s>>>(
+        (const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta, q, sg);
+}
+
+void launch_gcells_recompose(const FieldMeta* meta, const LevelDesc* Ld, const LevelDesc& Lh,
+                             int dtype, const void* q, const uint8_t* sg, const int64_t* coarse,
+                             void* dst, int final, cstream s) {
+  const uint32_t g = gcell_grid(Lh);
+  if (dtype == 0)
+    hp::note_launch(), k_gcells_recompose<float, 32><<<g, 256, 0, s>>>(meta, Ld, q, sg, coarse, dst,
+                                                                       final);
+  else
+    hp::note_launch(), k_gcells_recompose<double, 64><<<g, 256, 0, s>>>(meta, Ld, q, sg, coarse,
+                                                                        dst, final);
+}
+
+// ------------------------------------------------------------------ batched
+// unit = 256 cells of one (job, level) entry; the staging of entry e starts at
+// element R.soff of the job's buffer
+template <typename T>
+__global__ void __launch_bounds__(256) kb_gcells_levelmax(const BatchJob* __restrict__ jobs,
+                                                          const LevelRef* __restrict__ refs,
+                                                          const uint32_t* __restrict__ unit0,
+                                                          uint32_t nrefs, uint32_t total) {
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const GView<T> v{reinterpret_cast<const T*>(J.f), J.dims[1], J.dims[2], L.hlog, meta->E_f};
+    const uint32_t c = (u - unit0[e]) * 256 + threadIdx.x, n = gcell_count(L);
+    gcells_levelmax_range(v, L, c, c < n ? c + 1 : c, 1, meta);
+  }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(256) kb_gcells_encode(const BatchJob* __restrict__ jobs,
+                                                        const LevelRef* __restrict__ refs,
+                                                        const uint32_t* __restrict__ unit0,
+                                                        uint32_t nrefs, uint32_t total) {
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const GView<T> v{reinterpret_cast<const T*>(J.f), J.dims[1], J.dims[2], L.hlog, meta->E_f};
+    const uint32_t c = (u - unit0[e]) * 256 + threadIdx.x, n = gcell_count(L);
+    gcells_encode_range<T, B>(v, L, c, c < n ? c + 1 : c, 1, meta,
+                              reinterpret_cast<uint8_t*>(J.gq) + R.soff * (B / 8), J.gsg + R.soff);
+  }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(256) kb_gcells_recompose(const BatchJob* __restrict__ jobs,
+                                                           const LevelRef* __restrict__ refs,
+                                                           const uint32_t* __restrict__ unit0,
+                                                           uint32_t nrefs, uint32_t total) {
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    const FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const uint32_t c = (u - unit0[e]) * 256 + threadIdx.x, n = gcell_count(L);
+    gcells_recompose_range<T, B>(L, meta->bl[L.level], meta->E_f,
+                                 reinterpret_cast<const uint8_t*>(J.gq) + R.soff * (B / 8),
+                                 J.gsg + R.soff, R.coarse, R.final ? J.out : (void*)R.dst,
+                                 R.final != 0, c, c < n ? c + 1 : c, 1);
+  }
+}
+
+static uint32_t cap_units(uint32_t grid, uint32_t total) { return grid < total ? grid : total; }
+
+void launch_b_gcells_levelmax(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                              uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s) {
+  if (!total) return;
+  grid = cap_units(grid, total);
+  if (dtype == 0)
+    hp::note_launch(), kb_gcells_levelmax<float><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  else
+    hp::note_launch(), kb_gcells_levelmax<double><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+}
+
+void launch_b_gcells_encode(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                            uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s) {
+  if (!total) return;
+  grid = cap_units(grid, total);
+  if (dtype == 0)
+    hp::note_launch(), kb_gcells_encode<float, 32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  else
+    hp::note_launch(), kb_gcells_encode<double, 64><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+}
+
+void launch_b_gcells_recompose(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                               uint32_t nrefs, uint32_t total, int dtype, uint32_t grid,
+                               cstream s) {
+  if (!total) return;
+  grid = cap_units(grid, total);
+  if (dtype == 0)
+    hp::note_launch(), kb_gcells_recompose<float, 32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs,
+                                                                           total);
+  else
+    hp::note_launch(), kb_gcells_recompose<double, 64><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs,
+                                                                            total);
+}
+
+}  // namespace hp

@@ -34,14 +34,14 @@ struct LevelDesc {
   uint32_t tile0;      // first global tile of this level
   uint32_t ntiles;
   uint32_t gtile0;     // first slot of the level in the generic kernels (0 tiles when fast)
-  int32_t fast;        // level handled by the cell kernels
+  int32_t fast;        // 1: fused cell kernels, 2: general cell kernels, 0: tile kernels
   int32_t level;       // l (0 = root)
   int32_t hlog;        // log2 of the half-stride h (-1 for the root)
   uint32_t g[3];       // level grid G_h dims (z, y, x): ceil(n_d / h)
   uint32_t gc[3];      // coarse grid G_2h dims: ceil(g_d / 2)
   uint32_t off[9];     // offset of parity type t (t = 1..7) in the level, off[8] = n
   uint32_t cnt[8][3];  // nodes of type t along (z, y, x)
-  FastDiv dx[8], dy[8];
+  FastDiv dx[8], dy[8];  // per type t >= 1: divide by cnt[t][2], cnt[t][1]; [0]: by gc[2], gc[1]
 };
 
 struct GroupMeta {
@@ -123,6 +123,8 @@ struct BatchJob {
   int64_t* xa;
   int64_t* xb;
   void* out;
+  void* gq;          // staging of the general cell levels: aligned integers
+  uint8_t* gsg;      // and signs
   double tau;        // relative L-infinity bound
   int32_t small_end;  // last level recomposed by the one-CTA small-level kernel
   int32_t pad1;
@@ -135,6 +137,7 @@ struct LevelRef {
   int64_t* dst;           // recomposition: the level grid (unused when final)
   int32_t final;          // recomposition: the level writes the job's output
   int32_t pad;
+  uint64_t soff;          // general cell levels: first element of the level's staging
 };
 
 // launchers implemented in the .cu files --------------------------------------
@@ -263,9 +266,34 @@ void launch_b_recompose_copy(const BatchJob* jobs, const LevelRef* refs, const u
                              uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s);
 void launch_b_recompose_level(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
                               uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s);
+void launch_b_gcells_levelmax(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                              uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s);
+void launch_b_gcells_encode(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                            uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s);
+void launch_b_gcells_recompose(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                               uint32_t nrefs, uint32_t total, int dtype, uint32_t grid,
+                               cstream s);
+void launch_b_pack(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                   uint32_t nrefs, uint32_t total, int B, uint32_t grid, cstream s);
+void launch_b_unpack(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
+                     uint32_t nrefs, uint32_t total, int B, uint32_t grid, cstream s);
 // contiguous copies of every job's FieldMeta and RetrieveDev (for one download)
 void launch_b_gather(const BatchJob* jobs, uint32_t njobs, FieldMeta* metas, RetrieveDev* rds,
                      int32_t* statuses, cstream s);
+
+// gcells.cu (any level grid with h >= 1, either precision): coefficients
+// staged level-linear (q, sign), then Algorithm 1 by launch_bitplane_encode;
+// on retrieval launch_level_unpack fills the staging buffer
+void launch_gcells_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
+                            const LevelDesc& Lh, FieldMeta* meta, cstream s);
+void launch_gcells_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
+                          const LevelDesc& Lh, FieldMeta* meta, void* q, uint8_t* sign,
+                          cstream s);
+void launch_gcells_recompose(const FieldMeta* meta, const LevelDesc* Ld, const LevelDesc& Lh,
+                             int dtype, const void* q, const uint8_t* sign, const int64_t* coarse,
+                             void* dst, int final, cstream s);
+void launch_level_unpack(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,
+                         const LevelDesc& Lh, int B, void* q, uint8_t* sign, cstream s);
 
 // qoi.cu
 void launch_vmag_range(const float* vx, const float* vy, const float* vz, uint64_t N,

@@ -33,7 +33,8 @@ const char* kStageName[NSTAGE] = {
     "huff_bits", "group_offsets", "huff_encode", "rle_encode", "headers", "sequence", "select",
     "decode", "recompose_root", "recompose_copy", "recompose_level", "recompose_copy_out",
     "recompose_level_out", "vmag", "cells_levelmax", "cells_encode", "cells_recompose",
-    "cells_recompose_out", "recompose_small"};
+    "cells_recompose_out", "recompose_small", "gcells_levelmax", "gcells_quantize",
+    "bitplane_encode", "bitplane_decode", "gcells_recompose", "gcells_recompose_out"};
 
 void hp::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void hp::unnote_launches(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
@@ -75,6 +76,9 @@ hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t dims[3], 
   *N = n;
   return HPMDR_OK;
 }
+
+// levels below this many nodes keep the tile kernels (one launch for all of them)
+static const uint32_t kGeneralCellMinNodes = 1u << 15;
 
 static void plan_levels(Plan& P) {
   const int L = detail_levels(P.dims);
@@ -119,7 +123,16 @@ static void plan_levels(Plan& P) {
     D.tile0 = tile;
     D.ntiles = (uint32_t)((n + HP_TILE - 1) / HP_TILE);
     tile += D.ntiles;
-    D.fast = cell_path_ok(D, P.B) ? 1 : 0;
+    // cells of the level (its coarse grid), for the general cell kernels
+    D.dx[0] = make_fastdiv(std::max(D.gc[2], 1u));
+    D.dy[0] = make_fastdiv(std::max(D.gc[1], 1u));
+    if (cell_path_ok(D, P.B)) D.fast = 1;
+    else if (D.hlog >= 0 && D.n >= kGeneralCellMinNodes) D.fast = 2;
+    else D.fast = 0;
+    if (D.fast == 2) {
+      P.gstage_max = std::max<uint64_t>(P.gstage_max, D.n);
+      P.gstage_sum += D.n;
+    }
     D.gtile0 = gtile;
     if (!D.fast) gtile += D.ntiles;
   }
@@ -353,7 +366,10 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   const size_t o_hist = 0, o_gcost = align256(1024ull * ngt);
   const size_t o_cost = o_gcost + align256(8ull * ngt);
   const size_t o_words = o_cost + align256(4ull * tc), o_out = o_words + align256(4ull * tc);
-  const size_t o_lens = o_out + align256(4ull * tc), scratch_bytes = o_lens + align256(256ull * ngt);
+  const size_t o_lens = o_out + align256(4ull * tc), o_gq = o_lens + align256(256ull * ngt);
+  // staging of the general cell levels (one level at a time)
+  const uint64_t gmax = H->plan->gstage_max;
+  const size_t o_gsg = o_gq + align256(gmax * (H->B / 8)), scratch_bytes = o_gsg + align256(gmax);
   unsigned char* sc = nullptr;
   HP_TRY(H->A.alloc((void**)&sc, scratch_bytes, s));
   uint32_t* d_hist = (uint32_t*)(sc + o_hist);
@@ -362,6 +378,8 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   uint32_t* d_words = (uint32_t*)(sc + o_words);
   uint32_t* d_out = (uint32_t*)(sc + o_out);
   uint8_t* d_lens = (uint8_t*)(sc + o_lens);
+  void* d_gq = sc + o_gq;
+  uint8_t* d_gsg = sc + o_gsg;
   if (cudaMemsetAsync(sc, 0, o_cost, s) != cudaSuccess ||
       cudaMemcpyAsync(H->d_meta, H->plan->d_meta0, sizeof(FieldMeta), cudaMemcpyDeviceToDevice,
                       s) != cudaSuccess) {
@@ -383,9 +401,12 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   for (const LevelDesc& D : H->levels)
     if (!D.fast) gen_f += (double)D.n * esz, gen_p += (double)(H->B + 1) * D.W * 4.0;
   for (const LevelDesc& D : H->levels)
-    if (D.fast) {
+    if (D.fast == 1) {
       ProfScope p(P, ST_CELLS_MAX, lvl_bytes(D, false), s);
       launch_cells_levelmax((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta, s);
+    } else if (D.fast == 2) {
+      ProfScope p(P, ST_GCELLS_MAX, lvl_bytes(D, false), s);
+      launch_gcells_levelmax(f, H->dtype, H->dims, H->d_levels + D.level, D, H->d_meta, s);
     }
   if (H->generic_tiles) {
     ProfScope p(P, ST_LEVELMAX, gen_f, s);
@@ -393,11 +414,19 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
                     H->d_meta, s);
   }
   { ProfScope p(P, ST_BITLEN, 0, s); launch_bitlen(H->d_meta, s); }
+  const double qb = H->B / 8 + 1;  // staged bytes per node
   for (const LevelDesc& D : H->levels)
-    if (D.fast) {
+    if (D.fast == 1) {
       ProfScope p(P, ST_CELLS_ENC, lvl_bytes(D, true), s);
       launch_cells_encode((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta,
                           (uint32_t*)H->d_planes, s);
+    } else if (D.fast == 2) {
+      { ProfScope p(P, ST_GCELLS_ENC, lvl_bytes(D, false) + qb * D.n, s);
+        launch_gcells_encode(f, H->dtype, H->dims, H->d_levels + D.level, D, H->d_meta, d_gq,
+                             d_gsg, s); }
+      { ProfScope p(P, ST_PACK, qb * D.n + (double)(H->B + 1) * D.W * 4.0, s);
+        launch_bitplane_encode(d_gq, d_gsg, D.n, H->B, (uint32_t*)(H->d_planes + D.plane_off),
+                               s); }
     }
   if (H->generic_tiles) {
     ProfScope p(P, ST_ENCODE, gen_f + gen_p, s);
@@ -650,6 +679,12 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
     launch_decode(H->d_slots, H->d_meta, H->d_rd, H->max_items, H->d_planes, s); }
   const uint32_t* Pl = (const uint32_t*)H->d_planes;
   const int L = H->nlev - 1;
+  // staging of the general cell levels: scratch of this retrieval only
+  // (stream-ordered), so that it is not part of the handle's cache
+  const uint64_t gmax = H->plan->gstage_max;
+  void* d_gq = nullptr;
+  if (gmax) HP_TRY(H->A.alloc(&d_gq, gmax * (H->B / 8 + 1), s));
+  uint8_t* d_gsg = (uint8_t*)d_gq + gmax * (H->B / 8);
   // the root and the leading run of small generic levels run in one CTA
   int l_end = 0;
   while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= 4096) l_end++;
@@ -666,23 +701,33 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
     const bool final = l == L;
     void* dst = final ? d_out : (void*)(((L - l) % 2 == 1) ? H->d_xa : H->d_xb);
     const int fd = final ? H->dtype : -1;
-    if (H->levels[l].fast) {
+    if (H->levels[l].fast == 1) {
       ProfScope p(P, final ? ST_CELLS_REC_OUT : ST_CELLS_REC, 0, s);
-      H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
-      H->prof_lv.push_back({SIZE_MAX - 1, l * 4 + (final ? 2 : 0)});  // copy folded in
+      H->prof_lv.push_back({p.i, l * 8 + (final ? 3 : 1)});
+      H->prof_lv.push_back({SIZE_MAX - 1, l * 8 + (final ? 2 : 0)});  // copy folded in
       launch_cells_recompose(Pl, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst,
                              final ? 1 : 0, s);
+    } else if (H->levels[l].fast == 2) {
+      { ProfScope p(P, ST_UNPACK, 0, s);
+        H->prof_lv.push_back({p.i, l * 8 + 4});
+        launch_level_unpack(Pl, H->d_meta, H->d_levels + l, H->levels[l], H->B, d_gq, d_gsg,
+                            s); }
+      { ProfScope p(P, final ? ST_GCELLS_REC_OUT : ST_GCELLS_REC, 0, s);
+        H->prof_lv.push_back({p.i, l * 8 + (final ? 6 : 5)});
+        launch_gcells_recompose(H->d_meta, H->d_levels + l, H->levels[l], H->dtype, d_gq, d_gsg,
+                                coarse, dst, final ? 1 : 0, s); }
     } else {
       { ProfScope p(P, final ? ST_COPY_OUT : ST_COPY, 0, s);
-        H->prof_lv.push_back({p.i, l * 4 + (final ? 2 : 0)});
+        H->prof_lv.push_back({p.i, l * 8 + (final ? 2 : 0)});
         launch_recompose_copy(H->d_levels + l, H->levels[l], coarse, dst, fd, H->d_meta, s); }
       { ProfScope p(P, final ? ST_LEVEL_OUT : ST_LEVEL, 0, s);
-        H->prof_lv.push_back({p.i, l * 4 + (final ? 3 : 1)});
+        H->prof_lv.push_back({p.i, l * 8 + (final ? 3 : 1)});
         launch_recompose_level(Pl, H->d_meta, H->d_levels + l, H->levels[l], H->d_perm, coarse,
                                dst, H->B, fd, s); }
     }
     coarse = (const int64_t*)dst;
   }
+  H->A.release(d_gq, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g_last_error = std::string("retrieve launch: ") + cudaGetErrorString(e);
@@ -716,17 +761,23 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
   }
   size_t last = SIZE_MAX;
   double last_b = 0;
+  const double qb = H->B / 8 + 1;  // staged bytes per node of a general cell level
   for (auto& pe : H->prof_lv) {
-    const int l = pe.second / 4, kind = pe.second % 4;
+    const int l = pe.second / 8, kind = pe.second % 8;
     const LevelDesc& D = H->levels[l];
     const double coarse = (double)D.gc[0] * D.gc[1] * D.gc[2];
-    const double osz = (kind == 2 || kind == 3) ? esz : 8.0;
+    const double osz = (kind == 2 || kind == 3 || kind == 6) ? esz : 8.0;
+    const int g = rd.g[l];
+    const double planes = g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0;
     double b;
     if (kind == 0 || kind == 2) {
       b = coarse * 8.0 + coarse * osz;
+    } else if (kind == 4) {  // planes -> staging
+      b = planes + qb * D.n;
+    } else if (kind >= 5) {  // staging + coarse grid -> level grid (coarse nodes included)
+      b = qb * D.n + coarse * 8.0 + ((double)D.n + coarse) * osz;
     } else {
-      const int g = rd.g[l];
-      b = (g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0) + coarse * 8.0 + (double)D.n * osz;
+      b = planes + coarse * 8.0 + (double)D.n * osz;
     }
     if (pe.first == SIZE_MAX - 1) {  // a cell kernel also wrote the coarse nodes
       last_b += coarse * osz;
@@ -1326,7 +1377,7 @@ extern "C" hpmdr_status hpmdr_handle_drop_cache(hpmdr_ctx* ctx, hpmdr_handle* h)
 
 static uint64_t cache_scratch_bytes(const hpmdr_handle* h) {
   const int L = h->nlev - 1;
-  uint64_t b = 0;
+  uint64_t b = h->plan->gstage_max * (h->B / 8 + 1);
   if (L >= 2) {
     const LevelDesc& D = h->levels[L];
     b += 8ull * D.gc[0] * D.gc[1] * D.gc[2];

@@ -24,7 +24,8 @@ enum Stage {
   ST_STATS, ST_FINALIZE, ST_LEVELMAX, ST_BITLEN, ST_ENCODE, ST_CHUNK_STATS, ST_DECIDE,
   ST_HUFF_BITS, ST_OFFSETS, ST_HUFF_ENC, ST_RLE_ENC, ST_HEADERS, ST_SEQUENCE, ST_SELECT,
   ST_DECODE, ST_ROOT, ST_COPY, ST_LEVEL, ST_COPY_OUT, ST_LEVEL_OUT, ST_VMAG, ST_CELLS_MAX,
-  ST_CELLS_ENC, ST_CELLS_REC, ST_CELLS_REC_OUT, ST_SMALL, NSTAGE
+  ST_CELLS_ENC, ST_CELLS_REC, ST_CELLS_REC_OUT, ST_SMALL, ST_GCELLS_MAX, ST_GCELLS_ENC, ST_PACK,
+  ST_UNPACK, ST_GCELLS_REC, ST_GCELLS_REC_OUT, NSTAGE
 };
 extern const char* kStageName[NSTAGE];
 
@@ -171,6 +172,8 @@ struct Plan {
   std::vector<uint32_t> chunk_group;  // global chunk -> flat group index
   uint32_t total_tiles = 0, generic_tiles = 0, total_chunks = 0;
   uint64_t plane_bytes = 0, slot_bytes = 0;
+  // general cell levels: nodes of the largest one, and of all of them
+  uint64_t gstage_max = 0, gstage_sum = 0;
   std::unique_ptr<FieldMeta> meta0{new FieldMeta()};
   // one device buffer holding levels, perm, chunk map and meta0
   unsigned char* d_buf = nullptr;

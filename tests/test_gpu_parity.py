@@ -51,6 +51,12 @@ def _fields():
         "cells_2d": S.blobs((1, 64, 128), seed=13).numpy(),
         "cells_three_words": S.spectral((5, 9, 192), seed=14).numpy(),
         "cells_256": S.spectral((24, 40, 256), seed=15).numpy(),
+        # large levels of any size take the general cell kernels (staged transposes)
+        "gcells_odd": S.spectral((45, 47, 49), seed=16).numpy(),
+        "gcells_f64": S.blobs((40, 36, 44), seed=17, dtype=torch.float64).numpy(),
+        "gcells_2d": S.spectral((1, 300, 250), seed=18).numpy(),
+        "gcells_1d": S.blobs((1, 1, 70001), seed=19).numpy(),
+        "gcells_two_levels": S.spectral((90, 100, 110), seed=20).numpy(),
     }
 
 

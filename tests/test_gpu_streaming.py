@@ -141,7 +141,7 @@ def test_compact_and_drop_cache(ctx, shape, dtype):
             assert np.array_equal(out.cpu().numpy().view(np.uint8), ref.view(np.uint8))
             assert info.bytes_fetched_total >= prev
             prev = info.bytes_fetched_total
-        assert h.memory()[1] == cache_max
+        assert 0 < h.memory()[1] <= cache_max  # the transient staging is not held
         # tightening decoded only new groups; after dropping the cache the next
         # retrieval fetches everything it uses again
         h.drop_cache()
