@@ -369,6 +369,19 @@ def bench_streaming(args, binding):
     out = torch.empty(shape, dtype=torch.float64).pin_memory()
     ctx = binding.Context()
     fbytes = host.numel() * 8
+    # the host link: pinned copies of 1 GiB each way
+    probe_d = torch.empty(1 << 27, dtype=torch.float64, device="cuda")
+    probe_h = host.view(-1)[: 1 << 27]
+    link = {}
+    for name, dst, src in (("h2d", probe_d, probe_h), ("d2h", probe_h, probe_d)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        link[name] = 3 * (1 << 30) / (time.perf_counter() - t0) / 1e9
+    del probe_d
     res = {}
     for ns in (1, 3):
         def step():
@@ -391,7 +404,11 @@ def bench_streaming(args, binding):
             "gbs": round(7 * fbytes / res[3] / 1e9, 3),
             "gbs_one_stream": round(7 * fbytes / res[1] / 1e9, 3),
             "overlap_gain": round(res[1] / res[3], 2), "ms_per_step": round(1e3 * res[3], 2),
-            "streams": 3, "h2d_bytes_per_step": fbytes, "d2h_bytes_per_step": 6 * fbytes}
+            "streams": 3, "h2d_bytes_per_step": fbytes, "d2h_bytes_per_step": 6 * fbytes,
+            "link_gbs": {k: round(v, 1) for k, v in link.items()},
+            # the step's copies alone at the probed rates, against its time
+            "link_frac": round((fbytes / (link["h2d"] * 1e9) + 6 * fbytes / (link["d2h"] * 1e9))
+                               / res[3], 3)}
 
 
 # -------------------------------------------------------------- our arm
