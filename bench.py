@@ -293,6 +293,52 @@ def bench_serving(args, binding):
             "setup_s": round(setup_s, 1)}
 
 
+# ------------------------------------------------ lossless strategy comparison
+def bench_lossless(args, binding, field):
+    """The 512^3 field refactored and retrieved with every group Huffman-coded,
+    RLE-coded, or chosen by Algorithm 2 at T_cr = 1, 2, 4 (Sec. 7.2.2)."""
+    import ctypes as C
+    import torch
+    stream = torch.cuda.current_stream()
+    out = torch.empty_like(field)
+    fbytes = field.numel() * field.element_size()
+    variants = [("hybrid T_cr=1", dict(cr_num=1, cr_den=1)), ("hybrid T_cr=2", {}),
+                ("hybrid T_cr=4", dict(cr_num=4, cr_den=1)),
+                ("huffman only", dict(method=binding.HUFFMAN)),
+                ("rle only", dict(method=binding.RLE)), ("direct copy only", dict(method=binding.DC))]
+    res = []
+    for name, kw in variants:
+        ctx = binding.Context(**kw)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for rep in range(2):  # the second run is timed
+            ev[0].record(stream)
+            h = ctx.refactor(field)
+            ev[1].record(stream)
+            fetched = []
+            for tau in TAUS:
+                _, info, _ = h.retrieve(tau, out=out)
+                fetched.append(info.bytes_fetched_total)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            stored = 0
+            nlev = h.field_info()["nlevels"]
+            for l in range(nlev):
+                for g in range(h.level_info(l)[2]):  # stored lengths only, no copy
+                    ln, m = C.c_uint64(), C.c_int()
+                    binding.lib().hpmdr_handle_group(h._p, l, g, None, C.byref(ln), C.byref(m),
+                                                     (C.c_uint64 * 2)())
+                    stored += ln.value
+            h.free()
+        ref_ms, ret_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        res.append({"variant": name, "refactor_gbs": round(fbytes / (ref_ms * 1e-3) / 1e9, 2),
+                    "retrieve_gbs": round(6 * fbytes / (ret_ms * 1e-3) / 1e9, 2),
+                    "stored_bytes": stored, "ratio": round(fbytes / stored, 3),
+                    "fetched_bytes": fetched})
+        ctx.close()
+    return {"workload": "the 512^3 FP32 field: refactor + 6 incremental retrievals per variant",
+            "variants": res}
+
+
 # ------------------------------------------------------------ batched path
 def bench_batched(args, binding):
     """256 FP32 fields (per-axis sizes log-uniform in [32, 256]) refactored and
@@ -530,6 +576,10 @@ def run_ours(args):
         del field, out, host_in, host_out
         torch.cuda.empty_cache()
         extra = {}
+        if not args.no_ablation:
+            f2 = make_field(n, 2 + rank, "cuda")
+            extra["lossless_ablation"] = bench_lossless(args, binding, f2)
+            del f2
         if not args.no_serving:
             extra["serving"] = bench_serving(args, binding)
         if not args.no_batched:
@@ -571,6 +621,7 @@ def main():
     ap.add_argument("--ref-side", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-streaming", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)

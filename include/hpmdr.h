@@ -70,7 +70,11 @@ typedef struct {
   int group_m;              /* only 4 is supported */
   uint64_t size_threshold;  /* T_s: groups of S <= T_s bytes are copied */
   uint32_t cr_num, cr_den;  /* T_cr = cr_num / cr_den */
-  uint64_t reserved[4];
+  int32_t method;           /* 0: Algorithm 2 picks per group; 1 + HPMDR_DC / HPMDR_HUFFMAN /
+                               HPMDR_RLE: every group stored with that method (the lossless-
+                               strategy comparison of Sec. 7.2.2; slots sized for the worst case) */
+  int32_t reserved0;
+  uint64_t reserved[3];
 } hpmdr_config;
 
 typedef struct hpmdr_ctx hpmdr_ctx;        /* stream, allocator, workspace */

@@ -19,7 +19,8 @@ DC, HUFFMAN, RLE, PLACEHOLDER = 0, 1, 2, 3
 
 class Config(C.Structure):
     _fields_ = [("group_m", C.c_int), ("size_threshold", C.c_uint64), ("cr_num", C.c_uint32),
-                ("cr_den", C.c_uint32), ("reserved", C.c_uint64 * 4)]
+                ("cr_den", C.c_uint32), ("method", C.c_int32), ("reserved0", C.c_int32),
+                ("reserved", C.c_uint64 * 3)]
 
 
 class Allocator(C.Structure):
@@ -185,8 +186,9 @@ def _dtype_code(t):
 class Context:
     """hpmdr_ctx bound to a CUDA stream (torch's current stream by default)."""
 
-    def __init__(self, size_threshold=0, cr_num=0, cr_den=0, stream=None):
-        cfg = Config(4, size_threshold, cr_num, cr_den)
+    def __init__(self, size_threshold=0, cr_num=0, cr_den=0, stream=None, method=None):
+        """method: None for Algorithm 2, else DC / HUFFMAN / RLE for every group."""
+        cfg = Config(4, size_threshold, cr_num, cr_den, 0 if method is None else method + 1)
         self._p = vp()
         _check(lib().hpmdr_ctx_create(C.byref(self._p), C.byref(cfg), None, _stream_ptr(stream)),
                "hpmdr_ctx_create")

@@ -73,6 +73,7 @@ struct hpmdr_batch {
   cudaEvent_t ev = nullptr;
   uint64_t Ts = 4096;
   uint32_t cr_num = 2, cr_den = 1;
+  int force = -1;
   int dtype = 0;
   uint32_t n = 0;
   int sms = 152;
@@ -284,7 +285,7 @@ struct hpmdr_batch {
                   dtype == 0 ? 32 : 64, g, s);
     launch_b_encode(d_jobs, tab<uint32_t>(o_gen), n, t_gen, dtype, g, s);
     launch_b_chunk_stats(d_jobs, tab<uint32_t>(o_chunks), n, t_chunks, g, s);
-    launch_b_decide(d_jobs, tab<uint32_t>(o_groups), n, t_groups, Ts, cr_num, cr_den, g, s);
+    launch_b_decide(d_jobs, tab<uint32_t>(o_groups), n, t_groups, Ts, cr_num, cr_den, force, g, s);
     launch_b_huff_bits(d_jobs, tab<uint32_t>(o_chunks), n, t_chunks, g, s);
     launch_b_group_offsets(d_jobs, tab<uint32_t>(o_groups), n, t_groups, g, s);
     launch_b_huff_encode(d_jobs, tab<uint32_t>(o_chunks), n, t_chunks, g, s);
@@ -368,6 +369,7 @@ extern "C" hpmdr_status hpmdr_batch_create(hpmdr_ctx* ctx, uint64_t n, const uin
   b->Ts = ctx->Ts;
   b->cr_num = ctx->cr_num;
   b->cr_den = ctx->cr_den;
+  b->force = ctx->force;
   b->dtype = dtype;
   b->n = (uint32_t)n;
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, ctx->device);

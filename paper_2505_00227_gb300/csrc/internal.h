@@ -244,7 +244,8 @@ uint32_t cell_tiles(const LevelDesc& L);
 void launch_b_chunk_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                           uint32_t total, uint32_t grid, cstream s);
 void launch_b_decide(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
-                     uint64_t Ts, uint32_t cr_num, uint32_t cr_den, uint32_t grid, cstream s);
+                     uint64_t Ts, uint32_t cr_num, uint32_t cr_den, int force, uint32_t grid,
+                     cstream s);
 void launch_b_huff_bits(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                         uint32_t total, uint32_t grid, cstream s);
 void launch_b_group_offsets(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,

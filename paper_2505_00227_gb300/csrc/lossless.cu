@@ -1202,8 +1202,8 @@ __global__ void __launch_bounds__(256) kb_chunk_stats(HP_BATCH_PARAMS) {
   HP_BATCH_UNITS(chunk_stats_unit(J.planes, J.meta, J.chunk_group, J.hist, J.gcost, J.ccost, local))
 }
 __global__ void __launch_bounds__(256) kb_decide(HP_BATCH_PARAMS, uint64_t Ts, uint32_t cr_num,
-                                                 uint32_t cr_den) {
-  HP_BATCH_UNITS(decide_unit(J.meta, J.hist, J.gcost, J.lens, Ts, cr_num, cr_den, -1, local))
+                                                 uint32_t cr_den, int force) {
+  HP_BATCH_UNITS(decide_unit(J.meta, J.hist, J.gcost, J.lens, Ts, cr_num, cr_den, force, local))
 }
 __global__ void __launch_bounds__(256) kb_huff_bits(HP_BATCH_PARAMS) {
   HP_BATCH_UNITS(huff_bits_unit(J.planes, J.meta, J.chunk_group, J.lens, J.cwords, local))
@@ -1229,10 +1229,11 @@ void launch_b_chunk_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t 
     hp::note_launch(), kb_chunk_stats<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
 }
 void launch_b_decide(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
-                     uint64_t Ts, uint32_t cr_num, uint32_t cr_den, uint32_t grid, cstream s) {
+                     uint64_t Ts, uint32_t cr_num, uint32_t cr_den, int force, uint32_t grid,
+                     cstream s) {
   if (total)
     hp::note_launch(), kb_decide<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total, Ts,
-                                                                       cr_num, cr_den);
+                                                                       cr_num, cr_den, force);
 }
 void launch_b_huff_bits(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                         uint32_t total, uint32_t grid, cstream s) {

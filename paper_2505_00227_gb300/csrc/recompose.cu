@@ -86,13 +86,12 @@ __global__ void __launch_bounds__(256) k_recompose_copy(const LevelDesc* __restr
 }
 
 // detail nodes of one level, one warp tile of 1024 level-linear nodes starting
-// at node `base`: lane = word for the inverse transpose, then lane = node
-template <typename T, int B, bool FINAL>
-__device__ __forceinline__ void recompose_tile(const uint32_t* __restrict__ P, const LevelDesc& L,
-                                               uint32_t base, int k, int bl, int E_f,
-                                               const int64_t* __restrict__ coarse,
-                                               void* __restrict__ dst, uint32_t* hi, uint32_t* lo,
-                                               uint32_t* sgn) {
+// at node `base`.  Words: lane = word, the inverse transpose of the top k
+// planes into the tile's shared rows (hi, lo) and sign words (sgn).
+template <int B>
+__device__ __forceinline__ void recompose_words(const uint32_t* __restrict__ P, const LevelDesc& L,
+                                                uint32_t base, int k, uint32_t* hi, uint32_t* lo,
+                                                uint32_t* sgn) {
   const int lane = threadIdx.x & 31;
   const uint32_t W = L.W;
   const uint32_t wi = base / 32 + lane;
@@ -112,50 +111,67 @@ __device__ __forceinline__ void recompose_tile(const uint32_t* __restrict__ P, c
     }
     sgn[lane] = k > 0 ? P[wi] : 0u;
   }
+}
+
+// row r of the tile (lane = node): dequantize, add the corners, store
+template <typename T, int B, bool FINAL>
+__device__ __forceinline__ void recompose_row(const LevelDesc& L, uint32_t base, int r, int bl,
+                                              int E_f, const int64_t* __restrict__ coarse,
+                                              void* __restrict__ dst, const uint32_t* hi,
+                                              const uint32_t* lo, const uint32_t* sgn) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t j = base + r * 32 + lane;
+  if (j >= L.n) return;
+  const uint64_t qh = B == 64 ? (((uint64_t)hi[r * 33 + lane] << 32) | lo[r * 33 + lane])
+                              : (uint64_t)hi[r * 33 + lane];
+  const bool neg = (sgn[r] >> lane) & 1u;
+  const int64_t c8 = dequant(qh, neg, B, bl);
+  const NodePos p = node_pos(L, j);
+  uint32_t zs[2], ys[2], xs[2];
+  int nz = 1, ny = 1, nx = 1;
+  zs[0] = zs[1] = p.gz >> 1;
+  ys[0] = ys[1] = p.gy >> 1;
+  xs[0] = xs[1] = p.gx >> 1;
+  if (p.t & 4) {
+    uint32_t a, b;
+    axis_nb(p.gz, L.g[0], a, b);
+    zs[0] = a >> 1; zs[1] = b >> 1; nz = 2;
+  }
+  if (p.t & 2) {
+    uint32_t a, b;
+    axis_nb(p.gy, L.g[1], a, b);
+    ys[0] = a >> 1; ys[1] = b >> 1; ny = 2;
+  }
+  if (p.t & 1) {
+    uint32_t a, b;
+    axis_nb(p.gx, L.g[2], a, b);
+    xs[0] = a >> 1; xs[1] = b >> 1; nx = 2;
+  }
+  int64_t sum = 0;
+  for (int a = 0; a < nz; a++)
+    for (int b = 0; b < ny; b++)
+      for (int c = 0; c < nx; c++)
+        sum += coarse[((size_t)zs[a] * L.gc[1] + ys[b]) * L.gc[2] + xs[c]];
+  const int nodd = __popc(p.t);
+  const int64_t X = floor_shift(c8 * ((int64_t)1 << nodd) + 8 * sum, 3 + nodd);
+  const size_t d = ((size_t)p.gz * L.g[1] + p.gy) * L.g[2] + p.gx;
+  if (FINAL) reinterpret_cast<T*>(dst)[d] = convert_out<T>(X, E_f);
+  else reinterpret_cast<int64_t*>(dst)[d] = X;
+}
+
+template <typename T, int B, bool FINAL>
+__device__ __forceinline__ void recompose_tile(const uint32_t* __restrict__ P, const LevelDesc& L,
+                                               uint32_t base, int k, int bl, int E_f,
+                                               const int64_t* __restrict__ coarse,
+                                               void* __restrict__ dst, uint32_t* hi, uint32_t* lo,
+                                               uint32_t* sgn) {
+  recompose_words<B>(P, L, base, k, hi, lo, sgn);
   __syncwarp();
   // rows are independent: unrolled so that the coarse loads of several rows
   // are in flight together
 #pragma unroll 4
-  for (int r = 0; r < 32; r++) {
-    const uint32_t j = base + r * 32 + lane;
-    if (j < L.n) {
-      const uint64_t qh = B == 64 ? (((uint64_t)hi[r * 33 + lane] << 32) | lo[r * 33 + lane])
-                                  : (uint64_t)hi[r * 33 + lane];
-      const bool neg = (sgn[r] >> lane) & 1u;
-      const int64_t c8 = dequant(qh, neg, B, bl);
-      const NodePos p = node_pos(L, j);
-      uint32_t zs[2], ys[2], xs[2];
-      int nz = 1, ny = 1, nx = 1;
-      zs[0] = zs[1] = p.gz >> 1;
-      ys[0] = ys[1] = p.gy >> 1;
-      xs[0] = xs[1] = p.gx >> 1;
-      if (p.t & 4) {
-        uint32_t a, b;
-        axis_nb(p.gz, L.g[0], a, b);
-        zs[0] = a >> 1; zs[1] = b >> 1; nz = 2;
-      }
-      if (p.t & 2) {
-        uint32_t a, b;
-        axis_nb(p.gy, L.g[1], a, b);
-        ys[0] = a >> 1; ys[1] = b >> 1; ny = 2;
-      }
-      if (p.t & 1) {
-        uint32_t a, b;
-        axis_nb(p.gx, L.g[2], a, b);
-        xs[0] = a >> 1; xs[1] = b >> 1; nx = 2;
-      }
-      int64_t sum = 0;
-      for (int a = 0; a < nz; a++)
-        for (int b = 0; b < ny; b++)
-          for (int c = 0; c < nx; c++)
-            sum += coarse[((size_t)zs[a] * L.gc[1] + ys[b]) * L.gc[2] + xs[c]];
-      const int nodd = __popc(p.t);
-      const int64_t X = floor_shift(c8 * ((int64_t)1 << nodd) + 8 * sum, 3 + nodd);
-      const size_t d = ((size_t)p.gz * L.g[1] + p.gy) * L.g[2] + p.gx;
-      if (FINAL) reinterpret_cast<T*>(dst)[d] = convert_out<T>(X, E_f);
-      else reinterpret_cast<int64_t*>(dst)[d] = X;
-    }
-  }
+  for (int r = 0; r < 32; r++)
+    recompose_row<T, B, FINAL>(L, base, r, bl, E_f, coarse, dst, hi, lo, sgn);
   __syncwarp();
 }
 
@@ -223,15 +239,24 @@ __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict_
     }
     const int k = 4 * m->cur[l], bl = m->bl[l];
     const uint32_t* P = planes + D.plane_off / 4;
-    for (uint32_t tile = w; tile < D.ntiles; tile += WPB) {
+    // the level's tiles (at most WPB: small levels) are unpacked by one warp
+    // each, then their 32 rows are spread over all warps
+    const uint32_t nt = D.ntiles;
+    if ((uint32_t)w < nt)
+      recompose_words<B>(P, D, w * HP_TILE, k, s_hi + w * 32 * 33,
+                         s_lo + (B == 64 ? w * 32 * 33 : 0), s_sign + w * 32);
+    __syncthreads();
+    for (uint32_t q = w; q < nt * 32; q += WPB) {
+      const uint32_t tile = q / 32;
+      const int r = (int)(q % 32);
       if (final)
-        recompose_tile<T, B, true>(P, D, tile * HP_TILE, k, bl, E_f, coarse, dst,
-                                   s_hi + w * 32 * 33, s_lo + (B == 64 ? w * 32 * 33 : 0),
-                                   s_sign + w * 32);
+        recompose_row<T, B, true>(D, tile * HP_TILE, r, bl, E_f, coarse, dst,
+                                  s_hi + tile * 32 * 33, s_lo + (B == 64 ? tile * 32 * 33 : 0),
+                                  s_sign + tile * 32);
       else
-        recompose_tile<T, B, false>(P, D, tile * HP_TILE, k, bl, E_f, coarse, dst,
-                                    s_hi + w * 32 * 33, s_lo + (B == 64 ? w * 32 * 33 : 0),
-                                    s_sign + w * 32);
+        recompose_row<T, B, false>(D, tile * HP_TILE, r, bl, E_f, coarse, dst,
+                                   s_hi + tile * 32 * 33, s_lo + (B == 64 ? tile * 32 * 33 : 0),
+                                   s_sign + tile * 32);
     }
     __syncthreads();
     coarse = (const int64_t*)dst;

@@ -164,7 +164,7 @@ static void plan_levels(Plan& P) {
 
 // group geometry (Sec. 5.2: B/4 groups of 4 planes, the sign plane in group 0)
 // and slot capacities; fills meta0
-static void plan_groups(Plan& P, uint64_t Ts, uint32_t num, uint32_t den) {
+static void plan_groups(Plan& P, uint64_t Ts, uint32_t num, uint32_t den, int force) {
   FieldMeta& M = *P.meta0;
   uint32_t chunk = 0;
   uint64_t slot = 0;
@@ -182,7 +182,13 @@ static void plan_groups(Plan& P, uint64_t Ts, uint32_t num, uint32_t den) {
         P.chunk_group.push_back((uint32_t)(l * P.ngroups + g));
       chunk += G.nchunks;
       G.stored_len = G.S;
-      if (G.S > Ts) {
+      if (force == HPMDR_HUFFMAN || force == HPMDR_RLE) {
+        // forced coding: the worst case (16 bits per Huffman symbol, or one
+        // (byte, length) record per byte) plus header and word padding
+        G.cap = round16(2 * G.S + 4ull * G.nchunks + 512);
+        G.slot_off = slot;
+        slot += G.cap;
+      } else if (force < 0 && G.S > Ts) {
         // a coded group is chosen only if S / est > num / den, so est < S den / num
         G.cap = round16((G.S * den + num - 1) / num) + 16;
         G.slot_off = slot;
@@ -217,13 +223,13 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Plans are cached process-wide per (device, shape, B, T_s, T_cr).  Handles
 // hold a reference, so a plan evicted from the cache lives on while used.
 hpmdr_status get_plan(int device, const uint64_t dims[3], int dtype, uint64_t Ts,
-                             uint32_t num, uint32_t den, std::shared_ptr<const Plan>* out) {
-  typedef std::array<uint64_t, 8> Key;
+                             uint32_t num, uint32_t den, int force, std::shared_ptr<const Plan>* out) {
+  typedef std::array<uint64_t, 9> Key;
   static std::mutex* mu = new std::mutex();  // never destroyed: usable during exit
   static std::map<Key, std::shared_ptr<const Plan>>* cache =
       new std::map<Key, std::shared_ptr<const Plan>>();
   const Key key = {(uint64_t)device, dims[0], dims[1], dims[2], (uint64_t)dtype, Ts,
-                   (uint64_t)num, (uint64_t)den};
+                   (uint64_t)num, (uint64_t)den, (uint64_t)(force + 1)};
   {
     std::lock_guard<std::mutex> lock(*mu);
     auto it = cache->find(key);
@@ -240,7 +246,7 @@ hpmdr_status get_plan(int device, const uint64_t dims[3], int dtype, uint64_t Ts
   plan_levels(*P);
   if (P->nlev > HP_MAX_LEVELS) return HPMDR_ERR_ARG;
   init_meta(*P->meta0, dtype, P->B, P->nlev, P->ngroups);
-  plan_groups(*P, Ts, num, den);
+  plan_groups(*P, Ts, num, den, force);
   const size_t o_lv = 0, o_perm = align256(sizeof(LevelDesc) * P->nlev);
   const size_t o_cg = o_perm + align256(4ull * std::max(P->total_tiles, 1u));
   const size_t o_meta = o_cg + align256(4ull * std::max(P->total_chunks, 1u));
@@ -271,7 +277,9 @@ hpmdr_status new_handle(hpmdr_ctx* ctx, int ndims, const uint64_t dims_in[3], in
   H.reset(new hpmdr_handle());
   HP_TRY(check_dims(ndims, dims_in, H->dims, &H->N));
   if (plan_in) H->plan = *plan_in;
-  else HP_TRY(get_plan(ctx->device, H->dims, dtype, ctx->Ts, ctx->cr_num, ctx->cr_den, &H->plan));
+  else
+    HP_TRY(get_plan(ctx->device, H->dims, dtype, ctx->Ts, ctx->cr_num, ctx->cr_den, ctx->force,
+                    &H->plan));
   const Plan& P = *H->plan;
   H->A = ctx->A;
   H->stream = ctx->stream;
@@ -314,6 +322,8 @@ extern "C" hpmdr_status hpmdr_ctx_create(hpmdr_ctx** out, const hpmdr_config* cf
       c->cr_num = cfg->cr_num;
       c->cr_den = cfg->cr_den;
     }
+    if (cfg->method < 0 || cfg->method > 3) return HPMDR_ERR_ARG;
+    c->force = cfg->method - 1;
   }
   int ndev = 0;
   HP_CUDA(cudaGetDeviceCount(&ndev));
@@ -436,8 +446,8 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   { ProfScope p(P, ST_CHUNK_STATS, pb + cb, s);
     launch_chunk_stats(H->d_planes, H->d_meta, cm, d_hist, d_gcost, d_cost, s); }
   { ProfScope p(P, ST_DECIDE, cb, s);
-    launch_decide(H->d_meta, ngt, d_hist, d_gcost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den, -1,
-                  s); }
+    launch_decide(H->d_meta, ngt, d_hist, d_gcost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den,
+                  ctx->force, s); }
   { ProfScope p(P, ST_HUFF_BITS, 0, s); rp->hbits = p.i;
     launch_huff_bits(H->d_planes, H->d_meta, cm, d_lens, d_words, s); }
   { ProfScope p(P, ST_OFFSETS, 0, s);

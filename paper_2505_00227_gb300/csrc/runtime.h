@@ -149,6 +149,7 @@ struct hpmdr_ctx {
   int device = 0;
   uint64_t Ts = 4096;
   uint32_t cr_num = 2, cr_den = 1;
+  int force = -1;  // -1: Algorithm 2; else the method every group is stored with
   Allocator A;
   Profiler prof;
   std::vector<cudaStream_t> aux;  // extra streams of the chunk pipelines (created on demand)
@@ -240,7 +241,7 @@ uint64_t round16(uint64_t v);
 size_t align256(size_t v);
 hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t dims[3], uint64_t* N);
 hpmdr_status get_plan(int device, const uint64_t dims[3], int dtype, uint64_t Ts, uint32_t num,
-                      uint32_t den, std::shared_ptr<const Plan>* out);
+                      uint32_t den, int force, std::shared_ptr<const Plan>* out);
 // a handle with the plan of (ndims, dims, dtype) under ctx's coder settings
 hpmdr_status new_handle(hpmdr_ctx* ctx, int ndims, const uint64_t dims_in[3], int dtype,
                         const std::shared_ptr<const Plan>* plan_in,

@@ -36,10 +36,12 @@ __device__ __forceinline__ u128 sat_add(u128 a, u128 b) {
 struct SeqView {
   int B, nlev, ngroups, dtype, E_f, input_exact;
   int bl[HP_MAX_LEVELS], exact[HP_MAX_LEVELS];
-  uint64_t len[HP_MAX_LEVELS][HP_MAX_GROUPS];
+  int lim[HP_MAX_LEVELS];  // groups of the level that still reduce its error
+  // stored bytes per unit of error removed, len / 2^(bl - 4g): exact in double
+  // (len < 2^53, a power-of-two scale), so comparing keys is comparing the
+  // greedy ratios 2^(bl-4g) / len exactly
+  double key[HP_MAX_LEVELS][HP_MAX_GROUPS];
 };
-
-__device__ __forceinline__ uint64_t stored_len(const SeqView* m, int l, int g) { return m->len[l][g]; }
 
 template <class M>
 __device__ u128 level_delta(const M* m, int l, int k) {
@@ -47,17 +49,6 @@ __device__ u128 level_delta(const M* m, int l, int k) {
   if (bl == 0 || k >= bl) return 0;
   if (k >= m->B && m->exact[l]) return 0;
   return p2(bl - k + m->B);
-}
-
-// 2^(bl_a-k_a) * bytes_b > 2^(bl_b-k_b) * bytes_a, ties to the smaller level
-template <class M>
-__device__ bool better(const M* m, const int* g, int a, int b) {
-  const int sa = m->bl[a] - 4 * g[a], sb = m->bl[b] - 4 * g[b];
-  const u128 ba = stored_len(m, a, g[a]), bb = stored_len(m, b, g[b]);
-  const int lo = sa < sb ? sa : sb;
-  const u128 left = bb << (sa - lo), right = ba << (sb - lo);
-  if (left != right) return left > right;
-  return a < b;
 }
 
 // E from the sum of the per-level truncation errors (same terms as estimate())
@@ -96,7 +87,6 @@ __device__ __forceinline__ void sequence_warp(FieldMeta* m, int* g) {
       V.bl[l] = m->bl[l];
     }
   }
-  for (int i = lane; i < nlev * ng; i += 32) V.len[i / ng][i % ng] = m->grp[i / ng][i % ng].stored_len;
   if (lane == 0) {
     V.B = m->B;
     V.nlev = nlev;
@@ -106,40 +96,78 @@ __device__ __forceinline__ void sequence_warp(FieldMeta* m, int* g) {
     V.input_exact = m->input_exact;
   }
   __syncwarp();
-  const SeqView* v = &V;
-  u128 sum = 0;
-  if (lane == 0) {
-    for (int l = 0; l < nlev; l++) sum += level_delta(v, l, 0);
-    const u128 E = finish_estimate(v, sum);
-    m->E_hi[0] = (uint64_t)(E >> 64);
-    m->E_lo[0] = (uint64_t)E;
+  for (int i = lane; i < nlev * ng; i += 32) {
+    const int l = i / ng, q = i % ng;
+    V.key[l][q] = ldexp((double)m->grp[l][q].stored_len, -(V.bl[l] - 4 * q));
   }
+  const SeqView* v = &V;
+  for (int l = lane; l < nlev; l += 32) {
+    int q = 0;
+    while (q < ng && level_delta(v, l, 4 * q) != 0) q++;
+    V.lim[l] = q;
+  }
+  __syncwarp();
+  // 1. the sequence: repeatedly the level with the smallest key (ties to the
+  // smaller level) among those with a group left that reduces the error
+  __shared__ uint8_t s_seq[HP_SEQ_MAX], s_gq[HP_SEQ_MAX];
   int n = 0;
   while (n < HP_SEQ_MAX) {
     int best = -1;
+    double bk = 0;
     for (int l = lane; l < nlev; l += 32) {
-      if (g[l] >= ng || level_delta(v, l, 4 * g[l]) == 0) continue;
-      if (best < 0 || better(v, g, l, best)) best = l;
+      const int q = g[l];
+      if (q >= V.lim[l]) continue;
+      const double k = V.key[l][q];
+      if (best < 0 || k < bk) best = l, bk = k;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-      const int other = __shfl_xor_sync(HP_FULL, best, o);
-      if (other >= 0 && (best < 0 || better(v, g, other, best))) best = other;
+      const int ob = __shfl_xor_sync(HP_FULL, best, o);
+      const double ok = __shfl_xor_sync(HP_FULL, bk, o);
+      if (ob >= 0 && (best < 0 || ok < bk || (ok == bk && ob < best))) best = ob, bk = ok;
     }
     if (best < 0) break;
     if (lane == 0) {
-      sum -= level_delta(v, best, 4 * g[best]);
+      s_seq[n] = (uint8_t)best;
+      s_gq[n] = (uint8_t)g[best];
       g[best]++;
-      sum += level_delta(v, best, 4 * g[best]);
-      m->seq[n] = (uint8_t)best;
-      const u128 E = finish_estimate(v, sum);
-      m->E_hi[n + 1] = (uint64_t)(E >> 64);
-      m->E_lo[n + 1] = (uint64_t)E;
     }
     n++;
     __syncwarp();
   }
-  if (lane == 0) m->seq_len = n;
+  // 2. the estimate after every prefix: sum_n = S0 - (r_0 + ... + r_{n-1}),
+  // r_i = delta(l_i, 4 g_i) - delta(l_i, 4 g_i + 4) >= 0, an exact 128-bit
+  // prefix sum (lane = block of consecutive steps, then a warp scan)
+  u128 S0 = 0;
+  for (int l = 0; l < nlev; l++) S0 += level_delta(v, l, 0);
+  auto r_of = [&](int i) {
+    const int l = s_seq[i], q = s_gq[i];
+    return level_delta(v, l, 4 * q) - level_delta(v, l, 4 * q + 4);
+  };
+  const int per = (n + 31) / 32, i0 = lane * per, i1 = min(n, i0 + per);
+  u128 tot = 0;
+  for (int i = i0; i < i1; i++) tot += r_of(i);
+  u128 incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t hi = __shfl_up_sync(HP_FULL, (unsigned long long)(incl >> 64), o);
+    const uint64_t lo = __shfl_up_sync(HP_FULL, (unsigned long long)incl, o);
+    if (lane >= o) incl += ((u128)hi << 64) | lo;
+  }
+  u128 run = incl - tot;  // before this lane's block
+  for (int i = i0; i < i1; i++) {
+    run += r_of(i);
+    const u128 E = finish_estimate(v, S0 - run);
+    m->seq[i] = s_seq[i];
+    m->E_hi[i + 1] = (uint64_t)(E >> 64);
+    m->E_lo[i + 1] = (uint64_t)E;
+  }
+  if (lane == 0) {
+    const u128 E = finish_estimate(v, S0);
+    m->E_hi[0] = (uint64_t)(E >> 64);
+    m->E_lo[0] = (uint64_t)E;
+    m->seq_len = n;
+  }
 }
 
 __global__ void k_sequence(FieldMeta* m) {
@@ -190,18 +218,31 @@ __device__ void select_prefix(FieldMeta* m, double tau, int tau_is_abs, Retrieve
   }
   const double tau_abs = tau_is_abs ? tau : __dmul_rn(tau, m->range);
   const int n = m->seq_len, nlev = m->nlev, ng = m->ngroups;
-  if (lane == 0) {
+  {
+    // the estimates never increase along the sequence: the shortest prefix
+    // whose estimate meets the bound is the number of prefixes that do not.
+    // Lanes test 32 prefixes at a time (a stride search, then a fine one).
     const u128 T = tau_units(tau_abs, m->E_f, m->B);
-    // the estimates never increase along the sequence: binary search for the
-    // shortest prefix whose estimate meets the bound
-    int lo = 0, hi = n + 1;  // answer in [lo, hi]; hi = n + 1 means none
-    while (lo < hi) {
-      const int mid = (lo + hi) / 2;
-      const u128 E = ((u128)m->E_hi[mid] << 64) | m->E_lo[mid];
-      if (E <= T) hi = mid;
-      else lo = mid + 1;
+    auto fails = [&](int i) {  // prefix i does not meet the bound
+      if (i > n) return false;
+      const u128 E = ((u128)m->E_hi[i] << 64) | m->E_lo[i];
+      return E > T;
+    };
+    const int stride = (n + 1 + 31) / 32;  // prefixes 0..n
+    const unsigned coarse = __ballot_sync(HP_FULL, fails(lane * stride));
+    const int first_ok = coarse == HP_FULL ? 32 : __ffs(~coarse) - 1;  // first chunk start that meets
+    // the answer lies in ((first_ok - 1) * stride, first_ok * stride]
+    const int base = first_ok == 0 ? 0 : (first_ok - 1) * stride + 1;
+    int c = first_ok * stride;  // no prefix meets it: c > n after the clamp below
+    for (int b0 = base; b0 < first_ok * stride && b0 <= n; b0 += 32) {
+      const unsigned fine = __ballot_sync(HP_FULL, b0 + lane < first_ok * stride && fails(b0 + lane));
+      if (fine != HP_FULL) {
+        c = b0 + __ffs(~fine) - 1;
+        break;
+      }
     }
-    s_c = lo;
+    if (first_ok == 0) c = 0;
+    if (lane == 0) s_c = c > n ? n + 1 : c;
   }
   for (int l = lane; l <= HP_MAX_LEVELS; l += 32) s_g[l] = 0;
   __syncwarp();
@@ -215,8 +256,14 @@ __device__ void select_prefix(FieldMeta* m, double tau, int tau_is_abs, Retrieve
   uint64_t bnew = 0, btot = 0;
   for (int l = lane; l < nlev; l += 32) {
     const int gl = s_g[l], f0 = m->fetched[l], fe = gl > f0 ? gl : f0;
-    for (int q = f0; q < gl; q++) bnew += m->grp[l][q].stored_len;
-    for (int q = 0; q < fe; q++) btot += m->grp[l][q].stored_len;
+#pragma unroll
+    for (int q = 0; q < HP_MAX_GROUPS; q++) {  // unrolled: the loads issue together
+      if (q < fe) {
+        const uint64_t len = m->grp[l][q].stored_len;
+        btot += len;
+        if (q >= f0 && q < gl) bnew += len;
+      }
+    }
   }
   bnew = warp_sum_u64(bnew);
   btot = warp_sum_u64(btot);
