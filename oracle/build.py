@@ -8,7 +8,8 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["decompose.c", "bitplane.c", "lossless.c", "select.c", "qoi.c", "pipeline.c"]
+SOURCES = ["decompose.c", "bitplane.c", "lossless.c", "select.c", "qoi.c", "pipeline.c",
+           "qoi_iter.c"]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhpmdr_oracle.so")
 

@@ -142,6 +142,30 @@ const uint32_t* or_field_planes(const or_field* F, int l);
 const uint8_t*  or_field_group(const or_field* F, int l, int g, uint64_t* len, int* method,
                                uint64_t est[2]);
 
+/* Estimate (absolute) of the first g[l] groups of every level */
+void      or_field_estimate(const or_field* F, const int* g, double* E_abs);
+
+/* ---- QoI: total velocity V = vx^2 + vy^2 + vz^2, iterated (qoi_iter.c) -- */
+enum { OR_EST_CP = 0, OR_EST_MA = 1, OR_EST_MAPE = 2 };
+#define OR_QOI_MAX_ITERATIONS 4096
+#define OR_QOI_MAX_HALVINGS 1100
+typedef struct {
+  int status, iterations;
+  double tau_abs, est, eps[3];     /* requested, final QoI bound, final data estimates */
+  int prefix[3];                   /* sequence steps retrieved per variable */
+  int g[3][OR_MAX_LEVELS];         /* groups per level per variable */
+} or_qoi_report;
+double or_vtotal(float x, float y, float z);
+void   or_vtotal_range(const float* vx, const float* vy, const float* vz, uint64_t N,
+                       double* vmin, double* vmax);
+double or_vtotal_point_bound(float x, float y, float z, const double e[3]);
+double or_vtotal_bound(const float* x, const float* y, const float* z, uint64_t N,
+                       const double e[3], uint64_t* arg);
+double or_field_prefix_estimate(const or_field* F, int k);
+int    or_qoi_vtotal(const or_field* const F[3], uint64_t N, double vt_min, double vt_max,
+                     double tau_rel, int estimator, double c, float* out[3], float* qoi,
+                     or_qoi_report* rep);
+
 #ifdef __cplusplus
 }
 #endif

@@ -111,6 +111,14 @@ int or_field_select(const or_field* F, double tau_abs, int* g, double* E_abs, ui
   return or_select(&m, tau_abs, g, E_abs, E_hi, E_lo);
 }
 
+void or_field_estimate(const or_field* F, const int* g, double* E_abs) {
+  or_sel_meta m;
+  sel_meta(F, &m);
+  uint64_t hi, lo;
+  or_estimate(&m, g, &hi, &lo);
+  *E_abs = or_units_to_abs(hi, lo, F->E_f, F->B);
+}
+
 int or_field_sequence(const or_field* F, int* seq, int cap) {
   or_sel_meta m;
   sel_meta(F, &m);

@@ -35,6 +35,15 @@ class Stats(C.Structure):
                 ("range", C.c_double), ("E_f", C.c_int), ("input_exact", C.c_int)]
 
 
+class QoiReport(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("tau_abs", C.c_double),
+                ("est", C.c_double), ("eps", C.c_double * 3), ("prefix", C.c_int * 3),
+                ("g", (C.c_int * 64) * 3)]
+
+
+EST_CP, EST_MA, EST_MAPE = 0, 1, 2
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -88,6 +97,15 @@ def lib():
             "or_field_level": (None, [vp, C.c_int, u64p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "or_field_planes": (vp, [vp, C.c_int]),
             "or_field_group": (vp, [vp, C.c_int, C.c_int, u64p, C.POINTER(C.c_int), vp]),
+            "or_field_estimate": (None, [vp, vp, C.POINTER(C.c_double)]),
+            "or_vtotal": (C.c_double, [C.c_float, C.c_float, C.c_float]),
+            "or_vtotal_range": (None, [vp, vp, vp, C.c_uint64, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]),
+            "or_vtotal_point_bound": (C.c_double, [C.c_float, C.c_float, C.c_float, vp]),
+            "or_vtotal_bound": (C.c_double, [vp, vp, vp, C.c_uint64, vp, u64p]),
+            "or_field_prefix_estimate": (C.c_double, [vp, C.c_int]),
+            "or_qoi_vtotal": (C.c_int, [vp, C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_int,
+                                        C.c_double, vp, vp, C.POINTER(QoiReport)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -438,3 +456,42 @@ class Field:
         rc = lib().or_retrieve(self._h, tau_abs, _p(out), _p(g), C.byref(E), C.byref(hi),
                                C.byref(lo))
         return rc, out, g, E.value
+
+
+# ---------------------------------------------- QoI: total velocity, iterated
+def vtotal(x, y, z):
+    return float(lib().or_vtotal(float(x), float(y), float(z)))
+
+
+def vtotal_range(vx, vy, vz):
+    a = [np.ascontiguousarray(v, dtype=np.float32) for v in (vx, vy, vz)]
+    lo, hi = C.c_double(), C.c_double()
+    lib().or_vtotal_range(_p(a[0]), _p(a[1]), _p(a[2]), a[0].size, C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def vtotal_point_bound(x, y, z, e):
+    ee = np.ascontiguousarray(e, dtype=np.float64)
+    return float(lib().or_vtotal_point_bound(float(x), float(y), float(z), _p(ee)))
+
+
+def vtotal_bound(x, y, z, e):
+    a = [np.ascontiguousarray(v, dtype=np.float32) for v in (x, y, z)]
+    ee = np.ascontiguousarray(e, dtype=np.float64)
+    arg = C.c_uint64()
+    b = lib().or_vtotal_bound(_p(a[0]), _p(a[1]), _p(a[2]), a[0].size, _p(ee), C.byref(arg))
+    return float(b), int(arg.value)
+
+
+def qoi_vtotal(fields, vt_min, vt_max, tau_rel, estimator, c=10.0):
+    """Algorithm 3 for V = vx^2+vy^2+vz^2 over three oracle Fields (FP32).
+    Returns (status, [x_hat, y_hat, z_hat], V_hat, report)."""
+    F = (C.c_void_p * 3)(*[f._h for f in fields])
+    shape = fields[0].shape
+    outs = [np.zeros(shape, dtype=np.float32) for _ in range(3)]
+    po = (C.c_void_p * 3)(*[o.ctypes.data for o in outs])
+    q = np.zeros(shape, dtype=np.float32)
+    rep = QoiReport()
+    st = lib().or_qoi_vtotal(F, int(np.prod(shape)), float(vt_min), float(vt_max), float(tau_rel),
+                             int(estimator), float(c), po, _p(q), C.byref(rep))
+    return st, outs, q, rep
