@@ -339,6 +339,39 @@ def bench_lossless(args, binding, field):
             "variants": res}
 
 
+# ------------------------------------------- iterated QoI (total velocity)
+def bench_qoi_iter(args, binding):
+    """V = vx^2 + vy^2 + vz^2 over a 256^3 FP32 triplet: Algorithm 3 with the
+    CP, MA and MAPE next-bound estimators (Sec. 6.2), from empty caches."""
+    import torch
+    from paper_2505_00227_gb300 import synthetic
+    n = args.qoi_side
+    comps = synthetic.velocity_triplet(n, seed=11, device="cuda", device_noise=True)
+    ctx = binding.Context()
+    hs = [ctx.refactor(c) for c in comps]
+    ctx.prepare_vtotal(hs, *comps)
+    fbytes = 3 * comps[0].numel() * 4
+    del comps
+    out_q = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    res = []
+    for name, est in (("CP", binding.EST_CP), ("MA", binding.EST_MA), ("MAPE", binding.EST_MAPE)):
+        for tau in (1e-2, 1e-4):
+            for h in hs:
+                h.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, rep, st = ctx.retrieve_qoi_vtotal(hs, tau, est, out_q=out_q)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            res.append({"estimator": name, "tau_rel": tau, "status": st,
+                        "iterations": rep.iterations, "bound": rep.est, "tau_abs": rep.tau_abs,
+                        "bytes_fetched": rep.bytes_fetched_total, "ms": round(1e3 * sec, 2),
+                        "gbs": round(fbytes / sec / 1e9, 2)})
+    return {"workload": f"{n}^3 FP32 velocity triplet (spectral), QoI vx^2+vy^2+vz^2, from empty "
+                        "plane caches; GB/s = the three components' bytes over the call's time",
+            "runs": res}
+
+
 # ------------------------------------------------------------ batched path
 def bench_batched(args, binding):
     """256 FP32 fields (per-axis sizes log-uniform in [32, 256]) refactored and
@@ -580,6 +613,8 @@ def run_ours(args):
             f2 = make_field(n, 2 + rank, "cuda")
             extra["lossless_ablation"] = bench_lossless(args, binding, f2)
             del f2
+        if not args.no_qoi:
+            extra["qoi_iterative"] = bench_qoi_iter(args, binding)
         if not args.no_serving:
             extra["serving"] = bench_serving(args, binding)
         if not args.no_batched:
@@ -622,6 +657,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-qoi", action="store_true")
+    ap.add_argument("--qoi-side", type=int, default=256)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-streaming", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)

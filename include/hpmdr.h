@@ -131,6 +131,40 @@ HPMDR_API hpmdr_status hpmdr_retrieve_qoi_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[3
                                      void* out[3], void* out_vmag, int on_device,
                                      hpmdr_retrieve_info info[4]);
 
+/* ---- iterated QoI retrieval (Sec. 6.2, Algorithm 3) for the total velocity
+ * V = vx^2 + vy^2 + vz^2 of three FP32 handles of equal shape (V evaluated in
+ * FP64, written as FP32).  hpmdr_qoi_prepare_vtotal records the range of V of
+ * the original data (it must fit FP32).  hpmdr_retrieve_qoi_vtotal starts from
+ * eps_i = (tau / max V) * (max v_i - min v_i), tau = rel_qoi_bound * (max V -
+ * min V), and repeats: retrieve every variable to eps_i, bound the QoI error
+ * pointwise (2 |x_hat| E + E^2 per variable plus the output rounding; the
+ * maximum tau' is computed on the device), stop if tau' <= tau, else choose
+ * the next bounds with the estimator:
+ *   HPMDR_EST_CP    halve all bounds until the point of the largest tau'
+ *                   meets tau (reconstruction held fixed);
+ *   HPMDR_EST_MA    one more merged bitplane group per variable;
+ *   HPMDR_EST_MAPE  p = tau'/tau: bounds E_i / p while p > c (0: c = 10),
+ *                   MA once p <= c.
+ * Components go to out[i] (may be NULL) and V_hat to out_qoi; rep (may be
+ * NULL) receives the iterations, the final bound and data estimates.
+ * HPMDR_ERR_UNATTAINABLE when every variable is fully retrieved and tau' > tau. */
+typedef enum { HPMDR_EST_CP = 0, HPMDR_EST_MA = 1, HPMDR_EST_MAPE = 2 } hpmdr_qoi_estimator;
+typedef struct {
+  int status, iterations;
+  double tau_abs;                /* requested QoI bound */
+  double est;                    /* final QoI error bound tau' */
+  double eps[3];                 /* final data error estimates */
+  int prefix[3];                 /* greedy-sequence steps retrieved per variable */
+  int pad;
+  uint64_t bytes_fetched_total;  /* stored bytes used, over the three variables */
+} hpmdr_qoi_report;
+HPMDR_API hpmdr_status hpmdr_qoi_prepare_vtotal(hpmdr_ctx* ctx, hpmdr_handle* v[3], const void* vx,
+                                                const void* vy, const void* vz, int on_device);
+HPMDR_API hpmdr_status hpmdr_retrieve_qoi_vtotal(hpmdr_ctx* ctx, hpmdr_handle* v[3],
+                                                 double rel_qoi_bound, int estimator, double c,
+                                                 void* out[3], void* out_qoi, int on_device,
+                                                 hpmdr_qoi_report* rep);
+
 /* ---- handle inspection -------------------------------------------------- */
 HPMDR_API hpmdr_status hpmdr_handle_field_info(const hpmdr_handle* h, int* dtype, uint64_t dims[3],
                                      int* nlevels, int* E_f, int* input_exact,

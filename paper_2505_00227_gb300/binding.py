@@ -44,6 +44,15 @@ class RetrieveInfo(C.Structure):
         return (self.est_units_hi << 64) | self.est_units_lo
 
 
+class QoiReport(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("tau_abs", C.c_double),
+                ("est", C.c_double), ("eps", C.c_double * 3), ("prefix", C.c_int * 3),
+                ("pad", C.c_int), ("bytes_fetched_total", C.c_uint64)]
+
+
+EST_CP, EST_MA, EST_MAPE = 0, 1, 2
+
+
 class Request(C.Structure):
     _fields_ = [("kind", C.c_int), ("h", C.c_void_p * 3), ("rel_bound", C.c_double),
                 ("out", C.c_void_p * 3), ("out_vmag", C.c_void_p)]
@@ -79,6 +88,9 @@ _SIGS = {
     "hpmdr_qoi_prepare_vmag": (C.c_int, [vp, vp * 3, vp, vp, vp, C.c_int]),
     "hpmdr_retrieve_qoi_vmag": (C.c_int, [vp, vp * 3, C.c_double, vp * 3, vp, C.c_int,
                                           RetrieveInfo * 4]),
+    "hpmdr_qoi_prepare_vtotal": (C.c_int, [vp, vp * 3, vp, vp, vp, C.c_int]),
+    "hpmdr_retrieve_qoi_vtotal": (C.c_int, [vp, vp * 3, C.c_double, C.c_int, C.c_double, vp * 3,
+                                            vp, C.c_int, C.POINTER(QoiReport)]),
     "hpmdr_handle_field_info": (C.c_int, [vp, ip, C.c_uint64 * 3, ip, ip, ip, C.c_double * 4]),
     "hpmdr_handle_level_info": (C.c_int, [vp, C.c_int, u64p, ip, ip, ip]),
     "hpmdr_handle_group": (C.c_int, [vp, C.c_int, C.c_int, vp, u64p, ip, C.c_uint64 * 2]),
@@ -296,6 +308,27 @@ class Context:
                                           int(nstreams), infos)
         _check(st, "hpmdr_retrieve_chunked", allow=(ERR_UNATTAINABLE,))
         return list(infos), st
+
+    def prepare_vtotal(self, handles, vx, vy, vz):
+        arr = (vp * 3)(*[h._p for h in handles])
+        _check(lib().hpmdr_qoi_prepare_vtotal(self._p, arr, vp(vx.data_ptr()), vp(vy.data_ptr()),
+                                              vp(vz.data_ptr()), int(vx.is_cuda)),
+               "hpmdr_qoi_prepare_vtotal")
+
+    def retrieve_qoi_vtotal(self, handles, rel_bound, estimator, c=0.0, outs=None, out_q=None):
+        """Algorithm 3 for V = vx^2+vy^2+vz^2; returns (V_hat, report, status)."""
+        import torch
+        ref = handles[0]
+        if out_q is None:
+            out_q = torch.empty(ref.shape, dtype=torch.float32, device="cuda")
+        arr = (vp * 3)(*[h._p for h in handles])
+        oarr = (vp * 3)(*[(vp(o.data_ptr()) if o is not None else None) for o in (outs or [None] * 3)])
+        rep = QoiReport()
+        st = lib().hpmdr_retrieve_qoi_vtotal(self._p, arr, float(rel_bound), int(estimator), float(c),
+                                             oarr, vp(out_q.data_ptr()), int(out_q.is_cuda),
+                                             C.byref(rep))
+        _check(st, "hpmdr_retrieve_qoi_vtotal", allow=(ERR_UNATTAINABLE,))
+        return out_q, rep, st
 
     def prepare_vmag(self, handles, vx, vy, vz):
         arr = (vp * 3)(*[h._p for h in handles])

@@ -18,7 +18,7 @@ UNITS = ["stats.cu", "decompose.cu", "lossless.cu", "select.cu", "recompose.cu",
          "runtime.cu", "noalloc.cu", "serve.cu", "batch.cu", "gcells.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-         "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include")]
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
 
 
 def _sources():

@@ -301,5 +301,13 @@ void launch_vmag_range(const float* vx, const float* vy, const float* vz, uint64
                        float* qrange /* device: [min, max] */, cstream s);
 void launch_vmag(const float* vx, const float* vy, const float* vz, uint64_t N, float* out,
                  cstream s);
+// total velocity V = vx^2 + vy^2 + vz^2 (FP64 evaluation, FP32 output)
+void launch_vtotal_range(const float* vx, const float* vy, const float* vz, uint64_t N,
+                         double* vrange /* device: [min, max] */, cstream s);
+uint32_t vtotal_bound_blocks(uint64_t N);
+// out = V_hat; best[0] = bits of the largest pointwise bound, best[1] = its
+// first point (best holds 2 * vtotal_bound_blocks(N) words)
+void launch_vtotal_bound(const float* vx, const float* vy, const float* vz, uint64_t N,
+                         const double e[3], float* out, unsigned long long* best, cstream s);
 
 }  // namespace hp

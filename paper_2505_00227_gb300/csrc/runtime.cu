@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -1029,6 +1030,202 @@ extern "C" hpmdr_status hpmdr_retrieve_qoi_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[
     if (own[c]) ctx->A.release(comp[c], s);
   if (!on_device) ctx->A.release(d_vm, s);
   return st != HPMDR_OK ? st : worst;
+}
+
+// ------------------------------------------- iterated QoI: total velocity
+extern "C" hpmdr_status hpmdr_qoi_prepare_vtotal(hpmdr_ctx* ctx, hpmdr_handle* v[3],
+                                                 const void* vx, const void* vy, const void* vz,
+                                                 int on_device) {
+  if (!ctx || !v || !v[0] || !v[1] || !v[2] || !vx || !vy || !vz) return HPMDR_ERR_ARG;
+  for (int c = 0; c < 3; c++)
+    if (v[c]->dtype != HPMDR_F32 || v[c]->N != v[0]->N) return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  const uint64_t N = v[0]->N;
+  const void* src[3] = {vx, vy, vz};
+  void* tmp[3] = {nullptr, nullptr, nullptr};
+  double* d_r = nullptr;
+  double r[2] = {0, 0};
+  hpmdr_status st = HPMDR_OK;
+  do {
+    for (int c = 0; c < 3 && !on_device; c++) {
+      if ((st = ctx->A.alloc(&tmp[c], N * 4, s))) break;
+      if (cudaMemcpyAsync(tmp[c], src[c], N * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        st = HPMDR_ERR_CUDA;
+        break;
+      }
+      src[c] = tmp[c];
+    }
+    if (st) break;
+    if ((st = ctx->A.alloc((void**)&d_r, 16, s))) break;
+    launch_vtotal_range((const float*)src[0], (const float*)src[1], (const float*)src[2], N, d_r, s);
+    if (cudaMemcpyAsync(r, d_r, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    if (!(r[1] <= 0x1.fffffep127)) st = HPMDR_ERR_ARG;  // V must fit FP32
+    for (int c = 0; c < 3; c++) {
+      v[c]->vt_min = r[0];
+      v[c]->vt_max = r[1];
+      v[c]->vt_ready = st == HPMDR_OK;
+    }
+  } while (0);
+  for (int c = 0; c < 3; c++) ctx->A.release(tmp[c], s);
+  ctx->A.release(d_r, s);
+  return st;
+}
+
+// absolute estimate after the first k steps of the handle's greedy sequence
+static double prefix_estimate(const hpmdr_handle* H, int k) {
+  const FieldMeta& M = *H->meta;
+  if (k > M.seq_len) k = M.seq_len;
+  const double v = ldexp((double)M.E_hi[k], 64) + (double)M.E_lo[k];
+  return ldexp(v, M.E_f - 51 - H->B);
+}
+
+// the pointwise bound at one point (same operations as the device's)
+static double vtotal_point_bound_host(const float xs[3], const double e[3]) {
+  double b = 0.0;
+  for (int i = 0; i < 3; i++) {
+    double t = 2.0 * fabs((double)xs[i]);
+    t = t * e[i];
+    const double u = e[i] * e[i];
+    t = t + u;
+    b = b + t;
+  }
+  const double a = (double)xs[0] * (double)xs[0], bb = (double)xs[1] * (double)xs[1];
+  const double c = (double)xs[2] * (double)xs[2];
+  const double v = (a + bb) + c;
+  if (v > 0x1.fffffep127) return INFINITY;
+  b = b + v * 0x1p-24;
+  if (v != 0.0) b = b + 0x1p-150;
+  b = b + v * 0x1p-50;
+  return b;
+}
+
+// Algorithm 3 for V = vx^2 + vy^2 + vz^2: retrieve every variable to its data
+// bound, bound the QoI error on the device, and choose the next bounds by the
+// requested estimator until the bound meets tau.
+extern "C" hpmdr_status hpmdr_retrieve_qoi_vtotal(hpmdr_ctx* ctx, hpmdr_handle* v[3], double rel,
+                                                  int estimator, double c, void* out[3],
+                                                  void* out_qoi, int on_device,
+                                                  hpmdr_qoi_report* rep) {
+  if (!ctx || !v || !out_qoi || !(rel >= 0.0) || estimator < 0 || estimator > 2) return HPMDR_ERR_ARG;
+  for (int i = 0; i < 3; i++)
+    if (!v[i] || !v[i]->vt_ready || v[i]->N != v[0]->N) return HPMDR_ERR_ARG;
+  if (c == 0.0) c = 10.0;  // the paper's threshold
+  const cudaStream_t s = ctx->stream;
+  const uint64_t N = v[0]->N;
+  const double vt_min = v[0]->vt_min, vt_max = v[0]->vt_max;
+  const double tau = rel * (vt_max - vt_min);
+  hpmdr_qoi_report R;
+  memset(&R, 0, sizeof(R));
+  R.tau_abs = tau;
+  double eps[3], E[3];
+  int nseq[3];
+  for (int i = 0; i < 3; i++) {
+    eps[i] = vt_max > 0.0 ? (tau / vt_max) * v[i]->meta->range : 0.0;
+    nseq[i] = v[i]->meta->seq_len;
+  }
+  void* comp[3] = {nullptr, nullptr, nullptr};
+  bool own[3] = {false, false, false};
+  void* d_q = on_device ? out_qoi : nullptr;
+  unsigned long long* d_best = nullptr;
+  hpmdr_status st = HPMDR_OK, status = HPMDR_ERR_UNATTAINABLE;
+  do {
+    for (int i = 0; i < 3; i++) {
+      if (on_device && out && out[i]) comp[i] = out[i];
+      else {
+        if ((st = ctx->A.alloc(&comp[i], N * 4, s))) break;
+        own[i] = true;
+      }
+    }
+    if (st) break;
+    if (!d_q && (st = ctx->A.alloc(&d_q, N * 4, s))) break;
+    if ((st = ctx->A.alloc((void**)&d_best, 16ull * vtotal_bound_blocks(N), s))) break;
+    for (int it = 1; it <= 4096 && st == HPMDR_OK; it++) {
+      bool full = true;
+      uint64_t fetched = 0;
+      for (int i = 0; i < 3 && st == HPMDR_OK; i++) {
+        hpmdr_retrieve_info inf;
+        if ((st = enqueue_retrieve(ctx, v[i], eps[i], 1, comp[i], s))) break;
+        hpmdr_status r = collect_info(ctx, v[i], &inf, s);
+        if (r != HPMDR_OK && r != HPMDR_ERR_UNATTAINABLE) {
+          st = r;
+          break;
+        }
+        E[i] = inf.est_linf;
+        int k = 0;
+        for (int l = 0; l < inf.nlevels; l++) k += inf.groups_per_level[l];
+        R.prefix[i] = k;
+        if (k < nseq[i]) full = false;
+        fetched += inf.bytes_fetched_total;
+      }
+      if (st) break;
+      launch_vtotal_bound((const float*)comp[0], (const float*)comp[1], (const float*)comp[2], N,
+                          E, (float*)d_q, d_best, s);
+      unsigned long long best[2];
+      if (cudaMemcpyAsync(best, d_best, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        st = HPMDR_ERR_CUDA;
+        break;
+      }
+      double bmax;
+      memcpy(&bmax, &best[0], 8);
+      const double bound = bmax * (1.0 + 0x1p-40);
+      R.iterations = it;
+      R.est = bound;
+      R.bytes_fetched_total = fetched;
+      for (int i = 0; i < 3; i++) R.eps[i] = E[i];
+      if (bound <= tau) {
+        status = HPMDR_OK;
+        break;
+      }
+      if (full) break;
+      bool ma = estimator == HPMDR_EST_MA;
+      if (estimator == HPMDR_EST_MAPE) {
+        const double p = bound / tau;
+        if (p > c) {
+          for (int i = 0; i < 3; i++) eps[i] = E[i] / p;
+        } else {
+          ma = true;
+        }
+      } else if (estimator == HPMDR_EST_CP) {
+        float xs[3];
+        for (int i = 0; i < 3; i++)
+          if (cudaMemcpyAsync(&xs[i], (const float*)comp[i] + best[1], 4, cudaMemcpyDeviceToHost,
+                              s) != cudaSuccess)
+            st = HPMDR_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) st = HPMDR_ERR_CUDA;
+        double e[3] = {E[0], E[1], E[2]};
+        for (int k = 0; k < 1100; k++) {
+          for (int i = 0; i < 3; i++) e[i] = e[i] * 0.5;
+          if (vtotal_point_bound_host(xs, e) * (1.0 + 0x1p-40) <= tau) break;
+        }
+        for (int i = 0; i < 3; i++) eps[i] = e[i];
+      }
+      if (ma)
+        for (int i = 0; i < 3; i++)
+          if (R.prefix[i] < nseq[i]) eps[i] = prefix_estimate(v[i], R.prefix[i] + 1);
+    }
+    if (st) break;
+    if (!on_device) {
+      for (int i = 0; i < 3; i++)
+        if (out && out[i] && cudaMemcpyAsync(out[i], comp[i], N * 4, cudaMemcpyDeviceToHost, s) !=
+                                 cudaSuccess)
+          st = HPMDR_ERR_CUDA;
+      if (cudaMemcpyAsync(out_qoi, d_q, N * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = HPMDR_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = HPMDR_ERR_CUDA;
+  } while (0);
+  for (int i = 0; i < 3; i++)
+    if (own[i]) ctx->A.release(comp[i], s);
+  if (!on_device) ctx->A.release(d_q, s);
+  ctx->A.release(d_best, s);
+  R.status = st != HPMDR_OK ? st : status;
+  if (rep) *rep = R;
+  return (hpmdr_status)R.status;
 }
 
 // ------------------------------------------------------------- inspection

@@ -214,6 +214,8 @@ struct hpmdr_handle {
   std::unique_ptr<FieldMeta> meta{new FieldMeta()};  // host mirror after refactor/import
   bool qoi_ready = false;
   float qmin = 0, qmax = 0;
+  bool vt_ready = false;  // total velocity range of the triplet this handle belongs to
+  double vt_min = 0, vt_max = 0;
   // profiler entries of the last retrieval, patched with bytes known after it
   std::vector<std::pair<size_t, int>> prof_lv;  // (entry, level*4 + kind)
   size_t prof_decode = SIZE_MAX, prof_small = SIZE_MAX;
