@@ -31,7 +31,8 @@ METRIC = ("refactor & retrieve GB/s (1 GB300) and % HBM roofline; served p50/p99
           "latency")
 TAUS = [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6]
 WORKLOAD = ("512^3 FP32 spectral field (P(k)~k^-11/3, rescaled to [-1,1], seed 2 + rank): "
-            "refactor + 6 incremental retrievals at relative Linf 1e-1..1e-6")
+            "refactor + 6 incremental retrievals at relative Linf 1e-1..1e-6, enqueued "
+            "back to back (hpmdr_retrieve_async, one wait)")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -405,6 +406,56 @@ def bench_lossless(args, binding, field):
             "variants": res}
 
 
+# ------------------------------------------------ bitplane encoder designs
+def bench_bpdesign(args, binding):
+    """The Sec. 4 encoder designs on 32-bit data: encode n values into 33 planes
+    (sign + 32) and decode all planes back, n = 2^20, 2^24, 2^27; L2 flushed
+    before every timed launch; median of 5."""
+    import torch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = []
+    for lg in (20, 24, 27):
+        n = 1 << lg
+        g = torch.Generator(device="cuda").manual_seed(lg)
+        q = torch.randint(-(2**31), 2**31 - 1, (n,), dtype=torch.int32, device="cuda", generator=g)
+        sign = torch.randint(0, 2, (n,), dtype=torch.uint8, device="cuda", generator=g)
+        W = 4 * ((n + 127) // 128)
+        planes = torch.empty(33 * W, dtype=torch.int32, device="cuda")
+        qo = torch.empty_like(q)
+        so = torch.empty_like(sign)
+        ref = None
+        for name, d in binding.BP_DESIGNS.items():
+            times = {"encode": [], "decode": []}
+            for rep in range(7):
+                for kind in ("encode", "decode"):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    if kind == "encode":
+                        binding.bitplane_encode_design(q, sign, d, planes=planes)
+                    else:
+                        binding.bitplane_decode_design(planes, n, d, 32, q=qo, sign=so)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if rep >= 2:
+                        times[kind].append(e0.elapsed_time(e1))
+            if ref is None:
+                ref = planes.clone()
+            same = bool(torch.equal(planes, ref)) and bool(torch.equal(qo, q))
+            row = {"design": name, "n": n, "same_bytes": same}
+            for kind in ("encode", "decode"):
+                ms = statistics.median(times[kind])
+                row[kind + "_gbs"] = round(4 * n / (ms * 1e-3) / 1e9, 1)
+            res.append(row)
+        del q, sign, planes, qo, so, ref
+    del flush
+    torch.cuda.empty_cache()
+    return {"workload": "uniform random 32-bit values and signs; GB/s of 32-bit input "
+                        "(encode) or output (decode), all 32 magnitude planes",
+            "results": res}
+
+
 # ------------------------------------------- iterated QoI (total velocity)
 def bench_qoi_iter(args, binding):
     """V = vx^2 + vy^2 + vz^2 over a 256^3 FP32 triplet: Algorithm 3 with the
@@ -581,15 +632,19 @@ def run_ours(args):
     out = torch.empty_like(field)
     stream = torch.cuda.current_stream()
 
-    def step(rec=None):
+    def step(rec=None, sync=False):
+        """refactor, then the 6 incremental retrievals enqueued back to back
+        (asynchronous API: no host round trip between them) and one wait;
+        sync=True: the blocking call per retrieval instead"""
         h = ctx.refactor(field)
         if rec is not None:
             rec.append(torch.cuda.Event(enable_timing=True))
             rec[-1].record(stream)
-        infos = []
-        for tau in TAUS:
-            _, info, st = h.retrieve(tau, out=out)
-            infos.append(info)
+        if sync:
+            infos = [h.retrieve(tau, out=out)[1] for tau in TAUS]
+        else:
+            infos = [h.retrieve_async(tau, out) for tau in TAUS]
+            ctx.wait()
         h.free()
         return infos
 
@@ -629,6 +684,17 @@ def run_ours(args):
     ms_max = slowest_rank(ms, world, "cuda")
     step_bytes = 7 * fbytes
     value = job_throughput(step_bytes, ms_max * 1e-3, world)
+
+    # ---- the same steps with a blocking call per retrieval ---------------
+    barrier()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(args.steps):
+        step(sync=True)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms_sync = slowest_rank(s0.elapsed_time(s1) / args.steps, world, "cuda")
 
     # ---- end to end through the C ABI with pinned host buffers ---------
     host_in = field.cpu().pin_memory()
@@ -683,6 +749,8 @@ def run_ours(args):
             del f2
         if not args.no_qoi:
             extra["qoi_iterative"] = bench_qoi_iter(args, binding)
+        if not args.no_bpdesign:
+            extra["bitplane_designs"] = bench_bpdesign(args, binding)
         if not args.no_serving:
             extra["serving"] = bench_serving(args, binding)
         if not args.no_batched:
@@ -697,6 +765,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "field_bytes": fbytes, "step_bytes": step_bytes,
                        "l2": "inputs larger than L2 (512 MiB per field)",
                        "parallelism": f"replicas x{world}"},
+            "value_blocking_retrievals": round(job_throughput(step_bytes, ms_sync * 1e-3, world), 3),
             "refactor_gbs": round(fbytes / (refactor_ms * 1e-3) / 1e9, 3),
             "retrieve_gbs": round(6 * fbytes / (retrieve_ms * 1e-3) / 1e9, 3),
             "refactor_ms": round(refactor_ms, 4), "retrieve_ms": round(retrieve_ms, 4),
@@ -727,6 +796,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-qoi", action="store_true")
+    ap.add_argument("--no-bpdesign", action="store_true")
     ap.add_argument("--qoi-side", type=int, default=256)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-streaming", action="store_true")

@@ -120,6 +120,19 @@ HPMDR_API hpmdr_status hpmdr_retrieve(hpmdr_ctx* ctx, hpmdr_handle* h, double re
 HPMDR_API hpmdr_status hpmdr_retrieve_abs(hpmdr_ctx* ctx, hpmdr_handle* h, double abs_linf_bound, void* out,
                                 int out_on_device, hpmdr_retrieve_info* info);
 
+/* Asynchronous retrieval: the same work as hpmdr_retrieve with the output on
+ * the device, enqueued on the context stream; the call returns without waiting
+ * for the GPU, so back-to-back retrievals (of one handle, incremental as
+ * usual, or of several) run without host round trips between them.  *info
+ * (may be NULL; host memory owned by the caller) is filled by hpmdr_ctx_wait,
+ * which waits for everything enqueued on the context stream and returns
+ * HPMDR_OK, or the first status of a pending retrieval that was not OK (each
+ * info carries its own).  Up to 64 retrievals may be pending; one more waits
+ * first.  The handle, out and info must stay valid until hpmdr_ctx_wait. */
+HPMDR_API hpmdr_status hpmdr_retrieve_async(hpmdr_ctx* ctx, hpmdr_handle* h, double rel_linf_bound,
+                                            void* out, hpmdr_retrieve_info* info);
+HPMDR_API hpmdr_status hpmdr_ctx_wait(hpmdr_ctx* ctx);
+
 /* ---- QoI retrieval (Sec. 6.2, Algorithm 3) for the velocity magnitude
  * |v| = sqrt(vx^2 + vy^2 + vz^2) of three FP32 handles of equal shape.
  * rel_qoi_bound is relative to max|v| - min|v| of the refactored data.
@@ -325,6 +338,28 @@ HPMDR_API hpmdr_status hpmdr_bitplane_encode(const void* q, const uint8_t* sign,
  * sign plane when k > 0, else zeros */
 HPMDR_API hpmdr_status hpmdr_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, void* q_out,
                                    uint8_t* sign_out, void* stream);
+/* The bitplane encoder designs of Sec. 4 for B = 32, all writing the layout of
+ * hpmdr_bitplane_encode byte for byte (and decoding as hpmdr_bitplane_decode):
+ * the register block of Sec. 4.3 (the production encoder), the locality block
+ * of Sec. 4.1 (a thread moves the bits of 32 contiguous elements one at a
+ * time), and register shuffling (Sec. 4.2; a thread per element, a warp per
+ * word) with each of the four warp instructions.  The shuffle designs share one
+ * decoder (a broadcast per plane).  q (uint32) and planes must be 16-byte
+ * aligned; n < 2^32 - 256; k = 0..32.  HPMDR_ERR_ARG otherwise. */
+typedef enum {
+  HPMDR_BP_REGISTER_BLOCK = 0,
+  HPMDR_BP_LOCALITY_BLOCK = 1,
+  HPMDR_BP_SHUFFLE_BALLOT = 2,
+  HPMDR_BP_SHUFFLE_SHIFT = 3,
+  HPMDR_BP_SHUFFLE_MATCH_ANY = 4,
+  HPMDR_BP_SHUFFLE_REDUCE = 5
+} hpmdr_bp_design;
+HPMDR_API hpmdr_status hpmdr_bitplane_encode_design(const uint32_t* q, const uint8_t* sign,
+                                                    uint64_t n, int design, uint32_t* planes,
+                                                    void* stream);
+HPMDR_API hpmdr_status hpmdr_bitplane_decode_design(const uint32_t* planes, uint64_t n, int design,
+                                                    int k, uint32_t* q_out, uint8_t* sign_out,
+                                                    void* stream);
 /* Algorithm 2 on one byte group G (device memory, S bytes): force = -1 picks the
  * method as Algorithm 2 does, else HPMDR_DC / HPMDR_HUFFMAN / HPMDR_RLE.
  * out (device) needs cap bytes; *len receives the stored length. */
@@ -332,6 +367,16 @@ HPMDR_API hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uint
                                 uint8_t* out, uint64_t cap, uint64_t* len, int* method);
 HPMDR_API hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, uint64_t len, int method,
                                 uint8_t* G, uint64_t S);
+/* The last step of recomposition (Sec. 3, Algorithm 3's recompose; the output
+ * rounding of the fixed-point reading): out[i] = RN(X[i]) * 2^(E_f-48)
+ * in the output type, RN the round-to-nearest-even conversion of the integer,
+ * for FP32 followed by an exact power-of-two scale when -78 <= E_f <= 121 and
+ * else rounded through FP64 first; exactly what every retrieval writes.  X and
+ * out are device arrays of n values (out 4 or 8 bytes each); synchronous on the
+ * context stream.  HPMDR_ERR_ARG for a NULL pointer with n > 0, another dtype,
+ * or an E_f no field of the type has (FP32: -148..128, FP64: -1073..1024). */
+HPMDR_API hpmdr_status hpmdr_fixed_to_float(hpmdr_ctx* ctx, const int64_t* X, uint64_t n, int E_f,
+                                            hpmdr_dtype dtype, void* out);
 /* hpmdr_encode_group for callers that cannot allocate device memory (a
  * solver that owns all of HBM, or that forbids cudaMalloc/cudaFree between
  * steps because they may synchronize the device).  No counterpart in the

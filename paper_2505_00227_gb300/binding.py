@@ -103,6 +103,9 @@ _SIGS = {
     "hpmdr_handle_compact": (C.c_int, [vp, vp]),
     "hpmdr_handle_drop_cache": (C.c_int, [vp, vp]),
     "hpmdr_handle_memory": (C.c_int, [vp, u64p, u64p, u64p]),
+    "hpmdr_retrieve_async": (C.c_int, [vp, vp, C.c_double, vp, vp]),
+    "hpmdr_ctx_wait": (C.c_int, [vp]),
+    "hpmdr_fixed_to_float": (C.c_int, [vp, vp, C.c_uint64, C.c_int, C.c_int, vp]),
     "hpmdr_refactor_chunked": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_uint64 * 3, C.c_uint64 * 3,
                                          C.c_int, C.c_int, C.POINTER(vp), C.c_uint64, u64p]),
     "hpmdr_retrieve_chunked": (C.c_int, [vp, C.POINTER(vp), C.c_uint64, C.c_int, C.c_uint64 * 3,
@@ -127,6 +130,8 @@ _SIGS = {
     "hpmdr_batch_last_ms": (C.c_int, [vp, C.c_double * 2]),
     "hpmdr_bitplane_encode": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, vp]),
     "hpmdr_bitplane_decode": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp, vp]),
+    "hpmdr_bitplane_encode_design": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, vp]),
+    "hpmdr_bitplane_decode_design": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp, vp]),
     "hpmdr_encode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64, u64p, ip]),
     "hpmdr_decode_group": (C.c_int, [vp, vp, C.c_uint64, C.c_int, vp, C.c_uint64]),
     "hpmdr_encode_group_noalloc": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_uint64, C.c_uint32,
@@ -202,8 +207,18 @@ class Context:
         """method: None for Algorithm 2, else DC / HUFFMAN / RLE for every group."""
         cfg = Config(4, size_threshold, cr_num, cr_den, 0 if method is None else method + 1)
         self._p = vp()
+        self._keep = []  # infos and outputs of pending asynchronous retrievals
         _check(lib().hpmdr_ctx_create(C.byref(self._p), C.byref(cfg), None, _stream_ptr(stream)),
                "hpmdr_ctx_create")
+
+    def wait(self):
+        """Wait for the context stream; fills the infos of the asynchronous
+        retrievals.  Returns HPMDR_OK or the first pending status that was not
+        OK (HPMDR_ERR_UNATTAINABLE included); raises on other errors."""
+        st = lib().hpmdr_ctx_wait(self._p)
+        self._keep = []
+        _check(st, "hpmdr_ctx_wait", allow=(ERR_UNATTAINABLE,))
+        return st
 
     def profile(self, enable=True):
         """Record per-stage CUDA events on this context's stream (clears totals)."""
@@ -355,6 +370,17 @@ class Context:
         return st, G
 
 
+    def fixed_to_float(self, X, E_f, dtype):
+        """RN(X) * 2^(E_f - 48) in dtype for a device int64 tensor X (the output
+        conversion of every retrieval)."""
+        import torch
+        out = torch.empty(X.shape, dtype=dtype, device=X.device)
+        _check(lib().hpmdr_fixed_to_float(self._p, vp(X.data_ptr()), X.numel(), E_f,
+                                          F32 if dtype == torch.float32 else F64,
+                                          vp(out.data_ptr())), "hpmdr_fixed_to_float")
+        return out
+
+
 class Handle:
     """One refactored field (hpmdr_handle) and its incremental retrieval state."""
 
@@ -389,6 +415,15 @@ class Handle:
                 C.byref(info))
         _check(st, "hpmdr_retrieve", allow=(ERR_UNATTAINABLE,))
         return out, info, st
+
+    def retrieve_async(self, bound, out):
+        """Enqueue a retrieval into the CUDA tensor `out` without waiting; the
+        returned info is filled by Context.wait()."""
+        info = RetrieveInfo()
+        self.ctx._keep.append((info, out))
+        _check(lib().hpmdr_retrieve_async(self.ctx._p, self._p, float(bound), vp(out.data_ptr()),
+                                          C.byref(info)), "hpmdr_retrieve_async")
+        return info
 
     def field_info(self):
         dt, nl, ef, ie = C.c_int(), C.c_int(), C.c_int(), C.c_int()
@@ -478,6 +513,38 @@ def bitplane_decode(planes, n, B, k, stream=None):
                                        vp(s.data_ptr()), _stream_ptr(stream)),
            "hpmdr_bitplane_decode")
     return q, s
+
+
+BP_REGISTER_BLOCK, BP_LOCALITY_BLOCK, BP_SHUFFLE_BALLOT, BP_SHUFFLE_SHIFT, \
+    BP_SHUFFLE_MATCH_ANY, BP_SHUFFLE_REDUCE = range(6)
+BP_DESIGNS = {"register_block": 0, "locality_block": 1, "shuffle_ballot": 2, "shuffle_shift": 3,
+              "shuffle_match_any": 4, "shuffle_reduce": 5}
+
+
+def bitplane_encode_design(q, sign, design, planes=None, stream=None):
+    """One of the Sec. 4 encoder designs (B = 32) on a CUDA int32 tensor q."""
+    import torch
+    n = q.numel()
+    W = 4 * ((n + 127) // 128)
+    if planes is None:
+        planes = torch.empty(33 * W, dtype=torch.int32, device=q.device)
+    _check(lib().hpmdr_bitplane_encode_design(vp(q.data_ptr()), vp(sign.data_ptr()), n, design,
+                                              vp(planes.data_ptr()), _stream_ptr(stream)),
+           "hpmdr_bitplane_encode_design")
+    return planes
+
+
+def bitplane_decode_design(planes, n, design, k, q=None, sign=None, stream=None):
+    import torch
+    if q is None:
+        q = torch.empty(n, dtype=torch.int32, device=planes.device)
+    if sign is None:
+        sign = torch.empty(n, dtype=torch.uint8, device=planes.device)
+    _check(lib().hpmdr_bitplane_decode_design(vp(planes.data_ptr()), n, design, k,
+                                              vp(q.data_ptr()), vp(sign.data_ptr()),
+                                              _stream_ptr(stream)),
+           "hpmdr_bitplane_decode_design")
+    return q, sign
 
 
 class Server:

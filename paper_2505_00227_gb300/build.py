@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhpmdr.so")
 UNITS = ["stats.cu", "decompose.cu", "lossless.cu", "select.cu", "recompose.cu", "qoi.cu", "cells.cu",
-         "runtime.cu", "noalloc.cu", "serve.cu", "batch.cu", "gcells.cu"]
+         "runtime.cu", "noalloc.cu", "serve.cu", "batch.cu", "gcells.cu", "bpdesign.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]

@@ -321,17 +321,20 @@ void launch_cells_encode(const float* f, const uint64_t dims[3], const LevelDesc
 }
 
 // --------------------------------------------------------- retrieval side
-__device__ __forceinline__ float out_f32(int64_t X, int E_f) {
-  const int e = E_f - 48;
-  if (e >= -126 && E_f <= 121) return __fmul_rn(__ll2float_rn(X), __int_as_float((e + 127) << 23));
-  const double d = __dmul_rn(__ll2double_rn(X), __longlong_as_double((long long)(e + 1023) << 52));
-  return __double2float_rn(d);
-}
-
 typedef uint32_t CellSW[7][32];
 
+// How a level's coefficients come back, uniform over a launch: no planes
+// (k = 0 or an all-zero level: c8 = 0, the planes are not touched), bl <= 32
+// (c8 magnitude = q_hat >> (32 - bl)), bl > 32 (q_hat << (bl - 32)).
+// CR_ANY: decided per tile at run time (one instantiation for every case).
+enum { CR_NONE = 0, CR_NARROW = 1, CR_WIDE = 2, CR_ANY = 3 };
+
+__device__ __forceinline__ int cells_mode(int bl, int k) {
+  return (k == 0 || bl == 0) ? CR_NONE : (bl <= 32 ? CR_NARROW : CR_WIDE);
+}
+
 // recomposition of one tile of 1024 cells from the coarse grid and the planes
-template <bool FINAL>
+template <bool FINAL, int MODE>
 __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict__ P,
                                                      const LevelDesc& L, const CellGeom& G,
                                                      int E_f, int bl, int k,
@@ -343,23 +346,26 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
   const uint32_t gc1 = L.gc[1], gc2 = L.gc[2];
   uint32_t cz, cy0, x0;
   tile_origin(G, tile, cz, cy0, x0);
-  if (i < 224) {  // phase words: planes -> q_hat per cell
-    const int t = i / 32 + 1;
-    const uint32_t rw = i % 32, r = rw / G.NW, w = rw % G.NW, cy = cy0 + r;
-    if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
-      const uint32_t word = (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
-      uint32_t a[32];
+  const int md = MODE == CR_ANY ? cells_mode(bl, k) : MODE;
+  if (md != CR_NONE) {
+    if (i < 224) {  // phase words: planes -> q_hat per cell
+      const int t = i / 32 + 1;
+      const uint32_t rw = i % 32, r = rw / G.NW, w = rw % G.NW, cy = cy0 + r;
+      if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
+        const uint32_t word = (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
+        uint32_t a[32];
 #pragma unroll
-      for (int p = 0; p < 32; p++) a[31 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
-      if (k) transpose32(a);
+        for (int p = 0; p < 32; p++) a[31 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
+        transpose32(a);
 #pragma unroll
-      for (int j = 0; j < 8; j++)
-        *reinterpret_cast<uint4*>(&s_q[t - 1][rw][4 * j]) =
-            make_uint4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
-      s_sw[t - 1][rw] = k ? __ldcs(P + word) : 0u;
+        for (int j = 0; j < 8; j++)
+          *reinterpret_cast<uint4*>(&s_q[t - 1][rw][4 * j]) =
+              make_uint4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
+        s_sw[t - 1][rw] = __ldcs(P + word);
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
   {  // phase cells: one output row (2cz + oz, 2cy + oy) at a time
     const uint32_t r = i / per_row, xl = 4 * (i % per_row), cy = cy0 + r, cx = x0 + xl;
     if (cy < G.c[1]) {
@@ -368,6 +374,10 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       const uint32_t cz1 = 2 * cz + 2 < G.g[0] ? cz + 1 : cz, cy1 = 2 * cy + 2 < G.g[1] ? cy + 1 : cy;
       const uint32_t xe = 2 * cx + 8 < G.g[2] ? cx + 4 : cx + 3;
       const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
+      const int e = E_f - 48;
+      const bool fast_e = e >= -126 && E_f <= 121;
+      const float s24 = __int_as_float(((fast_e ? e : 0) + 24 + 127) << 23);
+      const float s0 = __int_as_float(((fast_e ? e : 0) + 127) << 23);
       auto load = [&](uint32_t z, uint32_t y, int64_t c[5]) {
         const int64_t* row = coarse + ((size_t)z * gc1 + y) * gc2;
         // cx is a multiple of 4 and gc2 of 32: two aligned 16-byte loads
@@ -379,19 +389,23 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
         c[3] = p1.y;
         c[4] = __ldg(row + xe);
       };
-      // c8 of the type-t nodes of the thread's 4 cells
-      auto c8of = [&](int t, int64_t c8[4]) {
+      // the staged q_hat of the type-t nodes of the thread's 4 cells and their
+      // sign bits; c8 of one of them
+      auto qof = [&](int t, uint32_t qh[4], uint32_t& sg) {
+        if (md == CR_NONE) return;
         const uint4 x = *reinterpret_cast<const uint4*>(&s_q[t - 1][rw][b0]);
-        const uint32_t qh[4] = {x.x, x.y, x.z, x.w};
-        const uint32_t sg = s_sw[t - 1][rw] >> b0;
-#pragma unroll
-        for (int kk = 0; kk < 4; kk++) {
-          uint64_t mag;
-          if (bl == 0) mag = 0;
-          else if (bl <= 32) mag = qh[kk] >> (32 - bl);
-          else mag = (uint64_t)qh[kk] << (bl - 32);
-          c8[kk] = ((sg >> kk) & 1u) ? -(int64_t)mag : (int64_t)mag;
-        }
+        qh[0] = x.x;
+        qh[1] = x.y;
+        qh[2] = x.z;
+        qh[3] = x.w;
+        sg = s_sw[t - 1][rw] >> b0;
+      };
+      auto c8at = [&](const uint32_t qh[4], uint32_t sg, int kk) -> int64_t {
+        if (md == CR_NONE) return 0;
+        const uint64_t mag = md == CR_NARROW ? (uint64_t)(qh[kk] >> (32 - bl))
+                                             : (uint64_t)qh[kk] << (bl - 32);
+        const uint64_t neg = 0ull - (uint64_t)((sg >> kk) & 1u);  // all ones if negative
+        return (int64_t)((mag ^ neg) - neg);
       };
       // Row (oz, oy): even-x nodes are type te = 2 oy + 4 oz (te = 0: the coarse
       // node itself), odd-x nodes te + 1.  e[kk] is the sum of the row's coarse
@@ -399,25 +413,40 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       // X = floor((c8 2^n + 8 S) / 2^(3+n)) = (c8 + S 2^(3-n)) >> 3.
       auto emit = [&](int oz, int oy, const int64_t e[5]) {
         const int te = 2 * oy + 4 * oz, ne = __popc(te), no = ne + 1;
-        int64_t V[8], ce[4], co[4];
-        if (te != 0) c8of(te, ce);
-        c8of(te + 1, co);
-#pragma unroll
-        for (int kk = 0; kk < 4; kk++) {
-          V[2 * kk] = te == 0 ? e[kk] : (ce[kk] + e[kk] * (8 >> ne)) >> 3;
-          V[2 * kk + 1] = (co[kk] + (e[kk] + e[kk + 1]) * (8 >> no)) >> 3;
-        }
+        uint32_t qe[4] = {0, 0, 0, 0}, qo[4] = {0, 0, 0, 0}, se = 0, so = 0;
+        if (te != 0) qof(te, qe, se);
+        qof(te + 1, qo, so);
         const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
-        if (FINAL) {
-          float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base);
-          d4[0] = make_float4(out_f32(V[0], E_f), out_f32(V[1], E_f), out_f32(V[2], E_f),
-                              out_f32(V[3], E_f));
-          d4[1] = make_float4(out_f32(V[4], E_f), out_f32(V[5], E_f), out_f32(V[6], E_f),
-                              out_f32(V[7], E_f));
-        } else {
-          longlong2* d2 = reinterpret_cast<longlong2*>(reinterpret_cast<int64_t*>(dst) + base);
 #pragma unroll
-          for (int kk = 0; kk < 4; kk++) d2[kk] = make_longlong2(V[2 * kk], V[2 * kk + 1]);
+        for (int hf = 0; hf < 2; hf++) {  // two cells (four nodes) at a time
+          int64_t V[4];
+#pragma unroll
+          for (int u = 0; u < 2; u++) {
+            const int kk = 2 * hf + u;
+            V[2 * u] = te == 0 ? e[kk] : (c8at(qe, se, kk) + e[kk] * (8 >> ne)) >> 3;
+            V[2 * u + 1] = (c8at(qo, so, kk) + (e[kk] + e[kk + 1]) * (8 >> no)) >> 3;
+          }
+          if (FINAL) {
+            // values below 2^48 in magnitude (the rule; a partial reconstruction
+            // of a rough field can pass it) take the short conversion
+            uint32_t big = 0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) big |= ((uint32_t)((uint64_t)V[u] >> 32) + 65536u) >> 17;
+            float o[4];
+            if (fast_e && big == 0) {
+#pragma unroll
+              for (int u = 0; u < 4; u++) o[u] = fixed_to_f32_small(V[u], s24, s0);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; u++) o[u] = fixed_to_f32(V[u], E_f);
+            }
+            reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base)[hf] =
+                make_float4(o[0], o[1], o[2], o[3]);
+          } else {
+            longlong2* d2 = reinterpret_cast<longlong2*>(reinterpret_cast<int64_t*>(dst) + base);
+            d2[2 * hf] = make_longlong2(V[0], V[1]);
+            d2[2 * hf + 1] = make_longlong2(V[2], V[3]);
+          }
         }
       };
       int64_t c0[5], a[5];
@@ -445,7 +474,18 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       }
     }
   }
-  __syncthreads();
+  if (md != CR_NONE) __syncthreads();  // the staging is reused by the next tile
+}
+
+template <bool FINAL, int MODE>
+__device__ __forceinline__ void cells_recompose_tiles(const uint32_t* __restrict__ P,
+                                                      const LevelDesc& L, const CellGeom& G,
+                                                      int E_f, int bl, int k,
+                                                      const int64_t* __restrict__ coarse,
+                                                      void* __restrict__ dst, CellQ& s_q,
+                                                      CellSW& s_sw) {
+  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
+    cells_recompose_tile<FINAL, MODE>(P, L, G, E_f, bl, k, coarse, dst, tile, s_q, s_sw);
 }
 
 template <bool FINAL>
@@ -461,8 +501,16 @@ __global__ void __launch_bounds__(256, 4) k_cells_recompose(const uint32_t* __re
   const CellGeom G = cell_geom(L);
   const int E_f = meta->E_f, bl = meta->bl[L.level], k = 4 * meta->cur[L.level];
   const uint32_t* P = planes + L.plane_off / 4;
-  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
-    cells_recompose_tile<FINAL>(P, L, G, E_f, bl, k, coarse, dst, tile, s_q, s_sw);
+  switch (cells_mode(bl, k)) {
+    case CR_NONE:
+      cells_recompose_tiles<FINAL, CR_NONE>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
+      break;
+    case CR_NARROW:
+      cells_recompose_tiles<FINAL, CR_NARROW>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
+      break;
+    default:
+      cells_recompose_tiles<FINAL, CR_WIDE>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
+  }
 }
 
 void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,
@@ -542,10 +590,11 @@ __global__ void __launch_bounds__(256, 3) kb_cells_recompose(const BatchJob* __r
     const CellGeom G = cell_geom(L);
     const uint32_t* P = reinterpret_cast<const uint32_t*>(J.planes) + L.plane_off / 4;
     const int E_f = meta->E_f, bl = meta->bl[L.level], k = 4 * meta->cur[L.level];
+    const uint32_t tile = u - unit0[e];
     if (R.final)
-      cells_recompose_tile<true>(P, L, G, E_f, bl, k, R.coarse, J.out, u - unit0[e], s_q, s_sw);
+      cells_recompose_tile<true, CR_ANY>(P, L, G, E_f, bl, k, R.coarse, J.out, tile, s_q, s_sw);
     else
-      cells_recompose_tile<false>(P, L, G, E_f, bl, k, R.coarse, R.dst, u - unit0[e], s_q, s_sw);
+      cells_recompose_tile<false, CR_ANY>(P, L, G, E_f, bl, k, R.coarse, R.dst, tile, s_q, s_sw);
   }
 }
 

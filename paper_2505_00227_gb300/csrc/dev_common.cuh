@@ -106,6 +106,58 @@ __device__ __forceinline__ int64_t fixed_point(double v, int E_f, uint32_t& floo
   return (u >> 63) ? -(int64_t)mag : (int64_t)mag;
 }
 
+// ------------------------------------------------------- output conversion
+// The last step of recomposition: f = RN(X) * 2^(E_f - 48), X the fixed-point
+// reconstruction, RN the IEEE 754 round-to-nearest-even conversion to the
+// output type followed by an exact power-of-two scale.  On this GPU the 64-bit
+// integer conversions run on the narrow FP64 pipe, so the common cases are
+// built without them.
+//
+// FP32, |X| < 2^48: X = h 2^24 + l with h = floor(X / 2^24), |h| <= 2^24, and
+// 0 <= l < 2^24, both exact in FP32 by 32-bit conversions; one fused
+// multiply-add rounds h 2^(24+e) + l 2^e once, and with the result normal
+// (e >= -126 and X != 0) that equals RN(X) 2^e.
+// (s24, s0) = (2^(24+e), 2^e); the caller has checked |X| < 2^48, e >= -126
+// and E_f <= 121
+__device__ __forceinline__ float fixed_to_f32_small(int64_t X, float s24, float s0) {
+  const float hf = __int2float_rn((int32_t)(X >> 24));
+  const float lf = __uint2float_rn((uint32_t)X & 0xffffffu);
+  return __fmaf_rn(hf, s24, __fmul_rn(lf, s0));
+}
+
+__device__ __forceinline__ float fixed_to_f32(int64_t X, int E_f) {
+  const int e = E_f - 48;
+  if (e >= -126 && E_f <= 121) {
+    const uint32_t t = (uint32_t)((uint64_t)X >> 32);
+    if (t + 65536u < 131072u)  // -2^48 <= X < 2^48
+      return fixed_to_f32_small(X, __int_as_float((e + 24 + 127) << 23),
+                                __int_as_float((e + 127) << 23));
+    return __fmul_rn(__ll2float_rn(X), __int_as_float((e + 127) << 23));
+  }
+  const double d = __dmul_rn(__ll2double_rn(X), __longlong_as_double((long long)(e + 1023) << 52));
+  return __double2float_rn(d);
+}
+
+// FP64, |X| < 2^53 and a finite normal result: exact, so the IEEE fields are
+// written directly (leading one at bit 52 of the shifted magnitude, exponent
+// carried by the addition); anything else takes the conversion instructions.
+__device__ __forceinline__ double fixed_to_f64(int64_t X, int E_f) {
+  const int e = E_f - 48;
+  const uint64_t sg = (uint64_t)(X >> 63);
+  const uint64_t M = ((uint64_t)X ^ sg) - sg;
+  const int lz = __clzll((long long)M);
+  if (M < (1ull << 53) && e >= -1022 && 63 - lz + e <= 1023) {
+    if (M == 0) return 0.0;
+    const uint64_t m53 = (M << lz) >> 11;  // bit 52 set, nothing lost
+    const uint64_t bits = ((uint64_t)(63 - lz + e + 1022) << 52) + m53;
+    return __longlong_as_double((long long)(bits | (sg << 63)));
+  }
+  const double x = __ll2double_rn(X);
+  if (e >= -1022) return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
+  const double y = __dmul_rn(x, __longlong_as_double((long long)(-500 + 1023) << 52));
+  return __dmul_rn(y, __longlong_as_double((long long)(e + 500 + 1023) << 52));
+}
+
 __device__ __forceinline__ uint64_t umag(int64_t c) {
   return c < 0 ? (uint64_t)(-c) : (uint64_t)c;
 }

@@ -186,20 +186,12 @@ __device__ __forceinline__ T gconvert(int64_t X, int E_f);
 
 template <>
 __device__ __forceinline__ float gconvert<float>(int64_t X, int E_f) {
-  const int e = E_f - 48;
-  if (e >= -126 && E_f <= 121)
-    return __fmul_rn(__ll2float_rn(X), __int_as_float((e + 127) << 23));
-  const double d = __dmul_rn(__ll2double_rn(X), __longlong_as_double((long long)(e + 1023) << 52));
-  return __double2float_rn(d);
+  return fixed_to_f32(X, E_f);
 }
 
 template <>
 __device__ __forceinline__ double gconvert<double>(int64_t X, int E_f) {
-  const int e = E_f - 48;
-  const double x = __ll2double_rn(X);
-  if (e >= -1022) return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
-  const double y = __dmul_rn(x, __longlong_as_double((long long)(-500 + 1023) << 52));
-  return __dmul_rn(y, __longlong_as_double((long long)(e + 500 + 1023) << 52));
+  return fixed_to_f64(X, E_f);
 }
 
 // the node's reconstruction X = floor((c8 2^n + 8 S) / 2^(3+n)) = (c8 + S 2^(3-n)) >> 3,

@@ -169,6 +169,10 @@ void launch_encode(const void* f, int dtype, const uint64_t dims[3], const Level
                    uint32_t* planes, cstream s);
 void launch_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int B,
                             uint32_t* planes, cstream s);
+void launch_bpd_encode(const uint32_t* q, const uint8_t* sign, uint64_t n, int design,
+                       uint32_t* planes, cstream s);
+void launch_bpd_decode(const uint32_t* planes, uint64_t n, int design, int k, uint32_t* q,
+                       uint8_t* sign, cstream s);
 void launch_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, void* q,
                             uint8_t* sign, cstream s);
 
@@ -203,6 +207,7 @@ void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd,
 // recompose.cu  (final_dtype: -1 = int64 level grid, 0 = float out, 1 = double out)
 void launch_recompose_root(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* L0,
                            int64_t* xroot, void* out, int dtype, cstream s);
+void launch_convert_fixed(const int64_t* X, uint64_t n, int E_f, int dtype, void* out, cstream s);
 void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const int64_t* coarse,
                            void* dst, int final_dtype, const FieldMeta* meta, cstream s);
 void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,

@@ -104,23 +104,47 @@ __device__ __forceinline__ void chunk_stats_unit(const uint8_t* __restrict__ pla
   __syncthreads();
   // run starts and histogram
   uint64_t mask = 0;
-  uint32_t prev = (t > 0 && nb) ? s_last[t - 1] : 0x100u;  // 0x100: the chunk start
   uint32_t zeros = 0;
+  if (nb == 64) {  // whole segment: a word at a time
+    uint32_t pb = t > 0 ? s_last[t - 1] : 0u;
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    const uint32_t x = wv[k];
-    const uint32_t zm = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);  // 0x80 per zero byte
+    for (int k = 0; k < 16; k++) {
+      const uint32_t x = wv[k];
+      const uint32_t d = x ^ ((x << 8) | pb);  // each byte against its predecessor
+      const uint32_t nz = (((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d) & 0x80808080u;
+      // bits 7, 15, 23, 31 gathered to bits 0..3 (the partial products never overlap)
+      mask |= (uint64_t)((((nz >> 7) * 0x204081u) >> 21) & 0xfu) << (4 * k);
+      pb = x >> 24;
+      zeros += __popc(~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu));
+      if ((nz & 0x80808000u) == 0) {  // four equal bytes: one update
+        if (x & 0xffu) atomicAdd(&hist[w][x & 0xffu], 4u);
+      } else {
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const uint32_t idx = 4 * k + q;
-      if (idx < nb) {
-        const uint32_t v = (x >> (8 * q)) & 0xffu;
-        if (v != prev) mask |= 1ull << idx;
-        prev = v;
-        if (v) atomicAdd(&hist[w][v], 1u);
+        for (int q = 0; q < 4; q++) {
+          const uint32_t v = (x >> (8 * q)) & 0xffu;
+          if (v) atomicAdd(&hist[w][v], 1u);
+        }
       }
     }
-    zeros += __popc(zm & (k * 4 + 4 <= nb ? 0xffffffffu : (k * 4 < nb ? (0xffffffffu >> (32 - 8 * (nb - 4 * k))) : 0u)));
+    if (t == 0) mask |= 1ull;  // the chunk's first byte starts a run
+  } else {
+    uint32_t prev = (t > 0 && nb) ? s_last[t - 1] : 0x100u;  // 0x100: the chunk start
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const uint32_t x = wv[k];
+      const uint32_t zm = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);  // 0x80 per zero byte
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const uint32_t idx = 4 * k + q;
+        if (idx < nb) {
+          const uint32_t v = (x >> (8 * q)) & 0xffu;
+          if (v != prev) mask |= 1ull << idx;
+          prev = v;
+          if (v) atomicAdd(&hist[w][v], 1u);
+        }
+      }
+      zeros += __popc(zm & (k * 4 + 4 <= nb ? 0xffffffffu : (k * 4 < nb ? (0xffffffffu >> (32 - 8 * (nb - 4 * k))) : 0u)));
+    }
   }
   if (zeros) atomicAdd(&hist[w][0], zeros);
   // first run start of each segment, suffix minimum over the following segments

@@ -15,20 +15,12 @@ __device__ __forceinline__ T convert_out(int64_t X, int E_f);
 
 template <>
 __device__ __forceinline__ float convert_out<float>(int64_t X, int E_f) {
-  const int e = E_f - 48;
-  if (e >= -126 && E_f <= 121)
-    return __fmul_rn(__ll2float_rn(X), __int_as_float((e + 127) << 23));
-  const double d = __dmul_rn(__ll2double_rn(X), __longlong_as_double((long long)(e + 1023) << 52));
-  return __double2float_rn(d);
+  return fixed_to_f32(X, E_f);
 }
 
 template <>
 __device__ __forceinline__ double convert_out<double>(int64_t X, int E_f) {
-  const int e = E_f - 48;
-  const double x = __ll2double_rn(X);
-  if (e >= -1022) return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
-  const double y = __dmul_rn(x, __longlong_as_double((long long)(-500 + 1023) << 52));
-  return __dmul_rn(y, __longlong_as_double((long long)(e + 500 + 1023) << 52));
+  return fixed_to_f64(X, E_f);
 }
 
 __device__ __forceinline__ int64_t dequant(uint64_t qh, bool neg, int B, int bl) {
@@ -277,6 +269,25 @@ static int sms() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
   return n;
+}
+
+// the output conversion alone, over a plain array of fixed-point values
+template <typename T>
+__global__ void k_convert_fixed(const int64_t* __restrict__ X, uint64_t n, int E_f,
+                                T* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = convert_out<T>(X[i], E_f);
+}
+
+void launch_convert_fixed(const int64_t* X, uint64_t n, int E_f, int dtype, void* out, cstream s) {
+  if (!n) return;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 152ull * 8) blocks = 152ull * 8;
+  if (dtype == 0)
+    hp::note_launch(), k_convert_fixed<float><<<(unsigned)blocks, 256, 0, s>>>(X, n, E_f, (float*)out);
+  else
+    hp::note_launch(), k_convert_fixed<double><<<(unsigned)blocks, 256, 0, s>>>(X, n, E_f, (double*)out);
 }
 
 void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const int64_t* coarse,

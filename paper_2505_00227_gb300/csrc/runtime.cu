@@ -346,6 +346,7 @@ extern "C" hpmdr_status hpmdr_ctx_create(hpmdr_ctx** out, const hpmdr_config* cf
 extern "C" void hpmdr_ctx_destroy(hpmdr_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  ctx->pending.clear();
   for (cudaStream_t s : ctx->aux) cudaStreamSynchronize(s);
   delete ctx;
 }
@@ -747,8 +748,10 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
   return HPMDR_OK;
 }
 
-// algorithmic bytes of the last retrieval's stages, once the selection is known
-static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const RetrieveDev& rd) {
+// algorithmic bytes of a retrieval's stages, once its selection is known
+static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const RetrieveDev& rd,
+                                 const std::vector<std::pair<size_t, int>>& prof_lv,
+                                 size_t prof_decode, size_t prof_small, int small_end) {
   if (!ctx->prof.on) return;
   const int ng = H->ngroups;
   const double esz = H->dtype == HPMDR_F32 ? 4.0 : 8.0;
@@ -757,10 +760,10 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
     const GroupMeta& G = H->meta->grp[rd.new_gi[i] / ng][rd.new_gi[i] % ng];
     dec += (double)G.stored_len + (double)G.S;
   }
-  ctx->prof.patch(H->prof_decode, dec);
+  ctx->prof.patch(prof_decode, dec);
   {  // small levels: their planes, coarse grids and outputs
     double b = 0;
-    for (int l = 1; l <= H->small_end; l++) {
+    for (int l = 1; l <= small_end; l++) {
       const LevelDesc& D = H->levels[l];
       const double coarse = (double)D.gc[0] * D.gc[1] * D.gc[2];
       const double osz = l == H->nlev - 1 ? esz : 8.0;
@@ -768,12 +771,12 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
       b += (g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0) + coarse * 8.0 +
            ((double)D.n + coarse) * osz;
     }
-    ctx->prof.patch(H->prof_small, b);
+    ctx->prof.patch(prof_small, b);
   }
   size_t last = SIZE_MAX;
   double last_b = 0;
   const double qb = H->B / 8 + 1;  // staged bytes per node of a general cell level
-  for (auto& pe : H->prof_lv) {
+  for (auto& pe : prof_lv) {
     const int l = pe.second / 8, kind = pe.second % 8;
     const LevelDesc& D = H->levels[l];
     const double coarse = (double)D.gc[0] * D.gc[1] * D.gc[2];
@@ -801,6 +804,8 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
   }
 }
 
+void fill_info(const hpmdr_handle* H, const RetrieveDev& rd, hpmdr_retrieve_info* info);
+
 hpmdr_status collect_info(hpmdr_ctx* ctx, hpmdr_handle* H, hpmdr_retrieve_info* info,
                                  cudaStream_t s) {
   RetrieveDev rd;
@@ -809,7 +814,12 @@ hpmdr_status collect_info(hpmdr_ctx* ctx, hpmdr_handle* H, hpmdr_retrieve_info* 
   HP_CUDA(cudaMemcpyAsync(&mstatus, &H->d_meta->status, 4, cudaMemcpyDeviceToHost, s));
   HP_CUDA(cudaStreamSynchronize(s));
   if (mstatus) return (hpmdr_status)mstatus;
-  patch_retrieve_bytes(ctx, H, rd);
+  patch_retrieve_bytes(ctx, H, rd, H->prof_lv, H->prof_decode, H->prof_small, H->small_end);
+  fill_info(H, rd, info);
+  return (hpmdr_status)rd.status;
+}
+
+void fill_info(const hpmdr_handle* H, const RetrieveDev& rd, hpmdr_retrieve_info* info) {
   if (info) {
     memset(info, 0, sizeof(*info));
     info->est_linf = rd.E_abs;
@@ -822,7 +832,6 @@ hpmdr_status collect_info(hpmdr_ctx* ctx, hpmdr_handle* H, hpmdr_retrieve_info* 
     for (int l = 0; l < H->nlev && l < 64; l++) info->groups_per_level[l] = rd.g[l];
     info->status = rd.status;
   }
-  return (hpmdr_status)rd.status;
 }
 
 static hpmdr_status retrieve_common(hpmdr_ctx* ctx, hpmdr_handle* H, double tau, int is_abs,
@@ -856,6 +865,75 @@ extern "C" hpmdr_status hpmdr_retrieve_abs(hpmdr_ctx* ctx, hpmdr_handle* h, doub
 // meets the relative bound against its global range.  Each chunk's
 // reconstruction goes to out (a dense (Z, Y, X) array) through a per-stream
 // staging buffer; the copy of one chunk overlaps the kernels of the next.
+// ------------------------------------------------ asynchronous retrieval
+static constexpr size_t kSlotBytes = (sizeof(RetrieveDev) + 16 + 255) / 256 * 256;
+
+static hpmdr_status ctx_wait(hpmdr_ctx* ctx) {
+  const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  hpmdr_status first = HPMDR_OK;
+  if (e != cudaSuccess) {
+    g_last_error = std::string("wait: ") + cudaGetErrorString(e);
+    first = HPMDR_ERR_CUDA;
+  }
+  for (PendingRetrieval& p : ctx->pending) {
+    const unsigned char* slot = (const unsigned char*)ctx->pinned + (size_t)p.slot * kSlotBytes;
+    const RetrieveDev& rd = *reinterpret_cast<const RetrieveDev*>(slot);
+    const int32_t mstatus = *reinterpret_cast<const int32_t*>(slot + sizeof(RetrieveDev));
+    hpmdr_status st = HPMDR_OK;
+    if (e != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+    } else if (mstatus) {
+      st = (hpmdr_status)mstatus;
+    } else {
+      patch_retrieve_bytes(ctx, p.H, rd, p.prof_lv, p.prof_decode, p.prof_small, p.small_end);
+      fill_info(p.H, rd, p.info);
+      st = (hpmdr_status)rd.status;
+    }
+    if (p.info && st != (hpmdr_status)rd.status) p.info->status = st;
+    if (first == HPMDR_OK && st != HPMDR_OK) first = st;
+  }
+  ctx->pending.clear();
+  return first;
+}
+
+extern "C" hpmdr_status hpmdr_retrieve_async(hpmdr_ctx* ctx, hpmdr_handle* H, double rel,
+                                             void* out, hpmdr_retrieve_info* info) {
+  if (!ctx || !H || !out || !(rel >= 0.0)) return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  if (!ctx->pinned) {
+    if (cudaHostAlloc(&ctx->pinned, kSlotBytes * hpmdr_ctx::kRing, cudaHostAllocDefault) !=
+        cudaSuccess) {
+      ctx->pinned = nullptr;
+      return HPMDR_ERR_NOMEM;
+    }
+  }
+  if ((int)ctx->pending.size() == hpmdr_ctx::kRing) {  // every slot in flight: drain
+    const hpmdr_status st = ctx_wait(ctx);
+    if (st != HPMDR_OK && st != HPMDR_ERR_UNATTAINABLE) return st;
+  }
+  HP_TRY(enqueue_retrieve(ctx, H, rel, 0, out, s));
+  PendingRetrieval p;
+  p.H = H;
+  p.info = info;
+  p.slot = ctx->ring_next;
+  ctx->ring_next = (ctx->ring_next + 1) % hpmdr_ctx::kRing;
+  unsigned char* slot = (unsigned char*)ctx->pinned + (size_t)p.slot * kSlotBytes;
+  HP_CUDA(cudaMemcpyAsync(slot, H->d_rd, sizeof(RetrieveDev), cudaMemcpyDeviceToHost, s));
+  HP_CUDA(cudaMemcpyAsync(slot + sizeof(RetrieveDev), &H->d_meta->status, 4,
+                          cudaMemcpyDeviceToHost, s));
+  p.prof_lv = H->prof_lv;
+  p.prof_decode = H->prof_decode;
+  p.prof_small = H->prof_small;
+  p.small_end = H->small_end;
+  ctx->pending.push_back(std::move(p));
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_ctx_wait(hpmdr_ctx* ctx) {
+  if (!ctx) return HPMDR_ERR_ARG;
+  return ctx_wait(ctx);
+}
+
 extern "C" hpmdr_status hpmdr_retrieve_chunked(hpmdr_ctx* ctx, hpmdr_handle* const* hs,
                                                uint64_t n, int ndims, const uint64_t dims[3],
                                                const uint64_t chunk[3], double rel, void* out,
@@ -1633,6 +1711,30 @@ extern "C" hpmdr_status hpmdr_bitplane_decode(const uint32_t* planes, uint64_t n
   return HPMDR_OK;
 }
 
+extern "C" hpmdr_status hpmdr_bitplane_encode_design(const uint32_t* q, const uint8_t* sign,
+                                                     uint64_t n, int design, uint32_t* planes,
+                                                     void* stream) {
+  if (!q || !sign || !planes || n == 0 || n >= 0xffffff00ull || design < 0 || design > 5 ||
+      ((uintptr_t)q & 15) || ((uintptr_t)planes & 15))
+    return HPMDR_ERR_ARG;
+  launch_bpd_encode(q, sign, n, design, planes, (cudaStream_t)stream);
+  HP_CUDA(cudaGetLastError());
+  HP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_bitplane_decode_design(const uint32_t* planes, uint64_t n, int design,
+                                                     int k, uint32_t* q_out, uint8_t* sign_out,
+                                                     void* stream) {
+  if (!planes || !q_out || !sign_out || n == 0 || n >= 0xffffff00ull || design < 0 || design > 5 ||
+      k < 0 || k > 32 || ((uintptr_t)q_out & 15) || ((uintptr_t)planes & 15))
+    return HPMDR_ERR_ARG;
+  launch_bpd_decode(planes, n, design, k, q_out, sign_out, (cudaStream_t)stream);
+  HP_CUDA(cudaGetLastError());
+  HP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return HPMDR_OK;
+}
+
 // one group as a one-level, one-group "field" through the same kernels
 extern "C" hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uint64_t S, int force,
                                            uint8_t* out, uint64_t cap, uint64_t* len, int* method) {
@@ -1721,6 +1823,17 @@ extern "C" hpmdr_status hpmdr_encode_group(hpmdr_ctx* ctx, const uint8_t* G, uin
   ctx->A.release(d_off, s);
   cudaStreamSynchronize(s);
   return st;
+}
+
+extern "C" hpmdr_status hpmdr_fixed_to_float(hpmdr_ctx* ctx, const int64_t* X, uint64_t n,
+                                             int E_f, hpmdr_dtype dtype, void* out) {
+  if (!ctx || (n && (!X || !out)) || (dtype != HPMDR_F32 && dtype != HPMDR_F64)) return HPMDR_ERR_ARG;
+  if (dtype == HPMDR_F32 ? (E_f < -148 || E_f > 128) : (E_f < -1073 || E_f > 1024))
+    return HPMDR_ERR_ARG;
+  launch_convert_fixed(X, n, E_f, (int)dtype, out, ctx->stream);
+  HP_CUDA(cudaGetLastError());
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HPMDR_OK;
 }
 
 extern "C" hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, uint64_t len,

@@ -144,6 +144,17 @@ struct Allocator {
   }
 };
 
+// an asynchronous retrieval waiting for hpmdr_ctx_wait: where its results land
+// and the profiler entries to patch once its selection is known
+struct PendingRetrieval {
+  hpmdr_handle* H = nullptr;
+  hpmdr_retrieve_info* info = nullptr;
+  int slot = 0;
+  std::vector<std::pair<size_t, int>> prof_lv;
+  size_t prof_decode = SIZE_MAX, prof_small = SIZE_MAX;
+  int small_end = 0;
+};
+
 struct hpmdr_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -153,9 +164,16 @@ struct hpmdr_ctx {
   Allocator A;
   Profiler prof;
   std::vector<cudaStream_t> aux;  // extra streams of the chunk pipelines (created on demand)
+  // asynchronous retrievals: a ring of page-locked result slots (selection
+  // record + device status) filled by copies on the stream, read at wait
+  static constexpr int kRing = 64;
+  void* pinned = nullptr;
+  int ring_next = 0;
+  std::vector<PendingRetrieval> pending;
   Profiler* P() { return prof.on ? &prof : nullptr; }
   ~hpmdr_ctx() {
     for (cudaStream_t s : aux) cudaStreamDestroy(s);
+    if (pinned) cudaFreeHost(pinned);
   }
 };
 
