@@ -398,6 +398,10 @@ HPMDR_API uint64_t hpmdr_kernel_launches(void);
 /* enable != 0: record CUDA events on the context stream around every kernel
  * stage (and clear the totals); 0: stop recording. */
 HPMDR_API hpmdr_status hpmdr_ctx_profile(hpmdr_ctx* ctx, int enable);
+/* as hpmdr_ctx_profile(ctx, 1), but only the stages whose bit (1 << index, the
+ * index of hpmdr_ctx_profile_entry) is set record events: two events per
+ * launch of a chosen stage, none elsewhere (0: stop recording) */
+HPMDR_API hpmdr_status hpmdr_ctx_profile_stages(hpmdr_ctx* ctx, uint64_t stage_mask);
 /* totals of stage `index` (0 .. count-1; HPMDR_ERR_ARG past the end): name,
  * summed event time in ms, launches, and algorithmic bytes (the bytes the
  * method must read and write in that stage; 0 where not defined) */

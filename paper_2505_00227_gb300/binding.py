@@ -105,6 +105,7 @@ _SIGS = {
     "hpmdr_handle_memory": (C.c_int, [vp, u64p, u64p, u64p]),
     "hpmdr_retrieve_async": (C.c_int, [vp, vp, C.c_double, vp, vp]),
     "hpmdr_ctx_wait": (C.c_int, [vp]),
+    "hpmdr_ctx_profile_stages": (C.c_int, [vp, C.c_uint64]),
     "hpmdr_fixed_to_float": (C.c_int, [vp, vp, C.c_uint64, C.c_int, C.c_int, vp]),
     "hpmdr_refactor_chunked": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_uint64 * 3, C.c_uint64 * 3,
                                          C.c_int, C.c_int, C.POINTER(vp), C.c_uint64, u64p]),
@@ -220,9 +221,28 @@ class Context:
         _check(st, "hpmdr_ctx_wait", allow=(ERR_UNATTAINABLE,))
         return st
 
-    def profile(self, enable=True):
-        """Record per-stage CUDA events on this context's stream (clears totals)."""
-        _check(lib().hpmdr_ctx_profile(self._p, int(enable)), "hpmdr_ctx_profile")
+    def profile(self, enable=True, stages=None):
+        """Record per-stage CUDA events on this context's stream (clears totals);
+        stages: names of the only stages that record (None: all)."""
+        if stages is None:
+            _check(lib().hpmdr_ctx_profile(self._p, int(enable)), "hpmdr_ctx_profile")
+            return
+        names = self.stage_names()
+        mask = 0
+        for nm in stages:
+            mask |= 1 << names.index(nm)
+        _check(lib().hpmdr_ctx_profile_stages(self._p, mask if enable else 0),
+               "hpmdr_ctx_profile_stages")
+
+    def stage_names(self):
+        out, i = [], 0
+        while True:
+            name, ms, calls, by = C.c_char_p(), C.c_double(), C.c_uint64(), C.c_double()
+            if lib().hpmdr_ctx_profile_entry(self._p, i, C.byref(name), C.byref(ms), C.byref(calls),
+                                             C.byref(by)) != OK:
+                return out
+            out.append(name.value.decode())
+            i += 1
 
     def profile_entries(self):
         """[(stage name, total ms, launches, algorithmic bytes)] since profile(True)."""

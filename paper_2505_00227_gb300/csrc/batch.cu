@@ -445,7 +445,8 @@ extern "C" hpmdr_status hpmdr_batch_create(hpmdr_ctx* ctx, uint64_t n, const uin
     J.xb = H->d_xb;
     const int L = H->nlev - 1;
     int l_end = 0;  // same split as the single-field retrieval
-    while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= 4096) l_end++;
+    while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= kSmallLevelNodes)
+      l_end++;
     J.small_end = l_end;
     H->small_end = l_end;
   }

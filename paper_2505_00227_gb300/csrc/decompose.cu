@@ -85,6 +85,9 @@ __device__ __forceinline__ void levelmax_tile(const FieldView<T>& v, const Level
   }
 }
 
+// single field: one CTA per tile, each warp 4 of its 32 rows (the generic
+// levels left to these kernels are small, so latency, not bandwidth, sets
+// their time: a tile's rows are computed side by side)
 template <typename T>
 __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDesc* __restrict__ levels,
                                                   int nlev, uint32_t total_tiles,
@@ -95,13 +98,28 @@ __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDes
   __syncthreads();
   if (meta->status) return;
   v.E_f = meta->E_f;
-  const uint32_t wpb = blockDim.x >> 5;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, rpw = 32 / (blockDim.x >> 5);
   int l = 0;
-  for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < total_tiles;
-       tile += gridDim.x * wpb) {
+  for (uint32_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     l = find_level(s_tile0, l, tile);
     const LevelDesc& L = levels[l];
-    levelmax_tile(v, L, perm[L.tile0 + (tile - L.gtile0)] * HP_TILE, meta);
+    const uint32_t base = perm[L.tile0 + (tile - L.gtile0)] * HP_TILE;
+    uint64_t mx = 0;
+    uint32_t fl = 0;
+#pragma unroll 4
+    for (int rr = 0; rr < rpw; rr++) {
+      const uint32_t j = base + (w * rpw + rr) * 32 + lane;
+      if (j < L.n) {
+        const uint64_t m = umag(level_c8(v, L, j, fl));
+        mx = m > mx ? m : mx;
+      }
+    }
+    mx = warp_max_u64(mx);
+    const unsigned anyfl = __any_sync(HP_FULL, fl != 0);
+    if (lane == 0) {
+      if (mx) atomicMax((unsigned long long*)&meta->m8[L.level], (unsigned long long)mx);
+      if (anyfl) atomicOr(&meta->floored, 1u);
+    }
   }
 }
 
@@ -115,8 +133,8 @@ static int sm_count() {
 void launch_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* levels,
                      int nlev, uint32_t total_tiles, const uint32_t* perm, FieldMeta* meta,
                      cstream s) {
-  uint32_t blocks = (total_tiles + 7) / 8;
-  uint32_t cap = (uint32_t)sm_count() * 16;
+  uint32_t blocks = total_tiles;
+  uint32_t cap = (uint32_t)sm_count() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (dtype == 0) {
@@ -209,36 +227,76 @@ __device__ __forceinline__ void encode_tile(const FieldView<T>& v, const LevelDe
   __syncwarp();
 }
 
+// single field: one CTA per tile (as k_levelmax); the warps stage the tile's
+// rows, then one warp transposes them into the plane words
 template <typename T, int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_encode(FieldView<T> v, const LevelDesc* __restrict__ levels, int nlev, uint32_t total_tiles,
              const uint32_t* __restrict__ perm, FieldMeta* meta, uint32_t* __restrict__ planes) {
-  constexpr int WPB = B == 32 ? 8 : 4;
+  constexpr int RPW = B == 32 ? 4 : 8;  // rows per warp
   __shared__ uint32_t s_tile0[HP_MAX_LEVELS + 1];
-  __shared__ uint32_t s_hi[WPB][32 * 33];
-  __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
+  __shared__ uint32_t s_hi[32 * 33];
+  __shared__ uint32_t s_lo[B == 64 ? 32 * 33 : 1];
+  __shared__ uint32_t s_sign[32];
   for (int l = threadIdx.x; l <= nlev; l += blockDim.x)
     s_tile0[l] = l < nlev ? levels[l].gtile0 : total_tiles;
   __syncthreads();
   if (meta->status) return;
   v.E_f = meta->E_f;
-  const int w = threadIdx.x >> 5;
-  uint32_t* hi = s_hi[w];
-  uint32_t* lo = s_lo[B == 64 ? w : 0];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int l = 0;
-  for (uint32_t tile = blockIdx.x * WPB + w; tile < total_tiles; tile += gridDim.x * WPB) {
+  for (uint32_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     l = find_level(s_tile0, l, tile);
     const LevelDesc& L = levels[l];
-    encode_tile<T, B>(v, L, perm[L.tile0 + (tile - L.gtile0)] * HP_TILE, meta, planes, hi, lo);
+    const uint32_t base = perm[L.tile0 + (tile - L.gtile0)] * HP_TILE;
+    const int bl = meta->bl[L.level];
+    uint64_t low = 0;
+    uint32_t fl = 0;
+#pragma unroll
+    for (int rr = 0; rr < RPW; rr++) {
+      const int r = w * RPW + rr;
+      const uint32_t j = base + r * 32 + lane;
+      uint64_t q = 0;
+      bool neg = false;
+      if (j < L.n) {
+        const int64_t c8 = level_c8(v, L, j, fl);
+        const uint64_t m = umag(c8);
+        neg = c8 < 0;
+        if (bl == 0) q = 0;
+        else if (B >= bl) q = m << (B - bl);
+        else {
+          q = m >> (bl - B);
+          low |= m & ((1ull << (bl - B)) - 1ull);
+        }
+      }
+      const uint32_t sw = __ballot_sync(HP_FULL, neg);
+      if (lane == 0) s_sign[r] = sw;
+      if (B == 64) {
+        s_hi[r * 33 + lane] = (uint32_t)(q >> 32);
+        s_lo[r * 33 + lane] = (uint32_t)q;
+      } else {
+        s_hi[r * 33 + lane] = (uint32_t)q;
+      }
+    }
+    low = warp_or_u64(low);
+    if (lane == 0 && low)
+      atomicOr((unsigned long long*)&meta->lowbits[L.level], (unsigned long long)low);
+    __syncthreads();
+    if (w == 0) {
+      const uint32_t wi = base / 32 + lane;
+      if (wi < L.W)
+        emit_word<B>(s_hi + lane * 33, s_lo + (B == 64 ? lane * 33 : 0), s_sign[lane],
+                     planes + L.plane_off / 4, L.W, wi);
+    }
+    __syncthreads();
   }
 }
 
 void launch_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* levels,
                    int nlev, uint32_t total_tiles, const uint32_t* perm, FieldMeta* meta,
                    uint32_t* planes, cstream s) {
-  uint32_t wpb = dtype == 0 ? 8 : 4;
-  uint32_t blocks = (total_tiles + wpb - 1) / wpb;
-  uint32_t cap = (uint32_t)sm_count() * (dtype == 0 ? 8 : 16);
+  uint32_t blocks = total_tiles;
+  uint32_t cap = (uint32_t)sm_count() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (dtype == 0) {

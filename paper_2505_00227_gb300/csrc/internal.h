@@ -27,6 +27,10 @@ struct FastDiv {
   uint32_t d, m, s;  // q = (umulhi(n, m) + n) >> s  for d > 1
 };
 
+// generic levels up to this many nodes (after the root) are recomposed by the
+// one-CTA kernel, a few tiles at a time, instead of a launch per level
+constexpr uint32_t kSmallLevelNodes = 4096;
+
 struct LevelDesc {
   uint64_t plane_off;  // byte offset of this level's planes in the plane buffer
   uint32_t n;          // nodes in the level

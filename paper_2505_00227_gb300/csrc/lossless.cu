@@ -211,6 +211,7 @@ void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uin
 __device__ void huffman_lengths_block(const uint64_t* f_in, uint8_t* len_out, uint64_t* f,
                                       int* sorted, uint64_t* w, int* parent, int* depth, int* flag) {
   const int t = threadIdx.x;  // 256 threads, t = symbol
+  __shared__ int s_max;
   f[t] = f_in[t];
   __syncthreads();
   for (int round = 0; round < 64; round++) {
@@ -226,36 +227,75 @@ __device__ void huffman_lengths_block(const uint64_t* f_in, uint8_t* len_out, ui
     }
     if (ft > 0) sorted[rank] = t;
     len_out[t] = 0;
+    if (t == 0) s_max = 0;
     __syncthreads();
-    if (t == 0) {
-      int maxlen = 0;
-      if (n == 1) {
-        len_out[sorted[0]] = 1;
-        maxlen = 1;
-      } else if (n > 1) {
+    if (n > 1) {
+      if (t == 0) {
+        // two-queue merge: leaves in (freq, symbol) order, internal nodes in
+        // creation order; the heads of both queues stay in registers
         for (int i = 0; i < n; i++) w[i] = f[sorted[i]];
         int nl = 0, ni = n, created = n;
+        uint64_t lw = w[0], iw = 0;
         for (int step = 0; step < n - 1; step++) {
-          int pick[2];
+          uint64_t sum = 0;
+#pragma unroll
           for (int k = 0; k < 2; k++) {
-            bool leaf_ok = nl < n, int_ok = ni < created;
-            if (leaf_ok && (!int_ok || w[nl] <= w[ni])) pick[k] = nl++;
-            else pick[k] = ni++;
+            const bool leaf_ok = nl < n, int_ok = ni < created;
+            int pick;
+            if (leaf_ok && (!int_ok || lw <= iw)) {
+              pick = nl++;
+              sum += lw;
+              lw = nl < n ? w[nl] : 0;
+            } else {
+              pick = ni++;
+              sum += iw;
+              iw = ni < created ? w[ni] : 0;
+            }
+            parent[pick] = created;
           }
-          w[created] = w[pick[0]] + w[pick[1]];
-          parent[pick[0]] = created;
-          parent[pick[1]] = created;
+          w[created] = sum;
+          if (ni == created) iw = sum;  // the internal queue was empty: new head
           created++;
         }
-        depth[created - 1] = 0;
-        for (int v = created - 2; v >= 0; v--) depth[v] = depth[parent[v]] + 1;
-        for (int i = 0; i < n; i++) {
-          len_out[sorted[i]] = (uint8_t)depth[i];
-          maxlen = depth[i] > maxlen ? depth[i] : maxlen;
-        }
+        parent[created - 1] = created - 1;  // the root
       }
-      *flag = maxlen > 16;
+      __syncthreads();
+      // depths by pointer jumping: d(v) accumulates along doubling ancestor links
+      const int nodes = 2 * n - 1;
+      for (int v = t; v < nodes; v += blockDim.x) depth[v] = v == nodes - 1 ? 0 : 1;
+      __syncthreads();
+      for (int it = 0; it < 9; it++) {  // depth < 256 <= 2^9
+        int nd[2], na[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int v = t + u * 256;
+          if (v < nodes) {
+            const int a = parent[v];
+            nd[u] = depth[v] + depth[a];
+            na[u] = parent[a];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int v = t + u * 256;
+          if (v < nodes) {
+            depth[v] = nd[u];
+            parent[v] = na[u];
+          }
+        }
+        __syncthreads();
+      }
+      if (t < n) {
+        len_out[sorted[t]] = (uint8_t)depth[t];
+        atomicMax(&s_max, depth[t]);
+      }
+    } else if (n == 1 && t == 0) {
+      len_out[sorted[0]] = 1;
+      s_max = 1;
     }
+    __syncthreads();
+    if (t == 0) *flag = s_max > 16;
     __syncthreads();
     if (!*flag) break;
     if (f[t] > 0) f[t] = (f[t] + 1) >> 1;

@@ -231,26 +231,29 @@ __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict_
     }
     const int k = 4 * m->cur[l], bl = m->bl[l];
     const uint32_t* P = planes + D.plane_off / 4;
-    // the level's tiles (at most WPB: small levels) are unpacked by one warp
-    // each, then their 32 rows are spread over all warps
+    // the level's tiles, WPB at a time: each unpacked by one warp, then their
+    // 32 rows spread over all warps
     const uint32_t nt = D.ntiles;
-    if ((uint32_t)w < nt)
-      recompose_words<B>(P, D, w * HP_TILE, k, s_hi + w * 32 * 33,
-                         s_lo + (B == 64 ? w * 32 * 33 : 0), s_sign + w * 32);
-    __syncthreads();
-    for (uint32_t q = w; q < nt * 32; q += WPB) {
-      const uint32_t tile = q / 32;
-      const int r = (int)(q % 32);
-      if (final)
-        recompose_row<T, B, true>(D, tile * HP_TILE, r, bl, E_f, coarse, dst,
-                                  s_hi + tile * 32 * 33, s_lo + (B == 64 ? tile * 32 * 33 : 0),
-                                  s_sign + tile * 32);
-      else
-        recompose_row<T, B, false>(D, tile * HP_TILE, r, bl, E_f, coarse, dst,
-                                   s_hi + tile * 32 * 33, s_lo + (B == 64 ? tile * 32 * 33 : 0),
-                                   s_sign + tile * 32);
+    for (uint32_t t0 = 0; t0 < nt; t0 += WPB) {
+      const uint32_t nr = nt - t0 < (uint32_t)WPB ? nt - t0 : (uint32_t)WPB;
+      if ((uint32_t)w < nr)
+        recompose_words<B>(P, D, (t0 + w) * HP_TILE, k, s_hi + w * 32 * 33,
+                           s_lo + (B == 64 ? w * 32 * 33 : 0), s_sign + w * 32);
+      __syncthreads();
+      for (uint32_t q = w; q < nr * 32; q += WPB) {
+        const uint32_t tl = q / 32;
+        const int r = (int)(q % 32);
+        if (final)
+          recompose_row<T, B, true>(D, (t0 + tl) * HP_TILE, r, bl, E_f, coarse, dst,
+                                    s_hi + tl * 32 * 33, s_lo + (B == 64 ? tl * 32 * 33 : 0),
+                                    s_sign + tl * 32);
+        else
+          recompose_row<T, B, false>(D, (t0 + tl) * HP_TILE, r, bl, E_f, coarse, dst,
+                                     s_hi + tl * 32 * 33, s_lo + (B == 64 ? tl * 32 * 33 : 0),
+                                     s_sign + tl * 32);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     coarse = (const int64_t*)dst;
   }
 }

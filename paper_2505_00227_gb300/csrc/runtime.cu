@@ -79,7 +79,7 @@ hpmdr_status check_dims(int ndims, const uint64_t dims_in[3], uint64_t dims[3], 
 }
 
 // levels below this many nodes keep the tile kernels (one launch for all of them)
-static const uint32_t kGeneralCellMinNodes = 1u << 15;
+static const uint32_t kGeneralCellMinNodes = 1u << 14;
 
 static void plan_levels(Plan& P) {
   const int L = detail_levels(P.dims);
@@ -699,7 +699,8 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
   uint8_t* d_gsg = (uint8_t*)d_gq + gmax * (H->B / 8);
   // the root and the leading run of small generic levels run in one CTA
   int l_end = 0;
-  while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= 4096) l_end++;
+  while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= kSmallLevelNodes)
+    l_end++;
   {
     ProfScope p(P, ST_SMALL, 0, s);
     H->prof_small = p.i;
@@ -1906,6 +1907,16 @@ extern "C" hpmdr_status hpmdr_ctx_profile(hpmdr_ctx* ctx, int enable) {
   HP_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->prof.reset();
   ctx->prof.on = enable != 0;
+  ctx->prof.mask = ~0ull;
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_ctx_profile_stages(hpmdr_ctx* ctx, uint64_t stage_mask) {
+  if (!ctx) return HPMDR_ERR_ARG;
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.reset();
+  ctx->prof.on = stage_mask != 0;
+  ctx->prof.mask = stage_mask;
   return HPMDR_OK;
 }
 

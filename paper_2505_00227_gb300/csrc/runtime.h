@@ -37,6 +37,7 @@ struct ProfEntry {
 
 struct Profiler {
   bool on = false;
+  uint64_t mask = ~0ull;  // stages that record events (bit = Stage)
   std::vector<cudaEvent_t> pool;
   std::vector<ProfEntry> pending;
   double ms[NSTAGE] = {}, bytes[NSTAGE] = {};
@@ -52,7 +53,7 @@ struct Profiler {
     return e;
   }
   size_t begin(int stage, double b, cudaStream_t s) {
-    if (!on) return SIZE_MAX;
+    if (!on || !((mask >> stage) & 1u)) return SIZE_MAX;
     ProfEntry p{stage, get(), get(), b};
     cudaEventRecord(p.a, s);
     pending.push_back(p);

@@ -37,11 +37,18 @@ struct SeqView {
   int B, nlev, ngroups, dtype, E_f, input_exact;
   int bl[HP_MAX_LEVELS], exact[HP_MAX_LEVELS];
   int lim[HP_MAX_LEVELS];  // groups of the level that still reduce its error
-  // stored bytes per unit of error removed, len / 2^(bl - 4g): exact in double
-  // (len < 2^53, a power-of-two scale), so comparing keys is comparing the
-  // greedy ratios 2^(bl-4g) / len exactly
-  double key[HP_MAX_LEVELS][HP_MAX_GROUPS];
+  // stored bytes per unit of error removed, len / 2^(bl - 4g), as the bits of
+  // the (exact, positive, normal) double: comparing the bits as unsigned
+  // integers is comparing the greedy ratios 2^(bl-4g) / len exactly
+  uint64_t key[HP_MAX_LEVELS][HP_MAX_GROUPS];
 };
+
+// the IEEE bits of len * 2^-s for 1 <= len < 2^53, |s| < 900
+__device__ __forceinline__ uint64_t ratio_key(uint64_t len, int s) {
+  const int lz = __clzll((long long)len);
+  const uint64_t frac = (len << lz << 1) >> 12;  // bits below the leading one
+  return ((uint64_t)(1023 + 63 - lz - s) << 52) | frac;
+}
 
 template <class M>
 __device__ u128 level_delta(const M* m, int l, int k) {
@@ -98,7 +105,8 @@ __device__ __forceinline__ void sequence_warp(FieldMeta* m, int* g) {
   __syncwarp();
   for (int i = lane; i < nlev * ng; i += 32) {
     const int l = i / ng, q = i % ng;
-    V.key[l][q] = ldexp((double)m->grp[l][q].stored_len, -(V.bl[l] - 4 * q));
+    const uint64_t len = m->grp[l][q].stored_len;
+    V.key[l][q] = len ? ratio_key(len, V.bl[l] - 4 * q) : 0;
   }
   const SeqView* v = &V;
   for (int l = lane; l < nlev; l += 32) {
@@ -108,33 +116,35 @@ __device__ __forceinline__ void sequence_warp(FieldMeta* m, int* g) {
   }
   __syncwarp();
   // 1. the sequence: repeatedly the level with the smallest key (ties to the
-  // smaller level) among those with a group left that reduces the error
+  // smaller level) among those with a group left that reduces the error.  Lane
+  // j owns levels j and j + 32 (their group counts in registers); a step is
+  // three warp minimum reductions: key high word, key low word, level.
   __shared__ uint8_t s_seq[HP_SEQ_MAX], s_gq[HP_SEQ_MAX];
+  int ga = 0, gb = 0;  // groups taken of levels lane, lane + 32
   int n = 0;
   while (n < HP_SEQ_MAX) {
-    int best = -1;
-    double bk = 0;
-    for (int l = lane; l < nlev; l += 32) {
-      const int q = g[l];
-      if (q >= V.lim[l]) continue;
-      const double k = V.key[l][q];
-      if (best < 0 || k < bk) best = l, bk = k;
+    uint64_t bk = ~0ull;
+    int best = 255;
+    if (lane < nlev && ga < V.lim[lane]) bk = V.key[lane][ga], best = lane;
+    if (lane + 32 < nlev && gb < V.lim[lane + 32]) {
+      const uint64_t k2 = V.key[lane + 32][gb];
+      if (k2 < bk) bk = k2, best = lane + 32;
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const int ob = __shfl_xor_sync(HP_FULL, best, o);
-      const double ok = __shfl_xor_sync(HP_FULL, bk, o);
-      if (ob >= 0 && (best < 0 || ok < bk || (ok == bk && ob < best))) best = ob, bk = ok;
-    }
-    if (best < 0) break;
-    if (lane == 0) {
+    const uint32_t hi = (uint32_t)(bk >> 32), lo = (uint32_t)bk;
+    const uint32_t mh = __reduce_min_sync(HP_FULL, hi);
+    if (mh == 0xffffffffu) break;  // no level has a useful group left
+    const uint32_t ml = __reduce_min_sync(HP_FULL, hi == mh ? lo : 0xffffffffu);
+    const uint32_t win = __reduce_min_sync(HP_FULL, (hi == mh && lo == ml) ? (uint32_t)best : 255u);
+    if ((int)win == best) {  // the owner records the step
+      const int q = best == lane ? ga++ : gb++;
       s_seq[n] = (uint8_t)best;
-      s_gq[n] = (uint8_t)g[best];
-      g[best]++;
+      s_gq[n] = (uint8_t)q;
     }
     n++;
-    __syncwarp();
   }
+  g[lane] = ga;
+  g[lane + 32] = gb;
+  __syncwarp();
   // 2. the estimate after every prefix: sum_n = S0 - (r_0 + ... + r_{n-1}),
   // r_i = delta(l_i, 4 g_i) - delta(l_i, 4 g_i + 4) >= 0, an exact 128-bit
   // prefix sum (lane = block of consecutive steps, then a warp scan)

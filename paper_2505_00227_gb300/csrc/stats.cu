@@ -1,6 +1,8 @@
 // Field statistics: max|f|, min f, max f in one streaming pass, then the
 // exponent E_f that fixes the alignment unit U = 2^(E_f-48) (Sec. 4, the
 // "AlignExponent" step of Algorithm 1 needs the maximum exponent first).
+#include <type_traits>
+
 #include "dev_common.cuh"
 
 namespace hp {
@@ -30,35 +32,47 @@ void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, 
   hp::note_launch(), k_meta_init<<<1, 1, 0, s>>>(meta, dtype, B, nlev, ngroups);
 }
 
-// 128-bit vector loads over the bulk, scalar loads for the tail.
+// 128-bit vector loads over the bulk (four in flight per thread), scalar loads
+// for the tail; FP32 keys are compared as 32-bit integers.
 template <typename T>
 __global__ void __launch_bounds__(256) k_stats(const T* __restrict__ f, uint64_t N,
                                                int aligned, FieldMeta* meta) {
-  constexpr int VEC = 16 / sizeof(T);
-  uint64_t amax = 0, kmin = ~0ull, kmax = 0;
+  constexpr int VEC = 16 / sizeof(T), UN = 4;
+  typedef typename std::conditional<sizeof(T) == 4, uint32_t, uint64_t>::type K;
+  K am = 0, kn = (K)~(K)0, kx = 0;
+  auto visit = [&](T v) {
+    const K a = (K)abs_key(v), o = (K)order_key(v);
+    am = a > am ? a : am;
+    kn = o < kn ? o : kn;
+    kx = o > kx ? o : kx;
+  };
   const uint64_t nvec = aligned ? N / VEC : 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint4* fv = reinterpret_cast<const uint4*>(f);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += stride) {
-    uint4 w = __ldcs(fv + i);
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (UN - 1) * stride < nvec; i += UN * stride) {
+    uint4 w[UN];
+#pragma unroll
+    for (int u = 0; u < UN; u++) w[u] = __ldcs(fv + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < UN; u++) {
+      T v[VEC];
+      memcpy(v, &w[u], 16);
+#pragma unroll
+      for (int k = 0; k < VEC; k++) visit(v[k]);
+    }
+  }
+  for (; i < nvec; i += stride) {
+    const uint4 w = __ldcs(fv + i);
     T v[VEC];
     memcpy(v, &w, 16);
 #pragma unroll
-    for (int k = 0; k < VEC; k++) {
-      uint64_t a = abs_key(v[k]), o = order_key(v[k]);
-      amax = a > amax ? a : amax;
-      kmin = o < kmin ? o : kmin;
-      kmax = o > kmax ? o : kmax;
-    }
+    for (int k = 0; k < VEC; k++) visit(v[k]);
   }
-  for (uint64_t i = nvec * VEC + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += stride) {
-    T v = f[i];
-    uint64_t a = abs_key(v), o = order_key(v);
-    amax = a > amax ? a : amax;
-    kmin = o < kmin ? o : kmin;
-    kmax = o > kmax ? o : kmax;
-  }
+  for (uint64_t t = nvec * VEC + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N;
+       t += stride)
+    visit(f[t]);
+  uint64_t amax = am, kmin = kn == (K)~(K)0 ? ~0ull : (uint64_t)kn, kmax = kx;
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     uint64_t a = __shfl_xor_sync(HP_FULL, amax, o);

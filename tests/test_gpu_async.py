@@ -74,6 +74,7 @@ def test_async_two_handles_and_ring_drain(B):
 
 def test_async_unattainable_and_bad_arguments(B):
     f = _field((20, 20, 20), 8)
+    f[3, 4, 5] = np.float32(1e-20)  # below the fixed-point unit: no retrieval is exact
     ctx = B.Context()
     h = ctx.refactor(torch.from_numpy(f).cuda())
     o1, o2, o3 = (torch.empty(f.shape, dtype=torch.float32, device="cuda") for _ in range(3))
@@ -88,3 +89,19 @@ def test_async_unattainable_and_bad_arguments(B):
     with pytest.raises(B.HpmdrError):
         h.retrieve_async(-1.0, o1)
     assert ctx.wait() == 0  # nothing pending
+
+
+def test_profile_selected_stages_only(B):
+    f = _field((64, 64, 128), 9)
+    ctx = B.Context()
+    h = ctx.refactor(torch.from_numpy(f).cuda())
+    out = torch.empty(f.shape, dtype=torch.float32, device="cuda")
+    ctx.profile(True, stages=["cells_recompose_out", "select"])
+    infos = [h.retrieve_async(t, out) for t in TAUS]
+    ctx.wait()
+    prof = {p[0]: p for p in ctx.profile_entries()}
+    ctx.profile(False)
+    assert prof["cells_recompose_out"][2] == len(TAUS) and prof["select"][2] == len(TAUS)
+    assert prof["cells_recompose_out"][1] > 0 and prof["cells_recompose_out"][3] > 0
+    assert all(p[2] == 0 for k, p in prof.items() if k not in ("cells_recompose_out", "select"))
+    assert all(i.status == 0 for i in infos)

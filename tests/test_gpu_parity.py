@@ -177,7 +177,19 @@ def _groups():
         "sparse": ((rng.random(70000) < 0.03) * rng.integers(1, 256, 70000)).astype(np.uint8),
         "runs": np.repeat(rng.integers(0, 5, 400), rng.integers(1, 300, 400)).astype(np.uint8),
         "ragged": rng.integers(0, 3, 16384 * 2 + 13).astype(np.uint8),
+        # Fibonacci counts: an uncapped code would be 25 bits deep, so the
+        # lengths are capped (counts halved and the code rebuilt, twice or more)
+        "fibonacci": _fibonacci_group(),
     }
+
+
+def _fibonacci_group():
+    counts, a, b = [], 1, 1
+    for _ in range(26):
+        counts.append(a)
+        a, b = b, a + b
+    G = np.repeat(np.arange(26, dtype=np.uint8) * 7 + 1, counts)
+    return np.random.default_rng(9).permutation(G).astype(np.uint8)
 
 
 @pytest.mark.parametrize("name", list(_groups()))
