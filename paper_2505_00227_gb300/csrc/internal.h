@@ -188,6 +188,19 @@ struct ChunkMap {
 // group_hist (256 per group) and group_cost (per group) must start at zero
 void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* group_hist,
                         unsigned long long* group_cost, uint32_t* chunk_cost, cstream s);
+// refactor: device-built lists of the Huffman and RLE chunks (lists holds
+// 2 total_chunks entries, counts 2 zeroed words), and the coders over them
+void launch_coder_lists(const FieldMeta* meta, ChunkMap cm, uint32_t* lists, uint32_t* counts,
+                        cstream s);
+void launch_huff_bits_list(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                           const uint8_t* lens, uint32_t* chunk_words, const uint32_t* lists,
+                           const uint32_t* counts, cstream s);
+void launch_huff_encode_list(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                             const uint8_t* lens, const uint32_t* chunk_out, uint8_t* slots,
+                             const uint32_t* lists, const uint32_t* counts, cstream s);
+void launch_rle_encode_list(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                            const uint32_t* chunk_out, uint8_t* slots, const uint32_t* lists,
+                            const uint32_t* counts, cstream s);
 void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* group_hist,
                    const unsigned long long* group_cost, uint8_t* lens, uint64_t Ts,
                    uint32_t cr_num, uint32_t cr_den, int force, cstream s);

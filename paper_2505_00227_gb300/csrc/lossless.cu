@@ -363,24 +363,55 @@ void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* group_his
                                                             cr_num, cr_den, force);
 }
 
+// block-wide exclusive prefix sum (any thread count that is a multiple of 32,
+// up to 1024); returns the inclusive total too
+__device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* scratch, uint32_t& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(HP_FULL, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) scratch[w] = x;
+  __syncthreads();
+  uint32_t base = 0, all = 0;
+  for (int k = 0; k < nw; k++) {
+    if (k < w) base += scratch[k];
+    all += scratch[k];
+  }
+  __syncthreads();
+  total = all;
+  return base + x - v;
+}
+
 // --------------------------------------------------- canonical Huffman codes
-// code[t] for the canonical code of lengths len[] ((length, symbol) order)
+// code[t] for the canonical code of lengths len[] ((length, symbol) order),
+// 256 threads: a symbol's rank among the symbols of its length is the count in
+// earlier warps (per-warp length counts) plus the earlier lanes of its own
+// warp holding the same length (a warp match)
 __device__ void canonical_codes_block(const uint8_t* len, uint32_t* code, uint32_t* first) {
-  const int t = threadIdx.x;
+  __shared__ uint32_t wcnt[8][17];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t < 8 * 17) (&wcnt[0][0])[t] = 0;
+  __syncthreads();
+  const uint32_t L = len[t];
+  const unsigned same = __match_any_sync(HP_FULL, L);
+  if ((int)(__ffs(same) - 1) == lane) wcnt[w][L] = __popc(same);  // one writer per length
+  __syncthreads();
   if (t == 0) {
-    uint32_t cnt[17];
-    for (int L = 0; L <= 16; L++) cnt[L] = 0;
-    for (int s = 0; s < 256; s++) cnt[len[s]]++;
     uint32_t c = 0;
-    for (int L = 1; L <= 16; L++) {
-      first[L] = c;
-      c = (c + cnt[L]) << 1;
+    for (int l = 1; l <= 16; l++) {
+      first[l] = c;
+      uint32_t n = 0;
+      for (int k = 0; k < 8; k++) n += wcnt[k][l];
+      c = (c + n) << 1;
     }
   }
   __syncthreads();
-  uint32_t L = len[t], r = 0;
   if (L) {
-    for (int s = 0; s < t; s++) r += (len[s] == L) ? 1u : 0u;
+    uint32_t r = __popc(same & ((1u << lane) - 1u));
+    for (int k = 0; k < w; k++) r += wcnt[k][L];
     code[t] = first[L] + r;
   } else {
     code[t] = 0;
@@ -438,6 +469,71 @@ void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
   hp::note_launch(), k_huff_bits<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_words);
 }
 
+// ------------------------------------------- coder work lists (refactor)
+// The chunks of the Huffman groups (lists[0 ..)) and of the RLE groups
+// (lists[tc ..)), appended in any order; counts[0], counts[1] start at zero.
+// The coder kernels then run persistent CTAs over their own list instead of a
+// CTA per chunk of the field (most chunks belong to direct-copy groups).
+__global__ void k_coder_lists(const FieldMeta* __restrict__ meta,
+                              const uint32_t* __restrict__ chunk_group, uint32_t tc,
+                              uint32_t* __restrict__ lists, uint32_t* __restrict__ counts) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (meta->status) return;
+  int m = 0;
+  if (c < tc) {
+    const uint32_t gi = chunk_group[c];
+    const int ng = meta->ngroups;
+    m = meta->grp[gi / ng][gi % ng].method;
+  }
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 1; k <= 2; k++) {  // one atomic per warp and method
+    const unsigned hit = __ballot_sync(HP_FULL, m == k);
+    if (!hit) continue;
+    uint32_t base = 0;
+    if (lane == __ffs(hit) - 1) base = atomicAdd(&counts[k - 1], (uint32_t)__popc(hit));
+    base = __shfl_sync(HP_FULL, base, __ffs(hit) - 1);
+    if (m == k) lists[(k - 1) * (size_t)tc + base + __popc(hit & ((1u << lane) - 1u))] = c;
+  }
+}
+
+void launch_coder_lists(const FieldMeta* meta, ChunkMap cm, uint32_t* lists, uint32_t* counts,
+                        cstream s) {
+  if (cm.total_chunks == 0) return;
+  hp::note_launch(), k_coder_lists<<<(cm.total_chunks + 255) / 256, 256, 0, s>>>(
+      meta, cm.chunk_group, cm.total_chunks, lists, counts);
+}
+
+__global__ void __launch_bounds__(256) k_huff_bits_list(const uint8_t* __restrict__ planes,
+                                                        const FieldMeta* __restrict__ meta,
+                                                        const uint32_t* __restrict__ chunk_group,
+                                                        const uint8_t* __restrict__ lens,
+                                                        uint32_t* __restrict__ chunk_words,
+                                                        const uint32_t* __restrict__ list,
+                                                        const uint32_t* __restrict__ count) {
+  const uint32_t n = *count;
+  for (uint32_t e = blockIdx.x; e < n; e += gridDim.x) {
+    huff_bits_unit(planes, meta, chunk_group, lens, chunk_words, list[e]);
+    __syncthreads();
+  }
+}
+
+static uint32_t coder_grid(uint32_t total, int per_sm) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t cap = (uint32_t)(sms * per_sm);
+  return total < cap ? (total ? total : 1u) : cap;
+}
+
+void launch_huff_bits_list(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                           const uint8_t* lens, uint32_t* chunk_words, const uint32_t* lists,
+                           const uint32_t* counts, cstream s) {
+  if (cm.total_chunks == 0) return;
+  hp::note_launch(), k_huff_bits_list<<<coder_grid(cm.total_chunks, 8), 256, 0, s>>>(
+      planes, meta, cm.chunk_group, lens, chunk_words, lists, counts);
+}
+
 // ------------------------------------ per-group chunk output offsets (scan)
 // Huffman: word offset of each chunk in the payload; RLE: byte offset.
 __device__ __forceinline__ void group_offsets_unit(FieldMeta* meta,
@@ -492,6 +588,10 @@ void launch_group_offsets(FieldMeta* meta, int ngroups_total, const uint32_t* ch
 }
 
 // -------------------------------------------------------- Huffman: encode
+// Thread t codes bytes [64 t, 64 t + 64) of the chunk: its bit offset comes
+// from a block scan of the code lengths, its bits are packed in a 64-bit
+// register and written a word at a time; only its first and last words can be
+// shared with a neighbour, and those are merged with atomicOr.
 __device__ __forceinline__ void huff_encode_unit(const uint8_t* __restrict__ planes,
                                                      const FieldMeta* __restrict__ meta,
                                                      const uint32_t* __restrict__ chunk_group,
@@ -502,7 +602,7 @@ __device__ __forceinline__ void huff_encode_unit(const uint8_t* __restrict__ pla
   __shared__ uint8_t len[256];
   __shared__ uint32_t code[256], first[17];
   __shared__ uint32_t outw[HP_CHUNK * 16 / 32];  // worst case: 16 bits per byte
-  __shared__ uint32_t scan[256];
+  __shared__ uint32_t scratch[8];
   if (meta->status) return;
   ChunkRef r = chunk_ref(meta, chunk_group, c_unit);
   if (r.gm->method != 1) return;
@@ -511,48 +611,62 @@ __device__ __forceinline__ void huff_encode_unit(const uint8_t* __restrict__ pla
   for (int i = t; i < HP_CHUNK * 16 / 32; i += 256) outw[i] = 0;
   __syncthreads();
   canonical_codes_block(len, code, first);
-  // thread t encodes bytes [64 t, 64 t + 64) of the chunk, in order
   const uint8_t* src = planes + r.gm->plane_off + r.start;
-  const uint32_t a = t * 64u, b = min(r.len, a + 64u);
-  uint8_t mine[64];
+  const uint32_t a = t * 64u, nb = r.len > a ? min(r.len - a, 64u) : 0u;
+  uint32_t wv[16];
+  if (nb == 64) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + a);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint4 v = __ldcs(s4 + k);
+      wv[4 * k] = v.x;
+      wv[4 * k + 1] = v.y;
+      wv[4 * k + 2] = v.z;
+      wv[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      uint32_t x = 0;
+      for (int q = 0; q < 4; q++)
+        if (4u * k + q < nb) x |= (uint32_t)src[a + 4 * k + q] << (8 * q);
+      wv[k] = x;
+    }
+  }
   uint32_t bits = 0;
-  for (uint32_t i = a; i < b; i += 16) {
-    if (i + 16 <= b) {
-      uint4 v = __ldcs(reinterpret_cast<const uint4*>(src + i));
-      memcpy(mine + (i - a), &v, 16);
-    } else {
-      for (uint32_t k = i; k < b; k++) mine[k - a] = src[k];
+#pragma unroll
+  for (int k = 0; k < 16; k++)
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if (4u * k + q < nb) bits += len[(wv[k] >> (8 * q)) & 0xffu];
+  uint32_t total;
+  const uint32_t pos = block_exscan(bits, scratch, total);
+  uint64_t acc = 0;  // pending bits, MSB-aligned
+  int nacc = (int)(pos & 31);
+  uint32_t wd = pos >> 5;
+  bool shared_word = true;  // the first word may hold the previous thread's bits
+#pragma unroll
+  for (int k = 0; k < 16; k++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (4u * k + q < nb) {
+        const uint32_t sym = (wv[k] >> (8 * q)) & 0xffu, L = len[sym];
+        acc |= (uint64_t)code[sym] << (64 - nacc - (int)L);
+        nacc += (int)L;
+        if (nacc >= 32) {
+          const uint32_t hi = (uint32_t)(acc >> 32);
+          if (shared_word) atomicOr(&outw[wd], hi);
+          else outw[wd] = hi;
+          shared_word = false;
+          acc <<= 32;
+          nacc -= 32;
+          wd++;
+        }
+      }
     }
-  }
-  for (uint32_t i = a; i < b; i++) bits += len[mine[i - a]];
-  scan[t] = bits;
+  if (nacc > 0 && bits > 0) atomicOr(&outw[wd], (uint32_t)(acc >> 32));  // shared with the next
   __syncthreads();
-  if (t == 0) {
-    uint32_t run = 0;
-    for (int k = 0; k < 256; k++) {
-      uint32_t v = scan[k];
-      scan[k] = run;
-      run += v;
-    }
-  }
-  __syncthreads();
-  uint32_t pos = scan[t];
-  for (uint32_t i = a; i < b; i++) {
-    uint32_t s = mine[i - a], L = len[s], cw = code[s];
-    uint32_t wd = pos >> 5, o = pos & 31;
-    if (o + L <= 32) {
-      atomicOr(&outw[wd], cw << (32 - o - L));
-    } else {
-      uint32_t spill = o + L - 32;
-      atomicOr(&outw[wd], cw >> spill);
-      atomicOr(&outw[wd + 1], cw << (32 - spill));
-    }
-    pos += L;
-  }
-  __shared__ uint32_t nbits;
-  if (t == 255) nbits = pos;
-  __syncthreads();
-  const uint32_t nwords = (nbits + 31) / 32;
+  const uint32_t nwords = (total + 31) / 32;
   uint32_t* dst = reinterpret_cast<uint32_t*>(slots + r.gm->slot_off +
                                               huff_header_bytes(r.gm->nchunks)) +
                   chunk_out[c_unit];
@@ -566,6 +680,29 @@ __global__ void __launch_bounds__(256) k_huff_encode(const uint8_t* __restrict__
                                                      const uint32_t* __restrict__ chunk_out,
                                                      uint8_t* __restrict__ slots) {
   huff_encode_unit(planes, meta, chunk_group, lens, chunk_out, slots, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256, 4) k_huff_encode_list(const uint8_t* __restrict__ planes,
+                                                          const FieldMeta* __restrict__ meta,
+                                                          const uint32_t* __restrict__ chunk_group,
+                                                          const uint8_t* __restrict__ lens,
+                                                          const uint32_t* __restrict__ chunk_out,
+                                                          uint8_t* __restrict__ slots,
+                                                          const uint32_t* __restrict__ list,
+                                                          const uint32_t* __restrict__ count) {
+  const uint32_t n = *count;
+  for (uint32_t e = blockIdx.x; e < n; e += gridDim.x) {
+    huff_encode_unit(planes, meta, chunk_group, lens, chunk_out, slots, list[e]);
+    __syncthreads();
+  }
+}
+
+void launch_huff_encode_list(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                             const uint8_t* lens, const uint32_t* chunk_out, uint8_t* slots,
+                             const uint32_t* lists, const uint32_t* counts, cstream s) {
+  if (cm.total_chunks == 0) return;
+  hp::note_launch(), k_huff_encode_list<<<coder_grid(cm.total_chunks, 4), 256, 0, s>>>(
+      planes, meta, cm.chunk_group, lens, chunk_out, slots, lists, counts);
 }
 
 void launch_huff_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
@@ -634,6 +771,28 @@ __global__ void __launch_bounds__(256) k_rle_encode(const uint8_t* __restrict__ 
                                                     const uint32_t* __restrict__ chunk_out,
                                                     uint8_t* __restrict__ slots) {
   rle_encode_unit(planes, meta, chunk_group, chunk_out, slots, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_rle_encode_list(const uint8_t* __restrict__ planes,
+                                                         const FieldMeta* __restrict__ meta,
+                                                         const uint32_t* __restrict__ chunk_group,
+                                                         const uint32_t* __restrict__ chunk_out,
+                                                         uint8_t* __restrict__ slots,
+                                                         const uint32_t* __restrict__ list,
+                                                         const uint32_t* __restrict__ count) {
+  const uint32_t n = *count;
+  for (uint32_t e = blockIdx.x; e < n; e += gridDim.x) {
+    rle_encode_unit(planes, meta, chunk_group, chunk_out, slots, list[e]);
+    __syncthreads();
+  }
+}
+
+void launch_rle_encode_list(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
+                            const uint32_t* chunk_out, uint8_t* slots, const uint32_t* lists,
+                            const uint32_t* counts, cstream s) {
+  if (cm.total_chunks == 0) return;
+  hp::note_launch(), k_rle_encode_list<<<coder_grid(cm.total_chunks, 4), 256, 0, s>>>(
+      planes, meta, cm.chunk_group, chunk_out, slots, lists + cm.total_chunks, counts + 1);
 }
 
 void launch_rle_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
@@ -712,6 +871,7 @@ __device__ __forceinline__ void set_corrupt(FieldMeta* meta) { atomicExch(&meta-
 // The bitmap covers the longest possible chunk (16384 codes of 16 bits); a
 // chunk claiming more bits is decoded by one lane and then fails its checks.  All reads stay inside the chunk's words; an
 // invalid code or a wrong symbol count marks the data corrupt.
+#define HP_DEC_THREADS 128
 #define HP_LUT_BITS 10
 #define HP_MAP_WORDS 8192  // bitmap of 262144 bit positions per warp: 16 bits x 16384 symbols
 
@@ -804,29 +964,6 @@ __device__ __forceinline__ bool huff_emit(const HuffTables& T, BitReader& rd, ui
   if (p & 3)
     for (uint32_t q = max(o, p & ~3u); q < p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
   return true;
-}
-
-// block-wide exclusive prefix sum over HP_DEC_THREADS values (any thread count
-// that is a multiple of 32, up to 1024); returns the inclusive total too
-#define HP_DEC_THREADS 128
-__device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* scratch, uint32_t& total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(HP_FULL, x, d);
-    if (lane >= d) x += y;
-  }
-  if (lane == 31) scratch[w] = x;
-  __syncthreads();
-  uint32_t base = 0, all = 0;
-  for (int k = 0; k < nw; k++) {
-    if (k < w) base += scratch[k];
-    all += scratch[k];
-  }
-  __syncthreads();
-  total = all;
-  return base + x - v;
 }
 
 __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm,

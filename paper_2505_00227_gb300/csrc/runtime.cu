@@ -376,12 +376,13 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   // per-call scratch in one block: group histograms and RLE sizes (zeroed,
   // accumulated by atomics), chunk costs, chunk words, chunk offsets, lengths
   const size_t o_hist = 0, o_gcost = align256(1024ull * ngt);
-  const size_t o_cost = o_gcost + align256(8ull * ngt);
+  const size_t o_counts = o_gcost + align256(8ull * ngt), o_cost = o_counts + 256;
   const size_t o_words = o_cost + align256(4ull * tc), o_out = o_words + align256(4ull * tc);
   const size_t o_lens = o_out + align256(4ull * tc), o_gq = o_lens + align256(256ull * ngt);
   // staging of the general cell levels (one level at a time)
   const uint64_t gmax = H->plan->gstage_max;
-  const size_t o_gsg = o_gq + align256(gmax * (H->B / 8)), scratch_bytes = o_gsg + align256(gmax);
+  const size_t o_gsg = o_gq + align256(gmax * (H->B / 8)), o_lists = o_gsg + align256(gmax);
+  const size_t scratch_bytes = o_lists + align256(8ull * tc);
   unsigned char* sc = nullptr;
   HP_TRY(H->A.alloc((void**)&sc, scratch_bytes, s));
   uint32_t* d_hist = (uint32_t*)(sc + o_hist);
@@ -392,6 +393,8 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   uint8_t* d_lens = (uint8_t*)(sc + o_lens);
   void* d_gq = sc + o_gq;
   uint8_t* d_gsg = sc + o_gsg;
+  uint32_t* d_counts = (uint32_t*)(sc + o_counts);  // zeroed with the histograms
+  uint32_t* d_lists = (uint32_t*)(sc + o_lists);
   if (cudaMemsetAsync(sc, 0, o_cost, s) != cudaSuccess ||
       cudaMemcpyAsync(H->d_meta, H->plan->d_meta0, sizeof(FieldMeta), cudaMemcpyDeviceToDevice,
                       s) != cudaSuccess) {
@@ -450,14 +453,16 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   { ProfScope p(P, ST_DECIDE, cb, s);
     launch_decide(H->d_meta, ngt, d_hist, d_gcost, d_lens, ctx->Ts, ctx->cr_num, ctx->cr_den,
                   ctx->force, s); }
+  launch_coder_lists(H->d_meta, cm, d_lists, d_counts, s);
   { ProfScope p(P, ST_HUFF_BITS, 0, s); rp->hbits = p.i;
-    launch_huff_bits(H->d_planes, H->d_meta, cm, d_lens, d_words, s); }
+    launch_huff_bits_list(H->d_planes, H->d_meta, cm, d_lens, d_words, d_lists, d_counts, s); }
   { ProfScope p(P, ST_OFFSETS, 0, s);
     launch_group_offsets(H->d_meta, ngt, d_words, d_cost, d_out, s); }
   { ProfScope p(P, ST_HUFF_ENC, 0, s); rp->henc = p.i;
-    launch_huff_encode(H->d_planes, H->d_meta, cm, d_lens, d_out, H->d_slots, s); }
+    launch_huff_encode_list(H->d_planes, H->d_meta, cm, d_lens, d_out, H->d_slots, d_lists,
+                            d_counts, s); }
   { ProfScope p(P, ST_RLE_ENC, 0, s); rp->renc = p.i;
-    launch_rle_encode(H->d_planes, H->d_meta, cm, d_out, H->d_slots, s); }
+    launch_rle_encode_list(H->d_planes, H->d_meta, cm, d_out, H->d_slots, d_lists, d_counts, s); }
   { ProfScope p(P, ST_HEADERS, 0, s); launch_headers(H->d_meta, ngt, d_lens, d_out, H->d_slots, s); }
   { ProfScope p(P, ST_SEQUENCE, 0, s); launch_sequence(H->d_meta, s); }
   H->A.release(sc, s);
