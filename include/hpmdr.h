@@ -133,6 +133,39 @@ HPMDR_API hpmdr_status hpmdr_retrieve_async(hpmdr_ctx* ctx, hpmdr_handle* h, dou
                                             void* out, hpmdr_retrieve_info* info);
 HPMDR_API hpmdr_status hpmdr_ctx_wait(hpmdr_ctx* ctx);
 
+/* ---- out-of-core pipeline (Sec. 5.3, the refactoring and retrieval pipelines)
+ * nvars variables of one shape (dims, ndims entries as for hpmdr_refactor) in
+ * host memory, cut into chunks as for hpmdr_refactor_chunked, are refactored
+ * unit by unit, unit u = v * nchunks + c, into serialized streams in host
+ * memory (the hpmdr_handle_export format, one per unit), and retrieved back
+ * from them.  Three queues, one CUDA stream each: host -> device copies,
+ * kernels, device -> host copies; unit u + 1's input goes in while unit u's
+ * kernels run and unit u - 1's result comes out; two device input (output)
+ * buffers alternate and at most three units' handles are on the device.
+ * queues = 3 runs that pipeline; queues = 1 puts every step of every unit on
+ * one stream, in order (nothing overlaps: the baseline of Sec. 5.3's
+ * comparison).  Overlap needs page-locked host memory for fields, streams and
+ * outputs.
+ * hpmdr_refactor_pipeline: out == NULL sets *total to a bound on the bytes of
+ * all streams; else out (16-byte aligned, *total bytes) receives the streams
+ * back to back, each 16-byte aligned, offsets[u] / sizes[u] (nvars * nchunks
+ * entries) their placement, and *total the bytes used.
+ * hpmdr_retrieve_pipeline: every unit of variable v at rel_bounds[v], relative
+ * to v's whole range (from the streams' headers), into the host array outs[v]
+ * (dims); infos (may be NULL) gets one record per unit.  Returns HPMDR_OK, or
+ * HPMDR_ERR_UNATTAINABLE when some unit could not meet its bound. */
+HPMDR_API hpmdr_status hpmdr_refactor_pipeline(hpmdr_ctx* ctx, int nvars, const void* const* fields,
+                                               int ndims, const uint64_t dims[3],
+                                               const uint64_t chunk[3], hpmdr_dtype dtype,
+                                               int queues, void* out, uint64_t* total,
+                                               uint64_t* offsets, uint64_t* sizes);
+HPMDR_API hpmdr_status hpmdr_retrieve_pipeline(hpmdr_ctx* ctx, int nvars, const void* streams,
+                                               const uint64_t* offsets, const uint64_t* sizes,
+                                               int ndims, const uint64_t dims[3],
+                                               const uint64_t chunk[3], const double* rel_bounds,
+                                               int queues, void* const* outs,
+                                               hpmdr_retrieve_info* infos);
+
 /* ---- QoI retrieval (Sec. 6.2, Algorithm 3) for the velocity magnitude
  * |v| = sqrt(vx^2 + vy^2 + vz^2) of three FP32 handles of equal shape.
  * rel_qoi_bound is relative to max|v| - min|v| of the refactored data.

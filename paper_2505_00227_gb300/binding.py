@@ -105,6 +105,10 @@ _SIGS = {
     "hpmdr_handle_memory": (C.c_int, [vp, u64p, u64p, u64p]),
     "hpmdr_retrieve_async": (C.c_int, [vp, vp, C.c_double, vp, vp]),
     "hpmdr_ctx_wait": (C.c_int, [vp]),
+    "hpmdr_refactor_pipeline": (C.c_int, [vp, C.c_int, vp, C.c_int, u64p, u64p, C.c_int, C.c_int,
+                                          vp, u64p, u64p, u64p]),
+    "hpmdr_retrieve_pipeline": (C.c_int, [vp, C.c_int, vp, u64p, u64p, C.c_int, u64p, u64p,
+                                          C.POINTER(C.c_double), C.c_int, vp, vp]),
     "hpmdr_ctx_profile_stages": (C.c_int, [vp, C.c_uint64]),
     "hpmdr_fixed_to_float": (C.c_int, [vp, vp, C.c_uint64, C.c_int, C.c_int, vp]),
     "hpmdr_refactor_chunked": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_uint64 * 3, C.c_uint64 * 3,
@@ -211,6 +215,49 @@ class Context:
         self._keep = []  # infos and outputs of pending asynchronous retrievals
         _check(lib().hpmdr_ctx_create(C.byref(self._p), C.byref(cfg), None, _stream_ptr(stream)),
                "hpmdr_ctx_create")
+
+    def refactor_pipeline(self, fields, chunk, queues=3):
+        """Out-of-core refactoring of host tensors of one shape (Sec. 5.3):
+        returns (streams as a page-locked uint8 tensor, offsets, sizes)."""
+        import torch
+        nv = len(fields)
+        shape = tuple(fields[0].shape)
+        dt = F32 if fields[0].dtype == torch.float32 else F64
+        nd = len(shape)
+        dims = (C.c_uint64 * 3)(*([1] * (3 - nd) + list(shape)))
+        ch = (C.c_uint64 * 3)(*([1] * (3 - nd) + list(chunk)))
+        ptrs = (vp * nv)(*[vp(f.data_ptr()) for f in fields])
+        total = C.c_uint64(0)
+        _check(lib().hpmdr_refactor_pipeline(self._p, nv, ptrs, nd, dims, ch, dt, queues, None,
+                                             C.byref(total), None, None), "hpmdr_refactor_pipeline")
+        out = torch.empty(total.value, dtype=torch.uint8).pin_memory()
+        ncell = 1
+        for d, c in zip(shape, chunk):
+            ncell *= (d + c - 1) // c
+        offs = (C.c_uint64 * (nv * ncell))()
+        sizes = (C.c_uint64 * (nv * ncell))()
+        _check(lib().hpmdr_refactor_pipeline(self._p, nv, ptrs, nd, dims, ch, dt, queues,
+                                             vp(out.data_ptr()), C.byref(total), offs, sizes),
+               "hpmdr_refactor_pipeline")
+        return out[: total.value], list(offs), list(sizes)
+
+    def retrieve_pipeline(self, streams, offsets, sizes, shape, chunk, bounds, outs, queues=3):
+        """Retrieve every unit of the streams into the host tensors `outs` (one
+        per variable) at the relative bounds; returns (infos, status)."""
+        nv = len(outs)
+        nd = len(shape)
+        dims = (C.c_uint64 * 3)(*([1] * (3 - nd) + list(shape)))
+        ch = (C.c_uint64 * 3)(*([1] * (3 - nd) + list(chunk)))
+        n = len(offsets)
+        offs = (C.c_uint64 * n)(*offsets)
+        szs = (C.c_uint64 * n)(*sizes)
+        b = (C.c_double * nv)(*[float(x) for x in bounds])
+        ptrs = (vp * nv)(*[vp(o.data_ptr()) for o in outs])
+        infos = (RetrieveInfo * n)()
+        st = lib().hpmdr_retrieve_pipeline(self._p, nv, vp(streams.data_ptr()), offs, szs, nd, dims,
+                                           ch, b, queues, ptrs, infos)
+        _check(st, "hpmdr_retrieve_pipeline", allow=(ERR_UNATTAINABLE,))
+        return list(infos), st
 
     def wait(self):
         """Wait for the context stream; fills the infos of the asynchronous

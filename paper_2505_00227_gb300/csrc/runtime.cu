@@ -1434,72 +1434,111 @@ struct Reader {
 };
 }  // namespace
 
+// one copy per run of byte ranges that are contiguous on both sides
+struct CopyRuns {
+  std::vector<std::array<uint64_t, 3>> v;  // dst, src, len
+  void add(void* dst, const void* src, uint64_t len) {
+    const uint64_t d = (uint64_t)(uintptr_t)dst, s = (uint64_t)(uintptr_t)src;
+    if (!v.empty() && v.back()[0] + v.back()[2] == d && v.back()[1] + v.back()[2] == s)
+      v.back()[2] += len;
+    else
+      v.push_back({d, s, len});
+  }
+  hpmdr_status issue(cudaMemcpyKind kind, cudaStream_t st) const {
+    for (const auto& c : v)
+      HP_CUDA(cudaMemcpyAsync((void*)(uintptr_t)c[0], (const void*)(uintptr_t)c[1], c[2], kind, st));
+    return HPMDR_OK;
+  }
+};
+
+// The export stream of h: its header written to buf (nullptr: sizes only),
+// and where each stored group goes (byte offset in the stream, length), in
+// (level, group) order.  Returns the stream length.
+static uint64_t export_layout(const hpmdr_handle* h, uint8_t* buf,
+                              std::vector<std::pair<uint64_t, uint64_t>>* pos) {
+  const FieldMeta& M = *h->meta;
+  Writer w{buf};
+  w.put("HPMDR1\0\0", 8);
+  w.val<uint32_t>(1);
+  w.val<uint32_t>(0);
+  w.val<int32_t>(h->dtype);
+  w.val<int32_t>(h->B);
+  w.val<int32_t>(h->nlev);
+  w.val<int32_t>(h->ngroups);
+  w.val<int32_t>(M.E_f);
+  w.val<int32_t>(M.input_exact);
+  for (int d = 0; d < 3; d++) w.val<uint64_t>(h->dims[d]);
+  w.val<double>(M.maxabs);
+  w.val<double>(M.vmin);
+  w.val<double>(M.vmax);
+  w.val<double>(M.range);
+  w.val<float>(h->qmin);
+  w.val<float>(h->qmax);
+  w.val<int32_t>(h->qoi_ready ? 1 : 0);
+  w.val<int32_t>(M.seq_len);
+  for (int l = 0; l < h->nlev; l++) {
+    w.val<int32_t>(M.bl[l]);
+    w.val<int32_t>(M.exact[l]);
+  }
+  for (int l = 0; l < h->nlev; l++)
+    for (int g = 0; g < h->ngroups; g++) {
+      const GroupMeta& G = M.grp[l][g];
+      w.val<uint64_t>(G.stored_len);
+      w.val<int32_t>(G.method);
+      w.val<int32_t>(0);
+      w.val<uint64_t>(G.est_H);
+      w.val<uint64_t>(G.est_R);
+    }
+  w.put(M.seq, M.seq_len);
+  w.pad(8);
+  for (int i = 0; i <= M.seq_len; i++) w.val<uint64_t>(M.E_hi[i]);
+  for (int i = 0; i <= M.seq_len; i++) w.val<uint64_t>(M.E_lo[i]);
+  w.pad(16);
+  if (pos) pos->clear();
+  for (int l = 0; l < h->nlev; l++)
+    for (int g = 0; g < h->ngroups; g++) {
+      const GroupMeta& G = M.grp[l][g];
+      if (pos) pos->push_back({w.n, G.stored_len});
+      w.n += G.stored_len;  // the group's bytes are copied by the caller
+      w.pad(16);
+    }
+  return w.n;
+}
+
+// largest export stream of a handle of this plan: header + every group stored
+// directly (a coded group is kept only when smaller) + alignment
+static uint64_t export_bound(const Plan& P) {
+  const uint64_t groups = (uint64_t)P.nlev * P.ngroups;
+  return 4096 + 8ull * P.nlev + 32 * groups + 17ull * (HP_SEQ_MAX + 1) + P.plane_bytes +
+         16 * groups;
+}
+
 extern "C" hpmdr_status hpmdr_handle_export(const hpmdr_handle* h, void* buf, uint64_t* len) {
   if (!h || !len) return HPMDR_ERR_ARG;
-  const FieldMeta& M = *h->meta;
-  for (int pass = 0; pass < 2; pass++) {
-    Writer w{pass ? (uint8_t*)buf : nullptr};
-    w.put("HPMDR1\0\0", 8);
-    w.val<uint32_t>(1);
-    w.val<uint32_t>(0);
-    w.val<int32_t>(h->dtype);
-    w.val<int32_t>(h->B);
-    w.val<int32_t>(h->nlev);
-    w.val<int32_t>(h->ngroups);
-    w.val<int32_t>(M.E_f);
-    w.val<int32_t>(M.input_exact);
-    for (int d = 0; d < 3; d++) w.val<uint64_t>(h->dims[d]);
-    w.val<double>(M.maxabs);
-    w.val<double>(M.vmin);
-    w.val<double>(M.vmax);
-    w.val<double>(M.range);
-    w.val<float>(h->qmin);
-    w.val<float>(h->qmax);
-    w.val<int32_t>(h->qoi_ready ? 1 : 0);
-    w.val<int32_t>(M.seq_len);
-    for (int l = 0; l < h->nlev; l++) {
-      w.val<int32_t>(M.bl[l]);
-      w.val<int32_t>(M.exact[l]);
-    }
-    for (int l = 0; l < h->nlev; l++)
-      for (int g = 0; g < h->ngroups; g++) {
-        const GroupMeta& G = M.grp[l][g];
-        w.val<uint64_t>(G.stored_len);
-        w.val<int32_t>(G.method);
-        w.val<int32_t>(0);
-        w.val<uint64_t>(G.est_H);
-        w.val<uint64_t>(G.est_R);
-      }
-    w.put(M.seq, M.seq_len);
-    w.pad(8);
-    for (int i = 0; i <= M.seq_len; i++) w.val<uint64_t>(M.E_hi[i]);
-    for (int i = 0; i <= M.seq_len; i++) w.val<uint64_t>(M.E_lo[i]);
-    w.pad(16);
-    for (int l = 0; l < h->nlev; l++)
-      for (int g = 0; g < h->ngroups; g++) {
-        const GroupMeta& G = M.grp[l][g];
-        if (pass) HP_CUDA(cudaMemcpy(w.p + w.n, group_src(h, l, g), G.stored_len,
-                                     cudaMemcpyDeviceToHost));
-        w.n += G.stored_len;
-        w.pad(16);
-      }
-    if (!pass) {
-      if (!buf) {
-        *len = w.n;
-        return HPMDR_OK;
-      }
-      if (*len < w.n) return HPMDR_ERR_ARG;
-    } else {
-      *len = w.n;
-    }
+  std::vector<std::pair<uint64_t, uint64_t>> pos;
+  const uint64_t n = export_layout(h, nullptr, &pos);
+  if (!buf) {
+    *len = n;
+    return HPMDR_OK;
   }
+  if (*len < n) return HPMDR_ERR_ARG;
+  export_layout(h, (uint8_t*)buf, nullptr);
+  size_t k = 0;
+  for (int l = 0; l < h->nlev; l++)
+    for (int g = 0; g < h->ngroups; g++, k++) {
+      uint8_t* dst = (uint8_t*)buf + pos[k].first;
+      HP_CUDA(cudaMemcpy(dst, group_src(h, l, g), pos[k].second, cudaMemcpyDeviceToHost));
+    }
+  *len = n;
   return HPMDR_OK;
 }
 
-extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uint64_t len,
-                                            hpmdr_handle** out) {
-  if (!ctx || !buf || !out) return HPMDR_ERR_ARG;
-  *out = nullptr;
+// A handle from an export stream: header parsed on the host, device buffers
+// allocated and the stored groups and metadata copied on stream s (not waited
+// for: buf must stay valid until s passes the copies).
+static hpmdr_status import_enqueue(hpmdr_ctx* ctx, const void* buf, uint64_t len,
+                                   const std::shared_ptr<const Plan>* plan, cudaStream_t s,
+                                   std::unique_ptr<hpmdr_handle>& out) {
   Reader r{(const uint8_t*)buf, len};
   char magic[8];
   r.get(magic, 8);
@@ -1516,8 +1555,11 @@ extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uin
   for (int d = 0; d < 3; d++) dims[d] = r.val<uint64_t>();
   if (!r.ok || check_dims(3, dims, dims, &N) != HPMDR_OK) return HPMDR_ERR_CORRUPT;
   std::unique_ptr<hpmdr_handle> H;
-  HP_TRY(new_handle(ctx, 3, dims, dtype, nullptr, H));
-  const cudaStream_t s = ctx->stream;
+  if (plan && *plan) {
+    const uint64_t* pd = (*plan)->dims;
+    if (pd[0] != dims[0] || pd[1] != dims[1] || pd[2] != dims[2] || (*plan)->B != B) plan = nullptr;
+  }
+  HP_TRY(new_handle(ctx, 3, dims, dtype, plan, H));
   if (H->nlev != nlev || nlev > HP_MAX_LEVELS) return HPMDR_ERR_CORRUPT;
   FieldMeta& M = *H->meta;
   M.E_f = E_f;
@@ -1568,20 +1610,294 @@ extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uin
   HP_TRY(H->A.alloc((void**)&H->d_planes, H->plane_bytes, s));
   HP_TRY(H->A.alloc((void**)&H->d_slots, H->slot_bytes, s));
   HP_TRY(H->A.alloc((void**)&H->d_meta, sizeof(FieldMeta), s));
+  CopyRuns runs;
   for (int l = 0; l < nlev; l++)
     for (int g = 0; g < H->ngroups; g++) {
       const GroupMeta& G = M.grp[l][g];
       if (r.n + G.stored_len > len) return HPMDR_ERR_CORRUPT;
       uint8_t* dst = G.method == HPMDR_DC ? H->d_planes + G.plane_off : H->d_slots + G.slot_off;
-      HP_CUDA(cudaMemcpyAsync(dst, r.p + r.n, G.stored_len, cudaMemcpyHostToDevice, s));
+      if (G.stored_len) runs.add(dst, r.p + r.n, G.stored_len);
       r.n += G.stored_len;
       r.pad(16);
     }
+  HP_TRY(runs.issue(cudaMemcpyHostToDevice, s));
   HP_CUDA(cudaMemcpyAsync(H->d_meta, H->meta.get(), sizeof(FieldMeta), cudaMemcpyHostToDevice, s));
-  HP_CUDA(cudaStreamSynchronize(s));
   count_items(H.get());
+  out = std::move(H);
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_handle_import(hpmdr_ctx* ctx, const void* buf, uint64_t len,
+                                            hpmdr_handle** out) {
+  if (!ctx || !buf || !out) return HPMDR_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<hpmdr_handle> H;
+  HP_TRY(import_enqueue(ctx, buf, len, nullptr, ctx->stream, H));
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
   *out = H.release();
   return HPMDR_OK;
+}
+
+// ------------------------------------------- out-of-core pipeline (Sec. 5.3)
+// Units u = v * nchunks + c ((variable, chunk) pairs) pass through three
+// queues, one CUDA stream each: host -> device copies (q1), kernels (q2) and
+// device -> host copies (q3).  Two device input/output buffers alternate, so
+// unit u + 1's copy in and unit u - 1's copy out overlap unit u's kernels; the
+// host reads a unit's metadata (to lay out its stream) while the GPU works on
+// the next one.
+struct UnitEvents {
+  std::vector<cudaEvent_t> ev;
+  ~UnitEvents() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  hpmdr_status make(size_t n) {
+    ev.assign(n, nullptr);
+    for (auto& e : ev) HP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return HPMDR_OK;
+  }
+};
+
+static hpmdr_status pipeline_units(ChunkGrid& G, int nvars, int ndims, const uint64_t dims[3],
+                                   const uint64_t chunk[3], uint64_t* U) {
+  if (nvars < 1 || nvars > 4096) return HPMDR_ERR_ARG;
+  HP_TRY(chunk_grid(ndims, dims, chunk, &G));
+  *U = (uint64_t)nvars * G.n;
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_refactor_pipeline(hpmdr_ctx* ctx, int nvars,
+                                                const void* const* fields, int ndims,
+                                                const uint64_t dims[3], const uint64_t chunk[3],
+                                                hpmdr_dtype dtype, int queues, void* out,
+                                                uint64_t* total, uint64_t* offsets,
+                                                uint64_t* sizes) {
+  if (!ctx || !total || (dtype != HPMDR_F32 && dtype != HPMDR_F64) || (queues != 1 && queues != 3))
+    return HPMDR_ERR_ARG;
+  ChunkGrid G;
+  uint64_t U = 0;
+  HP_TRY(pipeline_units(G, nvars, ndims, dims, chunk, &U));
+  const size_t esz = dtype == HPMDR_F32 ? 4 : 8;
+  // stream bound: per unit, the largest stream of its chunk shape
+  std::vector<uint64_t> bound(G.n);
+  {
+    std::shared_ptr<const Plan> full;
+    for (uint64_t c = 0; c < G.n; c++) {
+      uint64_t org[3], ext[3];
+      G.box(c, org, ext);
+      std::unique_ptr<hpmdr_handle> H;
+      HP_TRY(new_handle(ctx, 3, ext, dtype, nullptr, H));
+      bound[c] = round16(export_bound(*H->plan));
+    }
+  }
+  uint64_t need = 0;
+  for (uint64_t u = 0; u < U; u++) need += bound[u % G.n];
+  if (!out) {
+    *total = need;
+    return HPMDR_OK;
+  }
+  if (!fields || !offsets || !sizes || *total < need || ((uintptr_t)out & 15)) return HPMDR_ERR_ARG;
+  for (int v = 0; v < nvars; v++)
+    if (!fields[v]) return HPMDR_ERR_ARG;
+  std::vector<cudaStream_t> q;
+  HP_TRY(pipeline_streams(ctx, queues, q));
+  if (queues == 1) q.assign(3, q[0]);  // one queue: nothing overlaps (the baseline)
+  const size_t in_bytes = G.chunk[0] * G.chunk[1] * G.chunk[2] * esz;
+  void* in[2] = {nullptr, nullptr};
+  FieldMeta* pm = nullptr;  // page-locked metadata copies, one per unit in flight
+  UnitEvents eH, eC, eD;
+  hpmdr_status st = eH.make(U);
+  if (st == HPMDR_OK) st = eC.make(U);
+  if (st == HPMDR_OK) st = eD.make(U);
+  for (int i = 0; i < 2 && st == HPMDR_OK; i++) st = ctx->A.alloc(&in[i], in_bytes, q[1]);
+  if (st == HPMDR_OK && cudaHostAlloc((void**)&pm, 3 * sizeof(FieldMeta), cudaHostAllocDefault) !=
+                            cudaSuccess) {
+    pm = nullptr;
+    st = HPMDR_ERR_NOMEM;
+  }
+  std::vector<std::unique_ptr<hpmdr_handle>> hs(U);
+  std::vector<RefactorProf> rps(U);
+  std::shared_ptr<const Plan> full_plan;
+  uint64_t at = 0;  // next free byte of out
+  // unit w's metadata is on the host: lay out its stream, copy its groups out
+  auto finish = [&](uint64_t w) -> hpmdr_status {
+    HP_CUDA(cudaEventSynchronize(eC.ev[w]));
+    hpmdr_handle* H = hs[w].get();
+    memcpy(H->meta.get(), &pm[w % 3], sizeof(FieldMeta));
+    count_items(H);
+    if (H->meta->status) return (hpmdr_status)H->meta->status;
+    std::vector<std::pair<uint64_t, uint64_t>> pos;
+    uint8_t* dst = (uint8_t*)out + at;
+    const uint64_t n = export_layout(H, dst, &pos);
+    HP_CUDA(cudaStreamWaitEvent(q[2], eC.ev[w], 0));
+    CopyRuns runs;
+    size_t k = 0;
+    for (int l = 0; l < H->nlev; l++)
+      for (int g = 0; g < H->ngroups; g++, k++)
+        if (pos[k].second) runs.add(dst + pos[k].first, group_src(H, l, g), pos[k].second);
+    HP_TRY(runs.issue(cudaMemcpyDeviceToHost, q[2]));
+    HP_CUDA(cudaEventRecord(eD.ev[w], q[2]));
+    offsets[w] = at;
+    sizes[w] = n;
+    at += round16(n);
+    H->stream = q[2];  // its buffers are released after its copies out
+    hs[w].reset();
+    return HPMDR_OK;
+  };
+  for (uint64_t u = 0; u < U && st == HPMDR_OK; u++) {
+    const int v = (int)(u / G.n);
+    const uint64_t c = u % G.n;
+    uint64_t org[3], ext[3];
+    G.box(c, org, ext);
+    void* buf = in[u % 2];
+    // q1: the input buffer is free once unit u - 2's kernels are done
+    if (u >= 2 && (st = cudaStreamWaitEvent(q[0], eC.ev[u - 2], 0) ? HPMDR_ERR_CUDA : HPMDR_OK))
+      break;
+    if ((st = copy_box(buf, fields[v], G, org, ext, esz, true, cudaMemcpyHostToDevice, q[0])))
+      break;
+    if (cudaEventRecord(eH.ev[u], q[0]) != cudaSuccess) { st = HPMDR_ERR_CUDA; break; }
+    // q2: the kernels, then the metadata to the host
+    const bool fullc = ext[0] == G.chunk[0] && ext[1] == G.chunk[1] && ext[2] == G.chunk[2];
+    if ((st = new_handle(ctx, 3, ext, dtype, fullc && full_plan ? &full_plan : nullptr, hs[u])))
+      break;
+    if (fullc && !full_plan) full_plan = hs[u]->plan;
+    if (cudaStreamWaitEvent(q[1], eH.ev[u], 0) != cudaSuccess) { st = HPMDR_ERR_CUDA; break; }
+    if ((st = refactor_enqueue(ctx, hs[u].get(), buf, q[1], &rps[u]))) break;
+    if (cudaMemcpyAsync(&pm[u % 3], hs[u]->d_meta, sizeof(FieldMeta), cudaMemcpyDeviceToHost,
+                        q[1]) != cudaSuccess ||
+        cudaEventRecord(eC.ev[u], q[1]) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    // host: unit u - 1 (its kernels overlap unit u's copy in)
+    if (u >= 1) st = finish(u - 1);
+  }
+  if (st == HPMDR_OK && U >= 1) st = finish(U - 1);
+  hpmdr_status js = join_streams(q);
+  hs.clear();
+  for (int i = 0; i < 2; i++) ctx->A.release(in[i], q[1]);
+  join_streams(q);
+  if (pm) cudaFreeHost(pm);
+  if (st != HPMDR_OK) return st;
+  *total = at;
+  return js;
+}
+
+extern "C" hpmdr_status hpmdr_retrieve_pipeline(hpmdr_ctx* ctx, int nvars, const void* streams,
+                                                const uint64_t* offsets, const uint64_t* sizes,
+                                                int ndims, const uint64_t dims[3],
+                                                const uint64_t chunk[3], const double* rel_bounds,
+                                                int queues, void* const* outs,
+                                                hpmdr_retrieve_info* infos) {
+  if (!ctx || !streams || !offsets || !sizes || !rel_bounds || !outs || (queues != 1 && queues != 3))
+    return HPMDR_ERR_ARG;
+  ChunkGrid G;
+  uint64_t U = 0;
+  HP_TRY(pipeline_units(G, nvars, ndims, dims, chunk, &U));
+  for (int v = 0; v < nvars; v++)
+    if (!outs[v] || !(rel_bounds[v] >= 0.0)) return HPMDR_ERR_ARG;
+  const uint8_t* base = (const uint8_t*)streams;
+  // the global range of each variable, from the streams' headers (Sec. 5.3's
+  // sub-domains meet the bound relative to the whole variable)
+  std::vector<double> lo(nvars, 0.0), hi(nvars, 0.0);
+  int dtype = -1;
+  for (uint64_t u = 0; u < U; u++) {
+    Reader r{base + offsets[u], sizes[u]};
+    char magic[8];
+    r.get(magic, 8);
+    r.val<uint32_t>();
+    r.val<uint32_t>();
+    const int32_t dt = r.val<int32_t>();
+    for (int k = 0; k < 5; k++) r.val<int32_t>();
+    for (int d = 0; d < 3; d++) r.val<uint64_t>();
+    r.val<double>();
+    const double vmin = r.val<double>(), vmax = r.val<double>();
+    if (!r.ok || memcmp(magic, "HPMDR1\0\0", 8) != 0 || (dtype >= 0 && dt != dtype))
+      return HPMDR_ERR_CORRUPT;
+    dtype = dt;
+    const int v = (int)(u / G.n);
+    if (u % G.n == 0 || vmin < lo[v]) lo[v] = vmin;
+    if (u % G.n == 0 || vmax > hi[v]) hi[v] = vmax;
+  }
+  const size_t esz = dtype == 0 ? 4 : 8;
+  std::vector<cudaStream_t> q;
+  HP_TRY(pipeline_streams(ctx, queues, q));
+  if (queues == 1) q.assign(3, q[0]);  // one queue: nothing overlaps (the baseline)
+  const size_t box_bytes = G.chunk[0] * G.chunk[1] * G.chunk[2] * esz;
+  void* ob[2] = {nullptr, nullptr};
+  RetrieveDev* prd = nullptr;  // page-locked selection records, one per unit
+  UnitEvents eH, eC, eD;
+  hpmdr_status st = eH.make(U);
+  if (st == HPMDR_OK) st = eC.make(U);
+  if (st == HPMDR_OK) st = eD.make(U);
+  for (int i = 0; i < 2 && st == HPMDR_OK; i++) st = ctx->A.alloc(&ob[i], box_bytes, q[1]);
+  if (st == HPMDR_OK &&
+      cudaHostAlloc((void**)&prd, U * sizeof(RetrieveDev), cudaHostAllocDefault) != cudaSuccess) {
+    prd = nullptr;
+    st = HPMDR_ERR_NOMEM;
+  }
+  std::vector<std::unique_ptr<hpmdr_handle>> hs(U);
+  std::shared_ptr<const Plan> full_plan;
+  for (uint64_t u = 0; u < U && st == HPMDR_OK; u++) {
+    const int v = (int)(u / G.n);
+    const uint64_t c = u % G.n;
+    uint64_t org[3], ext[3];
+    G.box(c, org, ext);
+    // q1: unit u's stream in (at most two units' handles on the device)
+    if (u >= 2 && cudaStreamWaitEvent(q[0], eC.ev[u - 2], 0) != cudaSuccess) { st = HPMDR_ERR_CUDA; break; }
+    if ((st = import_enqueue(ctx, base + offsets[u], sizes[u], full_plan ? &full_plan : nullptr,
+                             q[0], hs[u])))
+      break;
+    const bool fullc = ext[0] == G.chunk[0] && ext[1] == G.chunk[1] && ext[2] == G.chunk[2];
+    for (int d = 0; d < 3; d++)
+      if (hs[u]->dims[d] != ext[d]) st = HPMDR_ERR_CORRUPT;
+    if (st != HPMDR_OK) break;
+    if (fullc && !full_plan) full_plan = hs[u]->plan;
+    if (cudaEventRecord(eH.ev[u], q[0]) != cudaSuccess) { st = HPMDR_ERR_CUDA; break; }
+    // q2: select, decode, recompose into the free output buffer
+    if (cudaStreamWaitEvent(q[1], eH.ev[u], 0) != cudaSuccess ||
+        (u >= 2 && cudaStreamWaitEvent(q[1], eD.ev[u - 2], 0) != cudaSuccess)) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    hpmdr_handle* H = hs[u].get();
+    if ((st = enqueue_retrieve(ctx, H, rel_bounds[v] * (hi[v] - lo[v]), 1, ob[u % 2], q[1])))
+      break;
+    if (cudaMemcpyAsync(&prd[u], H->d_rd, sizeof(RetrieveDev), cudaMemcpyDeviceToHost, q[1]) !=
+            cudaSuccess ||
+        cudaEventRecord(eC.ev[u], q[1]) != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    // q3: the box out
+    if (cudaStreamWaitEvent(q[2], eC.ev[u], 0) != cudaSuccess) { st = HPMDR_ERR_CUDA; break; }
+    if ((st = copy_box(outs[v], ob[u % 2], G, org, ext, esz, false, cudaMemcpyDeviceToHost, q[2])))
+      break;
+    if (cudaEventRecord(eD.ev[u], q[2]) != cudaSuccess) { st = HPMDR_ERR_CUDA; break; }
+    H->stream = q[1];
+    // unit u's device buffers go back to the pool once its kernels are done
+    // (the host object stays for the infos)
+    for (void** pp : {(void**)&H->d_planes, (void**)&H->d_slots, (void**)&H->d_meta,
+                      (void**)&H->d_rd, (void**)&H->d_xa, (void**)&H->d_xb, (void**)&H->d_xroot}) {
+      H->A.release(*pp, q[1]);
+      *pp = nullptr;
+    }
+  }
+  hpmdr_status js = join_streams(q);
+  hpmdr_status worst = HPMDR_OK;
+  if (st == HPMDR_OK && js == HPMDR_OK) {
+    for (uint64_t u = 0; u < U; u++) {
+      hpmdr_status r = (hpmdr_status)prd[u].status;
+      fill_info(hs[u].get(), prd[u], infos ? &infos[u] : nullptr);
+      if (r != HPMDR_OK && worst == HPMDR_OK) worst = r;
+    }
+  }
+  hs.clear();
+  for (int i = 0; i < 2; i++) ctx->A.release(ob[i], q[1]);
+  join_streams(q);
+  if (prd) cudaFreeHost(prd);
+  if (st != HPMDR_OK) return st;
+  if (js != HPMDR_OK) return js;
+  return worst;
 }
 
 __global__ void k_reset(FieldMeta* m) {
