@@ -177,11 +177,152 @@ __device__ __forceinline__ void cells_levelmax_flush(FieldMeta* meta, int level,
   }
 }
 
+// ----------------------------------------------- level max by estimate
+// The exact pass above spends most of its instructions on 64-bit fixed-point
+// arithmetic, but only bl = bitlen(max |C8|) is needed.  A pass in FP32 gives
+// every node's detail d = f - mean(corners) to within (k + 1) 2^(E_f - 24)
+// < 2^(E_f - 20) (k <= 8 corners summed in k - 1 roundings of partial sums
+// below k 2^E_f, one rounding of the difference), i.e. C8 = 8 d / U to within
+// 2^31 plus 16 for the floors of the fixed point.  So max |C8| lies within
+// 2^32 of 8 max|d~| / U; when that interval (widened to 2^33 for the FP64
+// evaluation below) has one bit length, that is bl.  Otherwise (a maximum
+// within about 2^-10 of a power of two at the usual magnitudes, a near-zero
+// level, a tiny field) the exact pass runs for the level.  The floor flag of
+// the level's own nodes is exact in both passes.
+__device__ __forceinline__ uint32_t float_floors(float v, int E_f) {
+  const uint32_t u = __float_as_uint(v), e = (u >> 23) & 0xffu;
+  uint32_t m = u & 0x7fffffu;
+  if (e) m |= 0x800000u;
+  const int r = 102 + E_f - (int)(e ? e : 1u);  // bits of m below the unit
+  if (r <= 0 || m == 0) return 0u;
+  return r >= 32 ? 1u : ((m & ((1u << r) - 1u)) != 0u);
+}
+
+__device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict__ f,
+                                                        const CellGeom& G, uint32_t ny,
+                                                        uint32_t nx, int hl, int E_f, uint32_t tile,
+                                                        float& mx, uint32_t& fl) {
+  const uint32_t i = threadIdx.x, per_row = G.XW / 4;
+  uint32_t cz, cy0, x0;
+  tile_origin(G, tile, cz, cy0, x0);
+  const uint32_t cy = cy0 + i / per_row, cx = x0 + 4 * (i % per_row);
+  if (cy >= G.c[1]) return;
+  const uint32_t Z0 = 2 * cz, Y0 = 2 * cy, X0 = 2 * cx;
+  const bool hz = Z0 + 1 < G.g[0], hy = Y0 + 1 < G.g[1];
+  const uint32_t Z2 = Z0 + 2 < G.g[0] ? Z0 + 2 : Z0, Y2 = Y0 + 2 < G.g[1] ? Y0 + 2 : Y0;
+  const uint32_t Xe = X0 + 8 < G.g[2] ? X0 + 8 : X0 + 6;
+  auto seg = [&](uint32_t z, uint32_t y, float v[8], bool odd) {
+    const float* r = f + ((size_t)(z << hl) * ny + (y << hl)) * nx;
+    if (hl == 0) {
+      const float4 p = __ldg(reinterpret_cast<const float4*>(r + X0));
+      const float4 q = __ldg(reinterpret_cast<const float4*>(r + X0) + 1);
+      v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+      v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        if (!(k & 1) || odd) v[k] = __ldg(r + ((size_t)(X0 + k) << hl));
+    }
+  };
+  auto coarse = [&](uint32_t z, uint32_t y, float c[5], float v[8], bool odd) {
+    seg(z, y, v, odd);
+#pragma unroll
+    for (int k = 0; k < 4; k++) c[k] = v[2 * k];
+    c[4] = __ldg(f + ((size_t)(z << hl) * ny + (y << hl)) * nx + ((size_t)Xe << hl));
+  };
+  auto take = [&](float node, float mean) {
+    mx = fmaxf(mx, fabsf(__fsub_rn(node, mean)));
+    fl |= float_floors(node, E_f);
+  };
+  float v[8], c0[5], a[5];
+  coarse(Z0, Y0, c0, v, true);
+#pragma unroll
+  for (int k = 0; k < 4; k++) take(v[2 * k + 1], __fmul_rn(__fadd_rn(c0[k], c0[k + 1]), 0.5f));
+  if (hy) {
+    coarse(Z0, Y2, a, v, false);
+#pragma unroll
+    for (int k = 0; k < 5; k++) a[k] = __fadd_rn(a[k], c0[k]);
+    seg(Z0, Y0 + 1, v, true);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      take(v[2 * k], __fmul_rn(a[k], 0.5f));
+      take(v[2 * k + 1], __fmul_rn(__fadd_rn(a[k], a[k + 1]), 0.25f));
+    }
+  }
+  if (hz) {
+    float c1[5];
+    coarse(Z2, Y0, c1, v, false);
+#pragma unroll
+    for (int k = 0; k < 5; k++) c0[k] = __fadd_rn(c0[k], c1[k]);
+    seg(Z0 + 1, Y0, v, true);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      take(v[2 * k], __fmul_rn(c0[k], 0.5f));
+      take(v[2 * k + 1], __fmul_rn(__fadd_rn(c0[k], c0[k + 1]), 0.25f));
+    }
+    if (hy) {
+      float c3[5];
+      coarse(Z2, Y2, c3, v, false);
+#pragma unroll
+      for (int k = 0; k < 5; k++) a[k] = __fadd_rn(a[k], __fadd_rn(c1[k], c3[k]));
+      seg(Z0 + 1, Y0 + 1, v, true);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        take(v[2 * k], __fmul_rn(a[k], 0.25f));
+        take(v[2 * k + 1], __fmul_rn(__fadd_rn(a[k], a[k + 1]), 0.125f));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_cells_levelmax_est(const float* __restrict__ f,
+                                                            uint32_t ny, uint32_t nx,
+                                                            const LevelDesc* __restrict__ Lp,
+                                                            FieldMeta* meta) {
+  if (meta->status) return;
+  const LevelDesc& L = *Lp;
+  const CellGeom G = cell_geom(L);
+  const int E_f = meta->E_f, hl = L.hlog;
+  float mx = 0.0f;
+  uint32_t fl = 0;
+  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
+    cells_levelmax_est_tile(f, G, ny, nx, hl, E_f, tile, mx, fl);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(HP_FULL, mx, o));
+  const unsigned anyfl = __any_sync(HP_FULL, fl != 0);
+  if ((threadIdx.x & 31) == 0) {
+    if (mx > 0.0f) atomicMax(&meta->m8est[L.level], __float_as_uint(mx));  // order of >= 0 floats
+    if (anyfl) atomicOr(&meta->floored, 1u);
+  }
+}
+
+// bl from the estimate when it is unambiguous (then m8 = 2^(bl-1)); false:
+// the exact pass must run
+__device__ __forceinline__ bool cells_bl_from_estimate(FieldMeta* meta, int level, bool write) {
+  const int E_f = meta->E_f;
+  const uint32_t bits = meta->m8est[level];
+  if (E_f < -90 || bits == 0u) return false;
+  const double M = (double)__uint_as_float(bits) * __longlong_as_double((long long)(51 - E_f + 1023) << 52);
+  const double lo = M - 0x1p33, hi = M + 0x1p33;
+  if (!(lo >= 1.0)) return false;
+  int el, eh;
+  frexp(lo, &el);
+  frexp(hi, &eh);
+  if (el != eh) return false;  // the interval holds a power of two
+  if (write) meta->m8[level] = 1ull << (el - 1);  // bitlen el
+  return true;
+}
+
 __global__ void __launch_bounds__(256, 4) k_cells_levelmax(const float* __restrict__ f, uint32_t ny,
                                                         uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                         FieldMeta* meta) {
   if (meta->status) return;
   const LevelDesc& L = *Lp;
+  // the estimate pass settled bl: one thread records it, nothing else to do
+  if (cells_bl_from_estimate(meta, L.level, false)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cells_bl_from_estimate(meta, L.level, true);
+    return;
+  }
   const CellGeom G = cell_geom(L);
   const int E_f = meta->E_f, hl = L.hlog;
   uint64_t mx = 0;
@@ -306,6 +447,8 @@ void launch_cells_levelmax(const float* f, const uint64_t dims[3], const LevelDe
   uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 4;
   if (blocks > cap) blocks = cap;
   if (!blocks) return;
+  hp::note_launch(), k_cells_levelmax_est<<<blocks, 256, 0, s>>>(f, (uint32_t)dims[1],
+                                                              (uint32_t)dims[2], Ld, meta);
   hp::note_launch(), k_cells_levelmax<<<blocks, 256, 0, s>>>(f, (uint32_t)dims[1], (uint32_t)dims[2],
                                                           Ld, meta);
 }

@@ -69,6 +69,7 @@ struct alignas(16) FieldMeta {
   uint32_t pad0;
   uint64_t m8[HP_MAX_LEVELS];             // max |C8| per level
   uint64_t lowbits[HP_MAX_LEVELS];        // OR of the bits dropped by alignment
+  uint32_t m8est[HP_MAX_LEVELS];          // FP32 bits of max |detail| from the estimate pass
   int32_t bl[HP_MAX_LEVELS], exact[HP_MAX_LEVELS];
   GroupMeta grp[HP_MAX_LEVELS][HP_MAX_GROUPS];
   // greedy sequence and the estimate after each prefix (128-bit units)

@@ -20,6 +20,7 @@ __global__ void k_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngr
   for (int l = 0; l < HP_MAX_LEVELS; l++) {
     meta->m8[l] = 0;
     meta->lowbits[l] = 0;
+    meta->m8est[l] = 0;
     meta->bl[l] = 0;
     meta->exact[l] = 1;
     meta->fetched[l] = 0;

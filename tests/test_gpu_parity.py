@@ -30,6 +30,14 @@ def ctx(B):
     return B.Context()
 
 
+def _spike(shape, at, value, extra=None):
+    f = np.zeros(shape, dtype=np.float32)
+    f[at] = np.float32(value)
+    if extra is not None:
+        f[extra[0]] = np.float32(extra[1])
+    return f
+
+
 def _fields():
     from paper_2505_00227_gb300 import synthetic as S
     rng = np.random.default_rng(11)
@@ -51,6 +59,15 @@ def _fields():
         "cells_2d": S.blobs((1, 64, 128), seed=13).numpy(),
         "cells_three_words": S.spectral((5, 9, 192), seed=14).numpy(),
         "cells_256": S.spectral((24, 40, 256), seed=15).numpy(),
+        # a level maximum exactly at a power of two (C8 = 2^50): the FP32 estimate of
+        # the level maximum is ambiguous there and the exact pass must decide
+        "cells_power_of_two": _spike((8, 8, 128), (3, 5, 77), 2.0 ** -10),
+        # all-zero finest level apart from one value below the fixed-point unit
+        "cells_floored": _spike((8, 8, 128), (2, 2, 6), 1.0, extra=((4, 4, 9), 1e-30)),
+        # values far below max|f|: the estimate's bound scales with max|f|
+        "cells_wide_range": (S.spectral((8, 16, 128), seed=24).numpy() *
+                             np.float32(1e-6)).astype(np.float32) +
+                            _spike((8, 16, 128), (0, 0, 0), 3.0),
         # large levels of any size take the general cell kernels (staged transposes)
         "gcells_odd": S.spectral((45, 47, 49), seed=16).numpy(),
         "gcells_f64": S.blobs((40, 36, 44), seed=17, dtype=torch.float64).numpy(),
