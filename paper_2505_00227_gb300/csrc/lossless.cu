@@ -968,7 +968,8 @@ __device__ __forceinline__ bool huff_emit(const HuffTables& T, BitReader& rd, ui
 
 __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const GroupMeta* gm,
                                   uint32_t cl, uint32_t len, uint8_t* __restrict__ dst,
-                                  HuffTables& T, uint32_t* scratch, FieldMeta* meta) {
+                                  HuffTables& T, uint32_t* scratch, FieldMeta* meta,
+                                  bool tables_ready) {
   const int tid = threadIdx.x, lane = tid & 31, NT = blockDim.x;
   const uint32_t nc = gm->nchunks;
   const uint64_t hdr = 272 + 4ull * (nc + 1);
@@ -983,83 +984,93 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
   const uint32_t* offs = reinterpret_cast<const uint32_t*>(stored + 272);
   const uint32_t w0 = offs[cl], w1 = offs[cl + 1];
   const uint64_t words = (gm->stored_len - hdr) / 4;
-  // ---- 1. decoding tables (warp 0), the gcd of the code lengths
-  __shared__ uint32_t s_flag, s_gl;
-  if (tid < 32) {
-    uint32_t myL[8];
-    bool bad = w0 > w1 || w1 > words;
-    uint32_t gl = 0;
-#pragma unroll
-    for (int r = 0; r < 8; r++) {
-      myL[r] = lens[32 * r + lane];
-      bad |= myL[r] > 16;
-      uint32_t x = gl, y = myL[r];
-      while (y) {
-        const uint32_t t = x % y;
-        x = y;
-        y = t;
-      }
-      gl = x;
-    }
-#pragma unroll
-    for (int dd = 16; dd; dd >>= 1) {
-      uint32_t x = gl, y = __shfl_xor_sync(HP_FULL, gl, dd);
-      while (y) {
-        const uint32_t t = x % y;
-        x = y;
-        y = t;
-      }
-      gl = x;
-    }
-    bad = __any_sync(HP_FULL, bad);
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int r = 0; r < 8; r++)
-      for (int L = 1; L <= 16; L++) {
-        const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
-        if (lane == L) cnt += __popc(m);
-      }
-    if (lane <= 16) T.count[lane] = lane ? cnt : 0;
-    __syncwarp();
-    if (lane == 0) {
-      uint32_t c = 0, idx = 0;
-      for (int L = 1; L <= 16; L++) {
-        T.first[L] = c;
-        T.index[L] = idx;
-        T.fill[L] = idx;
-        idx += T.count[L];
-        c = (c + T.count[L]) << 1;
-      }
-      s_flag = bad ? 1u : 0u;
-      s_gl = gl ? gl : 1u;
-    }
-    __syncwarp();
-    const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int r = 0; r < 8; r++) {
-      for (int L = 1; L <= 16; L++) {
-        const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
-        if (myL[r] == (uint32_t)L) T.sorted[T.fill[L] + __popc(m & lt)] = (uint8_t)(32 * r + lane);
-        __syncwarp();
-        if (lane == 0) T.fill[L] += __popc(m);
-        __syncwarp();
-      }
-    }
-  }
-  for (int i = tid; i < (1 << HP_LUT_BITS); i += NT) T.lut[i] = 0;
-  __syncthreads();
-  if (s_flag) {
+  if (w0 > w1 || w1 > words) {  // same outcome in every thread
     if (tid == 0) set_corrupt(meta);
     return;
   }
-  for (int L = 1; L <= HP_LUT_BITS; L++) {
-    const uint32_t n = T.count[L];
-    for (uint32_t k = tid; k < n; k += NT) {
-      const uint32_t code = T.first[L] + k, sym = T.sorted[T.index[L] + k];
-      const uint32_t span = 1u << (HP_LUT_BITS - L), base = code << (HP_LUT_BITS - L);
-      if (base + span <= (1u << HP_LUT_BITS))  // a code set breaking Kraft is caught below
-        for (uint32_t r = 0; r < span; r++) T.lut[base + r] = (uint16_t)((L << 8) | sym);
+  // ---- 1. decoding tables (warp 0), the gcd of the code lengths; kept from
+  // the previous chunk when that one belonged to the same group
+  __shared__ uint32_t s_flag, s_gl;
+  if (!tables_ready) {
+    if (tid < 32) {
+      uint32_t myL[8];
+      bool bad = false;
+      uint32_t gl = 0;
+#pragma unroll
+      for (int r = 0; r < 8; r++) {
+        myL[r] = lens[32 * r + lane];
+        bad |= myL[r] > 16;
+        uint32_t x = gl, y = myL[r];
+        while (y) {
+          const uint32_t t = x % y;
+          x = y;
+          y = t;
+        }
+        gl = x;
+      }
+#pragma unroll
+      for (int dd = 16; dd; dd >>= 1) {
+        uint32_t x = gl, y = __shfl_xor_sync(HP_FULL, gl, dd);
+        while (y) {
+          const uint32_t t = x % y;
+          x = y;
+          y = t;
+        }
+        gl = x;
+      }
+      bad = __any_sync(HP_FULL, bad);
+      uint32_t cnt = 0;
+#pragma unroll
+      for (int r = 0; r < 8; r++)
+        for (int L = 1; L <= 16; L++) {
+          const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
+          if (lane == L) cnt += __popc(m);
+        }
+      if (lane <= 16) T.count[lane] = lane ? cnt : 0;
+      __syncwarp();
+      if (lane == 0) {
+        uint32_t c = 0, idx = 0;
+        for (int L = 1; L <= 16; L++) {
+          T.first[L] = c;
+          T.index[L] = idx;
+          T.fill[L] = idx;
+          idx += T.count[L];
+          c = (c + T.count[L]) << 1;
+        }
+        s_flag = bad ? 1u : 0u;
+        s_gl = gl ? gl : 1u;
+      }
+      __syncwarp();
+      const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+      for (int r = 0; r < 8; r++) {
+        for (int L = 1; L <= 16; L++) {
+          const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
+          if (myL[r] == (uint32_t)L) T.sorted[T.fill[L] + __popc(m & lt)] = (uint8_t)(32 * r + lane);
+          __syncwarp();
+          if (lane == 0) T.fill[L] += __popc(m);
+          __syncwarp();
+        }
+      }
     }
+    for (int i = tid; i < (1 << HP_LUT_BITS); i += NT) T.lut[i] = 0;
+    __syncthreads();
+    if (s_flag) {
+      if (tid == 0) set_corrupt(meta);
+      return;
+    }
+    for (int L = 1; L <= HP_LUT_BITS; L++) {
+      const uint32_t n = T.count[L];
+      for (uint32_t k = tid; k < n; k += NT) {
+        const uint32_t code = T.first[L] + k, sym = T.sorted[T.index[L] + k];
+        const uint32_t span = 1u << (HP_LUT_BITS - L), base = code << (HP_LUT_BITS - L);
+        if (base + span <= (1u << HP_LUT_BITS))  // a code set breaking Kraft is caught below
+          for (uint32_t r = 0; r < span; r++) T.lut[base + r] = (uint16_t)((L << 8) | sym);
+      }
+    }
+  } else if (s_flag) {  // the group's tables were found corrupt
+    if (tid == 0) set_corrupt(meta);
+    return;
   }
   const uint32_t nbits = (w1 - w0) * 32, mw = (nbits + 31) / 32;
   for (uint32_t i = tid; i < mw && i < HP_MAP_WORDS; i += NT) T.map[i] = 0;
@@ -1329,7 +1340,8 @@ __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const Group
 __device__ __forceinline__ void decode_item(const uint8_t* __restrict__ slots, FieldMeta* meta,
                                             const RetrieveDev* __restrict__ rd,
                                             uint8_t* __restrict__ planes, uint32_t item,
-                                            HuffTables& T, uint32_t* scratch) {
+                                            HuffTables& T, uint32_t* scratch,
+                                            const GroupMeta** s_tab) {
   const uint32_t ngr = rd->n_new;
   const int ng = meta->ngroups;
   // newly fetched group holding this item: last k with new_pref[k] <= item
@@ -1347,7 +1359,10 @@ __device__ __forceinline__ void decode_item(const uint8_t* __restrict__ slots, F
   const uint8_t* stored = slots + gm->slot_off;
   uint8_t* dst = planes + gm->plane_off + start;
   if (gm->method == 1) {
-    huff_decode_chunk(stored, gm, cl, len, dst, T, scratch, meta);
+    const bool ready = *s_tab == gm;  // T holds this group's tables
+    __syncthreads();                  // every thread has read s_tab
+    huff_decode_chunk(stored, gm, cl, len, dst, T, scratch, meta, ready);
+    if (threadIdx.x == 0) *s_tab = gm;
   } else if (gm->method == 2) {
     if (threadIdx.x < 32) rle_decode_chunk(stored, gm, cl, len, dst, meta);
   } else {  // direct copy of a DC group held in the slots of a compact handle
@@ -1364,9 +1379,14 @@ __global__ void __launch_bounds__(HP_DEC_THREADS) k_decode(const uint8_t* __rest
   extern __shared__ __align__(16) unsigned char dec_smem[];
   HuffTables& T = *reinterpret_cast<HuffTables*>(dec_smem);
   __shared__ uint32_t scratch[HP_DEC_THREADS / 32];
-  const uint32_t total = rd->items;
-  for (uint32_t item = blockIdx.x; item < total; item += gridDim.x) {
-    decode_item(slots, meta, rd, planes, item, T, scratch);
+  __shared__ const GroupMeta* s_tab;
+  if (threadIdx.x == 0) s_tab = nullptr;
+  __syncthreads();
+  // consecutive chunks per CTA: a group's chunks mostly share its CTA's tables
+  const uint32_t total = rd->items, per = (total + gridDim.x - 1) / gridDim.x;
+  const uint32_t i0 = blockIdx.x * per, i1 = min(total, i0 + per);
+  for (uint32_t item = i0; item < i1; item++) {
+    decode_item(slots, meta, rd, planes, item, T, scratch, &s_tab);
     __syncthreads();
   }
 }
@@ -1485,11 +1505,14 @@ __global__ void __launch_bounds__(HP_DEC_THREADS) kb_decode(const BatchJob* __re
   extern __shared__ __align__(16) unsigned char dec_smem[];
   HuffTables& T = *reinterpret_cast<HuffTables*>(dec_smem);
   __shared__ uint32_t scratch[HP_DEC_THREADS / 32];
+  __shared__ const GroupMeta* s_tab;
+  if (threadIdx.x == 0) s_tab = nullptr;
+  __syncthreads();
   const uint32_t total = unit0[njobs];
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t j = unit_owner(unit0, njobs, u);
     const BatchJob& J = jobs[j];
-    decode_item(J.slots, J.meta, J.rd, J.planes, u - unit0[j], T, scratch);
+    decode_item(J.slots, J.meta, J.rd, J.planes, u - unit0[j], T, scratch, &s_tab);
     __syncthreads();
   }
 }

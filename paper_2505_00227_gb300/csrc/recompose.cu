@@ -203,16 +203,24 @@ __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict_
   uint32_t* s_sign = sm + (B == 64 ? 2 : 1) * WPB * 32 * 33;  // [WPB][32]
   if (m->status) return;
   const int L = nlev - 1, w = threadIdx.x >> 5, E_f = m->E_f;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {  // the root: lane p reads plane p, a ballot gathers q
+    const int lane = threadIdx.x;
     const LevelDesc& D = levels[0];
     const uint32_t* P = planes + D.plane_off / 4;
     const int k = 4 * m->cur[0];
     uint64_t q = 0;
-    for (int p = 0; p < k; p++) q |= (uint64_t)(P[(size_t)(1 + p) * D.W] & 1u) << (B - 1 - p);
-    const bool neg = k > 0 && (P[0] & 1u);
-    const int64_t X = dequant(q, neg, B, m->bl[0]) >> 3;
-    *xroot = X;
-    if (L == 0) *reinterpret_cast<T*>(out) = convert_out<T>(X, E_f);
+#pragma unroll
+    for (int r = 0; r < B / 32; r++) {
+      const int p = 32 * r + lane;  // plane p holds bit B - 1 - p
+      const bool b = p < k && (P[(size_t)(1 + p) * D.W] & 1u);
+      q |= (uint64_t)__brev(__ballot_sync(HP_FULL, b)) << (B - 32 - 32 * r);
+    }
+    if (lane == 0) {
+      const bool neg = k > 0 && (P[0] & 1u);
+      const int64_t X = dequant(q, neg, B, m->bl[0]) >> 3;
+      *xroot = X;
+      if (L == 0) *reinterpret_cast<T*>(out) = convert_out<T>(X, E_f);
+    }
   }
   __syncthreads();
   const int64_t* coarse = xroot;

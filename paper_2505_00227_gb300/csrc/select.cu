@@ -277,18 +277,40 @@ __device__ void select_prefix(FieldMeta* m, double tau, int tau_is_abs, Retrieve
   }
   bnew = warp_sum_u64(bnew);
   btot = warp_sum_u64(btot);
-  if (lane == 0) {
-    uint32_t n_new = 0, items = 0;
-    for (int l = 0; l < nlev; l++)
-      for (int q = m->fetched[l]; q < s_g[l]; q++) {
+  // the newly fetched groups to decode, in (level, group) order: lane = group
+  // of a run of 32 flat indices, ranks by ballot, chunk offsets by a warp scan
+  uint32_t n_new = 0, items = 0;
+  const int compact = m->compact;
+  for (int b0 = 0; b0 < nlev * ng; b0 += 32) {
+    const int i = b0 + lane;
+    bool take = false;
+    uint32_t nc = 0;
+    if (i < nlev * ng) {
+      const int l = i / ng, q = i % ng;
+      if (q >= m->fetched[l] && q < s_g[l]) {
         const GroupMeta& gm = m->grp[l][q];
-        if (gm.method != 0 || m->compact) {  // compact handles copy DC groups too
-          rd->new_gi[n_new] = (uint32_t)(l * ng + q);
-          rd->new_pref[n_new] = items;
-          items += gm.nchunks;
-          n_new++;
+        if (gm.method != 0 || compact) {  // compact handles copy DC groups too
+          take = true;
+          nc = gm.nchunks;
         }
       }
+    }
+    const unsigned bal = __ballot_sync(HP_FULL, take);
+    uint32_t incl = nc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(HP_FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (take) {
+      const uint32_t r = n_new + __popc(bal & ((1u << lane) - 1u));
+      rd->new_gi[r] = (uint32_t)i;
+      rd->new_pref[r] = items + incl - nc;
+    }
+    n_new += __popc(bal);
+    items += __shfl_sync(HP_FULL, incl, 31);
+  }
+  if (lane == 0) {
     rd->new_pref[n_new] = items;
     rd->n_new = n_new;
     rd->items = items;
