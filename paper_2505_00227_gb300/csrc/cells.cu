@@ -673,6 +673,35 @@ void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const
 uint32_t cell_tiles(const LevelDesc& L) { return cell_geom(L).ntiles; }
 
 // unit = one tile of 1024 cells of one (job, level) entry
+// the estimate pass over every (field, cell level) tile, as k_cells_levelmax_est
+__global__ void __launch_bounds__(256, 4) kb_cells_levelmax_est(const BatchJob* __restrict__ jobs,
+                                                             const LevelRef* __restrict__ refs,
+                                                             const uint32_t* __restrict__ unit0,
+                                                             uint32_t nrefs, uint32_t total) {
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const CellGeom G = cell_geom(L);
+    float mx = 0.0f;
+    uint32_t fl = 0;
+    cells_levelmax_est_tile(reinterpret_cast<const float*>(J.f), G, J.dims[1], J.dims[2], L.hlog,
+                            meta->E_f, u - unit0[e], mx, fl);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(HP_FULL, mx, o));
+    const unsigned anyfl = __any_sync(HP_FULL, fl != 0);
+    if ((threadIdx.x & 31) == 0) {
+      if (mx > 0.0f) atomicMax(&meta->m8est[L.level], __float_as_uint(mx));
+      if (anyfl) atomicOr(&meta->floored, 1u);
+    }
+  }
+}
+
+// the exact pass, per tile only where the estimate left bl open; the first
+// tile of a settled level records it
 __global__ void __launch_bounds__(256, 4) kb_cells_levelmax(const BatchJob* __restrict__ jobs,
                                                          const LevelRef* __restrict__ refs,
                                                          const uint32_t* __restrict__ unit0,
@@ -684,6 +713,10 @@ __global__ void __launch_bounds__(256, 4) kb_cells_levelmax(const BatchJob* __re
     FieldMeta* meta = J.meta;
     if (meta->status) continue;
     const LevelDesc& L = J.levels[R.level];
+    if (cells_bl_from_estimate(meta, L.level, false)) {
+      if (u == unit0[e] && threadIdx.x == 0) cells_bl_from_estimate(meta, L.level, true);
+      continue;
+    }
     const CellGeom G = cell_geom(L);
     uint64_t mx = 0;
     uint32_t fl = 0;
@@ -745,6 +778,7 @@ void launch_b_cells_levelmax(const BatchJob* jobs, const LevelRef* refs, const u
                              uint32_t nrefs, uint32_t total, uint32_t grid, cstream s) {
   if (!total) return;
   if (grid > total) grid = total;
+  hp::note_launch(), kb_cells_levelmax_est<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
   hp::note_launch(), kb_cells_levelmax<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
 }
 
