@@ -131,6 +131,14 @@ HPMDR_API hpmdr_status hpmdr_retrieve_abs(hpmdr_ctx* ctx, hpmdr_handle* h, doubl
  * first.  The handle, out and info must stay valid until hpmdr_ctx_wait. */
 HPMDR_API hpmdr_status hpmdr_retrieve_async(hpmdr_ctx* ctx, hpmdr_handle* h, double rel_linf_bound,
                                             void* out, hpmdr_retrieve_info* info);
+/* as hpmdr_retrieve_async with the output in host memory (page-locked for
+ * overlap): the reconstruction goes to one of two device buffers of the
+ * context and is copied out on a stream of its own, so the copy of one
+ * retrieval overlaps the kernels of the next; out is complete at
+ * hpmdr_ctx_wait. */
+HPMDR_API hpmdr_status hpmdr_retrieve_async_host(hpmdr_ctx* ctx, hpmdr_handle* h,
+                                                 double rel_linf_bound, void* out,
+                                                 hpmdr_retrieve_info* info);
 HPMDR_API hpmdr_status hpmdr_ctx_wait(hpmdr_ctx* ctx);
 
 /* ---- out-of-core pipeline (Sec. 5.3, the refactoring and retrieval pipelines)

@@ -104,6 +104,7 @@ _SIGS = {
     "hpmdr_handle_drop_cache": (C.c_int, [vp, vp]),
     "hpmdr_handle_memory": (C.c_int, [vp, u64p, u64p, u64p]),
     "hpmdr_retrieve_async": (C.c_int, [vp, vp, C.c_double, vp, vp]),
+    "hpmdr_retrieve_async_host": (C.c_int, [vp, vp, C.c_double, vp, vp]),
     "hpmdr_ctx_wait": (C.c_int, [vp]),
     "hpmdr_refactor_pipeline": (C.c_int, [vp, C.c_int, vp, C.c_int, u64p, u64p, C.c_int, C.c_int,
                                           vp, u64p, u64p, u64p]),
@@ -484,12 +485,14 @@ class Handle:
         return out, info, st
 
     def retrieve_async(self, bound, out):
-        """Enqueue a retrieval into the CUDA tensor `out` without waiting; the
-        returned info is filled by Context.wait()."""
+        """Enqueue a retrieval into `out` (a CUDA tensor, or page-locked host
+        memory) without waiting; out and the returned info are complete at
+        Context.wait()."""
         info = RetrieveInfo()
         self.ctx._keep.append((info, out))
-        _check(lib().hpmdr_retrieve_async(self.ctx._p, self._p, float(bound), vp(out.data_ptr()),
-                                          C.byref(info)), "hpmdr_retrieve_async")
+        fn = lib().hpmdr_retrieve_async if out.is_cuda else lib().hpmdr_retrieve_async_host
+        _check(fn(self.ctx._p, self._p, float(bound), vp(out.data_ptr()), C.byref(info)),
+               "hpmdr_retrieve_async")
         return info
 
     def field_info(self):

@@ -875,7 +875,11 @@ extern "C" hpmdr_status hpmdr_retrieve_abs(hpmdr_ctx* ctx, hpmdr_handle* h, doub
 static constexpr size_t kSlotBytes = (sizeof(RetrieveDev) + 16 + 255) / 256 * 256;
 
 static hpmdr_status ctx_wait(hpmdr_ctx* ctx) {
-  const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (ctx->copy_stream) {
+    const cudaError_t e2 = cudaStreamSynchronize(ctx->copy_stream);
+    if (e == cudaSuccess) e = e2;
+  }
   hpmdr_status first = HPMDR_OK;
   if (e != cudaSuccess) {
     g_last_error = std::string("wait: ") + cudaGetErrorString(e);
@@ -902,8 +906,21 @@ static hpmdr_status ctx_wait(hpmdr_ctx* ctx) {
   return first;
 }
 
+static hpmdr_status retrieve_async_impl(hpmdr_ctx* ctx, hpmdr_handle* H, double rel, void* out,
+                                       int out_on_device, hpmdr_retrieve_info* info);
+
 extern "C" hpmdr_status hpmdr_retrieve_async(hpmdr_ctx* ctx, hpmdr_handle* H, double rel,
                                              void* out, hpmdr_retrieve_info* info) {
+  return retrieve_async_impl(ctx, H, rel, out, 1, info);
+}
+
+extern "C" hpmdr_status hpmdr_retrieve_async_host(hpmdr_ctx* ctx, hpmdr_handle* H, double rel,
+                                                  void* out, hpmdr_retrieve_info* info) {
+  return retrieve_async_impl(ctx, H, rel, out, 0, info);
+}
+
+static hpmdr_status retrieve_async_impl(hpmdr_ctx* ctx, hpmdr_handle* H, double rel, void* out,
+                                       int out_on_device, hpmdr_retrieve_info* info) {
   if (!ctx || !H || !out || !(rel >= 0.0)) return HPMDR_ERR_ARG;
   const cudaStream_t s = ctx->stream;
   if (!ctx->pinned) {
@@ -917,7 +934,42 @@ extern "C" hpmdr_status hpmdr_retrieve_async(hpmdr_ctx* ctx, hpmdr_handle* H, do
     const hpmdr_status st = ctx_wait(ctx);
     if (st != HPMDR_OK && st != HPMDR_ERR_UNATTAINABLE) return st;
   }
-  HP_TRY(enqueue_retrieve(ctx, H, rel, 0, out, s));
+  int b = -1;
+  void* d_out = out;
+  if (!out_on_device) {  // into one of the two device buffers, then copied out
+    const size_t bytes = H->N * (H->dtype == HPMDR_F32 ? 4 : 8);
+    if (!ctx->copy_stream) {
+      HP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+      for (int i = 0; i < 2; i++) {
+        HP_CUDA(cudaEventCreateWithFlags(&ctx->ev_ready[i], cudaEventDisableTiming));
+        HP_CUDA(cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming));
+      }
+    }
+    if (ctx->out_stage_bytes < bytes) {  // grow: wait for the copies still reading them
+      HP_CUDA(cudaStreamSynchronize(ctx->copy_stream));
+      for (int i = 0; i < 2; i++) {
+        ctx->A.release(ctx->out_stage[i], s);
+        ctx->out_stage[i] = nullptr;
+        ctx->copied_pending[i] = false;
+      }
+      ctx->out_stage_bytes = 0;
+      for (int i = 0; i < 2; i++) HP_TRY(ctx->A.alloc(&ctx->out_stage[i], bytes, s));
+      ctx->out_stage_bytes = bytes;
+    }
+    b = ctx->out_next;
+    ctx->out_next ^= 1;
+    if (ctx->copied_pending[b]) HP_CUDA(cudaStreamWaitEvent(s, ctx->ev_copied[b], 0));
+    d_out = ctx->out_stage[b];
+  }
+  HP_TRY(enqueue_retrieve(ctx, H, rel, 0, d_out, s));
+  if (b >= 0) {
+    const size_t bytes = H->N * (H->dtype == HPMDR_F32 ? 4 : 8);
+    HP_CUDA(cudaEventRecord(ctx->ev_ready[b], s));
+    HP_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_ready[b], 0));
+    HP_CUDA(cudaMemcpyAsync(out, d_out, bytes, cudaMemcpyDeviceToHost, ctx->copy_stream));
+    HP_CUDA(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+    ctx->copied_pending[b] = true;
+  }
   PendingRetrieval p;
   p.H = H;
   p.info = info;

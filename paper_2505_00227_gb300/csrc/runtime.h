@@ -171,8 +171,23 @@ struct hpmdr_ctx {
   void* pinned = nullptr;
   int ring_next = 0;
   std::vector<PendingRetrieval> pending;
+  // asynchronous retrievals into host memory: two device output buffers, the
+  // copy of one to the host (on copy_stream) overlapping the next retrieval
+  void* out_stage[2] = {nullptr, nullptr};
+  size_t out_stage_bytes = 0;
+  int out_next = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+  bool copied_pending[2] = {false, false};
   Profiler* P() { return prof.on ? &prof : nullptr; }
   ~hpmdr_ctx() {
+    if (copy_stream) cudaStreamSynchronize(copy_stream);
+    for (int i = 0; i < 2; i++) {
+      A.release(out_stage[i], stream);
+      if (ev_ready[i]) cudaEventDestroy(ev_ready[i]);
+      if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
     for (cudaStream_t s : aux) cudaStreamDestroy(s);
     if (pinned) cudaFreeHost(pinned);
   }

@@ -105,3 +105,31 @@ def test_profile_selected_stages_only(B):
     assert prof["cells_recompose_out"][1] > 0 and prof["cells_recompose_out"][3] > 0
     assert all(p[2] == 0 for k, p in prof.items() if k not in ("cells_recompose_out", "select"))
     assert all(i.status == 0 for i in infos)
+
+
+def test_async_into_host_memory(B):
+    f = _field((40, 64, 128), 12)
+    F = O.Field(f)
+    ctx = B.Context()
+    h = ctx.refactor(torch.from_numpy(f).cuda())
+    outs = [torch.empty(f.shape, dtype=torch.float32).pin_memory() for _ in TAUS]
+    infos = [h.retrieve_async(t, o) for t, o in zip(TAUS, outs)]
+    shared = torch.empty(f.shape, dtype=torch.float32).pin_memory()
+    last = [h.retrieve_async(t, shared) for t in reversed(TAUS)]  # one buffer: the last wins
+    assert ctx.wait() == 0
+    for t, o, info in zip(TAUS, outs, infos):
+        rc, ref, g, E = F.retrieve(t * F.range)
+        assert info.status == rc and info.est_linf == E
+        assert np.array_equal(o.numpy().view(np.uint32), ref.view(np.uint32)), t
+    rc, ref, g, E = F.retrieve(TAUS[0] * F.range)
+    assert np.array_equal(shared.numpy().view(np.uint32), ref.view(np.uint32))
+    assert all(i.status == 0 for i in last)
+    # a larger handle afterwards grows the context's output buffers
+    f2 = _field((64, 64, 128), 13)
+    h2 = ctx.refactor(torch.from_numpy(f2).cuda())
+    o2 = torch.empty(f2.shape, dtype=torch.float32).pin_memory()
+    i2 = h2.retrieve_async(1e-4, o2)
+    assert ctx.wait() == 0
+    F2 = O.Field(f2)
+    rc, ref, g, E = F2.retrieve(1e-4 * F2.range)
+    assert i2.status == rc and np.array_equal(o2.numpy().view(np.uint32), ref.view(np.uint32))
