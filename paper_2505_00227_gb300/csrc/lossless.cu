@@ -992,81 +992,96 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
   // the previous chunk when that one belonged to the same group
   __shared__ uint32_t s_flag, s_gl;
   if (!tables_ready) {
-    if (tid < 32) {
-      uint32_t myL[8];
-      bool bad = false;
-      uint32_t gl = 0;
+    // every thread takes symbols tid and tid + 128: lengths counted per warp
+    // (warp matches), ranks among equal lengths from those counts, canonical
+    // first codes by one thread, then the lookup table entry by entry
+    __shared__ uint32_t s_wc[2][HP_DEC_THREADS / 32][17];
+    __shared__ uint32_t s_gw[HP_DEC_THREADS / 32];
+    const int w = tid >> 5, nw = NT >> 5;
+    for (int i = tid; i < 2 * (HP_DEC_THREADS / 32) * 17; i += NT) (&s_wc[0][0][0])[i] = 0;
+    __syncthreads();
+    uint32_t myL[2], rank[2];
+    bool bad = false;
+    uint32_t gl = 0;
 #pragma unroll
-      for (int r = 0; r < 8; r++) {
-        myL[r] = lens[32 * r + lane];
-        bad |= myL[r] > 16;
-        uint32_t x = gl, y = myL[r];
-        while (y) {
-          const uint32_t t = x % y;
-          x = y;
-          y = t;
-        }
-        gl = x;
+    for (int r = 0; r < 2; r++) {
+      myL[r] = lens[tid + r * HP_DEC_THREADS];
+      bad |= myL[r] > 16;
+      uint32_t x = gl, y = myL[r];
+      while (y) {
+        const uint32_t tt = x % y;
+        x = y;
+        y = tt;
       }
-#pragma unroll
-      for (int dd = 16; dd; dd >>= 1) {
-        uint32_t x = gl, y = __shfl_xor_sync(HP_FULL, gl, dd);
-        while (y) {
-          const uint32_t t = x % y;
-          x = y;
-          y = t;
-        }
-        gl = x;
-      }
-      bad = __any_sync(HP_FULL, bad);
-      uint32_t cnt = 0;
-#pragma unroll
-      for (int r = 0; r < 8; r++)
-        for (int L = 1; L <= 16; L++) {
-          const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
-          if (lane == L) cnt += __popc(m);
-        }
-      if (lane <= 16) T.count[lane] = lane ? cnt : 0;
-      __syncwarp();
-      if (lane == 0) {
-        uint32_t c = 0, idx = 0;
-        for (int L = 1; L <= 16; L++) {
-          T.first[L] = c;
-          T.index[L] = idx;
-          T.fill[L] = idx;
-          idx += T.count[L];
-          c = (c + T.count[L]) << 1;
-        }
-        s_flag = bad ? 1u : 0u;
-        s_gl = gl ? gl : 1u;
-      }
-      __syncwarp();
-      const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-      for (int r = 0; r < 8; r++) {
-        for (int L = 1; L <= 16; L++) {
-          const uint32_t m = __ballot_sync(HP_FULL, myL[r] == (uint32_t)L);
-          if (myL[r] == (uint32_t)L) T.sorted[T.fill[L] + __popc(m & lt)] = (uint8_t)(32 * r + lane);
-          __syncwarp();
-          if (lane == 0) T.fill[L] += __popc(m);
-          __syncwarp();
-        }
-      }
+      gl = x;
+      const unsigned m = __match_any_sync(HP_FULL, myL[r]);
+      rank[r] = __popc(m & ((1u << lane) - 1u));
+      if ((int)(__ffs(m) - 1) == lane && myL[r] <= 16) s_wc[r][w][myL[r]] = __popc(m);
     }
-    for (int i = tid; i < (1 << HP_LUT_BITS); i += NT) T.lut[i] = 0;
+#pragma unroll
+    for (int dd = 16; dd; dd >>= 1) {
+      uint32_t x = gl, y = __shfl_xor_sync(HP_FULL, gl, dd);
+      while (y) {
+        const uint32_t tt = x % y;
+        x = y;
+        y = tt;
+      }
+      gl = x;
+    }
+    if (lane == 0) s_gw[w] = gl;
+    bad = __syncthreads_or(bad ? 1 : 0) != 0;
+    if (tid == 0) {
+      uint32_t c = 0, idx = 0, g = 0;
+      for (int k = 0; k < nw; k++) {
+        uint32_t x = g, y = s_gw[k];
+        while (y) {
+          const uint32_t tt = x % y;
+          x = y;
+          y = tt;
+        }
+        g = x;
+      }
+      for (int L = 1; L <= 16; L++) {
+        uint32_t n = 0;
+        for (int r = 0; r < 2; r++)
+          for (int k = 0; k < nw; k++) n += s_wc[r][k][L];
+        T.count[L] = n;
+        T.first[L] = c;
+        T.index[L] = idx;
+        idx += n;
+        c = (c + n) << 1;
+      }
+      T.count[0] = 0;
+      s_flag = bad ? 1u : 0u;
+      s_gl = g ? g : 1u;
+    }
     __syncthreads();
     if (s_flag) {
       if (tid == 0) set_corrupt(meta);
       return;
     }
-    for (int L = 1; L <= HP_LUT_BITS; L++) {
-      const uint32_t n = T.count[L];
-      for (uint32_t k = tid; k < n; k += NT) {
-        const uint32_t code = T.first[L] + k, sym = T.sorted[T.index[L] + k];
-        const uint32_t span = 1u << (HP_LUT_BITS - L), base = code << (HP_LUT_BITS - L);
-        if (base + span <= (1u << HP_LUT_BITS))  // a code set breaking Kraft is caught below
-          for (uint32_t r = 0; r < span; r++) T.lut[base + r] = (uint16_t)((L << 8) | sym);
+#pragma unroll
+    for (int r = 0; r < 2; r++) {  // symbol order: slot 0 (0..127), then slot 1, warps in order
+      const uint32_t L = myL[r];
+      if (L) {
+        uint32_t before = rank[r];
+        for (int rr = 0; rr <= r; rr++)
+          for (int k = 0; k < (rr < r ? nw : w); k++) before += s_wc[rr][k][L];
+        T.sorted[T.index[L] + before] = (uint8_t)(tid + r * HP_DEC_THREADS);
       }
+    }
+    __syncthreads();
+    // entry e holds the code of length L <= HP_LUT_BITS that prefixes it, if any
+    for (int e = tid; e < (1 << HP_LUT_BITS); e += NT) {
+      uint16_t v = 0;
+      for (int L = 1; L <= HP_LUT_BITS; L++) {
+        const uint32_t c = (uint32_t)e >> (HP_LUT_BITS - L);
+        if (c - T.first[L] < T.count[L]) {
+          v = (uint16_t)((L << 8) | T.sorted[T.index[L] + (c - T.first[L])]);
+          break;
+        }
+      }
+      T.lut[e] = v;
     }
   } else if (s_flag) {  // the group's tables were found corrupt
     if (tid == 0) set_corrupt(meta);
