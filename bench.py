@@ -112,9 +112,10 @@ def traffic_for(kernel):
         with open(path) as fh:
             table = json.load(fh)
         e = table[kernel]
-        src = os.path.join(ROOT, "paper_2505_00227_gb300", "csrc", e["source"])
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != e["source_sha256"]:
-            return None
+        for name, sha in e["source_sha256"].items():  # the kernel's file and its headers
+            src = os.path.join(ROOT, "paper_2505_00227_gb300", "csrc", name)
+            if hashlib.sha256(open(src, "rb").read()).hexdigest() != sha:
+                return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
         return None

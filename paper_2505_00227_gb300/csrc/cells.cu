@@ -189,15 +189,6 @@ __device__ __forceinline__ void cells_levelmax_flush(FieldMeta* meta, int level,
 // within about 2^-10 of a power of two at the usual magnitudes, a near-zero
 // level, a tiny field) the exact pass runs for the level.  The floor flag of
 // the level's own nodes is exact in both passes.
-__device__ __forceinline__ uint32_t float_floors(float v, int E_f) {
-  const uint32_t u = __float_as_uint(v), e = (u >> 23) & 0xffu;
-  uint32_t m = u & 0x7fffffu;
-  if (e) m |= 0x800000u;
-  const int r = 102 + E_f - (int)(e ? e : 1u);  // bits of m below the unit
-  if (r <= 0 || m == 0) return 0u;
-  return r >= 32 ? 1u : ((m & ((1u << r) - 1u)) != 0u);
-}
-
 __device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict__ f,
                                                         const CellGeom& G, uint32_t ny,
                                                         uint32_t nx, int hl, int E_f, uint32_t tile,
@@ -294,23 +285,6 @@ __global__ void __launch_bounds__(256, 4) k_cells_levelmax_est(const float* __re
     if (mx > 0.0f) atomicMax(&meta->m8est[L.level], __float_as_uint(mx));  // order of >= 0 floats
     if (anyfl) atomicOr(&meta->floored, 1u);
   }
-}
-
-// bl from the estimate when it is unambiguous (then m8 = 2^(bl-1)); false:
-// the exact pass must run
-__device__ __forceinline__ bool cells_bl_from_estimate(FieldMeta* meta, int level, bool write) {
-  const int E_f = meta->E_f;
-  const uint32_t bits = meta->m8est[level];
-  if (E_f < -90 || bits == 0u) return false;
-  const double M = (double)__uint_as_float(bits) * __longlong_as_double((long long)(51 - E_f + 1023) << 52);
-  const double lo = M - 0x1p33, hi = M + 0x1p33;
-  if (!(lo >= 1.0)) return false;
-  int el, eh;
-  frexp(lo, &el);
-  frexp(hi, &eh);
-  if (el != eh) return false;  // the interval holds a power of two
-  if (write) meta->m8[level] = 1ull << (el - 1);  // bitlen el
-  return true;
 }
 
 __global__ void __launch_bounds__(256, 4) k_cells_levelmax(const float* __restrict__ f, uint32_t ny,

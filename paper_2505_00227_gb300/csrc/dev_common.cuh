@@ -158,6 +158,37 @@ __device__ __forceinline__ double fixed_to_f64(int64_t X, int E_f) {
   return __dmul_rn(y, __longlong_as_double((long long)(e + 500 + 1023) << 52));
 }
 
+// ---------------------------------------------- level maximum by estimate
+// (FP32 levels) a pass in FP32 bounds every detail to within 2^31 + 16 units of
+// U/8 (the error analysis is beside k_cells_levelmax_est); these helpers give
+// the exact floor flag of a value and turn the estimate into bl when its
+// interval holds one bit length.
+__device__ __forceinline__ uint32_t float_floors(float v, int E_f) {
+  const uint32_t u = __float_as_uint(v), e = (u >> 23) & 0xffu;
+  uint32_t m = u & 0x7fffffu;
+  if (e) m |= 0x800000u;
+  const int r = 102 + E_f - (int)(e ? e : 1u);  // bits of m below the unit
+  if (r <= 0 || m == 0) return 0u;
+  return r >= 32 ? 1u : ((m & ((1u << r) - 1u)) != 0u);
+}
+
+// bl from the estimate when it is unambiguous (then m8 = 2^(bl-1)); false:
+// the exact pass must run
+__device__ __forceinline__ bool cells_bl_from_estimate(FieldMeta* meta, int level, bool write) {
+  const int E_f = meta->E_f;
+  const uint32_t bits = meta->m8est[level];
+  if (E_f < -90 || bits == 0u) return false;
+  const double M = (double)__uint_as_float(bits) * __longlong_as_double((long long)(51 - E_f + 1023) << 52);
+  const double lo = M - 0x1p33, hi = M + 0x1p33;
+  if (!(lo >= 1.0)) return false;
+  int el, eh;
+  frexp(lo, &el);
+  frexp(hi, &eh);
+  if (el != eh) return false;  // the interval holds a power of two
+  if (write) meta->m8[level] = 1ull << (el - 1);  // bitlen el
+  return true;
+}
+
 __device__ __forceinline__ uint64_t umag(int64_t c) {
   return c < 0 ? (uint64_t)(-c) : (uint64_t)c;
 }

@@ -125,12 +125,94 @@ __device__ __forceinline__ void gcells_levelmax_range(const GView<T>& v, const L
   }
 }
 
+// FP32 levels: the estimate pass (bound and fallback as for the fused cells,
+// k_cells_levelmax_est): each detail f - mean(corners) in FP32, k - 1 roundings
+// of partial sums of at most k corners, one rounding of the difference
+__device__ __forceinline__ float gFf(const GView<float>& v, uint32_t z, uint32_t y, uint32_t x) {
+  return __ldg(v.f + ((size_t)(z << v.hl) * v.ny + (y << v.hl)) * v.nx + ((size_t)x << v.hl));
+}
+
+__device__ __forceinline__ void gcells_levelmax_est_range(const GView<float>& v,
+                                                          const LevelDesc& L, uint32_t c0,
+                                                          uint32_t c1, uint32_t step,
+                                                          FieldMeta* meta) {
+  float mx = 0.0f;
+  uint32_t fl = 0;
+  auto take = [&](float node, float mean) {
+    mx = fmaxf(mx, fabsf(__fsub_rn(node, mean)));
+    fl |= float_floors(node, v.E_f);
+  };
+  for (uint32_t c = c0; c < c1; c += step) {
+    const CellPos p = cell_pos(L, c);
+    const uint32_t Z0 = 2 * p.cz, Y0 = 2 * p.cy, X0 = 2 * p.cx;
+    const uint32_t Z2 = Z0 + 2 < L.g[0] ? Z0 + 2 : Z0, Y2 = Y0 + 2 < L.g[1] ? Y0 + 2 : Y0;
+    const uint32_t X2 = X0 + 2 < L.g[2] ? X0 + 2 : X0;
+    const float c000 = gFf(v, Z0, Y0, X0);
+    float c001 = 0.0f, c010 = 0.0f, c011 = 0.0f, s01 = 0.0f;
+    if (p.hx) {
+      c001 = gFf(v, Z0, Y0, X2);
+      take(gFf(v, Z0, Y0, X0 + 1), __fmul_rn(__fadd_rn(c000, c001), 0.5f));
+    }
+    if (p.hy) {
+      c010 = gFf(v, Z0, Y2, X0);
+      take(gFf(v, Z0, Y0 + 1, X0), __fmul_rn(__fadd_rn(c000, c010), 0.5f));
+      if (p.hx) {
+        c011 = gFf(v, Z0, Y2, X2);
+        s01 = __fadd_rn(__fadd_rn(c000, c001), __fadd_rn(c010, c011));
+        take(gFf(v, Z0, Y0 + 1, X0 + 1), __fmul_rn(s01, 0.25f));
+      }
+    }
+    if (p.hz) {
+      const float c100 = gFf(v, Z2, Y0, X0);
+      take(gFf(v, Z0 + 1, Y0, X0), __fmul_rn(__fadd_rn(c000, c100), 0.5f));
+      float c101 = 0.0f;
+      if (p.hx) {
+        c101 = gFf(v, Z2, Y0, X2);
+        take(gFf(v, Z0 + 1, Y0, X0 + 1),
+             __fmul_rn(__fadd_rn(__fadd_rn(c000, c001), __fadd_rn(c100, c101)), 0.25f));
+      }
+      if (p.hy) {
+        const float c110 = gFf(v, Z2, Y2, X0);
+        take(gFf(v, Z0 + 1, Y0 + 1, X0),
+             __fmul_rn(__fadd_rn(__fadd_rn(c000, c010), __fadd_rn(c100, c110)), 0.25f));
+        if (p.hx) {
+          const float c111 = gFf(v, Z2, Y2, X2);
+          const float s1 = __fadd_rn(__fadd_rn(c100, c101), __fadd_rn(c110, c111));
+          take(gFf(v, Z0 + 1, Y0 + 1, X0 + 1), __fmul_rn(__fadd_rn(s01, s1), 0.125f));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(HP_FULL, mx, o));
+  const unsigned anyfl = __any_sync(HP_FULL, fl != 0);
+  if ((threadIdx.x & 31) == 0) {
+    if (mx > 0.0f) atomicMax(&meta->m8est[L.level], __float_as_uint(mx));
+    if (anyfl) atomicOr(&meta->floored, 1u);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gcells_levelmax_est(const float* __restrict__ f,
+                                                             uint32_t ny, uint32_t nx,
+                                                             const LevelDesc* __restrict__ Lp,
+                                                             FieldMeta* meta) {
+  if (meta->status) return;
+  const LevelDesc& L = *Lp;
+  const GView<float> v{f, ny, nx, L.hlog, meta->E_f};
+  gcells_levelmax_est_range(v, L, blockIdx.x * blockDim.x + threadIdx.x, gcell_count(L),
+                            gridDim.x * blockDim.x, meta);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gcells_levelmax(const T* __restrict__ f, uint32_t ny,
                                                          uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                          FieldMeta* meta) {
   if (meta->status) return;
   const LevelDesc& L = *Lp;
+  if (sizeof(T) == 4 && cells_bl_from_estimate(meta, L.level, false)) {  // settled
+    if (blockIdx.x == 0 && threadIdx.x == 0) cells_bl_from_estimate(meta, L.level, true);
+    return;
+  }
   const GView<T> v{f, ny, nx, L.hlog, meta->E_f};
   gcells_levelmax_range(v, L, blockIdx.x * blockDim.x + threadIdx.x, gcell_count(L),
                         gridDim.x * blockDim.x, meta);
@@ -291,9 +373,12 @@ static uint32_t gcell_grid(const LevelDesc& L) {
 void launch_gcells_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
                             const LevelDesc& Lh, FieldMeta* meta, cstream s) {
   const uint32_t g = gcell_grid(Lh);
-  if (dtype == 0)
+  if (dtype == 0) {
+    hp::note_launch(), k_gcells_levelmax_est<<<g, 256, 0, s>>>(
+        (const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
     hp::note_launch(), k_gcells_levelmax<float><<<g, 256, 0, s>>>(
         (const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
+  }
   else
     hp::note_launch(), k_gcells_levelmax<double><<<g, 256, 0, s>>>(
         (const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
@@ -337,9 +422,31 @@ __global__ void __launch_bounds__(256) kb_gcells_levelmax(const BatchJob* __rest
     FieldMeta* meta = J.meta;
     if (meta->status) continue;
     const LevelDesc& L = J.levels[R.level];
+    if (sizeof(T) == 4 && cells_bl_from_estimate(meta, L.level, false)) {  // settled
+      if (u == unit0[e] && threadIdx.x == 0) cells_bl_from_estimate(meta, L.level, true);
+      continue;
+    }
     const GView<T> v{reinterpret_cast<const T*>(J.f), J.dims[1], J.dims[2], L.hlog, meta->E_f};
     const uint32_t c = (u - unit0[e]) * 256 + threadIdx.x, n = gcell_count(L);
     gcells_levelmax_range(v, L, c, c < n ? c + 1 : c, 1, meta);
+  }
+}
+
+__global__ void __launch_bounds__(256) kb_gcells_levelmax_est(const BatchJob* __restrict__ jobs,
+                                                              const LevelRef* __restrict__ refs,
+                                                              const uint32_t* __restrict__ unit0,
+                                                              uint32_t nrefs, uint32_t total) {
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t e = unit_owner(unit0, nrefs, u);
+    const LevelRef R = refs[e];
+    const BatchJob& J = jobs[R.job];
+    FieldMeta* meta = J.meta;
+    if (meta->status) continue;
+    const LevelDesc& L = J.levels[R.level];
+    const GView<float> v{reinterpret_cast<const float*>(J.f), J.dims[1], J.dims[2], L.hlog,
+                         meta->E_f};
+    const uint32_t c = (u - unit0[e]) * 256 + threadIdx.x, n = gcell_count(L);
+    gcells_levelmax_est_range(v, L, c, c < n ? c + 1 : c, 1, meta);
   }
 }
 
@@ -388,8 +495,10 @@ void launch_b_gcells_levelmax(const BatchJob* jobs, const LevelRef* refs, const 
                               uint32_t nrefs, uint32_t total, int dtype, uint32_t grid, cstream s) {
   if (!total) return;
   grid = cap_units(grid, total);
-  if (dtype == 0)
+  if (dtype == 0) {
+    hp::note_launch(), kb_gcells_levelmax_est<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
     hp::note_launch(), kb_gcells_levelmax<float><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  }
   else
     hp::note_launch(), kb_gcells_levelmax<double><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
 }
