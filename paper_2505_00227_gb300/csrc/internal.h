@@ -159,6 +159,10 @@ void set_smem_once(const void* func, int bytes);
 
 // stats.cu
 void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, cstream s);
+// word copies (sizes multiples of 4 bytes) into mapped page-locked host memory
+// by a one-CTA kernel; b and d are device pointers of the host buffers
+void launch_to_host(const void* a, void* b, size_t na_bytes, const void* c, void* d,
+                    size_t nc_bytes, cstream s);
 void launch_stats(const void* f, uint64_t N, int dtype, FieldMeta* meta, cstream s);
 void launch_stats_finalize(FieldMeta* meta, cstream s);
 

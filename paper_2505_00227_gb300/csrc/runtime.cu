@@ -474,11 +474,36 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   return HPMDR_OK;
 }
 
-// waits for H's refactor on s and mirrors its metadata to the host
+// page-locked host memory the device writes through its mapped address
+static hpmdr_status alloc_mapped(size_t bytes, void** host, void** dev) {
+  if (cudaHostAlloc(host, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    *host = nullptr;
+    cudaGetLastError();
+    return HPMDR_ERR_NOMEM;
+  }
+  if (cudaHostGetDevicePointer(dev, *host, 0) != cudaSuccess) {
+    cudaFreeHost(*host);
+    *host = nullptr;
+    g_last_error = "cudaHostGetDevicePointer failed";
+    cudaGetLastError();
+    return HPMDR_ERR_CUDA;
+  }
+  return HPMDR_OK;
+}
+
+static_assert(sizeof(FieldMeta) % 4 == 0 && sizeof(RetrieveDev) % 4 == 0,
+              "word copies to the host");
+
+// waits for H's refactor on s and mirrors its metadata to the host (a kernel
+// writes it to page-locked memory: a copy-engine transfer would wait behind
+// large copies still running on other streams)
 static hpmdr_status refactor_finish(hpmdr_ctx* ctx, hpmdr_handle* H, cudaStream_t s,
                                     const RefactorProf& rp) {
-  HP_CUDA(cudaMemcpyAsync(H->meta.get(), H->d_meta, sizeof(FieldMeta), cudaMemcpyDeviceToHost, s));
+  if (!ctx->pinned_meta) HP_TRY(alloc_mapped(sizeof(FieldMeta), &ctx->pinned_meta, &ctx->pinned_meta_dev));
+  launch_to_host(H->d_meta, ctx->pinned_meta_dev, sizeof(FieldMeta), nullptr, nullptr, 0, s);
+  HP_CUDA(cudaGetLastError());
   HP_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(H->meta.get(), ctx->pinned_meta, sizeof(FieldMeta));
   count_items(H);
   if (H->meta->status) return (hpmdr_status)H->meta->status;
   if (ctx->prof.on) {  // bytes of the coder stages, known once the methods are chosen
@@ -923,13 +948,7 @@ static hpmdr_status retrieve_async_impl(hpmdr_ctx* ctx, hpmdr_handle* H, double 
                                        int out_on_device, hpmdr_retrieve_info* info) {
   if (!ctx || !H || !out || !(rel >= 0.0)) return HPMDR_ERR_ARG;
   const cudaStream_t s = ctx->stream;
-  if (!ctx->pinned) {
-    if (cudaHostAlloc(&ctx->pinned, kSlotBytes * hpmdr_ctx::kRing, cudaHostAllocDefault) !=
-        cudaSuccess) {
-      ctx->pinned = nullptr;
-      return HPMDR_ERR_NOMEM;
-    }
-  }
+  if (!ctx->pinned) HP_TRY(alloc_mapped(kSlotBytes * hpmdr_ctx::kRing, &ctx->pinned, &ctx->pinned_dev));
   if ((int)ctx->pending.size() == hpmdr_ctx::kRing) {  // every slot in flight: drain
     const hpmdr_status st = ctx_wait(ctx);
     if (st != HPMDR_OK && st != HPMDR_ERR_UNATTAINABLE) return st;
@@ -975,10 +994,12 @@ static hpmdr_status retrieve_async_impl(hpmdr_ctx* ctx, hpmdr_handle* H, double 
   p.info = info;
   p.slot = ctx->ring_next;
   ctx->ring_next = (ctx->ring_next + 1) % hpmdr_ctx::kRing;
-  unsigned char* slot = (unsigned char*)ctx->pinned + (size_t)p.slot * kSlotBytes;
-  HP_CUDA(cudaMemcpyAsync(slot, H->d_rd, sizeof(RetrieveDev), cudaMemcpyDeviceToHost, s));
-  HP_CUDA(cudaMemcpyAsync(slot + sizeof(RetrieveDev), &H->d_meta->status, 4,
-                          cudaMemcpyDeviceToHost, s));
+  // the selection record and the status, by a kernel (not behind the copy
+  // engine's queue of output transfers)
+  unsigned char* slot = (unsigned char*)ctx->pinned_dev + (size_t)p.slot * kSlotBytes;
+  launch_to_host(H->d_rd, slot, sizeof(RetrieveDev), &H->d_meta->status, slot + sizeof(RetrieveDev),
+                 4, s);
+  HP_CUDA(cudaGetLastError());
   p.prof_lv = H->prof_lv;
   p.prof_decode = H->prof_decode;
   p.prof_small = H->prof_small;

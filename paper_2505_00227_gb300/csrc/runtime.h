@@ -168,7 +168,11 @@ struct hpmdr_ctx {
   // asynchronous retrievals: a ring of page-locked result slots (selection
   // record + device status) filled by copies on the stream, read at wait
   static constexpr int kRing = 64;
-  void* pinned = nullptr;
+  void* pinned = nullptr;      // mapped: written by a kernel (launch_to_host)
+  void* pinned_dev = nullptr;  // its device address
+  // the refactor's metadata mirror, written the same way
+  void* pinned_meta = nullptr;
+  void* pinned_meta_dev = nullptr;
   int ring_next = 0;
   std::vector<PendingRetrieval> pending;
   // asynchronous retrievals into host memory: two device output buffers, the
@@ -190,6 +194,7 @@ struct hpmdr_ctx {
     if (copy_stream) cudaStreamDestroy(copy_stream);
     for (cudaStream_t s : aux) cudaStreamDestroy(s);
     if (pinned) cudaFreeHost(pinned);
+    if (pinned_meta) cudaFreeHost(pinned_meta);
   }
 };
 

@@ -33,6 +33,23 @@ void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, 
   hp::note_launch(), k_meta_init<<<1, 1, 0, s>>>(meta, dtype, B, nlev, ngroups);
 }
 
+// Small device -> page-locked host copies written by a kernel (stores through
+// the mapped host pointer): they do not queue on the copy engines behind large
+// transfers of other streams.  Two word ranges per launch.
+__global__ void __launch_bounds__(256) k_to_host(const uint32_t* __restrict__ a, uint32_t* b,
+                                                 uint32_t na, const uint32_t* __restrict__ c,
+                                                 uint32_t* d, uint32_t nc) {
+  for (uint32_t i = threadIdx.x; i < na; i += blockDim.x) b[i] = a[i];
+  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) d[i] = c[i];
+}
+
+void launch_to_host(const void* a, void* b, size_t na_bytes, const void* c, void* d,
+                    size_t nc_bytes, cstream s) {
+  hp::note_launch(), k_to_host<<<1, 256, 0, s>>>((const uint32_t*)a, (uint32_t*)b,
+                                                 (uint32_t)(na_bytes / 4), (const uint32_t*)c,
+                                                 (uint32_t*)d, (uint32_t)(nc_bytes / 4));
+}
+
 // 128-bit vector loads over the bulk (four in flight per thread), scalar loads
 // for the tail; FP32 keys are compared as 32-bit integers.
 template <typename T>
