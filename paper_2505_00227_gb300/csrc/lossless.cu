@@ -871,7 +871,8 @@ __device__ __forceinline__ void set_corrupt(FieldMeta* meta) { atomicExch(&meta-
 // The bitmap covers the longest possible chunk (16384 codes of 16 bits); a
 // chunk claiming more bits is decoded by one lane and then fails its checks.  All reads stay inside the chunk's words; an
 // invalid code or a wrong symbol count marks the data corrupt.
-#define HP_DEC_THREADS 128
+#define HP_DEC_THREADS 512  // threads per decoded chunk: one speculative segment each
+#define HP_DEC_SYMS ((256 + HP_DEC_THREADS - 1) / HP_DEC_THREADS)  // symbols per thread (tables)
 #define HP_LUT_BITS 10
 #define HP_MAP_WORDS 8192  // bitmap of 262144 bit positions per warp: 16 bits x 16384 symbols
 
@@ -992,20 +993,21 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
   // the previous chunk when that one belonged to the same group
   __shared__ uint32_t s_flag, s_gl;
   if (!tables_ready) {
-    // every thread takes symbols tid and tid + 128: lengths counted per warp
-    // (warp matches), ranks among equal lengths from those counts, canonical
-    // first codes by one thread, then the lookup table entry by entry
-    __shared__ uint32_t s_wc[2][HP_DEC_THREADS / 32][17];
+    // thread tid takes symbols tid + r NT (r < HP_DEC_SYMS): lengths counted per
+    // warp (warp matches), ranks among equal lengths from those counts,
+    // canonical first codes by one thread, then the lookup table entry by entry
+    __shared__ uint32_t s_wc[HP_DEC_SYMS][HP_DEC_THREADS / 32][17];
     __shared__ uint32_t s_gw[HP_DEC_THREADS / 32];
     const int w = tid >> 5, nw = NT >> 5;
-    for (int i = tid; i < 2 * (HP_DEC_THREADS / 32) * 17; i += NT) (&s_wc[0][0][0])[i] = 0;
+    for (int i = tid; i < HP_DEC_SYMS * (HP_DEC_THREADS / 32) * 17; i += NT) (&s_wc[0][0][0])[i] = 0;
     __syncthreads();
-    uint32_t myL[2], rank[2];
+    uint32_t myL[HP_DEC_SYMS], rank[HP_DEC_SYMS];
     bool bad = false;
     uint32_t gl = 0;
 #pragma unroll
-    for (int r = 0; r < 2; r++) {
-      myL[r] = lens[tid + r * HP_DEC_THREADS];
+    for (int r = 0; r < HP_DEC_SYMS; r++) {
+      const int sym = tid + r * HP_DEC_THREADS;
+      myL[r] = sym < 256 ? lens[sym] : 0u;  // no such symbol: no code
       bad |= myL[r] > 16;
       uint32_t x = gl, y = myL[r];
       while (y) {
@@ -1043,7 +1045,7 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
       }
       for (int L = 1; L <= 16; L++) {
         uint32_t n = 0;
-        for (int r = 0; r < 2; r++)
+        for (int r = 0; r < HP_DEC_SYMS; r++)
           for (int k = 0; k < nw; k++) n += s_wc[r][k][L];
         T.count[L] = n;
         T.first[L] = c;
@@ -1061,7 +1063,7 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
       return;
     }
 #pragma unroll
-    for (int r = 0; r < 2; r++) {  // symbol order: slot 0 (0..127), then slot 1, warps in order
+    for (int r = 0; r < HP_DEC_SYMS; r++) {  // symbol order = (r, warp, lane) order
       const uint32_t L = myL[r];
       if (L) {
         uint32_t before = rank[r];
@@ -1121,87 +1123,59 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     e_me = pos;
   }
   __syncthreads();
-  // ---- 3. every segment continues into the next one until it lands on a start
-  // marked there; from segment 0 on, by induction, each join is a true boundary
-  uint32_t J = e_me, dj = 0;
-  bool joined = true;
-  if (tid + 1 < NT) {
-    joined = false;
-    if (e_me >= s_next) {
-      BitReader tr = rd;
-      uint32_t p = e_me;
-      tr.init(p);
-      while (p < s_next2) {
-        if ((T.map[p >> 5] >> (p & 31)) & 1u) {
-          joined = true;
-          break;
-        }
-        uint32_t sym;
-        const int L = huff_sym(T, tr, sym);
-        if (!L) break;
-        tr.consume(L);
-        p += L;
-        dj++;
+  // ---- 3. every segment's parse continues past its end until it lands on a
+  // codeword start marked by a later segment's parse (from there on the two
+  // agree) or runs off the data; jseg = the segment of that start (NT: none)
+  uint32_t J = e_me, dj = 0, jseg = NT;
+  if (tid + 1 < NT && e_me >= s_next) {
+    BitReader tr = rd;
+    uint32_t p = e_me, k = tid + 1;  // k: the segment holding p
+    tr.init(p);
+    while (p < nbits) {
+      while (k + 1 < (uint32_t)NT && p >= seg_start(k + 1)) k++;
+      if ((T.map[p >> 5] >> (p & 31)) & 1u) {
+        jseg = k;
+        break;
       }
-      if (!joined && p >= s_next2 && s_next2 >= nbits) joined = true;  // ran off the data end
-      J = p;
+      uint32_t sym;
+      const int L = huff_sym(T, tr, sym);
+      if (!L) break;
+      tr.consume(L);
+      p += L;
+      dj++;
     }
+    J = p;
   }
-  __shared__ uint32_t s_J[HP_DEC_THREADS], s_dj[HP_DEC_THREADS], s_e[HP_DEC_THREADS];
-  __shared__ uint32_t s_t[HP_DEC_THREADS], s_tc[HP_DEC_THREADS];
-  __shared__ int s_all;
+  // The true parse is segment 0's; a segment whose parse is true hands over, at
+  // its join, to the segment holding the join, whose parse is true from there
+  // (induction along this chain).  Chain segments emit from their true start
+  // through their join; the others emit nothing.
+  __shared__ uint32_t s_J[HP_DEC_THREADS], s_seg[HP_DEC_THREADS], s_t[HP_DEC_THREADS];
   s_J[tid] = J;
-  s_dj[tid] = dj;
-  s_e[tid] = e_me;
-  if (tid == 0) s_all = 1;
-  __syncthreads();
-  if (!joined) s_all = 0;
-  __syncthreads();
-  uint32_t t_me, tc_me;
-  if (s_all) {
-    t_me = tid == 0 ? 0u : s_e[tid - 1];
-    tc_me = tid == 0 ? c_me : s_dj[tid - 1] + c_me - map_count(T.map, s_me, min(s_J[tid - 1], s_next));
-    if (tid > 0 && s_J[tid - 1] >= s_next) tc_me = s_dj[tid - 1];  // the join lies past this segment
+  s_seg[tid] = jseg;
+  s_t[tid] = 0xffffffffu;
+  const bool adjacent = __syncthreads_and(jseg == (uint32_t)tid + 1 || tid + 1 == NT) != 0;
+  uint32_t t_me;
+  if (adjacent) {  // the usual case: every segment joins the next one
+    t_me = tid == 0 ? 0u : s_J[tid - 1];
   } else {
-    // rare: resolve the segments in order from the true start of segment 0
     if (tid == 0) {
-      uint32_t t = 0;
-      for (int i = 0; i < NT; i++) {
-        const uint32_t a = seg_start(i), b = seg_start(i + 1);
-        uint32_t p = t, d = 0, e = t, cnt = 0;
-        if (t < b) {
-          BitReader tr = rd;
-          tr.init(p);
-          bool jn = false;
-          while (p < b) {
-            if (p >= a && ((T.map[p >> 5] >> (p & 31)) & 1u)) {
-              jn = true;
-              break;
-            }
-            uint32_t sym;
-            const int L = huff_sym(T, tr, sym);
-            if (!L) break;
-            tr.consume(L);
-            p += L;
-            d++;
-          }
-          if (jn) {
-            cnt = d + (uint32_t)map_count(T.map, p, b);
-            e = s_e[i];
-          } else {
-            cnt = d;
-            e = p;
-          }
-        }
-        s_t[i] = t;
-        s_tc[i] = cnt;
-        t = e;
+      uint32_t c = 0, t = 0;
+      while (true) {
+        s_t[c] = t;
+        const uint32_t nx = s_seg[c];
+        if (nx >= (uint32_t)NT) break;
+        t = s_J[c];
+        c = nx;
       }
     }
     __syncthreads();
     t_me = s_t[tid];
-    tc_me = s_tc[tid];
   }
+  // true symbols of this segment's emit range: its own from t_me, then the
+  // continuation up to the join
+  const uint32_t tc_me =
+      t_me == 0xffffffffu ? 0u : c_me - map_count(T.map, s_me, t_me) + dj;
   // ---- 4. output offsets and the final decoding
   uint32_t total_tc;
   const uint32_t o = block_exscan(tc_me, scratch, total_tc);
@@ -1412,10 +1386,22 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t blocks = max_items, cap = (uint32_t)sms * 6;
-  if (blocks > cap) blocks = cap;
   const size_t smem = sizeof(HuffTables);
   set_smem_once((const void*)k_decode, (int)smem);
+  // one wave of resident CTAs: every CTA decodes the same number of consecutive
+  // chunks, so CTAs beyond the resident ones would double the launch's time
+  static int resident = 0;
+  if (!resident) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode, HP_DEC_THREADS, smem) !=
+            cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    resident = per_sm;
+  }
+  uint32_t blocks = max_items, cap = (uint32_t)sms * (uint32_t)resident;
+  if (blocks > cap) blocks = cap;
   hp::note_launch(), k_decode<<<blocks, HP_DEC_THREADS, smem, s>>>(slots, meta, rd, planes);
 }
 

@@ -197,7 +197,17 @@ def _groups():
         # Fibonacci counts: an uncapped code would be 25 bits deep, so the
         # lengths are capped (counts halved and the code rebuilt, twice or more)
         "fibonacci": _fibonacci_group(),
+        # code lengths 6..10 and mostly 8 / 9 (gcd 1): speculative parses of a
+        # chunk's segments often stay out of step past the next segment, so
+        # joins land several segments ahead
+        "skewed": _weighted_group(1.0 / (1 + np.arange(256) / 40.0), 3 * 16384 + 100, 3),
+        "near_uniform": _weighted_group(np.where(np.arange(256) < 200, 1.0, 0.55), 2 * 16384 + 77, 3),
     }
+
+
+def _weighted_group(w, n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.choice(256, size=n, p=w / w.sum()).astype(np.uint8)
 
 
 def _fibonacci_group():
