@@ -235,10 +235,11 @@ void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const 
 void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Lh,
                             const LevelDesc& Lh_host, const uint32_t* perm, const int64_t* coarse,
                             void* dst, int B, int final_dtype, cstream s);
-// root + levels 1..l_end (generic, small) in one CTA
+// root + levels 1..l_end (generic, small) in one CTA; levels_host: the host
+// copy of the level descriptors
 void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* levels,
-                            int l_end, int nlev, int64_t* xroot, int64_t* xa, int64_t* xb,
-                            void* out, int dtype, cstream s);
+                            const LevelDesc* levels_host, int l_end, int nlev, int64_t* xroot,
+                            int64_t* xa, int64_t* xb, void* out, int dtype, cstream s);
 
 // cells.cu (FP32 levels with g_x a multiple of 64)
 bool cell_path_ok(const LevelDesc& L, int B);

@@ -190,24 +190,76 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
 // sequential: each needs the whole coarser grid): X_root, then per level the
 // coarse-node copy and the detail tiles, separated by block barriers.  Grids
 // alternate between the two scratch buffers as in the per-level path.
+// With prefetch, the descriptors, coefficient counts and bit lengths of levels
+// 0..l_end and the plane words they use are first copied to shared memory in
+// one round of independent loads (after the staging: descriptors, k[], bl[],
+// then the words of each level packed in level order), so that the levels'
+// chain of dependent reads runs on shared memory.
 template <typename T, int B>
 __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict__ planes,
                                                      const FieldMeta* __restrict__ m,
                                                      const LevelDesc* __restrict__ levels,
                                                      int l_end, int nlev, int64_t* xroot,
                                                      int64_t* xa, int64_t* xb,
-                                                     void* __restrict__ out, uint32_t* sm) {
+                                                     void* __restrict__ out, uint32_t* sm,
+                                                     bool prefetch) {
   constexpr int WPB = 16;
   uint32_t* s_hi = sm;                                      // [WPB][32*33]
   uint32_t* s_lo = sm + WPB * 32 * 33;                      // [WPB][32*33] (B = 64)
   uint32_t* s_sign = sm + (B == 64 ? 2 : 1) * WPB * 32 * 33;  // [WPB][32]
+  // (the word offset of s_desc is even: 8-byte aligned)
+  LevelDesc* s_desc = reinterpret_cast<LevelDesc*>(s_sign + WPB * 32);  // [l_end + 1]
+  int* s_k = reinterpret_cast<int*>(s_desc + (l_end + 1));              // [l_end + 1]
+  int* s_bl = s_k + (l_end + 1);                                        // [l_end + 1]
+  uint32_t* s_pl = reinterpret_cast<uint32_t*>(
+      (reinterpret_cast<uintptr_t>(s_bl + (l_end + 1)) + 15) & ~(uintptr_t)15);
   if (m->status) return;
+  if (prefetch) {
+    const uint32_t nd = (uint32_t)(l_end + 1) * (uint32_t)(sizeof(LevelDesc) / 4);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(levels);
+    for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) reinterpret_cast<uint32_t*>(s_desc)[i] = src[i];
+    if (threadIdx.x <= (unsigned)l_end) {
+      s_k[threadIdx.x] = 4 * m->cur[threadIdx.x];
+      s_bl[threadIdx.x] = m->bl[threadIdx.x];
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    for (int l = 0; l <= l_end; l++) tot += (1u + (uint32_t)s_k[l]) * s_desc[l].W;
+    constexpr int U = 8;  // loads in flight per thread
+    for (uint32_t f0 = 0; f0 < tot; f0 += U * blockDim.x) {
+      uint32_t v[U], at[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint32_t f = f0 + u * blockDim.x + threadIdx.x;
+        at[u] = 0xffffffffu;
+        if (f < tot) {
+          uint32_t l = 0, acc = 0;
+          while (f >= acc + (1u + (uint32_t)s_k[l]) * s_desc[l].W) {
+            acc += (1u + (uint32_t)s_k[l]) * s_desc[l].W;
+            l++;
+          }
+          v[u] = planes[s_desc[l].plane_off / 4 + (f - acc)];
+          at[u] = f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (at[u] != 0xffffffffu) s_pl[at[u]] = v[u];
+    }
+    __syncthreads();
+  }
+  const LevelDesc* Ls = prefetch ? s_desc : levels;
+  uint32_t acc_pl = 0;  // prefetched words of the levels before the current one
+  auto level_planes = [&](int l) -> const uint32_t* {
+    return prefetch ? s_pl + acc_pl : planes + Ls[l].plane_off / 4;
+  };
+  auto level_k = [&](int l) { return prefetch ? s_k[l] : 4 * m->cur[l]; };
   const int L = nlev - 1, w = threadIdx.x >> 5, E_f = m->E_f;
   if (threadIdx.x < 32) {  // the root: lane p reads plane p, a ballot gathers q
     const int lane = threadIdx.x;
-    const LevelDesc& D = levels[0];
-    const uint32_t* P = planes + D.plane_off / 4;
-    const int k = 4 * m->cur[0];
+    const LevelDesc& D = Ls[0];
+    const uint32_t* P = level_planes(0);
+    const int k = level_k(0);
     uint64_t q = 0;
 #pragma unroll
     for (int r = 0; r < B / 32; r++) {
@@ -217,15 +269,16 @@ __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict_
     }
     if (lane == 0) {
       const bool neg = k > 0 && (P[0] & 1u);
-      const int64_t X = dequant(q, neg, B, m->bl[0]) >> 3;
+      const int64_t X = dequant(q, neg, B, prefetch ? s_bl[0] : m->bl[0]) >> 3;
       *xroot = X;
       if (L == 0) *reinterpret_cast<T*>(out) = convert_out<T>(X, E_f);
     }
   }
   __syncthreads();
+  if (prefetch) acc_pl += (1u + (uint32_t)s_k[0]) * s_desc[0].W;
   const int64_t* coarse = xroot;
   for (int l = 1; l <= l_end; l++) {
-    const LevelDesc& D = levels[l];
+    const LevelDesc& D = Ls[l];
     const bool final = l == L;
     void* dst = final ? out : (void*)(((L - l) % 2 == 1) ? xa : xb);
     // coarse nodes of G_h come from G_2h
@@ -237,8 +290,9 @@ __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict_
       if (final) reinterpret_cast<T*>(dst)[d] = convert_out<T>(coarse[i], E_f);
       else reinterpret_cast<int64_t*>(dst)[d] = coarse[i];
     }
-    const int k = 4 * m->cur[l], bl = m->bl[l];
-    const uint32_t* P = planes + D.plane_off / 4;
+    const int k = level_k(l), bl = prefetch ? s_bl[l] : m->bl[l];
+    const uint32_t* P = level_planes(l);
+    if (prefetch) acc_pl += (1u + (uint32_t)k) * D.W;
     // the level's tiles, WPB at a time: each unpacked by one warp, then their
     // 32 rows spread over all warps
     const uint32_t nt = D.ntiles;
@@ -270,9 +324,10 @@ template <typename T, int B>
 __global__ void __launch_bounds__(512)
     k_recompose_small(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
                       const LevelDesc* __restrict__ levels, int l_end, int nlev,
-                      int64_t* xroot, int64_t* xa, int64_t* xb, void* __restrict__ out) {
-  extern __shared__ uint32_t sm[];
-  recompose_small_body<T, B>(planes, m, levels, l_end, nlev, xroot, xa, xb, out, sm);
+                      int64_t* xroot, int64_t* xa, int64_t* xb, void* __restrict__ out,
+                      bool prefetch) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  recompose_small_body<T, B>(planes, m, levels, l_end, nlev, xroot, xa, xb, out, sm, prefetch);
 }
 
 static int sms() {
@@ -315,18 +370,29 @@ void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const 
     hp::note_launch(), k_recompose_copy<double, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
 }
 
+// shared memory for the prefetched plane words (every plane of every small level)
+constexpr size_t kSmallPrefetchBytes = 48 * 1024;
+
 void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* levels,
-                            int l_end, int nlev, int64_t* xroot, int64_t* xa, int64_t* xb,
-                            void* out, int dtype, cstream s) {
-  const size_t smem = (size_t)((dtype == 0 ? 1 : 2) * 16 * 32 * 33 + 16 * 32) * 4;
+                            const LevelDesc* levels_host, int l_end, int nlev, int64_t* xroot,
+                            int64_t* xa, int64_t* xb, void* out, int dtype, cstream s) {
+  const int B = dtype == 0 ? 32 : 64;
+  const size_t base = (size_t)((dtype == 0 ? 1 : 2) * 16 * 32 * 33 + 16 * 32) * 4;
+  const size_t meta_bytes = (size_t)(l_end + 1) * (sizeof(LevelDesc) + 8) + 16;
+  const size_t meta_max = (size_t)HP_MAX_LEVELS * (sizeof(LevelDesc) + 8) + 16;
+  uint64_t words = 0;
+  for (int l = 0; l <= l_end; l++) words += (uint64_t)(B + 1) * levels_host[l].W;
+  const bool prefetch = words * 4 <= kSmallPrefetchBytes;
+  const size_t smem = base + (prefetch ? meta_bytes + words * 4 : 0);
+  const int most = (int)(base + meta_max + kSmallPrefetchBytes);
   if (dtype == 0) {
-    set_smem_once((const void*)k_recompose_small<float, 32>, (int)smem);
+    set_smem_once((const void*)k_recompose_small<float, 32>, most);
     hp::note_launch(), k_recompose_small<float, 32><<<1, 512, smem, s>>>(
-        planes, meta, levels, l_end, nlev, xroot, xa, xb, out);
+        planes, meta, levels, l_end, nlev, xroot, xa, xb, out, prefetch);
   } else {
-    set_smem_once((const void*)k_recompose_small<double, 64>, (int)smem);
+    set_smem_once((const void*)k_recompose_small<double, 64>, most);
     hp::note_launch(), k_recompose_small<double, 64><<<1, 512, smem, s>>>(
-        planes, meta, levels, l_end, nlev, xroot, xa, xb, out);
+        planes, meta, levels, l_end, nlev, xroot, xa, xb, out, prefetch);
   }
 }
 
@@ -357,7 +423,7 @@ __global__ void __launch_bounds__(512) kb_recompose_small(const BatchJob* __rest
   extern __shared__ uint32_t sm[];
   const BatchJob& J = jobs[blockIdx.x];
   recompose_small_body<T, B>(reinterpret_cast<const uint32_t*>(J.planes), J.meta, J.levels,
-                             J.small_end, (int)J.nlev, J.xroot, J.xa, J.xb, J.out, sm);
+                             J.small_end, (int)J.nlev, J.xroot, J.xa, J.xb, J.out, sm, false);
 }
 
 void launch_b_recompose_small(const BatchJob* jobs, uint32_t njobs, int dtype, cstream s) {

@@ -735,8 +735,8 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
     ProfScope p(P, ST_SMALL, 0, s);
     H->prof_small = p.i;
     H->small_end = l_end;
-    launch_recompose_small(Pl, H->d_meta, H->d_levels, l_end, H->nlev, H->d_xroot, H->d_xa,
-                           H->d_xb, d_out, H->dtype, s);
+    launch_recompose_small(Pl, H->d_meta, H->d_levels, H->levels.data(), l_end, H->nlev,
+                           H->d_xroot, H->d_xa, H->d_xb, d_out, H->dtype, s);
   }
   const int64_t* coarse =
       l_end == 0 ? H->d_xroot : (((L - l_end) % 2 == 1) ? H->d_xa : H->d_xb);
