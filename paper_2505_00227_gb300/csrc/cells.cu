@@ -470,14 +470,29 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       const uint32_t rw = i % 32, r = rw / G.NW, w = rw % G.NW, cy = cy0 + r;
       if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
         const uint32_t word = (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
-        uint32_t a[32];
+        if (k <= 16) {  // the top 16 rows only (uniform over the launch)
+          uint32_t r[16];
 #pragma unroll
-        for (int p = 0; p < 32; p++) a[31 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
-        transpose32(a);
+          for (int p = 0; p < 16; p++) r[15 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
+          transpose16x2(r);
 #pragma unroll
-        for (int j = 0; j < 8; j++)
-          *reinterpret_cast<uint4*>(&s_q[t - 1][rw][4 * j]) =
-              make_uint4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
+          for (int j = 0; j < 4; j++) {
+            *reinterpret_cast<uint4*>(&s_q[t - 1][rw][4 * j]) =
+                make_uint4(r[4 * j] << 16, r[4 * j + 1] << 16, r[4 * j + 2] << 16, r[4 * j + 3] << 16);
+            *reinterpret_cast<uint4*>(&s_q[t - 1][rw][16 + 4 * j]) =
+                make_uint4(r[4 * j] & 0xffff0000u, r[4 * j + 1] & 0xffff0000u,
+                           r[4 * j + 2] & 0xffff0000u, r[4 * j + 3] & 0xffff0000u);
+          }
+        } else {
+          uint32_t a[32];
+#pragma unroll
+          for (int p = 0; p < 32; p++) a[31 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
+          transpose32(a);
+#pragma unroll
+          for (int j = 0; j < 8; j++)
+            *reinterpret_cast<uint4*>(&s_q[t - 1][rw][4 * j]) =
+                make_uint4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
+        }
         s_sw[t - 1][rw] = __ldcs(P + word);
       }
     }

@@ -59,6 +59,32 @@ __device__ __forceinline__ void transpose32(uint32_t a[32]) {
 #undef HP_TSTAGE
 }
 
+// Two 16x16 bit-matrix transposes side by side, one in each 16-bit half of
+// r[0..15]: on return r[c] bit i = old r[i] bit c and r[c] bit (16 + i) = old
+// r[i] bit (16 + c), for i, c < 16.  With at most 16 planes (the top rows of a
+// 32x32 transpose, the others zero) this gives the same result as transpose32
+// at about half the cost: out[c] = r[c] << 16 (c < 16), r[c - 16] & 0xffff0000.
+__device__ __forceinline__ void transpose16x2(uint32_t r[16]) {
+#pragma unroll
+  for (int i = 0; i < 8; i++) {  // the 8-bit stage moves whole bytes
+    const uint32_t x = r[i], y = r[i + 8];
+    r[i] = __byte_perm(x, y, 0x6240);
+    r[i + 8] = __byte_perm(x, y, 0x7351);
+  }
+#define HP_T16STAGE(S, M)                                          \
+  _Pragma("unroll") for (int i = 0; i < 16; i++) {                \
+    if ((i & S) == 0) {                                            \
+      uint32_t t = ((r[i] >> S) ^ r[i + S]) & (M);                 \
+      r[i + S] ^= t;                                               \
+      r[i] ^= t << S;                                              \
+    }                                                              \
+  }
+  HP_T16STAGE(4, 0x0F0F0F0Fu)
+  HP_T16STAGE(2, 0x33333333u)
+  HP_T16STAGE(1, 0x55555555u)
+#undef HP_T16STAGE
+}
+
 // ------------------------------------------------------------- fixed point
 // F = sign(v) * floor(|v| / 2^(E_f-48)), exactly, from the IEEE fields.
 __device__ __forceinline__ int64_t fixed_point(float v, int E_f, uint32_t& floored) {

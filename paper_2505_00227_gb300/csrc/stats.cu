@@ -1,6 +1,7 @@
 // Field statistics: max|f|, min f, max f in one streaming pass, then the
 // exponent E_f that fixes the alignment unit U = 2^(E_f-48) (Sec. 4, the
 // "AlignExponent" step of Algorithm 1 needs the maximum exponent first).
+#include <algorithm>
 #include <type_traits>
 
 #include "dev_common.cuh"
@@ -35,19 +36,36 @@ void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, 
 
 // Small device -> page-locked host copies written by a kernel (stores through
 // the mapped host pointer): they do not queue on the copy engines behind large
-// transfers of other streams.  Two word ranges per launch.
+// transfers of other streams.  Two ranges per launch, each in 16-byte units
+// when both ends allow it, else in words; a few CTAs so that every thread has
+// one or two stores in flight.
+__device__ __forceinline__ void to_host_range(const uint32_t* __restrict__ a, uint32_t* b,
+                                              uint32_t nw) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, T = gridDim.x * blockDim.x;
+  if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) {
+    const uint4* a4 = reinterpret_cast<const uint4*>(a);
+    uint4* b4 = reinterpret_cast<uint4*>(b);
+    for (uint32_t i = t; i < nw / 4; i += T) b4[i] = a4[i];
+    for (uint32_t i = nw / 4 * 4 + t; i < nw; i += T) b[i] = a[i];
+  } else {
+    for (uint32_t i = t; i < nw; i += T) b[i] = a[i];
+  }
+}
+
 __global__ void __launch_bounds__(256) k_to_host(const uint32_t* __restrict__ a, uint32_t* b,
                                                  uint32_t na, const uint32_t* __restrict__ c,
                                                  uint32_t* d, uint32_t nc) {
-  for (uint32_t i = threadIdx.x; i < na; i += blockDim.x) b[i] = a[i];
-  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) d[i] = c[i];
+  to_host_range(a, b, na);
+  to_host_range(c, d, nc);
 }
 
 void launch_to_host(const void* a, void* b, size_t na_bytes, const void* c, void* d,
                     size_t nc_bytes, cstream s) {
-  hp::note_launch(), k_to_host<<<1, 256, 0, s>>>((const uint32_t*)a, (uint32_t*)b,
-                                                 (uint32_t)(na_bytes / 4), (const uint32_t*)c,
-                                                 (uint32_t*)d, (uint32_t)(nc_bytes / 4));
+  const size_t units = (na_bytes + nc_bytes) / 16 + 1;
+  const unsigned blocks = (unsigned)std::min<size_t>(16, (units + 255) / 256);
+  hp::note_launch(), k_to_host<<<blocks, 256, 0, s>>>((const uint32_t*)a, (uint32_t*)b,
+                                                      (uint32_t)(na_bytes / 4), (const uint32_t*)c,
+                                                      (uint32_t*)d, (uint32_t)(nc_bytes / 4));
 }
 
 // 128-bit vector loads over the bulk (four in flight per thread), scalar loads
