@@ -470,7 +470,20 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       const uint32_t rw = i % 32, r = rw / G.NW, w = rw % G.NW, cy = cy0 + r;
       if (cy < L.cnt[t][1] && cz < L.cnt[t][0]) {
         const uint32_t word = (L.off[t] + (cz * L.cnt[t][1] + cy) * L.cnt[t][2] + x0) / 32 + w;
-        if (k <= 16) {  // the top 16 rows only (uniform over the launch)
+        if (k <= 8) {  // the top 8 rows only (uniform over the launch)
+          uint32_t r[8];
+#pragma unroll
+          for (int p = 0; p < 8; p++) r[7 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;
+          transpose8x4(r);
+#pragma unroll
+          for (int j = 0; j < 8; j++) {  // out[c]: byte c >> 3 of r[c & 7] to the top byte
+            const uint32_t sel = ((uint32_t)(j >> 1) << 12) | 0x444u;
+            const int c0 = (4 * j) & 7;
+            *reinterpret_cast<uint4*>(&s_q[t - 1][rw][4 * j]) =
+                make_uint4(__byte_perm(r[c0], 0u, sel), __byte_perm(r[c0 + 1], 0u, sel),
+                           __byte_perm(r[c0 + 2], 0u, sel), __byte_perm(r[c0 + 3], 0u, sel));
+          }
+        } else if (k <= 16) {  // the top 16 rows only
           uint32_t r[16];
 #pragma unroll
           for (int p = 0; p < 16; p++) r[15 - p] = p < k ? __ldcs(P + (size_t)(1 + p) * W + word) : 0u;

@@ -85,6 +85,25 @@ __device__ __forceinline__ void transpose16x2(uint32_t r[16]) {
 #undef HP_T16STAGE
 }
 
+// Four 8x8 bit-matrix transposes side by side, one in each byte of r[0..7]:
+// on return byte b of r[c] holds, in bit i, old r[i] bit (8 b + c).  With at
+// most 8 planes the 32x32 transpose reduces to this: out[c] = byte (c >> 3) of
+// r[c & 7], shifted to the top byte.
+__device__ __forceinline__ void transpose8x4(uint32_t r[8]) {
+#define HP_T8STAGE(S, M)                                           \
+  _Pragma("unroll") for (int i = 0; i < 8; i++) {                 \
+    if ((i & S) == 0) {                                            \
+      uint32_t t = ((r[i] >> S) ^ r[i + S]) & (M);                 \
+      r[i + S] ^= t;                                               \
+      r[i] ^= t << S;                                              \
+    }                                                              \
+  }
+  HP_T8STAGE(4, 0x0F0F0F0Fu)
+  HP_T8STAGE(2, 0x33333333u)
+  HP_T8STAGE(1, 0x55555555u)
+#undef HP_T8STAGE
+}
+
 // ------------------------------------------------------------- fixed point
 // F = sign(v) * floor(|v| / 2^(E_f-48)), exactly, from the IEEE fields.
 __device__ __forceinline__ int64_t fixed_point(float v, int E_f, uint32_t& floored) {
