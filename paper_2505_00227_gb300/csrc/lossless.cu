@@ -884,6 +884,7 @@ struct HuffTables {
   uint32_t fill[17];
   uint8_t sorted[256];
   uint32_t map[HP_MAP_WORDS];      // codeword starts of the speculative decodings
+  uint32_t words[HP_MAP_WORDS];    // the chunk's coded words, staged from global memory
 };
 
 struct BitReader {
@@ -997,61 +998,47 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     // warp (warp matches), ranks among equal lengths from those counts,
     // canonical first codes by one thread, then the lookup table entry by entry
     __shared__ uint32_t s_wc[HP_DEC_SYMS][HP_DEC_THREADS / 32][17];
-    __shared__ uint32_t s_gw[HP_DEC_THREADS / 32];
+    __shared__ uint32_t s_cnt[17];
     const int w = tid >> 5, nw = NT >> 5;
     for (int i = tid; i < HP_DEC_SYMS * (HP_DEC_THREADS / 32) * 17; i += NT) (&s_wc[0][0][0])[i] = 0;
     __syncthreads();
     uint32_t myL[HP_DEC_SYMS], rank[HP_DEC_SYMS];
     bool bad = false;
-    uint32_t gl = 0;
 #pragma unroll
     for (int r = 0; r < HP_DEC_SYMS; r++) {
       const int sym = tid + r * HP_DEC_THREADS;
       myL[r] = sym < 256 ? lens[sym] : 0u;  // no such symbol: no code
       bad |= myL[r] > 16;
-      uint32_t x = gl, y = myL[r];
-      while (y) {
-        const uint32_t tt = x % y;
-        x = y;
-        y = tt;
-      }
-      gl = x;
       const unsigned m = __match_any_sync(HP_FULL, myL[r]);
       rank[r] = __popc(m & ((1u << lane) - 1u));
       if ((int)(__ffs(m) - 1) == lane && myL[r] <= 16) s_wc[r][w][myL[r]] = __popc(m);
     }
-#pragma unroll
-    for (int dd = 16; dd; dd >>= 1) {
-      uint32_t x = gl, y = __shfl_xor_sync(HP_FULL, gl, dd);
-      while (y) {
-        const uint32_t tt = x % y;
-        x = y;
-        y = tt;
-      }
-      gl = x;
-    }
-    if (lane == 0) s_gw[w] = gl;
     bad = __syncthreads_or(bad ? 1 : 0) != 0;
-    if (tid == 0) {
+    if (tid >= 1 && tid <= 16) {  // codes of each length, one thread per length
+      uint32_t n = 0;
+      for (int r = 0; r < HP_DEC_SYMS; r++)
+        for (int k = 0; k < nw; k++) n += s_wc[r][k][tid];
+      s_cnt[tid] = n;
+    }
+    __syncthreads();
+    if (tid == 0) {  // canonical first codes and the gcd of the lengths in use
       uint32_t c = 0, idx = 0, g = 0;
-      for (int k = 0; k < nw; k++) {
-        uint32_t x = g, y = s_gw[k];
-        while (y) {
-          const uint32_t tt = x % y;
-          x = y;
-          y = tt;
-        }
-        g = x;
-      }
       for (int L = 1; L <= 16; L++) {
-        uint32_t n = 0;
-        for (int r = 0; r < HP_DEC_SYMS; r++)
-          for (int k = 0; k < nw; k++) n += s_wc[r][k][L];
+        const uint32_t n = s_cnt[L];
         T.count[L] = n;
         T.first[L] = c;
         T.index[L] = idx;
         idx += n;
         c = (c + n) << 1;
+        if (n) {
+          uint32_t x = g, y = (uint32_t)L;
+          while (y) {
+            const uint32_t tt = x % y;
+            x = y;
+            y = tt;
+          }
+          g = x;
+        }
       }
       T.count[0] = 0;
       s_flag = bad ? 1u : 0u;
@@ -1089,12 +1076,31 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     if (tid == 0) set_corrupt(meta);
     return;
   }
-  const uint32_t nbits = (w1 - w0) * 32, mw = (nbits + 31) / 32;
-  for (uint32_t i = tid; i < mw && i < HP_MAP_WORDS; i += NT) T.map[i] = 0;
+  const uint32_t nwords = w1 - w0, nbits = nwords * 32;
+  const uint32_t* gwords = reinterpret_cast<const uint32_t*>(stored + hdr) + w0;
+  const bool staged = nbits <= HP_MAP_WORDS * 32;  // always, for a valid chunk
+  if (staged) {  // the coded words to shared memory, 8 loads in flight per thread; map cleared
+    for (uint32_t i0 = 0; i0 < nwords; i0 += 8 * (uint32_t)NT) {
+      uint32_t v[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const uint32_t i = i0 + (uint32_t)(u * NT + tid);
+        v[u] = i < nwords ? gwords[i] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const uint32_t i = i0 + (uint32_t)(u * NT + tid);
+        if (i < nwords) {
+          T.words[i] = v[u];
+          T.map[i] = 0u;
+        }
+      }
+    }
+  }
   __syncthreads();
   BitReader rd;
-  rd.w = reinterpret_cast<const uint32_t*>(stored + hdr) + w0;
-  rd.nwords = w1 - w0;
+  rd.w = staged ? T.words : gwords;
+  rd.nwords = nwords;
   if (nbits > HP_MAP_WORDS * 32) {  // impossible for a valid chunk: one thread, then checks
     bool fail = false;
     if (tid == 0) fail = !huff_emit(T, rd, 0, len, dst, 0);
@@ -1154,28 +1160,36 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
   s_J[tid] = J;
   s_seg[tid] = jseg;
   s_t[tid] = 0xffffffffu;
-  const bool adjacent = __syncthreads_and(jseg == (uint32_t)tid + 1 || tid + 1 == NT) != 0;
+  // (a segment reaching the data end needs no successor)
+  const bool adjacent =
+      __syncthreads_and(jseg == (uint32_t)tid + 1 || tid + 1 == NT || s_next >= nbits) != 0;
   uint32_t t_me;
   if (adjacent) {  // the usual case: every segment joins the next one
     t_me = tid == 0 ? 0u : s_J[tid - 1];
   } else {
-    if (tid == 0) {
-      uint32_t c = 0, t = 0;
-      while (true) {
-        s_t[c] = t;
-        const uint32_t nx = s_seg[c];
-        if (nx >= (uint32_t)NT) break;
-        t = s_J[c];
-        c = nx;
-      }
+    // the chain from segment 0 by pointer doubling: after round r every segment
+    // within 2^(r+1) - 1 hand-overs of segment 0 is marked
+    __shared__ uint32_t s_on[HP_DEC_THREADS];
+    uint32_t p = jseg;
+    s_on[tid] = tid == 0 ? 1u : 0u;
+    __syncthreads();
+    for (int r = 0; (1 << r) < NT; r++) {
+      if (s_on[tid] && p < (uint32_t)NT) s_on[p] = 1u;
+      const uint32_t q = p < (uint32_t)NT ? s_seg[p] : (uint32_t)NT;
+      __syncthreads();
+      p = q;
+      s_seg[tid] = p;
+      __syncthreads();
     }
+    if (s_on[tid] && jseg < (uint32_t)NT) s_t[jseg] = J;  // the successor starts at the join
+    if (tid == 0) s_t[0] = 0u;
     __syncthreads();
     t_me = s_t[tid];
   }
   // true symbols of this segment's emit range: its own from t_me, then the
-  // continuation up to the join
+  // continuation up to the join (none for a segment past the data end)
   const uint32_t tc_me =
-      t_me == 0xffffffffu ? 0u : c_me - map_count(T.map, s_me, t_me) + dj;
+      (t_me == 0xffffffffu || s_me >= nbits) ? 0u : c_me - map_count(T.map, s_me, t_me) + dj;
   // ---- 4. output offsets and the final decoding
   uint32_t total_tc;
   const uint32_t o = block_exscan(tc_me, scratch, total_tc);
@@ -1361,7 +1375,7 @@ __device__ __forceinline__ void decode_item(const uint8_t* __restrict__ slots, F
   }
 }
 
-__global__ void __launch_bounds__(HP_DEC_THREADS) k_decode(const uint8_t* __restrict__ slots,
+__global__ void __launch_bounds__(HP_DEC_THREADS, 2) k_decode(const uint8_t* __restrict__ slots,
                                                            FieldMeta* meta,
                                                            const RetrieveDev* __restrict__ rd,
                                                            uint8_t* __restrict__ planes) {
@@ -1500,7 +1514,7 @@ void launch_b_items_prefix(const BatchJob* jobs, uint32_t njobs, uint32_t* unit0
   hp::note_launch(), kb_items_prefix<<<1, 32, 0, s>>>(jobs, njobs, unit0_out);
 }
 
-__global__ void __launch_bounds__(HP_DEC_THREADS) kb_decode(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(HP_DEC_THREADS, 2) kb_decode(const BatchJob* __restrict__ jobs,
                                                             const uint32_t* __restrict__ unit0,
                                                             uint32_t njobs) {
   extern __shared__ __align__(16) unsigned char dec_smem[];
