@@ -945,16 +945,21 @@ __device__ __forceinline__ uint32_t map_count(const uint32_t* map, uint32_t a, u
   return n;
 }
 
+// A run of zero bits at the reader is a run of the one-bit code "0" when the
+// code has one (canonical codes: the first code of length 1 is 0, symbol
+// sorted[0]); the passes below take up to 32 of its codewords at once.
+__device__ __forceinline__ uint32_t zero_run(const HuffTables& T, const BitReader& r,
+                                             uint32_t limit) {
+  if (T.count[1] == 0 || (r.buf >> 63)) return 0u;
+  return min(min((uint32_t)__clzll((long long)r.buf), 32u), limit);
+}
+
 // write the n symbols decoded from bit `pos` to dst[o ..)
 __device__ __forceinline__ bool huff_emit(const HuffTables& T, BitReader& rd, uint32_t pos,
                                           uint32_t n, uint8_t* __restrict__ dst, uint32_t o) {
   rd.init(pos);
   uint32_t acc = 0, p = o;
-  for (uint32_t k = 0; k < n; k++, p++) {
-    uint32_t sym;
-    const int L = huff_sym(T, rd, sym);
-    if (!L) return false;
-    rd.consume(L);
+  auto put = [&](uint32_t sym) {
     acc |= sym << (8 * (p & 3));
     if ((p & 3) == 3) {
       if (p - 3 >= o) reinterpret_cast<uint32_t*>(dst)[p >> 2] = acc;
@@ -962,6 +967,23 @@ __device__ __forceinline__ bool huff_emit(const HuffTables& T, BitReader& rd, ui
         for (uint32_t q = o; q <= p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
       acc = 0;
     }
+    p++;
+  };
+  const uint32_t z0 = T.sorted[0];
+  for (uint32_t k = 0; k < n;) {
+    const uint32_t run = zero_run(T, rd, n - k);
+    if (run) {
+      for (uint32_t q = 0; q < run; q++) put(z0);
+      rd.consume((int)run);
+      k += run;
+      continue;
+    }
+    uint32_t sym;
+    const int L = huff_sym(T, rd, sym);
+    if (!L) return false;
+    rd.consume(L);
+    put(sym);
+    k++;
   }
   if (p & 3)
     for (uint32_t q = max(o, p & ~3u); q < p; q++) dst[q] = (uint8_t)(acc >> (8 * (q & 3)));
@@ -1118,6 +1140,16 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     uint32_t pos = s_me;
     rd.init(pos);
     while (pos < s_next) {
+      const uint32_t run = zero_run(T, rd, s_next - pos);
+      if (run) {  // run starts pos .. pos + run - 1, all before s_next
+        const uint64_t m = ((1ull << run) - 1ull) << (pos & 31);
+        atomicOr(&T.map[pos >> 5], (uint32_t)m);
+        if (m >> 32) atomicOr(&T.map[(pos >> 5) + 1], (uint32_t)(m >> 32));
+        rd.consume((int)run);
+        pos += run;
+        c_me += run;
+        continue;
+      }
       uint32_t sym;
       const int L = huff_sym(T, rd, sym);
       if (!L) break;
@@ -1138,6 +1170,22 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     uint32_t p = e_me, k = tid + 1;  // k: the segment holding p
     tr.init(p);
     while (p < nbits) {
+      const uint32_t run = zero_run(T, tr, nbits - p);
+      if (run) {  // the first marked start among the run's, if any
+        const uint32_t wi = p >> 5;
+        const uint64_t two = (uint64_t)T.map[wi] | (wi + 1 < nwords ? (uint64_t)T.map[wi + 1] << 32 : 0ull);
+        const uint64_t hit = (two >> (p & 31)) & ((1ull << run) - 1ull);
+        const uint32_t adv = hit ? (uint32_t)(__ffsll((long long)hit) - 1) : run;
+        p += adv;
+        dj += adv;
+        if (hit) {
+          while (k + 1 < (uint32_t)NT && p >= seg_start(k + 1)) k++;
+          jseg = k;
+          break;
+        }
+        tr.consume((int)run);
+        continue;
+      }
       while (k + 1 < (uint32_t)NT && p >= seg_start(k + 1)) k++;
       if ((T.map[p >> 5] >> (p & 31)) & 1u) {
         jseg = k;
