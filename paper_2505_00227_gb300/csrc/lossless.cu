@@ -884,7 +884,6 @@ struct HuffTables {
   uint32_t fill[17];
   uint8_t sorted[256];
   uint32_t map[HP_MAP_WORDS];      // codeword starts of the speculative decodings
-  uint32_t words[HP_MAP_WORDS];    // the chunk's coded words, staged from global memory
 };
 
 struct BitReader {
@@ -1099,29 +1098,10 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     return;
   }
   const uint32_t nwords = w1 - w0, nbits = nwords * 32;
-  const uint32_t* gwords = reinterpret_cast<const uint32_t*>(stored + hdr) + w0;
-  const bool staged = nbits <= HP_MAP_WORDS * 32;  // always, for a valid chunk
-  if (staged) {  // the coded words to shared memory, 8 loads in flight per thread; map cleared
-    for (uint32_t i0 = 0; i0 < nwords; i0 += 8 * (uint32_t)NT) {
-      uint32_t v[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const uint32_t i = i0 + (uint32_t)(u * NT + tid);
-        v[u] = i < nwords ? gwords[i] : 0u;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const uint32_t i = i0 + (uint32_t)(u * NT + tid);
-        if (i < nwords) {
-          T.words[i] = v[u];
-          T.map[i] = 0u;
-        }
-      }
-    }
-  }
+  for (uint32_t i = tid; i < nwords && i < HP_MAP_WORDS; i += NT) T.map[i] = 0u;
   __syncthreads();
   BitReader rd;
-  rd.w = staged ? T.words : gwords;
+  rd.w = reinterpret_cast<const uint32_t*>(stored + hdr) + w0;
   rd.nwords = nwords;
   if (nbits > HP_MAP_WORDS * 32) {  // impossible for a valid chunk: one thread, then checks
     bool fail = false;
@@ -1423,7 +1403,7 @@ __device__ __forceinline__ void decode_item(const uint8_t* __restrict__ slots, F
   }
 }
 
-__global__ void __launch_bounds__(HP_DEC_THREADS, 2) k_decode(const uint8_t* __restrict__ slots,
+__global__ void __launch_bounds__(HP_DEC_THREADS) k_decode(const uint8_t* __restrict__ slots,
                                                            FieldMeta* meta,
                                                            const RetrieveDev* __restrict__ rd,
                                                            uint8_t* __restrict__ planes) {
@@ -1562,7 +1542,7 @@ void launch_b_items_prefix(const BatchJob* jobs, uint32_t njobs, uint32_t* unit0
   hp::note_launch(), kb_items_prefix<<<1, 32, 0, s>>>(jobs, njobs, unit0_out);
 }
 
-__global__ void __launch_bounds__(HP_DEC_THREADS, 2) kb_decode(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(HP_DEC_THREADS) kb_decode(const BatchJob* __restrict__ jobs,
                                                             const uint32_t* __restrict__ unit0,
                                                             uint32_t njobs) {
   extern __shared__ __align__(16) unsigned char dec_smem[];
