@@ -1432,16 +1432,15 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   set_smem_once((const void*)k_decode, (int)smem);
   // one wave of resident CTAs: every CTA decodes the same number of consecutive
   // chunks, so CTAs beyond the resident ones would double the launch's time
-  static int resident = 0;
-  if (!resident) {
+  static const int resident = [smem] {  // (thread-safe one-time initialisation)
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode, HP_DEC_THREADS, smem) !=
             cudaSuccess || per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
     }
-    resident = per_sm;
-  }
+    return per_sm;
+  }();
   uint32_t blocks = max_items, cap = (uint32_t)sms * (uint32_t)resident;
   if (blocks > cap) blocks = cap;
   hp::note_launch(), k_decode<<<blocks, HP_DEC_THREADS, smem, s>>>(slots, meta, rd, planes);
