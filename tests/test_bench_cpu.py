@@ -69,3 +69,26 @@ def test_replicas_take_the_slowest_rank_gloo():
     for rank, t, v in out:
         assert t == 2.0  # the slower rank's time on every rank
         assert v == pytest.approx(2 * 2e9 / 2.0 / 1e9)
+
+
+def test_traffic_figure_keyed_on_source_hashes(tmp_path, monkeypatch):
+    """The DRAM traffic figure of the bench line is reported only while the
+    kernel's file and every header listed beside it are unchanged."""
+    import hashlib
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    csrc = tmp_path / "paper_2505_00227_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cu").write_bytes(b"kernel")
+    (csrc / "h.cuh").write_bytes(b"header")
+    sha = {n: hashlib.sha256((csrc / n).read_bytes()).hexdigest() for n in ("k.cu", "h.cuh")}
+    (tmp_path / "profiles" / "traffic.json").write_text(
+        json.dumps({"k": {"source_sha256": sha, "dram_bytes_per_launch": 123}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for("k") == 123.0
+    assert bench.traffic_for("other") is None
+    (csrc / "h.cuh").write_bytes(b"header, changed")
+    assert bench.traffic_for("k") is None
