@@ -1011,8 +1011,8 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
     if (tid == 0) set_corrupt(meta);
     return;
   }
-  // ---- 1. decoding tables (warp 0), the gcd of the code lengths; kept from
-  // the previous chunk when that one belonged to the same group
+  // ---- 1. decoding tables (all threads), the gcd of the code lengths; kept
+  // from the previous chunk when that one belonged to the same group
   __shared__ uint32_t s_flag, s_gl;
   if (!tables_ready) {
     // thread tid takes symbols tid + r NT (r < HP_DEC_SYMS): lengths counted per
@@ -1114,7 +1114,7 @@ __device__ void huff_decode_chunk(const uint8_t* __restrict__ stored, const Grou
   auto seg_start = [&](int i) -> uint32_t {
     return i >= NT ? nbits : min((uint32_t)i * seg, nbits) / gl * gl;
   };
-  const uint32_t s_me = seg_start(tid), s_next = seg_start(tid + 1), s_next2 = seg_start(tid + 2);
+  const uint32_t s_me = seg_start(tid), s_next = seg_start(tid + 1);
   uint32_t c_me = 0, e_me = s_me;
   {
     uint32_t pos = s_me;
