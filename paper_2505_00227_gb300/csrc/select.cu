@@ -213,7 +213,10 @@ __device__ u128 tau_units(double tau, int E_f, int B) {
 // One warp: the prefix by binary search (lane 0), the groups per level by
 // counting the prefix's entries (all lanes), the per-level bytes by lane =
 // level, and the list of chunks to decode in (level, group) order (lane 0).
-__device__ void select_prefix(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* rd) {
+// m: the metadata read (a shared-memory copy, or the field's own); mw: the
+// field's metadata, where the fetched state is updated.
+__device__ void select_prefix(const FieldMeta* m, FieldMeta* mw, double tau, int tau_is_abs,
+                              RetrieveDev* rd) {
   __shared__ int s_g[HP_MAX_LEVELS + 1];
   __shared__ int s_c;
   const int lane = threadIdx.x & 31;
@@ -328,18 +331,45 @@ __device__ void select_prefix(FieldMeta* m, double tau, int tau_is_abs, Retrieve
   __syncwarp();
   for (int l = lane; l < nlev; l += 32) {  // after lane 0 has read the old state
     const int gl = s_g[l];
-    if (gl > m->fetched[l]) m->fetched[l] = gl;
-    m->cur[l] = gl;
+    if (gl > m->fetched[l]) mw->fetched[l] = gl;
+    mw->cur[l] = gl;
     rd->g[l] = gl;
   }
 }
 
-__global__ void k_select(FieldMeta* m, double tau, int tau_is_abs, RetrieveDev* rd) {
-  select_prefix(m, tau, tau_is_abs, rd);
+// The field's metadata is first copied to shared memory by the whole CTA (16-byte
+// units, 8 loads in flight per thread), so that the warp's chain of dependent
+// reads (estimates, sequence, fetched state, group sizes) runs on shared memory.
+__global__ void __launch_bounds__(256) k_select(FieldMeta* m, double tau, int tau_is_abs,
+                                                RetrieveDev* rd) {
+  extern __shared__ __align__(16) unsigned char sel_smem[];
+  FieldMeta* sm = reinterpret_cast<FieldMeta*>(sel_smem);
+  constexpr uint32_t N16 = sizeof(FieldMeta) / 16, N8 = (sizeof(FieldMeta) % 16) / 8;
+  const uint4* src = reinterpret_cast<const uint4*>(m);
+  uint4* dst = reinterpret_cast<uint4*>(sm);
+  for (uint32_t i0 = 0; i0 < N16; i0 += 8 * blockDim.x) {
+    uint4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint32_t i = i0 + u * blockDim.x + threadIdx.x;
+      if (i < N16) v[u] = src[i];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint32_t i = i0 + u * blockDim.x + threadIdx.x;
+      if (i < N16) dst[i] = v[u];
+    }
+  }
+  if (threadIdx.x < N8)
+    reinterpret_cast<uint64_t*>(sm)[2 * N16 + threadIdx.x] =
+        reinterpret_cast<const uint64_t*>(m)[2 * N16 + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x < 32) select_prefix(sm, m, tau, tau_is_abs, rd);
 }
 
 void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s) {
-  hp::note_launch(), k_select<<<1, 32, 0, s>>>(meta, tau, tau_is_abs, rd);
+  set_smem_once((const void*)k_select, (int)sizeof(FieldMeta));
+  hp::note_launch(), k_select<<<1, 256, sizeof(FieldMeta), s>>>(meta, tau, tau_is_abs, rd);
 }
 
 // ------------------------------------------------------------------ batched
@@ -354,7 +384,7 @@ void launch_b_sequence(const BatchJob* jobs, uint32_t njobs, cstream s) {
 
 __global__ void kb_select(const BatchJob* __restrict__ jobs) {
   const BatchJob& J = jobs[blockIdx.x];
-  select_prefix(J.meta, J.tau, 0, J.rd);
+  select_prefix(J.meta, J.meta, J.tau, 0, J.rd);
 }
 
 void launch_b_select(const BatchJob* jobs, uint32_t njobs, cstream s) {
