@@ -138,6 +138,20 @@ def job_throughput(bytes_per_rank, seconds_max, world):
     return world * bytes_per_rank / seconds_max / 1e9
 
 
+def stored_bytes(binding, h):
+    """Sum of a handle's stored group lengths (coded or direct-copy), read from
+    its metadata without copying the bytes."""
+    import ctypes as C
+    total = 0
+    for l in range(h.field_info()["nlevels"]):
+        for g in range(h.level_info(l)[2]):
+            ln, m = C.c_uint64(), C.c_int()
+            binding.lib().hpmdr_handle_group(h._p, l, g, None, C.byref(ln), C.byref(m),
+                                             (C.c_uint64 * 2)())
+            total += ln.value
+    return total
+
+
 # ------------------------------------------------------------- CPU oracle
 def oracle_step(f_np):
     from oracle import pyoracle as O
@@ -654,6 +668,29 @@ def bench_pipeline(args, binding):
             "stored_bytes": stored, "status": st}
 
 
+# ------------------------------------------------- one step for ncu captures
+def run_profile_step(args):
+    """One refactor + six incremental retrievals of the benchmark's field
+    (size --size), nothing timed and no JSON line: the command that ncu
+    captures, so that a profile holds one step's launches and little else."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2505_00227_gb300 import binding
+    torch.cuda.set_device(0)
+    field = make_field(args.size, 2, "cuda")
+    ctx = binding.Context()
+    out = torch.empty_like(field)
+    torch.cuda.synchronize()
+    for _ in range(args.profile_steps):
+        h = ctx.refactor(field)
+        for tau in TAUS:
+            h.retrieve(tau, out=out)
+        h.free()
+    torch.cuda.synchronize()
+    print(f"profile step ok: {args.profile_steps} step(s) of the {args.size}^3 field", flush=True)
+
+
 # -------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -698,6 +735,9 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    h0 = ctx.refactor(field)
+    stored = stored_bytes(binding, h0)  # the same for every step: same field, same coder
+    h0.free()
 
     # ---- per-stage breakdown: a pass of its own with an event pair around
     # every stage (about 40 pairs per step, which would stretch the timed step)
@@ -821,7 +861,15 @@ def run_ours(args):
                     "gbs": round(p[3] / (p[1] * 1e-3) / 1e9, 1) if p[3] > 0 and p[1] > 0 else None}
                    for p in sorted(stages, key=lambda p: -p[1])]
         fetched = [i.bytes_fetched_total for i in last_infos]
-        alg_refactor = fbytes  # the field is read once; stored bytes are written below
+        # the method's bytes of each phase (the field read and the stored groups
+        # written; the newly fetched stored groups read and six fields written)
+        # over the phase's time, against the measured copy bandwidth
+        alg_refactor = fbytes + stored
+        alg_retrieve = fetched[-1] + 6 * fbytes
+        phases = {"refactor_frac": round(alg_refactor / (refactor_ms * 1e-3) / 1e9 / peak, 4),
+                  "retrieve_frac": round(alg_retrieve / (retrieve_ms * 1e-3) / 1e9 / peak, 4),
+                  "refactor_bytes": alg_refactor, "retrieve_bytes": alg_retrieve,
+                  "peak": peak, "peak_kind": peak_kind}
         cpu = None
         cpu_par = None
         if world == 1 and not args.no_cpu_baseline:
@@ -860,7 +908,8 @@ def run_ours(args):
             "refactor_gbs": round(fbytes / (refactor_ms * 1e-3) / 1e9, 3),
             "retrieve_gbs": round(6 * fbytes / (retrieve_ms * 1e-3) / 1e9, 3),
             "refactor_ms": round(refactor_ms, 4), "retrieve_ms": round(retrieve_ms, 4),
-            "retrieved_bytes_total": fetched, "roofline": roof, "kernels": kernels,
+            "retrieved_bytes_total": fetched, "stored_bytes": stored, "roofline": roof,
+            "phase_roofline": phases, "kernels": kernels,
             "kernels_from": "a pass of the same steps with events around every stage "
                             "(the timed region records only the dominant kernel's)",
             "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_par,
@@ -903,7 +952,13 @@ def main():
     ap.add_argument("--batch-fields", type=int, default=256)
     ap.add_argument("--stream-shape", type=int, nargs=3, default=[1024, 1024, 512])
     ap.add_argument("--stream-steps", type=int, default=2)
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run --profile-steps untimed steps for an ncu capture and exit")
+    ap.add_argument("--profile-steps", type=int, default=1)
     args = ap.parse_args()
+    if args.profile_step:
+        run_profile_step(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

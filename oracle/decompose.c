@@ -257,66 +257,6 @@ void or_level_coeffs(const void* f, const uint64_t dims[3], int dtype, int E_f, 
   for_each_node(dims, l, coeff_node, &c);
 }
 
-typedef struct {
-  const void* f;
-  const uint64_t* dims;
-  int dtype, E_f;
-  uint64_t maxmag;
-} max_ctx;
-
-static void max_node(void* vctx, uint64_t j, const stencil* s) {
-  max_ctx* c = (max_ctx*)vctx;
-  int64_t C8;
-  coeff_ctx cc = {c->f, c->dims, c->dtype, c->E_f, &C8};
-  (void)j;
-  coeff_node(&cc, 0, s);
-  uint64_t m = C8 < 0 ? (uint64_t)(-C8) : (uint64_t)C8;
-  if (m > c->maxmag) c->maxmag = m;
-}
-
-/* bit length of max|C8| over level l, without storing the level */
-int or_level_bitlen(const void* f, const uint64_t dims[3], int dtype, int E_f, int l) {
-  if (l == 0) {
-    int64_t C8;
-    or_level_coeffs(f, dims, dtype, E_f, 0, &C8);
-    return bitlen64(C8 < 0 ? (uint64_t)(-C8) : (uint64_t)C8);
-  }
-  max_ctx c = {f, dims, dtype, E_f, 0};
-  for_each_node(dims, l, max_node, &c);
-  return bitlen64(c.maxmag);
-}
-
-/* C8 of the single node j of level l (j in the level's linear order) */
-int64_t or_node_coeff(const void* f, const uint64_t dims[3], int dtype, int E_f, int l, uint64_t j) {
-  int64_t C8 = 0;
-  if (l == 0) {
-    or_level_coeffs(f, dims, dtype, E_f, 0, &C8);
-    return C8;
-  }
-  uint64_t h = half_stride(dims, l), g[3];
-  for (int d = 0; d < 3; d++) g[d] = (dims[d] + h - 1) / h;
-  for (int t = 1; t < 8; t++) {
-    int odd[3] = {(t >> 2) & 1, (t >> 1) & 1, t & 1};
-    uint64_t cz = axis_count(g[0], odd[0]), cy = axis_count(g[1], odd[1]),
-             cx = axis_count(g[2], odd[2]);
-    uint64_t cnt = cz * cy * cx;
-    if (j >= cnt) {
-      j -= cnt;
-      continue;
-    }
-    stencil s;
-    uint64_t c = j % cx, b = (j / cx) % cy, a = j / (cx * cy);
-    s.i[0] = h * (2 * a + (uint64_t)odd[0]);
-    s.i[1] = h * (2 * b + (uint64_t)odd[1]);
-    s.i[2] = h * (2 * c + (uint64_t)odd[2]);
-    make_stencil(dims, h, odd, &s);
-    coeff_ctx cc = {f, dims, dtype, E_f, &C8};
-    coeff_node(&cc, 0, &s);
-    return C8;
-  }
-  return 0;
-}
-
 /* ------------------------------------------------------- recomposition */
 
 /* floor(a / 2^s) for signed a, written without relying on >> of negatives */

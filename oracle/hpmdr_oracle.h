@@ -54,9 +54,6 @@ int64_t or_fixed_point(const void* f, uint64_t i, int dtype, int E_f, int* floor
 void or_level_coeffs(const void* f, const uint64_t dims[3], int dtype, int E_f,
                      int l, int64_t* C8);
 
-/* bit length of max|C8| over level l, streamed; C8 of one node of level l */
-int     or_level_bitlen(const void* f, const uint64_t dims[3], int dtype, int E_f, int l);
-int64_t or_node_coeff(const void* f, const uint64_t dims[3], int dtype, int E_f, int l, uint64_t j);
 
 /* ---- exponent alignment + Algorithm 1 ----------------------------------- */
 int  or_bitlen_max(const int64_t* C8, uint64_t n);          /* bl = bitlen(max|C8|) */

@@ -57,8 +57,6 @@ def lib():
             "or_fixed_point": (C.c_int64, [cvp, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_int)]),
             "or_level_coeffs": (None, [cvp, dims_t, C.c_int, C.c_int, C.c_int, vp]),
             "or_bitlen_max": (C.c_int, [vp, C.c_uint64]),
-            "or_level_bitlen": (C.c_int, [cvp, dims_t, C.c_int, C.c_int, C.c_int]),
-            "or_node_coeff": (C.c_int64, [cvp, dims_t, C.c_int, C.c_int, C.c_int, C.c_uint64]),
             "or_quantize": (None, [vp, C.c_uint64, C.c_int, C.c_int, vp, vp]),
             "or_level_exact": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int]),
             "or_bitplane_encode": (None, [vp, vp, C.c_uint64, C.c_int, vp]),
@@ -166,16 +164,6 @@ def level_coeffs(f, E_f, l):
     out = np.zeros(n, dtype=np.int64)
     lib().or_level_coeffs(_p(f), _dims(f.shape), _dtype_code(f), E_f, l, _p(out))
     return out
-
-
-def level_bitlen(f, E_f, l):
-    f = np.ascontiguousarray(f)
-    return lib().or_level_bitlen(_p(f), _dims(f.shape), _dtype_code(f), E_f, l)
-
-
-def node_coeff(f, E_f, l, j):
-    f = np.ascontiguousarray(f)
-    return int(lib().or_node_coeff(_p(f), _dims(f.shape), _dtype_code(f), E_f, l, j))
 
 
 def bitlen_max(C8):

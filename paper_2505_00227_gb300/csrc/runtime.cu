@@ -779,7 +779,12 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
   return HPMDR_OK;
 }
 
-// algorithmic bytes of a retrieval's stages, once its selection is known
+// algorithmic bytes of a retrieval's stages, once its selection is known: the
+// stored bytes a decode reads and the plane bytes it writes; for the
+// recomposition, the plane words of the selected groups a launch reads and
+// the values it writes.  The int64 coarse grids a level reads and the staging
+// of the general cell levels are intermediates of this implementation, not
+// bytes of the method: they appear in the measured DRAM traffic only.
 static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const RetrieveDev& rd,
                                  const std::vector<std::pair<size_t, int>>& prof_lv,
                                  size_t prof_decode, size_t prof_small, int small_end) {
@@ -792,21 +797,19 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
     dec += (double)G.stored_len + (double)G.S;
   }
   ctx->prof.patch(prof_decode, dec);
-  {  // small levels: their planes, coarse grids and outputs
+  {  // small levels: their planes and the values they write
     double b = 0;
     for (int l = 1; l <= small_end; l++) {
       const LevelDesc& D = H->levels[l];
       const double coarse = (double)D.gc[0] * D.gc[1] * D.gc[2];
       const double osz = l == H->nlev - 1 ? esz : 8.0;
       const int g = rd.g[l];
-      b += (g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0) + coarse * 8.0 +
-           ((double)D.n + coarse) * osz;
+      b += (g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0) + ((double)D.n + coarse) * osz;
     }
     ctx->prof.patch(prof_small, b);
   }
   size_t last = SIZE_MAX;
   double last_b = 0;
-  const double qb = H->B / 8 + 1;  // staged bytes per node of a general cell level
   for (auto& pe : prof_lv) {
     const int l = pe.second / 8, kind = pe.second % 8;
     const LevelDesc& D = H->levels[l];
@@ -815,14 +818,14 @@ static void patch_retrieve_bytes(hpmdr_ctx* ctx, hpmdr_handle* H, const Retrieve
     const int g = rd.g[l];
     const double planes = g > 0 ? (double)(4 * g + 1) * D.W * 4.0 : 0.0;
     double b;
-    if (kind == 0 || kind == 2) {
-      b = coarse * 8.0 + coarse * osz;
+    if (kind == 0 || kind == 2) {  // the coarse nodes copied into the level grid
+      b = coarse * osz;
     } else if (kind == 4) {  // planes -> staging
-      b = planes + qb * D.n;
+      b = planes;
     } else if (kind >= 5) {  // staging + coarse grid -> level grid (coarse nodes included)
-      b = qb * D.n + coarse * 8.0 + ((double)D.n + coarse) * osz;
-    } else {
-      b = planes + coarse * 8.0 + (double)D.n * osz;
+      b = ((double)D.n + coarse) * osz;
+    } else {  // planes + coarse grid -> the level's nodes
+      b = planes + (double)D.n * osz;
     }
     if (pe.first == SIZE_MAX - 1) {  // a cell kernel also wrote the coarse nodes
       last_b += coarse * osz;

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 SHAPES = [(33, 20, 64), (17, 23, 30), (9, 40, 128), (32, 32, 32), (5, 7, 200), (1, 64, 128),
           (12, 100, 9), (40, 37, 192), (3, 3, 3), (1, 1, 1), (2, 64, 64), (20, 24, 40),
-          (45, 47, 49), (30, 50, 70)]
+          (45, 47, 49), (30, 50, 70), (3, 9, 512), (2, 5, 1024)]
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +82,7 @@ def _check_retrieve(batch, fs, taus, outs, infos, st):
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_batch_matches_oracle_and_plain_path(B, dtype):
-    shapes = SHAPES if dtype == torch.float32 else SHAPES[:6] + SHAPES[-2:]
+    shapes = SHAPES if dtype == torch.float32 else SHAPES[:6] + SHAPES[-4:]
     ctx, fs, dev, batch = _run(B, dtype, shapes)
     _check_refactor(batch, fs)
     prev = [0] * len(fs)

@@ -59,6 +59,15 @@ def _fields():
         "cells_2d": S.blobs((1, 64, 128), seed=13).numpy(),
         "cells_three_words": S.spectral((5, 9, 192), seed=14).numpy(),
         "cells_256": S.spectral((24, 40, 256), seed=15).numpy(),
+        # level x-extent 512, 1024 and 1536: the finest level takes the widest cell
+        # tile (8 plane words, 256 cells per row of a tile, 4 rows), the tile of the
+        # 512^3 field's finest level; 37 and 9 rows leave a ragged last row of tiles,
+        # 1024 and 1536 put two and three tiles along x
+        "cells_512": S.spectral((4, 6, 512), seed=25).numpy(),
+        "cells_512_ragged": S.spectral((6, 37, 512), seed=28).numpy(),
+        "cells_512_blobs": S.blobs((2, 9, 512), seed=27).numpy(),
+        "cells_1024": S.spectral((3, 5, 1024), seed=26).numpy(),
+        "cells_1536": S.spectral((2, 7, 1536), seed=29).numpy(),
         # a level maximum exactly at a power of two (C8 = 2^50): the FP32 estimate of
         # the level maximum is ambiguous there and the exact pass must decide
         "cells_power_of_two": _spike((8, 8, 128), (3, 5, 77), 2.0 ** -10),
