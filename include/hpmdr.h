@@ -418,16 +418,20 @@ HPMDR_API hpmdr_status hpmdr_decode_group(hpmdr_ctx* ctx, const uint8_t* in, uin
  * or an E_f no field of the type has (FP32: -148..128, FP64: -1073..1024). */
 HPMDR_API hpmdr_status hpmdr_fixed_to_float(hpmdr_ctx* ctx, const int64_t* X, uint64_t n, int E_f,
                                             hpmdr_dtype dtype, void* out);
-/* hpmdr_encode_group for callers that cannot allocate device memory (a
- * solver that owns all of HBM, or that forbids cudaMalloc/cudaFree between
- * steps because they may synchronize the device).  No counterpart in the
- * paper: it is the same Algorithm 2 encoder, bit for bit, but its scratch is a
- * static device array of about 70 KB held by every GPU that loads the
- * library until exit.  G (device, 16-byte aligned) holds S <= 16 MiB bytes;
- * larger groups give HPMDR_ERR_ARG.  size_threshold / cr_num / cr_den are the
- * T_s and T_cr of Algorithm 2 (0 = defaults).  The first call on a device looks
- * up the array's address (make it before any stream capture).  Calls share the
- * array: overlapping calls on the GPU race and must be serialized. */
+/* hpmdr_encode_group for callers that cannot allocate device memory: a
+ * solver that owns all of HBM, or one that forbids cudaMalloc/cudaFree between
+ * steps because they may synchronize the device.  The paper has no
+ * counterpart: this is the encoder of hpmdr_encode_group, bit for bit (same
+ * method choice, same stored bytes), with its scratch in a static device
+ * array of about 70 KB that every GPU loading the library holds until exit.
+ * G (device, 16-byte aligned) holds S <= 16 MiB bytes; larger groups give
+ * HPMDR_ERR_ARG.  size_threshold / cr_num / cr_den are hpmdr_encode_group's
+ * size and ratio thresholds (the hpmdr_config fields of the same names;
+ * 0 = defaults).  out (device) has cap bytes; the coded bytes not fitting
+ * gives HPMDR_ERR_ARG.  The call is synchronous: it waits on `stream` before
+ * returning.  The first call on a device looks up the array's address; make
+ * it before any stream capture.  Calls share the array, which keeps the last
+ * call's contents: calls that overlap on the GPU race and must be serialized. */
 HPMDR_API hpmdr_status hpmdr_encode_group_noalloc(const uint8_t* G, uint64_t S, int force,
                                                   uint64_t size_threshold, uint32_t cr_num,
                                                   uint32_t cr_den, uint8_t* out, uint64_t cap,

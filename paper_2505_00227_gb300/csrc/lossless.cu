@@ -12,8 +12,9 @@
 //   DC:      the group bytes as they are (they stay in the plane buffer).
 //
 // GPU mapping: one CTA per 16 KiB chunk for statistics and encoding (chunk in
-// shared memory), one CTA per group for the decision, one warp per chunk for
-// decoding.  No inter-CTA waits anywhere.
+// shared memory), one CTA per group for the decision, one CTA of 512 threads
+// per chunk for decoding (512 speculative Huffman segments; an RLE chunk is
+// decoded by the CTA's first warp).  No inter-CTA waits anywhere.
 #include "dev_common.cuh"
 
 namespace hp {
@@ -847,34 +848,40 @@ void launch_headers(FieldMeta* meta, int ngroups_total, const uint8_t* lens,
 }
 
 // ================================================================ decoding
-// One warp per queued chunk.  Every read of the stored bytes is checked
-// against the group's stored length; a failed check sets status CORRUPT and
-// abandons the chunk (no trap).
+// One CTA of HP_DEC_THREADS threads per queued chunk (a Huffman chunk takes
+// all of them, an RLE chunk the first warp).  Every read of the stored
+// bytes is checked against the group's stored length; a failed check sets
+// status CORRUPT and abandons the chunk (no trap).
 __device__ __forceinline__ void set_corrupt(FieldMeta* meta) { atomicExch(&meta->status, -4); }
 
-// Huffman decoding of one chunk by one warp, self-synchronizing:
-//  1. tables: canonical first code / count / sorted symbols per length (a
-//     counting sort by warp ballots) and a 10-bit lookup table for short codes;
-//  2. the chunk's bits are cut into 32 equal segments; lane i decodes from the
-//     start of its segment (maybe mid-codeword) up to the first codeword start
-//     at or beyond the next segment, marking every codeword start it visits in
-//     a bitmap of the chunk's bits (segments do not overlap, so each lane owns
-//     the marks of its segment);
-//  3. lane by lane, the true path enters segment i at t (the end of lane i-1's
-//     true decoding); lane i follows it until it lands on a marked bit, from
-//     where its speculative decoding is the true one (Huffman codes
-//     resynchronize), so its count is the codewords walked plus the marks from
-//     there on; if the walk leaves the segment first, the walk itself is the
-//     lane's true decoding;
-//  4. a prefix sum of the true counts gives each lane its output offset and
-//     every lane decodes its own span again, writing the bytes.
+// Huffman decoding of one chunk by one CTA, self-synchronizing:
+//  1. tables, built by all threads: canonical first code / count / sorted
+//     symbols per length (lengths counted per warp with warp matches, ranks
+//     among equal lengths from those counts) and a 10-bit lookup table for
+//     short codes; a CTA keeps a group's tables across consecutive chunks;
+//  2. the chunk's bits are cut into HP_DEC_THREADS segments whose starts lie on
+//     the lattice of the gcd of the code lengths; thread i decodes from the
+//     start of its segment (maybe mid-codeword) to the first codeword start at
+//     or beyond the next segment, marking every start it visits in a bitmap
+//     of the chunk's bits (runs of the one-bit code are taken up to 32
+//     codewords at a time);
+//  3. each thread's parse then continues past its segment until it lands on a
+//     start marked by a later segment (from there both parses agree: Huffman
+//     codes resynchronize) or runs off the data: its join point;
+//  4. the true parse is segment 0's and hands over at each join to the segment
+//     holding it.  When every segment joins the next one the emit ranges
+//     follow at once; otherwise the chain of hand-overs from segment 0 is found
+//     by pointer doubling.  Each chain segment counts its codewords from its
+//     true start through its join, a prefix sum gives the output offsets, and
+//     each chain segment decodes its span again, writing the bytes.
 // The bitmap covers the longest possible chunk (16384 codes of 16 bits); a
-// chunk claiming more bits is decoded by one lane and then fails its checks.  All reads stay inside the chunk's words; an
-// invalid code or a wrong symbol count marks the data corrupt.
+// chunk claiming more bits is decoded by one thread and then fails its checks.
+// All reads stay inside the chunk's words; an invalid code or a wrong symbol
+// count marks the data corrupt.
 #define HP_DEC_THREADS 512  // threads per decoded chunk: one speculative segment each
 #define HP_DEC_SYMS ((256 + HP_DEC_THREADS - 1) / HP_DEC_THREADS)  // symbols per thread (tables)
 #define HP_LUT_BITS 10
-#define HP_MAP_WORDS 8192  // bitmap of 262144 bit positions per warp: 16 bits x 16384 symbols
+#define HP_MAP_WORDS 8192  // bitmap of 262144 bit positions per chunk: 16 bits x 16384 symbols
 
 struct HuffTables {
   uint16_t lut[1 << HP_LUT_BITS];  // (len << 8) | symbol for codes of <= 10 bits, 0 otherwise

@@ -1,5 +1,6 @@
-// hpmdr_encode_group_noalloc: the Algorithm 2 group encoder (hybrid Huffman /
-// RLE / direct copy) for callers that cannot allocate device memory.
+// hpmdr_encode_group_noalloc: the hybrid group encoder of hpmdr_encode_group
+// (Huffman / RLE / direct copy, the same bytes and the same method choice) for
+// callers that cannot allocate device memory.
 //
 // Who needs it: code that compresses from inside a memory regime it does not
 // own, for example a simulation that reserved all of HBM for its own arena
@@ -18,6 +19,8 @@
 //   - the first call on each device looks up the array's device address with
 //     cudaGetSymbolAddress (with that device current); make that first call
 //     before any stream capture;
+//   - the call is synchronous: it waits on its stream for the status, the
+//     method and the stored length before it returns;
 //   - all calls share the one array and it keeps the last call's contents, so
 //     calls that overlap on the GPU (other streams, other host threads) race
 //     and must be serialized by the caller.
@@ -112,6 +115,9 @@ extern "C" hpmdr_status hpmdr_encode_group_noalloc(const uint8_t* G, uint64_t S,
   const cudaStream_t s = (cudaStream_t)stream;
   const uint32_t nc = (uint32_t)((S + HP_CHUNK - 1) / HP_CHUNK);
   hp::note_launch(), k_noalloc_init<<<1, 256, 0, s>>>(sc, S, cap, nc);
+  // a failed launch would leave the previous call's metadata in the array, and
+  // its status, method and length would be read back as this call's
+  if (cudaGetLastError() != cudaSuccess) return HPMDR_ERR_CUDA;
   ChunkMap cm{sc->chunk_group, nc};
   FieldMeta* m = &sc->meta;
   launch_chunk_stats(G, m, cm, sc->hist, &sc->cost, sc->chunk_cost, s);
@@ -121,6 +127,7 @@ extern "C" hpmdr_status hpmdr_encode_group_noalloc(const uint8_t* G, uint64_t S,
   launch_huff_encode(G, m, cm, sc->lens, sc->off, out, s);
   launch_rle_encode(G, m, cm, sc->off, out, s);
   launch_headers(m, 1, sc->lens, sc->off, out, s);
+  if (cudaGetLastError() != cudaSuccess) return HPMDR_ERR_CUDA;
   int32_t mstatus = 0, meth = 0;
   uint64_t stored = 0;
   if (cudaMemcpyAsync(&mstatus, &m->status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
