@@ -65,12 +65,15 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
   const bool hz = Z0 + 1 < G.g[0], hy = Y0 + 1 < G.g[1];
   const uint32_t Z2 = Z0 + 2 < G.g[0] ? Z0 + 2 : Z0, Y2 = Y0 + 2 < G.g[1] ? Y0 + 2 : Y0;
   const uint32_t Xe = X0 + 8 < G.g[2] ? X0 + 8 : X0 + 6;
+  const bool f32 = ((uintptr_t)f & 31u) == 0;  // rows start at multiples of 64 values
   uint32_t ign = 0;
   uint32_t& sf = SELF_FLOOR ? fl : ign;
   // values at x = X0 .. X0 + 7 of level-grid row (z, y); odd x only if asked
   auto seg = [&](uint32_t z, uint32_t y, float v[8], bool odd) {
     const float* r = f + ((size_t)(z << hl) * ny + (y << hl)) * nx;
-    if (hl == 0) {  // finest level: two 16-byte loads
+    if (hl == 0 && f32) {  // finest level, 32-byte aligned field: one 32-byte load
+      ld_nc_v8f(r + X0, v);
+    } else if (hl == 0) {  // two 16-byte loads
       const float4 p = __ldg(reinterpret_cast<const float4*>(r + X0));
       const float4 q = __ldg(reinterpret_cast<const float4*>(r + X0) + 1);
       v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
@@ -202,9 +205,12 @@ __device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict_
   const bool hz = Z0 + 1 < G.g[0], hy = Y0 + 1 < G.g[1];
   const uint32_t Z2 = Z0 + 2 < G.g[0] ? Z0 + 2 : Z0, Y2 = Y0 + 2 < G.g[1] ? Y0 + 2 : Y0;
   const uint32_t Xe = X0 + 8 < G.g[2] ? X0 + 8 : X0 + 6;
+  const bool f32 = ((uintptr_t)f & 31u) == 0;
   auto seg = [&](uint32_t z, uint32_t y, float v[8], bool odd) {
     const float* r = f + ((size_t)(z << hl) * ny + (y << hl)) * nx;
-    if (hl == 0) {
+    if (hl == 0 && f32) {
+      ld_nc_v8f(r + X0, v);
+    } else if (hl == 0) {
       const float4 p = __ldg(reinterpret_cast<const float4*>(r + X0));
       const float4 q = __ldg(reinterpret_cast<const float4*>(r + X0) + 1);
       v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
@@ -442,16 +448,22 @@ typedef uint32_t CellSW[7][32];
 
 // How a level's coefficients come back, uniform over a launch: no planes
 // (k = 0 or an all-zero level: c8 = 0, the planes are not touched), bl <= 32
-// (c8 magnitude = q_hat >> (32 - bl)), bl > 32 (q_hat << (bl - 32)).
+// (c8 magnitude = q_hat >> (32 - bl)), bl > 32 (q_hat << (bl - 32)), and
+// among those bl >= 35, where c8 / 8 is an integer (CR_WIDE3, below).
 // CR_ANY: decided per tile at run time (one instantiation for every case).
-enum { CR_NONE = 0, CR_NARROW = 1, CR_WIDE = 2, CR_ANY = 3 };
+enum { CR_NONE = 0, CR_NARROW = 1, CR_WIDE = 2, CR_ANY = 3, CR_WIDE3 = 4 };
 
 __device__ __forceinline__ int cells_mode(int bl, int k) {
-  return (k == 0 || bl == 0) ? CR_NONE : (bl <= 32 ? CR_NARROW : CR_WIDE);
+  return (k == 0 || bl == 0) ? CR_NONE
+                             : (bl <= 32 ? CR_NARROW : (bl >= 35 ? CR_WIDE3 : CR_WIDE));
 }
 
-// recomposition of one tile of 1024 cells from the coarse grid and the planes
-template <bool FINAL, int MODE>
+// recomposition of one tile of 1024 cells from the coarse grid and the planes.
+// SMALL (FINAL only): the retrieval's error bound proves |X| < 2^48 for every
+// value and the output exponent is in the normal range, so every value takes
+// the short conversion without a range test; the output is 32-byte aligned and
+// each thread writes a row's 8 values with one 32-byte store.
+template <bool FINAL, int MODE, bool SMALL = false>
 __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict__ P,
                                                      const LevelDesc& L, const CellGeom& G,
                                                      int E_f, int bl, int k,
@@ -523,15 +535,22 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       const bool fast_e = e >= -126 && E_f <= 121;
       const float s24 = __int_as_float(((fast_e ? e : 0) + 24 + 127) << 23);
       const float s0 = __int_as_float(((fast_e ? e : 0) + 127) << 23);
+      // a thread's rows of the output and of the coarse grid are 32-byte aligned
+      // when the buffers are: one 32-byte access per row then
+      const bool a32 = (((uintptr_t)dst | (uintptr_t)coarse) & 31u) == 0;
       auto load = [&](uint32_t z, uint32_t y, int64_t c[5]) {
         const int64_t* row = coarse + ((size_t)z * gc1 + y) * gc2;
-        // cx is a multiple of 4 and gc2 of 32: two aligned 16-byte loads
-        const longlong2 p0 = __ldg(reinterpret_cast<const longlong2*>(row + cx));
-        const longlong2 p1 = __ldg(reinterpret_cast<const longlong2*>(row + cx) + 1);
-        c[0] = p0.x;
-        c[1] = p0.y;
-        c[2] = p1.x;
-        c[3] = p1.y;
+        // cx is a multiple of 4 and gc2 of 32: aligned 32- or 16-byte loads
+        if (a32) {
+          ld_nc_v4s64(row + cx, c);
+        } else {
+          const longlong2 p0 = __ldg(reinterpret_cast<const longlong2*>(row + cx));
+          const longlong2 p1 = __ldg(reinterpret_cast<const longlong2*>(row + cx) + 1);
+          c[0] = p0.x;
+          c[1] = p0.y;
+          c[2] = p1.x;
+          c[3] = p1.y;
+        }
         c[4] = __ldg(row + xe);
       };
       // the staged q_hat of the type-t nodes of the thread's 4 cells and their
@@ -552,6 +571,16 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
         const uint64_t neg = 0ull - (uint64_t)((sg >> kk) & 1u);  // all ones if negative
         return (int64_t)((mag ^ neg) - neg);
       };
+      // CR_WIDE3: c8 = +-(q_hat << s) with s = bl - 32 >= 3, so c8 / 8 is the
+      // integer +-(q_hat << (s - 3)) and X = floor((c8 + E) / 8) = ex +- q_hat 2^(s-3)
+      // with ex = floor(E / 8) = S >> n.  One wide multiply-add gives
+      // q_hat 2^(s-3) + ex, and a negative sign is applied by complementing ex
+      // before it and the sum after it (~(y + ~ex) = ex - y).
+      const uint32_t p2 = MODE == CR_WIDE3 ? 1u << (bl - 35) : 0u;
+      auto wide3 = [&](uint32_t qh, uint32_t sg, int kk, int64_t ex) -> int64_t {
+        const uint64_t neg = (uint64_t)(int64_t)((int32_t)(sg << (31 - kk)) >> 31);
+        return (int64_t)(((uint64_t)qh * p2 + ((uint64_t)ex ^ neg)) ^ neg);
+      };
       // Row (oz, oy): even-x nodes are type te = 2 oy + 4 oz (te = 0: the coarse
       // node itself), odd-x nodes te + 1.  e[kk] is the sum of the row's coarse
       // corners along y and z; a type with n odd axes has
@@ -562,16 +591,25 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
         if (te != 0) qof(te, qe, se);
         qof(te + 1, qo, so);
         const size_t base = ((size_t)(2 * cz + oz) * G.g[1] + (2 * cy + oy)) * G.g[2] + 2 * cx;
+        float o8[8];  // FINAL && SMALL: the row's 8 values, one 32-byte store
 #pragma unroll
         for (int hf = 0; hf < 2; hf++) {  // two cells (four nodes) at a time
           int64_t V[4];
 #pragma unroll
           for (int u = 0; u < 2; u++) {
             const int kk = 2 * hf + u;
-            V[2 * u] = te == 0 ? e[kk] : (c8at(qe, se, kk) + e[kk] * (8 >> ne)) >> 3;
-            V[2 * u + 1] = (c8at(qo, so, kk) + (e[kk] + e[kk + 1]) * (8 >> no)) >> 3;
+            if (MODE == CR_WIDE3) {
+              V[2 * u] = te == 0 ? e[kk] : wide3(qe[kk], se, kk, e[kk] >> ne);
+              V[2 * u + 1] = wide3(qo[kk], so, kk, (e[kk] + e[kk + 1]) >> no);
+            } else {
+              V[2 * u] = te == 0 ? e[kk] : (c8at(qe, se, kk) + e[kk] * (8 >> ne)) >> 3;
+              V[2 * u + 1] = (c8at(qo, so, kk) + (e[kk] + e[kk + 1]) * (8 >> no)) >> 3;
+            }
           }
-          if (FINAL) {
+          if (FINAL && SMALL) {  // (the output is 32-byte aligned on this path)
+#pragma unroll
+            for (int u = 0; u < 4; u++) o8[4 * hf + u] = fixed_to_f32_small(V[u], s24, s0);
+          } else if (FINAL) {
             // values below 2^48 in magnitude (the rule; a partial reconstruction
             // of a rough field can pass it) take the short conversion
             uint32_t big = 0;
@@ -587,12 +625,15 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
             }
             reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base)[hf] =
                 make_float4(o[0], o[1], o[2], o[3]);
+          } else if (a32) {
+            st_v4s64(reinterpret_cast<int64_t*>(dst) + base + 4 * hf, V[0], V[1], V[2], V[3]);
           } else {
             longlong2* d2 = reinterpret_cast<longlong2*>(reinterpret_cast<int64_t*>(dst) + base);
             d2[2 * hf] = make_longlong2(V[0], V[1]);
             d2[2 * hf + 1] = make_longlong2(V[2], V[3]);
           }
         }
+        if (FINAL && SMALL) st_v8f(reinterpret_cast<float*>(dst) + base, o8);
       };
       int64_t c0[5], a[5];
       load(cz, cy, c0);
@@ -622,7 +663,7 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
   if (md != CR_NONE) __syncthreads();  // the staging is reused by the next tile
 }
 
-template <bool FINAL, int MODE>
+template <bool FINAL, int MODE, bool SMALL>
 __device__ __forceinline__ void cells_recompose_tiles(const uint32_t* __restrict__ P,
                                                       const LevelDesc& L, const CellGeom& G,
                                                       int E_f, int bl, int k,
@@ -630,7 +671,29 @@ __device__ __forceinline__ void cells_recompose_tiles(const uint32_t* __restrict
                                                       void* __restrict__ dst, CellQ& s_q,
                                                       CellSW& s_sw) {
   for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
-    cells_recompose_tile<FINAL, MODE>(P, L, G, E_f, bl, k, coarse, dst, tile, s_q, s_sw);
+    cells_recompose_tile<FINAL, MODE, SMALL>(P, L, G, E_f, bl, k, coarse, dst, tile, s_q, s_sw);
+}
+
+template <bool FINAL, bool SMALL>
+__device__ __forceinline__ void cells_recompose_modes(const uint32_t* __restrict__ P,
+                                                      const LevelDesc& L, const CellGeom& G,
+                                                      int E_f, int bl, int k,
+                                                      const int64_t* __restrict__ coarse,
+                                                      void* __restrict__ dst, CellQ& s_q,
+                                                      CellSW& s_sw) {
+  switch (cells_mode(bl, k)) {
+    case CR_NONE:
+      cells_recompose_tiles<FINAL, CR_NONE, SMALL>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
+      break;
+    case CR_NARROW:
+      cells_recompose_tiles<FINAL, CR_NARROW, SMALL>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
+      break;
+    case CR_WIDE3:
+      cells_recompose_tiles<FINAL, CR_WIDE3, SMALL>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
+      break;
+    default:
+      cells_recompose_tiles<FINAL, CR_WIDE, SMALL>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
+  }
 }
 
 template <bool FINAL>
@@ -646,16 +709,11 @@ __global__ void __launch_bounds__(256, 4) k_cells_recompose(const uint32_t* __re
   const CellGeom G = cell_geom(L);
   const int E_f = meta->E_f, bl = meta->bl[L.level], k = 4 * meta->cur[L.level];
   const uint32_t* P = planes + L.plane_off / 4;
-  switch (cells_mode(bl, k)) {
-    case CR_NONE:
-      cells_recompose_tiles<FINAL, CR_NONE>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
-      break;
-    case CR_NARROW:
-      cells_recompose_tiles<FINAL, CR_NARROW>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
-      break;
-    default:
-      cells_recompose_tiles<FINAL, CR_WIDE>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
-  }
+  if (FINAL && meta->out_small && E_f - 48 >= -126 && E_f <= 121 &&
+      ((uintptr_t)dst & 31u) == 0)
+    cells_recompose_modes<FINAL, true>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
+  else
+    cells_recompose_modes<FINAL, false>(P, L, G, E_f, bl, k, coarse, dst, s_q, s_sw);
 }
 
 void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,

@@ -104,6 +104,37 @@ __device__ __forceinline__ void transpose8x4(uint32_t r[8]) {
 #undef HP_T8STAGE
 }
 
+// ---------------------------------------------------- 32-byte accesses
+// One 256-bit global access per thread (addresses 32-byte aligned): a warp's
+// 32 threads then cover whole 32-byte sectors, where two 16-byte accesses at a
+// 32-byte stride would touch every sector twice, half of it each time.
+__device__ __forceinline__ void ld_nc_v8f(const float* p, float v[8]) {
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                 "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void ld_nc_v4s64(const int64_t* p, int64_t v[4]) {
+  long long a, b, c, d;
+  asm volatile("ld.global.nc.v4.s64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+               : "l"(p));
+  v[0] = a;
+  v[1] = b;
+  v[2] = c;
+  v[3] = d;
+}
+__device__ __forceinline__ void st_v8f(float* p, const float v[8]) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void st_v4s64(int64_t* p, int64_t a, int64_t b, int64_t c, int64_t d) {
+  asm volatile("st.global.v4.s64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"((long long)a),
+               "l"((long long)b), "l"((long long)c), "l"((long long)d)
+               : "memory");
+}
+
 // ------------------------------------------------------------- fixed point
 // F = sign(v) * floor(|v| / 2^(E_f-48)), exactly, from the IEEE fields.
 __device__ __forceinline__ int64_t fixed_point(float v, int E_f, uint32_t& floored) {

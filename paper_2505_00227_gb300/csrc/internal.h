@@ -82,7 +82,11 @@ struct alignas(16) FieldMeta {
   // QoI triplet data (velocity magnitude range) when prepared
   float qmin, qmax;
   // 1: every group (DC included) is read from the slot buffer on retrieval
-  int32_t compact, pad2;
+  int32_t compact;
+  // set by the selection of the current retrieval: 1 when its error bound
+  // proves |X| < 2^48 for every reconstructed value X (max|f| + E < 2^E_f),
+  // so the output conversion needs no per-value range test
+  int32_t out_small;
 };
 
 // retrieval info written by the selection kernel

@@ -327,6 +327,11 @@ __device__ void select_prefix(const FieldMeta* m, FieldMeta* mw, double tau, int
                          __ull2double_rn(m->E_lo[c]));
     rd->E_abs = ldexp(v, m->E_f - 51 - m->B);
     rd->tau_abs = tau_abs;
+    // every reconstructed value is within E of its input value, itself at most
+    // max|f| in magnitude: |X| U <= max|f| + E.  Below 2^E_f (= 2^48 U), with a
+    // margin for the roundings of this test, |X| < 2^48
+    const double bound = __dmul_rn(__dadd_rn(m->maxabs, rd->E_abs), 1.0 + 0x1p-40);
+    mw->out_small = bound < ldexp(1.0, m->E_f) ? 1 : 0;
   }
   __syncwarp();
   for (int l = lane; l < nlev; l += 32) {  // after lane 0 has read the old state
