@@ -56,7 +56,10 @@ bool cell_path_ok(const LevelDesc& L, int B) {
 // that do not exist at this (cz, cy) are not visited.  Corner sums: with c_yz the coarse value
 // row at (Z0 + 2 dz, Y0 + 2 dy) (clamped), a = c_00 + c_01, d = c_00 + c_10,
 // b = a + c_10 + c_11; a type's corners along x are entries k and k + 1.
-template <bool SELF_FLOOR, typename V>
+// FPCONV (no floor flag needed and -78 <= E_f): the fixed point of every value
+// by fixed_point_fp on the floating-point pipes instead of the IEEE-field
+// integer path; both give the same F.
+template <bool SELF_FLOOR, bool FPCONV = false, typename V>
 __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const CellGeom& G,
                                             uint32_t ny, uint32_t nx, int hl, int E_f,
                                             uint32_t cz, uint32_t cy, uint32_t cx, uint32_t& fl,
@@ -68,6 +71,10 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
   const bool f32 = ((uintptr_t)f & 31u) == 0;  // rows start at multiples of 64 values
   uint32_t ign = 0;
   uint32_t& sf = SELF_FLOOR ? fl : ign;
+  const float sc = FPCONV ? __int_as_float((48 - E_f + 127) << 23) : 0.0f;
+  auto fixp = [&](float x, uint32_t& fla) -> int64_t {
+    return FPCONV ? fixed_point_fp(x, sc) : fixed_point(x, E_f, fla);
+  };
   // values at x = X0 .. X0 + 7 of level-grid row (z, y); odd x only if asked
   auto seg = [&](uint32_t z, uint32_t y, float v[8], bool odd) {
     const float* r = f + ((size_t)(z << hl) * ny + (y << hl)) * nx;
@@ -89,15 +96,14 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
   auto coarse = [&](uint32_t z, uint32_t y, int64_t c[5], float v[8], bool odd) {
     seg(z, y, v, odd);
 #pragma unroll
-    for (int i = 0; i < 4; i++) c[i] = fixed_point(v[2 * i], E_f, ign);
-    c[4] = fixed_point(__ldg(f + ((size_t)(z << hl) * ny + (y << hl)) * nx + ((size_t)Xe << hl)), E_f,
-                       ign);
+    for (int i = 0; i < 4; i++) c[i] = fixp(v[2 * i], ign);
+    c[4] = fixp(__ldg(f + ((size_t)(z << hl) * ny + (y << hl)) * nx + ((size_t)Xe << hl)), ign);
   };
   float v[8];
   int64_t c0[5], a[5], c[4];
   coarse(Z0, Y0, c0, v, true);  // and the t = 1 nodes at odd x
 #pragma unroll
-  for (int k = 0; k < 4; k++) c[k] = (2 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 4;
+  for (int k = 0; k < 4; k++) c[k] = (2 * fixp(v[2 * k + 1], sf) - (c0[k] + c0[k + 1])) * 4;
   visit(1, c);
   if (hy) {
     coarse(Z0, Y2, a, v, false);
@@ -105,10 +111,10 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
     for (int i = 0; i < 5; i++) a[i] += c0[i];
     seg(Z0, Y0 + 1, v, true);
 #pragma unroll
-    for (int k = 0; k < 4; k++) c[k] = (2 * fixed_point(v[2 * k], E_f, sf) - a[k]) * 4;
+    for (int k = 0; k < 4; k++) c[k] = (2 * fixp(v[2 * k], sf) - a[k]) * 4;
     visit(2, c);
 #pragma unroll
-    for (int k = 0; k < 4; k++) c[k] = (4 * fixed_point(v[2 * k + 1], E_f, sf) - (a[k] + a[k + 1])) * 2;
+    for (int k = 0; k < 4; k++) c[k] = (4 * fixp(v[2 * k + 1], sf) - (a[k] + a[k + 1])) * 2;
     visit(3, c);
   }
   if (hz) {
@@ -118,10 +124,10 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
     for (int i = 0; i < 5; i++) c0[i] += c1[i];  // c0 becomes d
     seg(Z0 + 1, Y0, v, true);
 #pragma unroll
-    for (int k = 0; k < 4; k++) c[k] = (2 * fixed_point(v[2 * k], E_f, sf) - c0[k]) * 4;
+    for (int k = 0; k < 4; k++) c[k] = (2 * fixp(v[2 * k], sf) - c0[k]) * 4;
     visit(4, c);
 #pragma unroll
-    for (int k = 0; k < 4; k++) c[k] = (4 * fixed_point(v[2 * k + 1], E_f, sf) - (c0[k] + c0[k + 1])) * 2;
+    for (int k = 0; k < 4; k++) c[k] = (4 * fixp(v[2 * k + 1], sf) - (c0[k] + c0[k + 1])) * 2;
     visit(5, c);
     if (hy) {
       int64_t c3[5];
@@ -130,10 +136,10 @@ __device__ __forceinline__ void cells_visit(const float* __restrict__ f, const C
       for (int i = 0; i < 5; i++) a[i] += c1[i] + c3[i];  // a becomes b
       seg(Z0 + 1, Y0 + 1, v, true);
 #pragma unroll
-      for (int k = 0; k < 4; k++) c[k] = (4 * fixed_point(v[2 * k], E_f, sf) - a[k]) * 2;
+      for (int k = 0; k < 4; k++) c[k] = (4 * fixp(v[2 * k], sf) - a[k]) * 2;
       visit(6, c);
 #pragma unroll
-      for (int k = 0; k < 4; k++) c[k] = 8 * fixed_point(v[2 * k + 1], E_f, sf) - (a[k] + a[k + 1]);
+      for (int k = 0; k < 4; k++) c[k] = 8 * fixp(v[2 * k + 1], sf) - (a[k] + a[k + 1]);
       visit(7, c);
     }
   }
@@ -327,6 +333,7 @@ __device__ __forceinline__ void cells_zero_padding(const LevelDesc& L, uint32_t*
     P[(size_t)(k / pad) * W + used + k % pad] = 0u;
 }
 
+template <bool FPCONV>
 __device__ __forceinline__ void cells_encode_tile(const float* __restrict__ f, const CellGeom& G,
                                                   const LevelDesc& L, uint32_t ny, uint32_t nx,
                                                   int E_f, int bl, uint32_t* __restrict__ P,
@@ -341,7 +348,7 @@ __device__ __forceinline__ void cells_encode_tile(const float* __restrict__ f, c
     if (cy < G.c[1]) {
       const uint32_t rw = r * G.NW + xl / 32, b0 = xl % 32;
       uint32_t ign = 0;
-      cells_visit<false>(f, G, ny, nx, hl, E_f, cz, cy, cx, ign, [&](int t, const int64_t* c8) {
+      cells_visit<false, FPCONV>(f, G, ny, nx, hl, E_f, cz, cy, cx, ign, [&](int t, const int64_t* c8) {
         uint32_t q[4], nib = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -408,8 +415,13 @@ __global__ void __launch_bounds__(256, 3) k_cells_encode(const float* __restrict
   uint32_t* P = planes + L.plane_off / 4;
   uint64_t low = 0;
   if (blockIdx.x == 0) cells_zero_padding(L, P);
-  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
-    cells_encode_tile(f, G, L, ny, nx, E_f, bl, P, tile, low, s_q, s_s);
+  if (E_f >= -78) {  // 2^(48 - E_f) is a normal float
+    for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
+      cells_encode_tile<true>(f, G, L, ny, nx, E_f, bl, P, tile, low, s_q, s_s);
+  } else {
+    for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
+      cells_encode_tile<false>(f, G, L, ny, nx, E_f, bl, P, tile, low, s_q, s_s);
+  }
   cells_lowbits_flush(meta, L.level, low);
 }
 
@@ -804,8 +816,12 @@ __global__ void __launch_bounds__(256, 3) kb_cells_encode(const BatchJob* __rest
     const uint32_t tile = u - unit0[e];
     if (tile == 0) cells_zero_padding(L, P);
     uint64_t low = 0;
-    cells_encode_tile(reinterpret_cast<const float*>(J.f), G, L, J.dims[1], J.dims[2], meta->E_f,
-                      meta->bl[L.level], P, tile, low, s_q, s_s);
+    if (meta->E_f >= -78)
+      cells_encode_tile<true>(reinterpret_cast<const float*>(J.f), G, L, J.dims[1], J.dims[2],
+                              meta->E_f, meta->bl[L.level], P, tile, low, s_q, s_s);
+    else
+      cells_encode_tile<false>(reinterpret_cast<const float*>(J.f), G, L, J.dims[1], J.dims[2],
+                               meta->E_f, meta->bl[L.level], P, tile, low, s_q, s_s);
     cells_lowbits_flush(meta, L.level, low);
   }
 }

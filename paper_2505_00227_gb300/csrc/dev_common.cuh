@@ -159,6 +159,18 @@ __device__ __forceinline__ int64_t fixed_point(float v, int E_f, uint32_t& floor
   return (u >> 31) ? -(int64_t)mag : (int64_t)mag;
 }
 
+// The same F for an FP32 value without the floor flag, on the floating-point
+// pipes: with sc = 2^(48 - E_f) (a normal float, so -78 <= E_f), x = v sc is
+// exact (|x| < 2^48; a value whose product underflows has |x| < 1 and F = 0),
+// t = trunc(x / 2^24) is an integer of at most 24 bits, r = x - t 2^24 is exact
+// (|r| < 2^24, the sign of x or zero) and F = trunc(x) = t 2^24 + trunc(r).
+__device__ __forceinline__ int64_t fixed_point_fp(float v, float sc) {
+  const float x = __fmul_rn(v, sc);
+  const float t = truncf(__fmul_rn(x, 0x1p-24f));
+  const float r = __fmaf_rn(t, -0x1p24f, x);
+  return (int64_t)__float2int_rz(t) * 16777216ll + (int64_t)__float2int_rz(r);
+}
+
 __device__ __forceinline__ int64_t fixed_point(double v, int E_f, uint32_t& floored) {
   uint64_t u = (uint64_t)__double_as_longlong(v);
   uint32_t e = (uint32_t)((u >> 52) & 0x7ffu);
