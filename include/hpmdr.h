@@ -45,8 +45,10 @@ typedef enum {
   HPMDR_ERR_CUDA = -3,          /* a CUDA call failed (message: hpmdr_last_error) */
   HPMDR_ERR_CORRUPT = -4,       /* stored bytes failed a bounds or format check */
   HPMDR_ERR_UNATTAINABLE = -5,  /* even all bitplanes cannot meet the bound */
-  HPMDR_ERR_TIMEOUT = -6,       /* a bounded device or host wait gave up */
-  HPMDR_ERR_BUSY = -7           /* request not finished yet (serving) */
+  HPMDR_ERR_TIMEOUT = -6,       /* a bounded wait gave up (serving: a request queued past
+                                   its deadline) */
+  HPMDR_ERR_BUSY = -7,          /* request not finished yet (serving) */
+  HPMDR_ERR_CANCELLED = -8      /* request cancelled before it started (serving) */
 } hpmdr_status;
 
 typedef enum { HPMDR_F32 = 0, HPMDR_F64 = 1 } hpmdr_dtype;
@@ -315,6 +317,8 @@ typedef struct {
   int max_slots;        /* requests running at once, 1..64 */
   int keep_cache;       /* 1: keep plane caches between requests; 0: plain path */
   uint64_t hbm_budget;  /* device bytes for stored fields + plane caches + QoI scratch */
+  double queue_timeout_s;  /* > 0: a request still queued this long after its submit
+                              fails with HPMDR_ERR_TIMEOUT instead of starting; 0: none */
 } hpmdr_server_config;
 HPMDR_API hpmdr_status hpmdr_server_create(hpmdr_ctx* ctx, const hpmdr_server_config* cfg,
                                            hpmdr_server** out);
@@ -330,6 +334,12 @@ HPMDR_API hpmdr_status hpmdr_server_submit(hpmdr_server* s, const hpmdr_request*
  * instants in seconds of the monotonic clock (may be NULL). */
 HPMDR_API hpmdr_status hpmdr_server_poll(hpmdr_server* s, uint64_t ticket, int wait,
                                          hpmdr_retrieve_info info[4], double times[3]);
+/* Host-side cancellation: a request still queued is dropped (HPMDR_OK; its
+ * poll then returns HPMDR_ERR_CANCELLED); a request that has started or
+ * finished is not (HPMDR_ERR_BUSY; it completes and its poll gives its
+ * status); HPMDR_ERR_ARG for an unknown or already polled ticket.  The paper
+ * has no counterpart (its retrieval has no request stream). */
+HPMDR_API hpmdr_status hpmdr_server_cancel(hpmdr_server* s, uint64_t ticket);
 /* budget bytes in use, peak, cache evictions, completed, queued, running */
 HPMDR_API hpmdr_status hpmdr_server_stats(hpmdr_server* s, uint64_t stats[6]);
 

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhpmdr.so")
 
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_CORRUPT, ERR_UNATTAINABLE, ERR_TIMEOUT, ERR_BUSY = (
     0, -1, -2, -3, -4, -5, -6, -7)
+ERR_CANCELLED = -8
 F32, F64 = 0, 1
 DC, HUFFMAN, RLE, PLACEHOLDER = 0, 1, 2, 3
 
@@ -59,7 +60,8 @@ class Request(C.Structure):
 
 
 class ServerConfig(C.Structure):
-    _fields_ = [("max_slots", C.c_int), ("keep_cache", C.c_int), ("hbm_budget", C.c_uint64)]
+    _fields_ = [("max_slots", C.c_int), ("keep_cache", C.c_int), ("hbm_budget", C.c_uint64),
+                ("queue_timeout_s", C.c_double)]
 
 
 REQ_FIELD, REQ_VMAG = 0, 1
@@ -123,6 +125,7 @@ _SIGS = {
     "hpmdr_server_submit": (C.c_int, [vp, C.POINTER(Request), u64p]),
     "hpmdr_server_poll": (C.c_int, [vp, C.c_uint64, C.c_int, RetrieveInfo * 4, C.c_double * 3]),
     "hpmdr_server_stats": (C.c_int, [vp, C.c_uint64 * 6]),
+    "hpmdr_server_cancel": (C.c_int, [vp, C.c_uint64]),
     "hpmdr_batch_create": (C.c_int, [vp, C.c_uint64, u64p, C.c_int, C.POINTER(vp)]),
     "hpmdr_batch_destroy": (None, [vp]),
     "hpmdr_batch_handle": (C.c_int, [vp, C.c_uint64, C.POINTER(vp)]),
@@ -620,9 +623,10 @@ def bitplane_decode_design(planes, n, design, k, q=None, sign=None, stream=None)
 class Server:
     """hpmdr_server: concurrent retrieval requests over added handles."""
 
-    def __init__(self, ctx, hbm_budget, max_slots=8, keep_cache=True):
+    def __init__(self, ctx, hbm_budget, max_slots=8, keep_cache=True, queue_timeout_s=0.0):
         self.ctx = ctx
-        cfg = ServerConfig(int(max_slots), int(bool(keep_cache)), int(hbm_budget))
+        cfg = ServerConfig(int(max_slots), int(bool(keep_cache)), int(hbm_budget),
+                           float(queue_timeout_s))
         self._p = vp()
         _check(lib().hpmdr_server_create(ctx._p, C.byref(cfg), C.byref(self._p)),
                "hpmdr_server_create")
@@ -661,8 +665,17 @@ class Server:
         if st == ERR_BUSY:
             return None
         self._keep.pop(ticket, None)
-        _check(st, "hpmdr_server_poll", allow=(ERR_UNATTAINABLE,))
+        _check(st, "hpmdr_server_poll", allow=(ERR_UNATTAINABLE, ERR_TIMEOUT, ERR_CANCELLED))
         return st, list(infos), tuple(times)
+
+    def cancel(self, ticket):
+        """True if the request was still queued and is now cancelled (its poll
+        returns ERR_CANCELLED); False if it has started or finished."""
+        st = lib().hpmdr_server_cancel(self._p, ticket)
+        if st == ERR_BUSY:
+            return False
+        _check(st, "hpmdr_server_cancel")
+        return True
 
     def stats(self):
         a = (C.c_uint64 * 6)()

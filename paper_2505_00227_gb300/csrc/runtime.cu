@@ -1152,15 +1152,30 @@ extern "C" hpmdr_status hpmdr_retrieve_qoi_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[
     }
     if (st) break;
     if (!d_vm && (st = ctx->A.alloc(&d_vm, N * 4, s))) break;
-    for (int c = 0; c < 3; c++) {
-      if ((st = enqueue_retrieve(ctx, v[c], eps, 1, comp[c], s))) break;
-      hpmdr_status r = collect_info(ctx, v[c], &inf[c], s);
+    // the three component retrievals and |v| are enqueued back to back; each
+    // selection record and status is written by a kernel into a page-locked
+    // slot of the context's ring, read after the one wait below
+    if (!ctx->pending.empty()) {  // earlier asynchronous retrievals own ring slots
+      const hpmdr_status r = ctx_wait(ctx);
       if (r != HPMDR_OK && r != HPMDR_ERR_UNATTAINABLE) {
         st = r;
         break;
       }
-      if (r != HPMDR_OK) worst = r;
-      E[c] = inf[c].est_linf;
+    }
+    if (!ctx->pinned &&
+        (st = alloc_mapped(kSlotBytes * hpmdr_ctx::kRing, &ctx->pinned, &ctx->pinned_dev)))
+      break;
+    PendingRetrieval pr[3];
+    for (int c = 0; c < 3; c++) {
+      if ((st = enqueue_retrieve(ctx, v[c], eps, 1, comp[c], s))) break;
+      unsigned char* slot = (unsigned char*)ctx->pinned_dev + (size_t)c * kSlotBytes;
+      launch_to_host(v[c]->d_rd, slot, sizeof(RetrieveDev), &v[c]->d_meta->status,
+                     slot + sizeof(RetrieveDev), 4, s);
+      pr[c].H = v[c];
+      pr[c].prof_lv = v[c]->prof_lv;
+      pr[c].prof_decode = v[c]->prof_decode;
+      pr[c].prof_small = v[c]->prof_small;
+      pr[c].small_end = v[c]->small_end;
     }
     if (st) break;
     { ProfScope p(ctx->P(), ST_VMAG, 16.0 * N, s);
@@ -1174,7 +1189,27 @@ extern "C" hpmdr_status hpmdr_retrieve_qoi_vmag(hpmdr_ctx* ctx, hpmdr_handle* v[
       if (cudaMemcpyAsync(out_vmag, d_vm, N * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         st = HPMDR_ERR_CUDA;
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) st = HPMDR_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      st = HPMDR_ERR_CUDA;
+      break;
+    }
+    for (int c = 0; c < 3 && st == HPMDR_OK; c++) {
+      const unsigned char* slot = (const unsigned char*)ctx->pinned + (size_t)c * kSlotBytes;
+      const RetrieveDev& rd = *reinterpret_cast<const RetrieveDev*>(slot);
+      const int32_t mstatus = *reinterpret_cast<const int32_t*>(slot + sizeof(RetrieveDev));
+      if (mstatus) {
+        st = (hpmdr_status)mstatus;
+        break;
+      }
+      patch_retrieve_bytes(ctx, v[c], rd, pr[c].prof_lv, pr[c].prof_decode, pr[c].prof_small,
+                           pr[c].small_end);
+      fill_info(v[c], rd, &inf[c]);
+      const hpmdr_status r = (hpmdr_status)rd.status;
+      if (r != HPMDR_OK && r != HPMDR_ERR_UNATTAINABLE) st = r;
+      else if (r != HPMDR_OK) worst = r;
+      E[c] = inf[c].est_linf;
+    }
+    if (st) break;
     memset(&inf[3], 0, sizeof(inf[3]));
     inf[3].est_linf = qoi_estimate(E, (double)v[0]->qmax);
     inf[3].requested_abs = tau_q;
@@ -2342,6 +2377,7 @@ extern "C" const char* hpmdr_strerror(hpmdr_status s) {
     case HPMDR_ERR_UNATTAINABLE: return "error bound unattainable";
     case HPMDR_ERR_TIMEOUT: return "timeout";
     case HPMDR_ERR_BUSY: return "busy";
+    case HPMDR_ERR_CANCELLED: return "cancelled";
   }
   return "unknown status";
 }

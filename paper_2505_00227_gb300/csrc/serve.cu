@@ -16,6 +16,11 @@
 // Budget accounting: resident stored bytes of every added field + plane caches
 // held + the component scratch of running QoI requests.
 //
+// Host-side failure handling: a queued request can be cancelled, and with a
+// queue deadline a request that could not start in time fails with
+// HPMDR_ERR_TIMEOUT (workers wake at least every deadline to expire them).
+// Neither touches a running request: nothing is ever stopped on the device.
+//
 // Only the public entry points of the library are used here.
 #include <cuda_runtime.h>
 
@@ -125,8 +130,31 @@ struct hpmdr_server {
     return true;
   }
 
+  // a queued request leaves the queue without running (lock held)
+  void finish_unrun(Req* q, hpmdr_status st) {
+    q->status = st;
+    q->state = 2;
+    q->t_start = q->t_done = now_s();
+    cv_done.notify_all();
+  }
+
+  // queued requests past their deadline fail with HPMDR_ERR_TIMEOUT (lock held)
+  void expire() {
+    if (!(cfg.queue_timeout_s > 0.0)) return;
+    const double t = now_s();
+    for (auto it = queue.begin(); it != queue.end();) {
+      if (t - (*it)->t_submit > cfg.queue_timeout_s) {
+        finish_unrun(*it, HPMDR_ERR_TIMEOUT);
+        it = queue.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+
   // first queued request that can start now (lock held)
   Req* admit(hpmdr_ctx* ctx) {
+    expire();
     for (auto it = queue.begin(); it != queue.end(); ++it) {
       Req* q = *it;
       if (!idle(q)) continue;
@@ -168,7 +196,12 @@ struct hpmdr_server {
     std::unique_lock<std::mutex> lock(mu);
     while (true) {
       Req* q = nullptr;
-      while (!stop && !(q = admit(ctx))) cv_work.wait(lock);
+      while (!stop && !(q = admit(ctx))) {
+        if (cfg.queue_timeout_s > 0.0)  // wake to expire requests nobody else would
+          cv_work.wait_for(lock, std::chrono::duration<double>(cfg.queue_timeout_s));
+        else
+          cv_work.wait(lock);
+      }
       if (!q) return;
       lock.unlock();
       run(q, ctx);
@@ -193,7 +226,8 @@ struct hpmdr_server {
 
 extern "C" hpmdr_status hpmdr_server_create(hpmdr_ctx* ctx, const hpmdr_server_config* cfg,
                                             hpmdr_server** out) {
-  if (!ctx || !cfg || !out || cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->hbm_budget == 0)
+  if (!ctx || !cfg || !out || cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->hbm_budget == 0 ||
+      !(cfg->queue_timeout_s >= 0.0))
     return HPMDR_ERR_ARG;
   *out = nullptr;
   std::unique_ptr<hpmdr_server> S(new hpmdr_server());
@@ -307,6 +341,7 @@ extern "C" hpmdr_status hpmdr_server_poll(hpmdr_server* S, uint64_t ticket, int 
   auto it = S->reqs.find(ticket);
   if (it == S->reqs.end()) return HPMDR_ERR_ARG;
   Req* q = it->second.get();
+  if (q->state == 0) S->expire();
   if (q->state != 2) {
     if (!wait) return HPMDR_ERR_BUSY;
     S->cv_done.wait(lock, [q]() { return q->state == 2; });
@@ -320,6 +355,18 @@ extern "C" hpmdr_status hpmdr_server_poll(hpmdr_server* S, uint64_t ticket, int 
   const hpmdr_status st = q->status;
   S->reqs.erase(it);
   return st;
+}
+
+extern "C" hpmdr_status hpmdr_server_cancel(hpmdr_server* S, uint64_t ticket) {
+  if (!S) return HPMDR_ERR_ARG;
+  std::unique_lock<std::mutex> lock(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return HPMDR_ERR_ARG;
+  Req* q = it->second.get();
+  if (q->state != 0) return HPMDR_ERR_BUSY;  // started or done: it completes
+  S->queue.erase(std::find(S->queue.begin(), S->queue.end(), q));
+  S->finish_unrun(q, HPMDR_ERR_CANCELLED);
+  return HPMDR_OK;
 }
 
 extern "C" hpmdr_status hpmdr_server_stats(hpmdr_server* S, uint64_t stats[6]) {

@@ -144,3 +144,53 @@ def test_admission_errors(B, setup):
         srv.submit([hs["b"]], 1e-3, out=o)  # never added
     assert e.value.status == B.ERR_ARG
     srv.close()
+
+
+def test_cancel_queued_requests(B, setup):
+    """Host-side cancellation: a request still queued is dropped and polls as
+    cancelled; one that already started completes with its normal result."""
+    ctx, fields, hs, vel, vh, oracles = setup
+    srv = B.Server(ctx, 1 << 40, max_slots=1, keep_cache=False)
+    srv.add(hs["a"])
+    F = oracles["a"]
+    rc, ref, g, E = F.retrieve(1e-6 * F.range)
+    outs = [torch.empty(fields["a"].shape, dtype=torch.float32, device="cuda") for _ in range(24)]
+    tickets = [srv.submit([hs["a"]], 1e-6, out=o) for o in outs]  # one slot, one handle: serial
+    cancelled = [srv.cancel(t) for t in tickets[8:]]
+    assert any(cancelled)  # the last of 24 serial requests cannot all have started
+    for i, (t, o) in enumerate(zip(tickets, outs)):
+        st, info, times = srv.poll(t)
+        if i >= 8 and cancelled[i - 8]:
+            assert st == B.ERR_CANCELLED
+        else:
+            assert st == rc == 0 and info[0].groups == list(g)
+            assert np.array_equal(o.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+    with pytest.raises(B.HpmdrError) as e:
+        srv.cancel(tickets[0])  # already polled
+    assert e.value.status == B.ERR_ARG
+    assert srv.stats()["queued"] == 0
+    srv.close()
+
+
+def test_queue_deadline_times_out_waiting_requests(B, setup):
+    """A request still queued past the server's deadline fails with
+    ERR_TIMEOUT instead of starting; requests that ran are exact."""
+    ctx, fields, hs, vel, vh, oracles = setup
+    srv = B.Server(ctx, 1 << 40, max_slots=1, keep_cache=False, queue_timeout_s=1e-3)
+    srv.add(hs["c"])
+    F = oracles["c"]
+    rc, ref, g, E = F.retrieve(1e-5 * F.range)
+    outs = [torch.empty(fields["c"].shape, dtype=torch.float32, device="cuda") for _ in range(64)]
+    tickets = [srv.submit([hs["c"]], 1e-5, out=o) for o in outs]
+    res = [srv.poll(t) for t in tickets]
+    assert {r[0] for r in res} <= {0, B.ERR_TIMEOUT}
+    assert any(r[0] == B.ERR_TIMEOUT for r in res) and any(r[0] == 0 for r in res)
+    for (st, info, times), o in zip(res, outs):
+        if st == 0:
+            assert info[0].groups == list(g)
+            assert np.array_equal(o.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+        else:
+            assert times[2] - times[0] >= 1e-3  # failed only after its deadline
+    srv.close()
+    with pytest.raises(B.HpmdrError):
+        B.Server(ctx, 1 << 40, queue_timeout_s=-1.0)
