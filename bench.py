@@ -447,7 +447,7 @@ def bench_bpdesign(args, binding):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     res = []
-    for lg in (20, 24, 27):
+    for lg in args.bpd_log_sizes:
         n = 1 << lg
         g = torch.Generator(device="cuda").manual_seed(lg)
         q = torch.randint(-(2**31), 2**31 - 1, (n,), dtype=torch.int32, device="cuda", generator=g)
@@ -708,6 +708,31 @@ def run_profile_step(args):
     print(f"profile step ok: {args.profile_steps} step(s) of the {args.size}^3 field", flush=True)
 
 
+# ------------------------------------------------- one section on its own
+SECTIONS = ("small", "streaming", "pipeline", "ablation", "qoi", "bpdesign", "serving", "batched")
+
+
+def run_section(args):
+    """One bench section alone (for per-kernel ncu captures of that section's
+    kernels): its JSON object is printed, no bench line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2505_00227_gb300 import binding
+    torch.cuda.set_device(0)
+    name = args.section
+    if name == "ablation":
+        f = make_field(args.size, 2, "cuda")
+        res = bench_lossless(args, binding, f)
+    else:
+        fn = {"small": bench_small, "streaming": bench_streaming, "pipeline": bench_pipeline,
+              "qoi": bench_qoi_iter, "bpdesign": bench_bpdesign, "serving": bench_serving,
+              "batched": bench_batched}[name]
+        res = fn(args, binding)
+    torch.cuda.synchronize()
+    print(json.dumps({"section": name, "result": res}), flush=True)
+
+
 # -------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -961,6 +986,7 @@ def main():
     ap.add_argument("--no-qoi", action="store_true")
     ap.add_argument("--no-bpdesign", action="store_true")
     ap.add_argument("--qoi-side", type=int, default=256)
+    ap.add_argument("--bpd-log-sizes", type=int, nargs="+", default=[20, 24, 27])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-streaming", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
@@ -974,9 +1000,14 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="run --profile-steps untimed steps for an ncu capture and exit")
     ap.add_argument("--profile-steps", type=int, default=1)
+    ap.add_argument("--section", choices=SECTIONS, default=None,
+                    help="run one bench section alone (no bench line) and exit")
     args = ap.parse_args()
     if args.profile_step:
         run_profile_step(args)
+        return
+    if args.section:
+        run_section(args)
         return
     if args.warmup < 3:
         args.warmup = 3

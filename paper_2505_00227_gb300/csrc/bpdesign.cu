@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(128) k_bpd_locality_encode(const uint32_t* __r
                                                              const uint8_t* __restrict__ sign,
                                                              uint32_t n, uint32_t W,
                                                              uint32_t* __restrict__ P) {
+  hp::pdl_enter();
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // word
   if (t >= W) return;
   const uint64_t j0 = (uint64_t)t * 32;
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(128) k_bpd_locality_decode(const uint32_t* __r
                                                              uint32_t n, uint32_t W, int k,
                                                              uint32_t* __restrict__ q,
                                                              uint8_t* __restrict__ sign) {
+  hp::pdl_enter();
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= W) return;
   const uint64_t j0 = (uint64_t)t * 32;
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(256) k_bpd_shuffle_encode(const uint32_t* __re
                                                             const uint8_t* __restrict__ sign,
                                                             uint32_t n, uint32_t W,
                                                             uint32_t* __restrict__ P) {
+  hp::pdl_enter();
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31, word = (uint32_t)(g >> 5);
   if (word >= W) return;  // whole warps: blockDim is a multiple of 32
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(256) k_bpd_shuffle_decode(const uint32_t* __re
                                                             uint32_t n, uint32_t W, int k,
                                                             uint32_t* __restrict__ q,
                                                             uint8_t* __restrict__ sign) {
+  hp::pdl_enter();
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31, word = (uint32_t)(g >> 5);
   if (word >= W) return;
@@ -160,23 +164,27 @@ void launch_bpd_encode(const uint32_t* q, const uint8_t* sign, uint64_t n, int d
   const uint32_t W = (uint32_t)(4 * ((n + 127) / 128));
   if (design == 0) return launch_bitplane_encode(q, sign, n, 32, planes, s);
   if (design == BPD_LOCALITY) {
-    hp::note_launch(), k_bpd_locality_encode<<<(W + 127) / 128, 128, 0, s>>>(q, sign, (uint32_t)n, W,
+    hp::note_launch(), hp::launch_pdl(k_bpd_locality_encode, (W + 127) / 128, 128, 0, s, q, sign, (uint32_t)n, W,
                                                                          planes);
     return;
   }
   const uint32_t blocks = (uint32_t)(((uint64_t)W * 32 + 255) / 256);
   switch (design) {
     case BPD_BALLOT:
-      hp::note_launch(), k_bpd_shuffle_encode<BPD_BALLOT><<<blocks, 256, 0, s>>>(q, sign, (uint32_t)n, W, planes);
+      hp::note_launch(), hp::launch_pdl(k_bpd_shuffle_encode<BPD_BALLOT>, blocks, 256, 0, s, q,
+                                        sign, (uint32_t)n, W, planes);
       break;
     case BPD_SHIFT:
-      hp::note_launch(), k_bpd_shuffle_encode<BPD_SHIFT><<<blocks, 256, 0, s>>>(q, sign, (uint32_t)n, W, planes);
+      hp::note_launch(), hp::launch_pdl(k_bpd_shuffle_encode<BPD_SHIFT>, blocks, 256, 0, s, q, sign,
+                                        (uint32_t)n, W, planes);
       break;
     case BPD_MATCH:
-      hp::note_launch(), k_bpd_shuffle_encode<BPD_MATCH><<<blocks, 256, 0, s>>>(q, sign, (uint32_t)n, W, planes);
+      hp::note_launch(), hp::launch_pdl(k_bpd_shuffle_encode<BPD_MATCH>, blocks, 256, 0, s, q, sign,
+                                        (uint32_t)n, W, planes);
       break;
     default:
-      hp::note_launch(), k_bpd_shuffle_encode<BPD_REDUCE><<<blocks, 256, 0, s>>>(q, sign, (uint32_t)n, W, planes);
+      hp::note_launch(), hp::launch_pdl(k_bpd_shuffle_encode<BPD_REDUCE>, blocks, 256, 0, s, q,
+                                        sign, (uint32_t)n, W, planes);
   }
 }
 
@@ -185,12 +193,13 @@ void launch_bpd_decode(const uint32_t* planes, uint64_t n, int design, int k, ui
   const uint32_t W = (uint32_t)(4 * ((n + 127) / 128));
   if (design == 0) return launch_bitplane_decode(planes, n, 32, k, q, sign, s);
   if (design == BPD_LOCALITY) {
-    hp::note_launch(), k_bpd_locality_decode<<<(W + 127) / 128, 128, 0, s>>>(planes, (uint32_t)n, W, k,
+    hp::note_launch(), hp::launch_pdl(k_bpd_locality_decode, (W + 127) / 128, 128, 0, s, planes, (uint32_t)n, W, k,
                                                                          q, sign);
     return;
   }
   const uint32_t blocks = (uint32_t)(((uint64_t)W * 32 + 255) / 256);
-  hp::note_launch(), k_bpd_shuffle_decode<<<blocks, 256, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
+  hp::note_launch(), hp::launch_pdl(k_bpd_shuffle_decode, blocks, 256, 0, s, planes, (uint32_t)n, W,
+                                    k, q, sign);
 }
 
 }  // namespace hp

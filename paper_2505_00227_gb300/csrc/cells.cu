@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(256, 4) k_cells_levelmax_est(const float* __re
                                                             uint32_t ny, uint32_t nx,
                                                             const LevelDesc* __restrict__ Lp,
                                                             FieldMeta* meta) {
+  hp::pdl_enter();
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   const CellGeom G = cell_geom(L);
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(256, 4) k_cells_levelmax_est(const float* __re
 __global__ void __launch_bounds__(256, 4) k_cells_levelmax(const float* __restrict__ f, uint32_t ny,
                                                         uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                         FieldMeta* meta) {
+  hp::pdl_enter();
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   // the estimate pass settled bl: one thread records it, nothing else to do
@@ -406,6 +408,7 @@ __device__ __forceinline__ void cells_lowbits_flush(FieldMeta* meta, int level, 
 __global__ void __launch_bounds__(256, 3) k_cells_encode(const float* __restrict__ f, uint32_t ny,
                                                       uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                       FieldMeta* meta, uint32_t* __restrict__ planes) {
+  hp::pdl_enter();
   __shared__ CellQ s_q;
   __shared__ CellS s_s;
   if (meta->status) return;
@@ -439,9 +442,9 @@ void launch_cells_levelmax(const float* f, const uint64_t dims[3], const LevelDe
   uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 4;
   if (blocks > cap) blocks = cap;
   if (!blocks) return;
-  hp::note_launch(), k_cells_levelmax_est<<<blocks, 256, 0, s>>>(f, (uint32_t)dims[1],
+  hp::note_launch(), hp::launch_pdl(k_cells_levelmax_est, blocks, 256, 0, s, f, (uint32_t)dims[1],
                                                               (uint32_t)dims[2], Ld, meta);
-  hp::note_launch(), k_cells_levelmax<<<blocks, 256, 0, s>>>(f, (uint32_t)dims[1], (uint32_t)dims[2],
+  hp::note_launch(), hp::launch_pdl(k_cells_levelmax, blocks, 256, 0, s, f, (uint32_t)dims[1], (uint32_t)dims[2],
                                                           Ld, meta);
 }
 
@@ -451,7 +454,7 @@ void launch_cells_encode(const float* f, const uint64_t dims[3], const LevelDesc
   uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 3;  // one wave, 3 CTAs per SM
   if (blocks > cap) blocks = cap;
   if (!blocks) return;
-  hp::note_launch(), k_cells_encode<<<blocks, 256, 0, s>>>(f, (uint32_t)dims[1], (uint32_t)dims[2],
+  hp::note_launch(), hp::launch_pdl(k_cells_encode, blocks, 256, 0, s, f, (uint32_t)dims[1], (uint32_t)dims[2],
                                                         Ld, meta, planes);
 }
 
@@ -714,6 +717,7 @@ __global__ void __launch_bounds__(256, 4) k_cells_recompose(const uint32_t* __re
                                                          const LevelDesc* __restrict__ Lp,
                                                          const int64_t* __restrict__ coarse,
                                                          void* __restrict__ dst) {
+  hp::pdl_enter();
   __shared__ CellQ s_q;
   __shared__ CellSW s_sw;
   if (meta->status) return;
@@ -736,9 +740,11 @@ void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const
   if (blocks > cap) blocks = cap;
   if (!blocks) return;
   if (final)
-    hp::note_launch(), k_cells_recompose<true><<<blocks, 256, 0, s>>>(planes, meta, Ld, coarse, dst);
+    hp::note_launch(), hp::launch_pdl(k_cells_recompose<true>, blocks, 256, 0, s, planes, meta, Ld,
+                                      coarse, dst);
   else
-    hp::note_launch(), k_cells_recompose<false><<<blocks, 256, 0, s>>>(planes, meta, Ld, coarse, dst);
+    hp::note_launch(), hp::launch_pdl(k_cells_recompose<false>, blocks, 256, 0, s, planes, meta, Ld,
+                                      coarse, dst);
 }
 
 // ------------------------------------------------------------------ batched
@@ -750,6 +756,7 @@ __global__ void __launch_bounds__(256, 4) kb_cells_levelmax_est(const BatchJob* 
                                                              const LevelRef* __restrict__ refs,
                                                              const uint32_t* __restrict__ unit0,
                                                              uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t e = unit_owner(unit0, nrefs, u);
     const LevelRef R = refs[e];
@@ -778,6 +785,7 @@ __global__ void __launch_bounds__(256, 4) kb_cells_levelmax(const BatchJob* __re
                                                          const LevelRef* __restrict__ refs,
                                                          const uint32_t* __restrict__ unit0,
                                                          uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t e = unit_owner(unit0, nrefs, u);
     const LevelRef R = refs[e];
@@ -802,6 +810,7 @@ __global__ void __launch_bounds__(256, 3) kb_cells_encode(const BatchJob* __rest
                                                        const LevelRef* __restrict__ refs,
                                                        const uint32_t* __restrict__ unit0,
                                                        uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   __shared__ CellQ s_q;
   __shared__ CellS s_s;
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
@@ -830,6 +839,7 @@ __global__ void __launch_bounds__(256, 3) kb_cells_recompose(const BatchJob* __r
                                                           const LevelRef* __restrict__ refs,
                                                           const uint32_t* __restrict__ unit0,
                                                           uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   __shared__ CellQ s_q;
   __shared__ CellSW s_sw;
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
@@ -854,22 +864,26 @@ void launch_b_cells_levelmax(const BatchJob* jobs, const LevelRef* refs, const u
                              uint32_t nrefs, uint32_t total, uint32_t grid, cstream s) {
   if (!total) return;
   if (grid > total) grid = total;
-  hp::note_launch(), kb_cells_levelmax_est<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
-  hp::note_launch(), kb_cells_levelmax<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  hp::note_launch(), hp::launch_pdl(kb_cells_levelmax_est, grid, 256, 0, s, jobs, refs, unit0,
+                                    nrefs, total);
+  hp::note_launch(), hp::launch_pdl(kb_cells_levelmax, grid, 256, 0, s, jobs, refs, unit0, nrefs,
+                                    total);
 }
 
 void launch_b_cells_encode(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
                            uint32_t nrefs, uint32_t total, uint32_t grid, cstream s) {
   if (!total) return;
   if (grid > total) grid = total;
-  hp::note_launch(), kb_cells_encode<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  hp::note_launch(), hp::launch_pdl(kb_cells_encode, grid, 256, 0, s, jobs, refs, unit0, nrefs,
+                                    total);
 }
 
 void launch_b_cells_recompose(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
                               uint32_t nrefs, uint32_t total, uint32_t grid, cstream s) {
   if (!total) return;
   if (grid > total) grid = total;
-  hp::note_launch(), kb_cells_recompose<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  hp::note_launch(), hp::launch_pdl(kb_cells_recompose, grid, 256, 0, s, jobs, refs, unit0, nrefs,
+                                    total);
 }
 
 }  // namespace hp

@@ -92,6 +92,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_levelmax(FieldView<T> v, const LevelDesc* __restrict__ levels,
                                                   int nlev, uint32_t total_tiles,
                                                   const uint32_t* __restrict__ perm, FieldMeta* meta) {
+  hp::pdl_enter();
   __shared__ uint32_t s_tile0[HP_MAX_LEVELS + 1];
   for (int l = threadIdx.x; l <= nlev; l += blockDim.x)
     s_tile0[l] = l < nlev ? levels[l].gtile0 : total_tiles;
@@ -139,10 +140,12 @@ void launch_levelmax(const void* f, int dtype, const uint64_t dims[3], const Lev
   if (blocks == 0) blocks = 1;
   if (dtype == 0) {
     FieldView<float> v{(const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    hp::note_launch(), k_levelmax<float><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, perm, meta);
+    hp::note_launch(), hp::launch_pdl(k_levelmax<float>, blocks, 256, 0, s, v, levels, nlev,
+                                      total_tiles, perm, meta);
   } else {
     FieldView<double> v{(const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    hp::note_launch(), k_levelmax<double><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, perm, meta);
+    hp::note_launch(), hp::launch_pdl(k_levelmax<double>, blocks, 256, 0, s, v, levels, nlev,
+                                      total_tiles, perm, meta);
   }
 }
 
@@ -152,9 +155,14 @@ __device__ __forceinline__ void bitlen_level(FieldMeta* meta, int l) {
   if (l == 0) meta->input_exact = meta->floored ? 0 : 1;
 }
 
-__global__ void k_bitlen(FieldMeta* meta) { bitlen_level(meta, threadIdx.x); }
+__global__ void k_bitlen(FieldMeta* meta) {
+  hp::pdl_enter();
+  bitlen_level(meta, threadIdx.x);
+}
 
-void launch_bitlen(FieldMeta* meta, cstream s) { hp::note_launch(), k_bitlen<<<1, HP_MAX_LEVELS, 0, s>>>(meta); }
+void launch_bitlen(FieldMeta* meta, cstream s) {
+  hp::note_launch(), hp::launch_pdl(k_bitlen, 1, HP_MAX_LEVELS, 0, s, meta);
+}
 
 // ------------------------------------------------- register-block transpose out
 // Lane L holds in shared memory (row L, padded to 33 words) the 32 aligned
@@ -233,6 +241,7 @@ template <typename T, int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_encode(FieldView<T> v, const LevelDesc* __restrict__ levels, int nlev, uint32_t total_tiles,
              const uint32_t* __restrict__ perm, FieldMeta* meta, uint32_t* __restrict__ planes) {
+  hp::pdl_enter();
   constexpr int RPW = B == 32 ? 4 : 8;  // rows per warp
   __shared__ uint32_t s_tile0[HP_MAX_LEVELS + 1];
   __shared__ uint32_t s_hi[32 * 33];
@@ -301,10 +310,12 @@ void launch_encode(const void* f, int dtype, const uint64_t dims[3], const Level
   if (blocks == 0) blocks = 1;
   if (dtype == 0) {
     FieldView<float> v{(const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    hp::note_launch(), k_encode<float, 32><<<blocks, 256, 0, s>>>(v, levels, nlev, total_tiles, perm, meta, planes);
+    hp::note_launch(), hp::launch_pdl(k_encode<float, 32>, blocks, 256, 0, s, v, levels, nlev,
+                                      total_tiles, perm, meta, planes);
   } else {
     FieldView<double> v{(const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], 0};
-    hp::note_launch(), k_encode<double, 64><<<blocks, 128, 0, s>>>(v, levels, nlev, total_tiles, perm, meta, planes);
+    hp::note_launch(), hp::launch_pdl(k_encode<double, 64>, blocks, 128, 0, s, v, levels, nlev,
+                                      total_tiles, perm, meta, planes);
   }
 }
 
@@ -322,6 +333,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) kb_levelmax(const BatchJob* __restrict__ jobs,
                                                    const uint32_t* __restrict__ unit0,
                                                    uint32_t njobs, uint32_t total) {
+  hp::pdl_enter();
   const uint32_t wpb = blockDim.x >> 5;
   for (uint32_t u = blockIdx.x * wpb + (threadIdx.x >> 5); u < total; u += gridDim.x * wpb) {
     const uint32_t j = unit_owner(unit0, njobs, u);
@@ -340,22 +352,26 @@ void launch_b_levelmax(const BatchJob* jobs, const uint32_t* unit0, uint32_t njo
   if (!total) return;
   const uint32_t need = (total + 7) / 8;
   if (grid > need) grid = need;
-  if (dtype == 0) hp::note_launch(), kb_levelmax<float><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total);
-  else hp::note_launch(), kb_levelmax<double><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total);
+  if (dtype == 0) hp::note_launch(), hp::launch_pdl(kb_levelmax<float>, grid, 256, 0, s, jobs,
+                                                    unit0, njobs, total);
+  else hp::note_launch(), hp::launch_pdl(kb_levelmax<double>, grid, 256, 0, s, jobs, unit0, njobs,
+                                         total);
 }
 
 __global__ void kb_bitlen(const BatchJob* __restrict__ jobs) {
+  hp::pdl_enter();
   bitlen_level(jobs[blockIdx.x].meta, threadIdx.x);
 }
 
 void launch_b_bitlen(const BatchJob* jobs, uint32_t njobs, cstream s) {
-  if (njobs) hp::note_launch(), kb_bitlen<<<njobs, HP_MAX_LEVELS, 0, s>>>(jobs);
+  if (njobs) hp::note_launch(), hp::launch_pdl(kb_bitlen, njobs, HP_MAX_LEVELS, 0, s, jobs);
 }
 
 template <typename T, int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     kb_encode(const BatchJob* __restrict__ jobs, const uint32_t* __restrict__ unit0, uint32_t njobs,
               uint32_t total) {
+  hp::pdl_enter();
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -379,9 +395,11 @@ void launch_b_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs
   const uint32_t wpb = dtype == 0 ? 8 : 4, need = (total + wpb - 1) / wpb;
   if (grid > need) grid = need;
   if (dtype == 0)
-    hp::note_launch(), kb_encode<float, 32><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total);
+    hp::note_launch(), hp::launch_pdl(kb_encode<float, 32>, grid, 256, 0, s, jobs, unit0, njobs,
+                                      total);
   else
-    hp::note_launch(), kb_encode<double, 64><<<grid, 128, 0, s>>>(jobs, unit0, njobs, total);
+    hp::note_launch(), hp::launch_pdl(kb_encode<double, 64>, grid, 128, 0, s, jobs, unit0, njobs,
+                                      total);
 }
 
 // ------------------------------------------- stand-alone Algorithm 1 and inverse
@@ -417,6 +435,7 @@ template <int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_bitplane_encode(const void* __restrict__ qv, const uint8_t* __restrict__ sign, uint32_t n,
                       uint32_t W, uint32_t* __restrict__ planes) {
+  hp::pdl_enter();
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -469,6 +488,7 @@ template <int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_bitplane_decode(const uint32_t* __restrict__ planes, uint32_t n, uint32_t W, int k,
                       void* __restrict__ qv, uint8_t* __restrict__ sign) {
+  hp::pdl_enter();
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -487,6 +507,7 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_level_unpack(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ meta,
                    const LevelDesc* __restrict__ Lp, void* __restrict__ qv,
                    uint8_t* __restrict__ sign) {
+  hp::pdl_enter();
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -507,9 +528,11 @@ void launch_level_unpack(const uint32_t* planes, const FieldMeta* meta, const Le
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (B == 32)
-    hp::note_launch(), k_level_unpack<32><<<blocks, 256, 0, s>>>(planes, meta, Ld, q, sign);
+    hp::note_launch(), hp::launch_pdl(k_level_unpack<32>, blocks, 256, 0, s, planes, meta, Ld, q,
+                                      sign);
   else
-    hp::note_launch(), k_level_unpack<64><<<blocks, 128, 0, s>>>(planes, meta, Ld, q, sign);
+    hp::note_launch(), hp::launch_pdl(k_level_unpack<64>, blocks, 128, 0, s, planes, meta, Ld, q,
+                                      sign);
 }
 
 void launch_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int B, uint32_t* planes,
@@ -522,9 +545,11 @@ void launch_bitplane_encode(const void* q, const uint8_t* sign, uint64_t n, int 
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (B == 32)
-    hp::note_launch(), k_bitplane_encode<32><<<blocks, 256, 0, s>>>(q, sign, (uint32_t)n, W, planes);
+    hp::note_launch(), hp::launch_pdl(k_bitplane_encode<32>, blocks, 256, 0, s, q, sign,
+                                      (uint32_t)n, W, planes);
   else
-    hp::note_launch(), k_bitplane_encode<64><<<blocks, 128, 0, s>>>(q, sign, (uint32_t)n, W, planes);
+    hp::note_launch(), hp::launch_pdl(k_bitplane_encode<64>, blocks, 128, 0, s, q, sign,
+                                      (uint32_t)n, W, planes);
 }
 
 void launch_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, void* q,
@@ -537,9 +562,11 @@ void launch_bitplane_decode(const uint32_t* planes, uint64_t n, int B, int k, vo
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (B == 32)
-    hp::note_launch(), k_bitplane_decode<32><<<blocks, 256, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
+    hp::note_launch(), hp::launch_pdl(k_bitplane_decode<32>, blocks, 256, 0, s, planes, (uint32_t)n,
+                                      W, k, q, sign);
   else
-    hp::note_launch(), k_bitplane_decode<64><<<blocks, 128, 0, s>>>(planes, (uint32_t)n, W, k, q, sign);
+    hp::note_launch(), hp::launch_pdl(k_bitplane_decode<64>, blocks, 128, 0, s, planes, (uint32_t)n,
+                                      W, k, q, sign);
 }
 
 // batched Algorithm 1 / inverse over general cell levels: warp unit = one tile
@@ -548,6 +575,7 @@ template <int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     kb_pack(const BatchJob* __restrict__ jobs, const LevelRef* __restrict__ refs,
             const uint32_t* __restrict__ unit0, uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -569,6 +597,7 @@ template <int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     kb_unpack(const BatchJob* __restrict__ jobs, const LevelRef* __restrict__ refs,
               const uint32_t* __restrict__ unit0, uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -593,8 +622,10 @@ void launch_b_pack(const BatchJob* jobs, const LevelRef* refs, const uint32_t* u
   if (!total) return;
   const uint32_t wpb = B == 32 ? 8 : 4, need = (total + wpb - 1) / wpb;
   if (grid > need) grid = need;
-  if (B == 32) hp::note_launch(), kb_pack<32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
-  else hp::note_launch(), kb_pack<64><<<grid, 128, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  if (B == 32) hp::note_launch(), hp::launch_pdl(kb_pack<32>, grid, 256, 0, s, jobs, refs, unit0,
+                                                 nrefs, total);
+  else hp::note_launch(), hp::launch_pdl(kb_pack<64>, grid, 128, 0, s, jobs, refs, unit0, nrefs,
+                                         total);
 }
 
 void launch_b_unpack(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
@@ -602,8 +633,10 @@ void launch_b_unpack(const BatchJob* jobs, const LevelRef* refs, const uint32_t*
   if (!total) return;
   const uint32_t wpb = B == 32 ? 8 : 4, need = (total + wpb - 1) / wpb;
   if (grid > need) grid = need;
-  if (B == 32) hp::note_launch(), kb_unpack<32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
-  else hp::note_launch(), kb_unpack<64><<<grid, 128, 0, s>>>(jobs, refs, unit0, nrefs, total);
+  if (B == 32) hp::note_launch(), hp::launch_pdl(kb_unpack<32>, grid, 256, 0, s, jobs, refs, unit0,
+                                                 nrefs, total);
+  else hp::note_launch(), hp::launch_pdl(kb_unpack<64>, grid, 128, 0, s, jobs, refs, unit0, nrefs,
+                                         total);
 }
 
 }  // namespace hp

@@ -9,6 +9,35 @@
 
 namespace hp {
 
+// ------------------------------------------------- programmatic dependent launch
+// Every kernel is launched with programmatic stream serialization and starts by
+// waiting for the grid before it in the stream (griddepcontrol.wait: that grid
+// has completed and its writes are visible), then lets the next grid launch
+// (griddepcontrol.launch_dependents).  The next kernel's launch and CTA
+// scheduling then overlap the end of this one; its CTAs only begin work after
+// this grid has completed, so the stream order of every read and write is the
+// same as with ordinary launches.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------- division
 __host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
   FastDiv f;

@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(256) k_gcells_levelmax_est(const float* __rest
                                                              uint32_t ny, uint32_t nx,
                                                              const LevelDesc* __restrict__ Lp,
                                                              FieldMeta* meta) {
+  hp::pdl_enter();
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   const GView<float> v{f, ny, nx, L.hlog, meta->E_f};
@@ -207,6 +208,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gcells_levelmax(const T* __restrict__ f, uint32_t ny,
                                                          uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                          FieldMeta* meta) {
+  hp::pdl_enter();
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   if (sizeof(T) == 4 && cells_bl_from_estimate(meta, L.level, false)) {  // settled
@@ -255,6 +257,7 @@ __global__ void __launch_bounds__(256) k_gcells_encode(const T* __restrict__ f, 
                                                        uint32_t nx, const LevelDesc* __restrict__ Lp,
                                                        FieldMeta* meta, void* __restrict__ q,
                                                        uint8_t* __restrict__ sg) {
+  hp::pdl_enter();
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   const GView<T> v{f, ny, nx, L.hlog, meta->E_f};
@@ -353,6 +356,7 @@ __global__ void __launch_bounds__(256) k_gcells_recompose(const FieldMeta* __res
                                                           const uint8_t* __restrict__ sg,
                                                           const int64_t* __restrict__ coarse,
                                                           void* __restrict__ dst, int final) {
+  hp::pdl_enter();
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   gcells_recompose_range<T, B>(L, meta->bl[L.level], meta->E_f, q, sg, coarse, dst, final != 0,
@@ -374,25 +378,25 @@ void launch_gcells_levelmax(const void* f, int dtype, const uint64_t dims[3], co
                             const LevelDesc& Lh, FieldMeta* meta, cstream s) {
   const uint32_t g = gcell_grid(Lh);
   if (dtype == 0) {
-    hp::note_launch(), k_gcells_levelmax_est<<<g, 256, 0, s>>>(
-        (const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
-    hp::note_launch(), k_gcells_levelmax<float><<<g, 256, 0, s>>>(
-        (const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
+    hp::note_launch(), hp::launch_pdl(k_gcells_levelmax_est, g, 256, 0, s, (const float*)f,
+                                      (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
+    hp::note_launch(), hp::launch_pdl(k_gcells_levelmax<float>, g, 256, 0, s, (const float*)f,
+                                      (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
   }
   else
-    hp::note_launch(), k_gcells_levelmax<double><<<g, 256, 0, s>>>(
-        (const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
+    hp::note_launch(), hp::launch_pdl(k_gcells_levelmax<double>, g, 256, 0, s, (const double*)f,
+                                      (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta);
 }
 
 void launch_gcells_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
                           const LevelDesc& Lh, FieldMeta* meta, void* q, uint8_t* sg, cstream s) {
   const uint32_t g = gcell_grid(Lh);
   if (dtype == 0)
-    hp::note_launch(), k_gcells_encode<float, 32><<<g, 256, 0, s>>>(
-        (const float*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta, q, sg);
+    hp::note_launch(), hp::launch_pdl(k_gcells_encode<float, 32>, g, 256, 0, s, (const float*)f,
+                                      (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta, q, sg);
   else
-    hp::note_launch(), k_gcells_encode<double, 64><<<g, 256, 0, s>>>(
-        (const double*)f, (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta, q, sg);
+    hp::note_launch(), hp::launch_pdl(k_gcells_encode<double, 64>, g, 256, 0, s, (const double*)f,
+                                      (uint32_t)dims[1], (uint32_t)dims[2], Ld, meta, q, sg);
 }
 
 void launch_gcells_recompose(const FieldMeta* meta, const LevelDesc* Ld, const LevelDesc& Lh,
@@ -400,10 +404,10 @@ void launch_gcells_recompose(const FieldMeta* meta, const LevelDesc* Ld, const L
                              void* dst, int final, cstream s) {
   const uint32_t g = gcell_grid(Lh);
   if (dtype == 0)
-    hp::note_launch(), k_gcells_recompose<float, 32><<<g, 256, 0, s>>>(meta, Ld, q, sg, coarse, dst,
+    hp::note_launch(), hp::launch_pdl(k_gcells_recompose<float, 32>, g, 256, 0, s, meta, Ld, q, sg, coarse, dst,
                                                                        final);
   else
-    hp::note_launch(), k_gcells_recompose<double, 64><<<g, 256, 0, s>>>(meta, Ld, q, sg, coarse,
+    hp::note_launch(), hp::launch_pdl(k_gcells_recompose<double, 64>, g, 256, 0, s, meta, Ld, q, sg, coarse,
                                                                         dst, final);
 }
 
@@ -415,6 +419,7 @@ __global__ void __launch_bounds__(256) kb_gcells_levelmax(const BatchJob* __rest
                                                           const LevelRef* __restrict__ refs,
                                                           const uint32_t* __restrict__ unit0,
                                                           uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t e = unit_owner(unit0, nrefs, u);
     const LevelRef R = refs[e];
@@ -436,6 +441,7 @@ __global__ void __launch_bounds__(256) kb_gcells_levelmax_est(const BatchJob* __
                                                               const LevelRef* __restrict__ refs,
                                                               const uint32_t* __restrict__ unit0,
                                                               uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t e = unit_owner(unit0, nrefs, u);
     const LevelRef R = refs[e];
@@ -455,6 +461,7 @@ __global__ void __launch_bounds__(256) kb_gcells_encode(const BatchJob* __restri
                                                         const LevelRef* __restrict__ refs,
                                                         const uint32_t* __restrict__ unit0,
                                                         uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t e = unit_owner(unit0, nrefs, u);
     const LevelRef R = refs[e];
@@ -474,6 +481,7 @@ __global__ void __launch_bounds__(256) kb_gcells_recompose(const BatchJob* __res
                                                            const LevelRef* __restrict__ refs,
                                                            const uint32_t* __restrict__ unit0,
                                                            uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t e = unit_owner(unit0, nrefs, u);
     const LevelRef R = refs[e];
@@ -496,11 +504,14 @@ void launch_b_gcells_levelmax(const BatchJob* jobs, const LevelRef* refs, const 
   if (!total) return;
   grid = cap_units(grid, total);
   if (dtype == 0) {
-    hp::note_launch(), kb_gcells_levelmax_est<<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
-    hp::note_launch(), kb_gcells_levelmax<float><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_gcells_levelmax_est, grid, 256, 0, s, jobs, refs, unit0,
+                                      nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_gcells_levelmax<float>, grid, 256, 0, s, jobs, refs, unit0,
+                                      nrefs, total);
   }
   else
-    hp::note_launch(), kb_gcells_levelmax<double><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_gcells_levelmax<double>, grid, 256, 0, s, jobs, refs,
+                                      unit0, nrefs, total);
 }
 
 void launch_b_gcells_encode(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
@@ -508,9 +519,11 @@ void launch_b_gcells_encode(const BatchJob* jobs, const LevelRef* refs, const ui
   if (!total) return;
   grid = cap_units(grid, total);
   if (dtype == 0)
-    hp::note_launch(), kb_gcells_encode<float, 32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_gcells_encode<float, 32>, grid, 256, 0, s, jobs, refs,
+                                      unit0, nrefs, total);
   else
-    hp::note_launch(), kb_gcells_encode<double, 64><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_gcells_encode<double, 64>, grid, 256, 0, s, jobs, refs,
+                                      unit0, nrefs, total);
 }
 
 void launch_b_gcells_recompose(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
@@ -519,10 +532,10 @@ void launch_b_gcells_recompose(const BatchJob* jobs, const LevelRef* refs, const
   if (!total) return;
   grid = cap_units(grid, total);
   if (dtype == 0)
-    hp::note_launch(), kb_gcells_recompose<float, 32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs,
+    hp::note_launch(), hp::launch_pdl(kb_gcells_recompose<float, 32>, grid, 256, 0, s, jobs, refs, unit0, nrefs,
                                                                            total);
   else
-    hp::note_launch(), kb_gcells_recompose<double, 64><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs,
+    hp::note_launch(), hp::launch_pdl(kb_gcells_recompose<double, 64>, grid, 256, 0, s, jobs, refs, unit0, nrefs,
                                                                             total);
 }
 

@@ -194,13 +194,14 @@ __global__ void __launch_bounds__(256) k_chunk_stats(const uint8_t* __restrict__
                                                      uint32_t* __restrict__ group_hist,
                                                      unsigned long long* __restrict__ group_cost,
                                                      uint32_t* __restrict__ chunk_cost) {
+  hp::pdl_enter();
   chunk_stats_unit(planes, meta, chunk_group, group_hist, group_cost, chunk_cost, blockIdx.x);
 }
 
 void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uint32_t* group_hist,
                         unsigned long long* group_cost, uint32_t* chunk_cost, cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_chunk_stats<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group,
+  hp::note_launch(), hp::launch_pdl(k_chunk_stats, cm.total_chunks, 256, 0, s, planes, meta, cm.chunk_group,
                                                                    group_hist, group_cost,
                                                                    chunk_cost);
 }
@@ -354,13 +355,14 @@ __global__ void __launch_bounds__(256) k_decide(FieldMeta* meta, const uint32_t*
                                                 const unsigned long long* __restrict__ group_cost,
                                                 uint8_t* __restrict__ lens, uint64_t Ts,
                                                 uint32_t cr_num, uint32_t cr_den, int force) {
+  hp::pdl_enter();
   decide_unit(meta, group_hist, group_cost, lens, Ts, cr_num, cr_den, force, blockIdx.x);
 }
 
 void launch_decide(FieldMeta* meta, int ngroups_total, const uint32_t* group_hist,
                    const unsigned long long* group_cost, uint8_t* lens, uint64_t Ts,
                    uint32_t cr_num, uint32_t cr_den, int force, cstream s) {
-  hp::note_launch(), k_decide<<<ngroups_total, 256, 0, s>>>(meta, group_hist, group_cost, lens, Ts,
+  hp::note_launch(), hp::launch_pdl(k_decide, ngroups_total, 256, 0, s, meta, group_hist, group_cost, lens, Ts,
                                                             cr_num, cr_den, force);
 }
 
@@ -461,13 +463,15 @@ __global__ void __launch_bounds__(256) k_huff_bits(const uint8_t* __restrict__ p
                                                    const uint32_t* __restrict__ chunk_group,
                                                    const uint8_t* __restrict__ lens,
                                                    uint32_t* __restrict__ chunk_words) {
+  hp::pdl_enter();
   huff_bits_unit(planes, meta, chunk_group, lens, chunk_words, blockIdx.x);
 }
 
 void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm, const uint8_t* lens,
                       uint32_t* chunk_words, cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_huff_bits<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_words);
+  hp::note_launch(), hp::launch_pdl(k_huff_bits, cm.total_chunks, 256, 0, s, planes, meta,
+                                    cm.chunk_group, lens, chunk_words);
 }
 
 // ------------------------------------------- coder work lists (refactor)
@@ -478,6 +482,7 @@ void launch_huff_bits(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
 __global__ void k_coder_lists(const FieldMeta* __restrict__ meta,
                               const uint32_t* __restrict__ chunk_group, uint32_t tc,
                               uint32_t* __restrict__ lists, uint32_t* __restrict__ counts) {
+  hp::pdl_enter();
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (meta->status) return;
   int m = 0;
@@ -501,8 +506,8 @@ __global__ void k_coder_lists(const FieldMeta* __restrict__ meta,
 void launch_coder_lists(const FieldMeta* meta, ChunkMap cm, uint32_t* lists, uint32_t* counts,
                         cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_coder_lists<<<(cm.total_chunks + 255) / 256, 256, 0, s>>>(
-      meta, cm.chunk_group, cm.total_chunks, lists, counts);
+  hp::note_launch(), hp::launch_pdl(k_coder_lists, (cm.total_chunks + 255) / 256, 256, 0, s, meta,
+                                    cm.chunk_group, cm.total_chunks, lists, counts);
 }
 
 __global__ void __launch_bounds__(256) k_huff_bits_list(const uint8_t* __restrict__ planes,
@@ -512,6 +517,7 @@ __global__ void __launch_bounds__(256) k_huff_bits_list(const uint8_t* __restric
                                                         uint32_t* __restrict__ chunk_words,
                                                         const uint32_t* __restrict__ list,
                                                         const uint32_t* __restrict__ count) {
+  hp::pdl_enter();
   const uint32_t n = *count;
   for (uint32_t e = blockIdx.x; e < n; e += gridDim.x) {
     huff_bits_unit(planes, meta, chunk_group, lens, chunk_words, list[e]);
@@ -531,8 +537,8 @@ void launch_huff_bits_list(const uint8_t* planes, const FieldMeta* meta, ChunkMa
                            const uint8_t* lens, uint32_t* chunk_words, const uint32_t* lists,
                            const uint32_t* counts, cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_huff_bits_list<<<coder_grid(cm.total_chunks, 8), 256, 0, s>>>(
-      planes, meta, cm.chunk_group, lens, chunk_words, lists, counts);
+  hp::note_launch(), hp::launch_pdl(k_huff_bits_list, coder_grid(cm.total_chunks, 8), 256, 0, s,
+                                    planes, meta, cm.chunk_group, lens, chunk_words, lists, counts);
 }
 
 // ------------------------------------ per-group chunk output offsets (scan)
@@ -580,12 +586,14 @@ __global__ void __launch_bounds__(256) k_group_offsets(FieldMeta* meta,
                                                        const uint32_t* __restrict__ chunk_words,
                                                        const uint32_t* __restrict__ chunk_cost,
                                                        uint32_t* __restrict__ chunk_out) {
+  hp::pdl_enter();
   group_offsets_unit(meta, chunk_words, chunk_cost, chunk_out, blockIdx.x);
 }
 
 void launch_group_offsets(FieldMeta* meta, int ngroups_total, const uint32_t* chunk_words,
                           const uint32_t* chunk_cost, uint32_t* chunk_out, cstream s) {
-  hp::note_launch(), k_group_offsets<<<ngroups_total, 256, 0, s>>>(meta, chunk_words, chunk_cost, chunk_out);
+  hp::note_launch(), hp::launch_pdl(k_group_offsets, ngroups_total, 256, 0, s, meta, chunk_words,
+                                    chunk_cost, chunk_out);
 }
 
 // -------------------------------------------------------- Huffman: encode
@@ -680,6 +688,7 @@ __global__ void __launch_bounds__(256) k_huff_encode(const uint8_t* __restrict__
                                                      const uint8_t* __restrict__ lens,
                                                      const uint32_t* __restrict__ chunk_out,
                                                      uint8_t* __restrict__ slots) {
+  hp::pdl_enter();
   huff_encode_unit(planes, meta, chunk_group, lens, chunk_out, slots, blockIdx.x);
 }
 
@@ -691,6 +700,7 @@ __global__ void __launch_bounds__(256, 4) k_huff_encode_list(const uint8_t* __re
                                                           uint8_t* __restrict__ slots,
                                                           const uint32_t* __restrict__ list,
                                                           const uint32_t* __restrict__ count) {
+  hp::pdl_enter();
   const uint32_t n = *count;
   for (uint32_t e = blockIdx.x; e < n; e += gridDim.x) {
     huff_encode_unit(planes, meta, chunk_group, lens, chunk_out, slots, list[e]);
@@ -702,14 +712,15 @@ void launch_huff_encode_list(const uint8_t* planes, const FieldMeta* meta, Chunk
                              const uint8_t* lens, const uint32_t* chunk_out, uint8_t* slots,
                              const uint32_t* lists, const uint32_t* counts, cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_huff_encode_list<<<coder_grid(cm.total_chunks, 4), 256, 0, s>>>(
-      planes, meta, cm.chunk_group, lens, chunk_out, slots, lists, counts);
+  hp::note_launch(), hp::launch_pdl(k_huff_encode_list, coder_grid(cm.total_chunks, 4), 256, 0, s,
+                                    planes, meta, cm.chunk_group, lens, chunk_out, slots, lists,
+                                    counts);
 }
 
 void launch_huff_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
                         const uint8_t* lens, const uint32_t* chunk_out, uint8_t* slots, cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_huff_encode<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, lens, chunk_out,
+  hp::note_launch(), hp::launch_pdl(k_huff_encode, cm.total_chunks, 256, 0, s, planes, meta, cm.chunk_group, lens, chunk_out,
                                                 slots);
 }
 
@@ -771,6 +782,7 @@ __global__ void __launch_bounds__(256) k_rle_encode(const uint8_t* __restrict__ 
                                                     const uint32_t* __restrict__ chunk_group,
                                                     const uint32_t* __restrict__ chunk_out,
                                                     uint8_t* __restrict__ slots) {
+  hp::pdl_enter();
   rle_encode_unit(planes, meta, chunk_group, chunk_out, slots, blockIdx.x);
 }
 
@@ -781,6 +793,7 @@ __global__ void __launch_bounds__(256) k_rle_encode_list(const uint8_t* __restri
                                                          uint8_t* __restrict__ slots,
                                                          const uint32_t* __restrict__ list,
                                                          const uint32_t* __restrict__ count) {
+  hp::pdl_enter();
   const uint32_t n = *count;
   for (uint32_t e = blockIdx.x; e < n; e += gridDim.x) {
     rle_encode_unit(planes, meta, chunk_group, chunk_out, slots, list[e]);
@@ -792,14 +805,16 @@ void launch_rle_encode_list(const uint8_t* planes, const FieldMeta* meta, ChunkM
                             const uint32_t* chunk_out, uint8_t* slots, const uint32_t* lists,
                             const uint32_t* counts, cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_rle_encode_list<<<coder_grid(cm.total_chunks, 4), 256, 0, s>>>(
-      planes, meta, cm.chunk_group, chunk_out, slots, lists + cm.total_chunks, counts + 1);
+  hp::note_launch(), hp::launch_pdl(k_rle_encode_list, coder_grid(cm.total_chunks, 4), 256, 0, s,
+                                    planes, meta, cm.chunk_group, chunk_out, slots,
+                                    lists + cm.total_chunks, counts + 1);
 }
 
 void launch_rle_encode(const uint8_t* planes, const FieldMeta* meta, ChunkMap cm,
                        const uint32_t* chunk_out, uint8_t* slots, cstream s) {
   if (cm.total_chunks == 0) return;
-  hp::note_launch(), k_rle_encode<<<cm.total_chunks, 256, 0, s>>>(planes, meta, cm.chunk_group, chunk_out, slots);
+  hp::note_launch(), hp::launch_pdl(k_rle_encode, cm.total_chunks, 256, 0, s, planes, meta,
+                                    cm.chunk_group, chunk_out, slots);
 }
 
 // ---------------------------------------------------------- group headers
@@ -839,12 +854,14 @@ __global__ void __launch_bounds__(256) k_headers(const FieldMeta* __restrict__ m
                                                  const uint8_t* __restrict__ lens,
                                                  const uint32_t* __restrict__ chunk_out,
                                                  uint8_t* __restrict__ slots) {
+  hp::pdl_enter();
   headers_unit(meta, lens, chunk_out, slots, blockIdx.x);
 }
 
 void launch_headers(FieldMeta* meta, int ngroups_total, const uint8_t* lens,
                     const uint32_t* chunk_out, uint8_t* slots, cstream s) {
-  hp::note_launch(), k_headers<<<ngroups_total, 256, 0, s>>>(meta, lens, chunk_out, slots);
+  hp::note_launch(), hp::launch_pdl(k_headers, ngroups_total, 256, 0, s, meta, lens, chunk_out,
+                                    slots);
 }
 
 // ================================================================ decoding
@@ -1414,6 +1431,7 @@ __global__ void __launch_bounds__(HP_DEC_THREADS) k_decode(const uint8_t* __rest
                                                            FieldMeta* meta,
                                                            const RetrieveDev* __restrict__ rd,
                                                            uint8_t* __restrict__ planes) {
+  hp::pdl_enter();
   extern __shared__ __align__(16) unsigned char dec_smem[];
   HuffTables& T = *reinterpret_cast<HuffTables*>(dec_smem);
   __shared__ uint32_t scratch[HP_DEC_THREADS / 32];
@@ -1450,7 +1468,8 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
   }();
   uint32_t blocks = max_items, cap = (uint32_t)sms * (uint32_t)resident;
   if (blocks > cap) blocks = cap;
-  hp::note_launch(), k_decode<<<blocks, HP_DEC_THREADS, smem, s>>>(slots, meta, rd, planes);
+  hp::note_launch(), hp::launch_pdl(k_decode, blocks, HP_DEC_THREADS, smem, s, slots, meta, rd,
+                                    planes);
 }
 
 // ------------------------------------------------------------------ batched
@@ -1469,25 +1488,32 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
       uint32_t total
 
 __global__ void __launch_bounds__(256) kb_chunk_stats(HP_BATCH_PARAMS) {
+  hp::pdl_enter();
   HP_BATCH_UNITS(chunk_stats_unit(J.planes, J.meta, J.chunk_group, J.hist, J.gcost, J.ccost, local))
 }
 __global__ void __launch_bounds__(256) kb_decide(HP_BATCH_PARAMS, uint64_t Ts, uint32_t cr_num,
                                                  uint32_t cr_den, int force) {
+  hp::pdl_enter();
   HP_BATCH_UNITS(decide_unit(J.meta, J.hist, J.gcost, J.lens, Ts, cr_num, cr_den, force, local))
 }
 __global__ void __launch_bounds__(256) kb_huff_bits(HP_BATCH_PARAMS) {
+  hp::pdl_enter();
   HP_BATCH_UNITS(huff_bits_unit(J.planes, J.meta, J.chunk_group, J.lens, J.cwords, local))
 }
 __global__ void __launch_bounds__(256) kb_group_offsets(HP_BATCH_PARAMS) {
+  hp::pdl_enter();
   HP_BATCH_UNITS(group_offsets_unit(J.meta, J.cwords, J.ccost, J.cout, local))
 }
 __global__ void __launch_bounds__(256) kb_huff_encode(HP_BATCH_PARAMS) {
+  hp::pdl_enter();
   HP_BATCH_UNITS(huff_encode_unit(J.planes, J.meta, J.chunk_group, J.lens, J.cout, J.slots, local))
 }
 __global__ void __launch_bounds__(256) kb_rle_encode(HP_BATCH_PARAMS) {
+  hp::pdl_enter();
   HP_BATCH_UNITS(rle_encode_unit(J.planes, J.meta, J.chunk_group, J.cout, J.slots, local))
 }
 __global__ void __launch_bounds__(256) kb_headers(HP_BATCH_PARAMS) {
+  hp::pdl_enter();
   HP_BATCH_UNITS(headers_unit(J.meta, J.lens, J.cout, J.slots, local))
 }
 
@@ -1496,44 +1522,51 @@ static uint32_t cap_grid(uint32_t grid, uint32_t total) { return grid < total ? 
 void launch_b_chunk_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                           uint32_t total, uint32_t grid, cstream s) {
   if (total)
-    hp::note_launch(), kb_chunk_stats<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+    hp::note_launch(), hp::launch_pdl(kb_chunk_stats, cap_grid(grid, total), 256, 0, s, jobs, unit0,
+                                      njobs, total);
 }
 void launch_b_decide(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
                      uint64_t Ts, uint32_t cr_num, uint32_t cr_den, int force, uint32_t grid,
                      cstream s) {
   if (total)
-    hp::note_launch(), kb_decide<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total, Ts,
+    hp::note_launch(), hp::launch_pdl(kb_decide, cap_grid(grid, total), 256, 0, s, jobs, unit0, njobs, total, Ts,
                                                                        cr_num, cr_den, force);
 }
 void launch_b_huff_bits(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                         uint32_t total, uint32_t grid, cstream s) {
   if (total)
-    hp::note_launch(), kb_huff_bits<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+    hp::note_launch(), hp::launch_pdl(kb_huff_bits, cap_grid(grid, total), 256, 0, s, jobs, unit0,
+                                      njobs, total);
 }
 void launch_b_group_offsets(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                             uint32_t total, uint32_t grid, cstream s) {
   if (total)
-    hp::note_launch(), kb_group_offsets<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+    hp::note_launch(), hp::launch_pdl(kb_group_offsets, cap_grid(grid, total), 256, 0, s, jobs,
+                                      unit0, njobs, total);
 }
 void launch_b_huff_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                           uint32_t total, uint32_t grid, cstream s) {
   if (total)
-    hp::note_launch(), kb_huff_encode<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+    hp::note_launch(), hp::launch_pdl(kb_huff_encode, cap_grid(grid, total), 256, 0, s, jobs, unit0,
+                                      njobs, total);
 }
 void launch_b_rle_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                          uint32_t total, uint32_t grid, cstream s) {
   if (total)
-    hp::note_launch(), kb_rle_encode<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+    hp::note_launch(), hp::launch_pdl(kb_rle_encode, cap_grid(grid, total), 256, 0, s, jobs, unit0,
+                                      njobs, total);
 }
 void launch_b_headers(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
                       uint32_t grid, cstream s) {
   if (total)
-    hp::note_launch(), kb_headers<<<cap_grid(grid, total), 256, 0, s>>>(jobs, unit0, njobs, total);
+    hp::note_launch(), hp::launch_pdl(kb_headers, cap_grid(grid, total), 256, 0, s, jobs, unit0,
+                                      njobs, total);
 }
 
 // decode: unit = one item (chunk to decode) of one job; the per-job item
 // counts are known only after the selection, so unit0 is computed on the device
 __global__ void kb_items_prefix(const BatchJob* __restrict__ jobs, uint32_t njobs, uint32_t* unit0) {
+  hp::pdl_enter();
   if (threadIdx.x != 0) return;
   uint32_t run = 0;
   for (uint32_t j = 0; j < njobs; j++) {
@@ -1545,12 +1578,13 @@ __global__ void kb_items_prefix(const BatchJob* __restrict__ jobs, uint32_t njob
 }
 
 void launch_b_items_prefix(const BatchJob* jobs, uint32_t njobs, uint32_t* unit0_out, cstream s) {
-  hp::note_launch(), kb_items_prefix<<<1, 32, 0, s>>>(jobs, njobs, unit0_out);
+  hp::note_launch(), hp::launch_pdl(kb_items_prefix, 1, 32, 0, s, jobs, njobs, unit0_out);
 }
 
 __global__ void __launch_bounds__(HP_DEC_THREADS) kb_decode(const BatchJob* __restrict__ jobs,
                                                             const uint32_t* __restrict__ unit0,
                                                             uint32_t njobs) {
+  hp::pdl_enter();
   extern __shared__ __align__(16) unsigned char dec_smem[];
   HuffTables& T = *reinterpret_cast<HuffTables*>(dec_smem);
   __shared__ uint32_t scratch[HP_DEC_THREADS / 32];
@@ -1570,7 +1604,8 @@ void launch_b_decode(const BatchJob* jobs, const uint32_t* unit0_dev, uint32_t n
                      uint32_t grid, cstream s) {
   const size_t smem = sizeof(HuffTables);
   set_smem_once((const void*)kb_decode, (int)smem);
-  hp::note_launch(), kb_decode<<<grid, HP_DEC_THREADS, smem, s>>>(jobs, unit0_dev, njobs);
+  hp::note_launch(), hp::launch_pdl(kb_decode, grid, HP_DEC_THREADS, smem, s, jobs, unit0_dev,
+                                    njobs);
 }
 
 }  // namespace hp

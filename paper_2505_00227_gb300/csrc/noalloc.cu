@@ -74,6 +74,7 @@ static hpmdr_status noalloc_scratch(NoAllocScratch** out) {
 // before the coder kernels run.  (Per-chunk run costs, word counts and offsets
 // are fully written before they are read.)
 __global__ void k_noalloc_init(NoAllocScratch* sc, uint64_t S, uint64_t cap, uint32_t nchunks) {
+  hp::pdl_enter();
   FieldMeta& m = sc->meta;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     m.status = 0;
@@ -114,7 +115,7 @@ extern "C" hpmdr_status hpmdr_encode_group_noalloc(const uint8_t* G, uint64_t S,
   if (st != HPMDR_OK) return st;
   const cudaStream_t s = (cudaStream_t)stream;
   const uint32_t nc = (uint32_t)((S + HP_CHUNK - 1) / HP_CHUNK);
-  hp::note_launch(), k_noalloc_init<<<1, 256, 0, s>>>(sc, S, cap, nc);
+  hp::note_launch(), hp::launch_pdl(k_noalloc_init, 1, 256, 0, s, sc, S, cap, nc);
   // a failed launch would leave the previous call's metadata in the array, and
   // its status, method and length would be read back as this call's
   if (cudaGetLastError() != cudaSuccess) return HPMDR_ERR_CUDA;

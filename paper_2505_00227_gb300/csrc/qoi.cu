@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(256) k_vmag_range(const float* __restrict__ vx
                                                     const float* __restrict__ vy,
                                                     const float* __restrict__ vz, uint64_t N,
                                                     unsigned int* qr) {
+  hp::pdl_enter();
   uint32_t lo = 0x7f800000u, hi = 0;  // non-negative floats order as their bits
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -32,6 +33,7 @@ __global__ void __launch_bounds__(256) k_vmag_range(const float* __restrict__ vx
 }
 
 __global__ void k_vmag_range_init(unsigned int* qr) {
+  hp::pdl_enter();
   qr[0] = 0x7f800000u;
   qr[1] = 0;
 }
@@ -44,13 +46,15 @@ void launch_vmag_range(const float* vx, const float* vy, const float* vz, uint64
   uint64_t blocks = (N + 255) / 256, cap = (uint64_t)sms * 8;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  hp::note_launch(), k_vmag_range_init<<<1, 1, 0, s>>>((unsigned int*)qrange);
-  hp::note_launch(), k_vmag_range<<<(unsigned)blocks, 256, 0, s>>>(vx, vy, vz, N, (unsigned int*)qrange);
+  hp::note_launch(), hp::launch_pdl(k_vmag_range_init, 1, 1, 0, s, (unsigned int*)qrange);
+  hp::note_launch(), hp::launch_pdl(k_vmag_range, (unsigned)blocks, 256, 0, s, vx, vy, vz, N,
+                                    (unsigned int*)qrange);
 }
 
 __global__ void __launch_bounds__(256) k_vmag(const float* __restrict__ vx, const float* __restrict__ vy,
                                               const float* __restrict__ vz, uint64_t N,
                                               float* __restrict__ out) {
+  hp::pdl_enter();
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (uint64_t)gridDim.x * blockDim.x)
     out[i] = vmag(vx[i], vy[i], vz[i]);
@@ -64,7 +68,7 @@ void launch_vmag(const float* vx, const float* vy, const float* vz, uint64_t N, 
   uint64_t blocks = (N + 255) / 256, cap = (uint64_t)sms * 16;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  hp::note_launch(), k_vmag<<<(unsigned)blocks, 256, 0, s>>>(vx, vy, vz, N, out);
+  hp::note_launch(), hp::launch_pdl(k_vmag, (unsigned)blocks, 256, 0, s, vx, vy, vz, N, out);
 }
 
 // ----------------------------------------- total velocity V = vx^2 + vy^2 + vz^2
@@ -107,6 +111,7 @@ __global__ void __launch_bounds__(256) k_vtotal_range(const float* __restrict__ 
                                                       const float* __restrict__ vy,
                                                       const float* __restrict__ vz, uint64_t N,
                                                       unsigned long long* vr) {
+  hp::pdl_enter();
   unsigned long long lo = 0x7ff0000000000000ull, hi = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -127,6 +132,7 @@ __global__ void __launch_bounds__(256) k_vtotal_range(const float* __restrict__ 
 }
 
 __global__ void k_vtotal_range_init(unsigned long long* vr) {
+  hp::pdl_enter();
   vr[0] = 0x7ff0000000000000ull;
   vr[1] = 0;
 }
@@ -143,8 +149,8 @@ static uint32_t qoi_grid(uint64_t N, uint32_t per_sm) {
 void launch_vtotal_range(const float* vx, const float* vy, const float* vz, uint64_t N,
                          double* vrange, cstream s) {
   unsigned long long* vr = reinterpret_cast<unsigned long long*>(vrange);
-  hp::note_launch(), k_vtotal_range_init<<<1, 1, 0, s>>>(vr);
-  hp::note_launch(), k_vtotal_range<<<qoi_grid(N, 8), 256, 0, s>>>(vx, vy, vz, N, vr);
+  hp::note_launch(), hp::launch_pdl(k_vtotal_range_init, 1, 1, 0, s, vr);
+  hp::note_launch(), hp::launch_pdl(k_vtotal_range, qoi_grid(N, 8), 256, 0, s, vx, vy, vz, N, vr);
 }
 
 // V_hat into out, and per block the largest pointwise bound with its first
@@ -155,6 +161,7 @@ __global__ void __launch_bounds__(256) k_vtotal_bound(const float* __restrict__ 
                                                       double e0, double e1, double e2,
                                                       float* __restrict__ out,
                                                       unsigned long long* __restrict__ best) {
+  hp::pdl_enter();
   __shared__ unsigned long long s_b[8], s_i[8];
   unsigned long long bb = 0, bi = ~0ull;  // bounds are >= 0: their bits order them
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
@@ -183,6 +190,7 @@ __global__ void __launch_bounds__(256) k_vtotal_bound(const float* __restrict__ 
 }
 
 __global__ void k_vtotal_bound_final(unsigned long long* best, uint32_t nblocks) {
+  hp::pdl_enter();
   unsigned long long bb = 0, bi = ~0ull;
   for (uint32_t k = 0; k < nblocks; k++)
     if (best[2 * k + 1] != ~0ull && (bi == ~0ull || best[2 * k] > bb ||
@@ -197,8 +205,9 @@ uint32_t vtotal_bound_blocks(uint64_t N) { return qoi_grid(N, 4); }
 void launch_vtotal_bound(const float* vx, const float* vy, const float* vz, uint64_t N,
                          const double e[3], float* out, unsigned long long* best, cstream s) {
   const uint32_t g = vtotal_bound_blocks(N);
-  hp::note_launch(), k_vtotal_bound<<<g, 256, 0, s>>>(vx, vy, vz, N, e[0], e[1], e[2], out, best);
-  hp::note_launch(), k_vtotal_bound_final<<<1, 1, 0, s>>>(best, g);
+  hp::note_launch(), hp::launch_pdl(k_vtotal_bound, g, 256, 0, s, vx, vy, vz, N, e[0], e[1], e[2],
+                                    out, best);
+  hp::note_launch(), hp::launch_pdl(k_vtotal_bound_final, 1, 1, 0, s, best, g);
 }
 
 }  // namespace hp

@@ -35,6 +35,7 @@ __device__ __forceinline__ int64_t dequant(uint64_t qh, bool neg, int B, int bl)
 template <typename T>
 __global__ void k_recompose_root(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
                                  const LevelDesc* __restrict__ L0, int64_t* xroot, T* out) {
+  hp::pdl_enter();
   if (m->status) return;
   const int B = m->B, k = 4 * m->cur[0];
   const uint32_t* P = planes + L0->plane_off / 4;
@@ -50,9 +51,11 @@ __global__ void k_recompose_root(const uint32_t* __restrict__ planes, const Fiel
 void launch_recompose_root(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* L0,
                            int64_t* xroot, void* out, int dtype, cstream s) {
   if (dtype == 0)
-    hp::note_launch(), k_recompose_root<float><<<1, 1, 0, s>>>(planes, meta, L0, xroot, (float*)out);
+    hp::note_launch(), hp::launch_pdl(k_recompose_root<float>, 1, 1, 0, s, planes, meta, L0, xroot,
+                                      (float*)out);
   else
-    hp::note_launch(), k_recompose_root<double><<<1, 1, 0, s>>>(planes, meta, L0, xroot, (double*)out);
+    hp::note_launch(), hp::launch_pdl(k_recompose_root<double>, 1, 1, 0, s, planes, meta, L0, xroot,
+                                      (double*)out);
 }
 
 // coarse nodes (all coordinates even in G_h) are copied from G_2h
@@ -61,6 +64,7 @@ __global__ void __launch_bounds__(256) k_recompose_copy(const LevelDesc* __restr
                                                         const int64_t* __restrict__ coarse,
                                                         void* __restrict__ dst,
                                                         const FieldMeta* __restrict__ m) {
+  hp::pdl_enter();
   const LevelDesc& L = *Lp;
   const uint32_t cz = L.gc[0], cy = L.gc[1], cx = L.gc[2];
   const uint64_t total = (uint64_t)cz * cy * cx;
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     k_recompose_level(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
                       const LevelDesc* __restrict__ Lp, const uint32_t* __restrict__ perm,
                       const int64_t* __restrict__ coarse, void* __restrict__ dst) {
+  hp::pdl_enter();
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -326,6 +331,7 @@ __global__ void __launch_bounds__(512)
                       const LevelDesc* __restrict__ levels, int l_end, int nlev,
                       int64_t* xroot, int64_t* xa, int64_t* xb, void* __restrict__ out,
                       bool prefetch) {
+  hp::pdl_enter();
   extern __shared__ __align__(16) uint32_t sm[];
   recompose_small_body<T, B>(planes, m, levels, l_end, nlev, xroot, xa, xb, out, sm, prefetch);
 }
@@ -341,6 +347,7 @@ static int sms() {
 template <typename T>
 __global__ void k_convert_fixed(const int64_t* __restrict__ X, uint64_t n, int E_f,
                                 T* __restrict__ out) {
+  hp::pdl_enter();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     out[i] = convert_out<T>(X[i], E_f);
@@ -351,9 +358,11 @@ void launch_convert_fixed(const int64_t* X, uint64_t n, int E_f, int dtype, void
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 152ull * 8) blocks = 152ull * 8;
   if (dtype == 0)
-    hp::note_launch(), k_convert_fixed<float><<<(unsigned)blocks, 256, 0, s>>>(X, n, E_f, (float*)out);
+    hp::note_launch(), hp::launch_pdl(k_convert_fixed<float>, (unsigned)blocks, 256, 0, s, X, n,
+                                      E_f, (float*)out);
   else
-    hp::note_launch(), k_convert_fixed<double><<<(unsigned)blocks, 256, 0, s>>>(X, n, E_f, (double*)out);
+    hp::note_launch(), hp::launch_pdl(k_convert_fixed<double>, (unsigned)blocks, 256, 0, s, X, n,
+                                      E_f, (double*)out);
 }
 
 void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const int64_t* coarse,
@@ -363,11 +372,14 @@ void launch_recompose_copy(const LevelDesc* Lh, const LevelDesc& Lh_host, const 
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (final_dtype < 0)
-    hp::note_launch(), k_recompose_copy<float, false><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+    hp::note_launch(), hp::launch_pdl(k_recompose_copy<float, false>, (unsigned)blocks, 256, 0, s,
+                                      Lh, coarse, dst, meta);
   else if (final_dtype == 0)
-    hp::note_launch(), k_recompose_copy<float, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+    hp::note_launch(), hp::launch_pdl(k_recompose_copy<float, true>, (unsigned)blocks, 256, 0, s,
+                                      Lh, coarse, dst, meta);
   else
-    hp::note_launch(), k_recompose_copy<double, true><<<(unsigned)blocks, 256, 0, s>>>(Lh, coarse, dst, meta);
+    hp::note_launch(), hp::launch_pdl(k_recompose_copy<double, true>, (unsigned)blocks, 256, 0, s,
+                                      Lh, coarse, dst, meta);
 }
 
 // shared memory for the prefetched plane words (every plane of every small level)
@@ -387,12 +399,12 @@ void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const
   const int most = (int)(base + meta_max + kSmallPrefetchBytes);
   if (dtype == 0) {
     set_smem_once((const void*)k_recompose_small<float, 32>, most);
-    hp::note_launch(), k_recompose_small<float, 32><<<1, 512, smem, s>>>(
-        planes, meta, levels, l_end, nlev, xroot, xa, xb, out, prefetch);
+    hp::note_launch(), hp::launch_pdl(k_recompose_small<float, 32>, 1, 512, smem, s, planes, meta,
+                                      levels, l_end, nlev, xroot, xa, xb, out, prefetch);
   } else {
     set_smem_once((const void*)k_recompose_small<double, 64>, most);
-    hp::note_launch(), k_recompose_small<double, 64><<<1, 512, smem, s>>>(
-        planes, meta, levels, l_end, nlev, xroot, xa, xb, out, prefetch);
+    hp::note_launch(), hp::launch_pdl(k_recompose_small<double, 64>, 1, 512, smem, s, planes, meta,
+                                      levels, l_end, nlev, xroot, xa, xb, out, prefetch);
   }
 }
 
@@ -406,20 +418,25 @@ void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const
   const int thr = B == 32 ? 256 : 128;
   if (B == 32) {
     if (final_dtype < 0)
-      hp::note_launch(), k_recompose_level<float, 32, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
+      hp::note_launch(), hp::launch_pdl(k_recompose_level<float, 32, false>, blocks, thr, 0, s,
+                                        planes, meta, Lh, perm, coarse, dst);
     else
-      hp::note_launch(), k_recompose_level<float, 32, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
+      hp::note_launch(), hp::launch_pdl(k_recompose_level<float, 32, true>, blocks, thr, 0, s,
+                                        planes, meta, Lh, perm, coarse, dst);
   } else {
     if (final_dtype < 0)
-      hp::note_launch(), k_recompose_level<double, 64, false><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
+      hp::note_launch(), hp::launch_pdl(k_recompose_level<double, 64, false>, blocks, thr, 0, s,
+                                        planes, meta, Lh, perm, coarse, dst);
     else
-      hp::note_launch(), k_recompose_level<double, 64, true><<<blocks, thr, 0, s>>>(planes, meta, Lh, perm, coarse, dst);
+      hp::note_launch(), hp::launch_pdl(k_recompose_level<double, 64, true>, blocks, thr, 0, s,
+                                        planes, meta, Lh, perm, coarse, dst);
   }
 }
 
 // ------------------------------------------------------------------ batched
 template <typename T, int B>
 __global__ void __launch_bounds__(512) kb_recompose_small(const BatchJob* __restrict__ jobs) {
+  hp::pdl_enter();
   extern __shared__ uint32_t sm[];
   const BatchJob& J = jobs[blockIdx.x];
   recompose_small_body<T, B>(reinterpret_cast<const uint32_t*>(J.planes), J.meta, J.levels,
@@ -431,10 +448,10 @@ void launch_b_recompose_small(const BatchJob* jobs, uint32_t njobs, int dtype, c
   const size_t smem = (size_t)((dtype == 0 ? 1 : 2) * 16 * 32 * 33 + 16 * 32) * 4;
   if (dtype == 0) {
     set_smem_once((const void*)kb_recompose_small<float, 32>, (int)smem);
-    hp::note_launch(), kb_recompose_small<float, 32><<<njobs, 512, smem, s>>>(jobs);
+    hp::note_launch(), hp::launch_pdl(kb_recompose_small<float, 32>, njobs, 512, smem, s, jobs);
   } else {
     set_smem_once((const void*)kb_recompose_small<double, 64>, (int)smem);
-    hp::note_launch(), kb_recompose_small<double, 64><<<njobs, 512, smem, s>>>(jobs);
+    hp::note_launch(), hp::launch_pdl(kb_recompose_small<double, 64>, njobs, 512, smem, s, jobs);
   }
 }
 
@@ -444,6 +461,7 @@ __global__ void __launch_bounds__(256) kb_recompose_copy(const BatchJob* __restr
                                                          const LevelRef* __restrict__ refs,
                                                          const uint32_t* __restrict__ unit0,
                                                          uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t e = unit_owner(unit0, nrefs, u);
     const LevelRef R = refs[e];
@@ -467,6 +485,7 @@ template <typename T, int B>
 __global__ void __launch_bounds__(B == 32 ? 256 : 128)
     kb_recompose_level(const BatchJob* __restrict__ jobs, const LevelRef* __restrict__ refs,
                        const uint32_t* __restrict__ unit0, uint32_t nrefs, uint32_t total) {
+  hp::pdl_enter();
   constexpr int WPB = B == 32 ? 8 : 4;
   __shared__ uint32_t s_hi[WPB][32 * 33];
   __shared__ uint32_t s_lo[B == 64 ? WPB : 1][B == 64 ? 32 * 33 : 1];
@@ -496,9 +515,11 @@ void launch_b_recompose_copy(const BatchJob* jobs, const LevelRef* refs, const u
   if (!total) return;
   if (grid > total) grid = total;
   if (dtype == 0)
-    hp::note_launch(), kb_recompose_copy<float><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_recompose_copy<float>, grid, 256, 0, s, jobs, refs, unit0,
+                                      nrefs, total);
   else
-    hp::note_launch(), kb_recompose_copy<double><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_recompose_copy<double>, grid, 256, 0, s, jobs, refs, unit0,
+                                      nrefs, total);
 }
 
 void launch_b_recompose_level(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
@@ -507,9 +528,11 @@ void launch_b_recompose_level(const BatchJob* jobs, const LevelRef* refs, const 
   const uint32_t wpb = dtype == 0 ? 8 : 4, need = (total + wpb - 1) / wpb;
   if (grid > need) grid = need;
   if (dtype == 0)
-    hp::note_launch(), kb_recompose_level<float, 32><<<grid, 256, 0, s>>>(jobs, refs, unit0, nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_recompose_level<float, 32>, grid, 256, 0, s, jobs, refs,
+                                      unit0, nrefs, total);
   else
-    hp::note_launch(), kb_recompose_level<double, 64><<<grid, 128, 0, s>>>(jobs, refs, unit0, nrefs, total);
+    hp::note_launch(), hp::launch_pdl(kb_recompose_level<double, 64>, grid, 128, 0, s, jobs, refs,
+                                      unit0, nrefs, total);
 }
 
 }  // namespace hp

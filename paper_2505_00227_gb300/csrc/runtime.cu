@@ -2012,6 +2012,7 @@ extern "C" hpmdr_status hpmdr_retrieve_pipeline(hpmdr_ctx* ctx, int nvars, const
 }
 
 __global__ void k_reset(FieldMeta* m) {
+  hp::pdl_enter();
   for (int l = 0; l < HP_MAX_LEVELS; l++) {
     m->fetched[l] = 0;
     m->cur[l] = 0;
@@ -2021,7 +2022,7 @@ __global__ void k_reset(FieldMeta* m) {
 extern "C" hpmdr_status hpmdr_handle_reset(hpmdr_ctx* ctx, hpmdr_handle* h, int poison) {
   if (!ctx || !h) return HPMDR_ERR_ARG;
   const cudaStream_t s = ctx->stream;
-  hp::note_launch(), k_reset<<<1, 1, 0, s>>>(h->d_meta);
+  hp::note_launch(), hp::launch_pdl(k_reset, 1, 1, 0, s, h->d_meta);
   if (poison && h->d_planes)
     for (int l = 0; l < h->nlev; l++)
       for (int g = 0; g < h->ngroups; g++) {
@@ -2087,7 +2088,7 @@ extern "C" hpmdr_status hpmdr_handle_drop_cache(hpmdr_ctx* ctx, hpmdr_handle* h)
   if (!h->compact) return hpmdr_handle_compact(ctx, h);
   if (!h->d_planes) return HPMDR_OK;
   const cudaStream_t s = ctx->stream;
-  hp::note_launch(), k_reset<<<1, 1, 0, s>>>(h->d_meta);
+  hp::note_launch(), hp::launch_pdl(k_reset, 1, 1, 0, s, h->d_meta);
   h->release_cache(s);
   HP_CUDA(cudaGetLastError());
   return HPMDR_OK;

@@ -181,11 +181,14 @@ __device__ __forceinline__ void sequence_warp(FieldMeta* m, int* g) {
 }
 
 __global__ void k_sequence(FieldMeta* m) {
+  hp::pdl_enter();
   __shared__ int g[64];
   sequence_warp(m, g);
 }
 
-void launch_sequence(FieldMeta* meta, cstream s) { hp::note_launch(), k_sequence<<<1, 32, 0, s>>>(meta); }
+void launch_sequence(FieldMeta* meta, cstream s) {
+  hp::note_launch(), hp::launch_pdl(k_sequence, 1, 32, 0, s, meta);
+}
 
 // floor(tau * 2^(51+B-E_f)) from the IEEE fields of tau, saturating at 2^127
 __device__ u128 tau_units(double tau, int E_f, int B) {
@@ -347,6 +350,7 @@ __device__ void select_prefix(const FieldMeta* m, FieldMeta* mw, double tau, int
 // reads (estimates, sequence, fetched state, group sizes) runs on shared memory.
 __global__ void __launch_bounds__(256) k_select(FieldMeta* m, double tau, int tau_is_abs,
                                                 RetrieveDev* rd) {
+  hp::pdl_enter();
   extern __shared__ __align__(16) unsigned char sel_smem[];
   FieldMeta* sm = reinterpret_cast<FieldMeta*>(sel_smem);
   constexpr uint32_t N16 = sizeof(FieldMeta) / 16, N8 = (sizeof(FieldMeta) % 16) / 8;
@@ -374,26 +378,29 @@ __global__ void __launch_bounds__(256) k_select(FieldMeta* m, double tau, int ta
 
 void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s) {
   set_smem_once((const void*)k_select, (int)sizeof(FieldMeta));
-  hp::note_launch(), k_select<<<1, 256, sizeof(FieldMeta), s>>>(meta, tau, tau_is_abs, rd);
+  hp::note_launch(), hp::launch_pdl(k_select, 1, 256, sizeof(FieldMeta), s, meta, tau, tau_is_abs,
+                                    rd);
 }
 
 // ------------------------------------------------------------------ batched
 __global__ void kb_sequence(const BatchJob* __restrict__ jobs) {
+  hp::pdl_enter();
   __shared__ int g[64];
   sequence_warp(jobs[blockIdx.x].meta, g);
 }
 
 void launch_b_sequence(const BatchJob* jobs, uint32_t njobs, cstream s) {
-  if (njobs) hp::note_launch(), kb_sequence<<<njobs, 32, 0, s>>>(jobs);
+  if (njobs) hp::note_launch(), hp::launch_pdl(kb_sequence, njobs, 32, 0, s, jobs);
 }
 
 __global__ void kb_select(const BatchJob* __restrict__ jobs) {
+  hp::pdl_enter();
   const BatchJob& J = jobs[blockIdx.x];
   select_prefix(J.meta, J.meta, J.tau, 0, J.rd);
 }
 
 void launch_b_select(const BatchJob* jobs, uint32_t njobs, cstream s) {
-  if (njobs) hp::note_launch(), kb_select<<<njobs, 32, 0, s>>>(jobs);
+  if (njobs) hp::note_launch(), hp::launch_pdl(kb_select, njobs, 32, 0, s, jobs);
 }
 
 }  // namespace hp

@@ -9,6 +9,7 @@
 namespace hp {
 
 __global__ void k_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups) {
+  hp::pdl_enter();
   meta->status = 0;
   meta->dtype = dtype;
   meta->B = B;
@@ -31,7 +32,7 @@ __global__ void k_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngr
 }
 
 void launch_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngroups, cstream s) {
-  hp::note_launch(), k_meta_init<<<1, 1, 0, s>>>(meta, dtype, B, nlev, ngroups);
+  hp::note_launch(), hp::launch_pdl(k_meta_init, 1, 1, 0, s, meta, dtype, B, nlev, ngroups);
 }
 
 // Small device -> page-locked host copies written by a kernel (stores through
@@ -55,6 +56,7 @@ __device__ __forceinline__ void to_host_range(const uint32_t* __restrict__ a, ui
 __global__ void __launch_bounds__(256) k_to_host(const uint32_t* __restrict__ a, uint32_t* b,
                                                  uint32_t na, const uint32_t* __restrict__ c,
                                                  uint32_t* d, uint32_t nc) {
+  hp::pdl_enter();
   to_host_range(a, b, na);
   to_host_range(c, d, nc);
 }
@@ -63,7 +65,7 @@ void launch_to_host(const void* a, void* b, size_t na_bytes, const void* c, void
                     size_t nc_bytes, cstream s) {
   const size_t units = (na_bytes + nc_bytes) / 16 + 1;
   const unsigned blocks = (unsigned)std::min<size_t>(16, (units + 255) / 256);
-  hp::note_launch(), k_to_host<<<blocks, 256, 0, s>>>((const uint32_t*)a, (uint32_t*)b,
+  hp::note_launch(), hp::launch_pdl(k_to_host, blocks, 256, 0, s, (const uint32_t*)a, (uint32_t*)b,
                                                       (uint32_t)(na_bytes / 4), (const uint32_t*)c,
                                                       (uint32_t*)d, (uint32_t)(nc_bytes / 4));
 }
@@ -73,6 +75,7 @@ void launch_to_host(const void* a, void* b, size_t na_bytes, const void* c, void
 template <typename T>
 __global__ void __launch_bounds__(256) k_stats(const T* __restrict__ f, uint64_t N,
                                                int aligned, FieldMeta* meta) {
+  hp::pdl_enter();
   constexpr int VEC = 16 / sizeof(T), UN = 4;
   typedef typename std::conditional<sizeof(T) == 4, uint32_t, uint64_t>::type K;
   K am = 0, kn = (K)~(K)0, kx = 0;
@@ -148,9 +151,11 @@ void launch_stats(const void* f, uint64_t N, int dtype, FieldMeta* meta, cstream
   if (want < grid) grid = want ? want : 1;
   int aligned = ((uintptr_t)f & 15) == 0;
   if (dtype == 0)
-    hp::note_launch(), k_stats<float><<<(unsigned)grid, 256, 0, s>>>((const float*)f, N, aligned, meta);
+    hp::note_launch(), hp::launch_pdl(k_stats<float>, (unsigned)grid, 256, 0, s, (const float*)f, N,
+                                      aligned, meta);
   else
-    hp::note_launch(), k_stats<double><<<(unsigned)grid, 256, 0, s>>>((const double*)f, N, aligned, meta);
+    hp::note_launch(), hp::launch_pdl(k_stats<double>, (unsigned)grid, 256, 0, s, (const double*)f,
+                                      N, aligned, meta);
 }
 
 __device__ double key_to_double(uint64_t k, int dtype) {
@@ -196,9 +201,14 @@ __device__ void stats_finalize(FieldMeta* meta) {
   if (bad) meta->status = -1;  // HPMDR_ERR_ARG
 }
 
-__global__ void k_stats_finalize(FieldMeta* meta) { stats_finalize(meta); }
+__global__ void k_stats_finalize(FieldMeta* meta) {
+  hp::pdl_enter();
+  stats_finalize(meta);
+}
 
-void launch_stats_finalize(FieldMeta* meta, cstream s) { hp::note_launch(), k_stats_finalize<<<1, 1, 0, s>>>(meta); }
+void launch_stats_finalize(FieldMeta* meta, cstream s) {
+  hp::note_launch(), hp::launch_pdl(k_stats_finalize, 1, 1, 0, s, meta);
+}
 
 // ------------------------------------------------------------------ batched
 // 16-byte copy of n bytes (both 16-byte aligned, n a multiple of 16)
@@ -218,6 +228,7 @@ static_assert(sizeof(RetrieveDev) % 16 == 0, "RetrieveDev is copied in 16-byte w
 
 // one CTA per job: the plan's initial metadata, zeroed histograms and RLE sizes
 __global__ void __launch_bounds__(256) kb_init(const BatchJob* __restrict__ jobs) {
+  hp::pdl_enter();
   const BatchJob& J = jobs[blockIdx.x];
   block_copy16(J.meta, J.meta0, sizeof(FieldMeta));
   block_zero16(J.hist, 1024ull * J.ngt);
@@ -225,7 +236,7 @@ __global__ void __launch_bounds__(256) kb_init(const BatchJob* __restrict__ jobs
 }
 
 void launch_b_init(const BatchJob* jobs, uint32_t njobs, cstream s) {
-  if (njobs) hp::note_launch(), kb_init<<<njobs, 256, 0, s>>>(jobs);
+  if (njobs) hp::note_launch(), hp::launch_pdl(kb_init, njobs, 256, 0, s, jobs);
 }
 
 // unit = `seg` consecutive values of one field (seg a multiple of 256 * 16 bytes)
@@ -233,6 +244,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) kb_stats(const BatchJob* __restrict__ jobs,
                                                 const uint32_t* __restrict__ unit0, uint32_t njobs,
                                                 uint32_t total, uint32_t seg) {
+  hp::pdl_enter();
   constexpr int VEC = 16 / sizeof(T);
   __shared__ uint64_t sa[8], sb[8], sc[8];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -297,23 +309,28 @@ void launch_b_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
   if (!total) return;
   if (grid > total) grid = total;
   if (dtype == 0)
-    hp::note_launch(), kb_stats<float><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total, seg);
+    hp::note_launch(), hp::launch_pdl(kb_stats<float>, grid, 256, 0, s, jobs, unit0, njobs, total,
+                                      seg);
   else
-    hp::note_launch(), kb_stats<double><<<grid, 256, 0, s>>>(jobs, unit0, njobs, total, seg);
+    hp::note_launch(), hp::launch_pdl(kb_stats<double>, grid, 256, 0, s, jobs, unit0, njobs, total,
+                                      seg);
 }
 
 __global__ void kb_finalize(const BatchJob* __restrict__ jobs, uint32_t njobs) {
+  hp::pdl_enter();
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < njobs) stats_finalize(jobs[j].meta);
 }
 
 void launch_b_finalize(const BatchJob* jobs, uint32_t njobs, cstream s) {
-  if (njobs) hp::note_launch(), kb_finalize<<<(njobs + 63) / 64, 64, 0, s>>>(jobs, njobs);
+  if (njobs) hp::note_launch(), hp::launch_pdl(kb_finalize, (njobs + 63) / 64, 64, 0, s, jobs,
+                                               njobs);
 }
 
 __global__ void __launch_bounds__(256) kb_gather(const BatchJob* __restrict__ jobs,
                                                  FieldMeta* metas, RetrieveDev* rds,
                                                  int32_t* statuses) {
+  hp::pdl_enter();
   const BatchJob& J = jobs[blockIdx.x];
   if (metas) block_copy16(metas + blockIdx.x, J.meta, sizeof(FieldMeta));
   if (rds) block_copy16(rds + blockIdx.x, J.rd, sizeof(RetrieveDev));
@@ -322,7 +339,8 @@ __global__ void __launch_bounds__(256) kb_gather(const BatchJob* __restrict__ jo
 
 void launch_b_gather(const BatchJob* jobs, uint32_t njobs, FieldMeta* metas, RetrieveDev* rds,
                      int32_t* statuses, cstream s) {
-  if (njobs) hp::note_launch(), kb_gather<<<njobs, 256, 0, s>>>(jobs, metas, rds, statuses);
+  if (njobs) hp::note_launch(), hp::launch_pdl(kb_gather, njobs, 256, 0, s, jobs, metas, rds,
+                                               statuses);
 }
 
 }  // namespace hp
