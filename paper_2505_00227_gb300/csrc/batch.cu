@@ -272,13 +272,13 @@ struct hpmdr_batch {
     launch_b_stats(d_jobs, tab<uint32_t>(o_stats), n, t_stats, tune.seg, dtype, g, s);
     launch_b_finalize(d_jobs, n, s);
     launch_b_cells_levelmax(d_jobs, tab<LevelRef>(o_cells_refs), tab<uint32_t>(o_cells_u0),
-                            n_cells_refs, t_cells, g, s);
+                            n_cells_refs, t_cells, g, dtype, s);
     launch_b_gcells_levelmax(d_jobs, tab<LevelRef>(o_gc_refs), tab<uint32_t>(o_gc_u0), n_gc_refs,
                              t_gc, dtype, g, s);
     launch_b_levelmax(d_jobs, tab<uint32_t>(o_gen), n, t_gen, dtype, g, s);
     launch_b_bitlen(d_jobs, n, s);
     launch_b_cells_encode(d_jobs, tab<LevelRef>(o_cells_refs), tab<uint32_t>(o_cells_u0),
-                          n_cells_refs, t_cells, g, s);
+                          n_cells_refs, t_cells, g, dtype, s);
     launch_b_gcells_encode(d_jobs, tab<LevelRef>(o_gc_refs), tab<uint32_t>(o_gc_u0), n_gc_refs,
                            t_gc, dtype, g, s);
     launch_b_pack(d_jobs, tab<LevelRef>(o_gc_refs), tab<uint32_t>(o_pack_u0), n_gc_refs, t_pack,
@@ -303,7 +303,7 @@ struct hpmdr_batch {
     launch_b_recompose_small(d_jobs, n, dtype, s);
     for (const Round& R : rounds) {
       launch_b_cells_recompose(d_jobs, tab<LevelRef>(R.o_cells_refs), tab<uint32_t>(R.o_cells_u0),
-                               R.ncells, R.cells_total, g, s);
+                               R.ncells, R.cells_total, g, dtype, s);
       launch_b_unpack(d_jobs, tab<LevelRef>(R.o_gc_refs), tab<uint32_t>(R.o_unpack_u0), R.ngc,
                       R.unpack_total, dtype == 0 ? 32 : 64, g, s);
       launch_b_gcells_recompose(d_jobs, tab<LevelRef>(R.o_gc_refs), tab<uint32_t>(R.o_gc_u0), R.ngc,

@@ -12,15 +12,14 @@ namespace hp {
 // ------------------------------------------------- programmatic dependent launch
 // Every kernel is launched with programmatic stream serialization and starts by
 // waiting for the grid before it in the stream (griddepcontrol.wait: that grid
-// has completed and its writes are visible), then lets the next grid launch
-// (griddepcontrol.launch_dependents).  The next kernel's launch and CTA
-// scheduling then overlap the end of this one; its CTAs only begin work after
-// this grid has completed, so the stream order of every read and write is the
-// same as with ordinary launches.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// has completed and its writes are visible).  No kernel signals its dependents
+// early, so the next kernel is launched as this one's CTAs exit, and its launch
+// and CTA scheduling overlap the end of this grid instead of following its
+// completion; its CTAs only begin work after this grid has completed, so the
+// stream order of every read and write is that of ordinary launches.  (Signals
+// at kernel start were measured slower: waiting CTAs of the next kernel then
+// hold SM resources while this one's last wave runs.)
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
@@ -152,6 +151,16 @@ __device__ __forceinline__ void ld_nc_v4s64(const int64_t* p, int64_t v[4]) {
   v[1] = b;
   v[2] = c;
   v[3] = d;
+}
+__device__ __forceinline__ void ld_nc_v4d(const double* p, double v[4]) {
+  asm volatile("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+               : "l"(p));
+}
+__device__ __forceinline__ void st_v4d(double* p, const double v[4]) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]),
+               "d"(v[3])
+               : "memory");
 }
 __device__ __forceinline__ void st_v8f(float* p, const float v[8]) {
   asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]),

@@ -245,15 +245,15 @@ void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const
                             const LevelDesc* levels_host, int l_end, int nlev, int64_t* xroot,
                             int64_t* xa, int64_t* xb, void* out, int dtype, cstream s);
 
-// cells.cu (FP32 levels with g_x a multiple of 64)
+// cells.cu (levels with g_x a multiple of 64; FP32, B = 32, or FP64, B = 64)
 bool cell_path_ok(const LevelDesc& L, int B);
-void launch_cells_levelmax(const float* f, const uint64_t dims[3], const LevelDesc* Ld,
+void launch_cells_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
                            const LevelDesc& Lh, FieldMeta* meta, cstream s);
-void launch_cells_encode(const float* f, const uint64_t dims[3], const LevelDesc* Ld,
+void launch_cells_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
                          const LevelDesc& Lh, FieldMeta* meta, uint32_t* planes, cstream s);
 void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,
                             const LevelDesc& Lh, const int64_t* coarse, void* dst, int final,
-                            cstream s);
+                            int B, cstream s);
 
 // batched stage launchers (one launch covers every job).  unit0 tables live
 // in device memory; `grid` is the persistent grid size.
@@ -267,11 +267,12 @@ void launch_b_bitlen(const BatchJob* jobs, uint32_t njobs, cstream s);
 void launch_b_encode(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs, uint32_t total,
                      int dtype, uint32_t grid, cstream s);
 void launch_b_cells_levelmax(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
-                             uint32_t nrefs, uint32_t total, uint32_t grid, cstream s);
+                             uint32_t nrefs, uint32_t total, uint32_t grid, int dtype, cstream s);
 void launch_b_cells_encode(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
-                           uint32_t nrefs, uint32_t total, uint32_t grid, cstream s);
+                           uint32_t nrefs, uint32_t total, uint32_t grid, int dtype, cstream s);
 void launch_b_cells_recompose(const BatchJob* jobs, const LevelRef* refs, const uint32_t* unit0,
-                              uint32_t nrefs, uint32_t total, uint32_t grid, cstream s);
+                              uint32_t nrefs, uint32_t total, uint32_t grid, int dtype,
+                              cstream s);
 uint32_t cell_tiles(const LevelDesc& L);
 void launch_b_chunk_stats(const BatchJob* jobs, const uint32_t* unit0, uint32_t njobs,
                           uint32_t total, uint32_t grid, cstream s);

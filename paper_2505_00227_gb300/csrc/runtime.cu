@@ -418,7 +418,7 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   for (const LevelDesc& D : H->levels)
     if (D.fast == 1) {
       ProfScope p(P, ST_CELLS_MAX, lvl_bytes(D, false), s);
-      launch_cells_levelmax((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta, s);
+      launch_cells_levelmax(f, H->dtype, H->dims, H->d_levels + D.level, D, H->d_meta, s);
     } else if (D.fast == 2) {
       ProfScope p(P, ST_GCELLS_MAX, lvl_bytes(D, false), s);
       launch_gcells_levelmax(f, H->dtype, H->dims, H->d_levels + D.level, D, H->d_meta, s);
@@ -433,7 +433,7 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   for (const LevelDesc& D : H->levels)
     if (D.fast == 1) {
       ProfScope p(P, ST_CELLS_ENC, lvl_bytes(D, true), s);
-      launch_cells_encode((const float*)f, H->dims, H->d_levels + D.level, D, H->d_meta,
+      launch_cells_encode(f, H->dtype, H->dims, H->d_levels + D.level, D, H->d_meta,
                           (uint32_t*)H->d_planes, s);
     } else if (D.fast == 2) {
       { ProfScope p(P, ST_GCELLS_ENC, lvl_bytes(D, false) + qb * D.n, s);
@@ -749,7 +749,7 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
       H->prof_lv.push_back({p.i, l * 8 + (final ? 3 : 1)});
       H->prof_lv.push_back({SIZE_MAX - 1, l * 8 + (final ? 2 : 0)});  // copy folded in
       launch_cells_recompose(Pl, H->d_meta, H->d_levels + l, H->levels[l], coarse, dst,
-                             final ? 1 : 0, s);
+                             final ? 1 : 0, H->B, s);
     } else if (H->levels[l].fast == 2) {
       { ProfScope p(P, ST_UNPACK, 0, s);
         H->prof_lv.push_back({p.i, l * 8 + 4});

@@ -68,6 +68,11 @@ def _fields():
         "cells_512_blobs": S.blobs((2, 9, 512), seed=27).numpy(),
         "cells_1024": S.spectral((3, 5, 1024), seed=26).numpy(),
         "cells_1536": S.spectral((2, 7, 1536), seed=29).numpy(),
+        # FP64 levels of x-extent 128 .. 1024 take the cell kernels with 64 planes
+        "cells_f64_128": S.spectral((8, 12, 128), seed=31, dtype=torch.float64).numpy(),
+        "cells_f64_256_ragged": S.blobs((7, 37, 256), seed=33, dtype=torch.float64).numpy(),
+        "cells_f64_512": S.spectral((4, 6, 512), seed=32, dtype=torch.float64).numpy(),
+        "cells_f64_1024": S.spectral((2, 5, 1024), seed=34, dtype=torch.float64).numpy(),
         # a level maximum exactly at a power of two (C8 = 2^50): the FP32 estimate of
         # the level maximum is ambiguous there and the exact pass must decide
         "cells_power_of_two": _spike((8, 8, 128), (3, 5, 77), 2.0 ** -10),
@@ -169,6 +174,21 @@ def test_absolute_bounds_and_unattainable(ctx, tau_abs):
     f, F, h = _pair(ctx, "spectral_ragged")
     out, info, st = h.retrieve(tau_abs, absolute=True)
     _check_retrieval(f, F, out, info, st, tau_abs)
+
+
+@pytest.mark.parametrize("name", ["cells_f64_512", "cells_f64_256_ragged"])
+def test_f64_cells_deep_bounds(ctx, name):
+    """FP64 cell levels retrieved with more than 32 planes (the low-half planes
+    33..64): tight relative bounds, then every plane (absolute bound 0)."""
+    f, F, h = _pair(ctx, name)
+    for tau in (1e-9, 1e-12, 1e-14):
+        out, info, st = h.retrieve(tau)
+        _check_retrieval(f, F, out, info, st, tau * F.range)
+    out, info, st = h.retrieve(0.0, absolute=True)
+    _check_retrieval(f, F, out, info, st, 0.0)
+    # the sequence stops once every bit of a level is fetched (bl <= 53 < 64),
+    # which on the finest levels takes more than 32 planes
+    assert max(info.groups) > 8
 
 
 @pytest.mark.parametrize("n", [1, 31, 32, 1000, 1025, 4097, 70001])

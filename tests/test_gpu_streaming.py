@@ -52,6 +52,9 @@ def _cases():
         "f32_cells": (S.spectral((16, 16, 128), seed=21).numpy(), (8, 16, 128)),
         # FP32 chunks with a 512-wide finest level (the widest cell tile), ragged along y
         "f32_cells_512": (S.spectral((6, 13, 512), seed=30).numpy(), (3, 7, 512)),
+        # FP64 chunks whose large levels take the 64-plane cell kernels
+        "f64_cells": (S.spectral_trend((8, 16, 256), seed=35, dtype=torch.float64).numpy(),
+                      (4, 8, 256)),
         # one chunk covering everything (equals a plain refactor)
         "f32_single_chunk": (S.blobs((9, 10, 11), seed=22).numpy(), (64, 64, 64)),
         # chunks of one x-row
