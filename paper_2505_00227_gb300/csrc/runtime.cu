@@ -717,27 +717,51 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
   H->prof_decode = SIZE_MAX;
   H->prof_small = SIZE_MAX;
   { ProfScope p(P, ST_SELECT, 0, s); launch_select(H->d_meta, tau, is_abs, H->d_rd, s); }
-  { ProfScope p(P, ST_DECODE, 0, s); H->prof_decode = p.i;
-    launch_decode(H->d_slots, H->d_meta, H->d_rd, H->max_items, H->d_planes, s); }
   const uint32_t* Pl = (const uint32_t*)H->d_planes;
   const int L = H->nlev - 1;
+  // the root and the leading run of small generic levels run in one CTA
+  int l_end = 0;
+  while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= kSmallLevelNodes)
+    l_end++;
+  // When every group of those levels is a direct copy already in the plane
+  // buffer (not a compact handle, whose copies the decode makes), their
+  // recomposition needs nothing from the decode and runs beside it on the
+  // side stream, joined before the next level.
+  bool fork = !H->meta->compact;
+  for (int l = 0; fork && l <= l_end; l++)
+    for (int g = 0; g < H->ngroups; g++)
+      if (H->meta->grp[l][g].method != HPMDR_DC) fork = false;
+  auto small = [&](cudaStream_t st) {
+    ProfScope p(P, ST_SMALL, 0, st);
+    H->prof_small = p.i;
+    H->small_end = l_end;
+    launch_recompose_small(Pl, H->d_meta, H->d_levels, H->levels.data(), l_end, H->nlev,
+                           H->d_xroot, H->d_xa, H->d_xb, d_out, H->dtype, st);
+  };
+  if (fork) {
+    if (!ctx->side) {
+      HP_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+      HP_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+      HP_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
+    HP_CUDA(cudaEventRecord(ctx->ev_fork, s));
+    HP_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    small(ctx->side);
+  }
+  { ProfScope p(P, ST_DECODE, 0, s); H->prof_decode = p.i;
+    launch_decode(H->d_slots, H->d_meta, H->d_rd, H->max_items, H->d_planes, s); }
+  if (fork) {
+    HP_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
+    HP_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+  } else {
+    small(s);  // after the decode, which may write the planes it reads
+  }
   // staging of the general cell levels: scratch of this retrieval only
   // (stream-ordered), so that it is not part of the handle's cache
   const uint64_t gmax = H->plan->gstage_max;
   void* d_gq = nullptr;
   if (gmax) HP_TRY(H->A.alloc(&d_gq, gmax * (H->B / 8 + 1), s));
   uint8_t* d_gsg = (uint8_t*)d_gq + gmax * (H->B / 8);
-  // the root and the leading run of small generic levels run in one CTA
-  int l_end = 0;
-  while (l_end < L && !H->levels[l_end + 1].fast && H->levels[l_end + 1].n <= kSmallLevelNodes)
-    l_end++;
-  {
-    ProfScope p(P, ST_SMALL, 0, s);
-    H->prof_small = p.i;
-    H->small_end = l_end;
-    launch_recompose_small(Pl, H->d_meta, H->d_levels, H->levels.data(), l_end, H->nlev,
-                           H->d_xroot, H->d_xa, H->d_xb, d_out, H->dtype, s);
-  }
   const int64_t* coarse =
       l_end == 0 ? H->d_xroot : (((L - l_end) % 2 == 1) ? H->d_xa : H->d_xb);
   for (int l = l_end + 1; l <= L; l++) {

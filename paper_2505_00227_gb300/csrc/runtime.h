@@ -183,8 +183,15 @@ struct hpmdr_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
   bool copied_pending[2] = {false, false};
+  // a retrieval's root and small levels recomposed beside its decode
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Profiler* P() { return prof.on ? &prof : nullptr; }
   ~hpmdr_ctx() {
+    if (side) cudaStreamSynchronize(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
     if (copy_stream) cudaStreamSynchronize(copy_stream);
     for (int i = 0; i < 2; i++) {
       A.release(out_stage[i], stream);
