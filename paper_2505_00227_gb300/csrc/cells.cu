@@ -253,9 +253,12 @@ __device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict_
     for (int k = 0; k < 4; k++) c[k] = v[2 * k];
     c[4] = __ldg(f + ((size_t)(z << hl) * ny + (y << hl)) * nx + ((size_t)Xe << hl));
   };
+  // the floor flag on the floating-point pipes when 2^(48 - E_f) is a normal float
+  const bool fp_fl = E_f >= -78;
+  const float sc = __int_as_float(((fp_fl ? 48 - E_f : 0) + 127) << 23);
   auto take = [&](float node, float mean) {
     mx = fmaxf(mx, fabsf(__fsub_rn(node, mean)));
-    fl |= float_floors(node, E_f);
+    fl |= fp_fl ? float_floors_fp(node, sc) : float_floors(node, E_f);
   };
   float v[8], c0[5], a[5];
   coarse(Z0, Y0, c0, v, true);

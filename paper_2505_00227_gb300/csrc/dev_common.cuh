@@ -298,6 +298,14 @@ __device__ __forceinline__ uint32_t float_floors(float v, int E_f) {
   return r >= 32 ? 1u : ((m & ((1u << r) - 1u)) != 0u);
 }
 
+// The same flag on the floating-point pipes, for sc = 2^(48 - E_f) a normal
+// float: x = v sc is exact unless it underflows (then |x| < 1 and v != 0 loses
+// everything), and v loses bits exactly when x is not an integer.
+__device__ __forceinline__ uint32_t float_floors_fp(float v, float sc) {
+  const float x = __fmul_rn(v, sc);
+  return (x != truncf(x) || (x == 0.0f && v != 0.0f)) ? 1u : 0u;
+}
+
 // bl from the estimate when it is unambiguous (then m8 = 2^(bl-1)); false:
 // the exact pass must run
 __device__ __forceinline__ bool cells_bl_from_estimate(FieldMeta* meta, int level, bool write) {

@@ -138,9 +138,12 @@ __device__ __forceinline__ void gcells_levelmax_est_range(const GView<float>& v,
                                                           FieldMeta* meta) {
   float mx = 0.0f;
   uint32_t fl = 0;
+  // the floor flag on the floating-point pipes when 2^(48 - E_f) is a normal float
+  const bool fp_fl = v.E_f >= -78;
+  const float sc = __int_as_float(((fp_fl ? 48 - v.E_f : 0) + 127) << 23);
   auto take = [&](float node, float mean) {
     mx = fmaxf(mx, fabsf(__fsub_rn(node, mean)));
-    fl |= float_floors(node, v.E_f);
+    fl |= fp_fl ? float_floors_fp(node, sc) : float_floors(node, v.E_f);
   };
   for (uint32_t c = c0; c < c1; c += step) {
     const CellPos p = cell_pos(L, c);
