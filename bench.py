@@ -694,8 +694,15 @@ def run_profile_step(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2505_00227_gb300 import binding
+    from paper_2505_00227_gb300 import synthetic
     torch.cuda.set_device(0)
-    field = make_field(args.size, 2, "cuda")
+    if args.profile_field == "chunk_f64":  # one 256x256x512 chunk of the FP64 streaming field
+        field = synthetic.spectral_trend((256, 256, 512), seed=3, dtype=torch.float64,
+                                         device="cuda")
+        what = "256x256x512 FP64 chunk"
+    else:
+        field = make_field(args.size, 2, "cuda")
+        what = f"{args.size}^3 FP32 field"
     ctx = binding.Context()
     out = torch.empty_like(field)
     torch.cuda.synchronize()
@@ -705,7 +712,7 @@ def run_profile_step(args):
             h.retrieve(tau, out=out)
         h.free()
     torch.cuda.synchronize()
-    print(f"profile step ok: {args.profile_steps} step(s) of the {args.size}^3 field", flush=True)
+    print(f"profile step ok: {args.profile_steps} step(s) of the {what}", flush=True)
 
 
 # ------------------------------------------------- one section on its own
@@ -1000,6 +1007,8 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="run --profile-steps untimed steps for an ncu capture and exit")
     ap.add_argument("--profile-steps", type=int, default=1)
+    ap.add_argument("--profile-field", choices=["spectral_f32", "chunk_f64"],
+                    default="spectral_f32")
     ap.add_argument("--section", choices=SECTIONS, default=None,
                     help="run one bench section alone (no bench line) and exit")
     args = ap.parse_args()

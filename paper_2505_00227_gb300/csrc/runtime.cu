@@ -119,6 +119,11 @@ static void plan_levels(Plan& P) {
     }
     D.n = (uint32_t)n;
     D.W = (uint32_t)(4 * ((n + 127) / 128));
+    // every level starts on a 256-byte boundary of the plane buffer (padding
+    // between levels, never inside a group): with W a multiple of 8 words, a
+    // warp's 32 consecutive words of a plane then cover 4 whole 32-byte
+    // sectors instead of straddling 5
+    poff = (poff + 255) & ~(uint64_t)255;
     D.plane_off = poff;
     poff += (uint64_t)(P.B + 1) * D.W * 4;
     D.tile0 = tile;
