@@ -1,6 +1,6 @@
-// Cell-based kernels for the large, regular levels (FP32, level grid x-extent
-// a multiple of 64): level max, quantize + Algorithm 1 bitplane encoding, and
-// recomposition.  They compute exactly what the generic tile kernels compute
+// Cell-based kernels for the large, regular levels (FP32 or FP64, level grid
+// x-extent a multiple of 64): level max, quantize + Algorithm 1 bitplane
+// encoding, and recomposition.  They compute exactly what the generic tile kernels compute
 // (same coefficients, same bits), organised around 2x2x2 cells instead of the
 // level-linear order.
 //
