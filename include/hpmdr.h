@@ -220,6 +220,19 @@ HPMDR_API hpmdr_status hpmdr_retrieve_qoi_vtotal(hpmdr_ctx* ctx, hpmdr_handle* v
                                                  double rel_qoi_bound, int estimator, double c,
                                                  void* out[3], void* out_qoi, int on_device,
                                                  hpmdr_qoi_report* rep);
+/* One bounding step of hpmdr_retrieve_qoi_vtotal (Sec. 6.2, Algorithm 3's QoI
+ * error estimate) on given components: out[i] = V_hat = RN32(RN64(RN64(vx^2 +
+ * vy^2) + vz^2)) (squares exact in FP64), and the largest pointwise bound on
+ * |V_hat - V| for |x_hat_i - x_i| <= e[i] (2 |x_hat_i| e_i + e_i^2 summed, plus
+ * the FP32 rounding of V_hat: 2^-24 V_hat, 2^-150 below the normal range,
+ * +inf past FLT_MAX, and 2^-50 V_hat for the FP64 additions; FP64, every
+ * operation rounded to nearest) with its first point.  vx, vy, vz, out: device
+ * arrays of n FP32 values (caller owned); e: host, 3 values >= 0; *bound and
+ * *point: host.  Synchronous on the context stream.  HPMDR_ERR_ARG for n = 0,
+ * a NULL pointer or a negative e. */
+HPMDR_API hpmdr_status hpmdr_qoi_vtotal_bound(hpmdr_ctx* ctx, const float* vx, const float* vy,
+                                              const float* vz, uint64_t n, const double e[3],
+                                              float* out, double* bound, uint64_t* point);
 
 /* ---- handle inspection -------------------------------------------------- */
 HPMDR_API hpmdr_status hpmdr_handle_field_info(const hpmdr_handle* h, int* dtype, uint64_t dims[3],

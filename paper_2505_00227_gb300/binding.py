@@ -114,6 +114,8 @@ _SIGS = {
                                           C.POINTER(C.c_double), C.c_int, vp, vp]),
     "hpmdr_ctx_profile_stages": (C.c_int, [vp, C.c_uint64]),
     "hpmdr_fixed_to_float": (C.c_int, [vp, vp, C.c_uint64, C.c_int, C.c_int, vp]),
+    "hpmdr_qoi_vtotal_bound": (C.c_int, [vp, vp, vp, vp, C.c_uint64, C.c_double * 3, vp,
+                                         C.POINTER(C.c_double), u64p]),
     "hpmdr_refactor_chunked": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_uint64 * 3, C.c_uint64 * 3,
                                          C.c_int, C.c_int, C.POINTER(vp), C.c_uint64, u64p]),
     "hpmdr_retrieve_chunked": (C.c_int, [vp, C.POINTER(vp), C.c_uint64, C.c_int, C.c_uint64 * 3,
@@ -450,6 +452,20 @@ class Context:
                                           F32 if dtype == torch.float32 else F64,
                                           vp(out.data_ptr())), "hpmdr_fixed_to_float")
         return out
+
+
+    def vtotal_bound(self, vx, vy, vz, e):
+        """One QoI bounding step on three device FP32 tensors of one shape:
+        (V_hat, largest pointwise bound, its first point)."""
+        import torch
+        out = torch.empty(vx.shape, dtype=torch.float32, device=vx.device)
+        b, pt = C.c_double(), C.c_uint64()
+        _check(lib().hpmdr_qoi_vtotal_bound(self._p, vp(vx.data_ptr()), vp(vy.data_ptr()),
+                                            vp(vz.data_ptr()), vx.numel(),
+                                            (C.c_double * 3)(*[float(x) for x in e]),
+                                            vp(out.data_ptr()), C.byref(b), C.byref(pt)),
+               "hpmdr_qoi_vtotal_bound")
+        return out, b.value, pt.value
 
 
 class Handle:

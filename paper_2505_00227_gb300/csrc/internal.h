@@ -338,8 +338,10 @@ void launch_vmag(const float* vx, const float* vy, const float* vz, uint64_t N, 
 void launch_vtotal_range(const float* vx, const float* vy, const float* vz, uint64_t N,
                          double* vrange /* device: [min, max] */, cstream s);
 uint32_t vtotal_bound_blocks(uint64_t N);
+// bytes of the scratch `best` of launch_vtotal_bound (8-byte aligned)
+uint64_t vtotal_bound_scratch(uint64_t N);
 // out = V_hat; best[0] = bits of the largest pointwise bound, best[1] = its
-// first point (best holds 2 * vtotal_bound_blocks(N) words)
+// first point (best holds vtotal_bound_scratch(N) bytes)
 void launch_vtotal_bound(const float* vx, const float* vy, const float* vz, uint64_t N,
                          const double e[3], float* out, unsigned long long* best, cstream s);
 

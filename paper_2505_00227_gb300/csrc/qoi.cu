@@ -81,6 +81,43 @@ __device__ __forceinline__ double vtotal(float x, float y, float z) {
   return __dadd_rn(__dadd_rn(a, b), c);
 }
 
+// float(V_hat) without the FP64 pipe where that is provably the same value.
+// With |x|, |y|, |z| each 0 or in [2^-32, 2^60], the squares are split exactly
+// into FP32 pairs (x^2 = ah + al by one FMA) and summed with two exact
+// two-sums: V = s2 + L exactly, L a sum of five terms of at most 3 2^-24 V in
+// total, so its FP32 rounding errs by < 2^-44 V.  r = RN32(s2 + L) and the
+// residual d ~ V - r (d's own rounding < 2^-25 ulp(r)); the FP64 V_hat is
+// within 2^-51 V of V, so V_hat - r = d + err with |err| < 2^-19 ulp(r).  When
+// d + err stays strictly inside r's rounding interval (half an ulp above r; half
+// or, at a power of two, a quarter of an ulp below) RN32(V_hat) = r; otherwise
+// (within 2^-19 ulp of a midpoint, a tie, or the ranges left out) the FP64
+// evaluation decides.
+__device__ __forceinline__ float vtotal_f32(float x, float y, float z) {
+  const float ax = fabsf(x), ay = fabsf(y), az = fabsf(z);
+  const bool in = (ax == 0.0f || (ax >= 0x1p-32f && ax <= 0x1p60f)) &&
+                  (ay == 0.0f || (ay >= 0x1p-32f && ay <= 0x1p60f)) &&
+                  (az == 0.0f || (az >= 0x1p-32f && az <= 0x1p60f));
+  if (in) {
+    const float ah = __fmul_rn(x, x), al = __fmaf_rn(x, x, -ah);
+    const float bh = __fmul_rn(y, y), bl = __fmaf_rn(y, y, -bh);
+    const float ch = __fmul_rn(z, z), cl = __fmaf_rn(z, z, -ch);
+    const float s1 = __fadd_rn(ah, bh), t1 = __fsub_rn(s1, ah);
+    const float e1 = __fadd_rn(__fsub_rn(ah, __fsub_rn(s1, t1)), __fsub_rn(bh, t1));
+    const float s2 = __fadd_rn(s1, ch), t2 = __fsub_rn(s2, s1);
+    const float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, t2)), __fsub_rn(ch, t2));
+    if (s2 == 0.0f) return 0.0f;  // all three zero
+    const float L = __fadd_rn(__fadd_rn(__fadd_rn(al, bl), __fadd_rn(cl, e1)), e2);
+    const float r = __fadd_rn(s2, L);
+    const float d = __fadd_rn(__fsub_rn(s2, r), L);  // s2 - r is exact
+    const uint32_t rb = __float_as_uint(r);
+    const float u = __uint_as_float(((rb >> 23) - 23u) << 23);  // ulp(r); r >= 2^-64
+    const float m = d >= 0.0f ? __fmul_rn(u, 0.5f - 0x1p-19f)
+                              : __fmul_rn(u, ((rb & 0x7fffffu) ? 0.5f : 0.25f) - 0x1p-19f);
+    if (fabsf(d) < m) return r;
+  }
+  return __double2float_rn(vtotal(x, y, z));
+}
+
 // bound on |float(V_hat) - V| at one point for |x_hat_i - x_i| <= e_i:
 // sum of 2 |x_hat| e + e^2, the FP32 rounding of V_hat (relative 2^-24, 2^-150
 // absolute below the normal range, infinite past the FP32 range) and the FP64
@@ -153,61 +190,167 @@ void launch_vtotal_range(const float* vx, const float* vy, const float* vz, uint
   hp::note_launch(), hp::launch_pdl(k_vtotal_range, qoi_grid(N, 8), 256, 0, s, vx, vy, vz, N, vr);
 }
 
-// V_hat into out, and per block the largest pointwise bound with its first
-// point (best[2 block] = bound bits, best[2 block + 1] = point)
-__global__ void __launch_bounds__(256) k_vtotal_bound(const float* __restrict__ vx,
+// The largest pointwise bound only decides the iteration, so the FP64 bound is
+// evaluated only where it can be the largest.  A bracket lo <= b <= hi of the
+// FP64 bound b (vtotal_point_bound) in FP32 with directed rounding: the same
+// terms over the real numbers, with e_i rounded down (up), widened by 2^-20
+// relative (the FP64 evaluation rounds a dozen times, each within 2^-53) and by
+// the smallest FP32 subnormal (underflow, the 2^-150 term).  Overflow gives
+// hi = +inf (a candidate) and lo <= FLT_MAX, below b = +inf.  Pass 1 writes
+// V_hat and each block's largest lo; pass 2 takes T = max lo <= max b and
+// evaluates b exactly at the points with hi >= T, which include every point
+// whose b equals max b.  An FP64 V_hat above FLT_MAX (b = +inf) needs V within
+// 2^-52 relative of FLT_MAX, so hi is +inf from V >= 0x1.fffp127 on.
+__device__ __forceinline__ float vtotal_bound_lo(float x, float y, float z, const float el[3]) {
+  const float xs[3] = {x, y, z};
+  float b = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    const float t = __fmul_rd(__fmul_rd(2.0f, fabsf(xs[i])), el[i]);
+    b = __fadd_rd(b, __fadd_rd(t, __fmul_rd(el[i], el[i])));
+  }
+  const float v = __fadd_rd(__fadd_rd(__fmul_rd(x, x), __fmul_rd(y, y)), __fmul_rd(z, z));
+  b = __fadd_rd(b, __fmul_rd(v, 0x1p-24f));
+  b = __fadd_rd(b, __fmul_rd(v, 0x1p-50f));
+  b = __fsub_rd(__fmul_rd(b, 1.0f - 0x1p-20f), 0x1p-149f);
+  return b > 0.0f ? b : 0.0f;  // (a NaN gives 0)
+}
+
+__device__ __forceinline__ float vtotal_bound_hi(float x, float y, float z, const float eh[3]) {
+  const float xs[3] = {x, y, z};
+  float b = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    const float t = __fmul_ru(__fmul_ru(2.0f, fabsf(xs[i])), eh[i]);
+    b = __fadd_ru(b, __fadd_ru(t, __fmul_ru(eh[i], eh[i])));
+  }
+  const float v = __fadd_ru(__fadd_ru(__fmul_ru(x, x), __fmul_ru(y, y)), __fmul_ru(z, z));
+  // the FP64 V_hat can round past FLT_MAX (b = +inf) from just below it
+  if (v > 0x1.fffp127f) return __int_as_float(0x7f800000);
+  b = __fadd_ru(b, __fmul_ru(v, 0x1p-24f));
+  b = __fadd_ru(b, 0x1p-149f);
+  b = __fadd_ru(b, __fmul_ru(v, 0x1p-50f));
+  return __fadd_ru(__fmul_ru(b, 1.0f + 0x1p-20f), 0x1p-149f);
+}
+
+// pass 1: V_hat into out, lo_part[block] = the block's largest lo
+__global__ void __launch_bounds__(256) k_vtotal_value(const float* __restrict__ vx,
                                                       const float* __restrict__ vy,
                                                       const float* __restrict__ vz, uint64_t N,
                                                       double e0, double e1, double e2,
                                                       float* __restrict__ out,
-                                                      unsigned long long* __restrict__ best) {
+                                                      float* __restrict__ lo_part) {
   hp::pdl_enter();
-  __shared__ unsigned long long s_b[8], s_i[8];
-  unsigned long long bb = 0, bi = ~0ull;  // bounds are >= 0: their bits order them
+  __shared__ float s_lo[8];
+  const float el[3] = {__double2float_rd(e0), __double2float_rd(e1), __double2float_rd(e2)};
+  float lo = 0.0f;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const float x = vx[i], y = vy[i], z = vz[i];
-    out[i] = __double2float_rn(vtotal(x, y, z));
-    const unsigned long long b =
-        (unsigned long long)__double_as_longlong(vtotal_point_bound(x, y, z, e0, e1, e2));
-    if (bi == ~0ull || b > bb) bb = b, bi = i;  // a thread's points ascend: keep the first
+    out[i] = vtotal_f32(x, y, z);
+    lo = fmaxf(lo, vtotal_bound_lo(x, y, z, el));
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) lo = fmaxf(lo, __shfl_xor_sync(HP_FULL, lo, o));
+  if ((threadIdx.x & 31) == 0) s_lo[threadIdx.x >> 5] = lo;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < 8; k++) lo = fmaxf(lo, s_lo[k]);
+    lo_part[blockIdx.x] = lo;
+  }
+}
+
+// (b, i) beats (bb, bi): a valid point with a larger bound, or the same bound at
+// an earlier point (bounds are >= 0, so their bits order them)
+__device__ __forceinline__ bool vtotal_better(unsigned long long b, unsigned long long i,
+                                              unsigned long long bb, unsigned long long bi) {
+  return i != ~0ull && (bi == ~0ull || b > bb || (b == bb && i < bi));
+}
+
+__device__ __forceinline__ void vtotal_warp_best(unsigned long long& bb, unsigned long long& bi) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     const unsigned long long ob = __shfl_xor_sync(HP_FULL, bb, o), oi = __shfl_xor_sync(HP_FULL, bi, o);
-    if (oi != ~0ull && (bi == ~0ull || ob > bb || (ob == bb && oi < bi))) bb = ob, bi = oi;
+    if (vtotal_better(ob, oi, bb, bi)) bb = ob, bi = oi;
   }
+}
+
+// pass 2: per block the largest FP64 pointwise bound among the candidates, with
+// its first point (best[2 block] = bound bits, best[2 block + 1] = point)
+__global__ void __launch_bounds__(256) k_vtotal_bound(const float* __restrict__ vx,
+                                                      const float* __restrict__ vy,
+                                                      const float* __restrict__ vz, uint64_t N,
+                                                      double e0, double e1, double e2,
+                                                      const float* __restrict__ lo_part,
+                                                      uint32_t nparts,
+                                                      unsigned long long* __restrict__ best) {
+  hp::pdl_enter();
+  __shared__ unsigned long long s_b[8], s_i[8];
+  __shared__ float s_t[8];
+  float T = 0.0f;
+  for (uint32_t k = threadIdx.x; k < nparts; k += blockDim.x) T = fmaxf(T, lo_part[k]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) T = fmaxf(T, __shfl_xor_sync(HP_FULL, T, o));
+  if ((threadIdx.x & 31) == 0) s_t[threadIdx.x >> 5] = T;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 8; k++) T = fmaxf(T, s_t[k]);
+  const float eh[3] = {__double2float_ru(e0), __double2float_ru(e1), __double2float_ru(e2)};
+  unsigned long long bb = 0, bi = ~0ull;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const float x = vx[i], y = vy[i], z = vz[i];
+    if (!(vtotal_bound_hi(x, y, z, eh) < T)) {  // a candidate (a NaN bracket too)
+      const unsigned long long b =
+          (unsigned long long)__double_as_longlong(vtotal_point_bound(x, y, z, e0, e1, e2));
+      if (bi == ~0ull || b > bb) bb = b, bi = i;  // a thread's points ascend: keep the first
+    }
+  }
+  vtotal_warp_best(bb, bi);
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) s_b[w] = bb, s_i[w] = bi;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int k = 1; k < 8; k++)
-      if (s_i[k] != ~0ull && (bi == ~0ull || s_b[k] > bb || (s_b[k] == bb && s_i[k] < bi)))
-        bb = s_b[k], bi = s_i[k];
+      if (vtotal_better(s_b[k], s_i[k], bb, bi)) bb = s_b[k], bi = s_i[k];
     best[2 * blockIdx.x] = bb;
     best[2 * blockIdx.x + 1] = bi;
   }
 }
 
-__global__ void k_vtotal_bound_final(unsigned long long* best, uint32_t nblocks) {
+// the blocks' results -> best[0], best[1] (one block of 256 threads)
+__global__ void __launch_bounds__(256) k_vtotal_bound_final(unsigned long long* best,
+                                                            uint32_t nblocks) {
   hp::pdl_enter();
+  __shared__ unsigned long long s_b[8], s_i[8];
   unsigned long long bb = 0, bi = ~0ull;
-  for (uint32_t k = 0; k < nblocks; k++)
-    if (best[2 * k + 1] != ~0ull && (bi == ~0ull || best[2 * k] > bb ||
-                                     (best[2 * k] == bb && best[2 * k + 1] < bi)))
-      bb = best[2 * k], bi = best[2 * k + 1];
-  best[0] = bb;
-  best[1] = bi;
+  for (uint32_t k = threadIdx.x; k < nblocks; k += blockDim.x)
+    if (vtotal_better(best[2 * k], best[2 * k + 1], bb, bi)) bb = best[2 * k], bi = best[2 * k + 1];
+  vtotal_warp_best(bb, bi);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) s_b[w] = bb, s_i[w] = bi;
+  __syncthreads();  // every read of best[] is done before it is overwritten
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < 8; k++)
+      if (vtotal_better(s_b[k], s_i[k], bb, bi)) bb = s_b[k], bi = s_i[k];
+    best[0] = bb;
+    best[1] = bi;
+  }
 }
 
 uint32_t vtotal_bound_blocks(uint64_t N) { return qoi_grid(N, 4); }
 
+uint64_t vtotal_bound_scratch(uint64_t N) { return 24ull * vtotal_bound_blocks(N); }
+
 void launch_vtotal_bound(const float* vx, const float* vy, const float* vz, uint64_t N,
                          const double e[3], float* out, unsigned long long* best, cstream s) {
   const uint32_t g = vtotal_bound_blocks(N);
+  float* lo_part = reinterpret_cast<float*>(best + 2 * (size_t)g);
+  hp::note_launch(), hp::launch_pdl(k_vtotal_value, g, 256, 0, s, vx, vy, vz, N, e[0], e[1], e[2],
+                                    out, lo_part);
   hp::note_launch(), hp::launch_pdl(k_vtotal_bound, g, 256, 0, s, vx, vy, vz, N, e[0], e[1], e[2],
-                                    out, best);
-  hp::note_launch(), hp::launch_pdl(k_vtotal_bound_final, 1, 1, 0, s, best, g);
+                                    (const float*)lo_part, g, best);
+  hp::note_launch(), hp::launch_pdl(k_vtotal_bound_final, 1, 256, 0, s, best, g);
 }
 
 }  // namespace hp

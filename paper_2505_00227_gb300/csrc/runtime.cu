@@ -1366,7 +1366,7 @@ extern "C" hpmdr_status hpmdr_retrieve_qoi_vtotal(hpmdr_ctx* ctx, hpmdr_handle* 
     }
     if (st) break;
     if (!d_q && (st = ctx->A.alloc(&d_q, N * 4, s))) break;
-    if ((st = ctx->A.alloc((void**)&d_best, 16ull * vtotal_bound_blocks(N), s))) break;
+    if ((st = ctx->A.alloc((void**)&d_best, vtotal_bound_scratch(N), s))) break;
     for (int it = 1; it <= 4096 && st == HPMDR_OK; it++) {
       bool full = true;
       uint64_t fetched = 0;
@@ -2296,6 +2296,29 @@ extern "C" hpmdr_status hpmdr_fixed_to_float(hpmdr_ctx* ctx, const int64_t* X, u
   launch_convert_fixed(X, n, E_f, (int)dtype, out, ctx->stream);
   HP_CUDA(cudaGetLastError());
   HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HPMDR_OK;
+}
+
+extern "C" hpmdr_status hpmdr_qoi_vtotal_bound(hpmdr_ctx* ctx, const float* vx, const float* vy,
+                                               const float* vz, uint64_t n, const double e[3],
+                                               float* out, double* bound, uint64_t* point) {
+  if (!ctx || !n || !vx || !vy || !vz || !e || !out || !bound || !point) return HPMDR_ERR_ARG;
+  for (int i = 0; i < 3; i++)
+    if (!(e[i] >= 0.0)) return HPMDR_ERR_ARG;
+  const cudaStream_t s = ctx->stream;
+  unsigned long long* d_best = nullptr;
+  HP_TRY(ctx->A.alloc((void**)&d_best, vtotal_bound_scratch(n), s));
+  launch_vtotal_bound(vx, vy, vz, n, e, out, d_best, s);
+  unsigned long long best[2] = {0, 0};
+  hpmdr_status st = HPMDR_OK;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(best, d_best, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    st = HPMDR_ERR_CUDA;
+  ctx->A.release(d_best, s);
+  if (st) return st;
+  memcpy(bound, &best[0], 8);
+  *point = best[1];
   return HPMDR_OK;
 }
 
