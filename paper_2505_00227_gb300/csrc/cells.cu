@@ -746,9 +746,9 @@ __device__ __forceinline__ void cells_recompose_tile(const uint32_t* __restrict_
       };
       int64_t c0[5], a[5];
       load(cz, cy, c0);
+      load(cz, cy1, a);  // both rows' loads in flight before the first row's work
       emit(0, 0, c0);
       if (hy) {
-        load(cz, cy1, a);
 #pragma unroll
         for (int q = 0; q < 5; q++) a[q] += c0[q];
         emit(0, 1, a);
