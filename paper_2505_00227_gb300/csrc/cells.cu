@@ -218,10 +218,38 @@ __device__ __forceinline__ void cells_levelmax_flush(FieldMeta* meta, int level,
 // within about 2^-10 of a power of two at the usual magnitudes, a near-zero
 // level, a tiny field) the exact pass runs for the level.  The floor flag of
 // the level's own nodes is exact in both passes.
+//
+// STATS (the finest level, hl = 0): the same pass also gives the field
+// statistics of Sec. 4 (max|f|, min f, max f as order keys) and the least
+// set-bit exponent of the values, so the field is read once for both; the
+// estimate needs no E_f (its bound is applied after E_f is known), and the
+// floor flag is decided from the least exponent once E_f is (FieldMeta::lsb_min).
+// Every value lies in the four rows (Z0 | Z0+1, Y0 | Y0+1) of exactly one
+// thread's cells, which are the rows STATS visits.
+struct FieldStats32 {
+  uint32_t am, kn, kx;  // abs key max, order key min and max (as k_stats)
+  int32_t lsb;          // least exponent of a set bit (INT32_MAX: none)
+};
+
+__device__ __forceinline__ void fstats_add(FieldStats32& st, float v) {
+  const uint32_t u = __float_as_uint(v), a = u & 0x7fffffffu;
+  const uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  st.am = a > st.am ? a : st.am;
+  st.kn = o < st.kn ? o : st.kn;
+  st.kx = o > st.kx ? o : st.kx;
+  if (a) {  // v = m 2^(e - 150) (normal) or m 2^-149 (subnormal)
+    const uint32_t e = a >> 23, m = e ? ((a & 0x7fffffu) | 0x800000u) : a;
+    const int32_t lsb = (int32_t)(e ? e : 1u) - 151 + __ffs((int)m);
+    st.lsb = lsb < st.lsb ? lsb : st.lsb;
+  }
+}
+
+template <bool STATS = false>
 __device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict__ f,
                                                         const CellGeom& G, uint32_t ny,
                                                         uint32_t nx, int hl, int E_f, uint32_t tile,
-                                                        float& mx, uint32_t& fl) {
+                                                        float& mx, uint32_t& fl,
+                                                        FieldStats32* st = nullptr) {
   const uint32_t i = threadIdx.x, per_row = G.XW / 4;
   uint32_t cz, cy0, x0;
   tile_origin(G, tile, cz, cy0, x0);
@@ -258,10 +286,17 @@ __device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict_
   const float sc = __int_as_float(((fp_fl ? 48 - E_f : 0) + 127) << 23);
   auto take = [&](float node, float mean) {
     mx = fmaxf(mx, fabsf(__fsub_rn(node, mean)));
-    fl |= fp_fl ? float_floors_fp(node, sc) : float_floors(node, E_f);
+    if (!STATS) fl |= fp_fl ? float_floors_fp(node, sc) : float_floors(node, E_f);
+  };
+  auto own = [&](const float v[8]) {  // a row of this thread's cells (STATS)
+    if (STATS) {
+#pragma unroll
+      for (int k = 0; k < 8; k++) fstats_add(*st, v[k]);
+    }
   };
   float v[8], c0[5], a[5];
   coarse(Z0, Y0, c0, v, true);
+  own(v);
 #pragma unroll
   for (int k = 0; k < 4; k++) take(v[2 * k + 1], __fmul_rn(__fadd_rn(c0[k], c0[k + 1]), 0.5f));
   if (hy) {
@@ -269,6 +304,7 @@ __device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict_
 #pragma unroll
     for (int k = 0; k < 5; k++) a[k] = __fadd_rn(a[k], c0[k]);
     seg(Z0, Y0 + 1, v, true);
+    own(v);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       take(v[2 * k], __fmul_rn(a[k], 0.5f));
@@ -281,6 +317,7 @@ __device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict_
 #pragma unroll
     for (int k = 0; k < 5; k++) c0[k] = __fadd_rn(c0[k], c1[k]);
     seg(Z0 + 1, Y0, v, true);
+    own(v);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       take(v[2 * k], __fmul_rn(c0[k], 0.5f));
@@ -292,6 +329,7 @@ __device__ __forceinline__ void cells_levelmax_est_tile(const float* __restrict_
 #pragma unroll
       for (int k = 0; k < 5; k++) a[k] = __fadd_rn(a[k], __fadd_rn(c1[k], c3[k]));
       seg(Z0 + 1, Y0 + 1, v, true);
+      own(v);
 #pragma unroll
       for (int k = 0; k < 4; k++) {
         take(v[2 * k], __fmul_rn(a[k], 0.25f));
@@ -320,6 +358,38 @@ __global__ void __launch_bounds__(256, 4) k_cells_levelmax_est(const float* __re
   if ((threadIdx.x & 31) == 0) {
     if (mx > 0.0f) atomicMax(&meta->m8est[L.level], __float_as_uint(mx));  // order of >= 0 floats
     if (anyfl) atomicOr(&meta->floored, 1u);
+  }
+}
+
+// field statistics and the finest level's estimate in one read (FP32, the
+// finest level on the cell path); k_stats_finalize follows
+__global__ void __launch_bounds__(256, 4) k_stats_cells(const float* __restrict__ f, uint32_t ny,
+                                                     uint32_t nx, const LevelDesc* __restrict__ Lp,
+                                                     FieldMeta* meta) {
+  hp::pdl_enter();
+  if (meta->status) return;
+  const LevelDesc& L = *Lp;
+  const CellGeom G = cell_geom(L);
+  float mx = 0.0f;
+  uint32_t fl = 0;
+  FieldStats32 st{0u, 0xffffffffu, 0u, 0x7fffffff};
+  for (uint32_t tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x)
+    cells_levelmax_est_tile<true>(f, G, ny, nx, 0, 0, tile, mx, fl, &st);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(HP_FULL, mx, o));
+    st.am = max(st.am, __shfl_xor_sync(HP_FULL, st.am, o));
+    st.kn = min(st.kn, __shfl_xor_sync(HP_FULL, st.kn, o));
+    st.kx = max(st.kx, __shfl_xor_sync(HP_FULL, st.kx, o));
+    st.lsb = min(st.lsb, __shfl_xor_sync(HP_FULL, st.lsb, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mx > 0.0f) atomicMax(&meta->m8est[L.level], __float_as_uint(mx));  // order of >= 0 floats
+    atomicMax((unsigned long long*)&meta->key_absmax, (unsigned long long)st.am);
+    atomicMin((unsigned long long*)&meta->key_min,
+              st.kn == 0xffffffffu ? ~0ull : (unsigned long long)st.kn);
+    atomicMax((unsigned long long*)&meta->key_max, (unsigned long long)st.kx);
+    if (st.lsb != 0x7fffffff) atomicMin(&meta->lsb_min, st.lsb);
   }
 }
 
@@ -509,7 +579,7 @@ static int nsm() {
 // FP32: the estimate pass, then the exact pass where the estimate left bl open;
 // FP64: the exact pass
 void launch_cells_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
-                           const LevelDesc& Lh, FieldMeta* meta, cstream s) {
+                           const LevelDesc& Lh, FieldMeta* meta, cstream s, bool est_done) {
   const CellGeom G = cell_geom(Lh);
   // one wave of resident CTAs (4 per SM), each looping over tiles
   uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 4;
@@ -517,14 +587,29 @@ void launch_cells_levelmax(const void* f, int dtype, const uint64_t dims[3], con
   if (!blocks) return;
   const uint32_t ny = (uint32_t)dims[1], nx = (uint32_t)dims[2];
   if (dtype == 0) {
-    hp::note_launch(), hp::launch_pdl(k_cells_levelmax_est, blocks, 256, 0, s, (const float*)f, ny,
-                                      nx, Ld, meta);
+    if (!est_done)
+      hp::note_launch(), hp::launch_pdl(k_cells_levelmax_est, blocks, 256, 0, s, (const float*)f,
+                                        ny, nx, Ld, meta);
     hp::note_launch(), hp::launch_pdl(k_cells_levelmax<float>, blocks, 256, 0, s, (const float*)f,
                                       ny, nx, Ld, meta);
   } else {
     hp::note_launch(), hp::launch_pdl(k_cells_levelmax<double>, blocks, 256, 0, s,
                                       (const double*)f, ny, nx, Ld, meta);
   }
+}
+
+bool stats_cells_ok(int dtype, const LevelDesc& Lh) {
+  return dtype == 0 && Lh.fast == 1 && Lh.hlog == 0;
+}
+
+void launch_stats_cells(const float* f, const uint64_t dims[3], const LevelDesc* Ld,
+                        const LevelDesc& Lh, FieldMeta* meta, cstream s) {
+  const CellGeom G = cell_geom(Lh);
+  uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 4;
+  if (blocks > cap) blocks = cap;
+  if (!blocks) return;
+  hp::note_launch(), hp::launch_pdl(k_stats_cells, blocks, 256, 0, s, f, (uint32_t)dims[1],
+                                    (uint32_t)dims[2], Ld, meta);
 }
 
 void launch_cells_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,

@@ -149,10 +149,12 @@ void launch_levelmax(const void* f, int dtype, const uint64_t dims[3], const Lev
   }
 }
 
-// bl_l = bit length of max|C8|; input exactness from the floor flags
+// bl_l = bit length of max|C8|; input exactness from the floor flags and the
+// least set-bit exponent of the fused statistics pass
 __device__ __forceinline__ void bitlen_level(FieldMeta* meta, int l) {
   if (l < meta->nlev) meta->bl[l] = meta->m8[l] ? bitlen64(meta->m8[l]) : 0;
-  if (l == 0) meta->input_exact = meta->floored ? 0 : 1;
+  if (l == 0)
+    meta->input_exact = (meta->floored || meta->lsb_min < meta->E_f - 48) ? 0 : 1;
 }
 
 __global__ void k_bitlen(FieldMeta* meta) {

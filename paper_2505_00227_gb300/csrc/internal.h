@@ -66,7 +66,10 @@ struct alignas(16) FieldMeta {
   uint64_t key_absmax, key_min, key_max;  // order-preserving keys of max|f|, min, max
   double maxabs, vmin, vmax, range;
   uint32_t floored;                       // some f_i lost bits in the fixed point
-  uint32_t pad0;
+  // least exponent e of a set bit (weight 2^e) over the values the fused
+  // statistics pass saw (INT32_MAX: none); some value loses bits in the fixed
+  // point exactly when lsb_min < E_f - 48
+  int32_t lsb_min;
   uint64_t m8[HP_MAX_LEVELS];             // max |C8| per level
   uint64_t lowbits[HP_MAX_LEVELS];        // OR of the bits dropped by alignment
   uint32_t m8est[HP_MAX_LEVELS];          // FP32 bits of max |detail| from the estimate pass
@@ -247,8 +250,14 @@ void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const
 
 // cells.cu (levels with g_x a multiple of 64; FP32, B = 32, or FP64, B = 64)
 bool cell_path_ok(const LevelDesc& L, int B);
+// est_done: the FP32 estimate of this level came with the statistics pass
 void launch_cells_levelmax(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
-                           const LevelDesc& Lh, FieldMeta* meta, cstream s);
+                           const LevelDesc& Lh, FieldMeta* meta, cstream s, bool est_done = false);
+// the field statistics and the finest level's FP32 estimate in one read of the
+// field (FP32 fields whose finest level takes the cell kernels)
+bool stats_cells_ok(int dtype, const LevelDesc& finest);
+void launch_stats_cells(const float* f, const uint64_t dims[3], const LevelDesc* Ld,
+                        const LevelDesc& Lh, FieldMeta* meta, cstream s);
 void launch_cells_encode(const void* f, int dtype, const uint64_t dims[3], const LevelDesc* Ld,
                          const LevelDesc& Lh, FieldMeta* meta, uint32_t* planes, cstream s);
 void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* Ld,

@@ -219,6 +219,7 @@ static void init_meta(FieldMeta& M, int dtype, int B, int nlev, int ngroups) {
   M.key_min = ~0ull;
   M.key_max = 0;
   M.floored = 0;
+  M.lsb_min = INT32_MAX;
   for (int l = 0; l < HP_MAX_LEVELS; l++) M.exact[l] = 1;
   M.seq_len = 0;
   M.compact = 0;
@@ -410,7 +411,14 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   ChunkMap cm{H->d_chunk_group, H->total_chunks};
   Profiler* P = ctx->P();
   const double fb = (double)H->N * esz, pb = (double)H->plane_bytes, cb = 4.0 * tc + 1032.0 * ngt;
-  { ProfScope p(P, ST_STATS, fb, s); launch_stats(f, H->N, H->dtype, H->d_meta, s); }
+  // FP32 with a cell-path finest level: the statistics and that level's
+  // estimate share one read of the field
+  const LevelDesc& Dfin = H->levels[H->nlev - 1];
+  const bool fused = stats_cells_ok(H->dtype, Dfin);
+  { ProfScope p(P, ST_STATS, fb, s);
+    if (fused) launch_stats_cells((const float*)f, H->dims, H->d_levels + Dfin.level, Dfin,
+                                  H->d_meta, s);
+    else launch_stats(f, H->N, H->dtype, H->d_meta, s); }
   { ProfScope p(P, ST_FINALIZE, 0, s); launch_stats_finalize(H->d_meta, s); }
   // algorithmic bytes: the field once (split over the level kernels by node
   // count) and each level's planes once
@@ -423,7 +431,8 @@ static hpmdr_status refactor_enqueue(hpmdr_ctx* ctx, hpmdr_handle* H, const void
   for (const LevelDesc& D : H->levels)
     if (D.fast == 1) {
       ProfScope p(P, ST_CELLS_MAX, lvl_bytes(D, false), s);
-      launch_cells_levelmax(f, H->dtype, H->dims, H->d_levels + D.level, D, H->d_meta, s);
+      launch_cells_levelmax(f, H->dtype, H->dims, H->d_levels + D.level, D, H->d_meta, s,
+                            fused && D.level == Dfin.level);
     } else if (D.fast == 2) {
       ProfScope p(P, ST_GCELLS_MAX, lvl_bytes(D, false), s);
       launch_gcells_levelmax(f, H->dtype, H->dims, H->d_levels + D.level, D, H->d_meta, s);

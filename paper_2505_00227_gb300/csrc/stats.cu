@@ -19,6 +19,7 @@ __global__ void k_meta_init(FieldMeta* meta, int dtype, int B, int nlev, int ngr
   meta->key_min = ~0ull;
   meta->key_max = 0;
   meta->floored = 0;
+  meta->lsb_min = 0x7fffffff;
   for (int l = 0; l < HP_MAX_LEVELS; l++) {
     meta->m8[l] = 0;
     meta->lowbits[l] = 0;
