@@ -1046,15 +1046,20 @@ __global__ void __launch_bounds__(256, 3) k_cells_recompose64(const uint32_t* __
     cells_recompose_tile64<FINAL>(P, L, G, E_f, bl, k, coarse, dst, tile, S);
 }
 
+// The CTAs that share an SM (blocks b, b + sms, b + 2 sms, ... under the
+// block scheduler's round-robin placement) start 0.5 us apart: otherwise they
+// run their words phases (integer issue) and their cells phases (memory) in
+// step, and neither unit is kept busy while the other phase runs.
 template <bool FINAL>
 __global__ void __launch_bounds__(256, 4) k_cells_recompose(const uint32_t* __restrict__ planes,
                                                          const FieldMeta* __restrict__ meta,
                                                          const LevelDesc* __restrict__ Lp,
                                                          const int64_t* __restrict__ coarse,
-                                                         void* __restrict__ dst) {
+                                                         void* __restrict__ dst, uint32_t sms) {
   hp::pdl_enter();
   __shared__ CellQ s_q;
   __shared__ CellSW s_sw;
+  if (const uint32_t slot = blockIdx.x / sms) __nanosleep(500u * slot);
   if (meta->status) return;
   const LevelDesc& L = *Lp;
   const CellGeom G = cell_geom(L);
@@ -1090,12 +1095,13 @@ void launch_cells_recompose(const uint32_t* planes, const FieldMeta* meta, const
   uint32_t blocks = G.ntiles, cap = (uint32_t)nsm() * 4;  // one wave, 4 CTAs per SM
   if (blocks > cap) blocks = cap;
   if (!blocks) return;
+  const uint32_t sms = (uint32_t)nsm();
   if (final)
     hp::note_launch(), hp::launch_pdl(k_cells_recompose<true>, blocks, 256, 0, s, planes, meta, Ld,
-                                      coarse, dst);
+                                      coarse, dst, sms);
   else
     hp::note_launch(), hp::launch_pdl(k_cells_recompose<false>, blocks, 256, 0, s, planes, meta, Ld,
-                                      coarse, dst);
+                                      coarse, dst, sms);
 }
 
 // ------------------------------------------------------------------ batched
