@@ -78,6 +78,13 @@ def _fields():
         "cells_power_of_two": _spike((8, 8, 128), (3, 5, 77), 2.0 ** -10),
         # all-zero finest level apart from one value below the fixed-point unit
         "cells_floored": _spike((8, 8, 128), (2, 2, 6), 1.0, extra=((4, 4, 9), 1e-30)),
+        # the statistics pass decides input exactness from the least set-bit
+        # exponent: integers are exact; values spanning the FP32 subnormals (E_f far
+        # below -78) lose bits; a single half-unit value among exact ones loses bits
+        "cells_integers": rng.integers(-1000, 1000, size=(6, 8, 128)).astype(np.float32),
+        "cells_subnormal": (S.spectral((4, 8, 128), seed=36).numpy() *
+                            np.float32(1e-36)).astype(np.float32),
+        "cells_one_inexact": _spike((4, 8, 128), (1, 2, 3), 2.0 ** 40, extra=((3, 7, 100), 2.0 ** -9)),
         # values far below max|f|: the estimate's bound scales with max|f|
         "cells_wide_range": (S.spectral((8, 16, 128), seed=24).numpy() *
                              np.float32(1e-6)).astype(np.float32) +
