@@ -647,37 +647,57 @@ __device__ __forceinline__ void huff_encode_unit(const uint8_t* __restrict__ pla
       wv[k] = x;
     }
   }
+  // a word of four zero bytes (the common case in the sparse planes Huffman
+  // wins on) appends code[0] four times in one step when it has <= 8 bits
+  const uint32_t L0 = len[0];
+  const bool zfast = L0 > 0 && L0 <= 8;
+  const uint32_t c0 = code[0], z4len = 4 * L0;
+  const uint32_t z4 = zfast ? (((c0 << L0 | c0) << L0 | c0) << L0 | c0) : 0u;
   uint32_t bits = 0;
 #pragma unroll
-  for (int k = 0; k < 16; k++)
+  for (int k = 0; k < 16; k++) {
+    if (zfast && wv[k] == 0 && 4u * k + 3 < nb) {
+      bits += z4len;
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < 4; q++)
       if (4u * k + q < nb) bits += len[(wv[k] >> (8 * q)) & 0xffu];
+  }
   uint32_t total;
   const uint32_t pos = block_exscan(bits, scratch, total);
   uint64_t acc = 0;  // pending bits, MSB-aligned
   int nacc = (int)(pos & 31);
   uint32_t wd = pos >> 5;
   bool shared_word = true;  // the first word may hold the previous thread's bits
+  // append L <= 32 bits of value v (nacc < 32 before, so < 64 after)
+  auto put = [&](uint32_t v, int L) {
+    acc |= (uint64_t)v << (64 - nacc - L);
+    nacc += L;
+    if (nacc >= 32) {
+      const uint32_t hi = (uint32_t)(acc >> 32);
+      if (shared_word) atomicOr(&outw[wd], hi);
+      else outw[wd] = hi;
+      shared_word = false;
+      acc <<= 32;
+      nacc -= 32;
+      wd++;
+    }
+  };
 #pragma unroll
-  for (int k = 0; k < 16; k++)
+  for (int k = 0; k < 16; k++) {
+    if (zfast && wv[k] == 0 && 4u * k + 3 < nb) {
+      put(z4, (int)z4len);
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       if (4u * k + q < nb) {
-        const uint32_t sym = (wv[k] >> (8 * q)) & 0xffu, L = len[sym];
-        acc |= (uint64_t)code[sym] << (64 - nacc - (int)L);
-        nacc += (int)L;
-        if (nacc >= 32) {
-          const uint32_t hi = (uint32_t)(acc >> 32);
-          if (shared_word) atomicOr(&outw[wd], hi);
-          else outw[wd] = hi;
-          shared_word = false;
-          acc <<= 32;
-          nacc -= 32;
-          wd++;
-        }
+        const uint32_t sym = (wv[k] >> (8 * q)) & 0xffu;
+        put(code[sym], (int)len[sym]);
       }
     }
+  }
   if (nacc > 0 && bits > 0) atomicOr(&outw[wd], (uint32_t)(acc >> 32));  // shared with the next
   __syncthreads();
   const uint32_t nwords = (total + 31) / 32;
