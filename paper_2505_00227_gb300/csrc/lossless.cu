@@ -115,6 +115,10 @@ __device__ __forceinline__ void chunk_stats_unit(const uint8_t* __restrict__ pla
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       const uint32_t x = wv[k];
+      if ((x | pb) == 0) {  // four zero bytes after a zero byte: no run starts
+        zeros += 4;
+        continue;
+      }
       const uint32_t d = x ^ ((x << 8) | pb);  // each byte against its predecessor
       const uint32_t nz = (((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d) & 0x80808080u;
       // bits 7, 15, 23, 31 gathered to bits 0..3 (the partial products never overlap)
@@ -443,14 +447,20 @@ __device__ __forceinline__ void huff_bits_unit(const uint8_t* __restrict__ plane
   __syncthreads();
   const uint8_t* src = planes + r.gm->plane_off + r.start;
   uint32_t bits = 0;
+  const uint32_t z4 = 4u * len[0];  // a word of four zero bytes
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
   for (uint32_t i = threadIdx.x; i < r.len / 16; i += blockDim.x) {
     uint4 v = __ldcs(s4 + i);
     uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int k = 0; k < 4; k++)
+    for (int k = 0; k < 4; k++) {
+      if (wv[k] == 0) {
+        bits += z4;
+        continue;
+      }
 #pragma unroll
       for (int b = 0; b < 4; b++) bits += len[(wv[k] >> (8 * b)) & 0xffu];
+    }
   }
   for (uint32_t i = (r.len & ~15u) + threadIdx.x; i < r.len; i += blockDim.x) bits += len[src[i]];
   for (int o = 16; o; o >>= 1) bits += __shfl_xor_sync(HP_FULL, bits, o);
