@@ -230,8 +230,19 @@ void launch_decode(const uint8_t* slots, FieldMeta* meta, const RetrieveDev* rd,
                    uint32_t max_items, uint8_t* planes, cstream s);
 
 // select.cu
+// The groups used per level l <= l_end by a retrieval (l_end < 0: none given)
+struct SmallSel {
+  int32_t l_end;
+  int32_t cur[HP_MAX_LEVELS];
+};
 void launch_sequence(FieldMeta* meta, cstream s);
-void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s);
+// hs (may be null): a host selection of the small levels, checked against the
+// device's (a mismatch sets the retrieval status to HPMDR_ERR_CORRUPT)
+void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s,
+                   const SmallSel* hs = nullptr);
+// k_select's choice for levels 0 .. l_end, computed on the host from its copy
+// of the metadata, so that those levels can be recomposed beside k_select
+void host_select_small(const FieldMeta& m, double tau, int tau_is_abs, int l_end, SmallSel* out);
 
 // recompose.cu  (final_dtype: -1 = int64 level grid, 0 = float out, 1 = double out)
 void launch_recompose_root(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* L0,
@@ -244,9 +255,12 @@ void launch_recompose_level(const uint32_t* planes, const FieldMeta* meta, const
                             void* dst, int B, int final_dtype, cstream s);
 // root + levels 1..l_end (generic, small) in one CTA; levels_host: the host
 // copy of the level descriptors
+// hs (may be null): the groups per small level from host_select_small, used
+// instead of the metadata's current selection (which k_select may be writing)
 void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* levels,
                             const LevelDesc* levels_host, int l_end, int nlev, int64_t* xroot,
-                            int64_t* xa, int64_t* xb, void* out, int dtype, cstream s);
+                            int64_t* xa, int64_t* xb, void* out, int dtype, cstream s,
+                            const SmallSel* hs = nullptr);
 
 // cells.cu (levels with g_x a multiple of 64; FP32, B = 32, or FP64, B = 64)
 bool cell_path_ok(const LevelDesc& L, int B);

@@ -207,7 +207,8 @@ __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict_
                                                      int l_end, int nlev, int64_t* xroot,
                                                      int64_t* xa, int64_t* xb,
                                                      void* __restrict__ out, uint32_t* sm,
-                                                     bool prefetch) {
+                                                     bool prefetch,
+                                                     const int32_t* hcur = nullptr) {
   constexpr int WPB = 16;
   uint32_t* s_hi = sm;                                      // [WPB][32*33]
   uint32_t* s_lo = sm + WPB * 32 * 33;                      // [WPB][32*33] (B = 64)
@@ -224,7 +225,7 @@ __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict_
     const uint32_t* src = reinterpret_cast<const uint32_t*>(levels);
     for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) reinterpret_cast<uint32_t*>(s_desc)[i] = src[i];
     if (threadIdx.x <= (unsigned)l_end) {
-      s_k[threadIdx.x] = 4 * m->cur[threadIdx.x];
+      s_k[threadIdx.x] = 4 * (hcur ? hcur[threadIdx.x] : m->cur[threadIdx.x]);
       s_bl[threadIdx.x] = m->bl[threadIdx.x];
     }
     __syncthreads();
@@ -258,7 +259,7 @@ __device__ __forceinline__ void recompose_small_body(const uint32_t* __restrict_
   auto level_planes = [&](int l) -> const uint32_t* {
     return prefetch ? s_pl + acc_pl : planes + Ls[l].plane_off / 4;
   };
-  auto level_k = [&](int l) { return prefetch ? s_k[l] : 4 * m->cur[l]; };
+  auto level_k = [&](int l) { return prefetch ? s_k[l] : 4 * (hcur ? hcur[l] : m->cur[l]); };
   const int L = nlev - 1, w = threadIdx.x >> 5, E_f = m->E_f;
   if (threadIdx.x < 32) {  // the root: lane p reads plane p, a ballot gathers q
     const int lane = threadIdx.x;
@@ -330,10 +331,11 @@ __global__ void __launch_bounds__(512)
     k_recompose_small(const uint32_t* __restrict__ planes, const FieldMeta* __restrict__ m,
                       const LevelDesc* __restrict__ levels, int l_end, int nlev,
                       int64_t* xroot, int64_t* xa, int64_t* xb, void* __restrict__ out,
-                      bool prefetch) {
+                      bool prefetch, SmallSel hs) {
   hp::pdl_enter();
   extern __shared__ __align__(16) uint32_t sm[];
-  recompose_small_body<T, B>(planes, m, levels, l_end, nlev, xroot, xa, xb, out, sm, prefetch);
+  recompose_small_body<T, B>(planes, m, levels, l_end, nlev, xroot, xa, xb, out, sm, prefetch,
+                             hs.l_end >= 0 ? hs.cur : nullptr);
 }
 
 static int sms() {
@@ -387,7 +389,11 @@ constexpr size_t kSmallPrefetchBytes = 48 * 1024;
 
 void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const LevelDesc* levels,
                             const LevelDesc* levels_host, int l_end, int nlev, int64_t* xroot,
-                            int64_t* xa, int64_t* xb, void* out, int dtype, cstream s) {
+                            int64_t* xa, int64_t* xb, void* out, int dtype, cstream s,
+                            const SmallSel* hs) {
+  SmallSel h;
+  h.l_end = -1;
+  if (hs) h = *hs;
   const int B = dtype == 0 ? 32 : 64;
   const size_t base = (size_t)((dtype == 0 ? 1 : 2) * 16 * 32 * 33 + 16 * 32) * 4;
   const size_t meta_bytes = (size_t)(l_end + 1) * (sizeof(LevelDesc) + 8) + 16;
@@ -400,11 +406,11 @@ void launch_recompose_small(const uint32_t* planes, const FieldMeta* meta, const
   if (dtype == 0) {
     set_smem_once((const void*)k_recompose_small<float, 32>, most);
     hp::note_launch(), hp::launch_pdl(k_recompose_small<float, 32>, 1, 512, smem, s, planes, meta,
-                                      levels, l_end, nlev, xroot, xa, xb, out, prefetch);
+                                      levels, l_end, nlev, xroot, xa, xb, out, prefetch, h);
   } else {
     set_smem_once((const void*)k_recompose_small<double, 64>, most);
     hp::note_launch(), hp::launch_pdl(k_recompose_small<double, 64>, 1, 512, smem, s, planes, meta,
-                                      levels, l_end, nlev, xroot, xa, xb, out, prefetch);
+                                      levels, l_end, nlev, xroot, xa, xb, out, prefetch, h);
   }
 }
 

@@ -730,7 +730,6 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
   H->prof_lv.clear();
   H->prof_decode = SIZE_MAX;
   H->prof_small = SIZE_MAX;
-  { ProfScope p(P, ST_SELECT, 0, s); launch_select(H->d_meta, tau, is_abs, H->d_rd, s); }
   const uint32_t* Pl = (const uint32_t*)H->d_planes;
   const int L = H->nlev - 1;
   // the root and the leading run of small generic levels run in one CTA
@@ -741,16 +740,22 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
   // buffer (not a compact handle, whose copies the decode makes), their
   // recomposition needs nothing from the decode and runs beside it on the
   // side stream, joined before the next level.
+  // Their groups per level are computed on the host too (host_select_small, the
+  // same choice k_select makes, which k_select checks), so the kernel starts with
+  // k_select rather than after it.
   bool fork = !H->meta->compact;
   for (int l = 0; fork && l <= l_end; l++)
     for (int g = 0; g < H->ngroups; g++)
       if (H->meta->grp[l][g].method != HPMDR_DC) fork = false;
-  auto small = [&](cudaStream_t st) {
+  SmallSel hs;
+  hs.l_end = -1;
+  if (fork) host_select_small(*H->meta, tau, is_abs, l_end, &hs);
+  auto small = [&](cudaStream_t st, const SmallSel* sel) {
     ProfScope p(P, ST_SMALL, 0, st);
     H->prof_small = p.i;
     H->small_end = l_end;
     launch_recompose_small(Pl, H->d_meta, H->d_levels, H->levels.data(), l_end, H->nlev,
-                           H->d_xroot, H->d_xa, H->d_xb, d_out, H->dtype, st);
+                           H->d_xroot, H->d_xa, H->d_xb, d_out, H->dtype, st, sel);
   };
   if (fork) {
     if (!ctx->side) {
@@ -758,17 +763,19 @@ static hpmdr_status enqueue_retrieve(hpmdr_ctx* ctx, hpmdr_handle* H, double tau
       HP_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
       HP_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     }
-    HP_CUDA(cudaEventRecord(ctx->ev_fork, s));
+    HP_CUDA(cudaEventRecord(ctx->ev_fork, s));  // after the previous retrieval's kernels
     HP_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-    small(ctx->side);
+    small(ctx->side, &hs);
   }
+  { ProfScope p(P, ST_SELECT, 0, s);
+    launch_select(H->d_meta, tau, is_abs, H->d_rd, s, fork ? &hs : nullptr); }
   { ProfScope p(P, ST_DECODE, 0, s); H->prof_decode = p.i;
     launch_decode(H->d_slots, H->d_meta, H->d_rd, H->max_items, H->d_planes, s); }
   if (fork) {
     HP_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
     HP_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
   } else {
-    small(s);  // after the decode, which may write the planes it reads
+    small(s, nullptr);  // after the decode, which may write the planes it reads
   }
   // staging of the general cell levels: scratch of this retrieval only
   // (stream-ordered), so that it is not part of the handle's cache

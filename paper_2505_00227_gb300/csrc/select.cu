@@ -20,10 +20,18 @@ namespace hp {
 
 typedef unsigned __int128 u128;
 
-__device__ __forceinline__ u128 p2(int e) {
+__host__ __device__ __forceinline__ u128 p2(int e) {
   if (e < 0) return 0;
   if (e > 127) e = 127;
   return (u128)1 << e;
+}
+
+__host__ __device__ __forceinline__ int bitlen64_hd(uint64_t v) {
+#ifdef __CUDA_ARCH__
+  return 64 - __clzll((long long)v);
+#else
+  return v ? 64 - __builtin_clzll(v) : 0;
+#endif
 }
 
 __device__ __forceinline__ u128 sat_add(u128 a, u128 b) {
@@ -191,8 +199,10 @@ void launch_sequence(FieldMeta* meta, cstream s) {
 }
 
 // floor(tau * 2^(51+B-E_f)) from the IEEE fields of tau, saturating at 2^127
-__device__ u128 tau_units(double tau, int E_f, int B) {
-  const uint64_t u = (uint64_t)__double_as_longlong(tau);
+// (integer work only: the host computes the same value)
+__host__ __device__ u128 tau_units(double tau, int E_f, int B) {
+  uint64_t u;
+  memcpy(&u, &tau, 8);
   if (u >> 63) return 0;                       // negative (or -0)
   const uint32_t e = (uint32_t)(u >> 52);
   if (e == 0x7ff) return (u & 0xfffffffffffffull) ? 0 : p2(127);  // NaN -> 0, inf -> max
@@ -206,7 +216,7 @@ __device__ u128 tau_units(double tau, int E_f, int B) {
   if (m == 0) return 0;
   const int s = ex + 51 + B - E_f;             // tau = m 2^ex, scaled: m 2^s
   if (s >= 0) {
-    if (bitlen64(m) + s > 127) return p2(127);
+    if (bitlen64_hd(m) + s > 127) return p2(127);
     return (u128)m << s;
   }
   if (-s >= 64) return 0;
@@ -219,7 +229,7 @@ __device__ u128 tau_units(double tau, int E_f, int B) {
 // m: the metadata read (a shared-memory copy, or the field's own); mw: the
 // field's metadata, where the fetched state is updated.
 __device__ void select_prefix(const FieldMeta* m, FieldMeta* mw, double tau, int tau_is_abs,
-                              RetrieveDev* rd) {
+                              RetrieveDev* rd, const SmallSel* hs = nullptr) {
   __shared__ int s_g[HP_MAX_LEVELS + 1];
   __shared__ int s_c;
   const int lane = threadIdx.x & 31;
@@ -269,6 +279,11 @@ __device__ void select_prefix(const FieldMeta* m, FieldMeta* mw, double tau, int
   }
   for (int i = lane; i < c; i += 32) atomicAdd(&s_g[m->seq[i]], 1);
   __syncwarp();
+  // the small levels were recomposed with the host's selection (host_select_small):
+  // it must be this one
+  if (hs && hs->l_end >= 0 &&
+      __any_sync(HP_FULL, lane <= hs->l_end && s_g[lane] != hs->cur[lane]))
+    status = -4;  // HPMDR_ERR_CORRUPT
   uint64_t bnew = 0, btot = 0;
   for (int l = lane; l < nlev; l += 32) {
     const int gl = s_g[l], f0 = m->fetched[l], fe = gl > f0 ? gl : f0;
@@ -349,7 +364,7 @@ __device__ void select_prefix(const FieldMeta* m, FieldMeta* mw, double tau, int
 // units, 8 loads in flight per thread), so that the warp's chain of dependent
 // reads (estimates, sequence, fetched state, group sizes) runs on shared memory.
 __global__ void __launch_bounds__(256) k_select(FieldMeta* m, double tau, int tau_is_abs,
-                                                RetrieveDev* rd) {
+                                                RetrieveDev* rd, SmallSel hs) {
   hp::pdl_enter();
   extern __shared__ __align__(16) unsigned char sel_smem[];
   FieldMeta* sm = reinterpret_cast<FieldMeta*>(sel_smem);
@@ -373,13 +388,39 @@ __global__ void __launch_bounds__(256) k_select(FieldMeta* m, double tau, int ta
     reinterpret_cast<uint64_t*>(sm)[2 * N16 + threadIdx.x] =
         reinterpret_cast<const uint64_t*>(m)[2 * N16 + threadIdx.x];
   __syncthreads();
-  if (threadIdx.x < 32) select_prefix(sm, m, tau, tau_is_abs, rd);
+  if (threadIdx.x < 32) select_prefix(sm, m, tau, tau_is_abs, rd, &hs);
 }
 
-void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s) {
+void launch_select(FieldMeta* meta, double tau, int tau_is_abs, RetrieveDev* rd, cstream s,
+                   const SmallSel* hs) {
+  SmallSel h;
+  h.l_end = -1;
+  if (hs) h = *hs;
   set_smem_once((const void*)k_select, (int)sizeof(FieldMeta));
   hp::note_launch(), hp::launch_pdl(k_select, 1, 256, sizeof(FieldMeta), s, meta, tau, tau_is_abs,
-                                    rd);
+                                    rd, h);
+}
+
+// The groups per level l <= l_end that k_select will choose for tau, from the
+// host copy of the metadata (the greedy sequence and its estimates): the
+// shortest prefix whose estimate is at most tau in the same 128-bit units (the
+// estimates never increase along the sequence), all of it when none is.
+void host_select_small(const FieldMeta& m, double tau, int tau_is_abs, int l_end, SmallSel* out) {
+  const double tau_abs = tau_is_abs ? tau : tau * m.range;
+  const u128 T = tau_units(tau_abs, m.E_f, m.B);
+  const int n = m.seq_len;
+  int c = n;
+  for (int i = 0; i <= n; i++) {
+    const u128 E = ((u128)m.E_hi[i] << 64) | m.E_lo[i];
+    if (!(E > T)) {
+      c = i;
+      break;
+    }
+  }
+  out->l_end = l_end;
+  for (int l = 0; l < HP_MAX_LEVELS; l++) out->cur[l] = 0;
+  for (int i = 0; i < c; i++)
+    if (m.seq[i] <= l_end) out->cur[m.seq[i]]++;
 }
 
 // ------------------------------------------------------------------ batched
