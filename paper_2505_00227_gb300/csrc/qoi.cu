@@ -233,6 +233,35 @@ __device__ __forceinline__ float vtotal_bound_hi(float x, float y, float z, cons
   return __fadd_ru(__fmul_ru(b, 1.0f + 0x1p-20f), 0x1p-149f);
 }
 
+// A thread's points in ascending order: four consecutive points per step with
+// 16-byte loads when the arrays allow it, then the tail one at a time.
+// f(i, x, y, z) per point.
+template <typename F>
+__device__ __forceinline__ void vtotal_points(const float* __restrict__ vx,
+                                              const float* __restrict__ vy,
+                                              const float* __restrict__ vz, uint64_t N,
+                                              bool vec, F&& f) {
+  const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t st = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t n4 = vec ? N / 4 : 0;
+  for (uint64_t g = t0; g < n4; g += st) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(vx) + g);
+    const float4 b = __ldg(reinterpret_cast<const float4*>(vy) + g);
+    const float4 c = __ldg(reinterpret_cast<const float4*>(vz) + g);
+    f(4 * g, a.x, b.x, c.x);
+    f(4 * g + 1, a.y, b.y, c.y);
+    f(4 * g + 2, a.z, b.z, c.z);
+    f(4 * g + 3, a.w, b.w, c.w);
+  }
+  for (uint64_t i = 4 * n4 + t0; i < N; i += st) f(i, vx[i], vy[i], vz[i]);
+}
+
+__device__ __forceinline__ bool aligned16(const void* a, const void* b, const void* c,
+                                          const void* d) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+           reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+}
+
 // pass 1: V_hat into out, lo_part[block] = the block's largest lo
 __global__ void __launch_bounds__(256) k_vtotal_value(const float* __restrict__ vx,
                                                       const float* __restrict__ vy,
@@ -244,12 +273,11 @@ __global__ void __launch_bounds__(256) k_vtotal_value(const float* __restrict__ 
   __shared__ float s_lo[8];
   const float el[3] = {__double2float_rd(e0), __double2float_rd(e1), __double2float_rd(e2)};
   float lo = 0.0f;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const float x = vx[i], y = vy[i], z = vz[i];
+  const bool vec = aligned16(vx, vy, vz, out);
+  vtotal_points(vx, vy, vz, N, vec, [&](uint64_t i, float x, float y, float z) {
     out[i] = vtotal_f32(x, y, z);
     lo = fmaxf(lo, vtotal_bound_lo(x, y, z, el));
-  }
+  });
 #pragma unroll
   for (int o = 16; o; o >>= 1) lo = fmaxf(lo, __shfl_xor_sync(HP_FULL, lo, o));
   if ((threadIdx.x & 31) == 0) s_lo[threadIdx.x >> 5] = lo;
@@ -297,15 +325,14 @@ __global__ void __launch_bounds__(256) k_vtotal_bound(const float* __restrict__ 
   for (int k = 0; k < 8; k++) T = fmaxf(T, s_t[k]);
   const float eh[3] = {__double2float_ru(e0), __double2float_ru(e1), __double2float_ru(e2)};
   unsigned long long bb = 0, bi = ~0ull;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const float x = vx[i], y = vy[i], z = vz[i];
+  const bool vec = aligned16(vx, vy, vz, nullptr);
+  vtotal_points(vx, vy, vz, N, vec, [&](uint64_t i, float x, float y, float z) {
     if (!(vtotal_bound_hi(x, y, z, eh) < T)) {  // a candidate (a NaN bracket too)
       const unsigned long long b =
           (unsigned long long)__double_as_longlong(vtotal_point_bound(x, y, z, e0, e1, e2));
       if (bi == ~0ull || b > bb) bb = b, bi = i;  // a thread's points ascend: keep the first
     }
-  }
+  });
   vtotal_warp_best(bb, bi);
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) s_b[w] = bb, s_i[w] = bi;
