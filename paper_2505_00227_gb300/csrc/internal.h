@@ -363,9 +363,13 @@ void launch_vtotal_range(const float* vx, const float* vy, const float* vz, uint
 uint32_t vtotal_bound_blocks(uint64_t N);
 // bytes of the scratch `best` of launch_vtotal_bound (8-byte aligned)
 uint64_t vtotal_bound_scratch(uint64_t N);
+// a 3-double slot inside that scratch for a caller's data error bounds
+double* vtotal_bound_e(unsigned long long* best, uint64_t N);
 // out = V_hat; best[0] = bits of the largest pointwise bound, best[1] = its
-// first point (best holds vtotal_bound_scratch(N) bytes)
+// first point (best holds vtotal_bound_scratch(N) bytes).  e: device
+// addresses of the three data error bounds, read when the kernels run.
 void launch_vtotal_bound(const float* vx, const float* vy, const float* vz, uint64_t N,
-                         const double e[3], float* out, unsigned long long* best, cstream s);
+                         const double* const e[3], float* out, unsigned long long* best,
+                         cstream s);
 
 }  // namespace hp

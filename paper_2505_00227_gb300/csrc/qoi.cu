@@ -266,11 +266,12 @@ __device__ __forceinline__ bool aligned16(const void* a, const void* b, const vo
 __global__ void __launch_bounds__(256) k_vtotal_value(const float* __restrict__ vx,
                                                       const float* __restrict__ vy,
                                                       const float* __restrict__ vz, uint64_t N,
-                                                      double e0, double e1, double e2,
-                                                      float* __restrict__ out,
+                                                      const double* e0p, const double* e1p,
+                                                      const double* e2p, float* __restrict__ out,
                                                       float* __restrict__ lo_part) {
   hp::pdl_enter();
   __shared__ float s_lo[8];
+  const double e0 = *e0p, e1 = *e1p, e2 = *e2p;
   const float el[3] = {__double2float_rd(e0), __double2float_rd(e1), __double2float_rd(e2)};
   float lo = 0.0f;
   const bool vec = aligned16(vx, vy, vz, out);
@@ -308,11 +309,13 @@ __device__ __forceinline__ void vtotal_warp_best(unsigned long long& bb, unsigne
 __global__ void __launch_bounds__(256) k_vtotal_bound(const float* __restrict__ vx,
                                                       const float* __restrict__ vy,
                                                       const float* __restrict__ vz, uint64_t N,
-                                                      double e0, double e1, double e2,
+                                                      const double* e0p, const double* e1p,
+                                                      const double* e2p,
                                                       const float* __restrict__ lo_part,
                                                       uint32_t nparts,
                                                       unsigned long long* __restrict__ best) {
   hp::pdl_enter();
+  const double e0 = *e0p, e1 = *e1p, e2 = *e2p;
   __shared__ unsigned long long s_b[8], s_i[8];
   __shared__ float s_t[8];
   float T = 0.0f;
@@ -367,10 +370,17 @@ __global__ void __launch_bounds__(256) k_vtotal_bound_final(unsigned long long* 
 
 uint32_t vtotal_bound_blocks(uint64_t N) { return qoi_grid(N, 4); }
 
-uint64_t vtotal_bound_scratch(uint64_t N) { return 24ull * vtotal_bound_blocks(N); }
+// best[2 g] (u64), the blocks' lower bounds lo_part[g] (float), then 32 bytes
+// for a caller's copy of e[3] (vtotal_bound_e)
+uint64_t vtotal_bound_scratch(uint64_t N) { return 24ull * vtotal_bound_blocks(N) + 32; }
+
+double* vtotal_bound_e(unsigned long long* best, uint64_t N) {
+  return reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(best) + 24ull * vtotal_bound_blocks(N));
+}
 
 void launch_vtotal_bound(const float* vx, const float* vy, const float* vz, uint64_t N,
-                         const double e[3], float* out, unsigned long long* best, cstream s) {
+                         const double* const e[3], float* out, unsigned long long* best,
+                         cstream s) {
   const uint32_t g = vtotal_bound_blocks(N);
   float* lo_part = reinterpret_cast<float*>(best + 2 * (size_t)g);
   hp::note_launch(), hp::launch_pdl(k_vtotal_value, g, 256, 0, s, vx, vy, vz, N, e[0], e[1], e[2],

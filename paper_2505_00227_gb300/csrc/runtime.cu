@@ -1386,10 +1386,59 @@ extern "C" hpmdr_status hpmdr_retrieve_qoi_vtotal(hpmdr_ctx* ctx, hpmdr_handle* 
     for (int it = 1; it <= 4096 && st == HPMDR_OK; it++) {
       bool full = true;
       uint64_t fetched = 0;
+      // With three distinct handles the retrievals and the bound are enqueued back
+      // to back: the bound kernels read each variable's error estimate from its
+      // selection record, and one wait brings back the records, the statuses and
+      // the bound.  A handle given twice has one record, which its second
+      // retrieval overwrites: then each record is read right after its retrieval
+      // and the estimates are copied into the bound's own slots.
+      const bool distinct = v[0] != v[1] && v[0] != v[2] && v[1] != v[2];
+      RetrieveDev rdh[3];
+      int32_t msth[3] = {0, 0, 0};
+      bool ok = true;
+      for (int i = 0; i < 3 && st == HPMDR_OK && ok; i++) {
+        st = enqueue_retrieve(ctx, v[i], eps[i], 1, comp[i], s);
+        if (st == HPMDR_OK && !distinct)
+          ok = cudaMemcpyAsync(&rdh[i], v[i]->d_rd, sizeof(RetrieveDev), cudaMemcpyDeviceToHost,
+                               s) == cudaSuccess &&
+               cudaMemcpyAsync(&msth[i], &v[i]->d_meta->status, 4, cudaMemcpyDeviceToHost, s) ==
+                   cudaSuccess &&
+               cudaStreamSynchronize(s) == cudaSuccess;
+      }
+      if (st) break;
+      double* d_e = vtotal_bound_e(d_best, N);
+      if (!distinct && ok) {
+        const double eh[3] = {rdh[0].E_abs, rdh[1].E_abs, rdh[2].E_abs};
+        ok = cudaMemcpyAsync(d_e, eh, 24, cudaMemcpyHostToDevice, s) == cudaSuccess;
+      }
+      const double* const ep[3] = {
+          distinct ? &v[0]->d_rd->E_abs : d_e, distinct ? &v[1]->d_rd->E_abs : d_e + 1,
+          distinct ? &v[2]->d_rd->E_abs : d_e + 2};
+      if (ok)
+        launch_vtotal_bound((const float*)comp[0], (const float*)comp[1], (const float*)comp[2],
+                            N, ep, (float*)d_q, d_best, s);
+      unsigned long long best[2];
+      ok = ok && cudaGetLastError() == cudaSuccess &&
+           cudaMemcpyAsync(best, d_best, 16, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+      for (int i = 0; i < 3 && ok && distinct; i++)
+        ok = cudaMemcpyAsync(&rdh[i], v[i]->d_rd, sizeof(RetrieveDev), cudaMemcpyDeviceToHost,
+                             s) == cudaSuccess &&
+             cudaMemcpyAsync(&msth[i], &v[i]->d_meta->status, 4, cudaMemcpyDeviceToHost, s) ==
+                 cudaSuccess;
+      if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
+        st = HPMDR_ERR_CUDA;
+        break;
+      }
       for (int i = 0; i < 3 && st == HPMDR_OK; i++) {
+        if (msth[i]) {
+          st = (hpmdr_status)msth[i];
+          break;
+        }
+        patch_retrieve_bytes(ctx, v[i], rdh[i], v[i]->prof_lv, v[i]->prof_decode,
+                             v[i]->prof_small, v[i]->small_end);
         hpmdr_retrieve_info inf;
-        if ((st = enqueue_retrieve(ctx, v[i], eps[i], 1, comp[i], s))) break;
-        hpmdr_status r = collect_info(ctx, v[i], &inf, s);
+        fill_info(v[i], rdh[i], &inf);
+        const hpmdr_status r = (hpmdr_status)rdh[i].status;
         if (r != HPMDR_OK && r != HPMDR_ERR_UNATTAINABLE) {
           st = r;
           break;
@@ -1402,14 +1451,6 @@ extern "C" hpmdr_status hpmdr_retrieve_qoi_vtotal(hpmdr_ctx* ctx, hpmdr_handle* 
         fetched += inf.bytes_fetched_total;
       }
       if (st) break;
-      launch_vtotal_bound((const float*)comp[0], (const float*)comp[1], (const float*)comp[2], N,
-                          E, (float*)d_q, d_best, s);
-      unsigned long long best[2];
-      if (cudaMemcpyAsync(best, d_best, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) {
-        st = HPMDR_ERR_CUDA;
-        break;
-      }
       double bmax;
       memcpy(&bmax, &best[0], 8);
       const double bound = bmax * (1.0 + 0x1p-40);
@@ -2324,10 +2365,13 @@ extern "C" hpmdr_status hpmdr_qoi_vtotal_bound(hpmdr_ctx* ctx, const float* vx, 
   const cudaStream_t s = ctx->stream;
   unsigned long long* d_best = nullptr;
   HP_TRY(ctx->A.alloc((void**)&d_best, vtotal_bound_scratch(n), s));
-  launch_vtotal_bound(vx, vy, vz, n, e, out, d_best, s);
+  double* d_e = vtotal_bound_e(d_best, n);
+  const double* const ep[3] = {d_e, d_e + 1, d_e + 2};
   unsigned long long best[2] = {0, 0};
   hpmdr_status st = HPMDR_OK;
-  if (cudaGetLastError() != cudaSuccess ||
+  if (cudaMemcpyAsync(d_e, e, 24, cudaMemcpyHostToDevice, s) != cudaSuccess) st = HPMDR_ERR_CUDA;
+  if (st == HPMDR_OK) launch_vtotal_bound(vx, vy, vz, n, ep, out, d_best, s);
+  if (st != HPMDR_OK || cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(best, d_best, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     st = HPMDR_ERR_CUDA;

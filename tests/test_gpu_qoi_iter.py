@@ -67,3 +67,28 @@ def test_mape_without_threshold_is_ma(B):
         h.reset()
     _, mape, _ = ctx.retrieve_qoi_vtotal(hs, 1e-4, B.EST_MAPE, c=math.inf)
     assert ma.iterations == mape.iterations and list(ma.prefix) == list(mape.prefix)
+
+
+@pytest.mark.parametrize("est", ["EST_MA", "EST_CP"])
+def test_repeated_handle_matches_oracle(B, est):
+    """The same handle for two components (vx = vy): its one selection record
+    serves both retrievals of an iteration, which take the per-retrieval path.
+    A reconstruction depends only on the bound, so the decisions, components and
+    V_hat equal the oracle's on three separate fields."""
+    shape = (20, 24, 64)
+    a, _, c = _triplet(shape, 76)
+    v = [a, a, c]
+    ctx = B.Context()
+    da, dc = torch.from_numpy(a).cuda(), torch.from_numpy(c).cuda()
+    ha, hc = ctx.refactor(da), ctx.refactor(dc)
+    hs = [ha, ha, hc]
+    ctx.prepare_vtotal(hs, da, da, dc)
+    outs = [torch.empty(shape, dtype=torch.float32, device="cuda") for _ in range(3)]
+    q, rep, st = ctx.retrieve_qoi_vtotal(hs, 1e-4, getattr(B, est), outs=outs)
+    lo, hi = O.vtotal_range(*v)
+    ost, oouts, oq, orep = O.qoi_vtotal([O.Field(x) for x in v], lo, hi, 1e-4, getattr(O, est))
+    assert st == ost and rep.iterations == orep.iterations and rep.est == orep.est
+    assert list(rep.prefix) == list(orep.prefix) and list(rep.eps) == list(orep.eps)
+    for o, r in zip(outs, oouts):
+        assert np.array_equal(o.cpu().numpy().view(np.uint32), r.view(np.uint32))
+    assert np.array_equal(q.cpu().numpy().view(np.uint32), oq.view(np.uint32))
