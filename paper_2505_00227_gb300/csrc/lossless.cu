@@ -62,10 +62,12 @@ __device__ __forceinline__ void load_chunk(const uint8_t* __restrict__ src, uint
 // (a byte differing from its predecessor, the chunk's first byte always), and
 // only a segment's last run can reach 129 bytes, so its length comes from the
 // first run start of the following segments (a block-wide suffix minimum).
-// Zero bytes are counted with a word trick and added to the histogram once.
-// The histogram has four interleaved copies (bin v of copy c at word 4 v + c,
-// lane l updating copy l & 3): lanes of different copies never share a bank, so
-// a warp's atomic update needs fewer passes than with one copy per warp.
+// Zero bytes are not counted one by one: the zero bin is the chunk's length
+// less the other bins.  The histogram has four interleaved copies (bin v of copy
+// c at word 4 v + c, lane l updating copy l & 3): lanes of different copies
+// never share a bank, so a warp's atomic update needs fewer passes than with one
+// copy per warp.  The work per byte is integer issue, so the inner loops keep
+// it to a shift and a mask for the bin's byte offset.
 __device__ __forceinline__ void chunk_stats_unit(const uint8_t* __restrict__ planes,
                                                      const FieldMeta* __restrict__ meta,
                                                      const uint32_t* __restrict__ chunk_group,
@@ -76,13 +78,16 @@ __device__ __forceinline__ void chunk_stats_unit(const uint8_t* __restrict__ pla
   __shared__ __align__(16) uint32_t hist[4 * 256];
   __shared__ uint32_t s_first[256], s_wmin[8];
   __shared__ uint8_t s_last[256];
-  __shared__ uint32_t red[8];
+  __shared__ uint32_t red[16];
   const uint32_t c = c_unit, t = threadIdx.x;
   const int lane = t & 31, w = t >> 5;
   if (meta->status) return;
   ChunkRef r = chunk_ref(meta, chunk_group, c);
   for (int i = t; i < 4 * 256; i += blockDim.x) hist[i] = 0;
-  uint32_t* const hc = hist + (lane & 3);  // this lane's copy: bin v at hc[4 v]
+  const uint32_t lo4 = 4u * (lane & 3);  // byte offset of this lane's copy: bin v at 16 v + lo4
+  auto bump = [&](uint32_t off16, uint32_t n) {  // off16 = 16 v, v > 0
+    atomicAdd(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(hist) + (off16 | lo4)), n);
+  };
   const uint8_t* src = planes + r.gm->plane_off + r.start;
   const uint32_t a = 64 * t, b = min(r.len, a + 64u), nb = b > a ? b - a : 0u;
   uint32_t wv[16];
@@ -105,43 +110,47 @@ __device__ __forceinline__ void chunk_stats_unit(const uint8_t* __restrict__ pla
       wv[k] = x;
     }
   }
-  if (nb) s_last[t] = (uint8_t)(wv[(nb - 1) / 4] >> (8 * ((nb - 1) % 4)));
+  if (nb) {  // the segment's last byte (a select over the words keeps wv in registers)
+    const uint32_t kl = (nb - 1) / 4;
+    uint32_t lw = wv[15];
+#pragma unroll
+    for (int k = 0; k < 15; k++) lw = (uint32_t)k == kl ? wv[k] : lw;
+    s_last[t] = (uint8_t)(lw >> (8 * ((nb - 1) % 4)));
+  }
   __syncthreads();
   // run starts and histogram
   uint64_t mask = 0;
-  uint32_t zeros = 0;
   if (nb == 64) {  // whole segment: a word at a time
     uint32_t pb = t > 0 ? s_last[t - 1] : 0u;
+    uint32_t mlo = 0, mhi = 0;  // run starts of bytes 0..31 and 32..63
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       const uint32_t x = wv[k];
-      if ((x | pb) == 0) {  // four zero bytes after a zero byte: no run starts
-        zeros += 4;
-        continue;
-      }
+      if ((x | pb) == 0) continue;  // four zero bytes after a zero byte: no run starts
       const uint32_t d = x ^ ((x << 8) | pb);  // each byte against its predecessor
       const uint32_t nz = (((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d) & 0x80808080u;
-      // bits 7, 15, 23, 31 gathered to bits 0..3 (the partial products never overlap)
-      mask |= (uint64_t)((((nz >> 7) * 0x204081u) >> 21) & 0xfu) << (4 * k);
+      // bits 7, 15, 23, 31 to bits 28..31 (the partial products never overlap)
+      const uint32_t g = (nz * 0x204081u) >> 28;
+      if (k < 8) mlo |= g << (4 * k);
+      else mhi |= g << (4 * (k - 8));
       pb = x >> 24;
-      zeros += __popc(~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu));
       if ((nz & 0x80808000u) == 0) {  // four equal bytes: one update
-        if (x & 0xffu) atomicAdd(&hc[4 * (x & 0xffu)], 4u);
+        if (x & 0xffu) bump((x << 4) & 0xff0u, 4u);
       } else {
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-          const uint32_t v = (x >> (8 * q)) & 0xffu;
-          if (v) atomicAdd(&hc[4 * v], 1u);
+          const uint32_t off = (q == 0 ? x << 4 : x >> (8 * q - 4)) & 0xff0u;
+          if (off) bump(off, 1u);
         }
       }
     }
+    mask = (uint64_t)mhi << 32 | mlo;
     if (t == 0) mask |= 1ull;  // the chunk's first byte starts a run
   } else {
     uint32_t prev = (t > 0 && nb) ? s_last[t - 1] : 0x100u;  // 0x100: the chunk start
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       const uint32_t x = wv[k];
-      const uint32_t zm = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);  // 0x80 per zero byte
 #pragma unroll
       for (int q = 0; q < 4; q++) {
         const uint32_t idx = 4 * k + q;
@@ -149,13 +158,11 @@ __device__ __forceinline__ void chunk_stats_unit(const uint8_t* __restrict__ pla
           const uint32_t v = (x >> (8 * q)) & 0xffu;
           if (v != prev) mask |= 1ull << idx;
           prev = v;
-          if (v) atomicAdd(&hc[4 * v], 1u);
+          if (v) bump(16u * v, 1u);
         }
       }
-      zeros += __popc(zm & (k * 4 + 4 <= nb ? 0xffffffffu : (k * 4 < nb ? (0xffffffffu >> (32 - 8 * (nb - 4 * k))) : 0u)));
     }
   }
-  if (zeros) atomicAdd(&hc[0], zeros);
   // first run start of each segment, suffix minimum over the following segments
   const uint32_t INF = 0xffffffffu;
   uint32_t f = mask ? a + (uint32_t)(__ffsll((long long)mask) - 1) : INF;
@@ -180,18 +187,22 @@ __device__ __forceinline__ void chunk_stats_unit(const uint8_t* __restrict__ pla
     if (next - last >= 129u) cost += 1;
   }
   __syncthreads();
-  {  // the group's histogram is the sum over its chunks (integer atomics: exact)
-    uint32_t s = 0;
-    const uint4 h = reinterpret_cast<const uint4*>(hist)[t];  // the four copies of bin t
-    s = h.x + h.y + h.z + h.w;
-    if (s) atomicAdd(&group_hist[(size_t)r.gi * 256 + t], s);
+  uint32_t nzb;  // the group's histogram is the sum over its chunks (integer atomics: exact)
+  {
+    const uint4 h = reinterpret_cast<const uint4*>(hist)[t];  // the four copies of bin t (0 for t = 0)
+    nzb = h.x + h.y + h.z + h.w;
+    if (nzb) atomicAdd(&group_hist[(size_t)r.gi * 256 + t], nzb);
   }
-  for (int o = 16; o; o >>= 1) cost += __shfl_xor_sync(HP_FULL, cost, o);
-  if (lane == 0) red[w] = cost;
+  for (int o = 16; o; o >>= 1) {
+    cost += __shfl_xor_sync(HP_FULL, cost, o);
+    nzb += __shfl_xor_sync(HP_FULL, nzb, o);
+  }
+  if (lane == 0) red[w] = cost, red[8 + w] = nzb;
   __syncthreads();
   if (t == 0) {
-    uint32_t s = 0;
-    for (int k = 0; k < 8; k++) s += red[k];
+    uint32_t s = 0, nonzero = 0;
+    for (int k = 0; k < 8; k++) s += red[k], nonzero += red[8 + k];
+    if (r.len > nonzero) atomicAdd(&group_hist[(size_t)r.gi * 256], r.len - nonzero);  // zero bytes
     chunk_cost[c] = s;
     atomicAdd(&group_cost[r.gi], (unsigned long long)s);
   }
