@@ -1379,9 +1379,10 @@ __device__ void rle_decode_chunk(const uint8_t* __restrict__ stored, const Group
       uint32_t e = t;
       if (t >= a_next) {
         nout = 0;  // a record from the previous segment covers this one
-      } else if (t - a < 3 && val[t - a]) {
-        nout = outp[t - a];
-        e = endp[t - a];
+      } else if (t - a < 3 && (t == a ? val[0] : t == a + 1 ? val[1] : val[2])) {
+        // selects, not an index, keep the three parses in registers
+        nout = t == a ? outp[0] : t == a + 1 ? outp[1] : outp[2];
+        e = t == a ? endp[0] : t == a + 1 ? endp[1] : endp[2];
       } else {  // not one of the three phases (or malformed): parse again from t
         uint32_t s = t, out = 0;
         while (s < a_next) {
