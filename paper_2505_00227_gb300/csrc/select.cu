@@ -368,7 +368,8 @@ __global__ void __launch_bounds__(256) k_select(FieldMeta* m, double tau, int ta
   hp::pdl_enter();
   extern __shared__ __align__(16) unsigned char sel_smem[];
   FieldMeta* sm = reinterpret_cast<FieldMeta*>(sel_smem);
-  constexpr uint32_t N16 = sizeof(FieldMeta) / 16, N8 = (sizeof(FieldMeta) % 16) / 8;
+  constexpr uint32_t N16 = sizeof(FieldMeta) / 16;
+  static_assert(sizeof(FieldMeta) % 16 == 0, "the copy moves whole 16-byte units");
   const uint4* src = reinterpret_cast<const uint4*>(m);
   uint4* dst = reinterpret_cast<uint4*>(sm);
   for (uint32_t i0 = 0; i0 < N16; i0 += 8 * blockDim.x) {
@@ -384,9 +385,6 @@ __global__ void __launch_bounds__(256) k_select(FieldMeta* m, double tau, int ta
       if (i < N16) dst[i] = v[u];
     }
   }
-  if (threadIdx.x < N8)
-    reinterpret_cast<uint64_t*>(sm)[2 * N16 + threadIdx.x] =
-        reinterpret_cast<const uint64_t*>(m)[2 * N16 + threadIdx.x];
   __syncthreads();
   if (threadIdx.x < 32) select_prefix(sm, m, tau, tau_is_abs, rd, &hs);
 }
