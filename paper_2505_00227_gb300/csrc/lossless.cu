@@ -649,11 +649,11 @@ __device__ __forceinline__ void huff_encode_unit(const uint8_t* __restrict__ pla
   const uint8_t* src = planes + r.gm->plane_off + r.start;
   const uint32_t a = t * 64u, nb = r.len > a ? min(r.len - a, 64u) : 0u;
   uint32_t wv[16];
-  if (nb == 64) {
+  if (nb == 64) {  // cached loads: the code pass below reads the segment again
     const uint4* s4 = reinterpret_cast<const uint4*>(src + a);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      const uint4 v = __ldcs(s4 + k);
+      const uint4 v = __ldg(s4 + k);
       wv[4 * k] = v.x;
       wv[4 * k + 1] = v.y;
       wv[4 * k + 2] = v.z;
@@ -705,18 +705,33 @@ __device__ __forceinline__ void huff_encode_unit(const uint8_t* __restrict__ pla
       wd++;
     }
   };
+  if (nb == 64) {
+    // a whole segment: four 16-byte words per iteration, re-read from L1, so the
+    // appends are not unrolled 64 times (the unrolled form missed the
+    // instruction cache)
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + a);
+#pragma unroll 1
+    for (int j = 0; j < 4; j++) {
+      const uint4 v = __ldg(s4 + j);
+      const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    if (zfast && wv[k] == 0 && 4u * k + 3 < nb) {
-      put(z4, (int)z4len);
-      continue;
-    }
+      for (int u = 0; u < 4; u++) {
+        if (zfast && ws[u] == 0) {
+          put(z4, (int)z4len);
+          continue;
+        }
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      if (4u * k + q < nb) {
-        const uint32_t sym = (wv[k] >> (8 * q)) & 0xffu;
-        put(code[sym], (int)len[sym]);
+        for (int q = 0; q < 4; q++) {
+          const uint32_t sym = (ws[u] >> (8 * q)) & 0xffu;
+          put(code[sym], (int)len[sym]);
+        }
       }
+    }
+  } else {  // the ragged end of a group: bytes re-read one by one, up to nb
+#pragma unroll 1
+    for (uint32_t b = 0; b < nb; b++) {
+      const uint32_t sym = src[a + b];
+      put(code[sym], (int)len[sym]);
     }
   }
   if (nacc > 0 && bits > 0) atomicOr(&outw[wd], (uint32_t)(acc >> 32));  // shared with the next
