@@ -252,35 +252,60 @@ __device__ void huffman_lengths_block(const uint64_t* f_in, uint8_t* len_out, ui
     if (t == 0) s_max = 0;
     __syncthreads();
     if (n > 1) {
-      if (t == 0) {
-        // two-queue merge: leaves in (freq, symbol) order, internal nodes in
-        // creation order; the heads of both queues stay in registers
-        for (int i = 0; i < n; i++) w[i] = f[sorted[i]];
-        int nl = 0, ni = n, created = n;
-        uint64_t lw = w[0], iw = 0;
-        for (int step = 0; step < n - 1; step++) {
-          uint64_t sum = 0;
-#pragma unroll
-          for (int k = 0; k < 2; k++) {
-            const bool leaf_ok = nl < n, int_ok = ni < created;
-            int pick;
-            if (leaf_ok && (!int_ok || lw <= iw)) {
-              pick = nl++;
-              sum += lw;
-              lw = nl < n ? w[nl] : 0;
-            } else {
-              pick = ni++;
-              sum += iw;
-              iw = ni < created ? w[ni] : 0;
-            }
-            parent[pick] = created;
+      // The two-queue merge (leaves in (freq, symbol) order, internal nodes in
+      // creation order, a leaf first on equal weights) consumes the items in the
+      // order of the stable merge M of the leaves and the internal nodes, two per
+      // step: internal j = M[2j] + M[2j+1].  That is a fixed point in the
+      // internal weights, found here in parallel instead of by one thread.
+      // Started from +inf, the iterates stay sorted (pair sums of a sorted
+      // sequence) and no smaller than the true weights, and after r rounds the
+      // first r internal weights are exact: the loop ends by round n at the
+      // latest, with the merge positions of the exact weights.
+      __shared__ uint64_t s_m[512];
+      const uint64_t INF = ~0ull;
+      uint64_t* L = w;        // leaves w[0, n)
+      uint64_t* I = w + 256;  // internal nodes w[256, 256 + n - 1)
+      if (t < n) L[t] = f[sorted[t]];
+      if (t < n - 1) I[t] = INF;
+      __syncthreads();
+      int pl = 0, pi = 0;  // merge positions of leaf t and internal node t
+      for (int r = 0; r < n; r++) {
+        if (t < n) {  // leaf t follows t leaves and the internal nodes lighter than it
+          const uint64_t x = L[t];
+          int lo = 0, hi = n - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (I[mid] < x) lo = mid + 1;
+            else hi = mid;
           }
-          w[created] = sum;
-          if (ni == created) iw = sum;  // the internal queue was empty: new head
-          created++;
+          pl = t + lo;
+          s_m[pl] = x;
         }
-        parent[created - 1] = created - 1;  // the root
+        if (t < n - 1) {  // internal t follows t internal nodes and the leaves not heavier
+          const uint64_t y = I[t];
+          int lo = 0, hi = n;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (L[mid] <= y) lo = mid + 1;
+            else hi = mid;
+          }
+          pi = t + lo;
+          s_m[pi] = y;
+        }
+        __syncthreads();
+        bool changed = false;
+        if (t < n - 1) {
+          const uint64_t a = s_m[2 * t], b = s_m[2 * t + 1];
+          const uint64_t v = (a == INF || b == INF) ? INF : a + b;
+          changed = v != I[t];
+          I[t] = v;  // read only by thread t until the barrier below
+        }
+        if (!__syncthreads_or(changed ? 1 : 0)) break;
       }
+      // node ids: leaf i = i, internal node j = n + j; the item at merge
+      // position p hangs under internal node p / 2; the last one is the root
+      if (t < n) parent[t] = n + (pl >> 1);
+      if (t < n - 1) parent[n + t] = t == n - 2 ? n + t : n + (pi >> 1);
       __syncthreads();
       // depths by pointer jumping: d(v) accumulates along doubling ancestor links
       const int nodes = 2 * n - 1;
