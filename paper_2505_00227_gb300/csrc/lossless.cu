@@ -227,7 +227,7 @@ void launch_chunk_stats(const uint8_t* planes, FieldMeta* meta, ChunkMap cm, uin
 }
 
 // -------------------------------------------- Algorithm 2 decision per group
-// Huffman code lengths by the two-queue construction (leaves by (freq,
+// Huffman code lengths of the two-queue construction (leaves by (freq,
 // symbol), a leaf wins a weight tie, internal nodes in creation order), capped
 // at 16 by halving the counts and rebuilding.
 __device__ void huffman_lengths_block(const uint64_t* f_in, uint8_t* len_out, uint64_t* f,
